@@ -1,0 +1,334 @@
+"""Benchmark: Metropolis updates/s of GPU population annealing.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (one GPU): the large-population run — 3D +-1 Edwards-Anderson spin
+glass, L = 10 (1000 sites), R = 10^6 replicas, temperature steps chosen to hold
+the culling fraction at 0.272 up to beta = 5, 10 sweeps per step.  A "step" is
+one temperature step of the whole hot path: reweight, copy numbers + scan +
+parents, parent gather + 10 Metropolis sweeps + energy levels/histogram, family
+statistics.  The 2 GB double-buffered population is far larger than L2, so no
+flush is needed between steps.
+
+value   = Metropolis site updates (sum over timed steps of S N R~_t) / device time
+e2e     = the same metric through the public C ABI with a host read of every
+          step's observables (pa_step + pa_observables), transfers counted by the
+          library
+roofline: the sweep kernel (dominant), integer-ALU bound, see the design notes
+cpu_baseline: the CPU oracle (OpenMP over replicas) on a bounded sample.
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+(weak scaling, no collective on the data path); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Metropolis updates/s (L=10,R=1e6)"
+UNIT = "updates/s"
+# Integer instructions that one Philox4x32-10 word costs at least: each of the 10
+# rounds does two 32x32->64 multiplies and two 3-input XORs for four words.
+INT_OPS_PER_UPDATE = 10.0
+INT32_LANES_PER_SM = 128
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sweep_L10_R1e6_adaptive.txt")
+SWEEP_SOURCE = os.path.join(ROOT, "paper_1711_02146_gb300", "csrc", "pa_sweep.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def oracle_updates_per_s(w, R_sample: int, min_seconds: float, max_steps: int, n_threads: int):
+    """Times the oracle as it stands on the first temperature steps of workload w
+    with R reduced to R_sample; returns (updates/s, steps, seconds)."""
+    import oracle
+    oracle.build()
+    run = oracle.Run(oracle.RunConfig(L=w.L, R=R_sample, disorder_seed=w.disorder_seed, run_seed=w.run_seed,
+                                      betas=w.betas, n_temps=w.n_temps, beta_max=w.beta_max,
+                                      eps_target=w.eps_target, n_sweeps=w.n_sweeps, n_pop=w.n_pop,
+                                      n_threads=n_threads))
+    updates, steps = 0, 0
+    t0 = time.perf_counter()
+    while steps < max_steps:
+        if run.step() != 0:
+            break
+        steps += 1
+        updates += w.n_sweeps * w.N * run.obs(run.t)["R_tilde"] * w.n_pop
+        if time.perf_counter() - t0 >= min_seconds:
+            break
+    dt = time.perf_counter() - t0
+    return updates / dt, steps, dt
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1711_02146_gb300.workloads import C3
+    cores = os.cpu_count() or 1
+    R_sample = 4000
+    import oracle
+    oracle.build()
+    run = oracle.Run(oracle.RunConfig(L=C3.L, R=R_sample, disorder_seed=C3.disorder_seed, run_seed=C3.run_seed,
+                                      n_temps=C3.n_temps, beta_max=C3.beta_max, eps_target=C3.eps_target,
+                                      n_sweeps=C3.n_sweeps, n_threads=cores))
+    for _ in range(args.warmup):
+        run.step()
+    updates = 0
+    t0 = time.perf_counter()
+    steps = 0
+    for _ in range(args.steps):
+        if run.step() != 0:
+            break
+        steps += 1
+        updates += C3.n_sweeps * C3.N * run.obs(run.t)["R_tilde"]
+    dt = time.perf_counter() - t0
+    value = updates / dt
+    sample = (f"oracle, first {args.warmup}+{steps} temperature steps of the L=10 adaptive (eps=0.272) run "
+              f"with R reduced to {R_sample}; {cpu_model()}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+            "config": {"workload": C3.name, "L": C3.L, "R": R_sample, "eps_target": C3.eps_target,
+                       "n_sweeps": C3.n_sweeps},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def profile_traffic():
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was taken
+    on the current sweep kernel source (else None)."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    digest = hashlib.sha256(open(SWEEP_SOURCE, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(PROFILE_SUMMARY):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("sweep_source_sha256_16") != digest:
+        return None
+    try:
+        return float(vals["dram_bytes_per_full_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (there is no CPU fallback)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1711_02146_gb300 import build, pa
+    from paper_1711_02146_gb300.workloads import C3
+    build.build()
+    w = C3.with_(run_seed=C3.run_seed + 7919 * rank)
+    stream = torch.cuda.Stream()
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+
+    run = pa.Run.from_workload(w, stream=stream)
+    for _ in range(args.warmup):
+        run.step()
+    run.sync()
+    run.stats_reset(timing=True)
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        start.record(stream)
+        done = 0
+        for _ in range(args.steps):
+            if run.step() != 0:
+                break
+            done += 1
+        end.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = start.elapsed_time(end)
+    st = run.stats()
+    updates = st["updates"]
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        u = torch.tensor([updates], device="cuda", dtype=torch.float64)
+        dist.all_reduce(u)
+        updates = float(u.item())
+    value = updates / (ms / 1e3)
+
+    # e2e: the same steps through the public API, reading every step's observables back
+    e2e = None
+    if not run.t >= run.n_temps - 1:
+        run.stats_reset(timing=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n_e2e = 0
+        for _ in range(args.steps):
+            if run.step() != 0:
+                break
+            run.obs(run.t)
+            n_e2e += 1
+        dt = time.perf_counter() - t0
+        s2 = run.stats()
+        if n_e2e:
+            e2e = {"value": s2["updates"] / dt, "unit": UNIT,
+                   "h2d_bytes_per_step": s2["h2d_bytes"] // n_e2e, "d2h_bytes_per_step": s2["d2h_bytes"] // n_e2e,
+                   "steps": n_e2e, "api": "pa_step + pa_observables per step"}
+
+    clk = clocks.summary()
+    sweep_ms = st["phase_ms"]["sweep"] / max(st["phase_count"]["sweep"], 1)
+    updates_per_launch = st["updates"] / max(st["phase_count"]["sweep"], 1)
+    sm_mhz = clk["sm_mhz"] if clk else 2070.0
+    peak = n_sm * INT32_LANES_PER_SM * sm_mhz * 1e6 / 1e12       # Tera int32 ops/s
+    achieved = updates_per_launch * INT_OPS_PER_UPDATE / (sweep_ms / 1e3) / 1e12
+    traffic = profile_traffic()
+    if traffic is not None:
+        traffic = traffic * updates_per_launch / (w.n_sweeps * w.N * w.R)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tint32op/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "k_sweep<10,32,640>",
+                "launch_ms": sweep_ms, "updates_per_launch": updates_per_launch,
+                "peak_basis": f"{n_sm} SMs x {INT32_LANES_PER_SM} int32 lanes x {sm_mhz:.0f} MHz "
+                              f"({'median sampled under load' if clk else 'max clock, no samples'})",
+                "ops_per_update": INT_OPS_PER_UPDATE}
+    phase_share = {k: v / max(ms, 1e-9) for k, v in st["phase_ms"].items()}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": done,
+            "warmup": args.warmup, "ms_per_step": ms / max(done, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+            "config": {"workload": w.name, "L": w.L, "R": w.R, "eps_target": w.eps_target, "beta_max": w.beta_max,
+                       "n_sweeps": w.n_sweeps, "steps_timed": f"temperature steps {args.warmup + 1}.."
+                                                              f"{args.warmup + done}",
+                       "l2": "inputs larger than L2 (2 GB double-buffered int8 population)"},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": st["kernel_launches"],
+            "phase_share": phase_share, "clocks": clk}
+    run.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        v, steps, dt = oracle_updates_per_s(C3, R_sample=20000, min_seconds=10.0, max_steps=5, n_threads=cores)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"first {steps} temperature steps of the same run with R=2e4 "
+                                          f"({dt:.1f} s, {cpu_model()})"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/* pa.h — C ABI of the GB300 population annealing library (libpa.so).
+ *
+ * Population annealing (PA) as defined by Amey & Machta, "Analysis and
+ * Optimization of Population Annealing" (§II): a population of R replicas of a
+ * 3D Edwards-Anderson spin glass (L^3 sites, periodic, +-1 couplings J_nm) is
+ * cooled from beta = 0 through a schedule beta_0 < beta_1 < ...; each step
+ *   1. resamples beta_{t-1} -> beta_t: replica i gets n_i copies with
+ *      E n_i = tau_i = (R / R~) exp(-(beta_t - beta_{t-1}) E_i) / Q   (Eqs. tau, Q)
+ *      by the nearest-integer rule (n_i = floor or ceil of tau_i),
+ *   2. runs S_t checkerboard Metropolis sweeps at beta_t,
+ *   3. measures the estimators of §II.A and §III.A: energy moments, the free
+ *      energy -beta F~ (Eq. betaF), ground-state estimators (Eq. g0), family
+ *      statistics rho_t (Eq. rho_t_def2) and the family entropy, and the spin
+ *      overlap q histogram of two independent populations.
+ * The temperature schedule is either given, or chosen step by step to hold the
+ * expected culling fraction of Eq. (eq_num_elim) at a target (§IV.B).
+ *
+ * Every step of the path runs in CUDA kernels for sm_103a on the stream given
+ * at creation.  All pointers in this header are HOST pointers unless stated
+ * otherwise.  Functions never throw; they return a status code.
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed by (seed, purpose,
+ * population) and countered by (site, sweep, slot, step), so every result is a
+ * deterministic function of the configuration, independent of launch shapes.
+ *
+ * Conventions: site n = x + L (y + L z); bond (n, d) joins n and n + e_d; the
+ * energy level of a replica is k = (E + 3N) / 2 = its number of unsatisfied
+ * bonds; step t = 0 is beta = 0 (the paper indexes the schedule downwards).
+ */
+#ifndef PA_H
+#define PA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define PA_OK 0
+#define PA_DONE 1            /* pa_step: the schedule is complete, nothing was done */
+#define PA_ERR_INVALID (-1)  /* bad argument or configuration */
+#define PA_ERR_NOMEM (-2)    /* device or host allocation failed */
+#define PA_ERR_CAPACITY (-3) /* population outgrew R_cap (detected on the device; nothing written out of bounds) */
+#define PA_ERR_TIMEOUT (-4)  /* a bounded device wait gave up */
+#define PA_ERR_CUDA (-5)     /* a CUDA runtime call failed */
+#define PA_ERR_STATE (-6)    /* call out of order, e.g. a step that has not run yet */
+#define PA_ERR_EXTINCT (-7)  /* every replica received zero copies */
+
+/* ---- configuration of one run (§II; schedule §IV.B) ----
+ * L            lattice size; even, 2 <= L <= 16.
+ * n_pop        1, or 2 independent populations on the same couplings (for q).
+ * R            target population size, 1 <= R.
+ * R_cap        hard capacity of the population arrays (0 = R + 10 ceil(sqrt R) + 1024);
+ *              R <= R_cap < 2^31.
+ * disorder_seed, run_seed   < 2^56; couplings come from disorder_seed, spins,
+ *              Metropolis and resampling from run_seed (population index in the key).
+ * n_temps, betas  explicit schedule betas[0..n_temps) ascending with betas[0] = 0;
+ *              or betas = NULL for the adaptive schedule, with n_temps the step
+ *              limit, beta_max the last temperature and eps_target in (0,1) the
+ *              culling fraction to hold.
+ * n_sweeps, sweeps_per_step   sweeps of step t: sweeps_per_step[t] if non-NULL
+ *              (n_temps entries), else n_sweeps.  Step 0 never sweeps.
+ * q_bins       overlap histogram bins over q in [-1, 1] (odd, >= 3; 65 typical).
+ * The configuration and the arrays it points to are copied by pa_create. */
+typedef struct {
+  int32_t L;
+  int32_t n_pop;
+  int64_t R;
+  int64_t R_cap;
+  uint64_t disorder_seed;
+  uint64_t run_seed;
+  int32_t n_temps;
+  const double* betas;
+  double beta_max;
+  double eps_target;
+  int32_t n_sweeps;
+  const int32_t* sweeps_per_step;
+  int32_t q_bins;
+} pa_config;
+
+/* ---- observables of one population at step t (after the sweeps at beta_t) ----
+ * The resampling fields describe the move beta_{t-1} -> beta_t (zero at t = 0). */
+typedef struct {
+  int32_t t;
+  double beta, dbeta;
+  int64_t R_tilde;        /* population size R~_t */
+  int64_t sum_E, sum_E2;  /* exact sums of E and E^2 over the population */
+  int32_t E_min;          /* lowest energy in the population */
+  double mean_E, var_E;   /* population mean and variance of E */
+  int32_t kmin_prev;      /* lowest level of the step t-1 population */
+  double S_prime;         /* sum_i exp(-dbeta (E_i - E_min)) over the step t-1 population */
+  double lnQ;             /* ln Q(beta_{t-1}, beta_t), Eq. (Q) */
+  double minus_beta_F;    /* -beta_t F~(beta_t), Eq. (betaF) */
+  double eps_expected;    /* expected culling fraction, Eq. (eq_num_elim) / R */
+  int64_t culled;         /* replicas of step t-1 that received zero copies */
+  int64_t sum_eta2;       /* sum over families of eta^2 */
+  int64_t n_families;     /* families with at least one member */
+  double rho_t;           /* sum eta^2 / R~_t */
+  double S_f;             /* family entropy -sum nu ln nu, nu = eta / R~_t */
+  double rho_s;           /* R~_t / exp(S_f) */
+  int32_t E0;             /* lowest energy measured at steps 0..t */
+  double g0_tilde;        /* fraction of the population at E0 */
+  double g0_bar;          /* 2 exp(-beta E0 + beta F~), Eq. (g0) */
+  int64_t q_pairs;        /* overlap pairs (slot j of population 0 with slot j of 1) */
+  int64_t q_abs_le_02;    /* pairs with |q| <= 0.2 */
+  double I02;             /* q_abs_le_02 / q_pairs, the per-sample I(0.2) */
+} pa_obs;
+
+typedef struct pa_ctx pa_ctx;
+
+/* Creates a run: allocates its device memory (owned by the context), draws the
+ * couplings and the initial population (uniform spins, label = slot) with
+ * kernels on `cuda_stream` (a cudaStream_t; NULL = the legacy default stream)
+ * and measures step 0.  Returns PA_OK and *out, or an error (and *out = NULL). */
+int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out);
+
+/* Runs the next temperature step (resample, sweep, measure).  Asynchronous for
+ * an explicit schedule; the adaptive schedule reads the previous energy
+ * histogram back to the host to choose beta_t.  Returns PA_OK, PA_DONE when the
+ * schedule is complete, or an error recorded by an earlier step. */
+int pa_step(pa_ctx* ctx);
+
+/* Runs all remaining steps and synchronises; returns PA_OK or the first error. */
+int pa_run(pa_ctx* ctx);
+
+/* Index of the last step run (0 right after pa_create). */
+int32_t pa_current_step(const pa_ctx* ctx);
+
+/* Synchronises and fills *out for step t <= pa_current_step and population pop. */
+int pa_observables(pa_ctx* ctx, int32_t t, int32_t pop, pa_obs* out);
+
+/* Energy-level histogram c_t(k), k = 0..3N, of population pop at step t
+ * (out: 3N+1 int64 entries; cap = capacity of out in entries). */
+int pa_energy_hist(pa_ctx* ctx, int32_t t, int32_t pop, int64_t* out, int64_t cap);
+
+/* Overlap histogram of step t: bin b = ((Q + N)(q_bins - 1) + N) div 2N of
+ * Q = sum_n s^0_n s^1_n (two populations only; out: q_bins int64 entries). */
+int pa_q_hist(pa_ctx* ctx, int32_t t, int64_t* out, int64_t cap);
+
+/* Family-size histogram of the current population: *n pairs (eta[i], m[i]),
+ * eta ascending, m[i] = number of families of size eta[i].  Returns
+ * PA_ERR_CAPACITY (with *n set) if cap is too small. */
+int pa_family_hist(pa_ctx* ctx, int32_t pop, int64_t cap, int64_t* eta, int64_t* m, int64_t* n);
+
+/* Population size of pop at the current step. */
+int pa_population_size(pa_ctx* ctx, int32_t pop, int64_t* count);
+
+/* Copies slots [first, first + n) of population pop: spins replica-major
+ * [n][N] int8 (+1/-1), family labels and energies E (each may be NULL). */
+int pa_get_replicas(pa_ctx* ctx, int32_t pop, int64_t first, int64_t n, int8_t* spins, int32_t* labels,
+                    int32_t* energies);
+
+/* Copy numbers n_i of the old slots in the last resampling (*count = R~_{t-1})
+ * and the parent (old slot) of every new slot (*count = R~_t).  PA_ERR_STATE at step 0. */
+int pa_get_copy_counts(pa_ctx* ctx, int32_t pop, int32_t* counts, int64_t cap, int64_t* count);
+int pa_get_parents(pa_ctx* ctx, int32_t pop, int32_t* parents, int64_t cap, int64_t* count);
+
+/* Couplings J[3n + d] = +1/-1 (3N int8 entries). */
+int pa_get_couplings(pa_ctx* ctx, int8_t* J, int64_t cap);
+
+/* Inverse temperature of step t (t <= pa_current_step), or a negative value. */
+double pa_beta(const pa_ctx* ctx, int32_t t);
+
+/* ---- instrumentation ----
+ * Counters since the last pa_stats_reset: steps run, kernels launched by the
+ * library, bytes copied host->device and device->host (by this context), and,
+ * when timing is enabled, device time per phase measured with CUDA events
+ * recorded on the run's stream around each phase of every step:
+ *   PA_PHASE_REWEIGHT  Boltzmann reweighting tables (one block per population)
+ *   PA_PHASE_RESAMPLE  copy numbers, scan, parents and labels
+ *   PA_PHASE_SWEEP     parent gather + Metropolis sweeps + energy levels
+ *   PA_PHASE_FAMILY    family sizes, sum eta^2, family entropy
+ *   PA_PHASE_OVERLAP   overlap histogram (two populations only)
+ * pa_get_stats synchronises the stream. */
+#define PA_PHASE_REWEIGHT 0
+#define PA_PHASE_RESAMPLE 1
+#define PA_PHASE_SWEEP 2
+#define PA_PHASE_FAMILY 3
+#define PA_PHASE_OVERLAP 4
+#define PA_N_PHASES 5
+typedef struct {
+  int64_t steps;
+  int64_t kernel_launches;
+  int64_t h2d_bytes;
+  int64_t d2h_bytes;
+  int64_t updates;                 /* Metropolis site updates: sum over steps of S_t N R~_t */
+  double phase_ms[PA_N_PHASES];    /* summed device time per phase (timing enabled) */
+  int64_t phase_count[PA_N_PHASES];/* timed launches of each phase */
+} pa_stats;
+int pa_stats_reset(pa_ctx* ctx, int enable_timing);
+int pa_get_stats(pa_ctx* ctx, pa_stats* out);
+
+/* Waits for the context's stream; returns the first recorded error, if any. */
+int pa_sync(pa_ctx* ctx);
+
+/* Frees the context and its device memory (synchronises first). */
+int pa_destroy(pa_ctx* ctx);
+
+/* Static description of a status code. */
+const char* pa_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PA_H */

@@ -1,0 +1,84 @@
+// pa_internal.h — structures shared by the host runtime (pa_runtime.cpp) and
+// the kernels (pa_kernels.cu, pa_sweep.cu).  Plain C++ (no CUDA types) so the
+// runtime can be compiled by the host compiler alone.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+namespace pa {
+
+// Random-stream purposes (4 bits above the seed in the Philox key).
+enum Purpose : uint32_t { kCouplings = 0, kInit = 1, kMetropolis = 2, kResample = 3 };
+
+// Device status flags (OR-ed into one word by the kernels).
+enum StatusFlag : int32_t { kFlagCapacity = 1, kFlagExtinct = 2, kFlagTimeout = 4 };
+
+// Per-step, per-population record written by the kernels.
+struct StepRec {
+  int32_t R_tilde;      // population size after resampling into step t
+  int32_t R_prev;       // population size of step t-1
+  int32_t kmin_prev;    // lowest occupied level of step t-1
+  int32_t culled;       // old replicas that received zero copies
+  double S_prime;       // sum_k c_{t-1}(k) w(k - kmin)
+  double eps_expected;  // (1/R) sum_k c(k) (1 - tau_k)_+
+  unsigned long long sum_eta2;
+  unsigned long long n_families;
+  double nu_ln_nu;      // sum over families of nu ln nu, nu = eta / R~
+  unsigned long long q_pairs;   // population 0 only
+  unsigned long long q_small;   // population 0 only: pairs with 5|Q| <= N
+  int32_t S_t;          // sweeps done at this step
+  int32_t pad;
+};
+
+// Device buffers of one population.
+struct PopDev {
+  int8_t* spins[2];     // [N][pitch] int8 +1/-1, site-major (replicas contiguous)
+  int32_t* labels[2];   // [R_cap] family labels
+  int32_t* levels;      // [pitch] energy level k of each slot of the current population
+  int32_t* counts;      // [R_cap] copy numbers of the old slots
+  int32_t* parents;     // [R_cap] parent (old slot) of each new slot
+  int32_t* blocksums;   // [n_count_blocks] per-block copy totals, then their exclusive scan
+  uint32_t* hist;       // [n_temps][n_levels] energy-level histograms
+  int32_t* fl;          // [n_levels] floor(tau_k)
+  uint32_t* thr;        // [n_levels] 2^32 frac(tau_k)
+  int32_t* famcnt;      // [R] members per family label
+  int32_t* mhist;       // [R_cap + 1] number of families of each size
+  double* partials;     // [n_entropy_blocks] fixed-order partial sums of nu ln nu
+  StepRec* rec;         // [n_temps]
+  uint32_t key_met[2];
+  uint32_t key_res[2];
+  uint32_t key_init[2];
+};
+
+// Geometry of one run.
+struct RunGeom {
+  int32_t L, N, n_levels;
+  int64_t pitch;        // bytes per site row of the spin arrays (multiple of 128)
+  int32_t R;            // target population
+  int32_t R_cap;
+  int32_t n_pop;
+  int32_t q_bins;
+  int32_t n_count_blocks;    // resampling blocks (1024 slots each)
+  int32_t n_entropy_blocks;  // family-entropy reduction blocks
+};
+
+constexpr int kCountThreads = 256;     // threads per resampling block
+constexpr int kSlotsPerCountBlock = 1024;
+constexpr int kEntropyThreads = 256;
+constexpr int kEntropyPerBlock = 4096;
+
+// ---- launchers (pa_kernels.cu / pa_sweep.cu); each returns a cudaError_t as int ----
+int launch_init_couplings(const RunGeom& g, uint64_t disorder_seed, int8_t* J, uint32_t* jtab, void* stream);
+int launch_init_population(const RunGeom& g, PopDev* pops, int cur, void* stream);
+int launch_levels_and_hist(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, int t, void* stream);
+int launch_reweight(const RunGeom& g, PopDev* pops, const double* w, int t, void* stream);
+int launch_resample(const RunGeom& g, PopDev* pops, int cur, int t, int32_t* status, void* stream);
+int launch_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, int t, int n_sweeps,
+                 const uint32_t met_thr[3], void* stream);
+int launch_families(const RunGeom& g, PopDev* pops, int cur, int t, void* stream);
+int launch_overlap(const RunGeom& g, PopDev* pops, int cur, int t, unsigned long long* qhist, void* stream);
+// Largest lattice size the sweep kernel supports.
+constexpr int kMaxL = 16;
+bool sweep_supported(int L);
+
+}  // namespace pa

@@ -1,0 +1,476 @@
+// pa_kernels.cu — initialisation, reweighting, resampling, family and overlap
+// kernels of the population annealing step (Amey & Machta, §II, §III.A).
+//
+// Spin storage: int8 +1 (0x01) / -1 (0xFF), site-major: row n holds all slots of
+// site n contiguously (pitch bytes), so one 32-bit word carries four replicas
+// of one site.  For two spins a, b of that encoding a ^ b is 0x00 when equal and
+// 0xFE when different; XOR with a coupling mask (0xFE for J = -1, else 0) gives
+// 0xFE exactly for an unsatisfied bond, and bit 1 of each byte counts it.
+#include <cuda_runtime.h>
+
+#include "pa_device.cuh"
+#include "pa_internal.h"
+
+namespace pa {
+
+struct PopArgs {
+  PopDev p[2];
+};
+
+static PopArgs pack(const PopDev* pops, int n_pop) {
+  PopArgs a;
+  for (int i = 0; i < n_pop && i < 2; ++i) a.p[i] = pops[i];
+  return a;
+}
+
+constexpr uint32_t kBit1 = 0x02020202u;
+
+// ---------------------------------------------------------------- init (a0)
+
+// Couplings J(n, d) = +1 if bit 0 of Philox word d at counter (n, 0, 0, 0) is 0.
+// jtab[4n + d] is the XOR mask of the forward bond (n, d).
+__global__ void k_init_couplings(int N, uint32_t k0, uint32_t k1, int8_t* J, uint32_t* jtab) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const uint4 r = philox4x32_10(make_uint4((uint32_t)n, 0u, 0u, 0u), k0, k1);
+  const uint32_t w[3] = {r.x, r.y, r.z};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const bool neg = (w[d] & 1u) != 0;
+    J[3 * n + d] = neg ? (int8_t)-1 : (int8_t)1;
+    jtab[4 * n + d] = neg ? 0xFEFEFEFEu : 0u;
+  }
+  jtab[4 * n + 3] = 0u;
+}
+
+// Initial spins: slot j at site n is +1 if bit 0 of word (j & 3) of Philox at
+// counter (n, 0, j >> 2, 0) is 0, else -1.  Slots >= R are padded with +1.
+__global__ void k_init_population(RunGeom g, PopArgs a, int cur) {
+  const int pop = blockIdx.y;
+  const PopDev& P = a.p[pop];
+  const int64_t words = g.pitch / 4;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= words * g.N) return;
+  const int n = (int)(gid / words);
+  const uint32_t wi = (uint32_t)(gid % words);
+  const uint4 r = philox4x32_10(make_uint4((uint32_t)n, 0u, wi, 0u), P.key_init[0], P.key_init[1]);
+  uint32_t out = 0;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int64_t j = 4 * (int64_t)wi + b;
+    const uint32_t byte = (j < g.R && (word_of(r, b) & 1u)) ? 0xFFu : 0x01u;
+    out |= byte << (8 * b);
+  }
+  reinterpret_cast<uint32_t*>(P.spins[cur] + (size_t)n * g.pitch)[wi] = out;
+  if (n == 0) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int64_t j = 4 * (int64_t)wi + b;
+      if (j < g.R) P.labels[cur][j] = (int32_t)j;
+    }
+  }
+  if (n == 0 && wi == 0) P.rec[0].R_tilde = g.R;
+}
+
+// Energy level (unsatisfied bonds) of every slot from scratch, and the level
+// histogram of step t.  One thread per word (four replicas).
+__global__ void k_levels_and_hist(RunGeom g, PopArgs a, int cur, const uint32_t* __restrict__ jtab, int t) {
+  const int pop = blockIdx.y;
+  const PopDev& P = a.p[pop];
+  const int R = P.rec[t].R_tilde;
+  const int wi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (4 * wi >= R) return;
+  const int L = g.L;
+  const uint32_t* S = reinterpret_cast<const uint32_t*>(P.spins[cur]);
+  const int64_t pw = g.pitch / 4;
+  int cnt[4] = {0, 0, 0, 0};
+  uint32_t acc = 0;
+  int since = 0;
+  for (int n = 0; n < g.N; ++n) {
+    const int x = n % L, y = (n / L) % L, z = n / (L * L);
+    const int nx = (x + 1 == L ? 0 : x + 1) + L * (y + L * z);
+    const int ny = x + L * ((y + 1 == L ? 0 : y + 1) + L * z);
+    const int nz = x + L * (y + L * (z + 1 == L ? 0 : z + 1));
+    const uint32_t s = S[n * pw + wi];
+    acc += ((s ^ S[nx * pw + wi] ^ jtab[4 * n + 0]) & kBit1) + ((s ^ S[ny * pw + wi] ^ jtab[4 * n + 1]) & kBit1) +
+           ((s ^ S[nz * pw + wi] ^ jtab[4 * n + 2]) & kBit1);
+    if (++since == 40) {
+#pragma unroll
+      for (int b = 0; b < 4; ++b) cnt[b] += (acc >> (8 * b)) & 0xFFu;
+      acc = 0;
+      since = 0;
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < 4; ++b) cnt[b] += (acc >> (8 * b)) & 0xFFu;
+  uint32_t* hist = P.hist + (size_t)t * g.n_levels;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int j = 4 * wi + b;
+    if (j < R) {
+      const int k = cnt[b] >> 1;
+      P.levels[j] = k;
+      atomicAdd(&hist[k], 1u);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- reweight (a4)
+
+// One block per population.  From the level histogram c of step t-1 and the
+// weights w[j] = exp(-dbeta 2j) (computed on the host in FP64):
+//   S' = sum_{k >= kmin} c(k) w[k - kmin]         (ascending k, separate mul/add)
+//   tau_k = R w[k - kmin] / S'  ->  fl_k = floor(tau_k), thr_k = 2^32 (tau_k - fl_k)
+//   eps = (1/R) sum_k c(k) (1 - tau_k)_+          (Eq. eq_num_elim)
+// Empty levels add exact zeros to both sums, so they are skipped.
+__global__ void k_reweight(RunGeom g, PopArgs a, const double* __restrict__ w, int t) {
+  extern __shared__ int lst[];  // n_levels entries: occupied levels, ascending
+  __shared__ int scratch[33];
+  __shared__ double S_sh;
+  const PopDev& P = a.p[blockIdx.x];
+  const uint32_t* c = P.hist + (size_t)(t - 1) * g.n_levels;
+  int base = 0;
+  for (int k0 = 0; k0 < g.n_levels; k0 += blockDim.x) {
+    const int k = k0 + threadIdx.x;
+    const int f = (k < g.n_levels && c[k] > 0u) ? 1 : 0;
+    int tot;
+    const int pos = block_exclusive_scan(f, scratch, &tot);
+    if (f) lst[base + pos] = k;
+    base += tot;
+  }
+  __syncthreads();
+  const int nnz = base;
+  if (nnz == 0) return;  // cannot happen: the population is never empty here
+  const int kmin = lst[0];
+  if (threadIdx.x == 0) {
+    double S = 0.0;
+    for (int i = 0; i < nnz; ++i) {
+      const int k = lst[i];
+      S = __dadd_rn(S, __dmul_rn((double)c[k], w[k - kmin]));
+    }
+    S_sh = S;
+  }
+  __syncthreads();
+  const double S = S_sh;
+  const double Rd = (double)g.R;
+  for (int k = threadIdx.x; k < g.n_levels; k += blockDim.x) {
+    int f = 0;
+    uint32_t th = 0u;
+    if (k >= kmin) {
+      const double tau = __ddiv_rn(__dmul_rn(Rd, w[k - kmin]), S);
+      const double fl = floor(tau);
+      f = (int)fl;
+      th = (uint32_t)__dmul_rn(__dsub_rn(tau, fl), 4294967296.0);
+    }
+    P.fl[k] = f;
+    P.thr[k] = th;
+  }
+  if (threadIdx.x == 0) {
+    double eps = 0.0;
+    for (int i = 0; i < nnz; ++i) {
+      const int k = lst[i];
+      const double tau = __ddiv_rn(__dmul_rn(Rd, w[k - kmin]), S);
+      if (tau < 1.0) eps = __dadd_rn(eps, __dmul_rn((double)c[k], __dsub_rn(1.0, tau)));
+    }
+    StepRec& r = P.rec[t];
+    r.S_prime = S;
+    r.eps_expected = __ddiv_rn(eps, Rd);
+    r.kmin_prev = kmin;
+    r.R_prev = P.rec[t - 1].R_tilde;
+  }
+}
+
+// ---------------------------------------------------------------- resampling (a5, a6)
+
+// Copy numbers: n_i = fl(k_i) + [r_i < thr(k_i)], r_i = word (i & 3) of Philox at
+// counter (i >> 2, 0, 0, t) — the nearest-integer rule of §II.  Each block
+// covers 1024 old slots (four per thread) and stores its total.
+__global__ void __launch_bounds__(kCountThreads) k_counts(RunGeom g, PopArgs a, int t) {
+  __shared__ int red[kCountThreads / 32];
+  const PopDev& P = a.p[blockIdx.y];
+  const int R_old = P.rec[t - 1].R_tilde;
+  const int i0 = blockIdx.x * kSlotsPerCountBlock + 4 * threadIdx.x;
+  int sum = 0, cul = 0;
+  if (i0 < R_old) {
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)(i0 >> 2), 0u, 0u, (uint32_t)t), P.key_res[0], P.key_res[1]);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = i0 + b;
+      if (i < R_old) {
+        const int k = P.levels[i];
+        const int n = P.fl[k] + (word_of(r, b) < P.thr[k] ? 1 : 0);
+        P.counts[i] = n;
+        sum += n;
+        cul += (n == 0);
+      }
+    }
+  }
+  sum = warp_sum(sum);
+  cul = warp_sum(cul);
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = sum;
+    if (cul) atomicAdd(&P.rec[t].culled, cul);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int i = 0; i < kCountThreads / 32; ++i) s += red[i];
+    P.blocksums[blockIdx.x] = s;
+  }
+}
+
+// Exclusive scan of the block totals (one block per population); the grand
+// total is the new population size R~_t.  A total above R_cap sets the capacity
+// flag and is clamped so that no later kernel writes out of bounds.
+__global__ void k_scan_blocks(RunGeom g, PopArgs a, int t, int32_t* status) {
+  __shared__ int scratch[33];
+  const PopDev& P = a.p[blockIdx.x];
+  long long carry = 0;
+  for (int b0 = 0; b0 < g.n_count_blocks; b0 += blockDim.x) {
+    const int b = b0 + threadIdx.x;
+    const int v = b < g.n_count_blocks ? P.blocksums[b] : 0;
+    int tot;
+    const int ex = block_exclusive_scan(v, scratch, &tot);
+    const long long off = carry + ex;
+    if (b < g.n_count_blocks) P.blocksums[b] = off > 0x7fffffffLL ? 0x7fffffff : (int)off;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) {
+    int R_new = carry > g.R_cap ? g.R_cap : (int)carry;
+    if (carry > g.R_cap) atomicOr(status, kFlagCapacity);
+    if (carry == 0) atomicOr(status, kFlagExtinct);
+    P.rec[t].R_tilde = R_new;
+  }
+}
+
+// New population: slot offsets[i] + q (q < n_i) takes old slot i as parent and
+// inherits its family label, so labels stay sorted along the slots.
+__global__ void __launch_bounds__(kCountThreads) k_scatter(RunGeom g, PopArgs a, int cur, int t) {
+  __shared__ int scratch[33];
+  const PopDev& P = a.p[blockIdx.y];
+  const int R_old = P.rec[t - 1].R_tilde;
+  const int i0 = blockIdx.x * kSlotsPerCountBlock + 4 * threadIdx.x;
+  int n[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int b = 0; b < 4; ++b)
+    if (i0 + b < R_old) n[b] = P.counts[i0 + b];
+  const int local = n[0] + n[1] + n[2] + n[3];
+  long long off = (long long)block_exclusive_scan(local, scratch, nullptr) + P.blocksums[blockIdx.x];
+  const int32_t* lab_old = P.labels[cur];
+  int32_t* lab_new = P.labels[1 - cur];
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int i = i0 + b;
+    for (int q = 0; q < n[b]; ++q) {
+      const long long j = off + q;
+      if (j < g.R_cap) {
+        P.parents[j] = i;
+        lab_new[j] = lab_old[i];
+      }
+    }
+    off += n[b];
+  }
+}
+
+// ---------------------------------------------------------------- families (a7)
+
+// Members per label (warp-aggregated: sorted labels make equal labels adjacent).
+__global__ void k_fam_count(RunGeom g, PopArgs a, int cur, int t) {
+  const PopDev& P = a.p[blockIdx.y];
+  const int R_new = P.rec[t].R_tilde;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int l = j < R_new ? P.labels[cur][j] : -1;
+  const unsigned peers = __match_any_sync(0xffffffffu, l);
+  if (l >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&P.famcnt[l], __popc(peers));
+}
+
+// sum eta^2, alive families, and the family-size histogram m(eta).
+__global__ void k_fam_reduce(RunGeom g, PopArgs a, int t) {
+  __shared__ unsigned long long red[2][32];
+  const PopDev& P = a.p[blockIdx.y];
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long s2 = 0, nf = 0;
+  if (l < g.R) {
+    const int eta = P.famcnt[l];
+    if (eta > 0) {
+      s2 = (unsigned long long)eta * (unsigned long long)eta;
+      nf = 1;
+      atomicAdd(&P.mhist[eta], 1);
+    }
+  }
+  s2 = warp_sum(s2);
+  nf = warp_sum(nf);
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wp] = s2;
+    red[1][wp] = nf;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long a2 = 0, an = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      a2 += red[0][i];
+      an += red[1][i];
+    }
+    if (a2) atomicAdd(&P.rec[t].sum_eta2, a2);
+    if (an) atomicAdd(&P.rec[t].n_families, an);
+  }
+}
+
+// Fixed-order partial sums of m(eta) nu ln nu, nu = eta / R~ (the family
+// entropy is S_f = -sum): each block covers kEntropyPerBlock sizes, each thread
+// a contiguous run of them, then a fixed tree.
+__global__ void __launch_bounds__(kEntropyThreads) k_fam_entropy(RunGeom g, PopArgs a, int t) {
+  __shared__ double red[kEntropyThreads];
+  const PopDev& P = a.p[blockIdx.y];
+  const int R_new = P.rec[t].R_tilde;
+  constexpr int per = kEntropyPerBlock / kEntropyThreads;
+  const int e0 = 1 + blockIdx.x * kEntropyPerBlock + threadIdx.x * per;
+  double s = 0.0;
+  for (int i = 0; i < per; ++i) {
+    const int eta = e0 + i;
+    if (eta <= R_new) {
+      const int m = P.mhist[eta];
+      if (m > 0) {
+        const double nu = __ddiv_rn((double)eta, (double)R_new);
+        s = __dadd_rn(s, __dmul_rn((double)m, __dmul_rn(nu, log(nu))));
+      }
+    }
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = kEntropyThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] = __dadd_rn(red[threadIdx.x], red[threadIdx.x + h]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) P.partials[blockIdx.x] = red[0];
+}
+
+__global__ void k_fam_finish(RunGeom g, PopArgs a, int t) {
+  const PopDev& P = a.p[blockIdx.x];
+  if (threadIdx.x != 0) return;
+  double s = 0.0;
+  for (int b = 0; b < g.n_entropy_blocks; ++b) s = __dadd_rn(s, P.partials[b]);
+  P.rec[t].nu_ln_nu = s;
+}
+
+// ---------------------------------------------------------------- overlap (a8)
+
+// q between slot j of population 0 and slot j of population 1, j < min(R~0, R~1):
+// Q = N - 2 (sites that differ); bin = ((Q + N)(B - 1) + N) div 2N.
+__global__ void k_overlap(RunGeom g, PopArgs a, int cur, int t, unsigned long long* qhist) {
+  extern __shared__ unsigned int qh[];
+  __shared__ unsigned int small_sh;
+  const PopDev& A = a.p[0];
+  const PopDev& B = a.p[1];
+  const int pairs = min(A.rec[t].R_tilde, B.rec[t].R_tilde);
+  for (int i = threadIdx.x; i < g.q_bins; i += blockDim.x) qh[i] = 0u;
+  if (threadIdx.x == 0) small_sh = 0u;
+  __syncthreads();
+  const int wi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (4 * wi < pairs) {
+    const uint32_t* SA = reinterpret_cast<const uint32_t*>(A.spins[cur]);
+    const uint32_t* SB = reinterpret_cast<const uint32_t*>(B.spins[cur]);
+    const int64_t pw = g.pitch / 4;
+    int diff[4] = {0, 0, 0, 0};
+    uint32_t acc = 0;
+    int since = 0;
+    for (int n = 0; n < g.N; ++n) {
+      acc += ((SA[n * pw + wi] ^ SB[n * pw + wi]) >> 1) & 0x01010101u;
+      if (++since == 255) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) diff[b] += (acc >> (8 * b)) & 0xFFu;
+        acc = 0;
+        since = 0;
+      }
+    }
+    unsigned int small = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      diff[b] += (acc >> (8 * b)) & 0xFFu;
+      if (4 * wi + b < pairs) {
+        const long long Q = (long long)g.N - 2LL * diff[b];
+        const long long bin = ((Q + g.N) * (long long)(g.q_bins - 1) + g.N) / (2LL * g.N);
+        atomicAdd(&qh[bin], 1u);
+        const long long aq = Q < 0 ? -Q : Q;
+        small += (5 * aq <= g.N) ? 1u : 0u;
+      }
+    }
+    if (small) atomicAdd(&small_sh, small);
+  }
+  __syncthreads();
+  unsigned long long* row = qhist + (size_t)t * g.q_bins;
+  for (int i = threadIdx.x; i < g.q_bins; i += blockDim.x)
+    if (qh[i]) atomicAdd(&row[i], (unsigned long long)qh[i]);
+  if (threadIdx.x == 0) {
+    if (small_sh) atomicAdd(&a.p[0].rec[t].q_small, (unsigned long long)small_sh);
+    if (blockIdx.x == 0) a.p[0].rec[t].q_pairs = (unsigned long long)pairs;
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+
+static inline int grid_for(int64_t n, int per) { return (int)((n + per - 1) / per); }
+
+int launch_init_couplings(const RunGeom& g, uint64_t disorder_seed, int8_t* J, uint32_t* jtab, void* stream) {
+  const uint32_t k0 = (uint32_t)(disorder_seed & 0xffffffffu);
+  const uint32_t k1 = (uint32_t)(disorder_seed >> 32) | (kCouplings << 28);
+  k_init_couplings<<<grid_for(g.N, 128), 128, 0, (cudaStream_t)stream>>>(g.N, k0, k1, J, jtab);
+  return (int)cudaGetLastError();
+}
+
+int launch_init_population(const RunGeom& g, PopDev* pops, int cur, void* stream) {
+  const int64_t total = (g.pitch / 4) * g.N;
+  dim3 grid(grid_for(total, 256), g.n_pop);
+  k_init_population<<<grid, 256, 0, (cudaStream_t)stream>>>(g, pack(pops, g.n_pop), cur);
+  return (int)cudaGetLastError();
+}
+
+int launch_levels_and_hist(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, int t, void* stream) {
+  dim3 grid(grid_for(g.pitch / 4, 128), g.n_pop);
+  k_levels_and_hist<<<grid, 128, 0, (cudaStream_t)stream>>>(g, pack(pops, g.n_pop), cur, jtab, t);
+  return (int)cudaGetLastError();
+}
+
+int launch_reweight(const RunGeom& g, PopDev* pops, const double* w, int t, void* stream) {
+  const size_t smem = sizeof(int) * (size_t)g.n_levels;
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k_reweight, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+  }
+  k_reweight<<<g.n_pop, 1024, smem, (cudaStream_t)stream>>>(g, pack(pops, g.n_pop), w, t);
+  return (int)cudaGetLastError();
+}
+
+int launch_resample(const RunGeom& g, PopDev* pops, int cur, int t, int32_t* status, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  PopArgs a = pack(pops, g.n_pop);
+  dim3 grid(g.n_count_blocks, g.n_pop);
+  k_counts<<<grid, kCountThreads, 0, s>>>(g, a, t);
+  k_scan_blocks<<<g.n_pop, 1024, 0, s>>>(g, a, t, status);
+  k_scatter<<<grid, kCountThreads, 0, s>>>(g, a, cur, t);
+  return (int)cudaGetLastError();
+}
+
+int launch_families(const RunGeom& g, PopDev* pops, int cur, int t, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  PopArgs a = pack(pops, g.n_pop);
+  for (int p = 0; p < g.n_pop; ++p) {
+    cudaMemsetAsync(pops[p].famcnt, 0, sizeof(int32_t) * (size_t)g.R, s);
+    cudaMemsetAsync(pops[p].mhist, 0, sizeof(int32_t) * ((size_t)g.R_cap + 1), s);
+  }
+  k_fam_count<<<dim3(grid_for(g.R_cap, 256), g.n_pop), 256, 0, s>>>(g, a, cur, t);
+  k_fam_reduce<<<dim3(grid_for(g.R, 256), g.n_pop), 256, 0, s>>>(g, a, t);
+  k_fam_entropy<<<dim3(g.n_entropy_blocks, g.n_pop), kEntropyThreads, 0, s>>>(g, a, t);
+  k_fam_finish<<<g.n_pop, 32, 0, s>>>(g, a, t);
+  return (int)cudaGetLastError();
+}
+
+int launch_overlap(const RunGeom& g, PopDev* pops, int cur, int t, unsigned long long* qhist, void* stream) {
+  if (g.n_pop != 2) return 0;
+  const size_t smem = sizeof(unsigned int) * (size_t)g.q_bins;
+  k_overlap<<<grid_for(g.pitch / 4, 256), 256, smem, (cudaStream_t)stream>>>(g, pack(pops, 2), cur, t, qhist);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace pa

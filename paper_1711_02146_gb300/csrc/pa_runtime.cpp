@@ -1,0 +1,702 @@
+// pa_runtime.cpp — host side of the C ABI in include/pa.h.
+//
+// Owns the device memory of a run, launches the step kernels on the run's
+// stream, and finalises observables from the integer records the kernels write.
+// The FP64 host parts of the step are here: the Boltzmann weight table of a
+// temperature move, the Metropolis thresholds, the adaptive schedule (§IV.B)
+// and the estimators of §II.A / §III.A.  Compile with -ffp-contract=off so that
+// every expression rounds as written.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "../../include/pa.h"
+#include "pa_internal.h"
+
+using pa::PopDev;
+using pa::RunGeom;
+using pa::StepRec;
+
+struct pa_ctx {
+  pa_config cfg{};
+  std::vector<double> betas;   // filled as the run advances (adaptive) or at creation
+  std::vector<int32_t> sweeps;
+  bool adaptive = false;
+  RunGeom g{};
+  cudaStream_t stream = nullptr;
+  int t = 0;
+  bool done = false;
+  int cur = 0;
+  int error = PA_OK;
+  int8_t* J = nullptr;          // device [3N]
+  uint32_t* jtab = nullptr;     // device [N][4]
+  int32_t* status = nullptr;    // device flags
+  unsigned long long* qhist = nullptr;  // device [n_temps][q_bins]
+  PopDev pops[2]{};
+  // Boltzmann weight tables exp(-dbeta 2j), one per distinct dbeta (device)
+  std::map<uint64_t, double*> wtables;
+  double* wadapt = nullptr;     // adaptive schedule: the table of the current step
+  std::vector<void*> allocations;
+  // instrumentation (pa_stats)
+  pa_stats stats{};
+  bool timing = false;
+  std::vector<cudaEvent_t> events;                 // pool
+  size_t events_used = 0;
+  struct Timed { int phase; cudaEvent_t start, end; };
+  std::vector<Timed> timed;
+  std::vector<std::pair<int, int>> counted_steps;  // (t, S_t) since the last reset
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? PA_OK : PA_ERR_CUDA; }
+
+int copy_d2h(pa_ctx* c, void* dst, const void* src, size_t bytes) {
+  c->stats.d2h_bytes += (int64_t)bytes;
+  return cuda_status(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+}
+
+int copy_h2d(pa_ctx* c, void* dst, const void* src, size_t bytes) {
+  c->stats.h2d_bytes += (int64_t)bytes;
+  return cuda_status(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice));
+}
+
+cudaEvent_t next_event(pa_ctx* c) {
+  if (c->events_used == c->events.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->events.push_back(e);
+  }
+  return c->events[c->events_used++];
+}
+
+// Records CUDA events on the run's stream around one phase when timing is on.
+struct PhaseTimer {
+  pa_ctx* c;
+  int phase;
+  cudaEvent_t start = nullptr;
+  PhaseTimer(pa_ctx* ctx, int ph, int launches) : c(ctx), phase(ph) {
+    c->stats.kernel_launches += launches;
+    if (c->timing && (start = next_event(c)) != nullptr) cudaEventRecord(start, c->stream);
+  }
+  ~PhaseTimer() {
+    if (!start) return;
+    cudaEvent_t end = next_event(c);
+    if (!end) return;
+    cudaEventRecord(end, c->stream);
+    c->timed.push_back({phase, start, end});
+  }
+};
+
+template <typename T>
+int dalloc(pa_ctx* c, T** p, size_t count) {
+  void* q = nullptr;
+  if (count == 0) count = 1;
+  if (cudaMalloc(&q, sizeof(T) * count) != cudaSuccess) {
+    cudaGetLastError();
+    return PA_ERR_NOMEM;
+  }
+  c->allocations.push_back(q);
+  *p = static_cast<T*>(q);
+  return PA_OK;
+}
+
+void make_key(uint64_t seed, uint32_t purpose, uint32_t pop, uint32_t key[2]) {
+  key[0] = (uint32_t)(seed & 0xffffffffu);
+  key[1] = (uint32_t)(seed >> 32) | (purpose << 28) | (pop << 24);
+}
+
+// Metropolis thresholds floor(2^32 exp(-beta dE)), dE = 4, 8, 12, clamped to 2^32 - 1.
+void metropolis_thresholds(double beta, uint32_t thr[3]) {
+  for (int m = 1; m <= 3; ++m) {
+    double p = std::exp(-(beta * (double)(4 * m)));
+    double v = std::floor(std::ldexp(p, 32));
+    if (v > 4294967295.0) v = 4294967295.0;
+    thr[m - 1] = (uint32_t)v;
+  }
+}
+
+uint64_t bits_of(double x) {
+  uint64_t b;
+  std::memcpy(&b, &x, sizeof b);
+  return b;
+}
+
+// Host table w[j] = exp(-(dbeta * 2j)), j = 0..3N: the Boltzmann weight ratio of
+// a temperature move between a level and the lowest occupied one.
+std::vector<double> host_weights(int n_levels, double dbeta) {
+  std::vector<double> w((size_t)n_levels);
+  for (int j = 0; j < n_levels; ++j) w[(size_t)j] = std::exp(-(dbeta * (double)(2 * j)));
+  return w;
+}
+
+// Device weight table of step t.  Explicit schedules upload one table per
+// distinct dbeta at creation; the adaptive schedule rewrites one buffer after
+// the host has synchronised to choose dbeta (so no kernel still reads it).
+int weight_table(pa_ctx* c, double dbeta, const double** out) {
+  auto it = c->wtables.find(bits_of(dbeta));
+  if (it != c->wtables.end()) {
+    *out = it->second;
+    return PA_OK;
+  }
+  std::vector<double> w = host_weights(c->g.n_levels, dbeta);
+  double* d = nullptr;
+  int rc = PA_OK;
+  if (c->adaptive) {
+    if (!c->wadapt) rc = dalloc(c, &c->wadapt, w.size());
+    d = c->wadapt;
+  } else {
+    rc = dalloc(c, &d, w.size());
+  }
+  if (rc != PA_OK) return rc;
+  rc = copy_h2d(c, d, w.data(), sizeof(double) * w.size());
+  if (rc != PA_OK) return rc;
+  if (!c->adaptive) c->wtables[bits_of(dbeta)] = d;
+  *out = d;
+  return PA_OK;
+}
+
+// Expected culling fraction (1/R) sum_k c(k) (1 - tau_k)_+ of a move by dbeta
+// from level histogram c (occupied levels only; empty ones add exact zeros).
+double culling_fraction(const std::vector<int32_t>& occ, const std::vector<uint32_t>& c, int64_t R, double dbeta) {
+  const int kmin = occ[0];
+  double S = 0.0;
+  for (int k : occ) {
+    double w = std::exp(-(dbeta * (double)(2 * (k - kmin))));
+    S = S + (double)c[(size_t)k] * w;
+  }
+  double eps = 0.0;
+  for (int k : occ) {
+    double w = std::exp(-(dbeta * (double)(2 * (k - kmin))));
+    double tau = ((double)R * w) / S;
+    if (tau < 1.0) eps = eps + (double)c[(size_t)k] * (1.0 - tau);
+  }
+  return eps / (double)R;
+}
+
+// Adaptive step (§IV.B): the largest dbeta in (0, beta_max - beta] whose expected
+// culling fraction does not exceed the target, by 64 bisection halvings;
+// population 0 decides.
+int choose_dbeta(pa_ctx* c, double* dbeta) {
+  const int n = c->g.n_levels;
+  std::vector<uint32_t> h((size_t)n);
+  int rc = cuda_status(cudaStreamSynchronize(c->stream));
+  if (rc == PA_OK) rc = copy_d2h(c, h.data(), c->pops[0].hist + (size_t)(c->t) * n, sizeof(uint32_t) * n);
+  if (rc != PA_OK) return rc;
+  std::vector<int32_t> occ;
+  for (int k = 0; k < n; ++k)
+    if (h[(size_t)k] > 0) occ.push_back(k);
+  if (occ.empty()) return PA_ERR_EXTINCT;
+  const double prev = c->betas[(size_t)c->t];
+  const double rem = c->cfg.beta_max - prev;
+  const double target = c->cfg.eps_target;
+  if (culling_fraction(occ, h, c->cfg.R, rem) <= target) {
+    *dbeta = rem;
+    return PA_OK;
+  }
+  double lo = 0.0, hi = rem;
+  for (int it = 0; it < 64; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (culling_fraction(occ, h, c->cfg.R, mid) <= target)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  *dbeta = lo > 0.0 ? lo : hi;
+  return PA_OK;
+}
+
+int check_device_status(pa_ctx* c) {
+  int32_t flags = 0;
+  int rc = cuda_status(cudaStreamSynchronize(c->stream));
+  if (rc == PA_OK) rc = copy_d2h(c, &flags, c->status, sizeof flags);
+  if (rc != PA_OK) return rc;
+  if (flags & pa::kFlagCapacity) return PA_ERR_CAPACITY;
+  if (flags & pa::kFlagExtinct) return PA_ERR_EXTINCT;
+  if (flags & pa::kFlagTimeout) return PA_ERR_TIMEOUT;
+  return PA_OK;
+}
+
+int fail(pa_ctx* c, int rc) {
+  if (rc != PA_OK && c->error == PA_OK) c->error = rc;
+  return rc;
+}
+
+int launch_rc(int e) { return e == 0 ? PA_OK : PA_ERR_CUDA; }
+
+
+
+// Measurement kernels common to every step: families (and overlap).
+int measure(pa_ctx* c, int t) {
+  int rc;
+  {
+    PhaseTimer pt(c, PA_PHASE_FAMILY, 4);
+    rc = launch_rc(pa::launch_families(c->g, c->pops, c->cur, t, c->stream));
+  }
+  if (rc == PA_OK && c->g.n_pop == 2) {
+    PhaseTimer pt(c, PA_PHASE_OVERLAP, 1);
+    rc = launch_rc(pa::launch_overlap(c->g, c->pops, c->cur, t, c->qhist, c->stream));
+  }
+  return rc;
+}
+
+void destroy(pa_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (void* p : c->allocations) cudaFree(p);
+  for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+  delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pa_strerror(int s) {
+  switch (s) {
+    case PA_OK: return "ok";
+    case PA_DONE: return "schedule complete";
+    case PA_ERR_INVALID: return "invalid argument or configuration";
+    case PA_ERR_NOMEM: return "out of memory";
+    case PA_ERR_CAPACITY: return "population exceeded its capacity R_cap";
+    case PA_ERR_TIMEOUT: return "a bounded device wait timed out";
+    case PA_ERR_CUDA: return "CUDA runtime error";
+    case PA_ERR_STATE: return "call out of order";
+    case PA_ERR_EXTINCT: return "population became empty";
+    default: return "unknown status";
+  }
+}
+
+int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
+  if (!out) return PA_ERR_INVALID;
+  *out = nullptr;
+  if (!cfg) return PA_ERR_INVALID;
+  const int64_t R_cap = cfg->R_cap ? cfg->R_cap : cfg->R + 10 * (int64_t)std::ceil(std::sqrt((double)cfg->R)) + 1024;
+  if (!pa::sweep_supported(cfg->L) || cfg->R < 1 || cfg->n_pop < 1 || cfg->n_pop > 2 || cfg->n_temps < 1 ||
+      R_cap < cfg->R || R_cap >= ((int64_t)1 << 31) - 4096 || cfg->disorder_seed >= ((uint64_t)1 << 56) ||
+      cfg->run_seed >= ((uint64_t)1 << 56) || cfg->q_bins < 3 || cfg->q_bins > 4097 || cfg->n_sweeps < 0)
+    return PA_ERR_INVALID;
+  if (!cfg->betas && !(cfg->eps_target > 0.0 && cfg->eps_target < 1.0 && cfg->beta_max > 0.0)) return PA_ERR_INVALID;
+  if (cfg->betas) {
+    if (cfg->betas[0] != 0.0) return PA_ERR_INVALID;
+    for (int t = 1; t < cfg->n_temps; ++t)
+      if (!(cfg->betas[t] >= cfg->betas[t - 1])) return PA_ERR_INVALID;
+  }
+  if (cfg->sweeps_per_step)
+    for (int t = 0; t < cfg->n_temps; ++t)
+      if (cfg->sweeps_per_step[t] < 0) return PA_ERR_INVALID;
+
+  pa_ctx* c = new (std::nothrow) pa_ctx();
+  if (!c) return PA_ERR_NOMEM;
+  c->cfg = *cfg;
+  c->cfg.R_cap = R_cap;
+  c->adaptive = cfg->betas == nullptr;
+  c->betas.assign((size_t)cfg->n_temps, 0.0);
+  c->sweeps.assign((size_t)cfg->n_temps, cfg->n_sweeps);
+  for (int t = 0; t < cfg->n_temps; ++t) {
+    if (cfg->betas) c->betas[(size_t)t] = cfg->betas[t];
+    if (cfg->sweeps_per_step) c->sweeps[(size_t)t] = cfg->sweeps_per_step[t];
+  }
+  c->cfg.betas = nullptr;
+  c->cfg.sweeps_per_step = nullptr;
+  c->stream = (cudaStream_t)cuda_stream;
+
+  RunGeom& g = c->g;
+  g.L = cfg->L;
+  g.N = cfg->L * cfg->L * cfg->L;
+  g.n_levels = 3 * g.N + 1;
+  g.pitch = ((R_cap + 127) / 128) * 128;
+  g.R = (int32_t)cfg->R;
+  g.R_cap = (int32_t)R_cap;
+  g.n_pop = cfg->n_pop;
+  g.q_bins = cfg->q_bins;
+  g.n_count_blocks = (int32_t)((R_cap + pa::kSlotsPerCountBlock - 1) / pa::kSlotsPerCountBlock);
+  g.n_entropy_blocks = (int32_t)((R_cap + pa::kEntropyPerBlock - 1) / pa::kEntropyPerBlock);
+  const size_t T = (size_t)cfg->n_temps;
+
+  int rc = PA_OK;
+  rc = rc ? rc : dalloc(c, &c->J, (size_t)3 * g.N);
+  rc = rc ? rc : dalloc(c, &c->jtab, (size_t)4 * g.N);
+  rc = rc ? rc : dalloc(c, &c->status, 1);
+  rc = rc ? rc : dalloc(c, &c->qhist, T * (size_t)g.q_bins);
+  for (int p = 0; p < g.n_pop && rc == PA_OK; ++p) {
+    PopDev& P = c->pops[p];
+    for (int b = 0; b < 2 && rc == PA_OK; ++b) {
+      rc = dalloc(c, &P.spins[b], (size_t)g.N * (size_t)g.pitch);
+      rc = rc ? rc : dalloc(c, &P.labels[b], (size_t)g.pitch);
+    }
+    rc = rc ? rc : dalloc(c, &P.levels, (size_t)g.pitch);
+    rc = rc ? rc : dalloc(c, &P.counts, (size_t)g.pitch);
+    rc = rc ? rc : dalloc(c, &P.parents, (size_t)g.pitch);
+    rc = rc ? rc : dalloc(c, &P.blocksums, (size_t)g.n_count_blocks);
+    rc = rc ? rc : dalloc(c, &P.hist, T * (size_t)g.n_levels);
+    rc = rc ? rc : dalloc(c, &P.fl, (size_t)g.n_levels);
+    rc = rc ? rc : dalloc(c, &P.thr, (size_t)g.n_levels);
+    rc = rc ? rc : dalloc(c, &P.famcnt, (size_t)g.R);
+    rc = rc ? rc : dalloc(c, &P.mhist, (size_t)R_cap + 1);
+    rc = rc ? rc : dalloc(c, &P.partials, (size_t)g.n_entropy_blocks);
+    rc = rc ? rc : dalloc(c, &P.rec, T);
+    make_key(cfg->run_seed, pa::kMetropolis, (uint32_t)p, P.key_met);
+    make_key(cfg->run_seed, pa::kResample, (uint32_t)p, P.key_res);
+    make_key(cfg->run_seed, pa::kInit, (uint32_t)p, P.key_init);
+  }
+  if (rc != PA_OK) {
+    destroy(c);
+    return rc;
+  }
+  cudaStream_t s = c->stream;
+  rc = cuda_status(cudaMemsetAsync(c->status, 0, sizeof(int32_t), s));
+  if (rc == PA_OK) rc = cuda_status(cudaMemsetAsync(c->qhist, 0, sizeof(unsigned long long) * T * g.q_bins, s));
+  for (int p = 0; p < g.n_pop && rc == PA_OK; ++p) {
+    rc = cuda_status(cudaMemsetAsync(c->pops[p].hist, 0, sizeof(uint32_t) * T * (size_t)g.n_levels, s));
+    if (rc == PA_OK) rc = cuda_status(cudaMemsetAsync(c->pops[p].rec, 0, sizeof(StepRec) * T, s));
+  }
+  if (rc == PA_OK) rc = cuda_status(cudaStreamSynchronize(s));
+  for (int t = 1; t < cfg->n_temps && rc == PA_OK && !c->adaptive; ++t) {
+    const double* w = nullptr;
+    rc = weight_table(c, c->betas[(size_t)t] - c->betas[(size_t)t - 1], &w);
+  }
+  if (rc == PA_OK) rc = launch_rc(pa::launch_init_couplings(g, cfg->disorder_seed, c->J, c->jtab, s));
+  if (rc == PA_OK) rc = launch_rc(pa::launch_init_population(g, c->pops, 0, s));
+  if (rc == PA_OK) rc = launch_rc(pa::launch_levels_and_hist(g, c->pops, 0, c->jtab, 0, s));
+  if (rc == PA_OK) rc = measure(c, 0);
+  if (rc == PA_OK) rc = cuda_status(cudaStreamSynchronize(s));
+  if (rc != PA_OK) {
+    destroy(c);
+    return rc;
+  }
+  c->t = 0;
+  c->done = cfg->n_temps == 1;
+  *out = c;
+  return PA_OK;
+}
+
+int pa_step(pa_ctx* c) {
+  if (!c) return PA_ERR_INVALID;
+  if (c->error != PA_OK) return c->error;
+  if (c->done) return PA_DONE;
+  const int t = c->t + 1;
+  double dbeta;
+  if (c->adaptive) {
+    int rc = check_device_status(c);
+    if (rc == PA_OK) rc = choose_dbeta(c, &dbeta);
+    if (rc != PA_OK) return fail(c, rc);
+    double b = c->betas[(size_t)t - 1] + dbeta;
+    if (b >= c->cfg.beta_max || dbeta == c->cfg.beta_max - c->betas[(size_t)t - 1]) b = c->cfg.beta_max;
+    c->betas[(size_t)t] = b;
+  } else {
+    dbeta = c->betas[(size_t)t] - c->betas[(size_t)t - 1];
+  }
+  const double* w = nullptr;
+  int rc = weight_table(c, dbeta, &w);
+  if (rc != PA_OK) return fail(c, rc);
+  uint32_t met[3];
+  metropolis_thresholds(c->betas[(size_t)t], met);
+  cudaStream_t s = c->stream;
+  for (int p = 0; p < c->g.n_pop && rc == PA_OK; ++p)
+    rc = cuda_status(cudaMemsetAsync(c->pops[p].rec + t, 0, sizeof(StepRec), s));
+  if (rc == PA_OK) {
+    PhaseTimer pt(c, PA_PHASE_REWEIGHT, 1);
+    rc = launch_rc(pa::launch_reweight(c->g, c->pops, w, t, s));
+  }
+  if (rc == PA_OK) {
+    PhaseTimer pt(c, PA_PHASE_RESAMPLE, 3);
+    rc = launch_rc(pa::launch_resample(c->g, c->pops, c->cur, t, c->status, s));
+  }
+  if (rc == PA_OK) {
+    PhaseTimer pt(c, PA_PHASE_SWEEP, 1);
+    rc = launch_rc(pa::launch_sweep(c->g, c->pops, c->cur, c->jtab, t, c->sweeps[(size_t)t], met, s));
+  }
+  if (rc != PA_OK) return fail(c, rc);
+  c->cur = 1 - c->cur;
+  rc = measure(c, t);
+  if (rc != PA_OK) return fail(c, rc);
+  c->t = t;
+  c->stats.steps += 1;
+  c->counted_steps.emplace_back(t, c->sweeps[(size_t)t]);
+  if (t == c->cfg.n_temps - 1 || (c->adaptive && c->betas[(size_t)t] >= c->cfg.beta_max)) c->done = true;
+  return PA_OK;
+}
+
+int pa_stats_reset(pa_ctx* c, int enable_timing) {
+  if (!c) return PA_ERR_INVALID;
+  int rc = cuda_status(cudaStreamSynchronize(c->stream));
+  c->stats = pa_stats{};
+  c->timing = enable_timing != 0;
+  c->timed.clear();
+  c->events_used = 0;
+  c->counted_steps.clear();
+  return rc == PA_OK ? PA_OK : fail(c, rc);
+}
+
+int pa_get_stats(pa_ctx* c, pa_stats* out) {
+  if (!c || !out) return PA_ERR_INVALID;
+  int rc = cuda_status(cudaStreamSynchronize(c->stream));
+  if (rc != PA_OK) return fail(c, rc);
+  pa_stats st = c->stats;
+  for (int p = 0; p < PA_N_PHASES; ++p) {
+    st.phase_ms[p] = 0.0;
+    st.phase_count[p] = 0;
+  }
+  for (const auto& tm : c->timed) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, tm.start, tm.end) == cudaSuccess) {
+      st.phase_ms[tm.phase] += ms;
+      st.phase_count[tm.phase] += 1;
+    }
+  }
+  st.updates = 0;
+  for (const auto& ts : c->counted_steps)
+    for (int p = 0; p < c->g.n_pop; ++p) {
+      int32_t R = 0;
+      rc = cuda_status(cudaMemcpy(&R, &c->pops[p].rec[ts.first].R_tilde, sizeof R, cudaMemcpyDeviceToHost));
+      if (rc != PA_OK) return fail(c, rc);
+      st.updates += (int64_t)ts.second * c->g.N * R;
+    }
+  *out = st;
+  return PA_OK;
+}
+
+int pa_sync(pa_ctx* c) {
+  if (!c) return PA_ERR_INVALID;
+  int rc = cuda_status(cudaStreamSynchronize(c->stream));
+  if (rc == PA_OK) rc = check_device_status(c);
+  if (rc != PA_OK) fail(c, rc);
+  return c->error;
+}
+
+int pa_run(pa_ctx* c) {
+  if (!c) return PA_ERR_INVALID;
+  int rc;
+  while ((rc = pa_step(c)) == PA_OK) {
+  }
+  if (rc != PA_DONE) return rc;
+  return pa_sync(c);
+}
+
+int32_t pa_current_step(const pa_ctx* c) { return c ? c->t : -1; }
+
+double pa_beta(const pa_ctx* c, int32_t t) {
+  if (!c || t < 0 || t > c->t) return -1.0;
+  return c->betas[(size_t)t];
+}
+
+int pa_observables(pa_ctx* c, int32_t t, int32_t pop, pa_obs* out) {
+  if (!c || !out || t < 0 || pop < 0 || pop >= c->g.n_pop) return PA_ERR_INVALID;
+  if (t > c->t) return PA_ERR_STATE;
+  int rc = pa_sync(c);
+  if (rc != PA_OK) return rc;
+  const RunGeom& g = c->g;
+  std::vector<StepRec> rec((size_t)t + 1);
+  std::vector<uint32_t> hall((size_t)(t + 1) * g.n_levels);
+  rc = copy_d2h(c, rec.data(), c->pops[pop].rec, sizeof(StepRec) * rec.size());
+  if (rc == PA_OK) rc = copy_d2h(c, hall.data(), c->pops[pop].hist, sizeof(uint32_t) * hall.size());
+  if (rc != PA_OK) return fail(c, rc);
+  const uint32_t* h = hall.data() + (size_t)t * g.n_levels;
+  const int N = g.N;
+  // free energy, Eq. (betaF), and the lowest energy over steps 0..t
+  double lnQ_sum = 0.0, lnQ = 0.0;
+  int32_t E0 = 3 * N + 1;
+  for (int u = 0; u <= t; ++u) {
+    if (u > 0) {
+      const StepRec& r = rec[(size_t)u];
+      const double db = c->betas[(size_t)u] - c->betas[(size_t)u - 1];
+      const int32_t Emin_prev = 2 * r.kmin_prev - 3 * N;
+      lnQ = std::log(r.S_prime / (double)r.R_prev) - db * (double)Emin_prev;
+      lnQ_sum = lnQ_sum + lnQ;
+    }
+    const uint32_t* hu = hall.data() + (size_t)u * g.n_levels;
+    for (int k = 0; k < g.n_levels; ++k)
+      if (hu[k] > 0) {
+        E0 = std::min(E0, 2 * k - 3 * N);
+        break;
+      }
+  }
+  pa_obs o{};
+  const StepRec& r = rec[(size_t)t];
+  o.t = t;
+  o.beta = c->betas[(size_t)t];
+  o.dbeta = t > 0 ? c->betas[(size_t)t] - c->betas[(size_t)t - 1] : 0.0;
+  o.R_tilde = r.R_tilde;
+  int64_t sE = 0, sE2 = 0;
+  int32_t Emin = 3 * N + 1;
+  for (int k = 0; k < g.n_levels; ++k) {
+    if (!h[k]) continue;
+    const int64_t E = 2 * k - 3 * N;
+    sE += (int64_t)h[k] * E;
+    sE2 += (int64_t)h[k] * E * E;
+    Emin = std::min<int32_t>(Emin, (int32_t)E);
+  }
+  o.sum_E = sE;
+  o.sum_E2 = sE2;
+  o.E_min = Emin;
+  o.mean_E = (double)sE / (double)o.R_tilde;
+  o.var_E = (double)sE2 / (double)o.R_tilde - o.mean_E * o.mean_E;
+  o.kmin_prev = t > 0 ? r.kmin_prev : 0;
+  o.S_prime = t > 0 ? r.S_prime : 0.0;
+  o.lnQ = t > 0 ? lnQ : 0.0;
+  o.minus_beta_F = (double)N * std::log(2.0) + lnQ_sum;
+  o.eps_expected = t > 0 ? r.eps_expected : 0.0;
+  o.culled = t > 0 ? r.culled : 0;
+  o.sum_eta2 = (int64_t)r.sum_eta2;
+  o.n_families = (int64_t)r.n_families;
+  o.rho_t = (double)o.sum_eta2 / (double)o.R_tilde;
+  o.S_f = -r.nu_ln_nu;
+  o.rho_s = (double)o.R_tilde / std::exp(o.S_f);
+  o.E0 = E0;
+  o.g0_tilde = (double)h[(E0 + 3 * N) / 2] / (double)o.R_tilde;
+  o.g0_bar = 2.0 * std::exp(-(o.beta * (double)E0) - o.minus_beta_F);
+  if (g.n_pop == 2) {
+    StepRec r0;
+    rc = copy_d2h(c, &r0, c->pops[0].rec + t, sizeof r0);
+    if (rc != PA_OK) return fail(c, rc);
+    o.q_pairs = (int64_t)r0.q_pairs;
+    o.q_abs_le_02 = (int64_t)r0.q_small;
+    o.I02 = o.q_pairs > 0 ? (double)o.q_abs_le_02 / (double)o.q_pairs : 0.0;
+  }
+  *out = o;
+  return PA_OK;
+}
+
+int pa_energy_hist(pa_ctx* c, int32_t t, int32_t pop, int64_t* out, int64_t cap) {
+  if (!c || !out || t < 0 || pop < 0 || pop >= c->g.n_pop) return PA_ERR_INVALID;
+  if (t > c->t) return PA_ERR_STATE;
+  if (cap < c->g.n_levels) return PA_ERR_CAPACITY;
+  int rc = pa_sync(c);
+  if (rc != PA_OK) return rc;
+  std::vector<uint32_t> h((size_t)c->g.n_levels);
+  rc = cuda_status(cudaMemcpy(h.data(), c->pops[pop].hist + (size_t)t * c->g.n_levels, sizeof(uint32_t) * h.size(),
+                              cudaMemcpyDeviceToHost));
+  if (rc != PA_OK) return fail(c, rc);
+  for (size_t k = 0; k < h.size(); ++k) out[k] = h[k];
+  return PA_OK;
+}
+
+int pa_q_hist(pa_ctx* c, int32_t t, int64_t* out, int64_t cap) {
+  if (!c || !out || t < 0 || c->g.n_pop != 2) return PA_ERR_INVALID;
+  if (t > c->t) return PA_ERR_STATE;
+  if (cap < c->g.q_bins) return PA_ERR_CAPACITY;
+  int rc = pa_sync(c);
+  if (rc != PA_OK) return rc;
+  std::vector<unsigned long long> q((size_t)c->g.q_bins);
+  rc = cuda_status(cudaMemcpy(q.data(), c->qhist + (size_t)t * c->g.q_bins, sizeof(unsigned long long) * q.size(),
+                              cudaMemcpyDeviceToHost));
+  if (rc != PA_OK) return fail(c, rc);
+  for (size_t k = 0; k < q.size(); ++k) out[k] = (int64_t)q[k];
+  return PA_OK;
+}
+
+int pa_family_hist(pa_ctx* c, int32_t pop, int64_t cap, int64_t* eta, int64_t* m, int64_t* n) {
+  if (!c || !n || pop < 0 || pop >= c->g.n_pop) return PA_ERR_INVALID;
+  int rc = pa_sync(c);
+  if (rc != PA_OK) return rc;
+  int32_t R = 0;
+  rc = cuda_status(cudaMemcpy(&R, &c->pops[pop].rec[c->t].R_tilde, sizeof R, cudaMemcpyDeviceToHost));
+  std::vector<int32_t> mh((size_t)R + 1);
+  if (rc == PA_OK)
+    rc = cuda_status(cudaMemcpy(mh.data(), c->pops[pop].mhist, sizeof(int32_t) * mh.size(), cudaMemcpyDeviceToHost));
+  if (rc != PA_OK) return fail(c, rc);
+  int64_t k = 0;
+  for (int64_t e = 1; e <= R; ++e)
+    if (mh[(size_t)e] > 0) {
+      if (k < cap) {
+        if (eta) eta[k] = e;
+        if (m) m[k] = mh[(size_t)e];
+      }
+      ++k;
+    }
+  *n = k;
+  return k <= cap ? PA_OK : PA_ERR_CAPACITY;
+}
+
+int pa_population_size(pa_ctx* c, int32_t pop, int64_t* count) {
+  if (!c || !count || pop < 0 || pop >= c->g.n_pop) return PA_ERR_INVALID;
+  int rc = pa_sync(c);
+  if (rc != PA_OK) return rc;
+  int32_t R = 0;
+  rc = cuda_status(cudaMemcpy(&R, &c->pops[pop].rec[c->t].R_tilde, sizeof R, cudaMemcpyDeviceToHost));
+  if (rc != PA_OK) return fail(c, rc);
+  *count = R;
+  return PA_OK;
+}
+
+int pa_get_replicas(pa_ctx* c, int32_t pop, int64_t first, int64_t n, int8_t* spins, int32_t* labels,
+                    int32_t* energies) {
+  if (!c || pop < 0 || pop >= c->g.n_pop || first < 0 || n < 0) return PA_ERR_INVALID;
+  int64_t R = 0;
+  int rc = pa_population_size(c, pop, &R);
+  if (rc != PA_OK) return rc;
+  if (first + n > R) return PA_ERR_INVALID;
+  if (n == 0) return PA_OK;
+  const RunGeom& g = c->g;
+  const PopDev& P = c->pops[pop];
+  if (spins) {
+    std::vector<int8_t> tmp((size_t)g.N * (size_t)n);
+    rc = cuda_status(cudaMemcpy2D(tmp.data(), (size_t)n, P.spins[c->cur] + first, (size_t)g.pitch, (size_t)n,
+                                  (size_t)g.N, cudaMemcpyDeviceToHost));
+    if (rc != PA_OK) return fail(c, rc);
+    for (int64_t j = 0; j < n; ++j)
+      for (int s = 0; s < g.N; ++s) spins[(size_t)j * g.N + s] = tmp[(size_t)s * n + j];
+  }
+  if (labels) {
+    rc = cuda_status(cudaMemcpy(labels, P.labels[c->cur] + first, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    if (rc != PA_OK) return fail(c, rc);
+  }
+  if (energies) {
+    rc = cuda_status(cudaMemcpy(energies, P.levels + first, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    if (rc != PA_OK) return fail(c, rc);
+    for (int64_t j = 0; j < n; ++j) energies[j] = 2 * energies[j] - 3 * g.N;
+  }
+  return PA_OK;
+}
+
+int pa_get_copy_counts(pa_ctx* c, int32_t pop, int32_t* counts, int64_t cap, int64_t* count) {
+  if (!c || !count || pop < 0 || pop >= c->g.n_pop) return PA_ERR_INVALID;
+  if (c->t == 0) return PA_ERR_STATE;
+  int rc = pa_sync(c);
+  if (rc != PA_OK) return rc;
+  StepRec r;
+  rc = cuda_status(cudaMemcpy(&r, c->pops[pop].rec + c->t, sizeof r, cudaMemcpyDeviceToHost));
+  if (rc != PA_OK) return fail(c, rc);
+  *count = r.R_prev;
+  if (r.R_prev > cap) return PA_ERR_CAPACITY;
+  if (counts && r.R_prev > 0)
+    rc = cuda_status(cudaMemcpy(counts, c->pops[pop].counts, sizeof(int32_t) * r.R_prev, cudaMemcpyDeviceToHost));
+  return rc == PA_OK ? PA_OK : fail(c, rc);
+}
+
+int pa_get_parents(pa_ctx* c, int32_t pop, int32_t* parents, int64_t cap, int64_t* count) {
+  if (!c || !count || pop < 0 || pop >= c->g.n_pop) return PA_ERR_INVALID;
+  if (c->t == 0) return PA_ERR_STATE;
+  int64_t R = 0;
+  int rc = pa_population_size(c, pop, &R);
+  if (rc != PA_OK) return rc;
+  *count = R;
+  if (R > cap) return PA_ERR_CAPACITY;
+  if (parents && R > 0)
+    rc = cuda_status(cudaMemcpy(parents, c->pops[pop].parents, sizeof(int32_t) * R, cudaMemcpyDeviceToHost));
+  return rc == PA_OK ? PA_OK : fail(c, rc);
+}
+
+int pa_get_couplings(pa_ctx* c, int8_t* J, int64_t cap) {
+  if (!c || !J) return PA_ERR_INVALID;
+  if (cap < 3 * c->g.N) return PA_ERR_CAPACITY;
+  int rc = pa_sync(c);
+  if (rc != PA_OK) return rc;
+  rc = cuda_status(cudaMemcpy(J, c->J, (size_t)3 * c->g.N, cudaMemcpyDeviceToHost));
+  return rc == PA_OK ? PA_OK : fail(c, rc);
+}
+
+int pa_destroy(pa_ctx* c) {
+  if (!c) return PA_ERR_INVALID;
+  destroy(c);
+  return PA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,305 @@
+"""Thin ctypes binding of libpa.so (the C ABI declared in include/pa.h).
+
+Argument marshalling only: every step of a run executes in the library's CUDA
+kernels.  There is no CPU fallback — importing this module without a built
+libpa.so, or creating a run without a CUDA device, raises.
+
+PyTorch is optional here: a torch CUDA stream may be passed as ``stream``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpa.so")
+
+PA_OK, PA_DONE = 0, 1
+PA_ERR_INVALID, PA_ERR_NOMEM, PA_ERR_CAPACITY, PA_ERR_TIMEOUT = -1, -2, -3, -4
+PA_ERR_CUDA, PA_ERR_STATE, PA_ERR_EXTINCT = -5, -6, -7
+
+
+class PAError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        super().__init__(f"{fn} failed: {status} ({strerror(status)})")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("L", ctypes.c_int32),
+        ("n_pop", ctypes.c_int32),
+        ("R", ctypes.c_int64),
+        ("R_cap", ctypes.c_int64),
+        ("disorder_seed", ctypes.c_uint64),
+        ("run_seed", ctypes.c_uint64),
+        ("n_temps", ctypes.c_int32),
+        ("betas", ctypes.POINTER(ctypes.c_double)),
+        ("beta_max", ctypes.c_double),
+        ("eps_target", ctypes.c_double),
+        ("n_sweeps", ctypes.c_int32),
+        ("sweeps_per_step", ctypes.POINTER(ctypes.c_int32)),
+        ("q_bins", ctypes.c_int32),
+    ]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [
+        ("t", ctypes.c_int32),
+        ("beta", ctypes.c_double),
+        ("dbeta", ctypes.c_double),
+        ("R_tilde", ctypes.c_int64),
+        ("sum_E", ctypes.c_int64),
+        ("sum_E2", ctypes.c_int64),
+        ("E_min", ctypes.c_int32),
+        ("mean_E", ctypes.c_double),
+        ("var_E", ctypes.c_double),
+        ("kmin_prev", ctypes.c_int32),
+        ("S_prime", ctypes.c_double),
+        ("lnQ", ctypes.c_double),
+        ("minus_beta_F", ctypes.c_double),
+        ("eps_expected", ctypes.c_double),
+        ("culled", ctypes.c_int64),
+        ("sum_eta2", ctypes.c_int64),
+        ("n_families", ctypes.c_int64),
+        ("rho_t", ctypes.c_double),
+        ("S_f", ctypes.c_double),
+        ("rho_s", ctypes.c_double),
+        ("E0", ctypes.c_int32),
+        ("g0_tilde", ctypes.c_double),
+        ("g0_bar", ctypes.c_double),
+        ("q_pairs", ctypes.c_int64),
+        ("q_abs_le_02", ctypes.c_int64),
+        ("I02", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+PHASES = ("reweight", "resample", "sweep", "family", "overlap")
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("steps", ctypes.c_int64),
+        ("kernel_launches", ctypes.c_int64),
+        ("h2d_bytes", ctypes.c_int64),
+        ("d2h_bytes", ctypes.c_int64),
+        ("updates", ctypes.c_int64),
+        ("phase_ms", ctypes.c_double * 5),
+        ("phase_count", ctypes.c_int64 * 5),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k in ("steps", "kernel_launches", "h2d_bytes", "d2h_bytes", "updates")}
+        d["phase_ms"] = dict(zip(PHASES, list(self.phase_ms)))
+        d["phase_count"] = dict(zip(PHASES, list(self.phase_count)))
+        return d
+
+
+_lib = None
+
+# Every entry point declared in include/pa.h, with its ctypes signature.
+_i8p = ctypes.POINTER(ctypes.c_int8)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_vp = ctypes.c_void_p
+SIGNATURES = {
+    "pa_create": (ctypes.c_int, [ctypes.POINTER(Config), _vp, ctypes.POINTER(_vp)]),
+    "pa_step": (ctypes.c_int, [_vp]),
+    "pa_run": (ctypes.c_int, [_vp]),
+    "pa_current_step": (ctypes.c_int32, [_vp]),
+    "pa_observables": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(Obs)]),
+    "pa_energy_hist": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _i64p, ctypes.c_int64]),
+    "pa_q_hist": (ctypes.c_int, [_vp, ctypes.c_int32, _i64p, ctypes.c_int64]),
+    "pa_family_hist": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int64, _i64p, _i64p, _i64p]),
+    "pa_population_size": (ctypes.c_int, [_vp, ctypes.c_int32, _i64p]),
+    "pa_get_replicas": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _i8p, _i32p, _i32p]),
+    "pa_get_copy_counts": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p, ctypes.c_int64, _i64p]),
+    "pa_get_parents": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p, ctypes.c_int64, _i64p]),
+    "pa_get_couplings": (ctypes.c_int, [_vp, _i8p, ctypes.c_int64]),
+    "pa_beta": (ctypes.c_double, [_vp, ctypes.c_int32]),
+    "pa_stats_reset": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "pa_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(Stats)]),
+    "pa_sync": (ctypes.c_int, [_vp]),
+    "pa_destroy": (ctypes.c_int, [_vp]),
+    "pa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def lib():
+    """Loads libpa.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1711_02146_gb300.build` "
+                              "(or __graft_entry__.build()); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def strerror(status: int) -> str:
+    try:
+        return lib().pa_strerror(status).decode()
+    except ImportError:
+        return "?"
+
+
+def _check(fn: str, rc: int) -> int:
+    if rc < 0:
+        raise PAError(fn, rc)
+    return rc
+
+
+def _p(a: np.ndarray, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+class Run:
+    """One population annealing run on the GPU (a ``pa_ctx``)."""
+
+    def __init__(self, L: int, R: int, disorder_seed: int, run_seed: int, betas=None, *, n_temps: int = 0,
+                 beta_max: float = 0.0, eps_target: float = 0.0, n_sweeps: int = 10, sweeps_per_step=None,
+                 n_pop: int = 1, q_bins: int = 65, R_cap: int = 0, stream=None):
+        self.L, self.N, self.n_pop, self.q_bins = L, L ** 3, n_pop, q_bins
+        self.n_levels = 3 * self.N + 1
+        self._betas = None if betas is None else np.ascontiguousarray(betas, dtype=np.float64)
+        self._sweeps = None if sweeps_per_step is None else np.ascontiguousarray(sweeps_per_step, dtype=np.int32)
+        c = Config()
+        c.L, c.n_pop, c.R, c.R_cap = L, n_pop, R, R_cap
+        c.disorder_seed, c.run_seed = disorder_seed, run_seed
+        c.n_temps = len(self._betas) if self._betas is not None else n_temps
+        c.betas = _p(self._betas, ctypes.c_double) if self._betas is not None else None
+        c.beta_max, c.eps_target, c.n_sweeps = beta_max, eps_target, n_sweeps
+        c.sweeps_per_step = _p(self._sweeps, ctypes.c_int32) if self._sweeps is not None else None
+        c.q_bins = q_bins
+        self.n_temps = c.n_temps
+        h = _vp()
+        _check("pa_create", lib().pa_create(ctypes.byref(c), _stream_handle(stream), ctypes.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_workload(cls, w, stream=None, **over):
+        kw = dict(n_temps=w.n_temps, beta_max=w.beta_max, eps_target=w.eps_target, n_sweeps=w.n_sweeps,
+                  n_pop=w.n_pop, q_bins=w.q_bins, R_cap=w.R_cap)
+        kw.update(over)
+        return cls(w.L, w.R, w.disorder_seed, w.run_seed, w.betas, stream=stream, **kw)
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().pa_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- stepping
+    def step(self) -> int:
+        return _check("pa_step", lib().pa_step(self._h))
+
+    def run(self) -> None:
+        _check("pa_run", lib().pa_run(self._h))
+
+    def sync(self) -> None:
+        _check("pa_sync", lib().pa_sync(self._h))
+
+    @property
+    def t(self) -> int:
+        return int(lib().pa_current_step(self._h))
+
+    def beta(self, t: int) -> float:
+        return float(lib().pa_beta(self._h, t))
+
+    def stats_reset(self, timing: bool = False) -> None:
+        _check("pa_stats_reset", lib().pa_stats_reset(self._h, 1 if timing else 0))
+
+    def stats(self) -> dict:
+        st = Stats()
+        _check("pa_get_stats", lib().pa_get_stats(self._h, ctypes.byref(st)))
+        return st.as_dict()
+
+    # ---- results
+    def obs(self, t: int, pop: int = 0) -> dict:
+        o = Obs()
+        _check("pa_observables", lib().pa_observables(self._h, t, pop, ctypes.byref(o)))
+        return o.as_dict()
+
+    def energy_hist(self, t: int, pop: int = 0) -> np.ndarray:
+        out = np.zeros(self.n_levels, dtype=np.int64)
+        _check("pa_energy_hist", lib().pa_energy_hist(self._h, t, pop, _p(out, ctypes.c_int64), out.size))
+        return out
+
+    def q_hist(self, t: int) -> np.ndarray:
+        out = np.zeros(self.q_bins, dtype=np.int64)
+        _check("pa_q_hist", lib().pa_q_hist(self._h, t, _p(out, ctypes.c_int64), out.size))
+        return out
+
+    def family_hist(self, pop: int = 0):
+        n = ctypes.c_int64()
+        lib().pa_family_hist(self._h, pop, 0, None, None, ctypes.byref(n))
+        eta = np.zeros(max(n.value, 1), dtype=np.int64)
+        m = np.zeros(max(n.value, 1), dtype=np.int64)
+        _check("pa_family_hist", lib().pa_family_hist(self._h, pop, eta.size, _p(eta, ctypes.c_int64),
+                                                      _p(m, ctypes.c_int64), ctypes.byref(n)))
+        return eta[:n.value].copy(), m[:n.value].copy()
+
+    def size(self, pop: int = 0) -> int:
+        n = ctypes.c_int64()
+        _check("pa_population_size", lib().pa_population_size(self._h, pop, ctypes.byref(n)))
+        return n.value
+
+    def replicas(self, pop: int = 0, first: int = 0, n: Optional[int] = None):
+        """(spins [n, N] int8, labels int32, energies int32) of slots first..first+n."""
+        if n is None:
+            n = self.size(pop) - first
+        s = np.zeros((n, self.N), dtype=np.int8)
+        lab = np.zeros(n, dtype=np.int32)
+        E = np.zeros(n, dtype=np.int32)
+        _check("pa_get_replicas", lib().pa_get_replicas(self._h, pop, first, n, _p(s, ctypes.c_int8),
+                                                        _p(lab, ctypes.c_int32), _p(E, ctypes.c_int32)))
+        return s, lab, E
+
+    def population(self, pop: int = 0):
+        return self.replicas(pop, 0, None)
+
+    def copy_counts(self, pop: int = 0) -> np.ndarray:
+        n = ctypes.c_int64()
+        lib().pa_get_copy_counts(self._h, pop, None, 0, ctypes.byref(n))
+        out = np.zeros(max(n.value, 1), dtype=np.int32)
+        _check("pa_get_copy_counts", lib().pa_get_copy_counts(self._h, pop, _p(out, ctypes.c_int32), out.size,
+                                                              ctypes.byref(n)))
+        return out[:n.value].copy()
+
+    def parents(self, pop: int = 0) -> np.ndarray:
+        n = ctypes.c_int64()
+        lib().pa_get_parents(self._h, pop, None, 0, ctypes.byref(n))
+        out = np.zeros(max(n.value, 1), dtype=np.int32)
+        _check("pa_get_parents", lib().pa_get_parents(self._h, pop, _p(out, ctypes.c_int32), out.size,
+                                                      ctypes.byref(n)))
+        return out[:n.value].copy()
+
+    def couplings(self) -> np.ndarray:
+        J = np.zeros(3 * self.N, dtype=np.int8)
+        _check("pa_get_couplings", lib().pa_get_couplings(self._h, _p(J, ctypes.c_int8), J.size))
+        return J

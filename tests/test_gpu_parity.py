@@ -1,0 +1,204 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Integer results — spins, labels, energies, copy numbers, population sizes,
+energy/overlap/family histograms, the adaptive schedule — must match bit for
+bit; FP64 observables to 1e-12 relative (the host-side estimators use the same
+formulas on the same integer inputs, so in practice they match exactly except
+the family entropy, whose device reduction order differs).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-12
+INT_OBS = ("t", "R_tilde", "sum_E", "sum_E2", "E_min", "kmin_prev", "culled", "sum_eta2", "n_families", "E0",
+           "q_pairs", "q_abs_le_02")
+FLOAT_OBS = ("beta", "dbeta", "mean_E", "var_E", "S_prime", "lnQ", "minus_beta_F", "eps_expected", "rho_t", "S_f",
+             "rho_s", "g0_tilde", "g0_bar", "I02")
+
+
+@pytest.fixture(scope="module")
+def pa():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_02146_gb300 import build, pa as pa_mod
+    build.build()
+    return pa_mod
+
+
+def make_pair(pa, oracle_lib, L, R, betas=None, **kw):
+    gpu = pa.Run(L, R, kw.get("disorder_seed", 1), kw.get("run_seed", 2), betas,
+                 n_temps=kw.get("n_temps", 0), beta_max=kw.get("beta_max", 0.0), eps_target=kw.get("eps_target", 0.0),
+                 n_sweeps=kw.get("n_sweeps", 3), sweeps_per_step=kw.get("sweeps_per_step"), n_pop=kw.get("n_pop", 1),
+                 q_bins=kw.get("q_bins", 65), R_cap=kw.get("R_cap", 0))
+    ref = oracle_lib.Run(oracle_lib.RunConfig(L=L, R=R, disorder_seed=kw.get("disorder_seed", 1),
+                                              run_seed=kw.get("run_seed", 2), betas=betas, n_temps=kw.get("n_temps", 0),
+                                              beta_max=kw.get("beta_max", 0.0), eps_target=kw.get("eps_target", 0.0),
+                                              n_sweeps=kw.get("n_sweeps", 3),
+                                              sweeps_per_step=kw.get("sweeps_per_step"), n_pop=kw.get("n_pop", 1),
+                                              q_bins=kw.get("q_bins", 65), R_cap=kw.get("R_cap", 0)))
+    return gpu, ref
+
+
+def assert_obs_equal(g, r, ctx=""):
+    for k in INT_OBS:
+        assert g[k] == r[k], f"{ctx} {k}: gpu {g[k]} oracle {r[k]}"
+    for k in FLOAT_OBS:
+        a, b = g[k], r[k]
+        assert abs(a - b) <= REL * max(abs(a), abs(b)) + 1e-300, f"{ctx} {k}: gpu {a!r} oracle {b!r}"
+
+
+def assert_state_equal(gpu, ref, n_pop, ctx=""):
+    for pop in range(n_pop):
+        s, lab, E = gpu.population(pop)
+        rs, rlab, rE = ref.population(pop)
+        assert s.shape == rs.shape, f"{ctx} pop {pop}: population size {s.shape[0]} vs {rs.shape[0]}"
+        assert np.array_equal(lab, rlab), f"{ctx} pop {pop}: labels"
+        assert np.array_equal(E, rE), f"{ctx} pop {pop}: energies"
+        bad = np.nonzero(np.any(s != rs, axis=1))[0]
+        assert bad.size == 0, f"{ctx} pop {pop}: {bad.size} replicas differ, first {bad[:5]}"
+
+
+def linear(T, bmax):
+    return np.array([t * bmax / (T - 1) for t in range(T)])
+
+
+@pytest.mark.parametrize("L,R,T,S", [(2, 37, 6, 3), (4, 1000, 8, 3), (4, 1, 5, 2), (6, 777, 5, 2), (8, 3333, 4, 2),
+                                     (10, 515, 4, 2), (12, 300, 3, 1), (14, 129, 3, 1), (16, 65, 3, 1)])
+def test_stepwise_bit_exact(pa, oracle_lib, L, R, T, S):
+    betas = linear(T, 2.0)
+    gpu, ref = make_pair(pa, oracle_lib, L, R, betas, n_sweeps=S, disorder_seed=L, run_seed=100 + R)
+    assert np.array_equal(gpu.couplings(), ref.couplings())
+    assert_state_equal(gpu, ref, 1, "t=0")
+    assert_obs_equal(gpu.obs(0), ref.obs(0), "t=0")
+    for t in range(1, T):
+        assert gpu.step() == 0
+        ref.step()
+        assert np.array_equal(gpu.copy_counts(), ref.last_counts()), f"copy numbers at t={t}"
+        assert_state_equal(gpu, ref, 1, f"t={t}")
+        assert np.array_equal(gpu.energy_hist(t), ref.energy_hist(t)), f"energy histogram at t={t}"
+        assert_obs_equal(gpu.obs(t), ref.obs(t), f"t={t}")
+        eta, m = gpu.family_hist()
+        reta, rm = ref.family_hist()
+        assert np.array_equal(eta, reta) and np.array_equal(m, rm)
+    assert gpu.step() == 1  # PA_DONE
+
+
+def test_c1_full_run(pa, oracle_lib):
+    from paper_1711_02146_gb300.workloads import C1
+    gpu = pa.Run.from_workload(C1)
+    ref = oracle_lib.Run(oracle_lib.RunConfig(L=C1.L, R=C1.R, disorder_seed=C1.disorder_seed, run_seed=C1.run_seed,
+                                              betas=C1.betas, n_sweeps=C1.n_sweeps))
+    gpu.run()
+    ref.run()
+    assert_state_equal(gpu, ref, 1, "C1 end")
+    for t in range(len(C1.betas)):
+        assert np.array_equal(gpu.energy_hist(t), ref.energy_hist(t)), t
+        assert_obs_equal(gpu.obs(t), ref.obs(t), f"C1 t={t}")
+
+
+def test_two_populations_overlap(pa, oracle_lib):
+    betas = linear(12, 3.0)
+    gpu, ref = make_pair(pa, oracle_lib, 8, 2000, betas, n_sweeps=4, n_pop=2, disorder_seed=2, run_seed=9)
+    gpu.run()
+    ref.run()
+    assert_state_equal(gpu, ref, 2, "two populations")
+    for t in range(12):
+        assert np.array_equal(gpu.q_hist(t), ref.q_hist(t)), t
+        for pop in (0, 1):
+            assert_obs_equal(gpu.obs(t, pop), ref.obs(t, pop), f"t={t} pop={pop}")
+
+
+def test_adaptive_schedule(pa, oracle_lib):
+    gpu, ref = make_pair(pa, oracle_lib, 6, 4000, None, n_temps=300, beta_max=3.0, eps_target=0.2, n_sweeps=3,
+                         disorder_seed=5, run_seed=6)
+    gpu.run()
+    ref.run()
+    assert gpu.t == ref.t
+    for t in range(gpu.t + 1):
+        assert gpu.beta(t) == ref.beta(t), t          # bitwise identical schedule
+        assert_obs_equal(gpu.obs(t), ref.obs(t), f"adaptive t={t}")
+    assert_state_equal(gpu, ref, 1, "adaptive end")
+
+
+def test_sweep_schedule_and_zero_steps(pa, oracle_lib):
+    betas = np.array([0.0, 0.3, 0.3, 0.9, 1.4, 1.4])
+    sweeps = np.array([0, 0, 5, 1, 22, 3], dtype=np.int32)
+    gpu, ref = make_pair(pa, oracle_lib, 4, 900, betas, sweeps_per_step=sweeps, disorder_seed=3, run_seed=4)
+    gpu.run()
+    ref.run()
+    assert_state_equal(gpu, ref, 1, "sweep schedule")
+    for t in range(6):
+        assert_obs_equal(gpu.obs(t), ref.obs(t), f"t={t}")
+
+
+def test_capacity_overflow_is_reported(pa, oracle_lib):
+    betas = linear(6, 3.0)
+    for run_seed in range(20):
+        ref = oracle_lib.Run(oracle_lib.RunConfig(L=4, R=500, disorder_seed=1, run_seed=run_seed, betas=betas,
+                                                  n_sweeps=1, R_cap=500))
+        try:
+            ref.run()
+        except RuntimeError:
+            break
+    else:
+        pytest.skip("no overflowing seed found")
+    gpu = pa.Run(4, 500, 1, run_seed, betas, n_sweeps=1, R_cap=500)
+    with pytest.raises(pa.PAError) as e:
+        gpu.run()
+    assert e.value.status == pa.PA_ERR_CAPACITY
+
+
+def test_invalid_configurations_rejected(pa):
+    with pytest.raises(pa.PAError):
+        pa.Run(5, 10, 1, 1, linear(3, 1.0))            # odd L
+    with pytest.raises(pa.PAError):
+        pa.Run(18, 10, 1, 1, linear(3, 1.0))           # beyond the largest supported L
+    with pytest.raises(pa.PAError):
+        pa.Run(4, 10, 1 << 56, 1, linear(3, 1.0))      # seed too large
+    with pytest.raises(pa.PAError):
+        pa.Run(4, 10, 1, 1, np.array([0.1, 0.2]))      # schedule must start at beta = 0
+    with pytest.raises(pa.PAError):
+        pa.Run(4, 10, 1, 1, np.array([0.0, 0.5, 0.2]))  # descending
+
+
+def test_full_size_sampled_step(pa, oracle_lib):
+    """L=10, R=1e6 (the large-population workload), two steps on the GPU in the
+    launch configuration the benchmark times; sampled replicas are recomputed by
+    the oracle one by one from their parents."""
+    from paper_1711_02146_gb300.workloads import C3
+    gpu = pa.Run.from_workload(C3)
+    L, N = C3.L, C3.N
+    J = gpu.couplings()
+    assert np.array_equal(J, oracle_lib.couplings(L, C3.disorder_seed))
+    rng = np.random.default_rng(0)
+    for _ in range(2):
+        s_old, lab_old, E_old = gpu.population()
+        h_old = gpu.energy_hist(gpu.t)
+        assert np.array_equal(np.bincount((E_old + 3 * N) // 2, minlength=3 * N + 1), h_old)
+        for j in rng.integers(0, len(E_old), 16):
+            assert oracle_lib.energy(L, J, s_old[j]) == E_old[j]
+        gpu.step()
+        t = gpu.t
+        o = gpu.obs(t)
+        # resampling: oracle tables from the GPU's integer histogram
+        kmin, S, fl, thr, eps = oracle_lib.reweight(h_old, C3.R, o["dbeta"])
+        assert o["kmin_prev"] == kmin and o["S_prime"] == S and o["eps_expected"] == eps
+        counts = gpu.copy_counts()
+        assert counts.size == len(E_old)
+        for i in rng.integers(0, len(E_old), 4000):
+            k = (E_old[i] + 3 * N) // 2
+            assert counts[i] == oracle_lib.copy_count(C3.run_seed, 0, t, int(i), int(fl[k]), int(thr[k]))
+        parents = gpu.parents()
+        assert parents.size == counts.sum() == o["R_tilde"]
+        assert np.array_equal(parents, np.repeat(np.arange(len(E_old), dtype=np.int32), counts))
+        s_new, lab_new, E_new = gpu.population()
+        assert np.array_equal(lab_new, lab_old[parents])
+        met = oracle_lib.metropolis_thresholds(gpu.beta(t))
+        for j in rng.integers(0, len(E_new), 24):
+            ref, dE = oracle_lib.sweep_replica(L, J, s_old[parents[j]], C3.run_seed, 0, int(j), t, C3.n_sweeps, met)
+            assert np.array_equal(s_new[j], ref), f"slot {j}"
+            assert E_new[j] == E_old[parents[j]] + dE
+        assert np.array_equal(np.bincount((E_new + 3 * N) // 2, minlength=3 * N + 1), gpu.energy_hist(t))
