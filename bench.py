@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--R", type=int, default=0, help="override the population size (profiling runs)")
+    ap.add_argument("--probe", action="store_true", help="also run the integer-throughput probes")
     return ap.parse_args()
 
 
@@ -82,7 +85,7 @@ class ClockSampler:
             fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -226,6 +229,8 @@ def ours(args):
     from paper_1711_02146_gb300.workloads import C3
     build.build()
     w = C3.with_(run_seed=C3.run_seed + 7919 * rank)
+    if args.R:
+        w = w.with_(R=args.R, name=f"{C3.name}_R{args.R}")
     stream = torch.cuda.Stream()
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
@@ -265,7 +270,7 @@ def ours(args):
 
     # e2e: the same steps through the public API, reading every step's observables back
     e2e = None
-    if not run.t >= run.n_temps - 1:
+    if not args.no_e2e and not run.t >= run.n_temps - 1:
         run.stats_reset(timing=False)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -309,6 +314,8 @@ def ours(args):
             "roofline": roofline, "e2e": e2e, "gpu_launches": st["kernel_launches"],
             "phase_share": phase_share, "clocks": clk}
     run.close()
+    if args.probe:
+        line["int_probes_per_s"] = {k: pa.int_throughput(k) for k in pa.PROBES}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1

@@ -128,7 +128,23 @@ SIGNATURES = {
     "pa_sync": (ctypes.c_int, [_vp]),
     "pa_destroy": (ctypes.c_int, [_vp]),
     "pa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "pa_bench_int_throughput": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
 }
+
+PROBES = {"lop3": 0, "iadd": 1, "imad": 2, "mulwide": 3, "philox": 4}
+
+
+def int_throughput(kind: str, iters: int = 4096, blocks: int = 0, threads: int = 256):
+    """Integer-throughput probe (include/pa_bench.h): returns operations per second
+    (Philox words per second for kind="philox")."""
+    if blocks <= 0:
+        import torch
+        blocks = 16 * torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    ms, ops = ctypes.c_double(), ctypes.c_double()
+    _check("pa_bench_int_throughput", lib().pa_bench_int_throughput(PROBES[kind], iters, blocks, threads,
+                                                                    ctypes.byref(ms), ctypes.byref(ops)))
+    return ops.value / (ms.value / 1e3)
 
 
 def lib():
