@@ -2,22 +2,34 @@
 //
 // One CTA owns a tile of TJ = 4W consecutive slots of the NEW population and
 // all N sites of those replicas in shared memory (W 32-bit words per site row,
-// four int8 replicas per word).  It
+// four replicas per word).  It
 //   1. gathers each slot's spins from its parent in the old population (the
 //      replica copy of the resampling, §II, fused into the load),
 //   2. runs S checkerboard Metropolis sweeps at beta_t in shared memory (colour
-//      c = (x + y + z) & 1, colour 0 then colour 1; neighbours of a site all
-//      have the other colour, so every site of a colour updates independently),
-//   3. counts each replica's unsatisfied bonds (its energy level k), adds the
-//      tile to the level histogram of step t, and
+//      c = (x + y + z) & 1, colour 0 then colour 1; the neighbours of a site all
+//      have the other colour, so all sites of one colour update independently),
+//   3. counts each replica's unsatisfied bonds (its energy level k) and adds
+//      the tile to the level histogram of step t, and
 //   4. writes the tile to the new population buffer.
 // HBM traffic is one read and one write of the tile per step, whatever S is.
 //
 // Metropolis rule: flipping s_n costs dE = 2 s_n h_n = 12 - 4u, u = unsatisfied
-// bonds at n.  It is accepted when u >= 3 (dE <= 0) or when the Philox word r
-// is below thr[dE/4 - 1] = floor(2^32 exp(-beta dE)).  r is word (j & 3) of
+// bonds at n.  It is taken when u >= 3 (dE <= 0) or when the Philox word r is
+// below thr[dE/4 - 1] = floor(2^32 exp(-beta dE)).  r is word (j & 3) of
 // Philox4x32-10 at counter (n >> 1, 2s + c, j >> 2, t) keyed by (run_seed,
 // Metropolis, population): one call serves the four replicas of a word.
+//
+// Shared-memory encoding: a spin is one byte, 0x00 for +1 and 0x04 for -1 (HBM
+// holds int8 +1 = 0x01 / -1 = 0xFF).  For a bond, s_a ^ s_b ^ Jmask (Jmask =
+// 0x04 per byte for J = -1) is 0x04 exactly when the bond is unsatisfied, so the
+// byte-wise sum of the six bond terms is 4u, which is also the byte offset of
+// u's entry in a 7-word threshold table.
+//
+// Philox hoisting (same function, fewer multiplies): with counter words
+// (h, q, g, t) = (site, half-sweep, word, step), the round-1 and round-2
+// products depend either on the site and step only (tabulated once per launch
+// in shared memory) or on the thread and half-sweep only (registers), so each
+// block costs the 16 wide multiplies of rounds 3..10.
 #include <cuda_runtime.h>
 
 #include "pa_device.cuh"
@@ -25,18 +37,30 @@
 
 namespace pa {
 
+constexpr uint32_t kM0 = 0xD2511F53u;
+constexpr uint32_t kM1 = 0xCD9E8D57u;
+constexpr uint32_t kSpinBit = 0x04040404u;
+
 struct SweepArgs {
-  PopDev pops[2];
-  const uint32_t* jtab;  // [N][4] forward-bond XOR masks
+  PopDev pop;
+  const uint32_t* jtab;  // [N][4] forward-bond masks (0xFEFEFEFE for J = -1)
   int64_t pitch;
   int32_t n_levels;
   int32_t t;
   int32_t cur;
   int32_t n_sweeps;
   uint32_t thr4, thr8, thr12;
+  uint32_t k0[10];       // Metropolis round keys of this population
+  uint32_t k1[10];
 };
 
-constexpr uint32_t kBit1Mask = 0x02020202u;
+// Per-site shared-memory record: the six bond masks of the site, and the
+// site/step-dependent parts of Philox rounds 2-3 for h = n >> 1 (the third,
+// lo(M0 h), is one multiply and is recomputed).
+struct __align__(16) SiteRec {
+  uint32_t jxp, jxm, jyp, jym;
+  uint32_t jzp, jzm, ua, ub;
+};
 
 template <int L, int W, int NT>
 struct SweepShape {
@@ -44,21 +68,109 @@ struct SweepShape {
   static constexpr int ROWS = L * L;
   static constexpr int NP = NT / W;  // row partitions
   static constexpr int TJ = 4 * W;   // replicas per tile
-  static constexpr size_t SMEM = (size_t)N * W * 4 + (size_t)N * 16 + (size_t)TJ * 4;
+  static constexpr size_t SPIN_BYTES = (size_t)N * W * 4;
+  static constexpr size_t SMEM = SPIN_BYTES + (size_t)N * sizeof(SiteRec) + 8 * 4 + (size_t)TJ * 4;
   static_assert(NT % W == 0, "threads must tile the words of a row");
+  static_assert(32 % W == 0, "a warp must cover whole rows");
 };
 
+__device__ __forceinline__ void mulhilo(uint32_t m, uint32_t a, uint32_t& hi, uint32_t& lo) {
+  hi = __umulhi(m, a);
+  lo = m * a;
+}
+
+// Per-thread, per-half-sweep part of rounds 1-3.
+struct ThreadPhilox {
+  uint32_t ta;   // lo(M1 g): XORed with the site's ua to give round-2 word 0
+  uint32_t tb;   // hi(M0 A1) ^ k1_2: XORed with the site's uc to give round-2 word 2
+  uint32_t tdk;  // lo(M0 A1) ^ k1_3: round-3 word 2 is hi(M0 A2) ^ tdk
+};
+
+__device__ __forceinline__ ThreadPhilox thread_philox(uint32_t g, uint32_t q, const uint32_t* k0,
+                                                      const uint32_t* k1) {
+  uint32_t h1, l1;
+  mulhilo(kM1, g, h1, l1);
+  const uint32_t a1 = h1 ^ q ^ k0[0];
+  uint32_t ha, la;
+  mulhilo(kM0, a1, ha, la);
+  ThreadPhilox tp;
+  tp.ta = l1;
+  tp.tb = ha ^ k1[1];
+  tp.tdk = la ^ k1[2];
+  return tp;
+}
+
+// Rounds 3..10 from the hoisted parts; returns the four output words.
+__device__ __forceinline__ uint4 philox_tail(const SiteRec& sr, uint32_t uc, const ThreadPhilox& tp,
+                                             const uint32_t* k0, const uint32_t* k1) {
+  const uint32_t a2 = sr.ua ^ tp.ta;
+  const uint32_t c2 = tp.tb ^ uc;
+  uint32_t h, l, h2, l2;
+  mulhilo(kM1, c2, h, l);   // round 3
+  mulhilo(kM0, a2, h2, l2);
+  uint32_t x0 = h ^ sr.ub, x1 = l, x2 = h2 ^ tp.tdk, x3 = l2;
+#pragma unroll
+  for (int r = 3; r < 10; ++r) {  // rounds 4..10 (key index r)
+    mulhilo(kM1, x2, h, l);
+    mulhilo(kM0, x0, h2, l2);
+    const uint32_t n0 = h ^ x1 ^ k0[r];
+    const uint32_t n2 = h2 ^ x3 ^ k1[r];
+    x0 = n0;
+    x1 = l;
+    x2 = n2;
+    x3 = l2;
+  }
+  return make_uint4(x0, x1, x2, x3);
+}
+
+// One row (y, z) of colour-X0 sites: x = X0, X0 + 2, ...  All neighbour offsets
+// are compile-time; pointers are at (row base, this thread's word).
+template <int L, int W, int X0>
+__device__ __forceinline__ void sweep_row(uint32_t h0, uint32_t* __restrict__ p0, const uint32_t* __restrict__ pyp,
+                                          const uint32_t* __restrict__ pym, const uint32_t* __restrict__ pzp,
+                                          const uint32_t* __restrict__ pzm, const SiteRec* __restrict__ rec,
+                                          const uint32_t* __restrict__ thr_tab, const ThreadPhilox& tp,
+                                          const uint32_t* k0, const uint32_t* k1) {
+  const char* tb = reinterpret_cast<const char*>(thr_tab);
+#pragma unroll
+  for (int xh = 0; xh < L / 2; ++xh) {
+    const int x = 2 * xh + X0;
+    const int xp = x == L - 1 ? 0 : x + 1;
+    const int xm = x == 0 ? L - 1 : x - 1;
+    const SiteRec& sr = rec[x];
+    const uint32_t s0 = p0[x * W];
+    const uint32_t u4 = (s0 ^ p0[xp * W] ^ sr.jxp) + (s0 ^ p0[xm * W] ^ sr.jxm) + (s0 ^ pyp[x * W] ^ sr.jyp) +
+                        (s0 ^ pym[x * W] ^ sr.jym) + (s0 ^ pzp[x * W] ^ sr.jzp) + (s0 ^ pzm[x * W] ^ sr.jzm);
+    const uint32_t uc = kM0 * (h0 + (uint32_t)(x >> 1));  // lo(M0 h), h = n >> 1
+    const uint4 r = philox_tail(sr, uc, tp, k0, k1);
+    // u >= 3 (dE <= 0): always flip
+    const uint32_t always = ((u4 + 0x74747474u) >> 5) & kSpinBit;
+    uint32_t fm = always;
+    const uint32_t t0 = *reinterpret_cast<const uint32_t*>(tb + (u4 & 0xFFu));
+    const uint32_t t1 = *reinterpret_cast<const uint32_t*>(tb + __byte_perm(u4, 0u, 0x4441));
+    const uint32_t t2 = *reinterpret_cast<const uint32_t*>(tb + __byte_perm(u4, 0u, 0x4442));
+    const uint32_t t3 = *reinterpret_cast<const uint32_t*>(tb + (u4 >> 24));
+    fm |= r.x < t0 ? 0x00000004u : 0u;
+    fm |= r.y < t1 ? 0x00000400u : 0u;
+    fm |= r.z < t2 ? 0x00040000u : 0u;
+    fm |= r.w < t3 ? 0x04000000u : 0u;
+    p0[x * W] = s0 ^ fm;
+  }
+}
+
 template <int L, int W, int NT>
-__global__ void __launch_bounds__(NT) k_sweep(SweepArgs a) {
+__global__ void __launch_bounds__(NT) k_sweep(const __grid_constant__ SweepArgs a) {
   using S = SweepShape<L, W, NT>;
   constexpr int N = S::N, NP = S::NP, TJ = S::TJ, ROWS = S::ROWS;
   extern __shared__ __align__(16) uint32_t sm[];
-  uint32_t* sp = sm;                       // spins [N][W]
-  uint32_t* jt = sm + N * W;               // coupling masks [N][4]
-  int* ecnt = reinterpret_cast<int*>(jt + 4 * N);  // [TJ] unsatisfied-bond counts (x2)
+  uint32_t* sp = sm;                                                  // spins [N][W]
+  SiteRec* recs = reinterpret_cast<SiteRec*>(sm + (size_t)N * W);     // [N]
+  uint32_t* thr_tab = reinterpret_cast<uint32_t*>(recs + N);          // [8]
+  int* ecnt = reinterpret_cast<int*>(thr_tab + 8);                    // [TJ]
 
-  const int pop = blockIdx.y;
-  const PopDev& P = a.pops[pop];
+  const PopDev& P = a.pop;
+  const uint32_t* k0 = a.k0;
+  const uint32_t* k1 = a.k1;
   const int R_new = P.rec[a.t].R_tilde;
   const int tile0 = blockIdx.x * TJ;
   if (tile0 >= R_new) return;
@@ -66,10 +178,32 @@ __global__ void __launch_bounds__(NT) k_sweep(SweepArgs a) {
   const int word = tid % W;
   const int part = tid / W;
 
-  for (int i = tid; i < 4 * N; i += NT) jt[i] = a.jtab[i];
+  // site records: bond masks and the site/step parts of Philox rounds 1-3
+  for (int n = tid; n < N; n += NT) {
+    const int x = n % L, y = (n / L) % L, z = n / (L * L);
+    const int nxm = (x == 0 ? L - 1 : x - 1) + L * (y + L * z);
+    const int nym = x + L * ((y == 0 ? L - 1 : y - 1) + L * z);
+    const int nzm = x + L * (y + L * (z == 0 ? L - 1 : z - 1));
+    SiteRec r;
+    r.jxp = a.jtab[4 * n + 0] & kSpinBit;
+    r.jyp = a.jtab[4 * n + 1] & kSpinBit;
+    r.jzp = a.jtab[4 * n + 2] & kSpinBit;
+    r.jxm = a.jtab[4 * nxm + 0] & kSpinBit;
+    r.jym = a.jtab[4 * nym + 1] & kSpinBit;
+    r.jzm = a.jtab[4 * nzm + 2] & kSpinBit;
+    const uint32_t h = (uint32_t)n >> 1;
+    uint32_t hi0, lo0, hi1, lo1;
+    mulhilo(kM0, h, hi0, lo0);
+    const uint32_t c1 = hi0 ^ (uint32_t)a.t ^ k1[0];
+    mulhilo(kM1, c1, hi1, lo1);
+    r.ua = hi1 ^ k0[1];
+    r.ub = lo1 ^ k0[2];
+    recs[n] = r;
+  }
+  if (tid < 8) thr_tab[tid] = tid == 0 ? a.thr12 : tid == 1 ? a.thr8 : tid == 2 ? a.thr4 : 0u;
   for (int i = tid; i < TJ; i += NT) ecnt[i] = 0;
 
-  // 1. gather from the parents
+  // 1. gather from the parents (spin bit only)
   int par[4];
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
@@ -77,78 +211,70 @@ __global__ void __launch_bounds__(NT) k_sweep(SweepArgs a) {
     par[b] = j < R_new ? P.parents[j] : -1;
   }
   const int8_t* src = P.spins[a.cur];
+  // four consecutive, word-aligned parents: one 32-bit load per site
+  const bool contiguous = par[0] >= 0 && (par[0] & 3) == 0 && par[1] == par[0] + 1 && par[2] == par[0] + 2 &&
+                          par[3] == par[0] + 3;
+#pragma unroll 4
   for (int n = part; n < N; n += NP) {
     const int8_t* row = src + (size_t)n * a.pitch;
-    uint32_t w = 0;
+    uint32_t w;
+    if (contiguous) {
+      w = *reinterpret_cast<const uint32_t*>(row + par[0]);
+    } else {
+      w = 0;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const uint32_t v = par[b] >= 0 ? (uint32_t)(uint8_t)row[par[b]] : 0x01u;
-      w |= v << (8 * b);
+      for (int b = 0; b < 4; ++b) {
+        const uint32_t v = par[b] >= 0 ? (uint32_t)(uint8_t)row[par[b]] : 0x01u;
+        w |= v << (8 * b);
+      }
     }
-    sp[n * W + word] = w;
+    sp[n * W + word] = w & kSpinBit;
   }
   __syncthreads();
 
   // 2. sweeps
-  const uint32_t k0 = P.key_met[0], k1 = P.key_met[1];
-  const uint32_t wordidx = (uint32_t)(tile0 >> 2) + (uint32_t)word;
-  const uint32_t T4 = a.thr4, T8 = a.thr8, T12 = a.thr12;
+  const uint32_t g = (uint32_t)(tile0 >> 2) + (uint32_t)word;
   for (int s = 0; s < a.n_sweeps; ++s) {
 #pragma unroll 1
     for (int c = 0; c < 2; ++c) {
-      const uint32_t ctr1 = 2u * (uint32_t)s + (uint32_t)c;
+      const ThreadPhilox tp = thread_philox(g, 2u * (uint32_t)s + (uint32_t)c, k0, k1);
+#pragma unroll 1
       for (int r = part; r < ROWS; r += NP) {
         const int y = r % L, z = r / L;
         const int yp = y == L - 1 ? 0 : y + 1, ym = y == 0 ? L - 1 : y - 1;
         const int zp = z == L - 1 ? 0 : z + 1, zm = z == 0 ? L - 1 : z - 1;
-        const int b0 = r * L;
-        const int byp = (yp + L * z) * L, bym = (ym + L * z) * L;
-        const int bzp = (y + L * zp) * L, bzm = (y + L * zm) * L;
-        const int x0 = (y + z + c) & 1;
-#pragma unroll
-        for (int xh = 0; xh < L / 2; ++xh) {
-          const int x = 2 * xh + x0;
-          const int xp = x == L - 1 ? 0 : x + 1, xm = x == 0 ? L - 1 : x - 1;
-          const int n = b0 + x;
-          const uint32_t s0 = sp[n * W + word];
-          const uint32_t u2 = ((s0 ^ sp[(b0 + xp) * W + word] ^ jt[4 * n + 0]) & kBit1Mask) +
-                              ((s0 ^ sp[(b0 + xm) * W + word] ^ jt[4 * (b0 + xm) + 0]) & kBit1Mask) +
-                              ((s0 ^ sp[(byp + x) * W + word] ^ jt[4 * n + 1]) & kBit1Mask) +
-                              ((s0 ^ sp[(bym + x) * W + word] ^ jt[4 * (bym + x) + 1]) & kBit1Mask) +
-                              ((s0 ^ sp[(bzp + x) * W + word] ^ jt[4 * n + 2]) & kBit1Mask) +
-                              ((s0 ^ sp[(bzm + x) * W + word] ^ jt[4 * (bzm + x) + 2]) & kBit1Mask);
-          const uint4 rr = philox4x32_10(make_uint4((uint32_t)n >> 1, ctr1, wordidx, (uint32_t)a.t), k0, k1);
-          uint32_t fm = 0;
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const uint32_t u = (u2 >> (8 * b + 1)) & 7u;
-            const uint32_t rb = word_of(rr, b);
-            const bool acc = (u >= 3u) || (u == 2u ? rb < T4 : (u == 1u ? rb < T8 : rb < T12));
-            fm |= acc ? (0xFEu << (8 * b)) : 0u;
-          }
-          sp[n * W + word] = s0 ^ fm;
-        }
+        uint32_t* p0 = sp + (size_t)r * L * W + word;
+        const uint32_t* pyp = sp + (size_t)(yp + L * z) * L * W + word;
+        const uint32_t* pym = sp + (size_t)(ym + L * z) * L * W + word;
+        const uint32_t* pzp = sp + (size_t)(y + L * zp) * L * W + word;
+        const uint32_t* pzm = sp + (size_t)(y + L * zm) * L * W + word;
+        const SiteRec* rr = recs + r * L;
+        const uint32_t h0 = (uint32_t)(r * L) >> 1;  // L even: site r L + x has h = h0 + x / 2
+        if (((y + z + c) & 1) == 0)
+          sweep_row<L, W, 0>(h0, p0, pyp, pym, pzp, pzm, rr, thr_tab, tp, k0, k1);
+        else
+          sweep_row<L, W, 1>(h0, p0, pyp, pym, pzp, pzm, rr, thr_tab, tp, k0, k1);
       }
       __syncthreads();
     }
   }
 
-  // 3. energy levels: unsatisfied forward bonds of every site of the replicas
+  // 3. energy levels: unsatisfied forward bonds of every site (4 per bond per byte)
   {
     int cnt[4] = {0, 0, 0, 0};
     for (int r = part; r < ROWS; r += NP) {
       const int y = r % L, z = r / L;
       const int yp = y == L - 1 ? 0 : y + 1, zp = z == L - 1 ? 0 : z + 1;
-      const int b0 = r * L, byp = (yp + L * z) * L, bzp = (y + L * zp) * L;
-      uint32_t acc = 0;  // <= 6L per byte
+      const uint32_t* p0 = sp + (size_t)r * L * W + word;
+      const uint32_t* pyp = sp + (size_t)(yp + L * z) * L * W + word;
+      const uint32_t* pzp = sp + (size_t)(y + L * zp) * L * W + word;
+      const SiteRec* rr = recs + r * L;
+      uint32_t acc = 0;  // <= 12 L per byte
 #pragma unroll
       for (int x = 0; x < L; ++x) {
         const int xp = x == L - 1 ? 0 : x + 1;
-        const int n = b0 + x;
-        const uint32_t s0 = sp[n * W + word];
-        acc += ((s0 ^ sp[(b0 + xp) * W + word] ^ jt[4 * n + 0]) & kBit1Mask) +
-               ((s0 ^ sp[(byp + x) * W + word] ^ jt[4 * n + 1]) & kBit1Mask) +
-               ((s0 ^ sp[(bzp + x) * W + word] ^ jt[4 * n + 2]) & kBit1Mask);
+        const uint32_t s0 = p0[x * W];
+        acc += (s0 ^ p0[xp * W] ^ rr[x].jxp) + (s0 ^ pyp[x * W] ^ rr[x].jyp) + (s0 ^ pzp[x * W] ^ rr[x].jzp);
       }
 #pragma unroll
       for (int b = 0; b < 4; ++b) cnt[b] += (acc >> (8 * b)) & 0xFFu;
@@ -161,16 +287,16 @@ __global__ void __launch_bounds__(NT) k_sweep(SweepArgs a) {
   for (int i = tid; i < TJ; i += NT) {
     const int j = tile0 + i;
     if (j < R_new) {
-      const int k = ecnt[i] >> 1;
+      const int k = ecnt[i] >> 2;
       P.levels[j] = k;
       atomicAdd(&hist[k], 1u);
     }
   }
 
-  // 4. store the tile
+  // 4. store the tile as int8 +1 (0x01) / -1 (0xFF)
   uint32_t* dst = reinterpret_cast<uint32_t*>(P.spins[1 - a.cur]);
   const int64_t pw = a.pitch / 4;
-  for (int n = part; n < N; n += NP) dst[n * pw + (tile0 >> 2) + word] = sp[n * W + word];
+  for (int n = part; n < N; n += NP) dst[n * pw + (tile0 >> 2) + word] = (sp[n * W + word] >> 2) * 0xFEu + 0x01010101u;
 }
 
 template <int L, int W, int NT>
@@ -178,7 +304,7 @@ static int launch_t(const RunGeom& g, const SweepArgs& args, cudaStream_t s) {
   using S = SweepShape<L, W, NT>;
   cudaError_t e = cudaFuncSetAttribute(k_sweep<L, W, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
   if (e != cudaSuccess) return (int)e;
-  dim3 grid((unsigned)((g.R_cap + S::TJ - 1) / S::TJ), (unsigned)g.n_pop);
+  dim3 grid((unsigned)((g.R_cap + S::TJ - 1) / S::TJ));
   k_sweep<L, W, NT><<<grid, NT, S::SMEM, s>>>(args);
   return (int)cudaGetLastError();
 }
@@ -187,29 +313,41 @@ bool sweep_supported(int L) { return L >= 2 && L <= kMaxL && L % 2 == 0; }
 
 int launch_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, int t, int n_sweeps,
                  const uint32_t met_thr[3], void* stream) {
-  SweepArgs args;
-  for (int i = 0; i < g.n_pop && i < 2; ++i) args.pops[i] = pops[i];
-  args.jtab = jtab;
-  args.pitch = g.pitch;
-  args.n_levels = g.n_levels;
-  args.t = t;
-  args.cur = cur;
-  args.n_sweeps = n_sweeps;
-  args.thr4 = met_thr[0];
-  args.thr8 = met_thr[1];
-  args.thr12 = met_thr[2];
   cudaStream_t s = (cudaStream_t)stream;
-  switch (g.L) {
-    case 2: return launch_t<2, 32, 128>(g, args, s);
-    case 4: return launch_t<4, 32, 256>(g, args, s);
-    case 6: return launch_t<6, 32, 384>(g, args, s);
-    case 8: return launch_t<8, 32, 512>(g, args, s);
-    case 10: return launch_t<10, 32, 640>(g, args, s);
-    case 12: return launch_t<12, 16, 576>(g, args, s);
-    case 14: return launch_t<14, 8, 224>(g, args, s);
-    case 16: return launch_t<16, 8, 256>(g, args, s);
-    default: return (int)cudaErrorInvalidValue;
+  for (int i = 0; i < g.n_pop; ++i) {
+    SweepArgs args;
+    args.pop = pops[i];
+    uint32_t k0 = pops[i].key_met[0], k1 = pops[i].key_met[1];
+    for (int r = 0; r < 10; ++r) {
+      args.k0[r] = k0;
+      args.k1[r] = k1;
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    args.jtab = jtab;
+    args.pitch = g.pitch;
+    args.n_levels = g.n_levels;
+    args.t = t;
+    args.cur = cur;
+    args.n_sweeps = n_sweeps;
+    args.thr4 = met_thr[0];
+    args.thr8 = met_thr[1];
+    args.thr12 = met_thr[2];
+    int e;
+    switch (g.L) {
+      case 2: e = launch_t<2, 32, 128>(g, args, s); break;
+      case 4: e = launch_t<4, 32, 256>(g, args, s); break;
+      case 6: e = launch_t<6, 32, 384>(g, args, s); break;
+      case 8: e = launch_t<8, 32, 512>(g, args, s); break;
+      case 10: e = launch_t<10, 32, 640>(g, args, s); break;
+      case 12: e = launch_t<12, 16, 576>(g, args, s); break;
+      case 14: e = launch_t<14, 8, 224>(g, args, s); break;
+      case 16: e = launch_t<16, 4, 256>(g, args, s); break;
+      default: e = (int)cudaErrorInvalidValue;
+    }
+    if (e != 0) return e;
   }
+  return 0;
 }
 
 }  // namespace pa
