@@ -35,6 +35,12 @@
 #include "pa_device.cuh"
 #include "pa_internal.h"
 
+// Threads per CTA of the L = 10 sweep (a multiple of 32 whose row partitions
+// divide the 100 rows evenly: 640 = 20 partitions of 5 rows, 800 = 25 of 4).
+#ifndef PA_SWEEP_NT_L10
+#define PA_SWEEP_NT_L10 640
+#endif
+
 namespace pa {
 
 constexpr uint32_t kM0 = 0xD2511F53u;
@@ -123,39 +129,58 @@ __device__ __forceinline__ uint4 philox_tail(const SiteRec& sr, uint32_t uc, con
   return make_uint4(x0, x1, x2, x3);
 }
 
-// One row (y, z) of colour-X0 sites: x = X0, X0 + 2, ...  All neighbour offsets
-// are compile-time; pointers are at (row base, this thread's word).
+// One row (y, z) of colour-X0 sites: x = X0, X0 + 2, ...  The row is read in
+// full first (own row: all L sites, whose other-colour half are the x
+// neighbours; the four neighbour rows: the L/2 sites above/below the updated
+// ones), then every site of the row is updated from registers and written back,
+// so the L/2 Philox blocks of the row are independent instruction streams.
+// All neighbour offsets are compile-time; pointers are at (row base, word).
 template <int L, int W, int X0>
 __device__ __forceinline__ void sweep_row(uint32_t h0, uint32_t* __restrict__ p0, const uint32_t* __restrict__ pyp,
                                           const uint32_t* __restrict__ pym, const uint32_t* __restrict__ pzp,
                                           const uint32_t* __restrict__ pzm, const SiteRec* __restrict__ rec,
                                           const uint32_t* __restrict__ thr_tab, const ThreadPhilox& tp,
                                           const uint32_t* k0, const uint32_t* k1) {
+  constexpr int H = L / 2;
   const char* tb = reinterpret_cast<const char*>(thr_tab);
+  uint32_t row[L], nyp[H], nym[H], nzp[H], nzm[H];
 #pragma unroll
-  for (int xh = 0; xh < L / 2; ++xh) {
+  for (int x = 0; x < L; ++x) row[x] = p0[x * W];
+#pragma unroll
+  for (int xh = 0; xh < H; ++xh) {
+    const int x = 2 * xh + X0;
+    nyp[xh] = pyp[x * W];
+    nym[xh] = pym[x * W];
+    nzp[xh] = pzp[x * W];
+    nzm[xh] = pzm[x * W];
+  }
+  uint32_t out[H];
+#pragma unroll
+  for (int xh = 0; xh < H; ++xh) {
     const int x = 2 * xh + X0;
     const int xp = x == L - 1 ? 0 : x + 1;
     const int xm = x == 0 ? L - 1 : x - 1;
-    const SiteRec& sr = rec[x];
-    const uint32_t s0 = p0[x * W];
-    const uint32_t u4 = (s0 ^ p0[xp * W] ^ sr.jxp) + (s0 ^ p0[xm * W] ^ sr.jxm) + (s0 ^ pyp[x * W] ^ sr.jyp) +
-                        (s0 ^ pym[x * W] ^ sr.jym) + (s0 ^ pzp[x * W] ^ sr.jzp) + (s0 ^ pzm[x * W] ^ sr.jzm);
+    const SiteRec sr = rec[x];
+    const uint32_t s0 = row[x];
+    const uint32_t u4 = (s0 ^ row[xp] ^ sr.jxp) + (s0 ^ row[xm] ^ sr.jxm) + (s0 ^ nyp[xh] ^ sr.jyp) +
+                        (s0 ^ nym[xh] ^ sr.jym) + (s0 ^ nzp[xh] ^ sr.jzp) + (s0 ^ nzm[xh] ^ sr.jzm);
     const uint32_t uc = kM0 * (h0 + (uint32_t)(x >> 1));  // lo(M0 h), h = n >> 1
     const uint4 r = philox_tail(sr, uc, tp, k0, k1);
     // u >= 3 (dE <= 0): always flip
     const uint32_t always = ((u4 + 0x74747474u) >> 5) & kSpinBit;
-    uint32_t fm = always;
     const uint32_t t0 = *reinterpret_cast<const uint32_t*>(tb + (u4 & 0xFFu));
     const uint32_t t1 = *reinterpret_cast<const uint32_t*>(tb + __byte_perm(u4, 0u, 0x4441));
     const uint32_t t2 = *reinterpret_cast<const uint32_t*>(tb + __byte_perm(u4, 0u, 0x4442));
     const uint32_t t3 = *reinterpret_cast<const uint32_t*>(tb + (u4 >> 24));
+    uint32_t fm = always;
     fm |= r.x < t0 ? 0x00000004u : 0u;
     fm |= r.y < t1 ? 0x00000400u : 0u;
     fm |= r.z < t2 ? 0x00040000u : 0u;
     fm |= r.w < t3 ? 0x04000000u : 0u;
-    p0[x * W] = s0 ^ fm;
+    out[xh] = s0 ^ fm;
   }
+#pragma unroll
+  for (int xh = 0; xh < H; ++xh) p0[(2 * xh + X0) * W] = out[xh];
 }
 
 template <int L, int W, int NT>
@@ -214,21 +239,28 @@ __global__ void __launch_bounds__(NT) k_sweep(const __grid_constant__ SweepArgs 
   // four consecutive, word-aligned parents: one 32-bit load per site
   const bool contiguous = par[0] >= 0 && (par[0] & 3) == 0 && par[1] == par[0] + 1 && par[2] == par[0] + 2 &&
                           par[3] == par[0] + 3;
-#pragma unroll 4
-  for (int n = part; n < N; n += NP) {
-    const int8_t* row = src + (size_t)n * a.pitch;
-    uint32_t w;
-    if (contiguous) {
-      w = *reinterpret_cast<const uint32_t*>(row + par[0]);
-    } else {
-      w = 0;
+  // Rows are gathered GB at a time with every load issued before the first
+  // use, so each thread keeps 4 GB independent loads in flight.
+  constexpr int GB = (N / NP) % 10 == 0 ? 10 : ((N / NP) % 8 == 0 ? 8 : ((N / NP) % 4 == 0 ? 4 : 1));
+  for (int n0 = part; n0 < N; n0 += NP * GB) {
+    uint32_t v[GB][4];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const uint32_t v = par[b] >= 0 ? (uint32_t)(uint8_t)row[par[b]] : 0x01u;
-        w |= v << (8 * b);
+    for (int i = 0; i < GB; ++i) {
+      const int n = n0 + i * NP;
+      const int8_t* row = src + (size_t)(n < N ? n : 0) * a.pitch;
+      if (contiguous) {
+        v[i][0] = *reinterpret_cast<const uint32_t*>(row + par[0]);
+      } else {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) v[i][b] = par[b] >= 0 ? (uint32_t)(uint8_t)row[par[b]] : 0x01u;
       }
     }
-    sp[n * W + word] = w & kSpinBit;
+#pragma unroll
+    for (int i = 0; i < GB; ++i) {
+      const int n = n0 + i * NP;
+      const uint32_t w = contiguous ? v[i][0] : (v[i][0] | (v[i][1] << 8) | (v[i][2] << 16) | (v[i][3] << 24));
+      if (n < N) sp[n * W + word] = w & kSpinBit;
+    }
   }
   __syncthreads();
 
@@ -339,7 +371,7 @@ int launch_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, 
       case 4: e = launch_t<4, 32, 256>(g, args, s); break;
       case 6: e = launch_t<6, 32, 384>(g, args, s); break;
       case 8: e = launch_t<8, 32, 512>(g, args, s); break;
-      case 10: e = launch_t<10, 32, 640>(g, args, s); break;
+      case 10: e = launch_t<10, 32, PA_SWEEP_NT_L10>(g, args, s); break;
       case 12: e = launch_t<12, 16, 576>(g, args, s); break;
       case 14: e = launch_t<14, 8, 224>(g, args, s); break;
       case 16: e = launch_t<16, 4, 256>(g, args, s); break;
