@@ -40,6 +40,11 @@
 #ifndef PA_SWEEP_NT_L10
 #define PA_SWEEP_NT_L10 640
 #endif
+// Words per site row of the L = 10 tile (32: 128 replicas, one warp per row;
+// 16: 64 replicas, two rows per warp and two CTAs per SM).
+#ifndef PA_SWEEP_W_L10
+#define PA_SWEEP_W_L10 32
+#endif
 
 namespace pa {
 
@@ -75,14 +80,41 @@ struct SweepShape {
   static constexpr int NP = NT / W;  // row partitions
   static constexpr int TJ = 4 * W;   // replicas per tile
   static constexpr size_t SPIN_BYTES = (size_t)N * W * 4;
-  static constexpr size_t SMEM = SPIN_BYTES + (size_t)N * sizeof(SiteRec) + 8 * 4 + (size_t)TJ * 4;
+  static constexpr size_t SMEM = SPIN_BYTES + (size_t)N * sizeof(SiteRec) + (size_t)TJ * 4;
   static_assert(NT % W == 0, "threads must tile the words of a row");
   static_assert(32 % W == 0, "a warp must cover whole rows");
 };
 
+// Interleave the L/2 Philox blocks of a row round by round (1), or leave the
+// schedule of the L/2 independent blocks to the compiler (0).
+#ifndef PA_SWEEP_ROUND_MAJOR
+#define PA_SWEEP_ROUND_MAJOR 1
+#endif
+// 64-bit products as one wide multiply (0) or as separate high/low multiplies (1).
+#ifndef PA_SWEEP_SPLIT_MUL
+#define PA_SWEEP_SPLIT_MUL 0
+#endif
+
 __device__ __forceinline__ void mulhilo(uint32_t m, uint32_t a, uint32_t& hi, uint32_t& lo) {
+#if PA_SWEEP_SPLIT_MUL
+  asm("mul.hi.u32 %0, %1, %2;" : "=r"(hi) : "r"(m), "r"(a));
+  asm("mul.lo.u32 %0, %1, %2;" : "=r"(lo) : "r"(m), "r"(a));
+#else
   hi = __umulhi(m, a);
   lo = m * a;
+#endif
+}
+
+// Rows are visited in parity-class order: rho < L^2/2 are the rows with
+// (y + z) even, the rest odd, so consecutive rows share the x-offset of their
+// colour-c sites (a warp spanning several rows then runs one code path).
+template <int L>
+__device__ __forceinline__ void row_of(int rho, int& y, int& z, int& p) {
+  constexpr int HALF = L * L / 2, H = L / 2;
+  p = rho >= HALF;
+  const int i = rho - p * HALF;
+  z = i / H;
+  y = 2 * (i % H) + ((p + z) & 1);
 }
 
 // Per-thread, per-half-sweep part of rounds 1-3.
@@ -129,20 +161,58 @@ __device__ __forceinline__ uint4 philox_tail(const SiteRec& sr, uint32_t uc, con
   return make_uint4(x0, x1, x2, x3);
 }
 
-// One row (y, z) of colour-X0 sites: x = X0, X0 + 2, ...  The row is read in
-// full first (own row: all L sites, whose other-colour half are the x
-// neighbours; the four neighbour rows: the L/2 sites above/below the updated
-// ones), then every site of the row is updated from registers and written back,
-// so the L/2 Philox blocks of the row are independent instruction streams.
-// All neighbour offsets are compile-time; pointers are at (row base, word).
-template <int L, int W, int X0>
-__device__ __forceinline__ void sweep_row(uint32_t h0, uint32_t* __restrict__ p0, const uint32_t* __restrict__ pyp,
-                                          const uint32_t* __restrict__ pym, const uint32_t* __restrict__ pzp,
-                                          const uint32_t* __restrict__ pzm, const SiteRec* __restrict__ rec,
-                                          const uint32_t* __restrict__ thr_tab, const ThreadPhilox& tp,
-                                          const uint32_t* k0, const uint32_t* k1) {
+// Metropolis thresholds by 4u (bytes 0, 4, 8 -> u = 0, 1, 2; 12..28 unused), at a
+// fixed shared-memory address so that a lookup is one load at the byte offset.
+__shared__ __align__(16) uint32_t g_thr_tab[8];
+
+// Philox blocks of the L/2 colour sites of one row, rounds interleaved across
+// the sites.  Word b of block xh is the random number of replica 4g + b at site
+// h = h0 + xh (both colours of a site pair share h; the half-sweep is in tp).
+template <int L>
+__device__ __forceinline__ void philox_row(uint32_t h0, const SiteRec* __restrict__ rec, const ThreadPhilox& tp,
+                                           const uint32_t* k0, const uint32_t* k1, uint32_t (&q)[4][L / 2]) {
   constexpr int H = L / 2;
-  const char* tb = reinterpret_cast<const char*>(thr_tab);
+#pragma unroll
+  for (int xh = 0; xh < H; ++xh) {  // round 3 from the hoisted parts
+    const SiteRec& sr = rec[2 * xh];
+    const uint32_t uc = kM0 * (h0 + (uint32_t)xh);  // lo(M0 h)
+    uint32_t h, l, h2, l2;
+    mulhilo(kM1, tp.tb ^ uc, h, l);
+    mulhilo(kM0, sr.ua ^ tp.ta, h2, l2);
+    q[0][xh] = h ^ sr.ub;
+    q[1][xh] = l;
+    q[2][xh] = h2 ^ tp.tdk;
+    q[3][xh] = l2;
+  }
+#pragma unroll
+  for (int rr = 3; rr < 10; ++rr) {  // rounds 4..10
+#pragma unroll
+    for (int xh = 0; xh < H; ++xh) {
+      uint32_t h, l, h2, l2;
+      mulhilo(kM1, q[2][xh], h, l);
+      mulhilo(kM0, q[0][xh], h2, l2);
+      const uint32_t n0 = h ^ q[1][xh] ^ k0[rr];
+      const uint32_t n2 = h2 ^ q[3][xh] ^ k1[rr];
+      q[0][xh] = n0;
+      q[1][xh] = l;
+      q[2][xh] = n2;
+      q[3][xh] = l2;
+    }
+  }
+}
+
+// Metropolis update of the colour-X0 sites x = X0, X0 + 2, ... of one row from
+// the row's random words q.  The row is read in full first (own row: all L
+// sites, whose other-colour half are the x neighbours; the four neighbour rows:
+// the L/2 sites next to the updated ones), then updated and written back.  All
+// neighbour offsets are compile-time; pointers are at (row base, word).
+template <int L, int W, int X0>
+__device__ __forceinline__ void update_row(uint32_t* __restrict__ p0, const uint32_t* __restrict__ pyp,
+                                           const uint32_t* __restrict__ pym, const uint32_t* __restrict__ pzp,
+                                           const uint32_t* __restrict__ pzm, const SiteRec* __restrict__ rec,
+                                           const uint32_t (&q)[4][L / 2]) {
+  constexpr int H = L / 2;
+  const char* tb = reinterpret_cast<const char*>(g_thr_tab);
   uint32_t row[L], nyp[H], nym[H], nzp[H], nzm[H];
 #pragma unroll
   for (int x = 0; x < L; ++x) row[x] = p0[x * W];
@@ -154,33 +224,68 @@ __device__ __forceinline__ void sweep_row(uint32_t h0, uint32_t* __restrict__ p0
     nzp[xh] = pzp[x * W];
     nzm[xh] = pzm[x * W];
   }
-  uint32_t out[H];
 #pragma unroll
   for (int xh = 0; xh < H; ++xh) {
     const int x = 2 * xh + X0;
     const int xp = x == L - 1 ? 0 : x + 1;
     const int xm = x == 0 ? L - 1 : x - 1;
-    const SiteRec sr = rec[x];
+    const SiteRec& sr = rec[x];
     const uint32_t s0 = row[x];
     const uint32_t u4 = (s0 ^ row[xp] ^ sr.jxp) + (s0 ^ row[xm] ^ sr.jxm) + (s0 ^ nyp[xh] ^ sr.jyp) +
                         (s0 ^ nym[xh] ^ sr.jym) + (s0 ^ nzp[xh] ^ sr.jzp) + (s0 ^ nzm[xh] ^ sr.jzm);
-    const uint32_t uc = kM0 * (h0 + (uint32_t)(x >> 1));  // lo(M0 h), h = n >> 1
-    const uint4 r = philox_tail(sr, uc, tp, k0, k1);
-    // u >= 3 (dE <= 0): always flip
-    const uint32_t always = ((u4 + 0x74747474u) >> 5) & kSpinBit;
     const uint32_t t0 = *reinterpret_cast<const uint32_t*>(tb + (u4 & 0xFFu));
     const uint32_t t1 = *reinterpret_cast<const uint32_t*>(tb + __byte_perm(u4, 0u, 0x4441));
     const uint32_t t2 = *reinterpret_cast<const uint32_t*>(tb + __byte_perm(u4, 0u, 0x4442));
     const uint32_t t3 = *reinterpret_cast<const uint32_t*>(tb + (u4 >> 24));
-    uint32_t fm = always;
-    fm |= r.x < t0 ? 0x00000004u : 0u;
-    fm |= r.y < t1 ? 0x00000400u : 0u;
-    fm |= r.z < t2 ? 0x00040000u : 0u;
-    fm |= r.w < t3 ? 0x04000000u : 0u;
-    out[xh] = s0 ^ fm;
+    uint32_t acc = s0;  // spin bits, flipped where r < thr(u)
+    if (q[0][xh] < t0) acc ^= 0x00000004u;
+    if (q[1][xh] < t1) acc ^= 0x00000400u;
+    if (q[2][xh] < t2) acc ^= 0x00040000u;
+    if (q[3][xh] < t3) acc ^= 0x04000000u;
+    // u >= 3 (dE <= 0) always flips: u4 + 0x74 reaches bit 7 exactly when u4 >= 12;
+    // the table entries of those bytes are 0, so no compare above flipped them
+    p0[x * W] = (acc ^ ((u4 + 0x74747474u) >> 5)) & kSpinBit;
+  }
+}
+
+// Row k of a partition: rows of one parity class, interleaved across the
+// partitions of that class.
+template <int L, int NP>
+__device__ __forceinline__ int row_index(int part, int k, int p) {
+  constexpr int HALF = L * L / 2, H = L / 2, PC = NP / 2;
+  const int i = (part % PC) + k * PC;  // index within the class
+  const int z = i / H;
+  const int y = 2 * (i % H) + ((p + z) & 1);
+  return y + L * z;
+  (void)HALF;
+}
+
+// All rows of one partition for one half-sweep, colour sites at x = X0 mod 2:
+// the random words of row k+1 are computed in the same straight-line code as
+// the update of row k, so multiply-heavy and bitwise work overlap.
+template <int L, int W, int NP, int X0>
+__device__ __forceinline__ void sweep_rows(uint32_t* sp, const SiteRec* recs, int part, int p, const ThreadPhilox& tp,
+                                           const uint32_t* k0, const uint32_t* k1) {
+  constexpr int RPP = L * L / NP;  // rows per partition
+  uint32_t qa[4][L / 2], qb[4][L / 2];
+  {
+    const int r = row_index<L, NP>(part, 0, p);
+    philox_row<L>((uint32_t)(r * L) >> 1, recs + r * L, tp, k0, k1, qa);
   }
 #pragma unroll
-  for (int xh = 0; xh < H; ++xh) p0[(2 * xh + X0) * W] = out[xh];
+  for (int k = 0; k < RPP; ++k) {
+    const int r = row_index<L, NP>(part, k, p);
+    if (k + 1 < RPP) {
+      const int rn = row_index<L, NP>(part, k + 1, p);
+      philox_row<L>((uint32_t)(rn * L) >> 1, recs + rn * L, tp, k0, k1, (k & 1) ? qa : qb);
+    }
+    const int y = r % L, z = r / L;
+    const int yp = y == L - 1 ? 0 : y + 1, ym = y == 0 ? L - 1 : y - 1;
+    const int zp = z == L - 1 ? 0 : z + 1, zm = z == 0 ? L - 1 : z - 1;
+    update_row<L, W, X0>(sp + (size_t)r * L * W, sp + (size_t)(yp + L * z) * L * W, sp + (size_t)(ym + L * z) * L * W,
+                         sp + (size_t)(y + L * zp) * L * W, sp + (size_t)(y + L * zm) * L * W, recs + r * L,
+                         (k & 1) ? qb : qa);
+  }
 }
 
 template <int L, int W, int NT>
@@ -190,8 +295,8 @@ __global__ void __launch_bounds__(NT) k_sweep(const __grid_constant__ SweepArgs 
   extern __shared__ __align__(16) uint32_t sm[];
   uint32_t* sp = sm;                                                  // spins [N][W]
   SiteRec* recs = reinterpret_cast<SiteRec*>(sm + (size_t)N * W);     // [N]
-  uint32_t* thr_tab = reinterpret_cast<uint32_t*>(recs + N);          // [8]
-  int* ecnt = reinterpret_cast<int*>(thr_tab + 8);                    // [TJ]
+  uint32_t* thr_tab = g_thr_tab;
+  int* ecnt = reinterpret_cast<int*>(recs + N);                       // [TJ]
 
   const PopDev& P = a.pop;
   const uint32_t* k0 = a.k0;
@@ -264,29 +369,20 @@ __global__ void __launch_bounds__(NT) k_sweep(const __grid_constant__ SweepArgs 
   }
   __syncthreads();
 
-  // 2. sweeps
+  // 2. sweeps: partition `part` owns rows of parity class p = (y + z) & 1; in
+  // half-sweep c its colour sites sit at x = p ^ c mod 2 in every row.
+  static_assert(NP % 2 == 0 && (ROWS / 2) % (NP / 2) == 0, "row partitions must split each parity class");
   const uint32_t g = (uint32_t)(tile0 >> 2) + (uint32_t)word;
+  const int pclass = part / (NP / 2);
+  uint32_t* spw = sp + word;
   for (int s = 0; s < a.n_sweeps; ++s) {
 #pragma unroll 1
     for (int c = 0; c < 2; ++c) {
       const ThreadPhilox tp = thread_philox(g, 2u * (uint32_t)s + (uint32_t)c, k0, k1);
-#pragma unroll 1
-      for (int r = part; r < ROWS; r += NP) {
-        const int y = r % L, z = r / L;
-        const int yp = y == L - 1 ? 0 : y + 1, ym = y == 0 ? L - 1 : y - 1;
-        const int zp = z == L - 1 ? 0 : z + 1, zm = z == 0 ? L - 1 : z - 1;
-        uint32_t* p0 = sp + (size_t)r * L * W + word;
-        const uint32_t* pyp = sp + (size_t)(yp + L * z) * L * W + word;
-        const uint32_t* pym = sp + (size_t)(ym + L * z) * L * W + word;
-        const uint32_t* pzp = sp + (size_t)(y + L * zp) * L * W + word;
-        const uint32_t* pzm = sp + (size_t)(y + L * zm) * L * W + word;
-        const SiteRec* rr = recs + r * L;
-        const uint32_t h0 = (uint32_t)(r * L) >> 1;  // L even: site r L + x has h = h0 + x / 2
-        if (((y + z + c) & 1) == 0)
-          sweep_row<L, W, 0>(h0, p0, pyp, pym, pzp, pzm, rr, thr_tab, tp, k0, k1);
-        else
-          sweep_row<L, W, 1>(h0, p0, pyp, pym, pzp, pzm, rr, thr_tab, tp, k0, k1);
-      }
+      if ((pclass ^ c) == 0)
+        sweep_rows<L, W, NP, 0>(spw, recs, part, pclass, tp, k0, k1);
+      else
+        sweep_rows<L, W, NP, 1>(spw, recs, part, pclass, tp, k0, k1);
       __syncthreads();
     }
   }
@@ -371,7 +467,7 @@ int launch_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, 
       case 4: e = launch_t<4, 32, 256>(g, args, s); break;
       case 6: e = launch_t<6, 32, 384>(g, args, s); break;
       case 8: e = launch_t<8, 32, 512>(g, args, s); break;
-      case 10: e = launch_t<10, 32, PA_SWEEP_NT_L10>(g, args, s); break;
+      case 10: e = launch_t<10, PA_SWEEP_W_L10, PA_SWEEP_NT_L10>(g, args, s); break;
       case 12: e = launch_t<12, 16, 576>(g, args, s); break;
       case 14: e = launch_t<14, 8, 224>(g, args, s); break;
       case 16: e = launch_t<16, 4, 256>(g, args, s); break;
