@@ -165,15 +165,15 @@ __device__ __forceinline__ uint4 philox_tail(const SiteRec& sr, uint32_t uc, con
 // fixed shared-memory address so that a lookup is one load at the byte offset.
 __shared__ __align__(16) uint32_t g_thr_tab[8];
 
-// Philox blocks of the L/2 colour sites of one row, rounds interleaved across
-// the sites.  Word b of block xh is the random number of replica 4g + b at site
-// h = h0 + xh (both colours of a site pair share h; the half-sweep is in tp).
+// Philox blocks of the L/2 colour sites of one row.  Word b of block xh is the
+// random number of replica 4g + b at site h = h0 + xh (both colours of a site
+// pair share h; the half-sweep is folded into tp).  philox_init runs round 3
+// from the hoisted parts; philox_rounds runs rounds [r0, r1) of all blocks.
 template <int L>
-__device__ __forceinline__ void philox_row(uint32_t h0, const SiteRec* __restrict__ rec, const ThreadPhilox& tp,
-                                           const uint32_t* k0, const uint32_t* k1, uint32_t (&q)[4][L / 2]) {
-  constexpr int H = L / 2;
+__device__ __forceinline__ void philox_init(uint32_t h0, const SiteRec* __restrict__ rec, const ThreadPhilox& tp,
+                                            uint32_t (&q)[4][L / 2]) {
 #pragma unroll
-  for (int xh = 0; xh < H; ++xh) {  // round 3 from the hoisted parts
+  for (int xh = 0; xh < L / 2; ++xh) {
     const SiteRec& sr = rec[2 * xh];
     const uint32_t uc = kM0 * (h0 + (uint32_t)xh);  // lo(M0 h)
     uint32_t h, l, h2, l2;
@@ -184,10 +184,14 @@ __device__ __forceinline__ void philox_row(uint32_t h0, const SiteRec* __restric
     q[2][xh] = h2 ^ tp.tdk;
     q[3][xh] = l2;
   }
+}
+
+template <int L, int R0, int R1>
+__device__ __forceinline__ void philox_rounds(const uint32_t* k0, const uint32_t* k1, uint32_t (&q)[4][L / 2]) {
 #pragma unroll
-  for (int rr = 3; rr < 10; ++rr) {  // rounds 4..10
+  for (int rr = R0; rr < R1; ++rr) {  // key index rr = round rr + 1
 #pragma unroll
-    for (int xh = 0; xh < H; ++xh) {
+    for (int xh = 0; xh < L / 2; ++xh) {
       uint32_t h, l, h2, l2;
       mulhilo(kM1, q[2][xh], h, l);
       mulhilo(kM0, q[0][xh], h2, l2);
@@ -201,16 +205,27 @@ __device__ __forceinline__ void philox_row(uint32_t h0, const SiteRec* __restric
   }
 }
 
+// Rounds of the next row's Philox advanced after the update of site xh of the
+// current row: rounds 4..10 (key indices 3..9) spread over the L/2 sites.
+template <int L, int XH>
+__device__ __forceinline__ void philox_slice(const uint32_t* k0, const uint32_t* k1, uint32_t (&q)[4][L / 2]) {
+  constexpr int H = L / 2;
+  constexpr int R0 = 3 + (7 * XH) / H;
+  constexpr int R1 = 3 + (7 * (XH + 1)) / H;
+  philox_rounds<L, R0, R1>(k0, k1, q);
+}
+
 // Metropolis update of the colour-X0 sites x = X0, X0 + 2, ... of one row from
 // the row's random words q.  The row is read in full first (own row: all L
 // sites, whose other-colour half are the x neighbours; the four neighbour rows:
 // the L/2 sites next to the updated ones), then updated and written back.  All
 // neighbour offsets are compile-time; pointers are at (row base, word).
-template <int L, int W, int X0>
+template <int L, int W, int X0, bool NEXT>
 __device__ __forceinline__ void update_row(uint32_t* __restrict__ p0, const uint32_t* __restrict__ pyp,
                                            const uint32_t* __restrict__ pym, const uint32_t* __restrict__ pzp,
                                            const uint32_t* __restrict__ pzm, const SiteRec* __restrict__ rec,
-                                           const uint32_t (&q)[4][L / 2]) {
+                                           const uint32_t (&q)[4][L / 2], const uint32_t* k0, const uint32_t* k1,
+                                           uint32_t (&qn)[4][L / 2]) {
   constexpr int H = L / 2;
   const char* tb = reinterpret_cast<const char*>(g_thr_tab);
   uint32_t row[L], nyp[H], nym[H], nzp[H], nzm[H];
@@ -224,6 +239,8 @@ __device__ __forceinline__ void update_row(uint32_t* __restrict__ p0, const uint
     nzp[xh] = pzp[x * W];
     nzm[xh] = pzm[x * W];
   }
+  // phase 1: 4u per byte (unsatisfied bonds) of every site of the row
+  uint32_t u4[H];
 #pragma unroll
   for (int xh = 0; xh < H; ++xh) {
     const int x = 2 * xh + X0;
@@ -231,20 +248,40 @@ __device__ __forceinline__ void update_row(uint32_t* __restrict__ p0, const uint
     const int xm = x == 0 ? L - 1 : x - 1;
     const SiteRec& sr = rec[x];
     const uint32_t s0 = row[x];
-    const uint32_t u4 = (s0 ^ row[xp] ^ sr.jxp) + (s0 ^ row[xm] ^ sr.jxm) + (s0 ^ nyp[xh] ^ sr.jyp) +
-                        (s0 ^ nym[xh] ^ sr.jym) + (s0 ^ nzp[xh] ^ sr.jzp) + (s0 ^ nzm[xh] ^ sr.jzm);
-    const uint32_t t0 = *reinterpret_cast<const uint32_t*>(tb + (u4 & 0xFFu));
-    const uint32_t t1 = *reinterpret_cast<const uint32_t*>(tb + __byte_perm(u4, 0u, 0x4441));
-    const uint32_t t2 = *reinterpret_cast<const uint32_t*>(tb + __byte_perm(u4, 0u, 0x4442));
-    const uint32_t t3 = *reinterpret_cast<const uint32_t*>(tb + (u4 >> 24));
-    uint32_t acc = s0;  // spin bits, flipped where r < thr(u)
-    if (q[0][xh] < t0) acc ^= 0x00000004u;
-    if (q[1][xh] < t1) acc ^= 0x00000400u;
-    if (q[2][xh] < t2) acc ^= 0x00040000u;
-    if (q[3][xh] < t3) acc ^= 0x04000000u;
+    u4[xh] = (s0 ^ row[xp] ^ sr.jxp) + (s0 ^ row[xm] ^ sr.jxm) + (s0 ^ nyp[xh] ^ sr.jyp) + (s0 ^ nym[xh] ^ sr.jym) +
+             (s0 ^ nzp[xh] ^ sr.jzp) + (s0 ^ nzm[xh] ^ sr.jzm);
+  }
+  // phase 2: thresholds thr(u) of every replica of the row (all loads in flight together)
+  uint32_t th[4][H];
+#pragma unroll
+  for (int xh = 0; xh < H; ++xh) {
+    th[0][xh] = *reinterpret_cast<const uint32_t*>(tb + (u4[xh] & 0xFFu));
+    th[1][xh] = *reinterpret_cast<const uint32_t*>(tb + __byte_perm(u4[xh], 0u, 0x4441));
+    th[2][xh] = *reinterpret_cast<const uint32_t*>(tb + __byte_perm(u4[xh], 0u, 0x4442));
+    th[3][xh] = *reinterpret_cast<const uint32_t*>(tb + (u4[xh] >> 24));
+  }
+  // phase 3: flips and write-back
+#pragma unroll
+  for (int xh = 0; xh < H; ++xh) {
+    const int x = 2 * xh + X0;
+    uint32_t acc = row[x];  // spin bits, flipped where r < thr(u)
+    if (q[0][xh] < th[0][xh]) acc ^= 0x00000004u;
+    if (q[1][xh] < th[1][xh]) acc ^= 0x00000400u;
+    if (q[2][xh] < th[2][xh]) acc ^= 0x00040000u;
+    if (q[3][xh] < th[3][xh]) acc ^= 0x04000000u;
     // u >= 3 (dE <= 0) always flips: u4 + 0x74 reaches bit 7 exactly when u4 >= 12;
     // the table entries of those bytes are 0, so no compare above flipped them
-    p0[x * W] = (acc ^ ((u4 + 0x74747474u) >> 5)) & kSpinBit;
+    p0[x * W] = (acc ^ ((u4[xh] + 0x74747474u) >> 5)) & kSpinBit;
+    if (NEXT) {
+      if (xh == 0) philox_slice<L, 0>(k0, k1, qn);
+      if (xh == 1) philox_slice<L, 1>(k0, k1, qn);
+      if (xh == 2) philox_slice<L, 2>(k0, k1, qn);
+      if (xh == 3) philox_slice<L, 3>(k0, k1, qn);
+      if (xh == 4) philox_slice<L, 4>(k0, k1, qn);
+      if (xh == 5) philox_slice<L, 5>(k0, k1, qn);
+      if (xh == 6) philox_slice<L, 6>(k0, k1, qn);
+      if (xh == 7) philox_slice<L, 7>(k0, k1, qn);
+    }
   }
 }
 
@@ -267,24 +304,34 @@ template <int L, int W, int NP, int X0>
 __device__ __forceinline__ void sweep_rows(uint32_t* sp, const SiteRec* recs, int part, int p, const ThreadPhilox& tp,
                                            const uint32_t* k0, const uint32_t* k1) {
   constexpr int RPP = L * L / NP;  // rows per partition
+  static_assert(L / 2 <= 8, "the interleaved Philox slices cover at most 8 sites per row");
   uint32_t qa[4][L / 2], qb[4][L / 2];
   {
     const int r = row_index<L, NP>(part, 0, p);
-    philox_row<L>((uint32_t)(r * L) >> 1, recs + r * L, tp, k0, k1, qa);
+    philox_init<L>((uint32_t)(r * L) >> 1, recs + r * L, tp, qa);
+    philox_rounds<L, 3, 10>(k0, k1, qa);
   }
 #pragma unroll
   for (int k = 0; k < RPP; ++k) {
     const int r = row_index<L, NP>(part, k, p);
+    uint32_t(&cur)[4][L / 2] = (k & 1) ? qb : qa;
+    uint32_t(&nxt)[4][L / 2] = (k & 1) ? qa : qb;
     if (k + 1 < RPP) {
       const int rn = row_index<L, NP>(part, k + 1, p);
-      philox_row<L>((uint32_t)(rn * L) >> 1, recs + rn * L, tp, k0, k1, (k & 1) ? qa : qb);
+      philox_init<L>((uint32_t)(rn * L) >> 1, recs + rn * L, tp, nxt);
     }
     const int y = r % L, z = r / L;
     const int yp = y == L - 1 ? 0 : y + 1, ym = y == 0 ? L - 1 : y - 1;
     const int zp = z == L - 1 ? 0 : z + 1, zm = z == 0 ? L - 1 : z - 1;
-    update_row<L, W, X0>(sp + (size_t)r * L * W, sp + (size_t)(yp + L * z) * L * W, sp + (size_t)(ym + L * z) * L * W,
-                         sp + (size_t)(y + L * zp) * L * W, sp + (size_t)(y + L * zm) * L * W, recs + r * L,
-                         (k & 1) ? qb : qa);
+    uint32_t* p0 = sp + (size_t)r * L * W;
+    const uint32_t* pyp = sp + (size_t)(yp + L * z) * L * W;
+    const uint32_t* pym = sp + (size_t)(ym + L * z) * L * W;
+    const uint32_t* pzp = sp + (size_t)(y + L * zp) * L * W;
+    const uint32_t* pzm = sp + (size_t)(y + L * zm) * L * W;
+    if (k + 1 < RPP)
+      update_row<L, W, X0, true>(p0, pyp, pym, pzp, pzm, recs + r * L, cur, k0, k1, nxt);
+    else
+      update_row<L, W, X0, false>(p0, pyp, pym, pzp, pzm, recs + r * L, cur, k0, k1, nxt);
   }
 }
 
