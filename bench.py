@@ -39,10 +39,18 @@ if ROOT not in sys.path:
 
 METRIC = "Metropolis updates/s (L=10,R=1e6)"
 UNIT = "updates/s"
-# Integer instructions that one Philox4x32-10 word costs at least: each of the 10
-# rounds does two 32x32->64 multiplies and two 3-input XORs for four words.
-INT_OPS_PER_UPDATE = 10.0
-INT32_LANES_PER_SM = 128
+# Roofline of the sweep kernel: the 32x32->64 integer multiply.  Philox4x32-10
+# with the counter (site, half-sweep, group, step) needs 16 such multiplies per
+# block of four words once rounds 1-2 are hoisted (they depend only on the site
+# or only on the thread), i.e. 4 per site update; an SM issues 32 of them per
+# clock (128 int32 lanes, a 64-bit product taking four lane-slots; the
+# "mulwide" probe of include/pa_bench.h measures it).
+WIDE_MULS_PER_UPDATE = 4
+WIDE_MULS_PER_CLK_PER_SM = 32
+# HBM bytes per update of the sweep kernel: the tile is read (gather) and
+# written once per step, i.e. 2 bytes per site and replica every S sweeps, plus
+# 8 bytes of parent index and energy level per replica.
+
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sweep_L10_R1e6_adaptive.txt")
 SWEEP_SOURCE = os.path.join(ROOT, "paper_1711_02146_gb300", "csrc", "pa_sweep.cu")
 
@@ -215,6 +223,14 @@ def profile_traffic():
         return None
 
 
+def measured_hbm_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0  # fallback figure of an earlier GB300 measurement
+
+
 def ours(args):
     import torch
     rank, world, local = dist_env()
@@ -291,17 +307,22 @@ def ours(args):
     sweep_ms = st["phase_ms"]["sweep"] / max(st["phase_count"]["sweep"], 1)
     updates_per_launch = st["updates"] / max(st["phase_count"]["sweep"], 1)
     sm_mhz = clk["sm_mhz"] if clk else 2070.0
-    peak = n_sm * INT32_LANES_PER_SM * sm_mhz * 1e6 / 1e12       # Tera int32 ops/s
-    achieved = updates_per_launch * INT_OPS_PER_UPDATE / (sweep_ms / 1e3) / 1e12
+    peak = n_sm * (WIDE_MULS_PER_CLK_PER_SM / WIDE_MULS_PER_UPDATE) * sm_mhz * 1e6 / 1e9   # Gupdates/s
+    achieved = updates_per_launch / (sweep_ms / 1e3) / 1e9
     traffic = profile_traffic()
     if traffic is not None:
         traffic = traffic * updates_per_launch / (w.n_sweeps * w.N * w.R)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tint32op/s",
+    replicas = updates_per_launch / (w.n_sweeps * w.N)
+    hbm_bytes = 2.0 * w.N * replicas + 8.0 * replicas
+    hbm_peak = measured_hbm_gbs()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gupdates/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": "k_sweep<10,32,640>",
                 "launch_ms": sweep_ms, "updates_per_launch": updates_per_launch,
-                "peak_basis": f"{n_sm} SMs x {INT32_LANES_PER_SM} int32 lanes x {sm_mhz:.0f} MHz "
-                              f"({'median sampled under load' if clk else 'max clock, no samples'})",
-                "ops_per_update": INT_OPS_PER_UPDATE}
+                "peak_basis": f"{n_sm} SMs x {WIDE_MULS_PER_CLK_PER_SM} 64-bit multiplies/clk / "
+                              f"{WIDE_MULS_PER_UPDATE} per update x {sm_mhz:.0f} MHz "
+                              f"({'median SM clock sampled during the timed region' if clk else 'max clock, no samples'})",
+                "algorithmic_bytes_per_launch": hbm_bytes,
+                "hbm_GBps_achieved": hbm_bytes / (sweep_ms / 1e3) / 1e9, "hbm_GBps_peak_measured": hbm_peak}
     phase_share = {k: v / max(ms, 1e-9) for k, v in st["phase_ms"].items()}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": done,

@@ -311,7 +311,7 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
   g.L = cfg->L;
   g.N = cfg->L * cfg->L * cfg->L;
   g.n_levels = 3 * g.N + 1;
-  g.pitch = ((R_cap + 127) / 128) * 128;
+  g.pitch = ((R_cap + 255) / 256) * 256;  // a whole number of sweep tiles (<= 256 replicas)
   g.R = (int32_t)cfg->R;
   g.R_cap = (int32_t)R_cap;
   g.n_pop = cfg->n_pop;
