@@ -201,6 +201,40 @@ int pa_destroy(pa_ctx* ctx);
 /* Static description of a status code. */
 const char* pa_strerror(int status);
 
+/* ---- resampling without device allocation ----
+ * The paper has no counterpart: this is a service entry point for callers that
+ * cannot allocate device memory — code that runs under a framework's allocator
+ * that owns all device memory (a raw cudaMalloc there fails or fragments the
+ * pool), latency-critical loops in which cudaMalloc/cudaFree would synchronise
+ * the device, and deployments that budget device memory exactly.
+ *
+ * It computes what pa_step's resampling computes, on caller-owned DEVICE
+ * buffers: for old slots i < n_old with energy level levels[i] (unsatisfied
+ * bonds), the copy numbers counts[i] = fl[k] + [r_i < thr[k]] with
+ * r_i = word (i & 3) of Philox4x32-10 keyed by (run_seed, resampling, pop) at
+ * counter (i >> 2, 0, 0, t) (the nearest-integer rule of §II); the parent of
+ * every new slot j < min(*n_new, parents_cap) (parents[j] = i for
+ * offset_i <= j < offset_i + n_i, offsets the exclusive scan of the counts);
+ * and *n_new = sum_i n_i (device int64; parents beyond parents_cap are not
+ * written, so the caller compares *n_new with parents_cap).  fl and thr hold
+ * n_levels entries (floor(tau_k) and 2^32 frac(tau_k), as pa_step uses them).
+ *
+ * It allocates nothing: its scratch (the per-block totals of the scan) is a
+ * fixed 16 KiB array in the library's device memory, held by every GPU that
+ * loads the library until the process exits, which limits n_old to
+ * PA_NOALLOC_MAX_SLOTS (larger inputs return PA_ERR_INVALID before any launch).
+ * All calls on a device share that array: calls whose work overlaps on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller.  The first call on a device looks up the array's device address
+ * (once per device, with that device current), so make that first call before
+ * any stream capture.  Asynchronous on `cuda_stream` (NULL = legacy default
+ * stream); returns PA_OK, PA_ERR_INVALID or PA_ERR_CUDA. */
+#define PA_NOALLOC_MAX_BLOCKS 4096
+#define PA_NOALLOC_MAX_SLOTS (PA_NOALLOC_MAX_BLOCKS * 1024)
+int pa_resample_counts_noalloc(const int32_t* levels, int64_t n_old, const int32_t* fl, const uint32_t* thr,
+                               int32_t n_levels, uint64_t run_seed, int32_t pop, int32_t t, int32_t* counts,
+                               int32_t* parents, int64_t parents_cap, int64_t* n_new, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -128,9 +128,23 @@ SIGNATURES = {
     "pa_sync": (ctypes.c_int, [_vp]),
     "pa_destroy": (ctypes.c_int, [_vp]),
     "pa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "pa_resample_counts_noalloc": (ctypes.c_int, [_vp, ctypes.c_int64, _vp, _vp, ctypes.c_int32, ctypes.c_uint64,
+                                                   ctypes.c_int32, ctypes.c_int32, _vp, _vp, ctypes.c_int64, _vp,
+                                                   _vp]),
     "pa_bench_int_throughput": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
 }
+
+NOALLOC_MAX_SLOTS = 4096 * 1024
+
+
+def resample_counts_noalloc(levels, n_old, fl, thr, n_levels, run_seed, pop, t, counts, parents, parents_cap, n_new,
+                            stream=None) -> int:
+    """pa_resample_counts_noalloc on caller-owned device buffers (device pointers as ints,
+    e.g. torch tensors' data_ptr()); returns the status code."""
+    return int(lib().pa_resample_counts_noalloc(levels, n_old, fl, thr, n_levels, run_seed, pop, t, counts, parents,
+                                                parents_cap, n_new, _stream_handle(stream)))
+
 
 PROBES = {"lop3": 0, "iadd": 1, "imad": 2, "mulwide": 3, "philox": 4}
 
