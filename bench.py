@@ -33,6 +33,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -65,6 +67,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--R", type=int, default=0, help="override the population size (profiling runs)")
     ap.add_argument("--probe", action="store_true", help="also run the integer-throughput probes")
+    ap.add_argument("--batched-runs", type=int, default=64,
+                    help="runs of the batched mix (256 in the full workload; 0 = skip)")
+    ap.add_argument("--served-requests", type=int, default=128,
+                    help="requests of the serving stream (2000 in the full workload; 0 = skip)")
     return ap.parse_args()
 
 
@@ -223,6 +229,104 @@ def profile_traffic():
         return None
 
 
+def total_updates(w) -> int:
+    """Metropolis updates of a run with an explicit schedule, counting the target R
+    per step (the realised sizes fluctuate by O(sqrt R) around it)."""
+    return int(w.n_sweeps * w.N * w.R * (len(w.betas) - 1) * w.n_pop)
+
+
+def batched_vs_serial(pa, n_runs: int):
+    """The batched mix: all runs advanced together (pa_batch) vs one at a time
+    (pa_create + pa_run + pa_destroy), same GPU, creation included in both."""
+    import torch
+    from paper_1711_02146_gb300.workloads import batched_mix
+    ws = batched_mix(256)[:n_runs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b = pa.Batch(ws)
+    b.run()
+    t_batch = time.perf_counter() - t0
+    b.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for w in ws:
+        r = pa.Run.from_workload(w)
+        r.run()
+        r.close()
+    t_serial = time.perf_counter() - t0
+    upd = sum(total_updates(w) for w in ws)
+    return {"runs": len(ws), "workload": "L in {4,6,8,10}, R log-uniform [1e4,1e5], 101 linear temperatures, "
+                                        "10 sweeps (first %d of 256 disorder seeds 100..355)" % len(ws),
+            "runs_per_s": len(ws) / t_batch, "serial_runs_per_s": len(ws) / t_serial,
+            "speedup_vs_serial": t_serial / t_batch, "updates_per_s": upd / t_batch,
+            "serial_updates_per_s": upd / t_serial, "seconds": t_batch, "serial_seconds": t_serial}
+
+
+def served_vs_serial(pa, n_req: int, mem_budget: int):
+    """Continuous batching: requests arrive as a Poisson stream at 0.8 x the
+    served capacity (calibrated on the same mix) and are admitted by memory
+    footprint; latency = finish - arrival.  Serial: each request run alone, its
+    measured service time queued FIFO with the same arrivals."""
+    import torch
+    from paper_1711_02146_gb300.workloads import serving_stream
+    reqs = serving_stream(n_req)
+    ws = [w for w, _ in reqs]
+    # serial service times (one request at a time on the GPU)
+    service = []
+    for w in ws:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = pa.Run.from_workload(w)
+        r.run()
+        r.close()
+        service.append(time.perf_counter() - t0)
+    # capacity: everything submitted at once
+    srv = pa.Server(mem_budget, max_active=256, steps_per_poll=4)
+    t0 = time.perf_counter()
+    ids = [srv.submit(w) for w in ws]
+    pending = set(ids)
+    while pending:
+        for rid in srv.poll():
+            pending.discard(rid)
+    capacity = len(ws) / (time.perf_counter() - t0)
+    srv.close()
+    # the stream at 0.8 x capacity
+    gap = 1.0 / (0.8 * capacity)
+    arrivals = [a * gap for _, a in reqs]
+    srv = pa.Server(mem_budget, max_active=256, steps_per_poll=4)
+    t0 = time.perf_counter()
+    finish, arrive_of = {}, {}
+    nxt = 0
+    while len(finish) < len(ws):
+        now = time.perf_counter() - t0
+        while nxt < len(ws) and arrivals[nxt] <= now:
+            rid = srv.submit(ws[nxt])
+            arrive_of[rid] = arrivals[nxt]
+            nxt += 1
+        for rid in srv.poll():
+            finish[rid] = time.perf_counter() - t0
+    lat = np.array([finish[r] - arrive_of[r] for r in finish])
+    span = max(finish.values()) - arrivals[0]
+    srv.close()
+    # serial FIFO queue with the same arrivals
+    f_prev, slat = 0.0, []
+    for a, sv in zip(arrivals, service):
+        f_prev = max(a, f_prev) + sv
+        slat.append(f_prev - a)
+    slat = np.array(slat)
+    upd = sum(total_updates(w) for w in ws)
+    return {"requests": len(ws), "workload": "L in {4,6,8,10,12}, R log-uniform [1e3,2e5], 51/101/201 linear "
+                                             "temperatures, 10 sweeps, Poisson arrivals (first %d of 2000)" % len(ws),
+            "offered_load_runs_per_s": 0.8 * capacity, "capacity_runs_per_s": capacity,
+            "runs_per_s": len(ws) / span, "updates_per_s": upd / span,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "serial_runs_per_s": len(ws) / sum(service),
+            "serial_p50_latency_s": float(np.percentile(slat, 50)),
+            "serial_p99_latency_s": float(np.percentile(slat, 99)),
+            "throughput_vs_serial": (len(ws) / span) / (len(ws) / sum(service)),
+            "mem_budget_bytes": mem_budget}
+
+
 def measured_hbm_gbs():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -335,6 +439,11 @@ def ours(args):
             "roofline": roofline, "e2e": e2e, "gpu_launches": st["kernel_launches"],
             "phase_share": phase_share, "clocks": clk}
     run.close()
+    if rank == 0 and args.batched_runs > 0:
+        line["batched"] = batched_vs_serial(pa, args.batched_runs)
+    if rank == 0 and args.served_requests > 0:
+        free, _ = torch.cuda.mem_get_info()
+        line["served"] = served_vs_serial(pa, args.served_requests, int(0.5 * free))
     if args.probe:
         line["int_probes_per_s"] = {k: pa.int_throughput(k) for k in pa.PROBES}
 

@@ -201,6 +201,43 @@ int pa_destroy(pa_ctx* ctx);
 /* Static description of a status code. */
 const char* pa_strerror(int status);
 
+/* ---- many runs at once (SURVEY: batched and served workloads) ----
+ * Independent runs (different couplings, sizes, populations, schedules) share
+ * the GPU by running on their own non-blocking streams: their steps are issued
+ * round-robin from the host and their kernels overlap on the device.  Each run
+ * gives exactly the results it gives alone (its random streams depend only on
+ * its configuration).  These objects are not thread-safe. */
+
+/* Device bytes that pa_create allocates for cfg (for admission control). */
+int pa_footprint(const pa_config* cfg, size_t* bytes);
+
+typedef struct pa_batch pa_batch;
+/* Creates n runs (configs copied), each on its own stream. */
+int pa_batch_create(const pa_config* cfgs, int32_t n, pa_batch** out);
+/* Advances every run to the end of its schedule, one step of each run per
+ * round, then synchronises; returns PA_OK or the first error. */
+int pa_batch_run(pa_batch* batch);
+/* Borrowed view of run i (valid until pa_batch_destroy), for observables. */
+int pa_batch_ctx(pa_batch* batch, int32_t i, pa_ctx** view);
+int pa_batch_destroy(pa_batch* batch);
+
+/* Continuous-batching server: submitted runs wait in a FIFO queue and are
+ * admitted while the sum of admitted footprints stays within mem_budget bytes
+ * and at most max_active runs are on the GPU; every pa_server_poll issues up to
+ * steps_per_poll steps of each admitted run, retires runs whose last step has
+ * completed on the device (freeing their memory), admits waiting runs, and
+ * reports the ids that finished. */
+typedef struct pa_server pa_server;
+int pa_server_create(size_t mem_budget, int32_t max_active, int32_t steps_per_poll, pa_server** out);
+int pa_server_submit(pa_server* server, const pa_config* cfg, uint64_t* request_id);
+int pa_server_poll(pa_server* server, uint64_t* done_ids, int32_t cap, int32_t* n_done);
+/* Observables of population pop at the last step of a finished request, and
+ * that step's index; PA_ERR_STATE if the request has not finished. */
+int pa_server_result(pa_server* server, uint64_t request_id, int32_t pop, pa_obs* out, int32_t* last_step);
+/* Requests waiting and running. */
+int pa_server_load(pa_server* server, int32_t* queued, int32_t* active);
+int pa_server_destroy(pa_server* server);
+
 /* ---- resampling without device allocation ----
  * The paper has no counterpart: this is a service entry point for callers that
  * cannot allocate device memory — code that runs under a framework's allocator

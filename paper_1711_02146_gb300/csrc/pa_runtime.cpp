@@ -57,14 +57,18 @@ namespace {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? PA_OK : PA_ERR_CUDA; }
 
+// Copies are ordered on the run's stream and waited for on that stream only, so
+// runs on other streams keep going.
 int copy_d2h(pa_ctx* c, void* dst, const void* src, size_t bytes) {
   c->stats.d2h_bytes += (int64_t)bytes;
-  return cuda_status(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+  int rc = cuda_status(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream));
+  return rc == PA_OK ? cuda_status(cudaStreamSynchronize(c->stream)) : rc;
 }
 
 int copy_h2d(pa_ctx* c, void* dst, const void* src, size_t bytes) {
   c->stats.h2d_bytes += (int64_t)bytes;
-  return cuda_status(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice));
+  int rc = cuda_status(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+  return rc == PA_OK ? cuda_status(cudaStreamSynchronize(c->stream)) : rc;
 }
 
 cudaEvent_t next_event(pa_ctx* c) {
@@ -98,7 +102,8 @@ template <typename T>
 int dalloc(pa_ctx* c, T** p, size_t count) {
   void* q = nullptr;
   if (count == 0) count = 1;
-  if (cudaMalloc(&q, sizeof(T) * count) != cudaSuccess) {
+  // stream-ordered allocation: no device-wide synchronisation, so other runs keep going
+  if (cudaMallocAsync(&q, sizeof(T) * count, c->stream) != cudaSuccess) {
     cudaGetLastError();
     return PA_ERR_NOMEM;
   }
@@ -248,8 +253,7 @@ int measure(pa_ctx* c, int t) {
 
 void destroy(pa_ctx* c) {
   if (!c) return;
-  if (c->stream) cudaStreamSynchronize(c->stream);
-  for (void* p : c->allocations) cudaFree(p);
+  for (void* p : c->allocations) cudaFreeAsync(p, c->stream);
   for (cudaEvent_t e : c->events) cudaEventDestroy(e);
   delete c;
 }
@@ -271,6 +275,30 @@ const char* pa_strerror(int s) {
     case PA_ERR_EXTINCT: return "population became empty";
     default: return "unknown status";
   }
+}
+
+int pa_footprint(const pa_config* cfg, size_t* bytes) {
+  if (!cfg || !bytes || !pa::sweep_supported(cfg->L) || cfg->R < 1 || cfg->n_temps < 1 || cfg->n_pop < 1 ||
+      cfg->n_pop > 2)
+    return PA_ERR_INVALID;
+  const int64_t R_cap = cfg->R_cap ? cfg->R_cap : cfg->R + 10 * (int64_t)std::ceil(std::sqrt((double)cfg->R)) + 1024;
+  const size_t N = (size_t)cfg->L * cfg->L * cfg->L, nlev = 3 * N + 1, T = (size_t)cfg->n_temps;
+  const size_t pitch = (size_t)((R_cap + 255) / 256) * 256;
+  const size_t ncb = (size_t)((R_cap + pa::kSlotsPerCountBlock - 1) / pa::kSlotsPerCountBlock);
+  const size_t neb = (size_t)((R_cap + pa::kEntropyPerBlock - 1) / pa::kEntropyPerBlock);
+  size_t b = 3 * N + 16 * N + 4 + T * (size_t)cfg->q_bins * 8;
+  const size_t per_pop = 2 * N * pitch + 2 * 4 * pitch + 3 * 4 * pitch + 4 * ncb + 4 * T * nlev + 8 * nlev +
+                         4 * (size_t)cfg->R + 4 * ((size_t)R_cap + 1) + 8 * neb + T * sizeof(StepRec);
+  b += per_pop * (size_t)cfg->n_pop;
+  size_t tables = 1;
+  if (cfg->betas) {
+    std::map<uint64_t, int> distinct;
+    for (int t = 1; t < cfg->n_temps; ++t) distinct[bits_of(cfg->betas[t] - cfg->betas[t - 1])] = 1;
+    tables = distinct.size();
+  }
+  b += tables * nlev * 8;
+  *bytes = b;
+  return PA_OK;
 }
 
 int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
@@ -455,7 +483,7 @@ int pa_get_stats(pa_ctx* c, pa_stats* out) {
   for (const auto& ts : c->counted_steps)
     for (int p = 0; p < c->g.n_pop; ++p) {
       int32_t R = 0;
-      rc = cuda_status(cudaMemcpy(&R, &c->pops[p].rec[ts.first].R_tilde, sizeof R, cudaMemcpyDeviceToHost));
+      rc = copy_d2h(c, &R, &c->pops[p].rec[ts.first].R_tilde, sizeof R);
       if (rc != PA_OK) return fail(c, rc);
       st.updates += (int64_t)ts.second * c->g.N * R;
     }
@@ -571,8 +599,7 @@ int pa_energy_hist(pa_ctx* c, int32_t t, int32_t pop, int64_t* out, int64_t cap)
   int rc = pa_sync(c);
   if (rc != PA_OK) return rc;
   std::vector<uint32_t> h((size_t)c->g.n_levels);
-  rc = cuda_status(cudaMemcpy(h.data(), c->pops[pop].hist + (size_t)t * c->g.n_levels, sizeof(uint32_t) * h.size(),
-                              cudaMemcpyDeviceToHost));
+  rc = copy_d2h(c, h.data(), c->pops[pop].hist + (size_t)t * c->g.n_levels, sizeof(uint32_t) * h.size());
   if (rc != PA_OK) return fail(c, rc);
   for (size_t k = 0; k < h.size(); ++k) out[k] = h[k];
   return PA_OK;
@@ -585,8 +612,7 @@ int pa_q_hist(pa_ctx* c, int32_t t, int64_t* out, int64_t cap) {
   int rc = pa_sync(c);
   if (rc != PA_OK) return rc;
   std::vector<unsigned long long> q((size_t)c->g.q_bins);
-  rc = cuda_status(cudaMemcpy(q.data(), c->qhist + (size_t)t * c->g.q_bins, sizeof(unsigned long long) * q.size(),
-                              cudaMemcpyDeviceToHost));
+  rc = copy_d2h(c, q.data(), c->qhist + (size_t)t * c->g.q_bins, sizeof(unsigned long long) * q.size());
   if (rc != PA_OK) return fail(c, rc);
   for (size_t k = 0; k < q.size(); ++k) out[k] = (int64_t)q[k];
   return PA_OK;
@@ -597,10 +623,10 @@ int pa_family_hist(pa_ctx* c, int32_t pop, int64_t cap, int64_t* eta, int64_t* m
   int rc = pa_sync(c);
   if (rc != PA_OK) return rc;
   int32_t R = 0;
-  rc = cuda_status(cudaMemcpy(&R, &c->pops[pop].rec[c->t].R_tilde, sizeof R, cudaMemcpyDeviceToHost));
+  rc = copy_d2h(c, &R, &c->pops[pop].rec[c->t].R_tilde, sizeof R);
   std::vector<int32_t> mh((size_t)R + 1);
   if (rc == PA_OK)
-    rc = cuda_status(cudaMemcpy(mh.data(), c->pops[pop].mhist, sizeof(int32_t) * mh.size(), cudaMemcpyDeviceToHost));
+    rc = copy_d2h(c, mh.data(), c->pops[pop].mhist, sizeof(int32_t) * mh.size());
   if (rc != PA_OK) return fail(c, rc);
   int64_t k = 0;
   for (int64_t e = 1; e <= R; ++e)
@@ -620,7 +646,7 @@ int pa_population_size(pa_ctx* c, int32_t pop, int64_t* count) {
   int rc = pa_sync(c);
   if (rc != PA_OK) return rc;
   int32_t R = 0;
-  rc = cuda_status(cudaMemcpy(&R, &c->pops[pop].rec[c->t].R_tilde, sizeof R, cudaMemcpyDeviceToHost));
+  rc = copy_d2h(c, &R, &c->pops[pop].rec[c->t].R_tilde, sizeof R);
   if (rc != PA_OK) return fail(c, rc);
   *count = R;
   return PA_OK;
@@ -638,18 +664,20 @@ int pa_get_replicas(pa_ctx* c, int32_t pop, int64_t first, int64_t n, int8_t* sp
   const PopDev& P = c->pops[pop];
   if (spins) {
     std::vector<int8_t> tmp((size_t)g.N * (size_t)n);
-    rc = cuda_status(cudaMemcpy2D(tmp.data(), (size_t)n, P.spins[c->cur] + first, (size_t)g.pitch, (size_t)n,
-                                  (size_t)g.N, cudaMemcpyDeviceToHost));
+    c->stats.d2h_bytes += (int64_t)g.N * n;
+    rc = cuda_status(cudaMemcpy2DAsync(tmp.data(), (size_t)n, P.spins[c->cur] + first, (size_t)g.pitch, (size_t)n,
+                                       (size_t)g.N, cudaMemcpyDeviceToHost, c->stream));
+    if (rc == PA_OK) rc = cuda_status(cudaStreamSynchronize(c->stream));
     if (rc != PA_OK) return fail(c, rc);
     for (int64_t j = 0; j < n; ++j)
       for (int s = 0; s < g.N; ++s) spins[(size_t)j * g.N + s] = tmp[(size_t)s * n + j];
   }
   if (labels) {
-    rc = cuda_status(cudaMemcpy(labels, P.labels[c->cur] + first, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    rc = copy_d2h(c, labels, P.labels[c->cur] + first, sizeof(int32_t) * n);
     if (rc != PA_OK) return fail(c, rc);
   }
   if (energies) {
-    rc = cuda_status(cudaMemcpy(energies, P.levels + first, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    rc = copy_d2h(c, energies, P.levels + first, sizeof(int32_t) * n);
     if (rc != PA_OK) return fail(c, rc);
     for (int64_t j = 0; j < n; ++j) energies[j] = 2 * energies[j] - 3 * g.N;
   }
@@ -662,12 +690,12 @@ int pa_get_copy_counts(pa_ctx* c, int32_t pop, int32_t* counts, int64_t cap, int
   int rc = pa_sync(c);
   if (rc != PA_OK) return rc;
   StepRec r;
-  rc = cuda_status(cudaMemcpy(&r, c->pops[pop].rec + c->t, sizeof r, cudaMemcpyDeviceToHost));
+  rc = copy_d2h(c, &r, c->pops[pop].rec + c->t, sizeof r);
   if (rc != PA_OK) return fail(c, rc);
   *count = r.R_prev;
   if (r.R_prev > cap) return PA_ERR_CAPACITY;
   if (counts && r.R_prev > 0)
-    rc = cuda_status(cudaMemcpy(counts, c->pops[pop].counts, sizeof(int32_t) * r.R_prev, cudaMemcpyDeviceToHost));
+    rc = copy_d2h(c, counts, c->pops[pop].counts, sizeof(int32_t) * r.R_prev);
   return rc == PA_OK ? PA_OK : fail(c, rc);
 }
 
@@ -680,7 +708,7 @@ int pa_get_parents(pa_ctx* c, int32_t pop, int32_t* parents, int64_t cap, int64_
   *count = R;
   if (R > cap) return PA_ERR_CAPACITY;
   if (parents && R > 0)
-    rc = cuda_status(cudaMemcpy(parents, c->pops[pop].parents, sizeof(int32_t) * R, cudaMemcpyDeviceToHost));
+    rc = copy_d2h(c, parents, c->pops[pop].parents, sizeof(int32_t) * R);
   return rc == PA_OK ? PA_OK : fail(c, rc);
 }
 
@@ -689,7 +717,7 @@ int pa_get_couplings(pa_ctx* c, int8_t* J, int64_t cap) {
   if (cap < 3 * c->g.N) return PA_ERR_CAPACITY;
   int rc = pa_sync(c);
   if (rc != PA_OK) return rc;
-  rc = cuda_status(cudaMemcpy(J, c->J, (size_t)3 * c->g.N, cudaMemcpyDeviceToHost));
+  rc = copy_d2h(c, J, c->J, (size_t)3 * c->g.N);
   return rc == PA_OK ? PA_OK : fail(c, rc);
 }
 

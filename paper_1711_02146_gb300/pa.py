@@ -128,6 +128,18 @@ SIGNATURES = {
     "pa_sync": (ctypes.c_int, [_vp]),
     "pa_destroy": (ctypes.c_int, [_vp]),
     "pa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "pa_footprint": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_size_t)]),
+    "pa_batch_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_int32, ctypes.POINTER(_vp)]),
+    "pa_batch_run": (ctypes.c_int, [_vp]),
+    "pa_batch_ctx": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(_vp)]),
+    "pa_batch_destroy": (ctypes.c_int, [_vp]),
+    "pa_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_vp)]),
+    "pa_server_submit": (ctypes.c_int, [_vp, ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_uint64)]),
+    "pa_server_poll": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "pa_server_result": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(Obs),
+                                        ctypes.POINTER(ctypes.c_int32)]),
+    "pa_server_load": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "pa_server_destroy": (ctypes.c_int, [_vp]),
     "pa_resample_counts_noalloc": (ctypes.c_int, [_vp, ctypes.c_int64, _vp, _vp, ctypes.c_int32, ctypes.c_uint64,
                                                    ctypes.c_int32, ctypes.c_int32, _vp, _vp, ctypes.c_int64, _vp,
                                                    _vp]),
@@ -202,8 +214,137 @@ def _stream_handle(stream) -> Optional[int]:
     return int(stream.cuda_stream)  # torch.cuda.Stream
 
 
+class _ConfigHolder:
+    """A pa_config plus the arrays it points to (kept alive with it)."""
+
+    def __init__(self, L, R, disorder_seed, run_seed, betas=None, n_temps=0, beta_max=0.0, eps_target=0.0,
+                 n_sweeps=10, sweeps_per_step=None, n_pop=1, q_bins=65, R_cap=0):
+        self.betas = None if betas is None else np.ascontiguousarray(betas, dtype=np.float64)
+        self.sweeps = None if sweeps_per_step is None else np.ascontiguousarray(sweeps_per_step, dtype=np.int32)
+        c = Config()
+        c.L, c.n_pop, c.R, c.R_cap = L, n_pop, R, R_cap
+        c.disorder_seed, c.run_seed = disorder_seed, run_seed
+        c.n_temps = len(self.betas) if self.betas is not None else n_temps
+        c.betas = _p(self.betas, ctypes.c_double) if self.betas is not None else None
+        c.beta_max, c.eps_target, c.n_sweeps = beta_max, eps_target, n_sweeps
+        c.sweeps_per_step = _p(self.sweeps, ctypes.c_int32) if self.sweeps is not None else None
+        c.q_bins = q_bins
+        self.cfg = c
+
+    @classmethod
+    def from_workload(cls, w):
+        return cls(w.L, w.R, w.disorder_seed, w.run_seed, w.betas, n_temps=w.n_temps, beta_max=w.beta_max,
+                   eps_target=w.eps_target, n_sweeps=w.n_sweeps, n_pop=w.n_pop, q_bins=w.q_bins, R_cap=w.R_cap)
+
+
+def footprint(w) -> int:
+    """Device bytes a run of workload w allocates (pa_footprint)."""
+    h = _ConfigHolder.from_workload(w)
+    b = ctypes.c_size_t()
+    _check("pa_footprint", lib().pa_footprint(ctypes.byref(h.cfg), ctypes.byref(b)))
+    return b.value
+
+
+class _View:
+    """Observables of a borrowed pa_ctx (a run inside a batch)."""
+
+    def __init__(self, handle, owner, L, n_pop, q_bins):
+        self._h, self._owner = handle, owner
+        self.L, self.N, self.n_pop, self.q_bins = L, L ** 3, n_pop, q_bins
+        self.n_levels = 3 * self.N + 1
+
+
+class Batch:
+    """Many independent runs advanced together on their own streams (pa_batch)."""
+
+    def __init__(self, workloads):
+        self.workloads = list(workloads)
+        self._holders = [_ConfigHolder.from_workload(w) for w in self.workloads]
+        arr = (Config * len(self._holders))(*[h.cfg for h in self._holders])
+        self._arr = arr
+        h = _vp()
+        _check("pa_batch_create", lib().pa_batch_create(arr, len(self._holders), ctypes.byref(h)))
+        self._h = h
+
+    def run(self) -> None:
+        _check("pa_batch_run", lib().pa_batch_run(self._h))
+
+    def run_view(self, i: int) -> "Run":
+        v = _vp()
+        _check("pa_batch_ctx", lib().pa_batch_ctx(self._h, i, ctypes.byref(v)))
+        w = self.workloads[i]
+        return Run._borrowed(v, self, w.L, w.n_pop, w.q_bins)
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().pa_batch_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching server (pa_server): FIFO admission by device-memory footprint."""
+
+    def __init__(self, mem_budget: int, max_active: int = 256, steps_per_poll: int = 1):
+        h = _vp()
+        _check("pa_server_create", lib().pa_server_create(mem_budget, max_active, steps_per_poll, ctypes.byref(h)))
+        self._h = h
+        self._done = (ctypes.c_uint64 * 4096)()
+
+    def submit(self, w) -> int:
+        holder = _ConfigHolder.from_workload(w)
+        rid = ctypes.c_uint64()
+        _check("pa_server_submit", lib().pa_server_submit(self._h, ctypes.byref(holder.cfg), ctypes.byref(rid)))
+        return rid.value
+
+    def poll(self):
+        n = ctypes.c_int32()
+        _check("pa_server_poll", lib().pa_server_poll(self._h, self._done, len(self._done), ctypes.byref(n)))
+        return [int(self._done[i]) for i in range(n.value)]
+
+    def result(self, rid: int, pop: int = 0):
+        """(observables dict, last step) of a finished request; raises PAError with the
+        request's own status if it failed."""
+        o = Obs()
+        t = ctypes.c_int32()
+        _check("pa_server_result", lib().pa_server_result(self._h, rid, pop, ctypes.byref(o), ctypes.byref(t)))
+        return o.as_dict(), t.value
+
+    def load(self):
+        q, a = ctypes.c_int32(), ctypes.c_int32()
+        _check("pa_server_load", lib().pa_server_load(self._h, ctypes.byref(q), ctypes.byref(a)))
+        return q.value, a.value
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().pa_server_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Run:
     """One population annealing run on the GPU (a ``pa_ctx``)."""
+
+    @classmethod
+    def _borrowed(cls, handle, owner, L, n_pop, q_bins):
+        r = cls.__new__(cls)
+        r._h, r._owner, r._borrowed_view = handle, owner, True
+        r.L, r.N, r.n_pop, r.q_bins = L, L ** 3, n_pop, q_bins
+        r.n_levels = 3 * r.N + 1
+        r.n_temps = None
+        return r
 
     def __init__(self, L: int, R: int, disorder_seed: int, run_seed: int, betas=None, *, n_temps: int = 0,
                  beta_max: float = 0.0, eps_target: float = 0.0, n_sweeps: int = 10, sweeps_per_step=None,
@@ -233,6 +374,8 @@ class Run:
         return cls(w.L, w.R, w.disorder_seed, w.run_seed, w.betas, stream=stream, **kw)
 
     def close(self):
+        if getattr(self, "_borrowed_view", False):
+            return
         h = getattr(self, "_h", None)
         if h is not None and h.value:
             lib().pa_destroy(h)

@@ -1,0 +1,129 @@
+"""Batched and served runs (pa_batch, pa_server): every run gives exactly the
+result it gives alone, whatever else shares the GPU; admission respects the
+memory budget; a failing request does not disturb the others."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1711_02146_gb300.workloads import Workload, linear_betas
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pa():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_02146_gb300 import build, pa as pa_mod
+    build.build()
+    return pa_mod
+
+
+def mixed_workloads(n, seed=0):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        L = [4, 6, 8, 10][i % 4]
+        R = int(rng.integers(300, 3000))
+        T = int(rng.integers(4, 12))
+        out.append(Workload(f"mix{i}", L=L, R=R, disorder_seed=500 + i, run_seed=900 + i,
+                            betas=linear_betas(T, 2.5), n_sweeps=int(rng.integers(1, 4)), n_pop=1 + (i % 3 == 0)))
+    return out
+
+
+def standalone(pa, w):
+    r = pa.Run.from_workload(w)
+    r.run()
+    return r
+
+
+def assert_same_run(a, b, w):
+    t = a.t
+    assert b.t == t
+    for pop in range(w.n_pop):
+        assert a.obs(t, pop) == b.obs(t, pop)
+        sa, la, ea = a.population(pop)
+        sb, lb, eb = b.population(pop)
+        assert np.array_equal(sa, sb) and np.array_equal(la, lb) and np.array_equal(ea, eb)
+        assert np.array_equal(a.energy_hist(t, pop), b.energy_hist(t, pop))
+    if w.n_pop == 2:
+        assert np.array_equal(a.q_hist(t), b.q_hist(t))
+
+
+def test_batch_matches_standalone_runs(pa):
+    ws = mixed_workloads(9)
+    batch = pa.Batch(ws)
+    batch.run()
+    for i, w in enumerate(ws):
+        assert_same_run(batch.run_view(i), standalone(pa, w), w)
+    batch.close()
+
+
+def drain(server, ids, limit_s=120.0):
+    done = set()
+    t0 = time.time()
+    while len(done) < len(ids):
+        done.update(server.poll())
+        assert time.time() - t0 < limit_s, "server did not finish"
+    return done
+
+
+def test_server_results_identical_alone_and_in_the_mix(pa):
+    ws = mixed_workloads(12, seed=1)
+    budget = int(2.2 * max(pa.footprint(w) for w in ws))
+    server = pa.Server(budget, max_active=6, steps_per_poll=2)
+    ids = [server.submit(w) for w in ws]
+    peak_active = 0
+    done = set()
+    t0 = time.time()
+    while len(done) < len(ids):
+        done.update(server.poll())
+        q, a = server.load()
+        peak_active = max(peak_active, a)
+        assert a <= 6
+        assert time.time() - t0 < 120.0
+    assert peak_active >= 2           # requests did overlap on the device
+    for rid, w in zip(ids, ws):
+        ref = standalone(pa, w)
+        for pop in range(w.n_pop):
+            obs, last = server.result(rid, pop)
+            assert last == ref.t
+            assert obs == ref.obs(ref.t, pop)
+    server.close()
+
+
+def test_server_isolates_a_failing_request(pa, oracle_lib):
+    betas = linear_betas(6, 3.0)
+    for run_seed in range(30):  # a seed whose population outgrows a capacity equal to R
+        ref = oracle_lib.Run(oracle_lib.RunConfig(L=4, R=500, disorder_seed=1, run_seed=run_seed, betas=betas,
+                                                  n_sweeps=1, R_cap=500))
+        try:
+            ref.run()
+        except RuntimeError:
+            break
+    else:
+        pytest.skip("no overflowing seed found")
+    bad = Workload("bad", L=4, R=500, disorder_seed=1, run_seed=run_seed, betas=betas, n_sweeps=1, R_cap=500)
+    good = mixed_workloads(5, seed=2)
+    server = pa.Server(int(1e10), max_active=8)
+    ids = [server.submit(w) for w in good[:2]] + [server.submit(bad)] + [server.submit(w) for w in good[2:]]
+    drain(server, ids)
+    with pytest.raises(pa.PAError) as e:
+        server.result(ids[2])
+    assert e.value.status == pa.PA_ERR_CAPACITY
+    for rid, w in zip(ids[:2] + ids[3:], good):
+        ref = standalone(pa, w)
+        obs, last = server.result(rid)
+        assert last == ref.t and obs == ref.obs(ref.t)
+    server.close()
+
+
+def test_server_rejects_requests_beyond_the_budget(pa):
+    from paper_1711_02146_gb300.workloads import C1
+    server = pa.Server(1000)
+    with pytest.raises(pa.PAError) as e:
+        server.submit(C1)
+    assert e.value.status == pa.PA_ERR_NOMEM
+    server.close()
