@@ -261,27 +261,16 @@ __device__ __forceinline__ uint32_t nibbles_to_bytes(uint32_t x) {
   return b * 0xFEu + 0x01010101u;
 }
 
-template <int L, int W, int NT>
-__global__ void __launch_bounds__(NT, 1) k_sweep(const __grid_constant__ SweepArgs a) {
-  using S = SweepShape<L, W, NT>;
-  constexpr int N = S::N, NP = S::NP, TJ = S::TJ, ROWS = S::ROWS;
-  extern __shared__ __align__(16) uint32_t sm[];
-  uint32_t* sp = sm;                                               // spins [N][W]
-  SiteRec* recs = reinterpret_cast<SiteRec*>(sm + (size_t)N * W);  // [N]
-  int* ecnt = reinterpret_cast<int*>(recs + N);                    // [TJ]
+// ---- phases of a tile shared by both sweep kernels (nt consumer threads take part)
 
-  const PopDev& P = a.pop;
+// Site records (bond masks, site/step parts of Philox rounds 1-3) and the
+// threshold-pair table; all `nthreads` threads of the CTA help.
+template <int L>
+__device__ __forceinline__ void init_tables(const SweepArgs& a, SiteRec* recs, int tid, int nthreads) {
+  constexpr int N = L * L * L;
   const uint32_t* k0 = a.k0;
   const uint32_t* k1 = a.k1;
-  const int R_new = P.rec[a.t].R_tilde;
-  const int tile0 = blockIdx.x * TJ;
-  if (tile0 >= R_new) return;
-  const int tid = threadIdx.x;
-  const int word = tid % W;
-  const int part = tid / W;
-
-  // site records: bond masks and the site/step parts of Philox rounds 1-3
-  for (int n = tid; n < N; n += NT) {
+  for (int n = tid; n < N; n += nthreads) {
     const int x = n % L, y = (n / L) % L, z = n / (L * L);
     const int nxm = (x == 0 ? L - 1 : x - 1) + L * (y + L * z);
     const int nym = x + L * ((y == 0 ? L - 1 : y - 1) + L * z);
@@ -302,15 +291,20 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(const __grid_constant__ SweepAr
     r.ub = lo1 ^ k0[2];
     recs[n] = r;
   }
-  for (int b = tid; b < 256; b += NT) {
+  for (int b = tid; b < 256; b += nthreads) {
     const int lo = (b & 15) - 5, hi = (b >> 4) - 5;  // u of the two replicas
     const uint32_t tlo = lo == 0 ? a.thr12 : lo == 1 ? a.thr8 : lo == 2 ? a.thr4 : 0u;
     const uint32_t thi = hi == 0 ? a.thr12 : hi == 1 ? a.thr8 : hi == 2 ? a.thr4 : 0u;
     g_thr_pair[b] = make_uint2(tlo, thi);
   }
-  for (int i = tid; i < TJ; i += NT) ecnt[i] = 0;
+}
 
-  // 1. gather from the parents
+// Gather the tile's spins from the parents of its slots (nibble-packed).
+template <int L, int W, int NP>
+__device__ __forceinline__ void gather_tile(const SweepArgs& a, uint32_t* sp, int tile0, int R_new, int word,
+                                            int part) {
+  constexpr int N = L * L * L;
+  const PopDev& P = a.pop;
   int par[8];
 #pragma unroll
   for (int b = 0; b < 8; ++b) {
@@ -347,9 +341,87 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(const __grid_constant__ SweepAr
       if (n < N) sp[n * W + word] = bytes_to_nibbles(vv[i].x) | (bytes_to_nibbles(vv[i].y) << 16);
     }
   }
+}
+
+// Unsatisfied forward bonds of every replica of the tile, summed into ecnt.
+template <int L, int W, int NP>
+__device__ __forceinline__ void count_levels(const uint32_t* sp, const SiteRec* recs, int* ecnt, int word, int part) {
+  constexpr int ROWS = L * L;
+  int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int r = part; r < ROWS; r += NP) {
+    const int y = r % L, z = r / L;
+    const int yp = y == L - 1 ? 0 : y + 1, zp = z == L - 1 ? 0 : z + 1;
+    const uint32_t* p0 = sp + (size_t)r * L * W + word;
+    const uint32_t* pyp = sp + (size_t)(yp + L * z) * L * W + word;
+    const uint32_t* pzp = sp + (size_t)(y + L * zp) * L * W + word;
+    const SiteRec* rr = recs + r * L;
+    uint32_t even = 0, odd = 0;  // nibbles 0,2,4,6 / 1,3,5,7 in byte lanes, <= 3L each
+#pragma unroll
+    for (int x = 0; x < L; ++x) {
+      const int xp = x == L - 1 ? 0 : x + 1;
+      const uint32_t s0 = p0[x * W];
+      const uint32_t e = (s0 ^ p0[xp * W] ^ rr[x].jxp) + (s0 ^ pyp[x * W] ^ rr[x].jyp) + (s0 ^ pzp[x * W] ^ rr[x].jzp);
+      even += e & 0x0F0F0F0Fu;
+      odd += (e >> 4) & 0x0F0F0F0Fu;
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      cnt[2 * b] += (even >> (8 * b)) & 0xFFu;
+      cnt[2 * b + 1] += (odd >> (8 * b)) & 0xFFu;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) atomicAdd(&ecnt[8 * word + i], cnt[i]);
+}
+
+// Levels and histogram of the tile's slots (after count_levels and a barrier).
+template <int TJ>
+__device__ __forceinline__ void publish_levels(const SweepArgs& a, const int* ecnt, int tile0, int R_new, int tid,
+                                               int nthreads) {
+  const PopDev& P = a.pop;
+  uint32_t* hist = P.hist + (size_t)a.t * a.n_levels;
+  for (int i = tid; i < TJ; i += nthreads) {
+    const int j = tile0 + i;
+    if (j < R_new) {
+      const int k = ecnt[i];
+      P.levels[j] = k;
+      atomicAdd(&hist[k], 1u);
+    }
+  }
+}
+
+// Write the tile back as int8 +1 (0x01) / -1 (0xFF).
+template <int L, int W, int NP>
+__device__ __forceinline__ void store_tile(const SweepArgs& a, const uint32_t* sp, int tile0, int word, int part) {
+  constexpr int N = L * L * L;
+  int8_t* dst = a.pop.spins[1 - a.cur];
+  for (int n = part; n < N; n += NP) {
+    const uint32_t w = sp[n * W + word];
+    *reinterpret_cast<uint2*>(dst + (size_t)n * a.pitch + tile0 + 8 * word) =
+        make_uint2(nibbles_to_bytes(w), nibbles_to_bytes(w >> 16));
+  }
+}
+
+// Row-partitioned sweep kernel: every warp generates its own random words and
+// updates its rows.
+template <int L, int W, int NT>
+__global__ void __launch_bounds__(NT, 1) k_sweep(const __grid_constant__ SweepArgs a) {
+  using S = SweepShape<L, W, NT>;
+  constexpr int N = S::N, NP = S::NP, TJ = S::TJ;
+  extern __shared__ __align__(16) uint32_t sm[];
+  uint32_t* sp = sm;                                               // spins [N][W]
+  SiteRec* recs = reinterpret_cast<SiteRec*>(sm + (size_t)N * W);  // [N]
+  int* ecnt = reinterpret_cast<int*>(recs + N);                    // [TJ]
+  const int R_new = a.pop.rec[a.t].R_tilde;
+  const int tile0 = blockIdx.x * TJ;
+  if (tile0 >= R_new) return;
+  const int tid = threadIdx.x, word = tid % W, part = tid / W;
+  init_tables<L>(a, recs, tid, NT);
+  for (int i = tid; i < TJ; i += NT) ecnt[i] = 0;
+  gather_tile<L, W, NP>(a, sp, tile0, R_new, word, part);
   __syncthreads();
 
-  // 2. sweeps: partition `part` owns rows of parity class p = (y + z) & 1; in
+  // sweeps: partition `part` owns rows of parity class p = (y + z) & 1; in
   // half-sweep c its colour sites sit at x = p ^ c mod 2 in every row.
   const uint32_t g0 = 2u * ((uint32_t)(tile0 >> 3) + (uint32_t)word);  // Philox group of nibbles 0..3
   const int pclass = part / (NP / 2);
@@ -358,62 +430,19 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(const __grid_constant__ SweepAr
 #pragma unroll 1
     for (int c = 0; c < 2; ++c) {
       const uint32_t q = 2u * (uint32_t)s + (uint32_t)c;
-      const ThreadPhilox tpa = thread_philox(g0, q, k0, k1);
-      const ThreadPhilox tpb = thread_philox(g0 + 1u, q, k0, k1);
+      const ThreadPhilox tpa = thread_philox(g0, q, a.k0, a.k1);
+      const ThreadPhilox tpb = thread_philox(g0 + 1u, q, a.k0, a.k1);
       if ((pclass ^ c) == 0)
-        sweep_rows<L, W, NP, 0>(spw, recs, part, pclass, tpa, tpb, k0, k1);
+        sweep_rows<L, W, NP, 0>(spw, recs, part, pclass, tpa, tpb, a.k0, a.k1);
       else
-        sweep_rows<L, W, NP, 1>(spw, recs, part, pclass, tpa, tpb, k0, k1);
+        sweep_rows<L, W, NP, 1>(spw, recs, part, pclass, tpa, tpb, a.k0, a.k1);
       __syncthreads();
     }
   }
-
-  // 3. energy levels: unsatisfied forward bonds of every site
-  {
-    int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int r = part; r < ROWS; r += NP) {
-      const int y = r % L, z = r / L;
-      const int yp = y == L - 1 ? 0 : y + 1, zp = z == L - 1 ? 0 : z + 1;
-      const uint32_t* p0 = sp + (size_t)r * L * W + word;
-      const uint32_t* pyp = sp + (size_t)(yp + L * z) * L * W + word;
-      const uint32_t* pzp = sp + (size_t)(y + L * zp) * L * W + word;
-      const SiteRec* rr = recs + r * L;
-      uint32_t even = 0, odd = 0;  // nibbles 0,2,4,6 / 1,3,5,7 in byte lanes, <= 3L each
-#pragma unroll
-      for (int x = 0; x < L; ++x) {
-        const int xp = x == L - 1 ? 0 : x + 1;
-        const uint32_t s0 = p0[x * W];
-        const uint32_t e = (s0 ^ p0[xp * W] ^ rr[x].jxp) + (s0 ^ pyp[x * W] ^ rr[x].jyp) + (s0 ^ pzp[x * W] ^ rr[x].jzp);
-        even += e & 0x0F0F0F0Fu;
-        odd += (e >> 4) & 0x0F0F0F0Fu;
-      }
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        cnt[2 * b] += (even >> (8 * b)) & 0xFFu;
-        cnt[2 * b + 1] += (odd >> (8 * b)) & 0xFFu;
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) atomicAdd(&ecnt[8 * word + i], cnt[i]);
-  }
+  count_levels<L, W, NP>(sp, recs, ecnt, word, part);
   __syncthreads();
-  uint32_t* hist = P.hist + (size_t)a.t * a.n_levels;
-  for (int i = tid; i < TJ; i += NT) {
-    const int j = tile0 + i;
-    if (j < R_new) {
-      const int k = ecnt[i];
-      P.levels[j] = k;
-      atomicAdd(&hist[k], 1u);
-    }
-  }
-
-  // 4. store the tile as int8 +1 (0x01) / -1 (0xFF)
-  int8_t* dst = P.spins[1 - a.cur];
-  for (int n = part; n < N; n += NP) {
-    const uint32_t w = sp[n * W + word];
-    *reinterpret_cast<uint2*>(dst + (size_t)n * a.pitch + tile0 + 8 * word) =
-        make_uint2(nibbles_to_bytes(w), nibbles_to_bytes(w >> 16));
-  }
+  publish_levels<TJ>(a, ecnt, tile0, R_new, tid, NT);
+  store_tile<L, W, NP>(a, sp, tile0, word, part);
 }
 
 template <int L, int W, int NT>
