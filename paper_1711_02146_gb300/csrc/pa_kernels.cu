@@ -121,8 +121,8 @@ __global__ void k_levels_and_hist(RunGeom g, PopArgs a, int cur, const uint32_t*
 // weights w[j] = exp(-dbeta 2j) (computed on the host in FP64):
 //   S' = sum_{k >= kmin} c(k) w[k - kmin]         (ascending k, separate mul/add)
 //   tau_k = R w[k - kmin] / S'  ->  fl_k = floor(tau_k), thr_k = 2^32 (tau_k - fl_k)
-//   eps = (1/R) sum_k c(k) (1 - tau_k)_+          (Eq. eq_num_elim)
-// Empty levels add exact zeros to both sums, so they are skipped.
+//   eps = (1/R) sum_k c(k) (1 - tau_k)_+          (Eq. eq_num_elim; fixed tree order)
+// Empty levels add exact zeros to S', so they are skipped there.
 __global__ void k_reweight(RunGeom g, PopArgs a, const double* __restrict__ w, int t) {
   extern __shared__ int lst[];  // n_levels entries: occupied levels, ascending
   __shared__ int scratch[33];
@@ -153,6 +153,7 @@ __global__ void k_reweight(RunGeom g, PopArgs a, const double* __restrict__ w, i
   __syncthreads();
   const double S = S_sh;
   const double Rd = (double)g.R;
+  double eps_part = 0.0;  // this thread's levels, ascending
   for (int k = threadIdx.x; k < g.n_levels; k += blockDim.x) {
     int f = 0;
     uint32_t th = 0u;
@@ -161,20 +162,23 @@ __global__ void k_reweight(RunGeom g, PopArgs a, const double* __restrict__ w, i
       const double fl = floor(tau);
       f = (int)fl;
       th = (uint32_t)__dmul_rn(__dsub_rn(tau, fl), 4294967296.0);
+      if (tau < 1.0 && c[k] > 0u) eps_part = __dadd_rn(eps_part, __dmul_rn((double)c[k], __dsub_rn(1.0, tau)));
     }
     P.fl[k] = f;
     P.thr[k] = th;
   }
+  // expected culling fraction (Eq. eq_num_elim / R): fixed tree over the threads
+  __shared__ double eps_sh[1024];
+  eps_sh[threadIdx.x] = eps_part;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) eps_sh[threadIdx.x] = __dadd_rn(eps_sh[threadIdx.x], eps_sh[threadIdx.x + h]);
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
-    double eps = 0.0;
-    for (int i = 0; i < nnz; ++i) {
-      const int k = lst[i];
-      const double tau = __ddiv_rn(__dmul_rn(Rd, w[k - kmin]), S);
-      if (tau < 1.0) eps = __dadd_rn(eps, __dmul_rn((double)c[k], __dsub_rn(1.0, tau)));
-    }
     StepRec& r = P.rec[t];
     r.S_prime = S;
-    r.eps_expected = __ddiv_rn(eps, Rd);
+    r.eps_expected = __ddiv_rn(eps_sh[0], Rd);
     r.kmin_prev = kmin;
     r.R_prev = P.rec[t - 1].R_tilde;
   }
@@ -284,20 +288,21 @@ __global__ void k_fam_count(RunGeom g, PopArgs a, int cur, int t) {
   if (l >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&P.famcnt[l], __popc(peers));
 }
 
-// sum eta^2, alive families, and the family-size histogram m(eta).
+// sum eta^2, alive families, and the family-size histogram m(eta).  Lanes of a
+// warp with the same family size add to m(eta) with one atomic (most families
+// share a few small sizes, so per-thread atomics would pile onto one address).
 __global__ void k_fam_reduce(RunGeom g, PopArgs a, int t) {
   __shared__ unsigned long long red[2][32];
   const PopDev& P = a.p[blockIdx.y];
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long s2 = 0, nf = 0;
-  if (l < g.R) {
-    const int eta = P.famcnt[l];
-    if (eta > 0) {
-      s2 = (unsigned long long)eta * (unsigned long long)eta;
-      nf = 1;
-      atomicAdd(&P.mhist[eta], 1);
-    }
+  const int eta = l < g.R ? P.famcnt[l] : 0;
+  if (eta > 0) {
+    s2 = (unsigned long long)eta * (unsigned long long)eta;
+    nf = 1;
   }
+  const unsigned peers = __match_any_sync(0xffffffffu, eta);
+  if (eta > 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&P.mhist[eta], __popc(peers));
   s2 = warp_sum(s2);
   nf = warp_sum(nf);
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;

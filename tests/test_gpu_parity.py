@@ -187,7 +187,8 @@ def test_full_size_sampled_step(pa, oracle_lib):
         o = gpu.obs(t)
         # resampling: oracle tables from the GPU's integer histogram
         kmin, S, fl, thr, eps = oracle_lib.reweight(h_old, C3.R, o["dbeta"])
-        assert o["kmin_prev"] == kmin and o["S_prime"] == S and o["eps_expected"] == eps
+        assert o["kmin_prev"] == kmin and o["S_prime"] == S
+        assert o["eps_expected"] == pytest.approx(eps, rel=REL)  # summed in another order on the device
         counts = gpu.copy_counts()
         assert counts.size == len(E_old)
         for i in rng.integers(0, len(E_old), 4000):
