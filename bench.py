@@ -229,6 +229,19 @@ def profile_traffic():
         return None
 
 
+def reduce_over_ranks(ms: float, updates: float, dist=None, device: str = "cpu"):
+    """Whole-job timing of independent replicas: the slowest rank's time and the
+    updates of all ranks (identity without a process group)."""
+    if dist is None:
+        return float(ms), float(updates)
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(updates)], device=device, dtype=torch.float64)
+    dist.all_reduce(u)
+    return float(t.item()), float(u.item())
+
+
 def total_updates(w) -> int:
     """Metropolis updates of a run with an explicit schedule, counting the target R
     per step (the realised sizes fluctuate by O(sqrt R) around it)."""
@@ -378,14 +391,7 @@ def ours(args):
         dist.barrier()
     ms = start.elapsed_time(end)
     st = run.stats()
-    updates = st["updates"]
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        u = torch.tensor([updates], device="cuda", dtype=torch.float64)
-        dist.all_reduce(u)
-        updates = float(u.item())
+    ms, updates = reduce_over_ranks(ms, st["updates"], dist, "cuda")
     value = updates / (ms / 1e3)
 
     # e2e: the same steps through the public API, reading every step's observables back
