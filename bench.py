@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default sweep launch shapes (no autotuner launches before the timed steps)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--R", type=int, default=0, help="override the population size (profiling runs)")
     ap.add_argument("--probe", action="store_true", help="also run the integer-throughput probes")
@@ -210,9 +212,9 @@ def reference_arm(args):
 
 # ---------------------------------------------------------------- GPU arm
 
-def profile_traffic():
+def profile_traffic(kernel: str = "k_sweep<10,32,640,1>"):
     """DRAM bytes per sweep launch from the committed ncu summary, if it was taken
-    on the current sweep kernel source (else None)."""
+    on the current sweep kernel source and the launch shape in use (else None)."""
     if not os.path.exists(PROFILE_SUMMARY):
         return None
     digest = hashlib.sha256(open(SWEEP_SOURCE, "rb").read()).hexdigest()[:16]
@@ -222,6 +224,8 @@ def profile_traffic():
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
     if vals.get("sweep_source_sha256_16") != digest:
+        return None
+    if vals.get("sweep_kernel", "k_sweep<10,32,640,1>") != kernel:
         return None
     try:
         return float(vals["dram_bytes_per_full_launch"])
@@ -340,6 +344,20 @@ def served_vs_serial(pa, n_req: int, mem_budget: int):
             "mem_budget_bytes": mem_budget}
 
 
+def autotune_shapes(pa, sizes):
+    """Selects the sweep kernel's launch shape for every lattice size the bench
+    runs (pa_sweep_autotune on a scratch population of about 1e8 spins)."""
+    out = {}
+    for L in sorted(sizes):
+        R = max(4096, int(1e8 // L ** 3))
+        best, ms = pa.sweep_autotune(L, R, launches=3)
+        shapes = pa.sweep_shapes(L)
+        name = lambda sh: f"W{sh['words']}/T{sh['threads']}/x{sh['ctas_per_sm']}"
+        out[str(L)] = {"selected": name(shapes[best]), "scratch_R": R,
+                       "ms_per_launch": {name(sh): round(m, 4) for sh, m in zip(shapes, ms)}}
+    return out
+
+
 def measured_hbm_gbs():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -367,6 +385,13 @@ def ours(args):
     stream = torch.cuda.Stream()
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
+    sizes = {w.L}
+    if rank == 0 and args.batched_runs > 0:
+        sizes |= {4, 6, 8, 10}
+    if rank == 0 and args.served_requests > 0:
+        sizes |= {4, 6, 8, 10, 12}
+    tuned = None if args.no_autotune else autotune_shapes(pa, sizes)
+    shape = pa.sweep_shapes(w.L)[pa.sweep_selected(w.L)]
 
     run = pa.Run.from_workload(w, stream=stream)
     for _ in range(args.warmup):
@@ -419,14 +444,16 @@ def ours(args):
     sm_mhz = clk["sm_mhz"] if clk else 2070.0
     peak = n_sm * (WIDE_MULS_PER_CLK_PER_SM / WIDE_MULS_PER_UPDATE) * sm_mhz * 1e6 / 1e9   # Gupdates/s
     achieved = updates_per_launch / (sweep_ms / 1e3) / 1e9
-    traffic = profile_traffic()
+    kernel = f"k_sweep<{w.L},{shape['words']},{shape['threads']},{shape['ctas_per_sm']}>"
+    traffic = profile_traffic(kernel)
     if traffic is not None:
         traffic = traffic * updates_per_launch / (w.n_sweeps * w.N * w.R)
     replicas = updates_per_launch / (w.n_sweeps * w.N)
     hbm_bytes = 2.0 * w.N * replicas + 8.0 * replicas
     hbm_peak = measured_hbm_gbs()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gupdates/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "k_sweep<10,32,640>",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": kernel,
                 "launch_ms": sweep_ms, "updates_per_launch": updates_per_launch,
                 "peak_basis": f"{n_sm} SMs x {WIDE_MULS_PER_CLK_PER_SM} 64-bit multiplies/clk / "
                               f"{WIDE_MULS_PER_UPDATE} per update x {sm_mhz:.0f} MHz "
@@ -441,7 +468,8 @@ def ours(args):
             "config": {"workload": w.name, "L": w.L, "R": w.R, "eps_target": w.eps_target, "beta_max": w.beta_max,
                        "n_sweeps": w.n_sweeps, "steps_timed": f"temperature steps {args.warmup + 1}.."
                                                               f"{args.warmup + done}",
-                       "l2": "inputs larger than L2 (2 GB double-buffered int8 population)"},
+                       "l2": "inputs larger than L2 (2 GB double-buffered int8 population)",
+                       "sweep_shapes": tuned},
             "roofline": roofline, "e2e": e2e, "gpu_launches": st["kernel_launches"],
             "phase_share": phase_share, "clocks": clk}
     run.close()

@@ -201,7 +201,7 @@ int pa_destroy(pa_ctx* ctx);
 /* Static description of a status code. */
 const char* pa_strerror(int status);
 
-/* ---- many runs at once (SURVEY: batched and served workloads) ----
+/* ---- many runs at once (batched and served workloads) ----
  * Independent runs (different couplings, sizes, populations, schedules) share
  * the GPU by running on their own non-blocking streams: their steps are issued
  * round-robin from the host and their kernels overlap on the device.  Each run
@@ -237,6 +237,41 @@ int pa_server_result(pa_server* server, uint64_t request_id, int32_t pop, pa_obs
 /* Requests waiting and running. */
 int pa_server_load(pa_server* server, int32_t* queued, int32_t* active);
 int pa_server_destroy(pa_server* server);
+
+/* ---- launch shapes of the sweep kernel and their autotuner ----
+ * An implementation choice with no counterpart in the paper.  The sweep kernel
+ * is compiled for a few launch shapes per lattice size L: W words per site row
+ * (a CTA holds 8W replicas, all N sites, in shared memory), threads per CTA,
+ * and the CTAs per SM it is compiled for.  Every shape gives bit-identical
+ * results (the random words depend on slot and site, never on the tiling); they
+ * differ only in speed.  The first shape of each L is the default.  A run uses
+ * the shape selected for its L on the current device when it is created. */
+typedef struct {
+  int32_t L;
+  int32_t words;         /* W: 32-bit words per site row of a tile (8 replicas each) */
+  int32_t threads;       /* threads per CTA */
+  int32_t ctas_per_sm;   /* CTAs per SM the kernel is compiled for (register cap) */
+  int32_t smem_bytes;    /* dynamic shared memory per CTA */
+} pa_sweep_shape;
+
+/* The shapes compiled for L, default first: *n = their number; up to cap are
+ * written to shapes (which may be NULL when cap is 0).  No GPU is needed. */
+int pa_sweep_shapes(int32_t L, pa_sweep_shape* shapes, int32_t cap, int32_t* n);
+
+/* Selects shape `index` of L for runs created afterwards on the current
+ * device (-1: the default).  Thread-safe. */
+int pa_sweep_select(int32_t L, int32_t index);
+int pa_sweep_selected(int32_t L, int32_t* index);
+
+/* Autotuner: on the current device, creates a scratch run of size L with R
+ * replicas (one population, one temperature step from beta 0 to 0.5, 10
+ * sweeps), times `launches` sweep launches of every shape of L (after one
+ * untimed launch each) with CUDA events, selects the fastest for L and returns
+ * its index in *best.  ms_per_launch, if not NULL, receives up to cap per-shape
+ * times (a shape that cannot launch on this device gets a negative time).  The
+ * scratch run's memory is freed before returning; PA_ERR_NOMEM if it does not
+ * fit. */
+int pa_sweep_autotune(int32_t L, int32_t R, int32_t launches, double* ms_per_launch, int32_t cap, int32_t* best);
 
 /* ---- resampling without device allocation ----
  * The paper has no counterpart: this is a service entry point for callers that

@@ -46,7 +46,7 @@ def _up_to_date() -> bool:
 
 def _compile(src: str, extra) -> str:
     obj = os.path.join(OBJDIR, os.path.splitext(src)[0] + ".o")
-    # PA_NVCC_FLAGS: extra nvcc flags, e.g. -DPA_SWEEP_NT_L10=800 to pick a launch shape
+    # PA_NVCC_FLAGS: extra nvcc flags, e.g. -DPA_SWEEP_L10_NT=320 to pick a launch shape
     extra = list(extra) + os.environ.get("PA_NVCC_FLAGS", "").split()
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
            "-I", os.path.join(ROOT, "include"), "-c", os.path.join(CSRC, src), "-o", obj, *extra]

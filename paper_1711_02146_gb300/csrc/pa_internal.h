@@ -60,7 +60,16 @@ struct RunGeom {
   int32_t q_bins;
   int32_t n_count_blocks;    // resampling blocks (1024 slots each)
   int32_t n_entropy_blocks;  // family-entropy reduction blocks
+  int32_t sweep_shape;       // index of the sweep kernel's launch shape among those of L
 };
+
+// One launch shape of the sweep kernel (every shape gives identical results).
+struct SweepShapeInfo {
+  int32_t L, W, NT, MB;  // lattice size, words per site row, threads per CTA, CTAs per SM compiled for
+  int32_t smem;          // dynamic shared memory per CTA, bytes
+};
+int sweep_shape_count(int L);
+bool sweep_shape_info(int L, int i, SweepShapeInfo* out);
 
 constexpr int kCountThreads = 256;     // threads per resampling block
 constexpr int kSlotsPerCountBlock = 1024;

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -56,6 +57,18 @@ struct pa_ctx {
 namespace {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? PA_OK : PA_ERR_CUDA; }
+
+// Sweep launch shape selected per device and lattice size (an index among the
+// shapes compiled for L; static storage starts at 0, the default shape).
+constexpr int kMaxDevices = 64;
+std::atomic<int32_t> g_sweep_choice[kMaxDevices][pa::kMaxL + 1];
+
+int current_device(int* dev) {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) return PA_ERR_CUDA;
+  *dev = d;
+  return PA_OK;
+}
 
 // Copies are ordered on the run's stream and waited for on that stream only, so
 // runs on other streams keep going.
@@ -346,6 +359,8 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
   g.q_bins = cfg->q_bins;
   g.n_count_blocks = (int32_t)((R_cap + pa::kSlotsPerCountBlock - 1) / pa::kSlotsPerCountBlock);
   g.n_entropy_blocks = (int32_t)((R_cap + pa::kEntropyPerBlock - 1) / pa::kEntropyPerBlock);
+  int dev = 0;
+  g.sweep_shape = current_device(&dev) == PA_OK ? g_sweep_choice[dev][g.L].load() : 0;
   const size_t T = (size_t)cfg->n_temps;
 
   int rc = PA_OK;
@@ -724,6 +739,106 @@ int pa_get_couplings(pa_ctx* c, int8_t* J, int64_t cap) {
 int pa_destroy(pa_ctx* c) {
   if (!c) return PA_ERR_INVALID;
   destroy(c);
+  return PA_OK;
+}
+
+int pa_sweep_shapes(int32_t L, pa_sweep_shape* shapes, int32_t cap, int32_t* n) {
+  if (!n || cap < 0 || (cap > 0 && !shapes) || !pa::sweep_supported(L)) return PA_ERR_INVALID;
+  const int k = pa::sweep_shape_count(L);
+  *n = k;
+  for (int i = 0; i < k && i < cap; ++i) {
+    pa::SweepShapeInfo si{};
+    pa::sweep_shape_info(L, i, &si);
+    shapes[i].L = si.L;
+    shapes[i].words = si.W;
+    shapes[i].threads = si.NT;
+    shapes[i].ctas_per_sm = si.MB;
+    shapes[i].smem_bytes = si.smem;
+  }
+  return PA_OK;
+}
+
+int pa_sweep_select(int32_t L, int32_t index) {
+  if (!pa::sweep_supported(L) || index < -1 || index >= pa::sweep_shape_count(L)) return PA_ERR_INVALID;
+  int dev = 0;
+  const int rc = current_device(&dev);
+  if (rc != PA_OK) return rc;
+  g_sweep_choice[dev][L].store(index < 0 ? 0 : index);
+  return PA_OK;
+}
+
+int pa_sweep_selected(int32_t L, int32_t* index) {
+  if (!index || !pa::sweep_supported(L)) return PA_ERR_INVALID;
+  int dev = 0;
+  const int rc = current_device(&dev);
+  if (rc != PA_OK) return rc;
+  *index = g_sweep_choice[dev][L].load();
+  return PA_OK;
+}
+
+int pa_sweep_autotune(int32_t L, int32_t R, int32_t launches, double* ms_per_launch, int32_t cap, int32_t* best) {
+  if (!best || !pa::sweep_supported(L) || R < 1 || launches < 1 || cap < 0 || (cap > 0 && !ms_per_launch))
+    return PA_ERR_INVALID;
+  int dev = 0;
+  int rc = current_device(&dev);
+  if (rc != PA_OK) return rc;
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return PA_ERR_CUDA;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  rc = cuda_status(cudaEventCreate(&e0));
+  if (rc == PA_OK) rc = cuda_status(cudaEventCreate(&e1));
+  // scratch run: one step from beta 0 to 0.5 leaves a resampled population whose
+  // sweep can be relaunched (it reads one buffer and rewrites the other)
+  const double betas[2] = {0.0, 0.5};
+  pa_config cfg{};
+  cfg.L = L;
+  cfg.n_pop = 1;
+  cfg.R = R;
+  cfg.disorder_seed = 1;
+  cfg.run_seed = 1;
+  cfg.n_temps = 2;
+  cfg.betas = betas;
+  cfg.n_sweeps = 10;
+  cfg.q_bins = 65;
+  pa_ctx* c = nullptr;
+  if (rc == PA_OK) rc = pa_create(&cfg, s, &c);
+  if (rc == PA_OK) rc = pa_step(c);
+  if (rc == PA_OK) rc = pa_sync(c);
+  int best_i = -1;
+  double best_ms = 0.0;
+  if (rc == PA_OK) {
+    uint32_t met[3];
+    metropolis_thresholds(betas[1], met);
+    const int src = 1 - c->cur;  // the buffer the step's sweep gathered from
+    const int n = pa::sweep_shape_count(L);
+    for (int i = 0; i < n && rc == PA_OK; ++i) {
+      c->g.sweep_shape = i;
+      double t_ms = -1.0;
+      int e = pa::launch_sweep(c->g, c->pops, src, c->jtab, 1, cfg.n_sweeps, met, s);
+      if (e == 0) {
+        cudaEventRecord(e0, s);
+        for (int k = 0; k < launches && e == 0; ++k) e = pa::launch_sweep(c->g, c->pops, src, c->jtab, 1, cfg.n_sweeps, met, s);
+        cudaEventRecord(e1, s);
+        rc = cuda_status(cudaEventSynchronize(e1));
+        float f = 0.f;
+        if (rc == PA_OK && e == 0 && cudaEventElapsedTime(&f, e0, e1) == cudaSuccess) t_ms = (double)f / launches;
+      }
+      if (e != 0) cudaGetLastError();  // a shape that does not fit this device: skipped
+      if (ms_per_launch && i < cap) ms_per_launch[i] = t_ms;
+      if (t_ms >= 0.0 && (best_i < 0 || t_ms < best_ms)) {
+        best_i = i;
+        best_ms = t_ms;
+      }
+    }
+  }
+  if (c) pa_destroy(c);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  if (rc != PA_OK) return rc;
+  if (best_i < 0) return PA_ERR_CUDA;
+  g_sweep_choice[dev][L].store(best_i);
+  *best = best_i;
   return PA_OK;
 }
 

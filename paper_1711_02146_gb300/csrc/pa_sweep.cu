@@ -37,9 +37,6 @@
 #include "pa_internal.h"
 
 // Build-time knobs of the sweep's launch shape and code generation.
-#ifndef PA_SWEEP_NT_L10
-#define PA_SWEEP_NT_L10 640  // threads per CTA at L = 10 (row partitions must split 50 rows per class)
-#endif
 #ifndef PA_SWEEP_ROW_UNROLL
 #define PA_SWEEP_ROW_UNROLL 8  // rows of a partition unrolled per loop trip (8: all of them)
 #endif
@@ -404,8 +401,8 @@ __device__ __forceinline__ void store_tile(const SweepArgs& a, const uint32_t* s
 
 // Row-partitioned sweep kernel: every warp generates its own random words and
 // updates its rows.
-template <int L, int W, int NT>
-__global__ void __launch_bounds__(NT, 1) k_sweep(const __grid_constant__ SweepArgs a) {
+template <int L, int W, int NT, int MB>
+__global__ void __launch_bounds__(NT, MB) k_sweep(const __grid_constant__ SweepArgs a) {
   using S = SweepShape<L, W, NT>;
   constexpr int N = S::N, NP = S::NP, TJ = S::TJ;
   extern __shared__ __align__(16) uint32_t sm[];
@@ -445,21 +442,78 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(const __grid_constant__ SweepAr
   store_tile<L, W, NP>(a, sp, tile0, word, part);
 }
 
-template <int L, int W, int NT>
+template <int L, int W, int NT, int MB>
 static int launch_t(const RunGeom& g, const SweepArgs& args, cudaStream_t s) {
   using S = SweepShape<L, W, NT>;
-  cudaError_t e = cudaFuncSetAttribute(k_sweep<L, W, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_sweep<L, W, NT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
   if (e != cudaSuccess) return (int)e;
   dim3 grid((unsigned)((g.R_cap + S::TJ - 1) / S::TJ));
-  k_sweep<L, W, NT><<<grid, NT, S::SMEM, s>>>(args);
+  k_sweep<L, W, NT, MB><<<grid, NT, S::SMEM, s>>>(args);
   return (int)cudaGetLastError();
 }
 
+namespace {
+
+// Candidate launch shapes: words per site row W (8W replicas per tile),
+// threads per CTA, CTAs per SM the kernel is compiled for (its register cap).
+// The first entry of each L is the default (the fastest measured on GB300);
+// the autotuner may pick another.  All give identical results.  At L = 14 no
+// shape with whole warps keeps 8W | 256 and fits: 784 and 392 threads leave a
+// partial last warp and one warp whose rows straddle the two parity classes
+// (it runs both colour offsets; still far faster than 224 threads).
+struct ShapeEntry {
+  int L, W, NT, MB;
+  size_t smem;
+  int (*launch)(const RunGeom&, const SweepArgs&, cudaStream_t);
+};
+#define PA_SHAPE(L, W, NT, MB) {L, W, NT, MB, SweepShape<L, W, NT>::SMEM, &launch_t<L, W, NT, MB>}
+const ShapeEntry kShapes[] = {
+    PA_SHAPE(2, 32, 128, 1),
+    PA_SHAPE(4, 32, 256, 3),   PA_SHAPE(4, 32, 256, 1),  PA_SHAPE(4, 32, 512, 2),
+    PA_SHAPE(6, 32, 384, 2),   PA_SHAPE(6, 32, 384, 1),  PA_SHAPE(6, 32, 576, 1),
+    PA_SHAPE(8, 32, 512, 2),   PA_SHAPE(8, 32, 512, 1),  PA_SHAPE(8, 32, 256, 2),
+    PA_SHAPE(10, 32, 640, 1),  PA_SHAPE(10, 16, 320, 2),
+    PA_SHAPE(12, 16, 768, 1),  PA_SHAPE(12, 16, 576, 1), PA_SHAPE(12, 8, 384, 2),
+    PA_SHAPE(14, 8, 784, 1),   PA_SHAPE(14, 4, 392, 1),
+    PA_SHAPE(16, 4, 512, 1),   PA_SHAPE(16, 4, 1024, 1),
+};
+#undef PA_SHAPE
+constexpr int kNumShapes = (int)(sizeof(kShapes) / sizeof(kShapes[0]));
+
+const ShapeEntry* shape_of(int L, int i) {
+  if (i < 0) return nullptr;
+  for (int k = 0; k < kNumShapes; ++k)
+    if (kShapes[k].L == L && i-- == 0) return &kShapes[k];
+  return nullptr;
+}
+
+}  // namespace
+
 bool sweep_supported(int L) { return L >= 2 && L <= kMaxL && L % 2 == 0; }
+
+int sweep_shape_count(int L) {
+  int n = 0;
+  for (int k = 0; k < kNumShapes; ++k) n += kShapes[k].L == L;
+  return n;
+}
+
+bool sweep_shape_info(int L, int i, SweepShapeInfo* out) {
+  const ShapeEntry* e = shape_of(L, i);
+  if (!e || !out) return false;
+  out->L = e->L;
+  out->W = e->W;
+  out->NT = e->NT;
+  out->MB = e->MB;
+  out->smem = (int32_t)e->smem;
+  return true;
+}
 
 int launch_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, int t, int n_sweeps,
                  const uint32_t met_thr[3], void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
+  const ShapeEntry* shape = shape_of(g.L, g.sweep_shape);
+  if (!shape) return (int)cudaErrorInvalidValue;
   for (int i = 0; i < g.n_pop; ++i) {
     SweepArgs args;
     args.pop = pops[i];
@@ -479,18 +533,7 @@ int launch_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, 
     args.thr4 = met_thr[0];
     args.thr8 = met_thr[1];
     args.thr12 = met_thr[2];
-    int e;
-    switch (g.L) {
-      case 2: e = launch_t<2, 32, 128>(g, args, s); break;
-      case 4: e = launch_t<4, 32, 256>(g, args, s); break;
-      case 6: e = launch_t<6, 32, 384>(g, args, s); break;
-      case 8: e = launch_t<8, 32, 512>(g, args, s); break;
-      case 10: e = launch_t<10, 32, PA_SWEEP_NT_L10>(g, args, s); break;
-      case 12: e = launch_t<12, 16, 576>(g, args, s); break;
-      case 14: e = launch_t<14, 8, 224>(g, args, s); break;
-      case 16: e = launch_t<16, 4, 256>(g, args, s); break;
-      default: e = (int)cudaErrorInvalidValue;
-    }
+    const int e = shape->launch(g, args, s);
     if (e != 0) return e;
   }
   return 0;

@@ -101,6 +101,14 @@ class Stats(ctypes.Structure):
         return d
 
 
+class SweepShape(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("words", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("smem_bytes", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _lib = None
 
 # Every entry point declared in include/pa.h, with its ctypes signature.
@@ -140,6 +148,11 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_int32)]),
     "pa_server_load": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "pa_server_destroy": (ctypes.c_int, [_vp]),
+    "pa_sweep_shapes": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(SweepShape), ctypes.c_int32, _i32p]),
+    "pa_sweep_select": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32]),
+    "pa_sweep_selected": (ctypes.c_int, [ctypes.c_int32, _i32p]),
+    "pa_sweep_autotune": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_double), ctypes.c_int32, _i32p]),
     "pa_resample_counts_noalloc": (ctypes.c_int, [_vp, ctypes.c_int64, _vp, _vp, ctypes.c_int32, ctypes.c_uint64,
                                                    ctypes.c_int32, ctypes.c_int32, _vp, _vp, ctypes.c_int64, _vp,
                                                    _vp]),
@@ -148,6 +161,36 @@ SIGNATURES = {
 }
 
 NOALLOC_MAX_SLOTS = 4096 * 1024
+
+
+def sweep_shapes(L: int) -> list:
+    """Launch shapes compiled for the sweep kernel at size L, default first (no GPU needed)."""
+    n = ctypes.c_int32()
+    _check("pa_sweep_shapes", lib().pa_sweep_shapes(L, None, 0, ctypes.byref(n)))
+    arr = (SweepShape * n.value)()
+    _check("pa_sweep_shapes", lib().pa_sweep_shapes(L, arr, n.value, ctypes.byref(n)))
+    return [a.as_dict() for a in arr]
+
+
+def sweep_select(L: int, index: int) -> None:
+    """Shape `index` of L for runs created afterwards on the current device (-1: default)."""
+    _check("pa_sweep_select", lib().pa_sweep_select(L, index))
+
+
+def sweep_selected(L: int) -> int:
+    i = ctypes.c_int32()
+    _check("pa_sweep_selected", lib().pa_sweep_selected(L, ctypes.byref(i)))
+    return i.value
+
+
+def sweep_autotune(L: int, R: int, launches: int = 5):
+    """Times every sweep shape of L on a scratch run of R replicas and selects the
+    fastest on the current device; returns (index, [ms per launch of each shape])."""
+    n = len(sweep_shapes(L))
+    ms = (ctypes.c_double * n)()
+    best = ctypes.c_int32()
+    _check("pa_sweep_autotune", lib().pa_sweep_autotune(L, R, launches, ms, n, ctypes.byref(best)))
+    return best.value, list(ms)
 
 
 def resample_counts_noalloc(levels, n_old, fl, thr, n_levels, run_seed, pop, t, counts, parents, parents_cap, n_new,

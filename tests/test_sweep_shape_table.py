@@ -1,0 +1,41 @@
+"""The table of sweep launch shapes (host logic, no GPU): every shape fits the
+kernel's tiling rules and one SM of a GB300, and the default comes first."""
+import pytest
+
+SMEM_PER_SM = 228 * 1024      # shared memory per SM
+SMEM_PER_CTA = 227 * 1024     # largest dynamic allocation of one CTA
+RESERVED_PER_CTA = 1024       # shared memory the hardware keeps per resident CTA
+
+
+@pytest.fixture(scope="module")
+def pa():
+    from paper_1711_02146_gb300 import build, pa as pa_mod
+    build.build()
+    return pa_mod
+
+
+@pytest.mark.parametrize("L", [2, 4, 6, 8, 10, 12, 14, 16])
+def test_shapes_follow_the_tiling_rules(pa, L):
+    shapes = pa.sweep_shapes(L)
+    assert shapes, "every supported size has a shape"
+    N = L ** 3
+    seen = set()
+    for s in shapes:
+        W, NT, MB = s["words"], s["threads"], s["ctas_per_sm"]
+        assert s["L"] == L
+        assert (W, NT, MB) not in seen
+        seen.add((W, NT, MB))
+        assert 32 % W == 0 and NT % W == 0 and NT <= 1024   # a partial last warp is allowed (L = 14)
+        NP = NT // W                                   # row partitions
+        assert NP % 2 == 0 and (L * L // 2) % (NP // 2) == 0
+        assert 8 * W <= 256                            # a tile never crosses the 256-slot pitch unit
+        assert s["smem_bytes"] == N * W * 4 + N * 32 + 8 * W * 4
+        assert s["smem_bytes"] <= SMEM_PER_CTA
+        assert MB * (s["smem_bytes"] + RESERVED_PER_CTA) <= SMEM_PER_SM
+        assert MB * NT <= 2048
+
+
+def test_unsupported_sizes_are_rejected(pa):
+    for L in (0, 3, 18):
+        with pytest.raises(pa.PAError):
+            pa.sweep_shapes(L)
