@@ -9,6 +9,11 @@ free_energy_variance  rho_f from M independent runs of one disorder realization
 hardness_adaptive_population
                       the population-size scheme of §IV.A: run with R0; while
                       R <= 100 rho_t(R), rerun with R = 150 rho_t(R).
+schedule_comparison   §V.A: rho_t at beta = 5 under the unoptimized schedule
+                      (dbeta = 0.05, 10 sweeps per step) and the optimized one
+                      (constant culling fraction, 3/22/1 sweeps by temperature
+                      range, §IV.B) at equal sweeps per replica, per disorder
+                      realization.
 The M runs of free_energy_variance advance together as one batch (pa_batch).
 """
 from __future__ import annotations
@@ -79,3 +84,86 @@ def hardness_adaptive_population(workload, R0: int, check: float = 100.0, grow: 
             return {"R": R, "rho_t": rt, "equilibrated": True, "history": history}
         R = int(math.ceil(grow * rt))
     return {"R": history[-1][0], "rho_t": history[-1][1], "equilibrated": False, "history": history}
+
+
+# ---------------------------------------------------------------- schedule comparison (§IV.B, §V.A)
+
+def paper_sweep_schedule(betas, low: float = 0.5, high: float = 2.5, hot: int = 3, mid: int = 22,
+                         cold: int = 1) -> np.ndarray:
+    """§IV.B's ad hoc sweep schedule: `hot` sweeps per step below beta = low, `mid`
+    for low <= beta <= high, `cold` above (step 0, at beta = 0, does none)."""
+    b = np.asarray(betas, dtype=np.float64)
+    s = np.where(b < low, hot, np.where(b <= high, mid, cold)).astype(np.int32)
+    s[0] = 0
+    return s
+
+
+def constant_culling_betas(L: int, disorder_seed: int, R: int, eps: float, beta_max: float = 5.0,
+                           run_seed: int = 1, n_sweeps: int = 10) -> np.ndarray:
+    """The beta schedule of one pilot run that holds the culling fraction at eps
+    (§IV.B: chosen on a single disorder realization, then reused)."""
+    from .workloads import Workload
+    w = Workload("pilot", L=L, R=R, disorder_seed=disorder_seed, run_seed=run_seed, betas=None, n_temps=4096,
+                 beta_max=beta_max, eps_target=eps, n_sweeps=n_sweeps)
+    run = pa.Run.from_workload(w)
+    run.run()
+    betas = np.array([run.beta(t) for t in range(run.t + 1)])
+    run.close()
+    return betas
+
+
+def matched_optimized_schedule(L: int, disorder_seed: int, R: int, total_sweeps: int, beta_max: float = 5.0,
+                               run_seed: int = 1, iters: int = 14):
+    """A constant-culling beta schedule with the paper's 3/22/1 sweep schedule whose
+    total number of sweeps per replica is as close as bisection on eps gets to
+    `total_sweeps` (the comparison of §V.A holds the work fixed).  Returns
+    (betas, sweeps_per_step, eps)."""
+    lo, hi = 1e-3, 0.9            # larger eps -> bigger steps -> fewer sweeps
+    best = None
+    for _ in range(iters):
+        eps = math.sqrt(lo * hi)
+        betas = constant_culling_betas(L, disorder_seed, R, eps, beta_max, run_seed)
+        sw = paper_sweep_schedule(betas)
+        total = int(sw.sum())
+        if best is None or abs(total - total_sweeps) < abs(best[1].sum() - total_sweeps):
+            best = (betas, sw, eps)
+        if total == total_sweeps:
+            break
+        if total > total_sweeps:
+            lo = eps
+        else:
+            hi = eps
+    return best
+
+
+def schedule_comparison(L: int, R: int, disorder_seeds, beta_max: float = 5.0, dbeta: float = 0.05,
+                        sweeps: int = 10, pilot_R: int = 20000, run_seed: int = 11) -> Dict[str, object]:
+    """§V.A: rho_t at beta_max under the unoptimized schedule (constant dbeta,
+    `sweeps` sweeps per step) and the optimized one (constant culling fraction,
+    3/22/1 sweeps, the same total sweeps per replica), for every disorder
+    realization; all 2M runs advance together as one batch."""
+    from .workloads import Workload, linear_betas
+    n = int(round(beta_max / dbeta)) + 1
+    b_un = linear_betas(n, beta_max)
+    s_un = np.full(n, sweeps, dtype=np.int32)
+    s_un[0] = 0
+    seeds = list(disorder_seeds)
+    b_op, s_op, eps = matched_optimized_schedule(L, seeds[0], pilot_R, int(s_un.sum()), beta_max)
+    ws = []
+    for d in seeds:
+        ws.append(Workload(f"unopt_{d}", L=L, R=R, disorder_seed=d, run_seed=run_seed, betas=b_un,
+                           sweeps_per_step=s_un))
+        ws.append(Workload(f"opt_{d}", L=L, R=R, disorder_seed=d, run_seed=run_seed, betas=b_op, sweeps_per_step=s_op))
+    batch = pa.Batch(ws)
+    batch.run()
+    rho = np.zeros((len(seeds), 2))
+    for i in range(len(ws)):
+        v = batch.run_view(i)
+        rho[i // 2, i % 2] = v.obs(v.t)["rho_t"]
+    batch.close()
+    ratio = rho[:, 0] / rho[:, 1]
+    return {"rho_unopt": rho[:, 0], "rho_opt": rho[:, 1], "ratio": ratio,
+            "geo_mean_ratio": float(np.exp(np.mean(np.log(ratio)))),
+            "ratio_of_means": float(rho[:, 0].mean() / rho[:, 1].mean()),
+            "eps": eps, "n_steps_opt": len(b_op), "n_steps_unopt": n,
+            "sweeps_opt": int(s_op.sum()), "sweeps_unopt": int(s_un.sum())}

@@ -277,7 +277,8 @@ class _ConfigHolder:
     @classmethod
     def from_workload(cls, w):
         return cls(w.L, w.R, w.disorder_seed, w.run_seed, w.betas, n_temps=w.n_temps, beta_max=w.beta_max,
-                   eps_target=w.eps_target, n_sweeps=w.n_sweeps, n_pop=w.n_pop, q_bins=w.q_bins, R_cap=w.R_cap)
+                   eps_target=w.eps_target, n_sweeps=w.n_sweeps, sweeps_per_step=w.sweeps_per_step, n_pop=w.n_pop,
+                   q_bins=w.q_bins, R_cap=w.R_cap)
 
 
 def footprint(w) -> int:
@@ -412,7 +413,7 @@ class Run:
     @classmethod
     def from_workload(cls, w, stream=None, **over):
         kw = dict(n_temps=w.n_temps, beta_max=w.beta_max, eps_target=w.eps_target, n_sweeps=w.n_sweeps,
-                  n_pop=w.n_pop, q_bins=w.q_bins, R_cap=w.R_cap)
+                  sweeps_per_step=w.sweeps_per_step, n_pop=w.n_pop, q_bins=w.q_bins, R_cap=w.R_cap)
         kw.update(over)
         return cls(w.L, w.R, w.disorder_seed, w.run_seed, w.betas, stream=stream, **kw)
 

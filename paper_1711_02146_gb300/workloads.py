@@ -41,6 +41,7 @@ class Workload:
     beta_max: float = 5.0
     eps_target: float = 0.0
     n_sweeps: int = 10
+    sweeps_per_step: Optional[np.ndarray] = None  # explicit schedule: sweeps of every step (overrides n_sweeps)
     n_pop: int = 1
     q_bins: int = 65
     R_cap: int = 0

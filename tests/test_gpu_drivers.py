@@ -47,3 +47,12 @@ def test_hardness_adaptive_population(drivers):
         assert R_next == int(np.ceil(150 * rt_prev))   # with R = 150 rho_t
     if res["equilibrated"]:
         assert res["R"] > 100 * res["rho_t"]
+
+
+def test_optimized_schedule_beats_constant_steps(drivers):
+    # §V.A on a few L = 6 samples: equal sweeps per replica, smaller rho_t with the
+    # constant-culling beta schedule and the 3/22/1 sweep schedule
+    r = drivers.schedule_comparison(6, 4000, range(1, 13))
+    assert abs(r["sweeps_opt"] - r["sweeps_unopt"]) <= 0.03 * r["sweeps_unopt"]
+    assert r["n_steps_opt"] > 10
+    assert r["geo_mean_ratio"] > 1.0
