@@ -238,6 +238,27 @@ int pa_server_result(pa_server* server, uint64_t request_id, int32_t pop, pa_obs
 int pa_server_load(pa_server* server, int32_t* queued, int32_t* active);
 int pa_server_destroy(pa_server* server);
 
+/* ---- checkpoint and restore ----
+ * The state between two steps is device data only (the random streams are
+ * counter-based, so there is no generator state): the current population
+ * (spins, labels, levels), the step records, level and overlap histograms of
+ * steps 0..t, the last copy numbers and parent map, the family-size histogram,
+ * and the schedule so far.  A run restored from a checkpoint continues exactly
+ * as the original would have.  The paper has no counterpart (its runs are
+ * single CPU jobs); long runs at large R need it.
+ *
+ * pa_checkpoint synchronises, sets *size to the checkpoint's length and, if buf
+ * holds at least that many bytes (host memory), writes it; otherwise it returns
+ * PA_ERR_CAPACITY and writes nothing (call with buf = NULL to size a buffer).
+ * The format is this library's, in host byte order, not a portable archive. */
+int pa_checkpoint(pa_ctx* ctx, void* buf, size_t cap, size_t* size);
+
+/* Creates a run on cuda_stream from a checkpoint of a run with the same
+ * configuration (same sizes, seeds, schedule or adaptive target; a different
+ * configuration or a damaged buffer gives PA_ERR_INVALID).  The new context
+ * owns its memory like one from pa_create. */
+int pa_restore(const pa_config* cfg, const void* buf, size_t size, void* cuda_stream, pa_ctx** out);
+
 /* ---- launch shapes of the sweep kernel and their autotuner ----
  * An implementation choice with no counterpart in the paper.  The sweep kernel
  * is compiled for a few launch shapes per lattice size L: W words per site row

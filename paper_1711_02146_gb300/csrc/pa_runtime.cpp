@@ -273,6 +273,43 @@ void destroy(pa_ctx* c) {
 
 }  // namespace
 
+// ---------------------------------------------------------------- checkpoint / restore
+//
+// Layout of a checkpoint (host byte order): CkptHeader, the schedule (betas and
+// sweeps of all n_temps steps), then per population: step records and level
+// histograms of steps 0..t, the spins of the current population (site-major,
+// N rows of R~ bytes), its labels and levels, the copy numbers of the last
+// resampling (R~_{t-1} entries), the parent map (R~ entries) and the family-size
+// histogram (R~ + 1 entries); then the overlap histograms of steps 0..t.
+
+namespace {
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t version, header_bytes;
+  int32_t L, n_pop, q_bins, n_temps;
+  int64_t R, R_cap;
+  uint64_t disorder_seed, run_seed;
+  double eps_target, beta_max;
+  int32_t t, done, adaptive, n_sweeps;
+  int32_t R_tilde[2], R_prev[2];
+  uint64_t total_bytes;
+};
+constexpr char kCkptMagic[8] = {'P', 'A', 'C', 'K', 'P', 'T', '0', '1'};
+
+size_t ckpt_bytes(const RunGeom& g, int t, int n_temps, const int32_t* Rt, const int32_t* Rp) {
+  size_t b = sizeof(CkptHeader) + (size_t)n_temps * (sizeof(double) + sizeof(int32_t));
+  for (int p = 0; p < g.n_pop; ++p) {
+    b += (size_t)(t + 1) * (sizeof(StepRec) + sizeof(uint32_t) * (size_t)g.n_levels);
+    b += (size_t)g.N * (size_t)Rt[p];                         // spins
+    b += sizeof(int32_t) * ((size_t)Rt[p] * 3 + (size_t)Rp[p] + (size_t)Rt[p] + 1);  // labels, levels, parents, counts, mhist
+  }
+  b += sizeof(unsigned long long) * (size_t)(t + 1) * (size_t)g.q_bins;
+  return b;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* pa_strerror(int s) {
@@ -739,6 +776,159 @@ int pa_get_couplings(pa_ctx* c, int8_t* J, int64_t cap) {
 int pa_destroy(pa_ctx* c) {
   if (!c) return PA_ERR_INVALID;
   destroy(c);
+  return PA_OK;
+}
+
+
+int pa_checkpoint(pa_ctx* c, void* buf, size_t cap, size_t* size) {
+  if (!c || !size) return PA_ERR_INVALID;
+  int rc = pa_sync(c);
+  if (rc != PA_OK) return rc;
+  const RunGeom& g = c->g;
+  const int t = c->t;
+  int32_t Rt[2] = {0, 0}, Rp[2] = {0, 0};
+  for (int p = 0; p < g.n_pop; ++p) {
+    StepRec r;
+    rc = copy_d2h(c, &r, c->pops[p].rec + t, sizeof r);
+    if (rc != PA_OK) return fail(c, rc);
+    Rt[p] = r.R_tilde;
+    Rp[p] = t > 0 ? r.R_prev : 0;
+  }
+  const size_t need = ckpt_bytes(g, t, c->cfg.n_temps, Rt, Rp);
+  *size = need;
+  if (!buf || cap < need) return PA_ERR_CAPACITY;
+  char* o = static_cast<char*>(buf);
+  CkptHeader h{};
+  std::memcpy(h.magic, kCkptMagic, sizeof h.magic);
+  h.version = 1;
+  h.header_bytes = sizeof(CkptHeader);
+  h.L = g.L;
+  h.n_pop = g.n_pop;
+  h.q_bins = g.q_bins;
+  h.n_temps = c->cfg.n_temps;
+  h.R = c->cfg.R;
+  h.R_cap = c->cfg.R_cap;
+  h.disorder_seed = c->cfg.disorder_seed;
+  h.run_seed = c->cfg.run_seed;
+  h.eps_target = c->adaptive ? c->cfg.eps_target : 0.0;
+  h.beta_max = c->adaptive ? c->cfg.beta_max : 0.0;
+  h.t = t;
+  h.done = c->done ? 1 : 0;
+  h.adaptive = c->adaptive ? 1 : 0;
+  h.n_sweeps = c->cfg.n_sweeps;
+  for (int p = 0; p < 2; ++p) {
+    h.R_tilde[p] = Rt[p];
+    h.R_prev[p] = Rp[p];
+  }
+  h.total_bytes = need;
+  std::memcpy(o, &h, sizeof h);
+  o += sizeof h;
+  std::memcpy(o, c->betas.data(), sizeof(double) * (size_t)c->cfg.n_temps);
+  o += sizeof(double) * (size_t)c->cfg.n_temps;
+  std::memcpy(o, c->sweeps.data(), sizeof(int32_t) * (size_t)c->cfg.n_temps);
+  o += sizeof(int32_t) * (size_t)c->cfg.n_temps;
+  for (int p = 0; p < g.n_pop && rc == PA_OK; ++p) {
+    const PopDev& P = c->pops[p];
+    const size_t R = (size_t)Rt[p];
+    auto get = [&](const void* src, size_t bytes) {
+      if (rc == PA_OK && bytes) rc = copy_d2h(c, o, src, bytes);
+      o += bytes;
+    };
+    get(P.rec, sizeof(StepRec) * (size_t)(t + 1));
+    get(P.hist, sizeof(uint32_t) * (size_t)(t + 1) * (size_t)g.n_levels);
+    if (rc == PA_OK && R) {
+      c->stats.d2h_bytes += (int64_t)(g.N * R);
+      rc = cuda_status(cudaMemcpy2DAsync(o, R, P.spins[c->cur], (size_t)g.pitch, R, (size_t)g.N,
+                                         cudaMemcpyDeviceToHost, c->stream));
+      if (rc == PA_OK) rc = cuda_status(cudaStreamSynchronize(c->stream));
+    }
+    o += (size_t)g.N * R;
+    get(P.labels[c->cur], sizeof(int32_t) * R);
+    get(P.levels, sizeof(int32_t) * R);
+    get(P.counts, sizeof(int32_t) * (size_t)Rp[p]);
+    get(P.parents, sizeof(int32_t) * R);
+    get(P.mhist, sizeof(int32_t) * (R + 1));
+  }
+  if (rc == PA_OK) rc = copy_d2h(c, o, c->qhist, sizeof(unsigned long long) * (size_t)(t + 1) * (size_t)g.q_bins);
+  return rc == PA_OK ? PA_OK : fail(c, rc);
+}
+
+int pa_restore(const pa_config* cfg, const void* buf, size_t size, void* cuda_stream, pa_ctx** out) {
+  if (!out) return PA_ERR_INVALID;
+  *out = nullptr;
+  if (!cfg || !buf || size < sizeof(CkptHeader)) return PA_ERR_INVALID;
+  CkptHeader h;
+  std::memcpy(&h, buf, sizeof h);
+  if (std::memcmp(h.magic, kCkptMagic, sizeof h.magic) != 0 || h.version != 1 ||
+      h.header_bytes != sizeof(CkptHeader) || h.total_bytes != size)
+    return PA_ERR_INVALID;
+  const int64_t R_cap = cfg->R_cap ? cfg->R_cap : cfg->R + 10 * (int64_t)std::ceil(std::sqrt((double)cfg->R)) + 1024;
+  const bool adaptive = cfg->betas == nullptr;
+  if (h.L != cfg->L || h.n_pop != cfg->n_pop || h.q_bins != cfg->q_bins || h.n_temps != cfg->n_temps ||
+      h.R != cfg->R || h.R_cap != R_cap || h.disorder_seed != cfg->disorder_seed || h.run_seed != cfg->run_seed ||
+      h.adaptive != (adaptive ? 1 : 0) || h.n_sweeps != cfg->n_sweeps || h.t < 0 || h.t >= h.n_temps ||
+      (adaptive && (h.eps_target != cfg->eps_target || h.beta_max != cfg->beta_max)))
+    return PA_ERR_INVALID;
+  pa_ctx* c = nullptr;
+  int rc = pa_create(cfg, cuda_stream, &c);
+  if (rc != PA_OK) return rc;
+  const RunGeom& g = c->g;
+  const int t = h.t;
+  for (int p = 0; p < g.n_pop; ++p)
+    if (h.R_tilde[p] < 1 || h.R_tilde[p] > g.R_cap || h.R_prev[p] < 0 || h.R_prev[p] > g.R_cap) {
+      pa_destroy(c);
+      return PA_ERR_INVALID;
+    }
+  if (ckpt_bytes(g, t, h.n_temps, h.R_tilde, h.R_prev) != size) {
+    pa_destroy(c);
+    return PA_ERR_INVALID;
+  }
+  const char* in = static_cast<const char*>(buf) + sizeof h;
+  const double* betas = reinterpret_cast<const double*>(in);
+  in += sizeof(double) * (size_t)h.n_temps;
+  const int32_t* sweeps = reinterpret_cast<const int32_t*>(in);
+  in += sizeof(int32_t) * (size_t)h.n_temps;
+  // the schedule must be the one the checkpoint was taken with
+  for (int u = 0; u < h.n_temps; ++u) {
+    if (!adaptive && std::memcmp(&betas[u], &c->betas[(size_t)u], sizeof(double)) != 0) rc = PA_ERR_INVALID;
+    if (sweeps[u] != c->sweeps[(size_t)u]) rc = PA_ERR_INVALID;
+  }
+  if (rc != PA_OK) {
+    pa_destroy(c);
+    return rc;
+  }
+  for (int u = 0; u <= t; ++u) c->betas[(size_t)u] = betas[u];
+  c->cur = 0;
+  for (int p = 0; p < g.n_pop && rc == PA_OK; ++p) {
+    PopDev& P = c->pops[p];
+    const size_t R = (size_t)h.R_tilde[p];
+    auto put = [&](void* dst, size_t bytes) {
+      if (rc == PA_OK && bytes) rc = copy_h2d(c, dst, in, bytes);
+      in += bytes;
+    };
+    put(P.rec, sizeof(StepRec) * (size_t)(t + 1));
+    put(P.hist, sizeof(uint32_t) * (size_t)(t + 1) * (size_t)g.n_levels);
+    if (rc == PA_OK) {
+      c->stats.h2d_bytes += (int64_t)(g.N * R);
+      rc = cuda_status(cudaMemcpy2DAsync(P.spins[0], (size_t)g.pitch, in, R, R, (size_t)g.N,
+                                         cudaMemcpyHostToDevice, c->stream));
+      if (rc == PA_OK) rc = cuda_status(cudaStreamSynchronize(c->stream));
+    }
+    in += (size_t)g.N * R;
+    put(P.labels[0], sizeof(int32_t) * R);
+    put(P.levels, sizeof(int32_t) * R);
+    put(P.counts, sizeof(int32_t) * (size_t)h.R_prev[p]);
+    put(P.parents, sizeof(int32_t) * R);
+    put(P.mhist, sizeof(int32_t) * (R + 1));
+  }
+  if (rc == PA_OK) rc = copy_h2d(c, c->qhist, in, sizeof(unsigned long long) * (size_t)(t + 1) * (size_t)g.q_bins);
+  if (rc != PA_OK) {
+    pa_destroy(c);
+    return rc;
+  }
+  c->t = t;
+  c->done = h.done != 0;
+  *out = c;
   return PA_OK;
 }
 

@@ -148,6 +148,8 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_int32)]),
     "pa_server_load": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "pa_server_destroy": (ctypes.c_int, [_vp]),
+    "pa_checkpoint": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "pa_restore": (ctypes.c_int, [ctypes.POINTER(Config), _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]),
     "pa_sweep_shapes": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(SweepShape), ctypes.c_int32, _i32p]),
     "pa_sweep_select": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32]),
     "pa_sweep_selected": (ctypes.c_int, [ctypes.c_int32, _i32p]),
@@ -392,7 +394,9 @@ class Run:
 
     def __init__(self, L: int, R: int, disorder_seed: int, run_seed: int, betas=None, *, n_temps: int = 0,
                  beta_max: float = 0.0, eps_target: float = 0.0, n_sweeps: int = 10, sweeps_per_step=None,
-                 n_pop: int = 1, q_bins: int = 65, R_cap: int = 0, stream=None):
+                 n_pop: int = 1, q_bins: int = 65, R_cap: int = 0, stream=None, checkpoint: bytes = None):
+        """Creates a run (pa_create), or, given `checkpoint` (bytes from Run.checkpoint of a
+        run with this configuration), restores it (pa_restore)."""
         self.L, self.N, self.n_pop, self.q_bins = L, L ** 3, n_pop, q_bins
         self.n_levels = 3 * self.N + 1
         self._betas = None if betas is None else np.ascontiguousarray(betas, dtype=np.float64)
@@ -407,8 +411,23 @@ class Run:
         c.q_bins = q_bins
         self.n_temps = c.n_temps
         h = _vp()
-        _check("pa_create", lib().pa_create(ctypes.byref(c), _stream_handle(stream), ctypes.byref(h)))
+        if checkpoint is None:
+            _check("pa_create", lib().pa_create(ctypes.byref(c), _stream_handle(stream), ctypes.byref(h)))
+        else:
+            buf = ctypes.create_string_buffer(bytes(checkpoint), len(checkpoint))
+            _check("pa_restore", lib().pa_restore(ctypes.byref(c), buf, len(checkpoint), _stream_handle(stream),
+                                                  ctypes.byref(h)))
         self._h = h
+
+    def checkpoint(self) -> bytes:
+        """The run's state after its last step (pa_checkpoint)."""
+        n = ctypes.c_size_t()
+        rc = lib().pa_checkpoint(self._h, None, 0, ctypes.byref(n))
+        if rc != PA_ERR_CAPACITY:
+            _check("pa_checkpoint", rc)
+        buf = ctypes.create_string_buffer(n.value)
+        _check("pa_checkpoint", lib().pa_checkpoint(self._h, buf, n.value, ctypes.byref(n)))
+        return buf.raw[: n.value]
 
     @classmethod
     def from_workload(cls, w, stream=None, **over):
