@@ -21,6 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pa_oracle.c")
+_SRC_GAUSS = os.path.join(_HERE, "pa_oracle_gauss.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 OK, DONE, ERR_INVALID, ERR_NOMEM, ERR_CAPACITY = 0, 1, -1, -2, -3
@@ -30,12 +31,12 @@ P_COUPLINGS, P_INIT, P_METROPOLIS, P_RESAMPLE = 0, 1, 2, 3
 def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/liboracle.so`` (returns its path)."""
     if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
+            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_GAUSS),
                                                os.path.getmtime(os.path.join(_HERE, "pa_oracle.h")))):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
-           "-o", tmp, _SRC, "-lm"]
+           "-o", tmp, _SRC, _SRC_GAUSS, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -97,6 +98,25 @@ class Obs(ctypes.Structure):
 _lib = None
 
 
+class GObs(ctypes.Structure):
+    """Observables of a Gaussian-coupling run (org_obs)."""
+    _fields_ = [
+        ("t", ctypes.c_int32), ("beta", ctypes.c_double), ("dbeta", ctypes.c_double),
+        ("R_tilde", ctypes.c_int64), ("sum_E", ctypes.c_int64), ("sum_E2", ctypes.c_double),
+        ("E_min", ctypes.c_int64), ("mean_E", ctypes.c_double), ("var_E", ctypes.c_double),
+        ("E_min_prev", ctypes.c_int64), ("S_prime", ctypes.c_double), ("lnQ", ctypes.c_double),
+        ("minus_beta_F", ctypes.c_double), ("eps_expected", ctypes.c_double), ("culled", ctypes.c_int64),
+        ("sum_eta2", ctypes.c_int64), ("n_families", ctypes.c_int64), ("rho_t", ctypes.c_double),
+        ("S_f", ctypes.c_double), ("rho_s", ctypes.c_double), ("E0", ctypes.c_int64),
+        ("g0_tilde", ctypes.c_double), ("g0_bar", ctypes.c_double), ("q_pairs", ctypes.c_int64),
+        ("q_abs_le_02", ctypes.c_int64), ("I02", ctypes.c_double), ("ql_sum", ctypes.c_int64),
+        ("ql_mean", ctypes.c_double), ("e_l", ctypes.c_double), ("delta_KY", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -135,6 +155,25 @@ def lib():
             "or_couplings_of": (i8p, [vp]),
             "or_beta": (ctypes.c_double, [vp, ctypes.c_int32]),
             "or_destroy": (None, [vp]),
+            "org_couplings": (None, [ctypes.c_int32, ctypes.c_uint64, i32p]),
+            "org_energy": (ctypes.c_int64, [ctypes.c_int32, i32p, i8p]),
+            "org_half_factor": (ctypes.c_float, [ctypes.c_double, ctypes.c_int64]),
+            "org_acceptance_threshold": (ctypes.c_uint32, [ctypes.c_double, ctypes.c_int64, ctypes.c_int64]),
+            "org_sweep_replica": (ctypes.c_int64, [ctypes.c_int32, i32p, i8p, ctypes.c_uint64, ctypes.c_int32,
+                                                   ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_double]),
+            "org_weight_tables": (None, [ctypes.c_double, dp]),
+            "org_weight": (ctypes.c_double, [dp, ctypes.c_int64]),
+            "org_tree_sum": (ctypes.c_double, [dp, ctypes.c_int64]),
+            "org_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(vp)]),
+            "org_step": (ctypes.c_int, [vp]),
+            "org_run_all": (ctypes.c_int, [vp]),
+            "org_current_step": (ctypes.c_int32, [vp]),
+            "org_observables": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(GObs)]),
+            "org_q_hist": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.c_int32, i64p]),
+            "org_population": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.c_int64, i8p, i32p, i64p, i64p]),
+            "org_last_counts": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.c_int64, i32p, i64p]),
+            "org_couplings_of": (i32p, [vp]),
+            "org_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -365,4 +404,140 @@ class Run:
 
     def couplings(self) -> np.ndarray:
         p = lib().or_couplings_of(self._h)
+        return np.ctypeslib.as_array(p, shape=(3 * self.N,)).copy()
+
+
+# ---------------------------------------------------------------- Gaussian couplings
+
+JSCALE = 2 ** 20
+T_SIZE = 8192 + 8192
+
+
+def gcouplings(L: int, seed: int) -> np.ndarray:
+    """Fixed-point Gaussian couplings Jq[3N] (units of 2^-20)."""
+    J = np.zeros(3 * L ** 3, dtype=np.int32)
+    lib().org_couplings(L, seed, _p(J, ctypes.c_int32))
+    return J
+
+
+def genergy(L: int, Jq: np.ndarray, s: np.ndarray) -> int:
+    Jq = np.ascontiguousarray(Jq, dtype=np.int32)
+    s = np.ascontiguousarray(s, dtype=np.int8)
+    return int(lib().org_energy(L, _p(Jq, ctypes.c_int32), _p(s, ctypes.c_int8)))
+
+
+def gsweep_replica(L: int, Jq: np.ndarray, s: np.ndarray, run_seed: int, pop: int, slot: int, t: int,
+                   n_sweeps: int, beta: float):
+    """Sweeps of one replica with Gaussian couplings; returns (new spins, energy change)."""
+    Jq = np.ascontiguousarray(Jq, dtype=np.int32)
+    s2 = np.array(s, dtype=np.int8, copy=True)
+    dE = lib().org_sweep_replica(L, _p(Jq, ctypes.c_int32), _p(s2, ctypes.c_int8), run_seed, pop, slot, t,
+                                 n_sweeps, beta)
+    return s2, int(dE)
+
+
+def gacceptance_threshold(beta: float, dE1: int, dE2: int) -> int:
+    return int(lib().org_acceptance_threshold(beta, dE1, dE2))
+
+
+def gweight_tables(dbeta: float) -> np.ndarray:
+    T = np.zeros(T_SIZE, dtype=np.float64)
+    lib().org_weight_tables(dbeta, _p(T, ctypes.c_double))
+    return T
+
+
+def gweight(T: np.ndarray, d: int) -> float:
+    return float(lib().org_weight(_p(np.ascontiguousarray(T), ctypes.c_double), d))
+
+
+def tree_sum(x: np.ndarray) -> float:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return float(lib().org_tree_sum(_p(x, ctypes.c_double), x.shape[0]))
+
+
+class GRun:
+    """One oracle PA run with Gaussian couplings (explicit schedule)."""
+
+    def __init__(self, cfg: RunConfig):
+        if cfg.betas is None:
+            raise ValueError("Gaussian runs take an explicit schedule")
+        self.cfg = cfg
+        self.L, self.N = cfg.L, cfg.L ** 3
+        self._betas = np.ascontiguousarray(cfg.betas, dtype=np.float64)
+        self._sweeps = (None if cfg.sweeps_per_step is None
+                        else np.ascontiguousarray(cfg.sweeps_per_step, dtype=np.int32))
+        c = Config()
+        c.L, c.R = cfg.L, cfg.R
+        c.R_cap = cfg.R_cap or default_capacity(cfg.R)
+        c.disorder_seed, c.run_seed = cfg.disorder_seed, cfg.run_seed
+        c.n_pop, c.n_temps = cfg.n_pop, len(self._betas)
+        c.betas = _p(self._betas, ctypes.c_double)
+        c.n_sweeps = cfg.n_sweeps
+        c.sweeps_per_step = _p(self._sweeps, ctypes.c_int32) if self._sweeps is not None else None
+        c.q_bins, c.n_threads = cfg.q_bins, cfg.n_threads
+        self.R_cap, self.n_temps, self.n_pop, self.q_bins = c.R_cap, c.n_temps, cfg.n_pop, cfg.q_bins
+        h = ctypes.c_void_p()
+        rc = lib().org_create(ctypes.byref(c), ctypes.byref(h))
+        if rc != OK:
+            raise RuntimeError(f"org_create failed: {rc}")
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().org_destroy(h)
+            self._h = None
+
+    def step(self) -> int:
+        rc = lib().org_step(self._h)
+        if rc < 0:
+            raise RuntimeError(f"org_step failed: {rc}")
+        return rc
+
+    def run(self) -> None:
+        rc = lib().org_run_all(self._h)
+        if rc != OK:
+            raise RuntimeError(f"org_run_all failed: {rc}")
+
+    @property
+    def t(self) -> int:
+        return int(lib().org_current_step(self._h))
+
+    def obs(self, t: int, pop: int = 0) -> dict:
+        o = GObs()
+        rc = lib().org_observables(self._h, t, pop, ctypes.byref(o))
+        if rc != OK:
+            raise RuntimeError(f"org_observables failed: {rc}")
+        return o.as_dict()
+
+    def q_hist(self, t: int, link: bool = False) -> np.ndarray:
+        out = np.zeros(self.q_bins, dtype=np.int64)
+        rc = lib().org_q_hist(self._h, t, int(link), _p(out, ctypes.c_int64))
+        if rc != OK:
+            raise RuntimeError(f"org_q_hist failed: {rc}")
+        return out
+
+    def population(self, pop: int = 0):
+        """(spins [R~, N] int8, labels int32, energies int64 in units of 2^-20)."""
+        s = np.zeros((self.R_cap, self.N), dtype=np.int8)
+        lab = np.zeros(self.R_cap, dtype=np.int32)
+        E = np.zeros(self.R_cap, dtype=np.int64)
+        n = ctypes.c_int64()
+        rc = lib().org_population(self._h, pop, self.R_cap, _p(s, ctypes.c_int8), _p(lab, ctypes.c_int32),
+                                  _p(E, ctypes.c_int64), ctypes.byref(n))
+        if rc != OK:
+            raise RuntimeError(f"org_population failed: {rc}")
+        k = n.value
+        return s[:k].copy(), lab[:k].copy(), E[:k].copy()
+
+    def last_counts(self, pop: int = 0) -> np.ndarray:
+        out = np.zeros(self.R_cap, dtype=np.int32)
+        n = ctypes.c_int64()
+        rc = lib().org_last_counts(self._h, pop, self.R_cap, _p(out, ctypes.c_int32), ctypes.byref(n))
+        if rc != OK:
+            raise RuntimeError(f"org_last_counts failed: {rc}")
+        return out[:n.value].copy()
+
+    def couplings(self) -> np.ndarray:
+        p = lib().org_couplings_of(self._h)
         return np.ctypeslib.as_array(p, shape=(3 * self.N,)).copy()

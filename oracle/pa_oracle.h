@@ -123,6 +123,56 @@ const int8_t* or_couplings_of(const or_run* run);
 double or_beta(const or_run* run, int32_t t);
 void or_destroy(or_run* run);
 
+/* ---- Gaussian couplings (the paper's model, §II.A): pa_oracle_gauss.c ----
+ * Couplings J ~ N(0,1) clamped to [-5, 5] in fixed point Jq = round(J 2^20);
+ * energies in the same units (int64).  Explicit schedules, even L. */
+#define ORG_T2_SIZE 8192   /* entries of the coarsest weight table */
+
+typedef struct {
+  int32_t t;
+  double beta, dbeta;
+  int64_t R_tilde;
+  int64_t sum_E;            /* exact, units of 2^-20 */
+  double sum_E2;            /* exact 128-bit sum of E^2 rounded to double, units of 2^-40 */
+  int64_t E_min;            /* lowest energy at t */
+  double mean_E, var_E;     /* in units of J */
+  int64_t E_min_prev;       /* lowest energy of the step t-1 population */
+  double S_prime, lnQ, minus_beta_F, eps_expected;
+  int64_t culled, sum_eta2, n_families;
+  double rho_t, S_f, rho_s;
+  int64_t E0;               /* lowest energy measured up to t */
+  double g0_tilde, g0_bar;
+  int64_t q_pairs, q_abs_le_02;
+  double I02;
+  int64_t ql_sum;           /* sum over pairs of sum over bonds s1 s1 s2 s2 */
+  double ql_mean;           /* <q_l>, Eq. (ql) */
+  double e_l;               /* Eq. (el) */
+  double delta_KY;          /* e_l - <E>/N for this disorder sample (Eq. KY before the disorder average) */
+} org_obs;
+
+typedef struct org_run org_run;
+
+void org_couplings(int32_t L, uint64_t disorder_seed, int32_t* Jq);
+int64_t org_energy(int32_t L, const int32_t* Jq, const int8_t* s);
+float org_half_factor(double beta, int64_t dEh);
+uint32_t org_acceptance_threshold(double beta, int64_t dE1, int64_t dE2);
+int64_t org_sweep_replica(int32_t L, const int32_t* Jq, int8_t* s, uint64_t run_seed, int32_t pop, int64_t slot,
+                          int32_t t, int32_t n_sweeps, double beta);
+void org_weight_tables(double dbeta, double* T);   /* T: 8192 + ORG_T2_SIZE doubles */
+double org_weight(const double* T, int64_t d);
+double org_tree_sum(const double* x, int64_t n);
+int org_create(const or_config* cfg, org_run** out);
+int org_step(org_run* run);
+int org_run_all(org_run* run);
+int32_t org_current_step(const org_run* run);
+int org_observables(const org_run* run, int32_t t, int32_t pop, org_obs* out);
+int org_q_hist(const org_run* run, int32_t t, int32_t link, int64_t* out);
+int org_population(const org_run* run, int32_t pop, int64_t cap, int8_t* spins, int32_t* labels, int64_t* E,
+                   int64_t* n);
+int org_last_counts(const org_run* run, int32_t pop, int64_t cap, int32_t* counts, int64_t* n);
+const int32_t* org_couplings_of(const org_run* run);
+void org_destroy(org_run* run);
+
 #ifdef __cplusplus
 }
 #endif

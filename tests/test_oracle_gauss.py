@@ -1,0 +1,214 @@
+"""Pins of the Gaussian-coupling oracle (the paper's model, §II.A) against facts
+that do not come from the oracle itself: the normal law of the couplings, exact
+enumeration of all states at L = 2 (partition function, energy, link overlap),
+the Katzgraber-Young identity of Gaussian disorder (Eqs. KY, el), the Boltzmann
+distribution reached by the Metropolis sweeps, and the closed forms behind the
+acceptance and resampling tables."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+SCALE = 2.0 ** -20
+
+
+def _bonds(L):
+    N = L ** 3
+
+    def nb(n, d):
+        x, y, z = n % L, (n // L) % L, n // (L * L)
+        if d == 0:
+            x = (x + 1) % L
+        if d == 1:
+            y = (y + 1) % L
+        if d == 2:
+            z = (z + 1) % L
+        return x + L * (y + L * z)
+    return [(n, nb(n, d), 3 * n + d) for n in range(N) for d in range(3)]
+
+
+def _exact_l2(J, beta):
+    """Exact ln Z, <E> and the bond correlations <s s>_b of an L = 2 sample."""
+    L, N = 2, 8
+    bonds = _bonds(L)
+    states = np.array(list(itertools.product([1, -1], repeat=N)), dtype=np.int64)
+    ss = np.stack([states[:, a] * states[:, b] for a, b, _ in bonds], axis=1)
+    E = -(ss * np.array([J[k] for _, _, k in bonds], dtype=np.float64)).sum(axis=1)
+    lw = -beta * E
+    m = lw.max()
+    w = np.exp(lw - m)
+    Z = w.sum()
+    p = w / Z
+    return m + math.log(Z), float((p * E).sum()), (p[:, None] * ss).sum(axis=0), E, p
+
+
+def test_couplings_are_standard_normal():
+    J = np.concatenate([oracle.gcouplings(16, seed) for seed in (1, 2, 3)]).astype(np.float64) * SCALE
+    n = J.size
+    assert abs(J.mean()) < 4 / math.sqrt(n)
+    assert abs(J.var() - 1.0) < 4 * math.sqrt(2.0 / n)
+    # fourth moment of N(0,1) is 3; fraction beyond one sigma is 0.3173
+    assert abs((J ** 4).mean() - 3.0) < 0.15
+    assert abs((np.abs(J) > 1.0).mean() - 0.3173) < 0.01
+    assert np.abs(J).max() <= 5.0
+    Jq = oracle.gcouplings(8, 5)
+    assert Jq.dtype == np.int32 and np.array_equal(Jq, oracle.gcouplings(8, 5))
+    assert not np.array_equal(Jq, oracle.gcouplings(8, 6))
+
+
+def test_energy_symmetries():
+    L = 4
+    Jq = oracle.gcouplings(L, 11)
+    rng = np.random.default_rng(0)
+    s = rng.choice([-1, 1], size=L ** 3).astype(np.int8)
+    E = oracle.genergy(L, Jq, s)
+    assert oracle.genergy(L, Jq, -s) == E                       # global flip
+    assert oracle.genergy(L, Jq, np.ones(L ** 3, np.int8)) == -int(Jq.astype(np.int64).sum())
+    # gauge: s -> g s, J_nm -> g_n g_m J_nm leaves E unchanged
+    g = rng.choice([-1, 1], size=L ** 3)
+    Jg = Jq.copy()
+    for n, m, k in _bonds(L):
+        Jg[k] = Jq[k] * g[n] * g[m]
+    assert oracle.genergy(L, Jg, (s * g).astype(np.int8)) == E
+    # a single flip changes E by 2 s_n h_n
+    n0 = 13
+    h = sum(int(Jq[k]) * int(s[m] if a == n0 else s[a]) for a, m, k in _bonds(L) if n0 in (a, m))
+    s2 = s.copy()
+    s2[n0] = -s2[n0]
+    assert oracle.genergy(L, Jq, s2) - E == 2 * int(s[n0]) * h
+
+
+@pytest.mark.parametrize("beta", [0.1, 0.7, 2.0])
+def test_acceptance_threshold_is_the_boltzmann_factor(beta):
+    rng = np.random.default_rng(1)
+    for _ in range(300):
+        d1, d2 = (int(x) for x in rng.integers(-20 * 2 ** 20, 20 * 2 ** 20, size=2))
+        if d1 + d2 <= 0:
+            continue
+        exact = math.exp(-beta * (d1 + d2) * SCALE) * 2 ** 32
+        thr = oracle.gacceptance_threshold(beta, d1, d2)
+        assert abs(thr - min(exact, 2 ** 32 - 1)) <= 4e-7 * exact + 1   # single-precision product of two factors
+
+
+def test_weight_tables_and_tree_sum():
+    rng = np.random.default_rng(2)
+    for dbeta in (0.013, 0.2, 1.5):
+        T = oracle.gweight_tables(dbeta)
+        for d in [0, 1, 4095, 4096, 2 ** 24 - 1, 2 ** 24, 3 * 2 ** 30] + list(rng.integers(0, 2 ** 36, 50)):
+            x = dbeta * int(d) * SCALE
+            exact = math.exp(-x)
+            # a few roundings of the argument and of three factors: relative error ~ (1 + x) ulp
+            assert abs(oracle.gweight(T, int(d)) - exact) <= (2e-15 + 4e-16 * x) * exact + 1e-300
+    for n in (1, 255, 256, 257, 5000):
+        x = rng.random(n)
+        assert abs(oracle.tree_sum(x) - math.fsum(x)) <= 1e-13 * math.fsum(x)
+    x = rng.random(1000)
+    # the fixed order is the definition: chunk trees, then chunks in sequence
+    chunks = []
+    for c0 in range(0, 1000, 256):
+        a = np.zeros(256)
+        a[: min(256, 1000 - c0)] = x[c0:c0 + 256]
+        h = 128
+        while h >= 1:
+            a[:h] = a[:h] + a[h:2 * h]
+            h //= 2
+        chunks.append(a[0])
+    total = 0.0
+    for c in chunks:
+        total = total + c
+    assert oracle.tree_sum(x) == total
+
+
+def test_katzgraber_young_identity_by_enumeration():
+    """For Gaussian disorder [<E>/N] = -beta (N_b/N)(1 - [<q_l>]) exactly (Eqs. KY, el);
+    it holds for the oracle's couplings over many L = 2 samples within the error."""
+    beta, d = 1.1, []
+    bonds = _bonds(2)
+    for seed in range(1, 801):
+        J = oracle.gcouplings(2, seed).astype(np.float64) * SCALE
+        _, Em, corr, _, _ = _exact_l2(J, beta)
+        ql = float((corr ** 2).mean())
+        d.append(-3 * beta * (1 - ql) - Em / 8)
+    d = np.array(d)
+    assert abs(d.mean()) < 3.5 * d.std() / math.sqrt(d.size)
+    # and a biased coupling law would break it: shift every J by +0.5
+    d2 = []
+    for seed in range(1, 401):
+        J = oracle.gcouplings(2, seed).astype(np.float64) * SCALE + 0.5
+        _, Em, corr, _, _ = _exact_l2(J, beta)
+        d2.append(-3 * beta * (1 - float((corr ** 2).mean())) - Em / 8)
+    d2 = np.array(d2)
+    assert abs(d2.mean()) > 5 * d2.std() / math.sqrt(d2.size)
+
+
+@pytest.mark.parametrize("L", [4, 6])
+def test_sweep_energy_changes_add_up(L):
+    """The energy change a sweep reports equals the energy recomputed from scratch
+    (every flip's dE uses the right six bonds; at L = 2 the x+1 and x-1 bonds
+    join the same pair, so this needs L >= 4)."""
+    Jq = oracle.gcouplings(L, 31 + L)
+    rng = np.random.default_rng(L)
+    for j, beta in enumerate((0.2, 0.9, 3.0)):
+        s = rng.choice([-1, 1], size=L ** 3).astype(np.int8)
+        s2, dE = oracle.gsweep_replica(L, Jq, s, 5, 0, j, 2, 3, beta)
+        assert oracle.genergy(L, Jq, s2) - oracle.genergy(L, Jq, s) == dE
+        assert (s2 != s).any()
+
+
+def test_sweeps_sample_the_boltzmann_distribution():
+    L, beta, seed = 2, 0.8, 21
+    Jq = oracle.gcouplings(L, seed)
+    _, _, _, E, p = _exact_l2(Jq.astype(np.float64) * SCALE, beta)
+    Eq = np.rint(E / SCALE).astype(np.int64)
+    levels, inv = np.unique(Eq, return_inverse=True)
+    pl = np.bincount(inv, weights=p)
+    rng = np.random.default_rng(3)
+    n_chains, counts = 4000, np.zeros(levels.size)
+    for j in range(n_chains):
+        s = rng.choice([-1, 1], size=8).astype(np.int8)
+        s, _ = oracle.gsweep_replica(L, Jq, s, 99, 0, j, 1, 30, beta)
+        counts[np.searchsorted(levels, oracle.genergy(L, Jq, s))] += 1
+    exp_ = pl * n_chains
+    keep = exp_ > 5
+    chi2 = (((counts[keep] - exp_[keep]) ** 2) / exp_[keep]).sum()
+    dof = keep.sum() - 1
+    assert chi2 < dof + 5 * math.sqrt(2 * dof)
+
+
+def test_run_reproduces_exact_free_energy_energy_and_link_overlap():
+    L, seed, R = 2, 7, 30000
+    betas = np.linspace(0.0, 1.5, 16)
+    run = oracle.GRun(oracle.RunConfig(L=L, R=R, disorder_seed=seed, run_seed=3, betas=betas, n_sweeps=4, n_pop=2))
+    run.run()
+    J = run.couplings().astype(np.float64) * SCALE
+    for t in (5, 10, 15):
+        lnZ, Em, corr, _, _ = _exact_l2(J, betas[t])
+        o0, o1 = run.obs(t, 0), run.obs(t, 1)
+        assert abs(o0["minus_beta_F"] - lnZ) < 0.01
+        assert abs(o1["minus_beta_F"] - lnZ) < 0.01
+        assert abs(o0["mean_E"] - Em) < 0.05
+        ql_exact = float((corr ** 2).mean())
+        assert abs(o0["ql_mean"] - ql_exact) < 0.01
+        assert o0["ql_mean"] == o1["ql_mean"] and o0["q_pairs"] == min(o0["R_tilde"], o1["R_tilde"])
+        assert abs(o0["delta_KY"] - (-3 * betas[t] * (1 - o0["ql_mean"]) - o0["mean_E"] / 8)) < 1e-12
+    # population and histograms are consistent with the observables
+    s, lab, E = run.population(0)
+    o = run.obs(run.t, 0)
+    assert s.shape[0] == o["R_tilde"] and int(E.sum()) == o["sum_E"] and int(E.min()) == o["E_min"]
+    assert all(oracle.genergy(L, run.couplings(), s[j]) == E[j] for j in range(0, s.shape[0], 997))
+    assert run.q_hist(run.t).sum() == o["q_pairs"] and run.q_hist(run.t, link=True).sum() == o["q_pairs"]
+
+
+def test_run_is_independent_of_thread_count():
+    betas = np.linspace(0, 2.0, 6)
+    outs = []
+    for threads in (1, 3):
+        r = oracle.GRun(oracle.RunConfig(L=4, R=700, disorder_seed=2, run_seed=8, betas=betas, n_sweeps=2,
+                                         n_threads=threads))
+        r.run()
+        outs.append((r.population(0), r.obs(r.t, 0)))
+    (a, oa), (b, ob) = outs
+    assert all(np.array_equal(x, y) for x, y in zip(a, b)) and oa == ob
