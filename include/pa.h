@@ -63,7 +63,12 @@ extern "C" {
  * n_sweeps, sweeps_per_step   sweeps of step t: sweeps_per_step[t] if non-NULL
  *              (n_temps entries), else n_sweeps.  Step 0 never sweeps.
  * q_bins       overlap histogram bins over q in [-1, 1] (odd, >= 3; 65 typical).
+ * model        PA_MODEL_PM1: couplings +-1 with p = 1/2; PA_MODEL_GAUSS: couplings
+ *              ~ N(0,1) (the paper's model, §II.A), clamped to [-5, 5] and held in
+ *              fixed point (units of 2^-20), explicit schedules only.
  * The configuration and the arrays it points to are copied by pa_create. */
+#define PA_MODEL_PM1 0
+#define PA_MODEL_GAUSS 1
 typedef struct {
   int32_t L;
   int32_t n_pop;
@@ -78,6 +83,7 @@ typedef struct {
   int32_t n_sweeps;
   const int32_t* sweeps_per_step;
   int32_t q_bins;
+  int32_t model;
 } pa_config;
 
 /* ---- observables of one population at step t (after the sweeps at beta_t) ----
@@ -107,6 +113,34 @@ typedef struct {
   int64_t q_abs_le_02;    /* pairs with |q| <= 0.2 */
   double I02;             /* q_abs_le_02 / q_pairs, the per-sample I(0.2) */
 } pa_obs;
+
+/* ---- observables of a Gaussian-coupling run (model PA_MODEL_GAUSS) ----
+ * Energies are exact integers in units of 2^-20; mean_E, var_E and the derived
+ * quantities are in units of J.  The link overlap q_l (Eq. ql) is measured between
+ * slot j of the two populations, with e_l (Eq. el) and e_l - <E>/N, the
+ * per-sample term of Delta_KY (Eq. KY; its disorder average vanishes for
+ * Gaussian couplings in equilibrium). */
+typedef struct {
+  int32_t t;
+  double beta, dbeta;
+  int64_t R_tilde;
+  int64_t sum_E;          /* exact sum of E (units of 2^-20) */
+  double sum_E2;          /* exact sum of E^2 (units of 2^-40), rounded once to double */
+  int64_t E_min;          /* lowest energy at t */
+  double mean_E, var_E;
+  int64_t E_min_prev;     /* lowest energy of the step t-1 population */
+  double S_prime, lnQ, minus_beta_F, eps_expected;
+  int64_t culled, sum_eta2, n_families;
+  double rho_t, S_f, rho_s;
+  int64_t E0;             /* lowest energy at steps 0..t */
+  double g0_tilde, g0_bar;
+  int64_t q_pairs, q_abs_le_02;
+  double I02;
+  int64_t ql_sum;         /* sum over pairs of sum over bonds s1_n s1_m s2_n s2_m */
+  double ql_mean;         /* <q_l> = ql_sum / (3N q_pairs) */
+  double e_l;             /* -3 beta (1 - <q_l>) */
+  double delta_KY;        /* e_l - <E>/N */
+} pa_gobs;
 
 typedef struct pa_ctx pa_ctx;
 
@@ -162,6 +196,19 @@ int pa_get_couplings(pa_ctx* ctx, int8_t* J, int64_t cap);
 
 /* Inverse temperature of step t (t <= pa_current_step), or a negative value. */
 double pa_beta(const pa_ctx* ctx, int32_t t);
+
+/* ---- Gaussian-coupling runs (model PA_MODEL_GAUSS) ----
+ * pa_observables, pa_energy_hist and the energies of pa_get_replicas are for
+ * +-1 runs (PA_ERR_INVALID otherwise); a Gaussian run reads its observables,
+ * energies, link-overlap histogram and couplings here. */
+int pa_gobservables(pa_ctx* ctx, int32_t t, int32_t pop, pa_gobs* out);
+/* Energies (units of 2^-20) of slots [first, first + n) of population pop. */
+int pa_get_genergies(pa_ctx* ctx, int32_t pop, int64_t first, int64_t n, int64_t* E);
+/* Link-overlap histogram of step t: bin ((Q_l + 3N)(q_bins - 1) + 3N) div 6N of
+ * Q_l = sum over bonds s1_n s1_m s2_n s2_m; q_bins entries (two populations). */
+int pa_ql_hist(pa_ctx* ctx, int32_t t, int64_t* out, int64_t cap);
+/* Fixed-point couplings Jq[3n + d] (3N int32, units of 2^-20) of a Gaussian run. */
+int pa_get_gcouplings(pa_ctx* ctx, int32_t* Jq, int64_t cap);
 
 /* ---- instrumentation ----
  * Counters since the last pa_stats_reset: steps run, kernels launched by the

@@ -1,0 +1,370 @@
+// pa_gauss.cu — the Gaussian-coupling model (§II.A: J ~ N(0,1)): initial
+// energies, resampling from per-replica weights, energy moments and the link
+// overlap.  (Its sweep kernel, k_sweep_g, lives with the other sweep kernels.)
+//
+// Couplings and energies are fixed point (units of 2^-20, couplings clamped to
+// [-5, 5]), so energies, their sums and the link overlap are exact integers and
+// every floating-point decision has one definition shared with the oracle:
+//   - weight of old slot i: w_i = (T2[d >> 24] * T1[(d >> 12) & 4095]) * T0[d & 4095]
+//     with d = E_i - E_min and host tables T_k[m] = exp(-dbeta m 2^(12k) 2^-20);
+//   - S' = sum_i w_i and the culling sum sum_i (1 - tau_i)_+ in a fixed order:
+//     chunks of 256 slots, each by a binary tree, then the chunk totals in order;
+//   - tau_i = R w_i / S', n_i = floor(tau_i) + [r_i < 2^32 frac(tau_i)] (§II).
+#include <cuda_runtime.h>
+
+#include "pa_device.cuh"
+#include "pa_internal.h"
+
+namespace pa {
+
+namespace {
+
+struct GArgs {
+  PopDev p[2];
+};
+
+GArgs gpack(const PopDev* pops, int n_pop) {
+  GArgs a;
+  for (int i = 0; i < n_pop && i < 2; ++i) a.p[i] = pops[i];
+  return a;
+}
+
+__host__ __device__ inline int blocks_for(long long n, int per) { return (int)((n + per - 1) / per); }
+
+constexpr uint32_t kBit1 = 0x02020202u;  // bit 1 of each byte: the two int8 spins differ
+
+// ---------------------------------------------------------------- initial energies
+
+// E_j = -sum_bonds J s s = -Jtot + 2 sum over antiparallel bonds of J, for the
+// four slots of one 32-bit word of every site row (int8 spins, site-major).
+__global__ void k_g_energy_init(RunGeom g, GArgs a, int cur, const int32_t* __restrict__ Jq) {
+  const PopDev& P = a.p[blockIdx.y];
+  const int R = P.rec[0].R_tilde;
+  const int wi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (4 * wi >= R) return;
+  const int L = g.L;
+  const uint32_t* S = reinterpret_cast<const uint32_t*>(P.spins[cur]);
+  const int64_t pw = g.pitch / 4;
+  long long anti[4] = {0, 0, 0, 0}, jtot = 0;
+  for (int n = 0; n < g.N; ++n) {
+    const int x = n % L, y = (n / L) % L, z = n / (L * L);
+    const int nb[3] = {(x + 1 == L ? 0 : x + 1) + L * (y + L * z), x + L * ((y + 1 == L ? 0 : y + 1) + L * z),
+                       x + L * (y + L * (z + 1 == L ? 0 : z + 1))};
+    const uint32_t s = S[n * pw + wi];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const long long J = Jq[3 * n + d];
+      jtot += J;
+      const uint32_t x4 = (s ^ S[nb[d] * pw + wi]) & kBit1;
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        if ((x4 >> (8 * b + 1)) & 1u) anti[b] += J;
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int j = 4 * wi + b;
+    if (j < R) P.E64[j] = -jtot + 2 * anti[b];
+  }
+}
+
+// Opens the records of step t (what k_g_weights does for t >= 1).
+__global__ void k_g_open(GArgs a, int t) {
+  GRec& r = a.p[threadIdx.x].grec[t];
+  r.E_min = 0x7fffffffffffffffLL;
+  r.E0 = 0;
+  r.sum_E = 0;
+  r.sum_E2_lo = r.sum_E2_hi = 0;
+  r.n_at_E0 = 0;
+  r.ql_sum = 0;
+}
+
+// ---------------------------------------------------------------- resampling
+
+// Sum of a[0..256) of shared memory by the fixed binary tree; result in a[0].
+__device__ __forceinline__ void chunk_tree(double* a) {
+  for (int h = kChunk / 2; h >= 1; h >>= 1) {
+    if ((int)threadIdx.x < h) a[threadIdx.x] = __dadd_rn(a[threadIdx.x], a[threadIdx.x + h]);
+    __syncthreads();
+  }
+}
+
+// Weights of the old slots of step t-1 and their chunk partial sums.  Block 0
+// also opens the records of step t.
+__global__ void __launch_bounds__(kChunk) k_g_weights(RunGeom g, GArgs a, int t, const double* __restrict__ T) {
+  __shared__ double sh[kChunk];
+  PopDev& P = a.p[blockIdx.y];
+  const int R_old = P.rec[t - 1].R_tilde;
+  const long long Emin = P.grec[t - 1].E_min;
+  const int i = blockIdx.x * kChunk + threadIdx.x;
+  double w = 0.0;
+  if (i < R_old) {
+    const long long d = P.E64[i] - Emin;
+    w = __dmul_rn(__dmul_rn(T[8192 + (d >> 24)], T[4096 + ((d >> 12) & 4095)]), T[d & 4095]);
+    P.w[i] = w;
+  }
+  sh[threadIdx.x] = w;
+  __syncthreads();
+  chunk_tree(sh);
+  if (threadIdx.x == 0) P.part[blockIdx.x] = sh[0];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    P.rec[t].R_prev = R_old;
+    GRec& r = P.grec[t];
+    r.E_min = 0x7fffffffffffffffLL;
+    r.E0 = 0;
+    r.sum_E = 0;
+    r.sum_E2_lo = r.sum_E2_hi = 0;
+    r.n_at_E0 = 0;
+    r.ql_sum = 0;
+  }
+}
+
+// The chunk totals one after another (one thread), into S' (which = 0) or the
+// expected culling fraction (which = 1, divided by R).
+__global__ void k_g_chunks(RunGeom g, GArgs a, int t, int which) {
+  PopDev& P = a.p[blockIdx.x];
+  const int n = blocks_for(P.rec[t - 1].R_tilde, kChunk);
+  double total = 0.0;
+  for (int c = 0; c < n; ++c) total = __dadd_rn(total, P.part[c]);
+  if (which == 0)
+    P.rec[t].S_prime = total;
+  else
+    P.rec[t].eps_expected = __ddiv_rn(total, (double)g.R);
+}
+
+// tau_i = R w_i / S', its floor and 2^32-scaled fraction, and the chunk partial
+// sums of (1 - tau_i)_+.
+__global__ void __launch_bounds__(kChunk) k_g_tau(RunGeom g, GArgs a, int t) {
+  __shared__ double sh[kChunk];
+  PopDev& P = a.p[blockIdx.y];
+  const int R_old = P.rec[t - 1].R_tilde;
+  const double S = P.rec[t].S_prime;
+  const int i = blockIdx.x * kChunk + threadIdx.x;
+  double c = 0.0;
+  if (i < R_old) {
+    const double tau = __ddiv_rn(__dmul_rn((double)g.R, P.w[i]), S);
+    const double f = floor(tau);
+    P.gfl[i] = (int32_t)f;
+    P.gthr[i] = __double2uint_rz(__dmul_rn(__dsub_rn(tau, f), 4294967296.0));
+    c = tau < 1.0 ? __dsub_rn(1.0, tau) : 0.0;
+  }
+  sh[threadIdx.x] = c;
+  __syncthreads();
+  chunk_tree(sh);
+  if (threadIdx.x == 0) P.part[blockIdx.x] = sh[0];
+}
+
+// Copy numbers n_i = fl_i + [r_i < thr_i], r_i = word (i & 3) of Philox at counter
+// (i >> 2, 0, 0, t) keyed by (run seed, resampling, population); block totals
+// feed the scan of the ±1 path.
+__global__ void __launch_bounds__(kCountThreads) k_g_counts(RunGeom g, GArgs a, int t) {
+  __shared__ int red[kCountThreads / 32];
+  PopDev& P = a.p[blockIdx.y];
+  const int R_old = P.rec[t - 1].R_tilde;
+  const int i0 = blockIdx.x * kSlotsPerCountBlock + 4 * threadIdx.x;
+  int sum = 0, cul = 0;
+  if (i0 < R_old) {
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)(i0 >> 2), 0u, 0u, (uint32_t)t), P.key_res[0], P.key_res[1]);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = i0 + b;
+      if (i < R_old) {
+        const int n = P.gfl[i] + (word_of(r, b) < P.gthr[i] ? 1 : 0);
+        P.counts[i] = n;
+        sum += n;
+        cul += (n == 0);
+      }
+    }
+  }
+  sum = warp_sum(sum);
+  cul = warp_sum(cul);
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = sum;
+    if (cul) atomicAdd(&P.rec[t].culled, cul);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int k = 0; k < kCountThreads / 32; ++k) s += red[k];
+    P.blocksums[blockIdx.x] = s;
+  }
+}
+
+// ---------------------------------------------------------------- measurement
+
+constexpr int kMeasureThreads = 256;
+constexpr int kMeasurePerBlock = 4096;
+
+// Lowest energy, exact sum, and 128-bit partial sums of E^2 of the step-t population.
+__global__ void __launch_bounds__(kMeasureThreads) k_g_moments(RunGeom g, GArgs a, int t) {
+  __shared__ long long smin[kMeasureThreads / 32], ssum[kMeasureThreads / 32];
+  __shared__ unsigned long long s2lo[kMeasureThreads / 32], s2hi[kMeasureThreads / 32];
+  PopDev& P = a.p[blockIdx.y];
+  const int R = P.rec[t].R_tilde;
+  long long mn = 0x7fffffffffffffffLL, sm = 0;
+  unsigned __int128 s2 = 0;
+  const int base = blockIdx.x * kMeasurePerBlock;
+  for (int k = threadIdx.x; k < kMeasurePerBlock; k += kMeasureThreads) {
+    const int j = base + k;
+    if (j < R) {
+      const long long E = P.E64[j];
+      mn = E < mn ? E : mn;
+      sm += E;
+      s2 += (unsigned __int128)(E < 0 ? -E : E) * (unsigned __int128)(E < 0 ? -E : E);
+    }
+  }
+  unsigned long long lo = (unsigned long long)s2, hi = (unsigned long long)(s2 >> 64);
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long m2 = __shfl_down_sync(0xffffffffu, mn, o);
+    mn = m2 < mn ? m2 : mn;
+    sm += __shfl_down_sync(0xffffffffu, sm, o);
+    const unsigned long long lo2 = __shfl_down_sync(0xffffffffu, lo, o);
+    const unsigned long long hi2 = __shfl_down_sync(0xffffffffu, hi, o);
+    const unsigned long long nl = lo + lo2;
+    hi = hi + hi2 + (nl < lo ? 1ull : 0ull);
+    lo = nl;
+  }
+  const int wv = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    smin[wv] = mn;
+    ssum[wv] = sm;
+    s2lo[wv] = lo;
+    s2hi[wv] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned __int128 tot = 0;
+    for (int k = 0; k < kMeasureThreads / 32; ++k) {
+      mn = smin[k] < mn ? smin[k] : mn;
+      tot += ((unsigned __int128)s2hi[k] << 64) | s2lo[k];
+    }
+    long long st = 0;
+    for (int k = 0; k < kMeasureThreads / 32; ++k) st += ssum[k];
+    atomicMin(&P.grec[t].E_min, mn);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&P.grec[t].sum_E), (unsigned long long)st);
+    P.e2part[2 * blockIdx.x] = (unsigned long long)tot;
+    P.e2part[2 * blockIdx.x + 1] = (unsigned long long)(tot >> 64);
+  }
+}
+
+// One block per population: the exact sum of E^2, E0 = min(E0 of t-1, E_min of
+// t), and the number of replicas at E0.
+__global__ void k_g_finish(RunGeom g, GArgs a, int t) {
+  __shared__ long long cnt[32];
+  PopDev& P = a.p[blockIdx.x];
+  const int R = P.rec[t].R_tilde;
+  GRec& r = P.grec[t];
+  const long long E0 = (t == 0 || r.E_min < P.grec[t - 1].E0) ? r.E_min : P.grec[t - 1].E0;
+  long long c = 0;
+  for (int j = threadIdx.x; j < R; j += blockDim.x) c += P.E64[j] == E0;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) cnt[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long tot = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += cnt[k];
+    unsigned __int128 s2 = 0;
+    for (int b = 0; b < blocks_for(R, kMeasurePerBlock); ++b)
+      s2 += ((unsigned __int128)P.e2part[2 * b + 1] << 64) | P.e2part[2 * b];
+    r.sum_E2_lo = (unsigned long long)s2;
+    r.sum_E2_hi = (unsigned long long)(s2 >> 64);
+    r.E0 = E0;
+    r.n_at_E0 = tot;
+  }
+}
+
+// Link overlap (Eq. ql) between slot j of the two populations, four pairs per
+// thread: with c = s1 s2 per site, QL = sum over bonds of c_n c_m = N_b - 2
+// (bonds whose c differ); histogram bin ((QL + N_b)(B - 1) + N_b) div 2N_b.
+__global__ void k_g_link(RunGeom g, GArgs a, int cur, int t, unsigned long long* qlhist) {
+  extern __shared__ unsigned int qh[];
+  __shared__ long long ssum;
+  const PopDev& A = a.p[0];
+  const PopDev& B = a.p[1];
+  const int pairs = min(A.rec[t].R_tilde, B.rec[t].R_tilde);
+  for (int i = threadIdx.x; i < g.q_bins; i += blockDim.x) qh[i] = 0u;
+  if (threadIdx.x == 0) ssum = 0;
+  __syncthreads();
+  const int wi = blockIdx.x * blockDim.x + threadIdx.x;
+  const long long Nb = 3LL * g.N;
+  if (4 * wi < pairs) {
+    const int L = g.L;
+    const uint32_t* SA = reinterpret_cast<const uint32_t*>(A.spins[cur]);
+    const uint32_t* SB = reinterpret_cast<const uint32_t*>(B.spins[cur]);
+    const int64_t pw = g.pitch / 4;
+    int diff[4] = {0, 0, 0, 0};
+    uint32_t acc = 0;
+    int since = 0;
+    for (int n = 0; n < g.N; ++n) {
+      const int x = n % L, y = (n / L) % L, z = n / (L * L);
+      const int nx = (x + 1 == L ? 0 : x + 1) + L * (y + L * z);
+      const int ny = x + L * ((y + 1 == L ? 0 : y + 1) + L * z);
+      const int nz = x + L * (y + L * (z + 1 == L ? 0 : z + 1));
+      const uint32_t c = SA[n * pw + wi] ^ SB[n * pw + wi];
+      acc += ((c ^ SA[nx * pw + wi] ^ SB[nx * pw + wi]) & kBit1) + ((c ^ SA[ny * pw + wi] ^ SB[ny * pw + wi]) & kBit1) +
+             ((c ^ SA[nz * pw + wi] ^ SB[nz * pw + wi]) & kBit1);
+      if (++since == 40) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) diff[b] += (acc >> (8 * b + 1)) & 0x7Fu;
+        acc = 0;
+        since = 0;
+      }
+    }
+    long long local = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      diff[b] += (acc >> (8 * b + 1)) & 0x7Fu;
+      if (4 * wi + b < pairs) {
+        const long long QL = Nb - 2LL * diff[b];
+        atomicAdd(&qh[((QL + Nb) * (long long)(g.q_bins - 1) + Nb) / (2 * Nb)], 1u);
+        local += QL;
+      }
+    }
+    atomicAdd(reinterpret_cast<unsigned long long*>(&ssum), (unsigned long long)local);
+  }
+  __syncthreads();
+  unsigned long long* row = qlhist + (size_t)t * g.q_bins;
+  for (int i = threadIdx.x; i < g.q_bins; i += blockDim.x)
+    if (qh[i]) atomicAdd(&row[i], (unsigned long long)qh[i]);
+  if (threadIdx.x == 0 && ssum)
+    atomicAdd(reinterpret_cast<unsigned long long*>(&a.p[0].grec[t].ql_sum), (unsigned long long)ssum);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+
+int launch_g_energy_init(const RunGeom& g, PopDev* pops, int cur, const int32_t* Jq, void* stream) {
+  dim3 grid(blocks_for(g.pitch / 4, 128), g.n_pop);
+  k_g_energy_init<<<grid, 128, 0, (cudaStream_t)stream>>>(g, gpack(pops, g.n_pop), cur, Jq);
+  return (int)cudaGetLastError();
+}
+
+int launch_g_resample(const RunGeom& g, PopDev* pops, int cur, int t, const double* wtab, int32_t* status,
+                      void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  GArgs a = gpack(pops, g.n_pop);
+  const dim3 chunks(g.n_chunks, g.n_pop);
+  k_g_weights<<<chunks, kChunk, 0, s>>>(g, a, t, wtab);
+  k_g_chunks<<<g.n_pop, 1, 0, s>>>(g, a, t, 0);
+  k_g_tau<<<chunks, kChunk, 0, s>>>(g, a, t);
+  k_g_chunks<<<g.n_pop, 1, 0, s>>>(g, a, t, 1);
+  k_g_counts<<<dim3(g.n_count_blocks, g.n_pop), kCountThreads, 0, s>>>(g, a, t);
+  const int e = (int)cudaGetLastError();
+  return e ? e : launch_scan_scatter(g, pops, cur, t, status, stream);
+}
+
+int launch_g_measure(const RunGeom& g, PopDev* pops, int cur, int t, unsigned long long* qlhist, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  GArgs a = gpack(pops, g.n_pop);
+  if (t == 0) k_g_open<<<1, g.n_pop, 0, s>>>(a, 0);  // step 0 has no resampling to open its records
+  k_g_moments<<<dim3(g.n_measure_blocks, g.n_pop), kMeasureThreads, 0, s>>>(g, a, t);
+  k_g_finish<<<g.n_pop, 1024, 0, s>>>(g, a, t);
+  if (g.n_pop == 2) {
+    const size_t smem = sizeof(unsigned int) * (size_t)g.q_bins;
+    k_g_link<<<blocks_for(g.pitch / 4, 256), 256, smem, s>>>(g, a, cur, t, qlhist);
+  }
+  return (int)cudaGetLastError();
+}
+
+}  // namespace pa

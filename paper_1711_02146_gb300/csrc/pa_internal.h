@@ -30,6 +30,19 @@ struct StepRec {
   int32_t pad;
 };
 
+// Per-step, per-population record of the Gaussian-coupling model (energies in
+// fixed point, units of 2^-20).
+struct GRec {
+  long long E_min;                 // lowest energy of the step-t population
+  long long E0;                    // lowest energy over steps 0..t
+  long long sum_E;                 // exact sum of energies
+  unsigned long long sum_E2_lo;    // exact 128-bit sum of squared energies
+  unsigned long long sum_E2_hi;
+  long long n_at_E0;               // replicas at E0
+  long long ql_sum;                // population 0: sum over pairs of the link-overlap bond sum
+  long long pad;
+};
+
 // Device buffers of one population.
 struct PopDev {
   int8_t* spins[2];     // [N][pitch] int8 +1/-1, site-major (replicas contiguous)
@@ -45,6 +58,14 @@ struct PopDev {
   int32_t* mhist;       // [R_cap + 1] number of families of each size
   double* partials;     // [n_entropy_blocks] fixed-order partial sums of nu ln nu
   StepRec* rec;         // [n_temps]
+  // Gaussian-coupling model only (null otherwise)
+  long long* E64;       // [pitch] energies of the current population, units of 2^-20
+  double* w;            // [R_cap] resampling weights of the old population
+  double* part;         // [n_chunks] fixed-order partial sums (chunks of 256 slots)
+  int32_t* gfl;         // [R_cap] floor(tau_i)
+  uint32_t* gthr;       // [R_cap] 2^32 frac(tau_i)
+  unsigned long long* e2part;  // [2 * n_measure_blocks] 128-bit partial sums of E^2
+  GRec* grec;           // [n_temps]
   uint32_t key_met[2];
   uint32_t key_res[2];
   uint32_t key_init[2];
@@ -61,7 +82,21 @@ struct RunGeom {
   int32_t n_count_blocks;    // resampling blocks (1024 slots each)
   int32_t n_entropy_blocks;  // family-entropy reduction blocks
   int32_t sweep_shape;       // index of the sweep kernel's launch shape among those of L
+  int32_t model;             // 0: +-1 couplings, 1: Gaussian couplings (fixed point)
+  int32_t n_chunks;          // Gaussian: chunks of 256 slots of the weight sums
+  int32_t n_measure_blocks;  // Gaussian: blocks of the energy-moment reduction
 };
+
+// One entry of a site's acceptance table (Gaussian model): for one half of the
+// site's bonds and one pattern of antiparallel neighbours, the energy change of
+// that half (units of 2^-20) and its Boltzmann factor exp(-beta dE_h) in FP32.
+struct GTabEntry {
+  int32_t dE;
+  float F;
+};
+
+constexpr int kChunk = 256;            // slots per fixed-order partial sum (Gaussian weights)
+constexpr int kGTableWeights = 16384;  // doubles per step: weight tables T0 | T1 | T2
 
 // One launch shape of the sweep kernel (every shape gives identical results).
 struct SweepShapeInfo {
@@ -85,6 +120,14 @@ int launch_resample(const RunGeom& g, PopDev* pops, int cur, int t, int32_t* sta
 int launch_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, int t, int n_sweeps,
                  const uint32_t met_thr[3], void* stream);
 int launch_families(const RunGeom& g, PopDev* pops, int cur, int t, void* stream);
+// Gaussian-coupling model (pa_gauss.cu, and k_sweep_g in pa_sweep.cu)
+int launch_scan_scatter(const RunGeom& g, PopDev* pops, int cur, int t, int32_t* status, void* stream);
+int launch_g_energy_init(const RunGeom& g, PopDev* pops, int cur, const int32_t* Jq, void* stream);
+int launch_g_resample(const RunGeom& g, PopDev* pops, int cur, int t, const double* wtab, int32_t* status,
+                      void* stream);
+int launch_g_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, const int32_t* Jq, long long Jtot,
+                   const GTabEntry* gtab, int t, int n_sweeps, void* stream);
+int launch_g_measure(const RunGeom& g, PopDev* pops, int cur, int t, unsigned long long* qlhist, void* stream);
 int launch_overlap(const RunGeom& g, PopDev* pops, int cur, int t, unsigned long long* qhist, void* stream);
 // Largest lattice size the sweep kernel supports.
 constexpr int kMaxL = 16;

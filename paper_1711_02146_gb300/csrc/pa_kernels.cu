@@ -457,6 +457,14 @@ int launch_resample(const RunGeom& g, PopDev* pops, int cur, int t, int32_t* sta
   return (int)cudaGetLastError();
 }
 
+int launch_scan_scatter(const RunGeom& g, PopDev* pops, int cur, int t, int32_t* status, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  PopArgs a = pack(pops, g.n_pop);
+  k_scan_blocks<<<g.n_pop, 1024, 0, s>>>(g, a, t, status);
+  k_scatter<<<dim3(g.n_count_blocks, g.n_pop), kCountThreads, 0, s>>>(g, a, cur, t);
+  return (int)cudaGetLastError();
+}
+
 int launch_families(const RunGeom& g, PopDev* pops, int cur, int t, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   PopArgs a = pack(pops, g.n_pop);

@@ -52,6 +52,14 @@ struct pa_ctx {
   struct Timed { int phase; cudaEvent_t start, end; };
   std::vector<Timed> timed;
   std::vector<std::pair<int, int>> counted_steps;  // (t, S_t) since the last reset
+  // Gaussian-coupling model
+  int model = PA_MODEL_PM1;
+  int32_t* Jq = nullptr;                 // device [3N] fixed-point couplings
+  long long Jtot = 0;                    // sum of the couplings
+  pa::GTabEntry* gtab = nullptr;         // device [n_temps][N][16] acceptance tables
+  double* gw = nullptr;                  // device [n_temps][16384] weight tables
+  unsigned long long* qlhist = nullptr;  // device [n_temps][q_bins] link-overlap histograms
+  std::vector<int32_t> Jq_host;
 };
 
 namespace {
@@ -138,6 +146,80 @@ void metropolis_thresholds(double beta, uint32_t thr[3]) {
     if (v > 4294967295.0) v = 4294967295.0;
     thr[m - 1] = (uint32_t)v;
   }
+}
+
+// ---- Gaussian couplings (§II.A), host side: Box-Muller from Philox words at
+// counter (n, 1, 0, 0) of the couplings stream, clamped to [-5, 5], fixed point
+// Jq = round(J 2^20).  The tables below are what the device needs per step.
+
+void host_philox(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0;
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = (uint32_t)p1;
+    c[2] = n2;
+    c[3] = (uint32_t)p0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+int32_t fixed_coupling(double g) {
+  g = std::min(5.0, std::max(-5.0, g));
+  return (int32_t)std::llround(g * 1048576.0);
+}
+
+void gauss_couplings(int L, uint64_t seed, std::vector<int32_t>& Jq) {
+  const int N = L * L * L;
+  Jq.assign((size_t)3 * N, 0);
+  const uint32_t k0 = (uint32_t)(seed & 0xffffffffu);
+  const uint32_t k1 = (uint32_t)(seed >> 32) | ((uint32_t)pa::kCouplings << 28);
+  for (int n = 0; n < N; ++n) {
+    uint32_t w[4] = {(uint32_t)n, 1u, 0u, 0u};
+    host_philox(w, k0, k1);
+    const double u1 = ((double)w[0] + 0.5) * 0x1p-32, u2 = ((double)w[1] + 0.5) * 0x1p-32;
+    const double u3 = ((double)w[2] + 0.5) * 0x1p-32, u4 = ((double)w[3] + 0.5) * 0x1p-32;
+    const double ra = std::sqrt(-2.0 * std::log(u1)), rb = std::sqrt(-2.0 * std::log(u3));
+    const double ta = (2.0 * M_PI) * u2, tb = (2.0 * M_PI) * u4;
+    Jq[(size_t)3 * n + 0] = fixed_coupling(ra * std::cos(ta));
+    Jq[(size_t)3 * n + 1] = fixed_coupling(ra * std::sin(ta));
+    Jq[(size_t)3 * n + 2] = fixed_coupling(rb * std::cos(tb));
+  }
+}
+
+// Acceptance tables of one step: site n, half h (bonds x+1, x-1, y+1 | y-1,
+// z+1, z-1), pattern b (bit k set: bond k antiparallel): dE_h = 2 sum_k J_k
+// (1 - 2 b_k) and F_h = (float) exp(-beta dE_h 2^-20).
+void gauss_site_tables(const std::vector<int32_t>& Jq, int L, double beta, pa::GTabEntry* out) {
+  const int N = L * L * L;
+  for (int n = 0; n < N; ++n) {
+    const int x = n % L, y = (n / L) % L, z = n / (L * L);
+    const int xm = (x == 0 ? L - 1 : x - 1) + L * (y + L * z);
+    const int ym = x + L * ((y == 0 ? L - 1 : y - 1) + L * z);
+    const int zm = x + L * (y + L * (z == 0 ? L - 1 : z - 1));
+    const int64_t bond[2][3] = {{Jq[(size_t)3 * n + 0], Jq[(size_t)3 * xm + 0], Jq[(size_t)3 * n + 1]},
+                                {Jq[(size_t)3 * ym + 1], Jq[(size_t)3 * n + 2], Jq[(size_t)3 * zm + 2]}};
+    for (int h = 0; h < 2; ++h)
+      for (int b = 0; b < 8; ++b) {
+        int64_t dE = 0;
+        for (int k = 0; k < 3; ++k) dE += bond[h][k] * (((b >> k) & 1) ? -1 : 1);
+        dE *= 2;
+        pa::GTabEntry& e = out[(size_t)n * 16 + h * 8 + b];
+        e.dE = (int32_t)dE;
+        e.F = (float)std::exp(-(beta * ((double)dE * 0x1p-20)));
+      }
+  }
+}
+
+// Weight tables of one step: T0[m] = exp(-dbeta m 2^-20), T1[m] for m 2^12,
+// T2[m] for m 2^24 (8192 entries).
+void gauss_weight_tables(double dbeta, double* T) {
+  for (int m = 0; m < 4096; ++m) T[m] = std::exp(-(dbeta * ((double)m * 0x1p-20)));
+  for (int m = 0; m < 4096; ++m) T[4096 + m] = std::exp(-(dbeta * ((double)((int64_t)m << 12) * 0x1p-20)));
+  for (int m = 0; m < 8192; ++m) T[8192 + m] = std::exp(-(dbeta * ((double)((int64_t)m << 24) * 0x1p-20)));
 }
 
 uint64_t bits_of(double x) {
@@ -252,8 +334,12 @@ int launch_rc(int e) { return e == 0 ? PA_OK : PA_ERR_CUDA; }
 
 // Measurement kernels common to every step: families (and overlap).
 int measure(pa_ctx* c, int t) {
-  int rc;
-  {
+  int rc = PA_OK;
+  if (c->model == PA_MODEL_GAUSS) {
+    PhaseTimer pt(c, PA_PHASE_FAMILY, 3);
+    rc = launch_rc(pa::launch_g_measure(c->g, c->pops, c->cur, t, c->qlhist, c->stream));
+  }
+  if (rc == PA_OK) {
     PhaseTimer pt(c, PA_PHASE_FAMILY, 4);
     rc = launch_rc(pa::launch_families(c->g, c->pops, c->cur, t, c->stream));
   }
@@ -329,7 +415,7 @@ const char* pa_strerror(int s) {
 
 int pa_footprint(const pa_config* cfg, size_t* bytes) {
   if (!cfg || !bytes || !pa::sweep_supported(cfg->L) || cfg->R < 1 || cfg->n_temps < 1 || cfg->n_pop < 1 ||
-      cfg->n_pop > 2)
+      cfg->n_pop > 2 || cfg->model < PA_MODEL_PM1 || cfg->model > PA_MODEL_GAUSS)
     return PA_ERR_INVALID;
   const int64_t R_cap = cfg->R_cap ? cfg->R_cap : cfg->R + 10 * (int64_t)std::ceil(std::sqrt((double)cfg->R)) + 1024;
   const size_t N = (size_t)cfg->L * cfg->L * cfg->L, nlev = 3 * N + 1, T = (size_t)cfg->n_temps;
@@ -347,6 +433,11 @@ int pa_footprint(const pa_config* cfg, size_t* bytes) {
     tables = distinct.size();
   }
   b += tables * nlev * 8;
+  if (cfg->model == PA_MODEL_GAUSS) {
+    const size_t nchunk = (size_t)((R_cap + pa::kChunk - 1) / pa::kChunk), nmb = (size_t)((R_cap + 4095) / 4096);
+    b += 12 * N + T * N * sizeof(pa::GTabEntry) * 16 + T * (size_t)pa::kGTableWeights * 8 + T * (size_t)cfg->q_bins * 8;
+    b += (size_t)cfg->n_pop * (8 * pitch + 16 * (size_t)R_cap + 8 * nchunk + 16 * nmb + T * sizeof(pa::GRec));
+  }
   *bytes = b;
   return PA_OK;
 }
@@ -361,6 +452,8 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
       cfg->run_seed >= ((uint64_t)1 << 56) || cfg->q_bins < 3 || cfg->q_bins > 4097 || cfg->n_sweeps < 0)
     return PA_ERR_INVALID;
   if (!cfg->betas && !(cfg->eps_target > 0.0 && cfg->eps_target < 1.0 && cfg->beta_max > 0.0)) return PA_ERR_INVALID;
+  if (cfg->model < PA_MODEL_PM1 || cfg->model > PA_MODEL_GAUSS || (cfg->model == PA_MODEL_GAUSS && !cfg->betas))
+    return PA_ERR_INVALID;
   if (cfg->betas) {
     if (cfg->betas[0] != 0.0) return PA_ERR_INVALID;
     for (int t = 1; t < cfg->n_temps; ++t)
@@ -398,6 +491,10 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
   g.n_entropy_blocks = (int32_t)((R_cap + pa::kEntropyPerBlock - 1) / pa::kEntropyPerBlock);
   int dev = 0;
   g.sweep_shape = current_device(&dev) == PA_OK ? g_sweep_choice[dev][g.L].load() : 0;
+  g.model = cfg->model;
+  g.n_chunks = (int32_t)((R_cap + pa::kChunk - 1) / pa::kChunk);
+  g.n_measure_blocks = (int32_t)((R_cap + 4095) / 4096);
+  c->model = cfg->model;
   const size_t T = (size_t)cfg->n_temps;
 
   int rc = PA_OK;
@@ -425,6 +522,21 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
     make_key(cfg->run_seed, pa::kMetropolis, (uint32_t)p, P.key_met);
     make_key(cfg->run_seed, pa::kResample, (uint32_t)p, P.key_res);
     make_key(cfg->run_seed, pa::kInit, (uint32_t)p, P.key_init);
+    if (g.model == PA_MODEL_GAUSS) {
+      rc = rc ? rc : dalloc(c, &P.E64, (size_t)g.pitch);
+      rc = rc ? rc : dalloc(c, &P.w, (size_t)R_cap);
+      rc = rc ? rc : dalloc(c, &P.part, (size_t)g.n_chunks);
+      rc = rc ? rc : dalloc(c, &P.gfl, (size_t)R_cap);
+      rc = rc ? rc : dalloc(c, &P.gthr, (size_t)R_cap);
+      rc = rc ? rc : dalloc(c, &P.e2part, (size_t)2 * g.n_measure_blocks);
+      rc = rc ? rc : dalloc(c, &P.grec, T);
+    }
+  }
+  if (g.model == PA_MODEL_GAUSS) {
+    rc = rc ? rc : dalloc(c, &c->Jq, (size_t)3 * g.N);
+    rc = rc ? rc : dalloc(c, &c->gtab, T * (size_t)g.N * 16);
+    rc = rc ? rc : dalloc(c, &c->gw, T * (size_t)pa::kGTableWeights);
+    rc = rc ? rc : dalloc(c, &c->qlhist, T * (size_t)g.q_bins);
   }
   if (rc != PA_OK) {
     destroy(c);
@@ -438,13 +550,33 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
     if (rc == PA_OK) rc = cuda_status(cudaMemsetAsync(c->pops[p].rec, 0, sizeof(StepRec) * T, s));
   }
   if (rc == PA_OK) rc = cuda_status(cudaStreamSynchronize(s));
-  for (int t = 1; t < cfg->n_temps && rc == PA_OK && !c->adaptive; ++t) {
-    const double* w = nullptr;
-    rc = weight_table(c, c->betas[(size_t)t] - c->betas[(size_t)t - 1], &w);
+  if (g.model == PA_MODEL_GAUSS) {
+    // couplings, and the acceptance and weight tables of every step, on the host
+    gauss_couplings(g.L, cfg->disorder_seed, c->Jq_host);
+    for (int32_t v : c->Jq_host) c->Jtot += v;
+    std::vector<pa::GTabEntry> tab((size_t)g.N * 16);
+    std::vector<double> wt((size_t)pa::kGTableWeights);
+    if (rc == PA_OK) rc = copy_h2d(c, c->Jq, c->Jq_host.data(), sizeof(int32_t) * c->Jq_host.size());
+    for (int t = 1; t < cfg->n_temps && rc == PA_OK; ++t) {
+      gauss_site_tables(c->Jq_host, g.L, c->betas[(size_t)t], tab.data());
+      gauss_weight_tables(c->betas[(size_t)t] - c->betas[(size_t)t - 1], wt.data());
+      rc = copy_h2d(c, c->gtab + (size_t)t * g.N * 16, tab.data(), sizeof(pa::GTabEntry) * tab.size());
+      if (rc == PA_OK) rc = copy_h2d(c, c->gw + (size_t)t * pa::kGTableWeights, wt.data(), sizeof(double) * wt.size());
+    }
+    if (rc == PA_OK) rc = cuda_status(cudaMemsetAsync(c->J, 0, (size_t)3 * g.N, s));
+    if (rc == PA_OK) rc = cuda_status(cudaMemsetAsync(c->jtab, 0, sizeof(uint32_t) * 4 * g.N, s));
+    if (rc == PA_OK) rc = cuda_status(cudaMemsetAsync(c->qlhist, 0, sizeof(unsigned long long) * T * g.q_bins, s));
+    if (rc == PA_OK) rc = launch_rc(pa::launch_init_population(g, c->pops, 0, s));
+    if (rc == PA_OK) rc = launch_rc(pa::launch_g_energy_init(g, c->pops, 0, c->Jq, s));
+  } else {
+    for (int t = 1; t < cfg->n_temps && rc == PA_OK && !c->adaptive; ++t) {
+      const double* w = nullptr;
+      rc = weight_table(c, c->betas[(size_t)t] - c->betas[(size_t)t - 1], &w);
+    }
+    if (rc == PA_OK) rc = launch_rc(pa::launch_init_couplings(g, cfg->disorder_seed, c->J, c->jtab, s));
+    if (rc == PA_OK) rc = launch_rc(pa::launch_init_population(g, c->pops, 0, s));
+    if (rc == PA_OK) rc = launch_rc(pa::launch_levels_and_hist(g, c->pops, 0, c->jtab, 0, s));
   }
-  if (rc == PA_OK) rc = launch_rc(pa::launch_init_couplings(g, cfg->disorder_seed, c->J, c->jtab, s));
-  if (rc == PA_OK) rc = launch_rc(pa::launch_init_population(g, c->pops, 0, s));
-  if (rc == PA_OK) rc = launch_rc(pa::launch_levels_and_hist(g, c->pops, 0, c->jtab, 0, s));
   if (rc == PA_OK) rc = measure(c, 0);
   if (rc == PA_OK) rc = cuda_status(cudaStreamSynchronize(s));
   if (rc != PA_OK) {
@@ -473,25 +605,38 @@ int pa_step(pa_ctx* c) {
   } else {
     dbeta = c->betas[(size_t)t] - c->betas[(size_t)t - 1];
   }
-  const double* w = nullptr;
-  int rc = weight_table(c, dbeta, &w);
-  if (rc != PA_OK) return fail(c, rc);
-  uint32_t met[3];
-  metropolis_thresholds(c->betas[(size_t)t], met);
   cudaStream_t s = c->stream;
+  int rc = PA_OK;
   for (int p = 0; p < c->g.n_pop && rc == PA_OK; ++p)
     rc = cuda_status(cudaMemsetAsync(c->pops[p].rec + t, 0, sizeof(StepRec), s));
-  if (rc == PA_OK) {
-    PhaseTimer pt(c, PA_PHASE_REWEIGHT, 1);
-    rc = launch_rc(pa::launch_reweight(c->g, c->pops, w, t, s));
-  }
-  if (rc == PA_OK) {
-    PhaseTimer pt(c, PA_PHASE_RESAMPLE, 3);
-    rc = launch_rc(pa::launch_resample(c->g, c->pops, c->cur, t, c->status, s));
-  }
-  if (rc == PA_OK) {
-    PhaseTimer pt(c, PA_PHASE_SWEEP, 1);
-    rc = launch_rc(pa::launch_sweep(c->g, c->pops, c->cur, c->jtab, t, c->sweeps[(size_t)t], met, s));
+  if (c->model == PA_MODEL_GAUSS) {
+    if (rc == PA_OK) {
+      PhaseTimer pt(c, PA_PHASE_RESAMPLE, 7);
+      rc = launch_rc(pa::launch_g_resample(c->g, c->pops, c->cur, t, c->gw + (size_t)t * pa::kGTableWeights,
+                                           c->status, s));
+    }
+    if (rc == PA_OK) {
+      PhaseTimer pt(c, PA_PHASE_SWEEP, 1);
+      rc = launch_rc(pa::launch_g_sweep(c->g, c->pops, c->cur, c->jtab, c->Jq, c->Jtot,
+                                        c->gtab + (size_t)t * c->g.N * 16, t, c->sweeps[(size_t)t], s));
+    }
+  } else {
+    const double* w = nullptr;
+    if (rc == PA_OK) rc = weight_table(c, dbeta, &w);
+    uint32_t met[3];
+    metropolis_thresholds(c->betas[(size_t)t], met);
+    if (rc == PA_OK) {
+      PhaseTimer pt(c, PA_PHASE_REWEIGHT, 1);
+      rc = launch_rc(pa::launch_reweight(c->g, c->pops, w, t, s));
+    }
+    if (rc == PA_OK) {
+      PhaseTimer pt(c, PA_PHASE_RESAMPLE, 3);
+      rc = launch_rc(pa::launch_resample(c->g, c->pops, c->cur, t, c->status, s));
+    }
+    if (rc == PA_OK) {
+      PhaseTimer pt(c, PA_PHASE_SWEEP, 1);
+      rc = launch_rc(pa::launch_sweep(c->g, c->pops, c->cur, c->jtab, t, c->sweeps[(size_t)t], met, s));
+    }
   }
   if (rc != PA_OK) return fail(c, rc);
   c->cur = 1 - c->cur;
@@ -568,7 +713,7 @@ double pa_beta(const pa_ctx* c, int32_t t) {
 }
 
 int pa_observables(pa_ctx* c, int32_t t, int32_t pop, pa_obs* out) {
-  if (!c || !out || t < 0 || pop < 0 || pop >= c->g.n_pop) return PA_ERR_INVALID;
+  if (!c || !out || t < 0 || pop < 0 || pop >= c->g.n_pop || c->model != PA_MODEL_PM1) return PA_ERR_INVALID;
   if (t > c->t) return PA_ERR_STATE;
   int rc = pa_sync(c);
   if (rc != PA_OK) return rc;
@@ -645,7 +790,7 @@ int pa_observables(pa_ctx* c, int32_t t, int32_t pop, pa_obs* out) {
 }
 
 int pa_energy_hist(pa_ctx* c, int32_t t, int32_t pop, int64_t* out, int64_t cap) {
-  if (!c || !out || t < 0 || pop < 0 || pop >= c->g.n_pop) return PA_ERR_INVALID;
+  if (!c || !out || t < 0 || pop < 0 || pop >= c->g.n_pop || c->model != PA_MODEL_PM1) return PA_ERR_INVALID;
   if (t > c->t) return PA_ERR_STATE;
   if (cap < c->g.n_levels) return PA_ERR_CAPACITY;
   int rc = pa_sync(c);
@@ -729,6 +874,7 @@ int pa_get_replicas(pa_ctx* c, int32_t pop, int64_t first, int64_t n, int8_t* sp
     if (rc != PA_OK) return fail(c, rc);
   }
   if (energies) {
+    if (c->model != PA_MODEL_PM1) return PA_ERR_INVALID;
     rc = copy_d2h(c, energies, P.levels + first, sizeof(int32_t) * n);
     if (rc != PA_OK) return fail(c, rc);
     for (int64_t j = 0; j < n; ++j) energies[j] = 2 * energies[j] - 3 * g.N;
@@ -779,9 +925,107 @@ int pa_destroy(pa_ctx* c) {
   return PA_OK;
 }
 
+int pa_gobservables(pa_ctx* c, int32_t t, int32_t pop, pa_gobs* out) {
+  if (!c || !out || t < 0 || pop < 0 || pop >= c->g.n_pop || c->model != PA_MODEL_GAUSS) return PA_ERR_INVALID;
+  if (t > c->t) return PA_ERR_STATE;
+  int rc = pa_sync(c);
+  if (rc != PA_OK) return rc;
+  const RunGeom& g = c->g;
+  const int N = g.N;
+  std::vector<StepRec> rec((size_t)t + 1);
+  std::vector<pa::GRec> gr((size_t)t + 1);
+  rc = copy_d2h(c, rec.data(), c->pops[pop].rec, sizeof(StepRec) * rec.size());
+  if (rc == PA_OK) rc = copy_d2h(c, gr.data(), c->pops[pop].grec, sizeof(pa::GRec) * gr.size());
+  if (rc != PA_OK) return fail(c, rc);
+  // Eq. (Q) with weights measured from the lowest energy, Eq. (betaF)
+  double lnQ_sum = 0.0, lnQ = 0.0;
+  for (int u = 1; u <= t; ++u) {
+    const double db = c->betas[(size_t)u] - c->betas[(size_t)u - 1];
+    lnQ = std::log(rec[(size_t)u].S_prime / (double)rec[(size_t)u].R_prev) -
+          db * ((double)gr[(size_t)u - 1].E_min * 0x1p-20);
+    lnQ_sum = lnQ_sum + lnQ;
+  }
+  const StepRec& r = rec[(size_t)t];
+  const pa::GRec& q = gr[(size_t)t];
+  pa_gobs o{};
+  o.t = t;
+  o.beta = c->betas[(size_t)t];
+  o.dbeta = t > 0 ? c->betas[(size_t)t] - c->betas[(size_t)t - 1] : 0.0;
+  o.R_tilde = r.R_tilde;
+  o.sum_E = q.sum_E;
+  const unsigned __int128 e2 = ((unsigned __int128)q.sum_E2_hi << 64) | q.sum_E2_lo;
+  o.sum_E2 = (double)e2;
+  o.E_min = q.E_min;
+  o.mean_E = ((double)q.sum_E / (double)o.R_tilde) * 0x1p-20;
+  o.var_E = (o.sum_E2 / (double)o.R_tilde) * 0x1p-40 - o.mean_E * o.mean_E;
+  o.E_min_prev = t > 0 ? gr[(size_t)t - 1].E_min : 0;
+  o.S_prime = t > 0 ? r.S_prime : 0.0;
+  o.lnQ = t > 0 ? lnQ : 0.0;
+  o.minus_beta_F = (double)N * std::log(2.0) + lnQ_sum;
+  o.eps_expected = t > 0 ? r.eps_expected : 0.0;
+  o.culled = t > 0 ? r.culled : 0;
+  o.sum_eta2 = (int64_t)r.sum_eta2;
+  o.n_families = (int64_t)r.n_families;
+  o.rho_t = (double)o.sum_eta2 / (double)o.R_tilde;
+  o.S_f = -r.nu_ln_nu;
+  o.rho_s = (double)o.R_tilde / std::exp(o.S_f);
+  o.E0 = q.E0;
+  o.g0_tilde = (double)q.n_at_E0 / (double)o.R_tilde;
+  o.g0_bar = 2.0 * std::exp(-(o.beta * ((double)q.E0 * 0x1p-20)) - o.minus_beta_F);
+  if (g.n_pop == 2) {
+    StepRec r0;
+    pa::GRec q0;
+    rc = copy_d2h(c, &r0, c->pops[0].rec + t, sizeof r0);
+    if (rc == PA_OK) rc = copy_d2h(c, &q0, c->pops[0].grec + t, sizeof q0);
+    if (rc != PA_OK) return fail(c, rc);
+    o.q_pairs = (int64_t)r0.q_pairs;
+    o.q_abs_le_02 = (int64_t)r0.q_small;
+    o.I02 = o.q_pairs > 0 ? (double)o.q_abs_le_02 / (double)o.q_pairs : 0.0;
+    o.ql_sum = q0.ql_sum;
+    o.ql_mean = o.q_pairs > 0 ? (double)o.ql_sum / ((double)(3 * (int64_t)N) * (double)o.q_pairs) : 0.0;
+    // Eq. (el), and e_l - e of this sample (Eq. KY before the disorder average)
+    o.e_l = -(o.beta * 3.0) * (1.0 - o.ql_mean);
+    o.delta_KY = o.e_l - o.mean_E / (double)N;
+  }
+  *out = o;
+  return PA_OK;
+}
+
+int pa_get_genergies(pa_ctx* c, int32_t pop, int64_t first, int64_t n, int64_t* E) {
+  if (!c || !E || pop < 0 || pop >= c->g.n_pop || first < 0 || n < 0 || c->model != PA_MODEL_GAUSS)
+    return PA_ERR_INVALID;
+  int64_t R = 0;
+  int rc = pa_population_size(c, pop, &R);
+  if (rc != PA_OK) return rc;
+  if (first + n > R) return PA_ERR_INVALID;
+  if (n == 0) return PA_OK;
+  rc = copy_d2h(c, E, c->pops[pop].E64 + first, sizeof(int64_t) * n);
+  return rc == PA_OK ? PA_OK : fail(c, rc);
+}
+
+int pa_ql_hist(pa_ctx* c, int32_t t, int64_t* out, int64_t cap) {
+  if (!c || !out || t < 0 || c->model != PA_MODEL_GAUSS || c->g.n_pop != 2) return PA_ERR_INVALID;
+  if (t > c->t) return PA_ERR_STATE;
+  if (cap < c->g.q_bins) return PA_ERR_CAPACITY;
+  int rc = pa_sync(c);
+  if (rc != PA_OK) return rc;
+  std::vector<unsigned long long> h((size_t)c->g.q_bins);
+  rc = copy_d2h(c, h.data(), c->qlhist + (size_t)t * c->g.q_bins, sizeof(unsigned long long) * h.size());
+  if (rc != PA_OK) return fail(c, rc);
+  for (size_t i = 0; i < h.size(); ++i) out[i] = (int64_t)h[i];
+  return PA_OK;
+}
+
+int pa_get_gcouplings(pa_ctx* c, int32_t* Jq, int64_t cap) {
+  if (!c || !Jq || c->model != PA_MODEL_GAUSS) return PA_ERR_INVALID;
+  if (cap < 3 * c->g.N) return PA_ERR_CAPACITY;
+  std::memcpy(Jq, c->Jq_host.data(), sizeof(int32_t) * c->Jq_host.size());
+  return PA_OK;
+}
+
 
 int pa_checkpoint(pa_ctx* c, void* buf, size_t cap, size_t* size) {
-  if (!c || !size) return PA_ERR_INVALID;
+  if (!c || !size || c->model != PA_MODEL_PM1) return PA_ERR_INVALID;
   int rc = pa_sync(c);
   if (rc != PA_OK) return rc;
   const RunGeom& g = c->g;
@@ -864,6 +1108,7 @@ int pa_restore(const pa_config* cfg, const void* buf, size_t size, void* cuda_st
     return PA_ERR_INVALID;
   const int64_t R_cap = cfg->R_cap ? cfg->R_cap : cfg->R + 10 * (int64_t)std::ceil(std::sqrt((double)cfg->R)) + 1024;
   const bool adaptive = cfg->betas == nullptr;
+  if (cfg->model != PA_MODEL_PM1) return PA_ERR_INVALID;
   if (h.L != cfg->L || h.n_pop != cfg->n_pop || h.q_bins != cfg->q_bins || h.n_temps != cfg->n_temps ||
       h.R != cfg->R || h.R_cap != R_cap || h.disorder_seed != cfg->disorder_seed || h.run_seed != cfg->run_seed ||
       h.adaptive != (adaptive ? 1 : 0) || h.n_sweeps != cfg->n_sweeps || h.t < 0 || h.t >= h.n_temps ||

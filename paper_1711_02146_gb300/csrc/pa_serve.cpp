@@ -166,7 +166,7 @@ int pa_server_create(size_t mem_budget, int32_t max_active, int32_t steps_per_po
 }
 
 int pa_server_submit(pa_server* s, const pa_config* cfg, uint64_t* id) {
-  if (!s || !cfg || !id) return PA_ERR_INVALID;
+  if (!s || !cfg || !id || cfg->model != PA_MODEL_PM1) return PA_ERR_INVALID;  // results are pa_obs (+-1 runs)
   size_t fp = 0;
   int rc = pa_footprint(cfg, &fp);
   if (rc != PA_OK) return rc;

@@ -157,6 +157,40 @@ __device__ __forceinline__ void philox_row(uint32_t h0, const SiteRec* __restric
   }
 }
 
+// Philox blocks (rounds 3..10) of one colour site h for the two groups of a
+// word: w8[b] is word b of group 0's block (b < 4) or group 1's (b >= 4).
+__device__ __forceinline__ void philox_site(uint32_t h, const SiteRec& sr, const ThreadPhilox& tpa,
+                                            const ThreadPhilox& tpb, const uint32_t* k0, const uint32_t* k1,
+                                            uint32_t (&w8)[8]) {
+  const uint32_t uc = kM0 * h;  // lo(M0 h)
+#pragma unroll
+  for (int gi = 0; gi < 2; ++gi) {
+    const ThreadPhilox& tp = gi ? tpb : tpa;
+    uint32_t hh, l, h2, l2;
+    mulhilo(kM1, tp.tb ^ uc, hh, l);
+    mulhilo(kM0, sr.ua ^ tp.ta, h2, l2);
+    w8[4 * gi + 0] = hh ^ sr.ub;
+    w8[4 * gi + 1] = l;
+    w8[4 * gi + 2] = h2 ^ tp.tdk;
+    w8[4 * gi + 3] = l2;
+  }
+#pragma unroll
+  for (int rr = 3; rr < 10; ++rr) {
+#pragma unroll
+    for (int gi = 0; gi < 2; ++gi) {
+      uint32_t hh, l, h2, l2;
+      mulhilo(kM1, w8[4 * gi + 2], hh, l);
+      mulhilo(kM0, w8[4 * gi + 0], h2, l2);
+      const uint32_t n0 = hh ^ w8[4 * gi + 1] ^ k0[rr];
+      const uint32_t n2 = h2 ^ w8[4 * gi + 3] ^ k1[rr];
+      w8[4 * gi + 0] = n0;
+      w8[4 * gi + 1] = l;
+      w8[4 * gi + 2] = n2;
+      w8[4 * gi + 3] = l2;
+    }
+  }
+}
+
 // Metropolis update of the colour sites x = X0, X0 + 2, ... of one row from the
 // row's random words q.  The row is read in full first (own row: all L sites,
 // whose other-colour half are the x neighbours; the four neighbour rows: the
@@ -442,6 +476,151 @@ __global__ void __launch_bounds__(NT, MB) k_sweep(const __grid_constant__ SweepA
   store_tile<L, W, NP>(a, sp, tile0, word, part);
 }
 
+// ---- Gaussian couplings (§II.A): the same tiles, gather, store and Philox words;
+// the acceptance of a flip comes from per-site tables built on the host for the
+// step's beta.  For each half of a site's bonds (x+1, x-1, y+1 | y-1, z+1, z-1)
+// and each pattern of antiparallel neighbours (bit k: bond k of the half), the
+// table holds that half's energy change dE_h (fixed point, units of 2^-20) and
+// F_h = (float) exp(-beta dE_h).  A flip is taken when dE_1 + dE_2 <= 0, or
+// when the Philox word is below min(floor(2^32 F_1 F_2), 2^32 - 1) with the
+// product rounded once in FP32.  Energies are recounted from scratch after the
+// sweeps: E = -sum J + 2 sum over antiparallel bonds of J (exact integers).
+
+struct GSweepArgs {
+  SweepArgs base;
+  const GTabEntry* gtab;  // [N][2][8] acceptance tables of this step
+  const int32_t* Jq;      // [3N] fixed-point couplings of the forward bonds
+  long long Jtot;         // sum of all couplings
+};
+
+template <int L, int W, int NP, int X0>
+__device__ __forceinline__ void sweep_rows_g(uint32_t* sp, const SiteRec* recs, int part, int p,
+                                             const ThreadPhilox& tpa, const ThreadPhilox& tpb, const uint32_t* k0,
+                                             const uint32_t* k1, const GTabEntry* __restrict__ gtab) {
+  constexpr int H = L / 2, RPP = L * L / NP;
+  const int2* tab = reinterpret_cast<const int2*>(gtab);
+#pragma unroll 1
+  for (int k = 0; k < RPP; ++k) {
+    const int r = row_index<L, NP>(part, k, p);
+    const int y = r % L, z = r / L;
+    const int yp = y == L - 1 ? 0 : y + 1, ym = y == 0 ? L - 1 : y - 1;
+    const int zp = z == L - 1 ? 0 : z + 1, zm = z == 0 ? L - 1 : z - 1;
+    uint32_t* p0 = sp + (size_t)r * L * W;
+    const uint32_t* pyp = sp + (size_t)(yp + L * z) * L * W;
+    const uint32_t* pym = sp + (size_t)(ym + L * z) * L * W;
+    const uint32_t* pzp = sp + (size_t)(y + L * zp) * L * W;
+    const uint32_t* pzm = sp + (size_t)(y + L * zm) * L * W;
+    uint32_t row[L];
+#pragma unroll
+    for (int x = 0; x < L; ++x) row[x] = p0[x * W];
+#pragma unroll
+    for (int xh = 0; xh < H; ++xh) {
+      const int x = 2 * xh + X0;
+      const int xp = x == L - 1 ? 0 : x + 1;
+      const int xm = x == 0 ? L - 1 : x - 1;
+      uint32_t w8[8];
+      philox_site((uint32_t)(r * L) / 2u + (uint32_t)xh, recs[r * L + x], tpa, tpb, k0, k1, w8);
+      const uint32_t s0 = row[x];
+      const uint32_t P1 = (s0 ^ row[xp]) | ((s0 ^ row[xm]) << 1) | ((s0 ^ pyp[x * W]) << 2);
+      const uint32_t P2 = (s0 ^ pym[x * W]) | ((s0 ^ pzp[x * W]) << 1) | ((s0 ^ pzm[x * W]) << 2);
+      const int2* tb = tab + (size_t)(r * L + x) * 16;
+      uint32_t flip = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int2 e1 = __ldg(tb + ((P1 >> (4 * i)) & 7u));
+        const int2 e2 = __ldg(tb + 8 + ((P2 >> (4 * i)) & 7u));
+        const float pr = __fmul_rn(__int_as_float(e1.y), __int_as_float(e2.y));
+        const uint32_t thr = __float2uint_rz(__fmul_rn(pr, 4294967296.0f));
+        if (e1.x + e2.x <= 0 || w8[i] < thr) flip |= 1u << (4 * i);
+      }
+      p0[x * W] = s0 ^ flip;
+    }
+  }
+}
+
+// Antiparallel forward bonds of every replica of the tile weighted by J, summed into ecnt.
+template <int L, int W, int NP>
+__device__ __forceinline__ void count_energies_g(const uint32_t* sp, const int32_t* __restrict__ Jq, long long* ecnt,
+                                                 int word, int part) {
+  constexpr int ROWS = L * L;
+  int acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // |sum| < 2^31 for every launch shape in use
+  for (int r = part; r < ROWS; r += NP) {
+    const int y = r % L, z = r / L;
+    const int yp = y == L - 1 ? 0 : y + 1, zp = z == L - 1 ? 0 : z + 1;
+    const uint32_t* p0 = sp + (size_t)r * L * W + word;
+    const uint32_t* pyp = sp + (size_t)(yp + L * z) * L * W + word;
+    const uint32_t* pzp = sp + (size_t)(y + L * zp) * L * W + word;
+#pragma unroll
+    for (int x = 0; x < L; ++x) {
+      const int xp = x == L - 1 ? 0 : x + 1;
+      const int n = r * L + x;
+      const uint32_t s0 = p0[x * W];
+      const uint32_t ax = s0 ^ p0[xp * W], ay = s0 ^ pyp[x * W], az = s0 ^ pzp[x * W];
+      const int jx = __ldg(Jq + 3 * n), jy = __ldg(Jq + 3 * n + 1), jz = __ldg(Jq + 3 * n + 2);
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        acc[i] += (jx & -(int)((ax >> (4 * i)) & 1u)) + (jy & -(int)((ay >> (4 * i)) & 1u)) +
+                  (jz & -(int)((az >> (4 * i)) & 1u));
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    atomicAdd(reinterpret_cast<unsigned long long*>(&ecnt[8 * word + i]), (unsigned long long)(long long)acc[i]);
+}
+
+template <int L, int W, int NT, int MB>
+__global__ void __launch_bounds__(NT, MB) k_sweep_g(const __grid_constant__ GSweepArgs ga) {
+  using S = SweepShape<L, W, NT>;
+  constexpr int N = S::N, NP = S::NP, TJ = S::TJ;
+  const SweepArgs& a = ga.base;
+  extern __shared__ __align__(16) uint32_t sm[];
+  uint32_t* sp = sm;
+  SiteRec* recs = reinterpret_cast<SiteRec*>(sm + (size_t)N * W);
+  long long* ecnt = reinterpret_cast<long long*>(recs + N);
+  const int R_new = a.pop.rec[a.t].R_tilde;
+  const int tile0 = blockIdx.x * TJ;
+  if (tile0 >= R_new) return;
+  const int tid = threadIdx.x, word = tid % W, part = tid / W;
+  init_tables<L>(a, recs, tid, NT);
+  for (int i = tid; i < TJ; i += NT) ecnt[i] = 0;
+  gather_tile<L, W, NP>(a, sp, tile0, R_new, word, part);
+  __syncthreads();
+  const uint32_t g0 = 2u * ((uint32_t)(tile0 >> 3) + (uint32_t)word);
+  const int pclass = part / (NP / 2);
+  uint32_t* spw = sp + word;
+  for (int s = 0; s < a.n_sweeps; ++s) {
+#pragma unroll 1
+    for (int c = 0; c < 2; ++c) {
+      const uint32_t q = 2u * (uint32_t)s + (uint32_t)c;
+      const ThreadPhilox tpa = thread_philox(g0, q, a.k0, a.k1);
+      const ThreadPhilox tpb = thread_philox(g0 + 1u, q, a.k0, a.k1);
+      if ((pclass ^ c) == 0)
+        sweep_rows_g<L, W, NP, 0>(spw, recs, part, pclass, tpa, tpb, a.k0, a.k1, ga.gtab);
+      else
+        sweep_rows_g<L, W, NP, 1>(spw, recs, part, pclass, tpa, tpb, a.k0, a.k1, ga.gtab);
+      __syncthreads();
+    }
+  }
+  count_energies_g<L, W, NP>(sp, ga.Jq, ecnt, word, part);
+  __syncthreads();
+  for (int i = tid; i < TJ; i += NT) {
+    const int j = tile0 + i;
+    if (j < R_new) a.pop.E64[j] = -ga.Jtot + 2 * ecnt[i];
+  }
+  store_tile<L, W, NP>(a, sp, tile0, word, part);
+}
+
+template <int L, int W, int NT, int MB>
+static int launch_g_t(const RunGeom& g, const GSweepArgs& args, cudaStream_t s) {
+  using S = SweepShape<L, W, NT>;
+  const size_t smem = S::SMEM + (size_t)S::TJ * 4;  // energy counters are 8 bytes, not 4
+  cudaError_t e = cudaFuncSetAttribute(k_sweep_g<L, W, NT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  dim3 grid((unsigned)((g.R_cap + S::TJ - 1) / S::TJ));
+  k_sweep_g<L, W, NT, MB><<<grid, NT, smem, s>>>(args);
+  return (int)cudaGetLastError();
+}
+
 template <int L, int W, int NT, int MB>
 static int launch_t(const RunGeom& g, const SweepArgs& args, cudaStream_t s) {
   using S = SweepShape<L, W, NT>;
@@ -534,6 +713,47 @@ int launch_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, 
     args.thr8 = met_thr[1];
     args.thr12 = met_thr[2];
     const int e = shape->launch(g, args, s);
+    if (e != 0) return e;
+  }
+  return 0;
+}
+
+int launch_g_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, const int32_t* Jq, long long Jtot,
+                   const GTabEntry* gtab, int t, int n_sweeps, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int i = 0; i < g.n_pop; ++i) {
+    GSweepArgs ga;
+    SweepArgs& args = ga.base;
+    args.pop = pops[i];
+    uint32_t k0 = pops[i].key_met[0], k1 = pops[i].key_met[1];
+    for (int r = 0; r < 10; ++r) {
+      args.k0[r] = k0;
+      args.k1[r] = k1;
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    args.jtab = jtab;
+    args.pitch = g.pitch;
+    args.n_levels = g.n_levels;
+    args.t = t;
+    args.cur = cur;
+    args.n_sweeps = n_sweeps;
+    args.thr4 = args.thr8 = args.thr12 = 0u;
+    ga.gtab = gtab;
+    ga.Jq = Jq;
+    ga.Jtot = Jtot;
+    int e;
+    switch (g.L) {  // one launch shape per L, compiled for one CTA per SM (no register spills)
+      case 2: e = launch_g_t<2, 32, 128, 1>(g, ga, s); break;
+      case 4: e = launch_g_t<4, 32, 256, 1>(g, ga, s); break;
+      case 6: e = launch_g_t<6, 32, 384, 1>(g, ga, s); break;
+      case 8: e = launch_g_t<8, 32, 512, 1>(g, ga, s); break;
+      case 10: e = launch_g_t<10, 32, 640, 1>(g, ga, s); break;
+      case 12: e = launch_g_t<12, 16, 576, 1>(g, ga, s); break;
+      case 14: e = launch_g_t<14, 8, 784, 1>(g, ga, s); break;
+      case 16: e = launch_g_t<16, 4, 512, 1>(g, ga, s); break;
+      default: e = (int)cudaErrorInvalidValue;
+    }
     if (e != 0) return e;
   }
   return 0;

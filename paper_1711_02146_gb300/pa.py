@@ -43,7 +43,30 @@ class Config(ctypes.Structure):
         ("n_sweeps", ctypes.c_int32),
         ("sweeps_per_step", ctypes.POINTER(ctypes.c_int32)),
         ("q_bins", ctypes.c_int32),
+        ("model", ctypes.c_int32),
     ]
+
+
+PA_MODEL_PM1, PA_MODEL_GAUSS = 0, 1
+
+
+class GObs(ctypes.Structure):
+    """Observables of a Gaussian-coupling run (pa_gobs)."""
+    _fields_ = [
+        ("t", ctypes.c_int32), ("beta", ctypes.c_double), ("dbeta", ctypes.c_double),
+        ("R_tilde", ctypes.c_int64), ("sum_E", ctypes.c_int64), ("sum_E2", ctypes.c_double),
+        ("E_min", ctypes.c_int64), ("mean_E", ctypes.c_double), ("var_E", ctypes.c_double),
+        ("E_min_prev", ctypes.c_int64), ("S_prime", ctypes.c_double), ("lnQ", ctypes.c_double),
+        ("minus_beta_F", ctypes.c_double), ("eps_expected", ctypes.c_double), ("culled", ctypes.c_int64),
+        ("sum_eta2", ctypes.c_int64), ("n_families", ctypes.c_int64), ("rho_t", ctypes.c_double),
+        ("S_f", ctypes.c_double), ("rho_s", ctypes.c_double), ("E0", ctypes.c_int64),
+        ("g0_tilde", ctypes.c_double), ("g0_bar", ctypes.c_double), ("q_pairs", ctypes.c_int64),
+        ("q_abs_le_02", ctypes.c_int64), ("I02", ctypes.c_double), ("ql_sum", ctypes.c_int64),
+        ("ql_mean", ctypes.c_double), ("e_l", ctypes.c_double), ("delta_KY", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class Obs(ctypes.Structure):
@@ -148,6 +171,10 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_int32)]),
     "pa_server_load": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "pa_server_destroy": (ctypes.c_int, [_vp]),
+    "pa_gobservables": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(GObs)]),
+    "pa_get_genergies": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _i64p]),
+    "pa_ql_hist": (ctypes.c_int, [_vp, ctypes.c_int32, _i64p, ctypes.c_int64]),
+    "pa_get_gcouplings": (ctypes.c_int, [_vp, _i32p, ctypes.c_int64]),
     "pa_checkpoint": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "pa_restore": (ctypes.c_int, [ctypes.POINTER(Config), _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]),
     "pa_sweep_shapes": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(SweepShape), ctypes.c_int32, _i32p]),
@@ -263,7 +290,7 @@ class _ConfigHolder:
     """A pa_config plus the arrays it points to (kept alive with it)."""
 
     def __init__(self, L, R, disorder_seed, run_seed, betas=None, n_temps=0, beta_max=0.0, eps_target=0.0,
-                 n_sweeps=10, sweeps_per_step=None, n_pop=1, q_bins=65, R_cap=0):
+                 n_sweeps=10, sweeps_per_step=None, n_pop=1, q_bins=65, R_cap=0, model=0):
         self.betas = None if betas is None else np.ascontiguousarray(betas, dtype=np.float64)
         self.sweeps = None if sweeps_per_step is None else np.ascontiguousarray(sweeps_per_step, dtype=np.int32)
         c = Config()
@@ -274,13 +301,14 @@ class _ConfigHolder:
         c.beta_max, c.eps_target, c.n_sweeps = beta_max, eps_target, n_sweeps
         c.sweeps_per_step = _p(self.sweeps, ctypes.c_int32) if self.sweeps is not None else None
         c.q_bins = q_bins
+        c.model = model
         self.cfg = c
 
     @classmethod
     def from_workload(cls, w):
         return cls(w.L, w.R, w.disorder_seed, w.run_seed, w.betas, n_temps=w.n_temps, beta_max=w.beta_max,
                    eps_target=w.eps_target, n_sweeps=w.n_sweeps, sweeps_per_step=w.sweeps_per_step, n_pop=w.n_pop,
-                   q_bins=w.q_bins, R_cap=w.R_cap)
+                   q_bins=w.q_bins, R_cap=w.R_cap, model=w.model)
 
 
 def footprint(w) -> int:
@@ -319,7 +347,7 @@ class Batch:
         v = _vp()
         _check("pa_batch_ctx", lib().pa_batch_ctx(self._h, i, ctypes.byref(v)))
         w = self.workloads[i]
-        return Run._borrowed(v, self, w.L, w.n_pop, w.q_bins)
+        return Run._borrowed(v, self, w.L, w.n_pop, w.q_bins, w.model)
 
     def close(self):
         h = getattr(self, "_h", None)
@@ -384,17 +412,19 @@ class Run:
     """One population annealing run on the GPU (a ``pa_ctx``)."""
 
     @classmethod
-    def _borrowed(cls, handle, owner, L, n_pop, q_bins):
+    def _borrowed(cls, handle, owner, L, n_pop, q_bins, model=0):
         r = cls.__new__(cls)
         r._h, r._owner, r._borrowed_view = handle, owner, True
         r.L, r.N, r.n_pop, r.q_bins = L, L ** 3, n_pop, q_bins
         r.n_levels = 3 * r.N + 1
         r.n_temps = None
+        r.model = model
         return r
 
     def __init__(self, L: int, R: int, disorder_seed: int, run_seed: int, betas=None, *, n_temps: int = 0,
                  beta_max: float = 0.0, eps_target: float = 0.0, n_sweeps: int = 10, sweeps_per_step=None,
-                 n_pop: int = 1, q_bins: int = 65, R_cap: int = 0, stream=None, checkpoint: bytes = None):
+                 n_pop: int = 1, q_bins: int = 65, R_cap: int = 0, stream=None, checkpoint: bytes = None,
+                 model: int = 0):
         """Creates a run (pa_create), or, given `checkpoint` (bytes from Run.checkpoint of a
         run with this configuration), restores it (pa_restore)."""
         self.L, self.N, self.n_pop, self.q_bins = L, L ** 3, n_pop, q_bins
@@ -409,6 +439,8 @@ class Run:
         c.beta_max, c.eps_target, c.n_sweeps = beta_max, eps_target, n_sweeps
         c.sweeps_per_step = _p(self._sweeps, ctypes.c_int32) if self._sweeps is not None else None
         c.q_bins = q_bins
+        c.model = model
+        self.model = model
         self.n_temps = c.n_temps
         h = _vp()
         if checkpoint is None:
@@ -432,7 +464,7 @@ class Run:
     @classmethod
     def from_workload(cls, w, stream=None, **over):
         kw = dict(n_temps=w.n_temps, beta_max=w.beta_max, eps_target=w.eps_target, n_sweeps=w.n_sweeps,
-                  sweeps_per_step=w.sweeps_per_step, n_pop=w.n_pop, q_bins=w.q_bins, R_cap=w.R_cap)
+                  sweeps_per_step=w.sweeps_per_step, n_pop=w.n_pop, q_bins=w.q_bins, R_cap=w.R_cap, model=w.model)
         kw.update(over)
         return cls(w.L, w.R, w.disorder_seed, w.run_seed, w.betas, stream=stream, **kw)
 
@@ -517,7 +549,39 @@ class Run:
         return s, lab, E
 
     def population(self, pop: int = 0):
+        """(spins [R~, N] int8, labels int32, energies): int32 energies for +-1
+        couplings, int64 energies in units of 2^-20 for Gaussian ones."""
+        if getattr(self, "model", 0) == PA_MODEL_GAUSS:
+            n = self.size(pop)
+            s = np.zeros((n, self.N), dtype=np.int8)
+            lab = np.zeros(n, dtype=np.int32)
+            _check("pa_get_replicas", lib().pa_get_replicas(self._h, pop, 0, n, _p(s, ctypes.c_int8),
+                                                            _p(lab, ctypes.c_int32), None))
+            return s, lab, self.genergies(pop)
         return self.replicas(pop, 0, None)
+
+    # ---- Gaussian couplings
+    def gobs(self, t: int, pop: int = 0) -> dict:
+        o = GObs()
+        _check("pa_gobservables", lib().pa_gobservables(self._h, t, pop, ctypes.byref(o)))
+        return o.as_dict()
+
+    def genergies(self, pop: int = 0) -> np.ndarray:
+        n = self.size(pop)
+        E = np.zeros(max(n, 1), dtype=np.int64)
+        if n:
+            _check("pa_get_genergies", lib().pa_get_genergies(self._h, pop, 0, n, _p(E, ctypes.c_int64)))
+        return E[:n]
+
+    def ql_hist(self, t: int) -> np.ndarray:
+        out = np.zeros(self.q_bins, dtype=np.int64)
+        _check("pa_ql_hist", lib().pa_ql_hist(self._h, t, _p(out, ctypes.c_int64), out.size))
+        return out
+
+    def gcouplings(self) -> np.ndarray:
+        out = np.zeros(3 * self.N, dtype=np.int32)
+        _check("pa_get_gcouplings", lib().pa_get_gcouplings(self._h, _p(out, ctypes.c_int32), out.size))
+        return out
 
     def copy_counts(self, pop: int = 0) -> np.ndarray:
         n = ctypes.c_int64()

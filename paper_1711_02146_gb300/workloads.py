@@ -45,6 +45,7 @@ class Workload:
     n_pop: int = 1
     q_bins: int = 65
     R_cap: int = 0
+    model: int = 0                       # 0: +-1 couplings, 1: Gaussian couplings (explicit schedules)
 
     @property
     def N(self) -> int:

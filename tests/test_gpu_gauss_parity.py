@@ -1,0 +1,108 @@
+"""GPU parity of the Gaussian-coupling model (§II.A) against the oracle: couplings,
+spins, labels, energies, copy numbers, overlap and link-overlap histograms and
+every integer observable bit for bit; FP64 observables to 1e-12 relative."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-12
+INT_OBS = ("t", "R_tilde", "sum_E", "E_min", "E_min_prev", "culled", "sum_eta2", "n_families", "E0", "q_pairs",
+           "q_abs_le_02", "ql_sum")
+FLOAT_OBS = ("beta", "dbeta", "sum_E2", "mean_E", "var_E", "S_prime", "lnQ", "minus_beta_F", "eps_expected", "rho_t",
+             "S_f", "rho_s", "g0_tilde", "g0_bar", "I02", "ql_mean", "e_l", "delta_KY")
+
+
+@pytest.fixture(scope="module")
+def pa():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_02146_gb300 import build, pa as pa_mod
+    build.build()
+    return pa_mod
+
+
+def make_pair(pa, oracle_lib, L, R, betas, n_sweeps, n_pop=1, seed=1, run_seed=2):
+    gpu = pa.Run(L, R, seed, run_seed, betas, n_sweeps=n_sweeps, n_pop=n_pop, model=pa.PA_MODEL_GAUSS)
+    ref = oracle_lib.GRun(oracle_lib.RunConfig(L=L, R=R, disorder_seed=seed, run_seed=run_seed, betas=betas,
+                                               n_sweeps=n_sweeps, n_pop=n_pop))
+    return gpu, ref
+
+
+def assert_obs(g, r, ctx):
+    for k in INT_OBS:
+        assert g[k] == r[k], f"{ctx} {k}: gpu {g[k]} oracle {r[k]}"
+    for k in FLOAT_OBS:
+        a, b = g[k], r[k]
+        if a == b:
+            continue
+        assert abs(a - b) <= REL * max(abs(a), abs(b)) + 1e-300, f"{ctx} {k}: gpu {a!r} oracle {b!r}"
+
+
+def assert_state(gpu, ref, n_pop, ctx):
+    for p in range(n_pop):
+        s, lab, E = gpu.population(p)
+        rs, rlab, rE = ref.population(p)
+        assert s.shape == rs.shape, f"{ctx} pop {p}: size {s.shape[0]} vs {rs.shape[0]}"
+        assert np.array_equal(lab, rlab), f"{ctx} pop {p}: labels"
+        assert np.array_equal(E, rE), f"{ctx} pop {p}: energies"
+        bad = np.nonzero(np.any(s != rs, axis=1))[0]
+        assert bad.size == 0, f"{ctx} pop {p}: {bad.size} replicas differ, first {bad[:5]}"
+
+
+@pytest.mark.parametrize("L,R", [(2, 77), (4, 700), (6, 555), (8, 1333), (10, 515), (12, 300), (14, 129), (16, 65)])
+def test_stepwise_bit_exact(pa, oracle_lib, L, R):
+    betas = np.linspace(0.0, 2.5, 5)
+    gpu, ref = make_pair(pa, oracle_lib, L, R, betas, 2, seed=L, run_seed=50 + R)
+    assert np.array_equal(gpu.gcouplings(), ref.couplings())
+    assert_state(gpu, ref, 1, "t=0")
+    assert_obs(gpu.gobs(0), ref.obs(0), "t=0")
+    for t in range(1, len(betas)):
+        assert gpu.step() == 0
+        ref.step()
+        assert np.array_equal(gpu.copy_counts(), ref.last_counts()), f"copy numbers at t={t}"
+        assert_state(gpu, ref, 1, f"t={t}")
+        assert_obs(gpu.gobs(t), ref.obs(t), f"t={t}")
+    assert gpu.step() == pa.PA_DONE
+
+
+def test_two_populations_overlaps(pa, oracle_lib):
+    betas = np.linspace(0.0, 3.0, 9)
+    gpu, ref = make_pair(pa, oracle_lib, 6, 900, betas, 3, n_pop=2, seed=3, run_seed=4)
+    for t in range(len(betas)):
+        if t:
+            gpu.step()
+            ref.step()
+        for p in range(2):
+            assert_obs(gpu.gobs(t, p), ref.obs(t, p), f"t={t} pop {p}")
+        assert np.array_equal(gpu.q_hist(t), ref.q_hist(t)), f"q histogram at t={t}"
+        assert np.array_equal(gpu.ql_hist(t), ref.q_hist(t, link=True)), f"q_l histogram at t={t}"
+    assert_state(gpu, ref, 2, "end")
+
+
+def test_longer_run_and_sweep_schedule(pa, oracle_lib):
+    betas = np.linspace(0.0, 3.0, 21)
+    sweeps = np.array([0] + [3] * 6 + [7] * 8 + [1] * 6, dtype=np.int32)
+    gpu = pa.Run(8, 3000, 9, 10, betas, sweeps_per_step=sweeps, model=pa.PA_MODEL_GAUSS)
+    ref = oracle_lib.GRun(oracle_lib.RunConfig(L=8, R=3000, disorder_seed=9, run_seed=10, betas=betas,
+                                               sweeps_per_step=sweeps))
+    gpu.run()
+    ref.run()
+    for t in (1, 10, 20):
+        assert_obs(gpu.gobs(t), ref.obs(t), f"t={t}")
+    assert_state(gpu, ref, 1, "end")
+
+
+def test_gaussian_runs_refuse_the_pm1_readers_and_adaptive_schedules(pa):
+    run = pa.Run(4, 100, 1, 1, np.linspace(0, 1, 3), model=pa.PA_MODEL_GAUSS)
+    for call in (lambda: run.obs(0), lambda: run.energy_hist(0), lambda: run.checkpoint(),
+                 lambda: run.replicas(0, 0, 5)):
+        with pytest.raises(pa.PAError) as e:
+            call()
+        assert e.value.status == pa.PA_ERR_INVALID
+    with pytest.raises(pa.PAError):
+        pa.Run(4, 100, 1, 1, None, n_temps=10, beta_max=2.0, eps_target=0.3, model=pa.PA_MODEL_GAUSS)
+    pm1 = pa.Run(4, 100, 1, 1, np.linspace(0, 1, 3))
+    with pytest.raises(pa.PAError):
+        pm1.gobs(0)
