@@ -71,6 +71,11 @@ def parse():
     ap.add_argument("--probe", action="store_true", help="also run the integer-throughput probes")
     ap.add_argument("--batched-runs", type=int, default=64,
                     help="runs of the batched mix (256 in the full workload; 0 = skip)")
+    ap.add_argument("--gaussian-steps", type=int, default=6,
+                    help="timed steps of the Gaussian-coupling workload (0 = skip)")
+    ap.add_argument("--gaussian-R", type=int, default=0, help="override its population size (profiling runs)")
+    ap.add_argument("--gaussian-only", action="store_true",
+                    help="time only the Gaussian-coupling workload (profiling runs; prints its object)")
     ap.add_argument("--served-requests", type=int, default=128,
                     help="requests of the serving stream (2000 in the full workload; 0 = skip)")
     return ap.parse_args()
@@ -358,6 +363,68 @@ def autotune_shapes(pa, sizes):
     return out
 
 
+def gaussian_workload():
+    """The paper's model (Gaussian couplings) at the headline size: L = 10,
+    R = 1e6, 101 linear temperatures to beta = 5, 10 sweeps per step."""
+    from paper_1711_02146_gb300.workloads import Workload, linear_betas
+    return Workload("L10_R1e6_gauss_linear101", L=10, R=1_000_000, disorder_seed=3, run_seed=1003,
+                    betas=linear_betas(101, 5.0), n_sweeps=10, model=1)
+
+
+def gaussian_measurement(pa, steps: int, warmup: int, peak: float, cpu: bool, R: int = 0):
+    """Whole-step and sweep-kernel updates/s of the Gaussian-coupling model, and
+    the Gaussian oracle timed on a sample of the same run."""
+    import torch
+    w = gaussian_workload()
+    if R:
+        w = w.with_(R=R, name=f"{w.name}_R{R}")
+    stream = torch.cuda.Stream()
+    run = pa.Run.from_workload(w, stream=stream)
+    for _ in range(warmup):
+        run.step()
+    run.sync()
+    run.stats_reset(timing=True)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    done = 0
+    for _ in range(steps):
+        if run.step() != 0:
+            break
+        done += 1
+    end.record(stream)
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(end)
+    st = run.stats()
+    o = run.gobs(run.t)
+    run.close()
+    sweep_ms = st["phase_ms"]["sweep"] / max(st["phase_count"]["sweep"], 1)
+    per_launch = st["updates"] / max(st["phase_count"]["sweep"], 1)
+    achieved = per_launch / (sweep_ms / 1e3) / 1e9
+    out = {"workload": w.name, "steps_timed": f"temperature steps {warmup + 1}..{warmup + done}",
+           "value": st["updates"] / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / max(done, 1),
+           "sweep": {"achieved": achieved, "peak": peak, "unit": "Gupdates/s", "frac": achieved / peak,
+                     "launch_ms": sweep_ms, "kernel": "k_sweep_g<10,32,640,1>"},
+           "phase_share": {k: v / max(ms, 1e-9) for k, v in st["phase_ms"].items()},
+           "last_step": {"beta": o["beta"], "R_tilde": o["R_tilde"], "mean_E_per_spin": o["mean_E"] / w.N,
+                         "rho_t": o["rho_t"]}}
+    if cpu:
+        import oracle
+        oracle.build()
+        cores = os.cpu_count() or 1
+        ref = oracle.GRun(oracle.RunConfig(L=w.L, R=20000, disorder_seed=w.disorder_seed, run_seed=w.run_seed,
+                                           betas=w.betas, n_sweeps=w.n_sweeps, n_threads=cores))
+        updates, n, t0 = 0, 0, time.perf_counter()
+        while n < 5 and time.perf_counter() - t0 < 10.0:
+            ref.step()
+            n += 1
+            updates += w.n_sweeps * w.N * ref.obs(ref.t)["R_tilde"]
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": updates / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"first {n} temperature steps of the same run with R=2e4 ({dt:.1f} s)"}
+    return out
+
+
 def measured_hbm_gbs():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -379,6 +446,12 @@ def ours(args):
     from paper_1711_02146_gb300 import build, pa
     from paper_1711_02146_gb300.workloads import C3
     build.build()
+    if args.gaussian_only:
+        n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+        peak = n_sm * (WIDE_MULS_PER_CLK_PER_SM / WIDE_MULS_PER_UPDATE) * 2070.0 * 1e6 / 1e9
+        print(json.dumps(gaussian_measurement(pa, args.gaussian_steps, args.warmup, peak, cpu=False,
+                                              R=args.gaussian_R)), flush=True)
+        return
     w = C3.with_(run_seed=C3.run_seed + 7919 * rank)
     if args.R:
         w = w.with_(R=args.R, name=f"{C3.name}_R{args.R}")
@@ -478,6 +551,9 @@ def ours(args):
     if rank == 0 and args.served_requests > 0:
         free, _ = torch.cuda.mem_get_info()
         line["served"] = served_vs_serial(pa, args.served_requests, int(0.5 * free))
+    if rank == 0 and args.gaussian_steps > 0:
+        line["gaussian"] = gaussian_measurement(pa, args.gaussian_steps, args.warmup, peak,
+                                                cpu=world == 1 and not args.no_cpu_baseline, R=args.gaussian_R)
     if args.probe:
         line["int_probes_per_s"] = {k: pa.int_throughput(k) for k in pa.PROBES}
 

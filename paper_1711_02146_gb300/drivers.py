@@ -9,6 +9,8 @@ free_energy_variance  rho_f from M independent runs of one disorder realization
 hardness_adaptive_population
                       the population-size scheme of §IV.A: run with R0; while
                       R <= 100 rho_t(R), rerun with R = 150 rho_t(R).
+katzgraber_young      Delta_KY(beta) = [e_l - e]_J over Gaussian disorder
+                      realizations (Eqs. KY, el), two populations per sample.
 schedule_comparison   §V.A: rho_t at beta = 5 under the unoptimized schedule
                       (dbeta = 0.05, 10 sweeps per step) and the optimized one
                       (constant culling fraction, 3/22/1 sweeps by temperature
@@ -167,3 +169,31 @@ def schedule_comparison(L: int, R: int, disorder_seeds, beta_max: float = 5.0, d
             "ratio_of_means": float(rho[:, 0].mean() / rho[:, 1].mean()),
             "eps": eps, "n_steps_opt": len(b_op), "n_steps_unopt": n,
             "sweeps_opt": int(s_op.sum()), "sweeps_unopt": int(s_un.sum())}
+
+
+# ---------------------------------------------------------------- Katzgraber-Young measure (§II.A)
+
+def katzgraber_young(L: int, R: int, disorder_seeds, betas, n_sweeps: int = 10, run_seed: int = 1):
+    """Delta_KY(beta) = [e_l - e]_J (Eqs. KY, el) over Gaussian disorder
+    realizations: every sample runs two independent populations (model 1) as
+    one batch; returns per step the disorder averages of e, e_l and their
+    difference with its standard error."""
+    from .workloads import Workload
+    seeds = list(disorder_seeds)
+    ws = [Workload(f"ky_{d}", L=L, R=R, disorder_seed=d, run_seed=run_seed, betas=np.asarray(betas, np.float64),
+                   n_sweeps=n_sweeps, n_pop=2, model=1) for d in seeds]
+    batch = pa.Batch(ws)
+    batch.run()
+    T = len(betas)
+    e = np.zeros((len(seeds), T))
+    el = np.zeros((len(seeds), T))
+    for i in range(len(ws)):
+        v = batch.run_view(i)
+        for t in range(T):
+            o = v.gobs(t, 0)
+            e[i, t] = o["mean_E"] / (L ** 3)
+            el[i, t] = o["e_l"]
+    batch.close()
+    d = el - e
+    return {"beta": np.asarray(betas, np.float64), "e": e.mean(axis=0), "e_l": el.mean(axis=0),
+            "delta_KY": d.mean(axis=0), "delta_KY_err": d.std(axis=0, ddof=1) / math.sqrt(len(seeds))}

@@ -56,3 +56,12 @@ def test_optimized_schedule_beats_constant_steps(drivers):
     assert abs(r["sweeps_opt"] - r["sweeps_unopt"]) <= 0.03 * r["sweeps_unopt"]
     assert r["n_steps_opt"] > 10
     assert r["geo_mean_ratio"] > 1.0
+
+
+def test_katzgraber_young_vanishes_in_equilibrium(drivers):
+    # Gaussian couplings, high temperatures, well-equilibrated populations:
+    # the disorder average [e_l - e] is zero within its error (Eq. KY)
+    r = drivers.katzgraber_young(4, 3000, range(1, 25), np.linspace(0.0, 1.2, 13), n_sweeps=5)
+    for t in range(1, 13):
+        assert abs(r["delta_KY"][t]) < 4 * r["delta_KY_err"][t] + 0.01, (t, r["delta_KY"][t], r["delta_KY_err"][t])
+    assert r["e"][12] < r["e"][1] < 0
