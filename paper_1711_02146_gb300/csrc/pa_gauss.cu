@@ -119,17 +119,28 @@ __global__ void __launch_bounds__(kChunk) k_g_weights(RunGeom g, GArgs a, int t,
   }
 }
 
-// The chunk totals one after another (one thread), into S' (which = 0) or the
-// expected culling fraction (which = 1, divided by R).
-__global__ void k_g_chunks(RunGeom g, GArgs a, int t, int which) {
+// The chunk totals one after another, into S' (which = 0) or the expected
+// culling fraction (which = 1, divided by R).  The block stages the partials in
+// shared memory, 4096 at a time, and one thread adds them in order.
+__global__ void __launch_bounds__(1024) k_g_chunks(RunGeom g, GArgs a, int t, int which) {
+  __shared__ double buf[4096];
   PopDev& P = a.p[blockIdx.x];
   const int n = blocks_for(P.rec[t - 1].R_tilde, kChunk);
   double total = 0.0;
-  for (int c = 0; c < n; ++c) total = __dadd_rn(total, P.part[c]);
-  if (which == 0)
-    P.rec[t].S_prime = total;
-  else
-    P.rec[t].eps_expected = __ddiv_rn(total, (double)g.R);
+  for (int c0 = 0; c0 < n; c0 += 4096) {
+    const int m = min(4096, n - c0);
+    for (int k = threadIdx.x; k < m; k += blockDim.x) buf[k] = P.part[c0 + k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int k = 0; k < m; ++k) total = __dadd_rn(total, buf[k]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (which == 0)
+      P.rec[t].S_prime = total;
+    else
+      P.rec[t].eps_expected = __ddiv_rn(total, (double)g.R);
+  }
 }
 
 // tau_i = R w_i / S', its floor and 2^32-scaled fraction, and the chunk partial
@@ -247,30 +258,34 @@ __global__ void __launch_bounds__(kMeasureThreads) k_g_moments(RunGeom g, GArgs 
   }
 }
 
-// One block per population: the exact sum of E^2, E0 = min(E0 of t-1, E_min of
-// t), and the number of replicas at E0.
+// One thread per population: the exact sum of E^2 and E0 = min(E0 of t-1, E_min of t).
 __global__ void k_g_finish(RunGeom g, GArgs a, int t) {
-  __shared__ long long cnt[32];
-  PopDev& P = a.p[blockIdx.x];
+  PopDev& P = a.p[threadIdx.x];
   const int R = P.rec[t].R_tilde;
   GRec& r = P.grec[t];
-  const long long E0 = (t == 0 || r.E_min < P.grec[t - 1].E0) ? r.E_min : P.grec[t - 1].E0;
+  unsigned __int128 s2 = 0;
+  for (int b = 0; b < blocks_for(R, kMeasurePerBlock); ++b)
+    s2 += ((unsigned __int128)P.e2part[2 * b + 1] << 64) | P.e2part[2 * b];
+  r.sum_E2_lo = (unsigned long long)s2;
+  r.sum_E2_hi = (unsigned long long)(s2 >> 64);
+  r.E0 = (t == 0 || r.E_min < P.grec[t - 1].E0) ? r.E_min : P.grec[t - 1].E0;
+  r.n_at_E0 = 0;
+}
+
+// Replicas at E0.
+__global__ void __launch_bounds__(kMeasureThreads) k_g_count_E0(RunGeom g, GArgs a, int t) {
+  PopDev& P = a.p[blockIdx.y];
+  const int R = P.rec[t].R_tilde;
+  const long long E0 = P.grec[t].E0;
+  const int base = blockIdx.x * kMeasurePerBlock;
   long long c = 0;
-  for (int j = threadIdx.x; j < R; j += blockDim.x) c += P.E64[j] == E0;
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-  if ((threadIdx.x & 31) == 0) cnt[threadIdx.x >> 5] = c;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    long long tot = 0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += cnt[k];
-    unsigned __int128 s2 = 0;
-    for (int b = 0; b < blocks_for(R, kMeasurePerBlock); ++b)
-      s2 += ((unsigned __int128)P.e2part[2 * b + 1] << 64) | P.e2part[2 * b];
-    r.sum_E2_lo = (unsigned long long)s2;
-    r.sum_E2_hi = (unsigned long long)(s2 >> 64);
-    r.E0 = E0;
-    r.n_at_E0 = tot;
+  for (int k = threadIdx.x; k < kMeasurePerBlock; k += kMeasureThreads) {
+    const int j = base + k;
+    if (j < R) c += P.E64[j] == E0;
   }
+  c = warp_sum(c);
+  if ((threadIdx.x & 31) == 0 && c)
+    atomicAdd(reinterpret_cast<unsigned long long*>(&P.grec[t].n_at_E0), (unsigned long long)c);
 }
 
 // Link overlap (Eq. ql) between slot j of the two populations, four pairs per
@@ -346,9 +361,9 @@ int launch_g_resample(const RunGeom& g, PopDev* pops, int cur, int t, const doub
   GArgs a = gpack(pops, g.n_pop);
   const dim3 chunks(g.n_chunks, g.n_pop);
   k_g_weights<<<chunks, kChunk, 0, s>>>(g, a, t, wtab);
-  k_g_chunks<<<g.n_pop, 1, 0, s>>>(g, a, t, 0);
+  k_g_chunks<<<g.n_pop, 1024, 0, s>>>(g, a, t, 0);
   k_g_tau<<<chunks, kChunk, 0, s>>>(g, a, t);
-  k_g_chunks<<<g.n_pop, 1, 0, s>>>(g, a, t, 1);
+  k_g_chunks<<<g.n_pop, 1024, 0, s>>>(g, a, t, 1);
   k_g_counts<<<dim3(g.n_count_blocks, g.n_pop), kCountThreads, 0, s>>>(g, a, t);
   const int e = (int)cudaGetLastError();
   return e ? e : launch_scan_scatter(g, pops, cur, t, status, stream);
@@ -359,7 +374,8 @@ int launch_g_measure(const RunGeom& g, PopDev* pops, int cur, int t, unsigned lo
   GArgs a = gpack(pops, g.n_pop);
   if (t == 0) k_g_open<<<1, g.n_pop, 0, s>>>(a, 0);  // step 0 has no resampling to open its records
   k_g_moments<<<dim3(g.n_measure_blocks, g.n_pop), kMeasureThreads, 0, s>>>(g, a, t);
-  k_g_finish<<<g.n_pop, 1024, 0, s>>>(g, a, t);
+  k_g_finish<<<1, g.n_pop, 0, s>>>(g, a, t);
+  k_g_count_E0<<<dim3(g.n_measure_blocks, g.n_pop), kMeasureThreads, 0, s>>>(g, a, t);
   if (g.n_pop == 2) {
     const size_t smem = sizeof(unsigned int) * (size_t)g.q_bins;
     k_g_link<<<blocks_for(g.pitch / 4, 256), 256, smem, s>>>(g, a, cur, t, qlhist);

@@ -24,6 +24,7 @@ static PopArgs pack(const PopDev* pops, int n_pop) {
 }
 
 constexpr uint32_t kBit1 = 0x02020202u;
+constexpr int kScatterOwn = 16;  // copies a thread writes alone; larger families are written by the warp
 
 // ---------------------------------------------------------------- init (a0)
 
@@ -262,14 +263,35 @@ __global__ void __launch_bounds__(kCountThreads) k_scatter(RunGeom g, PopArgs a,
   long long off = (long long)block_exclusive_scan(local, scratch, nullptr) + P.blocksums[blockIdx.x];
   const int32_t* lab_old = P.labels[cur];
   int32_t* lab_new = P.labels[1 - cur];
+  const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
     const int i = i0 + b;
-    for (int q = 0; q < n[b]; ++q) {
-      const long long j = off + q;
-      if (j < g.R_cap) {
-        P.parents[j] = i;
-        lab_new[j] = lab_old[i];
+    // a slot with few copies writes them itself; the copies of a large family are
+    // written by the whole warp, one such slot at a time
+    const bool big = n[b] > kScatterOwn;
+    if (!big)
+      for (int q = 0; q < n[b]; ++q) {
+        const long long j = off + q;
+        if (j < g.R_cap) {
+          P.parents[j] = i;
+          lab_new[j] = lab_old[i];
+        }
+      }
+    unsigned int pending = __ballot_sync(0xffffffffu, big);
+    while (pending) {
+      const int src = __ffs(pending) - 1;
+      pending &= pending - 1;
+      const long long o = __shfl_sync(0xffffffffu, off, src);
+      const int cnt = __shfl_sync(0xffffffffu, n[b], src);
+      const int ii = __shfl_sync(0xffffffffu, i, src);
+      const int32_t lab = lab_old[ii];
+      for (int q = lane; q < cnt; q += 32) {
+        const long long j = o + q;
+        if (j < g.R_cap) {
+          P.parents[j] = ii;
+          lab_new[j] = lab;
+        }
       }
     }
     off += n[b];

@@ -106,3 +106,53 @@ def test_gaussian_runs_refuse_the_pm1_readers_and_adaptive_schedules(pa):
     pm1 = pa.Run(4, 100, 1, 1, np.linspace(0, 1, 3))
     with pytest.raises(pa.PAError):
         pm1.gobs(0)
+
+
+def test_full_size_sampled_steps(pa, oracle_lib):
+    """L = 10, R = 1e6 with Gaussian couplings (the benchmark's Gaussian workload),
+    two steps in the benchmark's launch configuration: the resampling is recomputed
+    from the GPU's energies with the oracle's definitions (weights, fixed-order sums,
+    copy numbers), and sampled replicas are swept again by the oracle from their parents."""
+    import bench
+    w = bench.gaussian_workload()
+    gpu = pa.Run.from_workload(w)
+    L, N, R = w.L, w.N, w.R
+    Jq = gpu.gcouplings()
+    assert np.array_equal(Jq, oracle_lib.gcouplings(L, w.disorder_seed))
+    rng = np.random.default_rng(0)
+    for _ in range(2):
+        s_old, lab_old, E_old = gpu.population()
+        for j in rng.integers(0, len(E_old), 16):
+            assert oracle_lib.genergy(L, Jq, s_old[j]) == E_old[j]
+        gpu.step()
+        t = gpu.t
+        o = gpu.gobs(t)
+        # resampling, from the oracle's definitions on the GPU's energies
+        T = oracle_lib.gweight_tables(o["dbeta"])
+        d = E_old - E_old.min()
+        wts = (T[8192 + (d >> 24)] * T[4096 + ((d >> 12) & 4095)]) * T[d & 4095]
+        for i in rng.integers(0, len(E_old), 200):
+            assert oracle_lib.gweight(T, int(d[i])) == wts[i]
+        S = oracle_lib.tree_sum(wts)
+        assert o["S_prime"] == S and o["E_min_prev"] == int(E_old.min())
+        tau = (float(R) * wts) / S
+        assert o["eps_expected"] == oracle_lib.tree_sum(np.where(tau < 1.0, 1.0 - tau, 0.0)) / float(R)
+        fl = np.floor(tau)
+        thr = ((tau - fl) * 4294967296.0).astype(np.uint32)
+        counts = gpu.copy_counts()
+        assert counts.size == len(E_old)
+        for i in rng.integers(0, len(E_old), 4000):
+            assert counts[i] == oracle_lib.copy_count(w.run_seed, 0, t, int(i), int(fl[i]), int(thr[i]))
+        parents = gpu.parents()
+        assert parents.size == counts.sum() == o["R_tilde"]
+        assert np.array_equal(parents, np.repeat(np.arange(len(E_old), dtype=np.int32), counts))
+        s_new, lab_new, E_new = gpu.population()
+        assert np.array_equal(lab_new, lab_old[parents])
+        for j in rng.integers(0, len(E_new), 24):
+            ref, dE = oracle_lib.gsweep_replica(L, Jq, s_old[parents[j]], w.run_seed, 0, int(j), t, w.n_sweeps,
+                                                gpu.beta(t))
+            assert np.array_equal(s_new[j], ref), f"slot {j}"
+            assert E_new[j] == E_old[parents[j]] + dE
+        # exact moments of the new population
+        assert o["sum_E"] == int(E_new.sum()) and o["E_min"] == int(E_new.min())
+        assert o["sum_E2"] == float(sum(int(e) * int(e) for e in E_new.tolist()))
