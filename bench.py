@@ -69,14 +69,14 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--R", type=int, default=0, help="override the population size (profiling runs)")
     ap.add_argument("--probe", action="store_true", help="also run the integer-throughput probes")
-    ap.add_argument("--batched-runs", type=int, default=64,
+    ap.add_argument("--batched-runs", type=int, default=256,
                     help="runs of the batched mix (256 in the full workload; 0 = skip)")
     ap.add_argument("--gaussian-steps", type=int, default=6,
                     help="timed steps of the Gaussian-coupling workload (0 = skip)")
     ap.add_argument("--gaussian-R", type=int, default=0, help="override its population size (profiling runs)")
     ap.add_argument("--gaussian-only", action="store_true",
                     help="time only the Gaussian-coupling workload (profiling runs; prints its object)")
-    ap.add_argument("--served-requests", type=int, default=128,
+    ap.add_argument("--served-requests", type=int, default=256,
                     help="requests of the serving stream (2000 in the full workload; 0 = skip)")
     return ap.parse_args()
 
@@ -346,6 +346,8 @@ def served_vs_serial(pa, n_req: int, mem_budget: int):
             "serial_p50_latency_s": float(np.percentile(slat, 50)),
             "serial_p99_latency_s": float(np.percentile(slat, 99)),
             "throughput_vs_serial": (len(ws) / span) / (len(ws) / sum(service)),
+            "capacity_vs_serial": capacity / (len(ws) / sum(service)),
+            "p50_latency_serial_over_served": float(np.percentile(slat, 50) / np.percentile(lat, 50)),
             "mem_budget_bytes": mem_budget}
 
 

@@ -127,3 +127,27 @@ def test_server_rejects_requests_beyond_the_budget(pa):
         server.submit(C1)
     assert e.value.status == pa.PA_ERR_NOMEM
     server.close()
+
+
+def test_batch_mixes_models(pa):
+    """Gaussian and +-1 runs in one batch give exactly their standalone results."""
+    ws = [Workload("pm", L=6, R=900, disorder_seed=3, run_seed=4, betas=linear_betas(6, 2.0), n_sweeps=2),
+          Workload("ga", L=8, R=700, disorder_seed=5, run_seed=6, betas=linear_betas(7, 2.5), n_sweeps=2, model=1),
+          Workload("ga2", L=4, R=1500, disorder_seed=7, run_seed=8, betas=linear_betas(5, 1.5), n_sweeps=3,
+                   n_pop=2, model=1)]
+    batch = pa.Batch(ws)
+    batch.run()
+    for i, w in enumerate(ws):
+        a, b = batch.run_view(i), standalone(pa, w)
+        if w.model == 0:
+            assert_same_run(a, b, w)
+            continue
+        t = a.t
+        assert b.t == t
+        for pop in range(w.n_pop):
+            assert a.gobs(t, pop) == b.gobs(t, pop)
+            for x, y in zip(a.population(pop), b.population(pop)):
+                assert np.array_equal(x, y)
+        if w.n_pop == 2:
+            assert np.array_equal(a.ql_hist(t), b.ql_hist(t))
+    batch.close()
