@@ -7,6 +7,7 @@
 // and the estimators of §II.A / §III.A.  Compile with -ffp-contract=off so that
 // every expression rounds as written.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -102,11 +103,20 @@ cudaEvent_t next_event(pa_ctx* c) {
 }
 
 // Records CUDA events on the run's stream around one phase when timing is on.
+// NVTX range for profilers (no cost unless a tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
+const char* const kPhaseNames[PA_N_PHASES] = {"reweight", "resample", "sweep", "family", "overlap"};
+
 struct PhaseTimer {
   pa_ctx* c;
   int phase;
   cudaEvent_t start = nullptr;
-  PhaseTimer(pa_ctx* ctx, int ph, int launches) : c(ctx), phase(ph) {
+  NvtxRange range;
+  PhaseTimer(pa_ctx* ctx, int ph, int launches) : c(ctx), phase(ph), range(kPhaseNames[ph]) {
     c->stats.kernel_launches += launches;
     if (c->timing && (start = next_event(c)) != nullptr) cudaEventRecord(start, c->stream);
   }
@@ -591,6 +601,7 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
 
 int pa_step(pa_ctx* c) {
   if (!c) return PA_ERR_INVALID;
+  NvtxRange range("pa_step");
   if (c->error != PA_OK) return c->error;
   if (c->done) return PA_DONE;
   const int t = c->t + 1;
