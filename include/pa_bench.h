@@ -12,6 +12,11 @@
  *   PA_BENCH_IMAD      mad.lo.u32                               1 op
  *   PA_BENCH_MULWIDE   mul.wide.u32 + lop3 (fold hi into lo)    2 ops
  *   PA_BENCH_PHILOX    one Philox4x32-10 block (4 words)        counted as 4 words
+ *   PA_BENCH_MULWIDE_ADD  mul.wide.u32 + add.u32 (hi + lo)      2 ops
+ *   PA_BENCH_LOP3_IADD    lop3.b32 + add.u32                    2 ops
+ * The pairs tell how the issue of a wide multiply (or a 3-input logic op) and a
+ * full-rate add share one scheduler: with no sharing a pair costs the slower of
+ * the two, with full sharing the sum.
  * On return *ms is the device time (CUDA events, after one warm-up launch) and
  * *ops the number of operations (words for PA_BENCH_PHILOX) executed.  Runs on
  * the current device, legacy default stream; allocates and frees a small
@@ -29,6 +34,8 @@ extern "C" {
 #define PA_BENCH_IMAD 2
 #define PA_BENCH_MULWIDE 3
 #define PA_BENCH_PHILOX 4
+#define PA_BENCH_MULWIDE_ADD 5
+#define PA_BENCH_LOP3_IADD 6
 
 int pa_bench_int_throughput(int kind, int64_t iters, int blocks, int threads, double* ms, double* ops);
 

@@ -30,6 +30,12 @@ __device__ __forceinline__ uint32_t mulwide_fold(uint32_t a, uint32_t m) {
   return lop3_xor(lo, hi, a);
 }
 
+__device__ __forceinline__ uint32_t mulwide_add(uint32_t a, uint32_t m) {
+  uint64_t p;
+  asm volatile("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(a), "r"(m));
+  return add_u32((uint32_t)p, (uint32_t)(p >> 32));
+}
+
 template <int KIND>
 __global__ void k_probe(int64_t iters, uint32_t seed, uint32_t* out) {
   const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -53,6 +59,8 @@ __global__ void k_probe(int64_t iters, uint32_t seed, uint32_t* out) {
       if (KIND == PA_BENCH_IADD) x[i] = add_u32(x[i], b);
       if (KIND == PA_BENCH_IMAD) x[i] = mad_lo(x[i], b, c);
       if (KIND == PA_BENCH_MULWIDE) x[i] = mulwide_fold(x[i], b);
+      if (KIND == PA_BENCH_MULWIDE_ADD) x[i] = mulwide_add(x[i], b);
+      if (KIND == PA_BENCH_LOP3_IADD) x[i] = add_u32(lop3_xor(x[i], b, c), c);
     }
   }
   uint32_t acc = 0;
@@ -93,6 +101,8 @@ extern "C" int pa_bench_int_throughput(int kind, int64_t iters, int blocks, int 
     case PA_BENCH_IMAD: *ops = 8 * n; return run_probe<PA_BENCH_IMAD>(iters, blocks, threads, ms);
     case PA_BENCH_MULWIDE: *ops = 16 * n; return run_probe<PA_BENCH_MULWIDE>(iters, blocks, threads, ms);
     case PA_BENCH_PHILOX: *ops = 4 * n; return run_probe<PA_BENCH_PHILOX>(iters, blocks, threads, ms);
+    case PA_BENCH_MULWIDE_ADD: *ops = 16 * n; return run_probe<PA_BENCH_MULWIDE_ADD>(iters, blocks, threads, ms);
+    case PA_BENCH_LOP3_IADD: *ops = 16 * n; return run_probe<PA_BENCH_LOP3_IADD>(iters, blocks, threads, ms);
     default: return PA_ERR_INVALID;
   }
 }
