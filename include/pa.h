@@ -49,7 +49,10 @@ extern "C" {
 #define PA_ERR_EXTINCT (-7)  /* every replica received zero copies */
 
 /* ---- configuration of one run (§II; schedule §IV.B) ----
- * L            lattice size; even, 2 <= L <= 16.
+ * L            lattice size; even, 2 <= L <= 64 (up to 16 a CTA holds a tile of
+ *              replicas in shared memory for all sweeps of a step; beyond, the
+ *              sweeps run in global memory, one launch per half-sweep; Gaussian
+ *              couplings up to 16).
  * n_pop        1, or 2 independent populations on the same couplings (for q).
  * R            target population size, 1 <= R.
  * R_cap        hard capacity of the population arrays (0 = R + 10 ceil(sqrt R) + 1024);

@@ -19,8 +19,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpa.so")
 OBJDIR = os.path.join(HERE, "_build")
-SOURCES = ["pa_kernels.cu", "pa_sweep.cu", "pa_gauss.cu", "pa_microbench.cu", "pa_noalloc.cu", "pa_runtime.cpp",
-           "pa_serve.cpp"]
+SOURCES = ["pa_kernels.cu", "pa_sweep.cu", "pa_sweep_global.cu", "pa_gauss.cu", "pa_microbench.cu", "pa_noalloc.cu",
+           "pa_runtime.cpp", "pa_serve.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

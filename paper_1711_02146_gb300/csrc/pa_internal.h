@@ -131,6 +131,13 @@ int launch_g_measure(const RunGeom& g, PopDev* pops, int cur, int t, unsigned lo
 int launch_overlap(const RunGeom& g, PopDev* pops, int cur, int t, unsigned long long* qhist, void* stream);
 // Largest lattice size the sweep kernel supports.
 constexpr int kMaxL = 16;
-bool sweep_supported(int L);
+// Largest lattice size of a run (larger lattices than kMaxL sweep in global memory).
+constexpr int kMaxLGlobal = 64;
+bool sweep_supported(int L);        // shared-memory sweep kernels (even L <= kMaxL)
+bool lattice_supported(int L);      // every lattice a run accepts (even L <= kMaxLGlobal)
+// Global-memory sweep for kMaxL < L <= kMaxLGlobal (pa_sweep_global.cu): replica copy,
+// S half-sweep launches in place, energy levels.
+int launch_sweep_global(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, int t, int n_sweeps,
+                        const uint32_t met_thr[3], void* stream);
 
 }  // namespace pa

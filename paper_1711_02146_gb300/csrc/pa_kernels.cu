@@ -124,11 +124,14 @@ __global__ void k_levels_and_hist(RunGeom g, PopArgs a, int cur, const uint32_t*
 //   tau_k = R w[k - kmin] / S'  ->  fl_k = floor(tau_k), thr_k = 2^32 (tau_k - fl_k)
 //   eps = (1/R) sum_k c(k) (1 - tau_k)_+          (Eq. eq_num_elim; fixed tree order)
 // Empty levels add exact zeros to S', so they are skipped there.
-__global__ void k_reweight(RunGeom g, PopArgs a, const double* __restrict__ w, int t) {
-  extern __shared__ int lst[];  // n_levels entries: occupied levels, ascending
+__global__ void k_reweight(RunGeom g, PopArgs a, const double* __restrict__ w, int t, int list_in_smem) {
+  extern __shared__ int lst_sh[];  // n_levels entries: occupied levels, ascending
   __shared__ int scratch[33];
   __shared__ double S_sh;
   const PopDev& P = a.p[blockIdx.x];
+  // the list lives in shared memory when it fits; otherwise in the floor table,
+  // which is only written (below) after the list has been read
+  int* lst = list_in_smem ? lst_sh : P.fl;
   const uint32_t* c = P.hist + (size_t)(t - 1) * g.n_levels;
   int base = 0;
   for (int k0 = 0; k0 < g.n_levels; k0 += blockDim.x) {
@@ -460,12 +463,13 @@ int launch_levels_and_hist(const RunGeom& g, PopDev* pops, int cur, const uint32
 }
 
 int launch_reweight(const RunGeom& g, PopDev* pops, const double* w, int t, void* stream) {
-  const size_t smem = sizeof(int) * (size_t)g.n_levels;
+  const bool in_smem = g.n_levels <= 3 * kMaxL * kMaxL * kMaxL + 1;  // every lattice of the shared-memory sweep
+  const size_t smem = in_smem ? sizeof(int) * (size_t)g.n_levels : 0;
   if (smem > 48 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(k_reweight, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
   }
-  k_reweight<<<g.n_pop, 1024, smem, (cudaStream_t)stream>>>(g, pack(pops, g.n_pop), w, t);
+  k_reweight<<<g.n_pop, 1024, smem, (cudaStream_t)stream>>>(g, pack(pops, g.n_pop), w, t, in_smem ? 1 : 0);
   return (int)cudaGetLastError();
 }
 

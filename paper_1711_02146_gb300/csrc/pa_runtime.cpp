@@ -424,7 +424,7 @@ const char* pa_strerror(int s) {
 }
 
 int pa_footprint(const pa_config* cfg, size_t* bytes) {
-  if (!cfg || !bytes || !pa::sweep_supported(cfg->L) || cfg->R < 1 || cfg->n_temps < 1 || cfg->n_pop < 1 ||
+  if (!cfg || !bytes || !pa::lattice_supported(cfg->L) || cfg->R < 1 || cfg->n_temps < 1 || cfg->n_pop < 1 ||
       cfg->n_pop > 2 || cfg->model < PA_MODEL_PM1 || cfg->model > PA_MODEL_GAUSS)
     return PA_ERR_INVALID;
   const int64_t R_cap = cfg->R_cap ? cfg->R_cap : cfg->R + 10 * (int64_t)std::ceil(std::sqrt((double)cfg->R)) + 1024;
@@ -457,12 +457,13 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
   *out = nullptr;
   if (!cfg) return PA_ERR_INVALID;
   const int64_t R_cap = cfg->R_cap ? cfg->R_cap : cfg->R + 10 * (int64_t)std::ceil(std::sqrt((double)cfg->R)) + 1024;
-  if (!pa::sweep_supported(cfg->L) || cfg->R < 1 || cfg->n_pop < 1 || cfg->n_pop > 2 || cfg->n_temps < 1 ||
+  if (!pa::lattice_supported(cfg->L) || cfg->R < 1 || cfg->n_pop < 1 || cfg->n_pop > 2 || cfg->n_temps < 1 ||
       R_cap < cfg->R || R_cap >= ((int64_t)1 << 31) - 4096 || cfg->disorder_seed >= ((uint64_t)1 << 56) ||
       cfg->run_seed >= ((uint64_t)1 << 56) || cfg->q_bins < 3 || cfg->q_bins > 4097 || cfg->n_sweeps < 0)
     return PA_ERR_INVALID;
   if (!cfg->betas && !(cfg->eps_target > 0.0 && cfg->eps_target < 1.0 && cfg->beta_max > 0.0)) return PA_ERR_INVALID;
-  if (cfg->model < PA_MODEL_PM1 || cfg->model > PA_MODEL_GAUSS || (cfg->model == PA_MODEL_GAUSS && !cfg->betas))
+  if (cfg->model < PA_MODEL_PM1 || cfg->model > PA_MODEL_GAUSS ||
+      (cfg->model == PA_MODEL_GAUSS && (!cfg->betas || !pa::sweep_supported(cfg->L))))
     return PA_ERR_INVALID;
   if (cfg->betas) {
     if (cfg->betas[0] != 0.0) return PA_ERR_INVALID;
@@ -500,7 +501,7 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
   g.n_count_blocks = (int32_t)((R_cap + pa::kSlotsPerCountBlock - 1) / pa::kSlotsPerCountBlock);
   g.n_entropy_blocks = (int32_t)((R_cap + pa::kEntropyPerBlock - 1) / pa::kEntropyPerBlock);
   int dev = 0;
-  g.sweep_shape = current_device(&dev) == PA_OK ? g_sweep_choice[dev][g.L].load() : 0;
+  g.sweep_shape = (pa::sweep_supported(g.L) && current_device(&dev) == PA_OK) ? g_sweep_choice[dev][g.L].load() : 0;
   g.model = cfg->model;
   g.n_chunks = (int32_t)((R_cap + pa::kChunk - 1) / pa::kChunk);
   g.n_measure_blocks = (int32_t)((R_cap + 4095) / 4096);
@@ -644,9 +645,12 @@ int pa_step(pa_ctx* c) {
       PhaseTimer pt(c, PA_PHASE_RESAMPLE, 3);
       rc = launch_rc(pa::launch_resample(c->g, c->pops, c->cur, t, c->status, s));
     }
-    if (rc == PA_OK) {
+    if (rc == PA_OK && pa::sweep_supported(c->g.L)) {
       PhaseTimer pt(c, PA_PHASE_SWEEP, 1);
       rc = launch_rc(pa::launch_sweep(c->g, c->pops, c->cur, c->jtab, t, c->sweeps[(size_t)t], met, s));
+    } else if (rc == PA_OK) {  // lattices beyond a shared-memory tile: sweeps in global memory
+      PhaseTimer pt(c, PA_PHASE_SWEEP, c->g.n_pop * (1 + 2 * c->sweeps[(size_t)t]) + 1);
+      rc = launch_rc(pa::launch_sweep_global(c->g, c->pops, c->cur, c->jtab, t, c->sweeps[(size_t)t], met, s));
     }
   }
   if (rc != PA_OK) return fail(c, rc);

@@ -88,6 +88,35 @@ def test_stepwise_bit_exact(pa, oracle_lib, L, R, T, S):
     assert gpu.step() == 1  # PA_DONE
 
 
+@pytest.mark.parametrize("L,R", [(18, 61), (24, 40), (32, 21), (64, 8)])
+def test_large_lattices_sweep_in_global_memory(pa, oracle_lib, L, R):
+    """16 < L <= 64: the replica copy and the half-sweeps run in global memory, the
+    reweighting keeps its level list in global memory; results are the oracle's."""
+    betas = linear(3, 1.5)
+    gpu, ref = make_pair(pa, oracle_lib, L, R, betas, n_sweeps=2, disorder_seed=L, run_seed=7 + R, n_pop=2)
+    assert np.array_equal(gpu.couplings(), ref.couplings())
+    for t in range(1, 3):
+        assert gpu.step() == 0
+        ref.step()
+        assert np.array_equal(gpu.copy_counts(), ref.last_counts()), f"copy numbers at t={t}"
+        assert_state_equal(gpu, ref, 2, f"t={t}")
+        for p in range(2):
+            assert np.array_equal(gpu.energy_hist(t, p), ref.energy_hist(t, p)), f"energy histogram at t={t}"
+            assert_obs_equal(gpu.obs(t, p), ref.obs(t, p), f"t={t} pop {p}")
+        assert np.array_equal(gpu.q_hist(t), ref.q_hist(t))
+    with pytest.raises(pa.PAError):
+        pa.sweep_shapes(L)
+
+
+def test_lattices_beyond_64_are_rejected(pa):
+    for L in (66, 65, 17):
+        with pytest.raises(pa.PAError) as e:
+            pa.Run(L, 10, 1, 1, linear(3, 1.0))
+        assert e.value.status == pa.PA_ERR_INVALID
+    with pytest.raises(pa.PAError):   # Gaussian couplings stay within the shared-memory sweep
+        pa.Run(18, 10, 1, 1, linear(3, 1.0), model=pa.PA_MODEL_GAUSS)
+
+
 def test_c1_full_run(pa, oracle_lib):
     from paper_1711_02146_gb300.workloads import C1
     gpu = pa.Run.from_workload(C1)
