@@ -76,7 +76,7 @@ def parse():
     ap.add_argument("--gaussian-R", type=int, default=0, help="override its population size (profiling runs)")
     ap.add_argument("--gaussian-only", action="store_true",
                     help="time only the Gaussian-coupling workload (profiling runs; prints its object)")
-    ap.add_argument("--served-requests", type=int, default=256,
+    ap.add_argument("--served-requests", type=int, default=2000,
                     help="requests of the serving stream (2000 in the full workload; 0 = skip)")
     return ap.parse_args()
 
@@ -461,9 +461,9 @@ def ours(args):
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
     sizes = {w.L}
-    if rank == 0 and args.batched_runs > 0:
+    if rank == 0 and world == 1 and args.batched_runs > 0:
         sizes |= {4, 6, 8, 10}
-    if rank == 0 and args.served_requests > 0:
+    if rank == 0 and world == 1 and args.served_requests > 0:
         sizes |= {4, 6, 8, 10, 12}
     tuned = None if args.no_autotune else autotune_shapes(pa, sizes)
     shape = pa.sweep_shapes(w.L)[pa.sweep_selected(w.L)]
@@ -548,12 +548,13 @@ def ours(args):
             "roofline": roofline, "e2e": e2e, "gpu_launches": st["kernel_launches"],
             "phase_share": phase_share, "clocks": clk}
     run.close()
-    if rank == 0 and args.batched_runs > 0:
+    # the many-run workloads and the Gaussian model are single-GPU measurements
+    if rank == 0 and world == 1 and args.batched_runs > 0:
         line["batched"] = batched_vs_serial(pa, args.batched_runs)
-    if rank == 0 and args.served_requests > 0:
+    if rank == 0 and world == 1 and args.served_requests > 0:
         free, _ = torch.cuda.mem_get_info()
         line["served"] = served_vs_serial(pa, args.served_requests, int(0.5 * free))
-    if rank == 0 and args.gaussian_steps > 0:
+    if rank == 0 and world == 1 and args.gaussian_steps > 0:
         line["gaussian"] = gaussian_measurement(pa, args.gaussian_steps, args.warmup, peak,
                                                 cpu=world == 1 and not args.no_cpu_baseline, R=args.gaussian_R)
     if args.probe:
