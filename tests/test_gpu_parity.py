@@ -234,3 +234,32 @@ def test_full_size_sampled_step(pa, oracle_lib):
             assert np.array_equal(s_new[j], ref), f"slot {j}"
             assert E_new[j] == E_old[parents[j]] + dE
         assert np.array_equal(np.bincount((E_new + 3 * N) // 2, minlength=3 * N + 1), gpu.energy_hist(t))
+
+
+def test_c2_full_size_two_populations(pa, oracle_lib):
+    """L = 8, R = 1e5, two populations (the overlap workload) at full size: the whole
+    q histogram and I(0.2) recomputed from both GPU populations, and sampled replicas
+    of population 1 swept again by the oracle (population index in the random key)."""
+    from paper_1711_02146_gb300.workloads import C2
+    gpu = pa.Run.from_workload(C2)
+    L, N = C2.L, C2.N
+    J = gpu.couplings()
+    rng = np.random.default_rng(1)
+    for _ in range(2):
+        s_old, _, E_old = gpu.population(1)
+        gpu.step()
+        t = gpu.t
+        A, B = gpu.population(0)[0], gpu.population(1)[0]
+        pairs = min(A.shape[0], B.shape[0])
+        Q = (A[:pairs].astype(np.int32) * B[:pairs].astype(np.int32)).sum(axis=1).astype(np.int64)
+        bins = ((Q + N) * (C2.q_bins - 1) + N) // (2 * N)
+        assert np.array_equal(np.bincount(bins, minlength=C2.q_bins), gpu.q_hist(t))
+        o = gpu.obs(t, 0)
+        assert o["q_pairs"] == pairs and o["q_abs_le_02"] == int((5 * np.abs(Q) <= N).sum())
+        parents = gpu.parents(1)
+        s_new, _, E_new = gpu.population(1)
+        met = oracle_lib.metropolis_thresholds(gpu.beta(t))
+        for j in rng.integers(0, len(E_new), 16):
+            ref, dE = oracle_lib.sweep_replica(L, J, s_old[parents[j]], C2.run_seed, 1, int(j), t, C2.n_sweeps, met)
+            assert np.array_equal(s_new[j], ref), f"pop 1 slot {j}"
+            assert E_new[j] == E_old[parents[j]] + dE
