@@ -186,7 +186,7 @@ def test_invalid_configurations_rejected(pa):
     with pytest.raises(pa.PAError):
         pa.Run(5, 10, 1, 1, linear(3, 1.0))            # odd L
     with pytest.raises(pa.PAError):
-        pa.Run(18, 10, 1, 1, linear(3, 1.0))           # beyond the largest supported L
+        pa.Run(66, 10, 1, 1, linear(3, 1.0))           # beyond the largest supported L (64)
     with pytest.raises(pa.PAError):
         pa.Run(4, 10, 1 << 56, 1, linear(3, 1.0))      # seed too large
     with pytest.raises(pa.PAError):
