@@ -456,22 +456,21 @@ def tree_sum(x: np.ndarray) -> float:
 
 
 class GRun:
-    """One oracle PA run with Gaussian couplings (explicit schedule)."""
+    """One oracle PA run with Gaussian couplings (explicit or adaptive schedule)."""
 
     def __init__(self, cfg: RunConfig):
-        if cfg.betas is None:
-            raise ValueError("Gaussian runs take an explicit schedule")
         self.cfg = cfg
         self.L, self.N = cfg.L, cfg.L ** 3
-        self._betas = np.ascontiguousarray(cfg.betas, dtype=np.float64)
+        self._betas = None if cfg.betas is None else np.ascontiguousarray(cfg.betas, dtype=np.float64)
         self._sweeps = (None if cfg.sweeps_per_step is None
                         else np.ascontiguousarray(cfg.sweeps_per_step, dtype=np.int32))
         c = Config()
         c.L, c.R = cfg.L, cfg.R
         c.R_cap = cfg.R_cap or default_capacity(cfg.R)
         c.disorder_seed, c.run_seed = cfg.disorder_seed, cfg.run_seed
-        c.n_pop, c.n_temps = cfg.n_pop, len(self._betas)
-        c.betas = _p(self._betas, ctypes.c_double)
+        c.n_pop, c.n_temps = cfg.n_pop, (len(self._betas) if self._betas is not None else cfg.n_temps)
+        c.betas = _p(self._betas, ctypes.c_double) if self._betas is not None else None
+        c.beta_max, c.eps_target = cfg.beta_max, cfg.eps_target
         c.n_sweeps = cfg.n_sweeps
         c.sweeps_per_step = _p(self._sweeps, ctypes.c_int32) if self._sweeps is not None else None
         c.q_bins, c.n_threads = cfg.q_bins, cfg.n_threads

@@ -125,7 +125,7 @@ void or_destroy(or_run* run);
 
 /* ---- Gaussian couplings (the paper's model, §II.A): pa_oracle_gauss.c ----
  * Couplings J ~ N(0,1) clamped to [-5, 5] in fixed point Jq = round(J 2^20);
- * energies in the same units (int64).  Explicit schedules, even L. */
+ * energies in the same units (int64).  Explicit or adaptive schedules, even L. */
 #define ORG_T2_SIZE 8192   /* entries of the coarsest weight table */
 
 typedef struct {

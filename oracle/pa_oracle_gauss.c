@@ -18,7 +18,9 @@
  *     T_k[m] = exp(-dbeta m 2^(12k) 2^-20), d = (E - E_min) in fixed point;
  *   - S' and the culling sum are taken in a fixed order: chunks of 256 slots,
  *     each by a binary tree (a[i] += a[i + h], h = 128, 64, ..., 1), and the
- *     chunk totals one after another.
+ *     chunk totals one after another;
+ *   - the adaptive schedule (§IV.B) bisects on the culling fraction computed
+ *     with exactly these weights and sums.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -318,12 +320,16 @@ static void free_g(org_run* r) {
 int org_create(const or_config* cfg, org_run** out) {
   *out = NULL;
   if (!cfg || cfg->L < 2 || cfg->L % 2 != 0 || cfg->R < 1 || cfg->n_temps < 1 || cfg->n_pop < 1 || cfg->n_pop > 2 ||
-      cfg->q_bins < 3 || !cfg->betas || cfg->disorder_seed >= ((uint64_t)1 << 56) ||
+      cfg->q_bins < 3 || cfg->disorder_seed >= ((uint64_t)1 << 56) ||
       cfg->run_seed >= ((uint64_t)1 << 56) || cfg->R_cap < cfg->R || cfg->R_cap >= ((int64_t)1 << 31))
     return OR_ERR_INVALID;
-  if (cfg->betas[0] != 0.0) return OR_ERR_INVALID;
-  for (int32_t t = 1; t < cfg->n_temps; ++t)
-    if (!(cfg->betas[t] >= cfg->betas[t - 1])) return OR_ERR_INVALID;
+  if (!cfg->betas && !(cfg->eps_target > 0.0 && cfg->eps_target < 1.0 && cfg->beta_max > 0.0))
+    return OR_ERR_INVALID;
+  if (cfg->betas) {
+    if (cfg->betas[0] != 0.0) return OR_ERR_INVALID;
+    for (int32_t t = 1; t < cfg->n_temps; ++t)
+      if (!(cfg->betas[t] >= cfg->betas[t - 1])) return OR_ERR_INVALID;
+  }
   org_run* r = (org_run*)calloc(1, sizeof(org_run));
   if (!r) return OR_ERR_NOMEM;
   r->cfg = *cfg;
@@ -341,10 +347,10 @@ int org_create(const or_config* cfg, org_run** out) {
     return OR_ERR_NOMEM;
   }
   for (int32_t t = 0; t < T; ++t) {
-    r->betas[t] = cfg->betas[t];
+    r->betas[t] = cfg->betas ? cfg->betas[t] : 0.0;
     r->sweeps[t] = cfg->sweeps_per_step ? cfg->sweeps_per_step[t] : cfg->n_sweeps;
   }
-  r->cfg.betas = r->betas;
+  r->cfg.betas = cfg->betas ? r->betas : NULL; /* non-NULL marks an explicit schedule */
   r->cfg.sweeps_per_step = NULL;
   org_couplings(r->L, cfg->disorder_seed, r->Jq);
   for (int32_t p = 0; p < cfg->n_pop; ++p) {
@@ -380,15 +386,72 @@ int org_create(const or_config* cfg, org_run** out) {
     free_g(r);
     return rc;
   }
-  r->done = T == 1;
+  r->done = T == 1 || (!cfg->betas && cfg->beta_max <= 0.0);
   *out = r;
+  return OR_OK;
+}
+
+/* Expected culling fraction (Eq. eq_num_elim / R) of a move by dbeta from the
+ * population p, with this file's weights and summation order. */
+static double eps_g(const org_run* r, const org_pop* P, double dbeta, double* T, double* w) {
+  const int64_t* E = P->E[P->cur];
+  int64_t Emin = INT64_MAX;
+  for (int64_t i = 0; i < P->Rt; ++i)
+    if (E[i] < Emin) Emin = E[i];
+  org_weight_tables(dbeta, T);
+  for (int64_t i = 0; i < P->Rt; ++i) w[i] = org_weight(T, E[i] - Emin);
+  double S = org_tree_sum(w, P->Rt);
+  for (int64_t i = 0; i < P->Rt; ++i) {
+    double tau = ((double)r->cfg.R * w[i]) / S;
+    w[i] = tau < 1.0 ? 1.0 - tau : 0.0;
+  }
+  return org_tree_sum(w, P->Rt) / (double)r->cfg.R;
+}
+
+/* Adaptive step (§IV.B), as for +-1 couplings: the largest dbeta in
+ * (0, beta_max - beta] whose culling fraction does not exceed the target, by 64
+ * bisection halvings; population 0 decides. */
+static int choose_dbeta_g(const org_run* r, int32_t t, double* dbeta) {
+  const org_pop* P = &r->pops[0];
+  double* T = (double*)malloc(sizeof(double) * (8192 + ORG_T2_SIZE));
+  double* w = (double*)malloc(sizeof(double) * (size_t)(P->Rt > 0 ? P->Rt : 1));
+  if (!T || !w) {
+    free(T);
+    free(w);
+    return OR_ERR_NOMEM;
+  }
+  double rem = r->cfg.beta_max - r->betas[t - 1];
+  if (eps_g(r, P, rem, T, w) <= r->cfg.eps_target) {
+    *dbeta = rem;
+  } else {
+    double lo = 0.0, hi = rem;
+    for (int it = 0; it < 64; ++it) {
+      double mid = 0.5 * (lo + hi);
+      if (eps_g(r, P, mid, T, w) <= r->cfg.eps_target)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    *dbeta = lo > 0.0 ? lo : hi;
+  }
+  free(T);
+  free(w);
   return OR_OK;
 }
 
 int org_step(org_run* r) {
   if (r->done) return OR_DONE;
   int32_t t = r->t + 1, N = r->N;
-  double dbeta = r->betas[t] - r->betas[t - 1];
+  double dbeta;
+  if (r->cfg.betas) {
+    dbeta = r->betas[t] - r->betas[t - 1];
+  } else {
+    int rc = choose_dbeta_g(r, t, &dbeta);
+    if (rc != OR_OK) return rc;
+    double b = r->betas[t - 1] + dbeta;
+    if (b >= r->cfg.beta_max || dbeta == r->cfg.beta_max - r->betas[t - 1]) b = r->cfg.beta_max;
+    r->betas[t] = b;
+  }
   double* T = (double*)malloc(sizeof(double) * (8192 + ORG_T2_SIZE));
   if (!T) return OR_ERR_NOMEM;
   org_weight_tables(dbeta, T);
@@ -471,7 +534,7 @@ int org_step(org_run* r) {
   int rc = measure_g(r, t);
   if (rc != OR_OK) return rc;
   r->t = t;
-  if (t == r->cfg.n_temps - 1) r->done = 1;
+  if (t == r->cfg.n_temps - 1 || (!r->cfg.betas && r->betas[t] >= r->cfg.beta_max)) r->done = 1;
   return OR_OK;
 }
 

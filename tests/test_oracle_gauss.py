@@ -212,3 +212,25 @@ def test_run_is_independent_of_thread_count():
         outs.append((r.population(0), r.obs(r.t, 0)))
     (a, oa), (b, ob) = outs
     assert all(np.array_equal(x, y) for x, y in zip(a, b)) and oa == ob
+
+
+def test_adaptive_schedule_holds_the_culling_fraction():
+    """§IV.B with Gaussian couplings: every step but the last has the largest dbeta
+    whose expected culling fraction does not exceed the target; the run ends at
+    beta_max; the free energy still follows the exact one (L = 2)."""
+    eps, bmax = 0.25, 2.0
+    run = oracle.GRun(oracle.RunConfig(L=2, R=20000, disorder_seed=5, run_seed=6, betas=None, n_temps=400,
+                                       beta_max=bmax, eps_target=eps, n_sweeps=3))
+    run.run()
+    T = run.t
+    betas = [run.obs(t)["beta"] for t in range(T + 1)]
+    assert betas[-1] == bmax and all(b2 > b1 for b1, b2 in zip(betas, betas[1:]))
+    for t in range(1, T + 1):
+        e = run.obs(t)["eps_expected"]
+        assert e <= eps
+        if t < T:
+            assert e >= eps * (1 - 1e-9)
+    J = run.couplings().astype(np.float64) * SCALE
+    for t in (T // 2, T):
+        lnZ, _, _, _, _ = _exact_l2(J, betas[t])
+        assert abs(run.obs(t)["minus_beta_F"] - lnZ) < 0.02
