@@ -369,6 +369,19 @@ int launch_g_resample(const RunGeom& g, PopDev* pops, int cur, int t, const doub
   return e ? e : launch_scan_scatter(g, pops, cur, t, status, stream);
 }
 
+int launch_g_eps_trial(const RunGeom& g, PopDev* pops, int t, const double* wtab, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  RunGeom g1 = g;  // population 0 decides the step
+  g1.n_pop = 1;
+  GArgs a = gpack(pops, 1);
+  const dim3 chunks(g1.n_chunks, 1);
+  k_g_weights<<<chunks, kChunk, 0, s>>>(g1, a, t, wtab);
+  k_g_chunks<<<1, 1024, 0, s>>>(g1, a, t, 0);
+  k_g_tau<<<chunks, kChunk, 0, s>>>(g1, a, t);
+  k_g_chunks<<<1, 1024, 0, s>>>(g1, a, t, 1);
+  return (int)cudaGetLastError();
+}
+
 int launch_g_measure(const RunGeom& g, PopDev* pops, int cur, int t, unsigned long long* qlhist, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   GArgs a = gpack(pops, g.n_pop);

@@ -127,6 +127,10 @@ int launch_g_resample(const RunGeom& g, PopDev* pops, int cur, int t, const doub
                       void* stream);
 int launch_g_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, const int32_t* Jq, long long Jtot,
                    const GTabEntry* gtab, int t, int n_sweeps, void* stream);
+// The expected culling fraction of population 0 for the weight tables wtab, into
+// rec[t].eps_expected (also overwrites the step-t weights, sums and tables, which the
+// resampling recomputes): one evaluation of the adaptive bisection.
+int launch_g_eps_trial(const RunGeom& g, PopDev* pops, int t, const double* wtab, void* stream);
 int launch_g_measure(const RunGeom& g, PopDev* pops, int cur, int t, unsigned long long* qlhist, void* stream);
 int launch_overlap(const RunGeom& g, PopDev* pops, int cur, int t, unsigned long long* qhist, void* stream);
 // Largest lattice size the sweep kernel supports.

@@ -322,6 +322,42 @@ int choose_dbeta(pa_ctx* c, double* dbeta) {
   return PA_OK;
 }
 
+// Adaptive step for Gaussian couplings: the same bisection, with the culling
+// fraction of each trial computed on the device from that trial's weight tables
+// (the definitions the resampling uses), population 0 deciding.
+int gauss_eps(pa_ctx* c, int t, double dbeta, double* eps) {
+  std::vector<double> wt((size_t)pa::kGTableWeights);
+  gauss_weight_tables(dbeta, wt.data());
+  int rc = copy_h2d(c, c->gw, wt.data(), sizeof(double) * wt.size());
+  if (rc == PA_OK) rc = pa::launch_g_eps_trial(c->g, c->pops, t, c->gw, c->stream) == 0 ? PA_OK : PA_ERR_CUDA;
+  if (rc == PA_OK) rc = copy_d2h(c, eps, &c->pops[0].rec[t].eps_expected, sizeof(double));
+  return rc;
+}
+
+int choose_dbeta_gauss(pa_ctx* c, double* dbeta) {
+  const int t = c->t + 1;
+  const double rem = c->cfg.beta_max - c->betas[(size_t)c->t];
+  const double target = c->cfg.eps_target;
+  double e = 0.0;
+  int rc = gauss_eps(c, t, rem, &e);
+  if (rc != PA_OK) return rc;
+  if (e <= target) {
+    *dbeta = rem;
+    return PA_OK;
+  }
+  double lo = 0.0, hi = rem;
+  for (int it = 0; it < 64 && rc == PA_OK; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    rc = gauss_eps(c, t, mid, &e);
+    if (e <= target)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  *dbeta = lo > 0.0 ? lo : hi;
+  return rc;
+}
+
 int check_device_status(pa_ctx* c) {
   int32_t flags = 0;
   int rc = cuda_status(cudaStreamSynchronize(c->stream));
@@ -445,7 +481,9 @@ int pa_footprint(const pa_config* cfg, size_t* bytes) {
   b += tables * nlev * 8;
   if (cfg->model == PA_MODEL_GAUSS) {
     const size_t nchunk = (size_t)((R_cap + pa::kChunk - 1) / pa::kChunk), nmb = (size_t)((R_cap + 4095) / 4096);
-    b += 12 * N + T * N * sizeof(pa::GTabEntry) * 16 + T * (size_t)pa::kGTableWeights * 8 + T * (size_t)cfg->q_bins * 8;
+    const size_t slots = cfg->betas ? T : 1;
+    b += 12 * N + slots * N * sizeof(pa::GTabEntry) * 16 + slots * (size_t)pa::kGTableWeights * 8 +
+         T * (size_t)cfg->q_bins * 8;
     b += (size_t)cfg->n_pop * (8 * pitch + 16 * (size_t)R_cap + 8 * nchunk + 16 * nmb + T * sizeof(pa::GRec));
   }
   *bytes = b;
@@ -463,7 +501,7 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
     return PA_ERR_INVALID;
   if (!cfg->betas && !(cfg->eps_target > 0.0 && cfg->eps_target < 1.0 && cfg->beta_max > 0.0)) return PA_ERR_INVALID;
   if (cfg->model < PA_MODEL_PM1 || cfg->model > PA_MODEL_GAUSS ||
-      (cfg->model == PA_MODEL_GAUSS && (!cfg->betas || !pa::sweep_supported(cfg->L))))
+      (cfg->model == PA_MODEL_GAUSS && !pa::sweep_supported(cfg->L)))
     return PA_ERR_INVALID;
   if (cfg->betas) {
     if (cfg->betas[0] != 0.0) return PA_ERR_INVALID;
@@ -545,8 +583,9 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
   }
   if (g.model == PA_MODEL_GAUSS) {
     rc = rc ? rc : dalloc(c, &c->Jq, (size_t)3 * g.N);
-    rc = rc ? rc : dalloc(c, &c->gtab, T * (size_t)g.N * 16);
-    rc = rc ? rc : dalloc(c, &c->gw, T * (size_t)pa::kGTableWeights);
+    const size_t slots = c->adaptive ? 1 : T;  // adaptive: this step's tables, rebuilt every step
+    rc = rc ? rc : dalloc(c, &c->gtab, slots * (size_t)g.N * 16);
+    rc = rc ? rc : dalloc(c, &c->gw, slots * (size_t)pa::kGTableWeights);
     rc = rc ? rc : dalloc(c, &c->qlhist, T * (size_t)g.q_bins);
   }
   if (rc != PA_OK) {
@@ -568,7 +607,7 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
     std::vector<pa::GTabEntry> tab((size_t)g.N * 16);
     std::vector<double> wt((size_t)pa::kGTableWeights);
     if (rc == PA_OK) rc = copy_h2d(c, c->Jq, c->Jq_host.data(), sizeof(int32_t) * c->Jq_host.size());
-    for (int t = 1; t < cfg->n_temps && rc == PA_OK; ++t) {
+    for (int t = 1; t < cfg->n_temps && rc == PA_OK && !c->adaptive; ++t) {
       gauss_site_tables(c->Jq_host, g.L, c->betas[(size_t)t], tab.data());
       gauss_weight_tables(c->betas[(size_t)t] - c->betas[(size_t)t - 1], wt.data());
       rc = copy_h2d(c, c->gtab + (size_t)t * g.N * 16, tab.data(), sizeof(pa::GTabEntry) * tab.size());
@@ -609,7 +648,7 @@ int pa_step(pa_ctx* c) {
   double dbeta;
   if (c->adaptive) {
     int rc = check_device_status(c);
-    if (rc == PA_OK) rc = choose_dbeta(c, &dbeta);
+    if (rc == PA_OK) rc = c->model == PA_MODEL_GAUSS ? choose_dbeta_gauss(c, &dbeta) : choose_dbeta(c, &dbeta);
     if (rc != PA_OK) return fail(c, rc);
     double b = c->betas[(size_t)t - 1] + dbeta;
     if (b >= c->cfg.beta_max || dbeta == c->cfg.beta_max - c->betas[(size_t)t - 1]) b = c->cfg.beta_max;
@@ -622,15 +661,24 @@ int pa_step(pa_ctx* c) {
   for (int p = 0; p < c->g.n_pop && rc == PA_OK; ++p)
     rc = cuda_status(cudaMemsetAsync(c->pops[p].rec + t, 0, sizeof(StepRec), s));
   if (c->model == PA_MODEL_GAUSS) {
+    const size_t slot = c->adaptive ? 0 : (size_t)t;
+    if (c->adaptive && rc == PA_OK) {  // this step's tables, for the beta just chosen
+      std::vector<pa::GTabEntry> tab((size_t)c->g.N * 16);
+      std::vector<double> wt((size_t)pa::kGTableWeights);
+      gauss_site_tables(c->Jq_host, c->g.L, c->betas[(size_t)t], tab.data());
+      gauss_weight_tables(dbeta, wt.data());
+      rc = copy_h2d(c, c->gtab, tab.data(), sizeof(pa::GTabEntry) * tab.size());
+      if (rc == PA_OK) rc = copy_h2d(c, c->gw, wt.data(), sizeof(double) * wt.size());
+    }
     if (rc == PA_OK) {
       PhaseTimer pt(c, PA_PHASE_RESAMPLE, 7);
-      rc = launch_rc(pa::launch_g_resample(c->g, c->pops, c->cur, t, c->gw + (size_t)t * pa::kGTableWeights,
+      rc = launch_rc(pa::launch_g_resample(c->g, c->pops, c->cur, t, c->gw + slot * pa::kGTableWeights,
                                            c->status, s));
     }
     if (rc == PA_OK) {
       PhaseTimer pt(c, PA_PHASE_SWEEP, 1);
       rc = launch_rc(pa::launch_g_sweep(c->g, c->pops, c->cur, c->jtab, c->Jq, c->Jtot,
-                                        c->gtab + (size_t)t * c->g.N * 16, t, c->sweeps[(size_t)t], s));
+                                        c->gtab + slot * c->g.N * 16, t, c->sweeps[(size_t)t], s));
     }
   } else {
     const double* w = nullptr;

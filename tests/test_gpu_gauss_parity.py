@@ -94,15 +94,13 @@ def test_longer_run_and_sweep_schedule(pa, oracle_lib):
     assert_state(gpu, ref, 1, "end")
 
 
-def test_gaussian_runs_refuse_the_pm1_readers_and_adaptive_schedules(pa):
+def test_gaussian_runs_refuse_the_pm1_readers(pa):
     run = pa.Run(4, 100, 1, 1, np.linspace(0, 1, 3), model=pa.PA_MODEL_GAUSS)
     for call in (lambda: run.obs(0), lambda: run.energy_hist(0), lambda: run.checkpoint(),
                  lambda: run.replicas(0, 0, 5)):
         with pytest.raises(pa.PAError) as e:
             call()
         assert e.value.status == pa.PA_ERR_INVALID
-    with pytest.raises(pa.PAError):
-        pa.Run(4, 100, 1, 1, None, n_temps=10, beta_max=2.0, eps_target=0.3, model=pa.PA_MODEL_GAUSS)
     pm1 = pa.Run(4, 100, 1, 1, np.linspace(0, 1, 3))
     with pytest.raises(pa.PAError):
         pm1.gobs(0)
@@ -156,3 +154,29 @@ def test_full_size_sampled_steps(pa, oracle_lib):
         # exact moments of the new population
         assert o["sum_E"] == int(E_new.sum()) and o["E_min"] == int(E_new.min())
         assert o["sum_E2"] == float(sum(int(e) * int(e) for e in E_new.tolist()))
+
+
+@pytest.mark.parametrize("L,R,eps,bmax,n_pop", [(4, 900, 0.3, 2.5, 1), (6, 1500, 0.2, 3.0, 2), (10, 4000, 0.45, 2.0, 1)])
+def test_adaptive_schedule_bit_exact(pa, oracle_lib, L, R, eps, bmax, n_pop):
+    """§IV.B with Gaussian couplings: every trial culling fraction of the bisection is
+    the oracle's to the bit, so the chosen temperatures are identical, and with them
+    every population and observable."""
+    gpu = pa.Run(L, R, 3, 40 + L, None, n_temps=400, beta_max=bmax, eps_target=eps, n_sweeps=2, n_pop=n_pop,
+                 model=pa.PA_MODEL_GAUSS)
+    ref = oracle_lib.GRun(oracle_lib.RunConfig(L=L, R=R, disorder_seed=3, run_seed=40 + L, betas=None, n_temps=400,
+                                               beta_max=bmax, eps_target=eps, n_sweeps=2, n_pop=n_pop))
+    t = 0
+    while True:
+        rg, rr = gpu.step(), ref.step()
+        if rr == oracle_lib.DONE:
+            assert rg == pa.PA_DONE
+            break
+        assert rg == 0
+        t += 1
+        for p in range(n_pop):
+            assert_obs(gpu.gobs(t, p), ref.obs(t, p), f"t={t} pop {p}")
+        assert gpu.gobs(t)["beta"] == ref.obs(t)["beta"]
+        assert np.array_equal(gpu.copy_counts(), ref.last_counts()), f"copy numbers at t={t}"
+        assert_state(gpu, ref, n_pop, f"t={t}")
+    assert t >= 3 and gpu.gobs(t)["beta"] == bmax
+    assert all(gpu.gobs(u)["eps_expected"] <= eps for u in range(1, t + 1))
