@@ -41,13 +41,15 @@ if ROOT not in sys.path:
 
 METRIC = "Metropolis updates/s (L=10,R=1e6)"
 UNIT = "updates/s"
-# Roofline of the sweep kernel: the 32x32->64 integer multiply.  Philox4x32-10
+# Roofline of the sweep kernels: the 32x32->64 integer multiply.  Philox4x32-10
 # with the counter (site, half-sweep, group, step) needs 16 such multiplies per
-# block of four words once rounds 1-2 are hoisted (they depend only on the site
-# or only on the thread), i.e. 4 per site update; an SM issues 32 of them per
-# clock (128 int32 lanes, a 64-bit product taking four lane-slots; the
-# "mulwide" probe of include/pa_bench.h measures it).
-WIDE_MULS_PER_UPDATE = 4
+# block once rounds 1-2 are hoisted (they depend only on the site or only on the
+# thread).  The +-1 sweep reads 16 bits per update (one block for eight replicas,
+# the tie-break block only on a tie, probability 2^-16), i.e. 2 per update; the
+# Gaussian sweep reads a 32-bit word per update, i.e. 4.  An SM issues 32 of them
+# per clock (the "mulwide" probe of include/pa_bench.h measures it).
+WIDE_MULS_PER_UPDATE = 2
+WIDE_MULS_PER_UPDATE_GAUSS = 4
 WIDE_MULS_PER_CLK_PER_SM = 32
 # HBM bytes per update of the sweep kernel: the tile is read (gather) and
 # written once per step, i.e. 2 bytes per site and replica every S sweeps, plus
@@ -450,7 +452,7 @@ def ours(args):
     build.build()
     if args.gaussian_only:
         n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-        peak = n_sm * (WIDE_MULS_PER_CLK_PER_SM / WIDE_MULS_PER_UPDATE) * 2070.0 * 1e6 / 1e9
+        peak = n_sm * (WIDE_MULS_PER_CLK_PER_SM / WIDE_MULS_PER_UPDATE_GAUSS) * 2070.0 * 1e6 / 1e9
         print(json.dumps(gaussian_measurement(pa, args.gaussian_steps, args.warmup, peak, cpu=False,
                                               R=args.gaussian_R)), flush=True)
         return
@@ -555,7 +557,8 @@ def ours(args):
         free, _ = torch.cuda.mem_get_info()
         line["served"] = served_vs_serial(pa, args.served_requests, int(0.5 * free))
     if rank == 0 and world == 1 and args.gaussian_steps > 0:
-        line["gaussian"] = gaussian_measurement(pa, args.gaussian_steps, args.warmup, peak,
+        line["gaussian"] = gaussian_measurement(pa, args.gaussian_steps, args.warmup,
+                                                peak * WIDE_MULS_PER_UPDATE / WIDE_MULS_PER_UPDATE_GAUSS,
                                                 cpu=world == 1 and not args.no_cpu_baseline, R=args.gaussian_R)
     if args.probe:
         line["int_probes_per_s"] = {k: pa.int_throughput(k) for k in pa.PROBES}

@@ -8,7 +8,7 @@
 namespace pa {
 
 // Random-stream purposes (4 bits above the seed in the Philox key).
-enum Purpose : uint32_t { kCouplings = 0, kInit = 1, kMetropolis = 2, kResample = 3 };
+enum Purpose : uint32_t { kCouplings = 0, kInit = 1, kMetropolis = 2, kResample = 3, kMetropolisTie = 4 };
 
 // Device status flags (OR-ed into one word by the kernels).
 enum StatusFlag : int32_t { kFlagCapacity = 1, kFlagExtinct = 2, kFlagTimeout = 4 };
@@ -67,6 +67,7 @@ struct PopDev {
   unsigned long long* e2part;  // [2 * n_measure_blocks] 128-bit partial sums of E^2
   GRec* grec;           // [n_temps]
   uint32_t key_met[2];
+  uint32_t key_tie[2];   // tie-break stream of the +-1 Metropolis test
   uint32_t key_res[2];
   uint32_t key_init[2];
 };

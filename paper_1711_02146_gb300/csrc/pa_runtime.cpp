@@ -569,6 +569,7 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
     rc = rc ? rc : dalloc(c, &P.partials, (size_t)g.n_entropy_blocks);
     rc = rc ? rc : dalloc(c, &P.rec, T);
     make_key(cfg->run_seed, pa::kMetropolis, (uint32_t)p, P.key_met);
+    make_key(cfg->run_seed, pa::kMetropolisTie, (uint32_t)p, P.key_tie);
     make_key(cfg->run_seed, pa::kResample, (uint32_t)p, P.key_res);
     make_key(cfg->run_seed, pa::kInit, (uint32_t)p, P.key_init);
     if (g.model == PA_MODEL_GAUSS) {

@@ -14,23 +14,31 @@
 // HBM traffic is one read and one write of the tile per step, whatever S is.
 //
 // Metropolis rule: flipping s_n costs dE = 2 s_n h_n = 12 - 4u, u = unsatisfied
-// bonds at n.  It is taken when u >= 3 (dE <= 0) or when the Philox word r is
-// below thr[dE/4 - 1] = floor(2^32 exp(-beta dE)).  r is word (j & 3) of
-// Philox4x32-10 at counter (n >> 1, 2s + c, j >> 2, t) keyed by (run_seed,
-// Metropolis, population): one block serves four replicas, two blocks a word.
+// bonds at n.  It is taken when u >= 3 (dE <= 0), or with probability
+// thr / 2^32, thr = floor(2^32 exp(-beta dE)), read as a 32-bit uniform in two
+// halves: the replica's 16-bit uniform U against the top half of thr decides
+// unless the two are equal (probability 2^-16), and only then the tie-break
+// uniform V against the low half.  U is half (j & 1) of word (j & 7) >> 1 of
+// Philox4x32-10 at counter (n >> 1, 2s + c, j >> 3, t) keyed by (run_seed,
+// Metropolis, population): one block serves the eight replicas of a word.  V is
+// the same half of the same word under the tie-break key.
 //
 // Shared-memory encoding: replica i of a word is nibble i, spin -1 <=> bit 0
 // set.  For a bond, s_a ^ s_b ^ Jmask (Jmask = 1 per nibble for J = -1) is 1
 // exactly when the bond is unsatisfied, so the nibble-wise sum of the six bond
 // terms plus 5 is v = u + 5 in [5, 11]: bit 3 of v says u >= 3 (always flip),
-// and a byte of v (two replicas) indexes a 256-entry table holding both
-// replicas' thresholds, so one 64-bit shared load serves two replicas.
+// and a byte of v (replicas 2k and 2k+1) indexes a 256-entry table holding both
+// replicas' thresholds, so one 64-bit shared load serves the two replicas whose
+// uniforms share Philox word k.  Comparing that whole word with a threshold
+// decides the high-half replica whenever it is not tied, and the low half
+// shifted up decides the other; a tie anywhere in a site sends it to tie_corrections,
+// which recomputes both blocks and corrects the tied replicas.
 //
 // Philox hoisting (same function, fewer multiplies): with counter words
 // (h, q, g, t) = (site, half-sweep, group, step), the round-1 and round-2
 // products depend either on the site and step only (tabulated once per launch
 // in shared memory) or on the thread and half-sweep only (registers), so each
-// block costs the 16 wide multiplies of rounds 3..10.
+// block costs the 16 wide multiplies of rounds 3..10, two per update.
 #include <cuda_runtime.h>
 
 #include "pa_device.cuh"
@@ -113,50 +121,6 @@ __device__ __forceinline__ ThreadPhilox thread_philox(uint32_t g, uint32_t q, co
   return tp;
 }
 
-// Philox blocks (rounds 3..10) of the L/2 colour sites of one row for the two
-// groups of a word: q[b][xh] is word b of the block of group 0 (b < 4) or
-// group 1 (b >= 4) at site h = h0 + xh.
-template <int L>
-__device__ __forceinline__ void philox_row(uint32_t h0, const SiteRec* __restrict__ rec, const ThreadPhilox& tpa,
-                                           const ThreadPhilox& tpb, const uint32_t* k0, const uint32_t* k1,
-                                           uint32_t (&q)[8][L / 2]) {
-  constexpr int H = L / 2;
-#pragma unroll
-  for (int xh = 0; xh < H; ++xh) {  // round 3 from the hoisted parts
-    const SiteRec& sr = rec[2 * xh];
-    const uint32_t uc = kM0 * (h0 + (uint32_t)xh);  // lo(M0 h)
-#pragma unroll
-    for (int gi = 0; gi < 2; ++gi) {
-      const ThreadPhilox& tp = gi ? tpb : tpa;
-      uint32_t h, l, h2, l2;
-      mulhilo(kM1, tp.tb ^ uc, h, l);
-      mulhilo(kM0, sr.ua ^ tp.ta, h2, l2);
-      q[4 * gi + 0][xh] = h ^ sr.ub;
-      q[4 * gi + 1][xh] = l;
-      q[4 * gi + 2][xh] = h2 ^ tp.tdk;
-      q[4 * gi + 3][xh] = l2;
-    }
-  }
-#pragma unroll
-  for (int rr = 3; rr < 10; ++rr) {  // rounds 4..10 (key index rr)
-#pragma unroll
-    for (int xh = 0; xh < H; ++xh) {
-#pragma unroll
-      for (int gi = 0; gi < 2; ++gi) {
-        uint32_t h, l, h2, l2;
-        mulhilo(kM1, q[4 * gi + 2][xh], h, l);
-        mulhilo(kM0, q[4 * gi + 0][xh], h2, l2);
-        const uint32_t n0 = h ^ q[4 * gi + 1][xh] ^ k0[rr];
-        const uint32_t n2 = h2 ^ q[4 * gi + 3][xh] ^ k1[rr];
-        q[4 * gi + 0][xh] = n0;
-        q[4 * gi + 1][xh] = l;
-        q[4 * gi + 2][xh] = n2;
-        q[4 * gi + 3][xh] = l2;
-      }
-    }
-  }
-}
-
 // Philox blocks (rounds 3..10) of one colour site h for the two groups of a
 // word: w8[b] is word b of group 0's block (b < 4) or group 1's (b >= 4).
 __device__ __forceinline__ void philox_site(uint32_t h, const SiteRec& sr, const ThreadPhilox& tpa,
@@ -191,16 +155,95 @@ __device__ __forceinline__ void philox_site(uint32_t h, const SiteRec& sr, const
   }
 }
 
+// Philox blocks (rounds 3..10) of the L/2 colour sites of one row for the one
+// group of a word (+-1 couplings): q[b][xh] is word b at site h = h0 + xh.
+template <int L>
+__device__ __forceinline__ void philox_row1(uint32_t h0, const SiteRec* __restrict__ rec, const ThreadPhilox& tp,
+                                            const uint32_t* k0, const uint32_t* k1, uint32_t (&q)[4][L / 2]) {
+  constexpr int H = L / 2;
+#pragma unroll
+  for (int xh = 0; xh < H; ++xh) {  // round 3 from the hoisted parts
+    const SiteRec& sr = rec[2 * xh];
+    const uint32_t uc = kM0 * (h0 + (uint32_t)xh);  // lo(M0 h)
+    uint32_t h, l, h2, l2;
+    mulhilo(kM1, tp.tb ^ uc, h, l);
+    mulhilo(kM0, sr.ua ^ tp.ta, h2, l2);
+    q[0][xh] = h ^ sr.ub;
+    q[1][xh] = l;
+    q[2][xh] = h2 ^ tp.tdk;
+    q[3][xh] = l2;
+  }
+#pragma unroll
+  for (int rr = 3; rr < 10; ++rr) {  // rounds 4..10 (key index rr)
+#pragma unroll
+    for (int xh = 0; xh < H; ++xh) {
+      uint32_t h, l, h2, l2;
+      mulhilo(kM1, q[2][xh], h, l);
+      mulhilo(kM0, q[0][xh], h2, l2);
+      const uint32_t n0 = h ^ q[1][xh] ^ k0[rr];
+      const uint32_t n2 = h2 ^ q[3][xh] ^ k1[rr];
+      q[0][xh] = n0;
+      q[1][xh] = l;
+      q[2][xh] = n2;
+      q[3][xh] = l2;
+    }
+  }
+}
+
+// Full Philox4x32-10 block from the per-round keys k0[r], k1[r].
+__device__ __forceinline__ void philox_rounds(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, const uint32_t* k0,
+                                              const uint32_t* k1, uint32_t (&o)[4]) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t h0, l0, h1, l1;
+    mulhilo(kM0, c0, h0, l0);
+    mulhilo(kM1, c2, h1, l1);
+    c0 = h1 ^ c1 ^ k0[r];
+    c1 = l1;
+    c2 = h0 ^ c3 ^ k1[r];
+    c3 = l0;
+  }
+  o[0] = c0;
+  o[1] = c1;
+  o[2] = c2;
+  o[3] = c3;
+}
+
+// Corrections for the tied replicas of one word at one site (v = u + 5 per
+// nibble, counter (h, qc, g, t)): bit 4i is set where replica i's exact decision
+// (the tie-break uniform against the low half of its threshold) differs from the
+// one the fast test took.  Rare, so both blocks are recomputed.
+// Its inputs are plain values and key pointers: handing it the kernel's argument
+// block instead made the fast path of the sweep about 5% slower on GB300.
+__device__ __noinline__ uint32_t tie_corrections(uint32_t v, uint32_t h, uint32_t qc, uint32_t g, uint32_t t,
+                                                 const uint32_t* k0, const uint32_t* k1, const uint32_t* ktie) {
+  const char* tb = reinterpret_cast<const char*>(g_thr_pair);
+  uint32_t om[4];
+  philox_rounds(h, qc, g, t, k0, k1, om);
+  const uint4 otv = philox4x32_10(make_uint4(h, qc, g, t), ktie[0], ktie[1]);
+  const uint32_t ot[4] = {otv.x, otv.y, otv.z, otv.w};
+  uint32_t corr = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint2 th = *reinterpret_cast<const uint2*>(tb + (((v >> (8 * k)) & 0xFFu) << 3));
+    const uint32_t r = om[k], rl = r << 16;
+    if (((rl ^ th.x) < 0x10000u) && ((rl < th.x) != ((ot[k] & 0xFFFFu) < (th.x & 0xFFFFu)))) corr ^= 1u << (8 * k);
+    if (((r ^ th.y) < 0x10000u) && ((r < th.y) != ((ot[k] >> 16) < (th.y & 0xFFFFu)))) corr ^= 1u << (8 * k + 4);
+  }
+  return corr;
+}
+
 // Metropolis update of the colour sites x = X0, X0 + 2, ... of one row from the
-// row's random words q.  The row is read in full first (own row: all L sites,
-// whose other-colour half are the x neighbours; the four neighbour rows: the
-// L/2 sites next to the updated ones).  All neighbour offsets are compile-time;
-// pointers are at (row base, this thread's word).
+// row's random words q (counter words h0 + xh, qc, g).  The row is read in full
+// first (own row: all L sites, whose other-colour half are the x neighbours;
+// the four neighbour rows: the L/2 sites next to the updated ones).  All
+// neighbour offsets are compile-time; pointers are at (row base, this thread's word).
 template <int L, int W, int X0>
 __device__ __forceinline__ void update_row(uint32_t* __restrict__ p0, const uint32_t* __restrict__ pyp,
                                            const uint32_t* __restrict__ pym, const uint32_t* __restrict__ pzp,
                                            const uint32_t* __restrict__ pzm, const SiteRec* __restrict__ rec,
-                                           const uint32_t (&q)[8][L / 2]) {
+                                           const uint32_t (&q)[4][L / 2], uint32_t h0, uint32_t qc, uint32_t g,
+                                           uint32_t t, const uint32_t* k0, const uint32_t* k1, const uint32_t* ktie) {
   constexpr int H = L / 2;
   const char* tb = reinterpret_cast<const char*>(g_thr_pair);
   uint32_t row[L], nyp[H], nym[H], nzp[H], nzm[H];
@@ -226,26 +269,36 @@ __device__ __forceinline__ void update_row(uint32_t* __restrict__ p0, const uint
     v[xh] = (s0 ^ row[xp] ^ sr.jxp) + (s0 ^ row[xm] ^ sr.jxm) + (s0 ^ nyp[xh] ^ sr.jyp) + (s0 ^ nym[xh] ^ sr.jym) +
             (s0 ^ nzp[xh] ^ sr.jzp) + (s0 ^ nzm[xh] ^ sr.jzm) + kBias;
   }
-  // thresholds of every replica of the row, two per 64-bit load
-  uint2 th[4][H];
-#pragma unroll
-  for (int xh = 0; xh < H; ++xh) {
-    th[0][xh] = *reinterpret_cast<const uint2*>(tb + ((v[xh] << 3) & 0x7F8u));
-    th[1][xh] = *reinterpret_cast<const uint2*>(tb + ((v[xh] >> 5) & 0x7F8u));
-    th[2][xh] = *reinterpret_cast<const uint2*>(tb + ((v[xh] >> 13) & 0x7F8u));
-    th[3][xh] = *reinterpret_cast<const uint2*>(tb + ((v[xh] >> 21) & 0x7F8u));
-  }
-  // flips (nibble i <-> word i & 3 of group i >> 2) and write-back
+  // flips: replicas 2k and 2k+1 (byte k of v) read the low and high halves of word k
+  uint32_t acc[H];
+  uint32_t tied = 0;  // bit xh: some replica of site xh has its uniform equal to its threshold's top half
 #pragma unroll
   for (int xh = 0; xh < H; ++xh) {
     const int x = 2 * xh + X0;
-    uint32_t acc = row[x];
+    uint32_t f = row[x];
+    bool tie = false;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const uint32_t t = (i & 1) ? th[i >> 1][xh].y : th[i >> 1][xh].x;
-      if (q[i][xh] < t) acc ^= 1u << (4 * i);
+    for (int k = 0; k < 4; ++k) {
+      const uint2 th = *reinterpret_cast<const uint2*>(tb + (k == 0 ? ((v[xh] << 3) & 0x7F8u)
+                                                                     : ((v[xh] >> (8 * k - 3)) & 0x7F8u)));
+      const uint32_t r = q[k][xh];
+      const uint32_t rl = r << 16;
+      if (rl < th.x) f ^= 1u << (8 * k);
+      if (r < th.y) f ^= 1u << (8 * k + 4);
+      tie = tie || ((rl ^ th.x) < 0x10000u) || ((r ^ th.y) < 0x10000u);
     }
-    p0[x * W] = (acc ^ (v[xh] >> 3)) & kNib;  // bit 3 of v: u >= 3 always flips
+    acc[xh] = f;
+    if (tie) tied |= 1u << xh;
+  }
+  if (tied) {
+#pragma unroll
+    for (int xh = 0; xh < H; ++xh)
+      if ((tied >> xh) & 1u) acc[xh] ^= tie_corrections(v[xh], h0 + (uint32_t)xh, qc, g, t, k0, k1, ktie);
+  }
+#pragma unroll
+  for (int xh = 0; xh < H; ++xh) {
+    const int x = 2 * xh + X0;
+    p0[x * W] = (acc[xh] ^ (v[xh] >> 3)) & kNib;  // bit 3 of v: u >= 3 always flips
   }
 }
 
@@ -263,21 +316,23 @@ __device__ __forceinline__ int row_index(int part, int k, int p) {
 // All rows of one partition for one half-sweep; the colour sites sit at
 // x = X0 mod 2 in every row of the partition's parity class.
 template <int L, int W, int NP, int X0>
-__device__ __forceinline__ void sweep_rows(uint32_t* sp, const SiteRec* recs, int part, int p,
-                                           const ThreadPhilox& tpa, const ThreadPhilox& tpb, const uint32_t* k0,
-                                           const uint32_t* k1) {
+__device__ __forceinline__ void sweep_rows(uint32_t* sp, const SiteRec* recs, int part, int p, const ThreadPhilox& tp,
+                                           const uint32_t* k0, const uint32_t* k1, uint32_t qc, uint32_t g, uint32_t t,
+                                           const uint32_t* ktie) {
   constexpr int RPP = L * L / NP;  // rows per partition
   constexpr int UNROLL = RPP < kSweepRowUnroll ? RPP : kSweepRowUnroll;
 #pragma unroll UNROLL
   for (int k = 0; k < RPP; ++k) {
     const int r = row_index<L, NP>(part, k, p);
-    uint32_t q[8][L / 2];
-    philox_row<L>((uint32_t)(r * L) >> 1, recs + r * L, tpa, tpb, k0, k1, q);
+    const uint32_t h0 = (uint32_t)(r * L) >> 1;
+    uint32_t q[4][L / 2];
+    philox_row1<L>(h0, recs + r * L, tp, k0, k1, q);
     const int y = r % L, z = r / L;
     const int yp = y == L - 1 ? 0 : y + 1, ym = y == 0 ? L - 1 : y - 1;
     const int zp = z == L - 1 ? 0 : z + 1, zm = z == 0 ? L - 1 : z - 1;
     update_row<L, W, X0>(sp + (size_t)r * L * W, sp + (size_t)(yp + L * z) * L * W, sp + (size_t)(ym + L * z) * L * W,
-                         sp + (size_t)(y + L * zp) * L * W, sp + (size_t)(y + L * zm) * L * W, recs + r * L, q);
+                         sp + (size_t)(y + L * zp) * L * W, sp + (size_t)(y + L * zm) * L * W, recs + r * L, q, h0,
+                         qc, g, t, k0, k1, ktie);
   }
 }
 
@@ -454,19 +509,18 @@ __global__ void __launch_bounds__(NT, MB) k_sweep(const __grid_constant__ SweepA
 
   // sweeps: partition `part` owns rows of parity class p = (y + z) & 1; in
   // half-sweep c its colour sites sit at x = p ^ c mod 2 in every row.
-  const uint32_t g0 = 2u * ((uint32_t)(tile0 >> 3) + (uint32_t)word);  // Philox group of nibbles 0..3
+  const uint32_t g = (uint32_t)(tile0 >> 3) + (uint32_t)word;  // Philox group: the word's eight replicas
   const int pclass = part / (NP / 2);
   uint32_t* spw = sp + word;
   for (int s = 0; s < a.n_sweeps; ++s) {
 #pragma unroll 1
     for (int c = 0; c < 2; ++c) {
       const uint32_t q = 2u * (uint32_t)s + (uint32_t)c;
-      const ThreadPhilox tpa = thread_philox(g0, q, a.k0, a.k1);
-      const ThreadPhilox tpb = thread_philox(g0 + 1u, q, a.k0, a.k1);
+      const ThreadPhilox tp = thread_philox(g, q, a.k0, a.k1);
       if ((pclass ^ c) == 0)
-        sweep_rows<L, W, NP, 0>(spw, recs, part, pclass, tpa, tpb, a.k0, a.k1);
+        sweep_rows<L, W, NP, 0>(spw, recs, part, pclass, tp, a.k0, a.k1, q, g, (uint32_t)a.t, a.pop.key_tie);
       else
-        sweep_rows<L, W, NP, 1>(spw, recs, part, pclass, tpa, tpb, a.k0, a.k1);
+        sweep_rows<L, W, NP, 1>(spw, recs, part, pclass, tp, a.k0, a.k1, q, g, (uint32_t)a.t, a.pop.key_tie);
       __syncthreads();
     }
   }

@@ -5,9 +5,11 @@
 // global memory; the energy levels are counted afterwards by k_levels_and_hist.
 //
 // Layout as everywhere: int8 spins +1 = 0x01 / -1 = 0xFF, site-major rows of
-// pitch bytes, so one 32-bit word holds four replicas of one site and one thread
-// updates those four with one Philox4x32-10 block: counter (n >> 1, 2s + c,
-// j >> 2, t), word j & 3 for slot j (the stream every other sweep uses).
+// pitch bytes, so one 64-bit word holds eight replicas of one site and one
+// thread updates those eight with one Philox4x32-10 block: counter (n >> 1,
+// 2s + c, j >> 3, t), half j & 1 of word (j & 7) >> 1 for slot j, with the
+// tie-break block under its own key when a 16-bit uniform equals the top half
+// of its threshold (the acceptance rule of the shared-memory sweep).
 #include <cuda_runtime.h>
 
 #include "pa_device.cuh"
@@ -45,7 +47,15 @@ __global__ void __launch_bounds__(kThreads) k_copy_parents(RunGeom g, PopDev P, 
   *reinterpret_cast<uint32_t*>(dst + (size_t)j0) = out;
 }
 
-// One half-sweep (colour c of sweep s) of every replica, four replicas per thread.
+// Twice the unsatisfied bonds of each of four replicas (one byte each) of site n.
+__device__ __forceinline__ uint32_t unsatisfied2(uint32_t s0, uint32_t sxp, uint32_t sxm, uint32_t syp, uint32_t sym,
+                                                 uint32_t szp, uint32_t szm, uint32_t jxp, uint32_t jxm, uint32_t jyp,
+                                                 uint32_t jym, uint32_t jzp, uint32_t jzm) {
+  return ((s0 ^ sxp ^ jxp) & kBit1) + ((s0 ^ sxm ^ jxm) & kBit1) + ((s0 ^ syp ^ jyp) & kBit1) +
+         ((s0 ^ sym ^ jym) & kBit1) + ((s0 ^ szp ^ jzp) & kBit1) + ((s0 ^ szm ^ jzm) & kBit1);
+}
+
+// One half-sweep (colour c of sweep s) of every replica, eight replicas per thread.
 __global__ void __launch_bounds__(kThreads) k_sweep_global(RunGeom g, PopDev P, int buf, const uint32_t* __restrict__ jtab,
                                                            int t, int s, int c, uint32_t thr4, uint32_t thr8,
                                                            uint32_t thr12, int64_t words) {
@@ -55,7 +65,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep_global(RunGeom g, PopDev P, 
   if (idx >= words * (int64_t)(g.N / 2)) return;
   const int gs = (int)(idx / words);  // colour site: row r, half-index xh
   const int wi = (int)(idx % words);
-  if (4 * wi >= R) return;
+  if (8 * wi >= R) return;
   const int L = g.L;
   const int r = gs / H, xh = gs % H;
   const int y = r % L, z = r / L;
@@ -64,26 +74,40 @@ __global__ void __launch_bounds__(kThreads) k_sweep_global(RunGeom g, PopDev P, 
   const int xp = (x + 1 == L ? 0 : x + 1) + L * r, xm = (x == 0 ? L - 1 : x - 1) + L * r;
   const int yp = x + L * ((y + 1 == L ? 0 : y + 1) + L * z), ym = x + L * ((y == 0 ? L - 1 : y - 1) + L * z);
   const int zp = x + L * (y + L * (z + 1 == L ? 0 : z + 1)), zm = x + L * (y + L * (z == 0 ? L - 1 : z - 1));
-  const int64_t pw = g.pitch / 4;
-  uint32_t* S = reinterpret_cast<uint32_t*>(P.spins[buf]);
-  const uint32_t s0 = S[n * pw + wi];
-  // twice the unsatisfied bonds of each replica, one byte each
-  const uint32_t u2 = ((s0 ^ S[xp * pw + wi] ^ jtab[4 * n + 0]) & kBit1) +
-                      ((s0 ^ S[xm * pw + wi] ^ jtab[4 * xm + 0]) & kBit1) +
-                      ((s0 ^ S[yp * pw + wi] ^ jtab[4 * n + 1]) & kBit1) +
-                      ((s0 ^ S[ym * pw + wi] ^ jtab[4 * ym + 1]) & kBit1) +
-                      ((s0 ^ S[zp * pw + wi] ^ jtab[4 * n + 2]) & kBit1) +
-                      ((s0 ^ S[zm * pw + wi] ^ jtab[4 * zm + 2]) & kBit1);
-  const uint4 rw = philox4x32_10(make_uint4((uint32_t)(n >> 1), (uint32_t)(2 * s + c), (uint32_t)wi, (uint32_t)t),
-                                 P.key_met[0], P.key_met[1]);
-  uint32_t flip = 0;
+  const int64_t pw = g.pitch / 8;
+  uint2* S = reinterpret_cast<uint2*>(P.spins[buf]);
+  const uint2 s0 = S[n * pw + wi], sxp = S[xp * pw + wi], sxm = S[xm * pw + wi], syp = S[yp * pw + wi],
+              sym = S[ym * pw + wi], szp = S[zp * pw + wi], szm = S[zm * pw + wi];
+  const uint32_t jxp = jtab[4 * n + 0], jxm = jtab[4 * xm + 0], jyp = jtab[4 * n + 1], jym = jtab[4 * ym + 1],
+                 jzp = jtab[4 * n + 2], jzm = jtab[4 * zm + 2];
+  const uint32_t u2[2] = {unsatisfied2(s0.x, sxp.x, sxm.x, syp.x, sym.x, szp.x, szm.x, jxp, jxm, jyp, jym, jzp, jzm),
+                          unsatisfied2(s0.y, sxp.y, sxm.y, syp.y, sym.y, szp.y, szm.y, jxp, jxm, jyp, jym, jzp, jzm)};
+  const uint4 ctr = make_uint4((uint32_t)(n >> 1), (uint32_t)(2 * s + c), (uint32_t)wi, (uint32_t)t);
+  const uint4 rw = philox4x32_10(ctr, P.key_met[0], P.key_met[1]);
+  uint32_t flip[2] = {0u, 0u};
+  bool have_tie = false;
+  uint4 rt = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    const uint32_t u = (u2 >> (8 * b + 1)) & 0xFu;  // 0..6; flipping costs dE = 12 - 4u
-    const uint32_t thr = u == 2 ? thr4 : u == 1 ? thr8 : u == 0 ? thr12 : 0u;
-    if (u >= 3 || word_of(rw, b) < thr) flip |= 0xFEu << (8 * b);
+  for (int i = 0; i < 8; ++i) {
+    const uint32_t u = (u2[i >> 2] >> (8 * (i & 3) + 1)) & 0xFu;  // 0..6; flipping costs dE = 12 - 4u
+    bool accept = u >= 3;
+    if (!accept) {
+      const uint32_t thr = u == 2 ? thr4 : u == 1 ? thr8 : thr12;
+      const uint32_t w = word_of(rw, i >> 1);
+      const uint32_t U = (i & 1) ? w >> 16 : w & 0xFFFFu;
+      accept = U < (thr >> 16);
+      if (U == (thr >> 16)) {
+        if (!have_tie) {
+          rt = philox4x32_10(ctr, P.key_tie[0], P.key_tie[1]);
+          have_tie = true;
+        }
+        const uint32_t wt = word_of(rt, i >> 1);
+        accept = ((i & 1) ? wt >> 16 : wt & 0xFFFFu) < (thr & 0xFFFFu);
+      }
+    }
+    if (accept) flip[i >> 2] |= 0xFEu << (8 * (i & 3));
   }
-  S[n * pw + wi] = s0 ^ flip;
+  S[n * pw + wi] = make_uint2(s0.x ^ flip[0], s0.y ^ flip[1]);
 }
 
 }  // namespace
@@ -93,16 +117,16 @@ bool lattice_supported(int L) { return L >= 2 && L <= kMaxLGlobal && L % 2 == 0;
 int launch_sweep_global(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, int t, int n_sweeps,
                         const uint32_t met_thr[3], void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
-  const int64_t words = (g.R_cap + 3) / 4;
+  const int64_t words = (g.R_cap + 3) / 4, words8 = (g.R_cap + 7) / 8;
   for (int p = 0; p < g.n_pop; ++p) {
     const int64_t copy_threads = words * g.N;
     k_copy_parents<<<(unsigned)((copy_threads + kThreads - 1) / kThreads), kThreads, 0, st>>>(g, pops[p], cur, t,
                                                                                               words);
-    const int64_t half = words * (int64_t)(g.N / 2);
+    const int64_t half = words8 * (int64_t)(g.N / 2);
     for (int s = 0; s < n_sweeps; ++s)
       for (int c = 0; c < 2; ++c)
         k_sweep_global<<<(unsigned)((half + kThreads - 1) / kThreads), kThreads, 0, st>>>(
-            g, pops[p], 1 - cur, jtab, t, s, c, met_thr[0], met_thr[1], met_thr[2], words);
+            g, pops[p], 1 - cur, jtab, t, s, c, met_thr[0], met_thr[1], met_thr[2], words8);
     const int e = (int)cudaGetLastError();
     if (e) return e;
   }

@@ -67,3 +67,24 @@ def test_sweep_replica_is_deterministic_and_seeded(oracle_lib):
     # beta -> infinity: only dE <= 0 moves are taken, so the energy never rises
     z, dEz = oracle_lib.sweep_replica(L, J, s0, 99, 0, 5, 3, 4, oracle_lib.metropolis_thresholds(60.0))
     assert dEz <= 0
+
+
+@pytest.mark.parametrize("thr", [0, 1, 0xFFFF, 0x10000, 0x10001, 0x1234ABCD, 0x8000FFFF, 0xFFFF0000, 0xFFFFFFFE,
+                                 0xFFFFFFFF])
+def test_two_stage_acceptance_has_the_probability_of_one_32bit_uniform(oracle_lib, thr):
+    """Over all 16-bit U (the replica's uniform) and V (its tie-break uniform) the
+    rule accepts exactly thr of the 2^32 pairs, i.e. with probability thr / 2^32,
+    the same as one 32-bit uniform below thr; and V matters only when U equals
+    the top half of thr."""
+    accept = oracle_lib.metropolis_accept
+    rng = np.random.default_rng(thr & 0xFFFF)
+    top = thr >> 16
+    total = 0
+    for U in range(1 << 16):
+        if U == top:
+            total += sum(accept(U, V, thr) for V in range(1 << 16))
+        else:
+            a = accept(U, 0, thr)
+            assert a == accept(U, 0xFFFF, thr) == accept(U, int(rng.integers(1 << 16)), thr)
+            total += (1 << 16) * a
+    assert total == thr
