@@ -311,15 +311,16 @@ int pa_restore(const pa_config* cfg, const void* buf, size_t size, void* cuda_st
 
 /* ---- launch shapes of the sweep kernel and their autotuner ----
  * An implementation choice with no counterpart in the paper.  The sweep kernel
- * is compiled for a few launch shapes per lattice size L: W words per site row
- * (a CTA holds 8W replicas, all N sites, in shared memory), threads per CTA,
+ * (+-1 couplings) is compiled for a few launch shapes per lattice size L: W
+ * words per site row (a CTA holds 32W replicas, one bit each, all N sites, in
+ * shared memory), threads per CTA,
  * and the CTAs per SM it is compiled for.  Every shape gives bit-identical
  * results (the random words depend on slot and site, never on the tiling); they
  * differ only in speed.  The first shape of each L is the default.  A run uses
  * the shape selected for its L on the current device when it is created. */
 typedef struct {
   int32_t L;
-  int32_t words;         /* W: 32-bit words per site row of a tile (8 replicas each) */
+  int32_t words;         /* W: 32-bit words per site row of a tile (32 replicas each) */
   int32_t threads;       /* threads per CTA */
   int32_t ctas_per_sm;   /* CTAs per SM the kernel is compiled for (register cap) */
   int32_t smem_bytes;    /* dynamic shared memory per CTA */

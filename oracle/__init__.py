@@ -25,7 +25,7 @@ _SRC_GAUSS = os.path.join(_HERE, "pa_oracle_gauss.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 OK, DONE, ERR_INVALID, ERR_NOMEM, ERR_CAPACITY = 0, 1, -1, -2, -3
-P_COUPLINGS, P_INIT, P_METROPOLIS, P_RESAMPLE, P_METROPOLIS_TIE = 0, 1, 2, 3, 4
+P_COUPLINGS, P_INIT, P_METROPOLIS, P_RESAMPLE = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -134,7 +134,10 @@ def lib():
             "or_couplings": (None, [ctypes.c_int32, ctypes.c_uint64, i8p]),
             "or_energy": (ctypes.c_int32, [ctypes.c_int32, i8p, i8p]),
             "or_metropolis_thresholds": (None, [ctypes.c_double, u32p]),
-            "or_metropolis_accept": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]),
+            "or_metropolis_uniform": (ctypes.c_uint32, [ctypes.c_uint64, ctypes.c_int32, ctypes.c_uint32,
+                                                         ctypes.c_uint32, ctypes.c_int64, ctypes.c_int32]),
+            "or_metropolis_test": (ctypes.c_int32, [ctypes.c_uint64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32,
+                                                    ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32]),
             "or_sweep_replica": (ctypes.c_int32, [ctypes.c_int32, i8p, i8p, ctypes.c_uint64, ctypes.c_int32,
                                                   ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, u32p]),
             "or_reweight": (ctypes.c_int32, [ctypes.c_int32, i64p, ctypes.c_int64, ctypes.c_double, dp,
@@ -222,9 +225,14 @@ def metropolis_thresholds(beta: float) -> np.ndarray:
     return out
 
 
-def metropolis_accept(U: int, V: int, thr: int) -> bool:
-    """Acceptance from the replica's 16-bit uniform U and tie-break uniform V (§II)."""
-    return bool(lib().or_metropolis_accept(U, V, thr))
+def metropolis_uniform(run_seed: int, pop: int, site_index: int, half_sweep: int, slot: int, t: int) -> int:
+    """The replica's 32-bit Metropolis uniform: its bit column in the stream (§II)."""
+    return int(lib().or_metropolis_uniform(run_seed, pop, site_index, half_sweep, slot, t))
+
+
+def metropolis_test(run_seed: int, pop: int, site_index: int, half_sweep: int, slot: int, t: int, thr: int) -> bool:
+    """uniform < thr, read from the top bit down until the first differing bit."""
+    return bool(lib().or_metropolis_test(run_seed, pop, site_index, half_sweep, slot, t, thr))
 
 
 def sweep_replica(L: int, J: np.ndarray, s: np.ndarray, run_seed: int, pop: int, slot: int, t: int,

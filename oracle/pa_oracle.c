@@ -13,7 +13,8 @@
  *   or_energy            pinned: ferromagnet / Neel ground states, enumeration identities
  *   or_enumerate_levels  pinned: sum g = 2^N, g(E) = g(-E) for even L, beta=0 variance 3N,
  *                        ferromagnet degeneracies, gauge invariance, high-T expansion
- *   or_metropolis_accept pinned: exact acceptance count thr over all (U, V) for many thr
+ *   or_metropolis_test   pinned: equals the plain comparison of the full bit-column uniform;
+ *                        the uniform is uniform and independent between slots
  *   or_sweep_replica     pinned: Boltzmann energy distribution vs enumeration (L=2, 3)
  *   or_reweight          pinned: sum_k c_k tau_k = R, tau ratios = Boltzmann ratios
  *   or_copy_count / or_resample_tau
@@ -130,12 +131,15 @@ static int32_t local_field(int32_t L, const int8_t* J, const int8_t* s, int32_t 
 
 /* ------------------------------------------------------------------------- */
 /* Metropolis MCMC at fixed beta (§II: "an MCMC procedure such as the Metropolis
- * algorithm").  dE <= 0 is always accepted; a flip costing dE > 0 is accepted with
- * probability thr / 2^32, thr = floor(2^32 exp(-beta dE)), i.e. when a 32-bit
- * uniform is below thr.  That uniform is read in two halves: its top half is U,
- * the replica's own 16 bits of the Metropolis stream, compared with the top half
- * of thr; its low half V, from the tie-break stream, is needed (and read) only when
- * U equals that top half, and is compared with the low half of thr. */
+ * algorithm").  dE <= 0 is always accepted; a flip costing dE > 0 is accepted when
+ * the replica's 32-bit uniform r is below thr = floor(2^32 exp(-beta dE)).
+ *
+ * r is the replica's bit column in the Metropolis stream: bit 31 - p of r
+ * (p = 0 .. 31) is bit (slot mod 32) of word (p mod 4) of the Philox block at
+ * counter (site, half-sweep, 8 floor(slot / 32) + floor(p / 4), t).  The test
+ * r < thr reads r from its top bit down and stops at the first bit where r and
+ * thr differ (r < thr exactly when there r has 0 and thr has 1), so a decision
+ * draws only the blocks that reach that bit: two bits on average. */
 
 void or_metropolis_thresholds(double beta, uint32_t thr[3]) {
   for (int m = 1; m <= 3; ++m) {
@@ -146,30 +150,48 @@ void or_metropolis_thresholds(double beta, uint32_t thr[3]) {
   }
 }
 
-int32_t or_metropolis_accept(uint32_t U, uint32_t V, uint32_t thr) {
-  uint32_t thr_hi = thr >> 16, thr_lo = thr & 0xFFFFu;
-  if (U < thr_hi) return 1;
-  if (U > thr_hi) return 0;
-  return V < thr_lo ? 1 : 0;
+static void metropolis_block(const uint32_t key[2], uint32_t site_index, uint32_t half_sweep, int64_t slot, int p,
+                             int32_t t, uint32_t out[4]) {
+  uint32_t ctr[4] = {site_index, half_sweep, (uint32_t)(8 * (slot >> 5) + (p >> 2)), (uint32_t)t};
+  or_philox4x32_10(ctr, key, out);
+}
+
+uint32_t or_metropolis_uniform(uint64_t run_seed, int32_t pop, uint32_t site_index, uint32_t half_sweep,
+                               int64_t slot, int32_t t) {
+  uint32_t key[2], out[4], r = 0;
+  or_key(run_seed, OR_P_METROPOLIS, (uint32_t)pop, key);
+  for (int p = 0; p < 32; ++p) {
+    if ((p & 3) == 0) metropolis_block(key, site_index, half_sweep, slot, p, t, out);
+    r |= ((out[p & 3] >> (slot & 31)) & 1u) << (31 - p);
+  }
+  return r;
+}
+
+static int32_t test_below(const uint32_t key[2], uint32_t site_index, uint32_t half_sweep, int64_t slot, int32_t t,
+                          uint32_t thr) {
+  uint32_t out[4];
+  for (int p = 0; p < 32; ++p) {
+    if ((p & 3) == 0) metropolis_block(key, site_index, half_sweep, slot, p, t, out);
+    uint32_t r_bit = (out[p & 3] >> (slot & 31)) & 1u, thr_bit = (thr >> (31 - p)) & 1u;
+    if (r_bit != thr_bit) return r_bit < thr_bit;
+  }
+  return 0; /* r == thr */
+}
+
+int32_t or_metropolis_test(uint64_t run_seed, int32_t pop, uint32_t site_index, uint32_t half_sweep, int64_t slot,
+                           int32_t t, uint32_t thr) {
+  uint32_t key[2];
+  or_key(run_seed, OR_P_METROPOLIS, (uint32_t)pop, key);
+  return test_below(key, site_index, half_sweep, slot, t, thr);
 }
 
 static int32_t n_colours(int32_t L) { return (L % 2 == 0) ? 2 : 3; }
 
-/* The 16-bit uniform of replica `slot` at one site and half-sweep: Philox block at
- * counter (site, half-sweep, slot / 8, t), word (slot mod 8) / 2, low half for an
- * even slot and high half for an odd one. */
-static uint32_t half_word(const uint32_t key[2], uint32_t site_index, uint32_t half_sweep, int64_t slot,
-                          int32_t t) {
-  uint32_t w = philox_word(key, site_index, half_sweep, (uint32_t)(slot >> 3), (uint32_t)t, (int)((slot & 7) >> 1));
-  return (slot & 1) ? (w >> 16) : (w & 0xFFFFu);
-}
-
 int32_t or_sweep_replica(int32_t L, const int8_t* J, int8_t* s, uint64_t run_seed, int32_t pop,
                          int64_t slot, int32_t t, int32_t n_sweeps, const uint32_t thr[3]) {
   int32_t ncol = n_colours(L);
-  uint32_t key[2], key_tie[2];
+  uint32_t key[2];
   or_key(run_seed, OR_P_METROPOLIS, (uint32_t)pop, key);
-  or_key(run_seed, OR_P_METROPOLIS_TIE, (uint32_t)pop, key_tie);
   int32_t dE_total = 0;
   for (int32_t sw = 0; sw < n_sweeps; ++sw) {
     for (int32_t c = 0; c < ncol; ++c) {
@@ -182,14 +204,7 @@ int32_t or_sweep_replica(int32_t L, const int8_t* J, int8_t* s, uint64_t run_see
             int32_t dE = 2 * s[n] * h;
             uint32_t site_index = (ncol == 2) ? (uint32_t)(n >> 1) : (uint32_t)n;
             uint32_t half_sweep = (uint32_t)(ncol * sw + c);
-            int accept = dE <= 0;
-            if (!accept) {
-              uint32_t th = thr[dE / 4 - 1];
-              uint32_t U = half_word(key, site_index, half_sweep, slot, t);
-              uint32_t V = (U == (th >> 16)) ? half_word(key_tie, site_index, half_sweep, slot, t) : 0u;
-              accept = or_metropolis_accept(U, V, th);
-            }
-            if (accept) {
+            if (dE <= 0 || test_below(key, site_index, half_sweep, slot, t, thr[dE / 4 - 1])) {
               s[n] = (int8_t)(-s[n]);
               dE_total += dE;
             }

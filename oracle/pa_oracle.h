@@ -27,7 +27,7 @@
 extern "C" {
 #endif
 
-enum { OR_P_COUPLINGS = 0, OR_P_INIT = 1, OR_P_METROPOLIS = 2, OR_P_RESAMPLE = 3, OR_P_METROPOLIS_TIE = 4 };
+enum { OR_P_COUPLINGS = 0, OR_P_INIT = 1, OR_P_METROPOLIS = 2, OR_P_RESAMPLE = 3 };
 
 enum { OR_OK = 0, OR_DONE = 1, OR_ERR_INVALID = -1, OR_ERR_NOMEM = -2, OR_ERR_CAPACITY = -3 };
 
@@ -86,9 +86,13 @@ void or_couplings(int32_t L, uint64_t disorder_seed, int8_t* J);
 int32_t or_energy(int32_t L, const int8_t* J, const int8_t* s);
 /* Metropolis thresholds for dE = 4, 8, 12 at inverse temperature beta */
 void or_metropolis_thresholds(double beta, uint32_t thr[3]);
-/* Acceptance of a flip with threshold thr from the replica's 16-bit uniform U and
- * its 16-bit tie-break uniform V (read only when U equals the top half of thr) */
-int32_t or_metropolis_accept(uint32_t U, uint32_t V, uint32_t thr);
+/* The 32-bit Metropolis uniform of replica `slot` at one site and half-sweep (its
+ * bit column across the stream's words), and the test uniform < thr read from the
+ * top bit down, stopping at the first bit where the two differ */
+uint32_t or_metropolis_uniform(uint64_t run_seed, int32_t pop, uint32_t site_index, uint32_t half_sweep,
+                               int64_t slot, int32_t t);
+int32_t or_metropolis_test(uint64_t run_seed, int32_t pop, uint32_t site_index, uint32_t half_sweep, int64_t slot,
+                           int32_t t, uint32_t thr);
 /* S sweeps of one replica (slot j) at step t, in place; returns the energy change */
 int32_t or_sweep_replica(int32_t L, const int8_t* J, int8_t* s, uint64_t run_seed, int32_t pop,
                          int64_t slot, int32_t t, int32_t n_sweeps, const uint32_t thr[3]);

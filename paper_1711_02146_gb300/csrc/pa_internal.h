@@ -8,7 +8,7 @@
 namespace pa {
 
 // Random-stream purposes (4 bits above the seed in the Philox key).
-enum Purpose : uint32_t { kCouplings = 0, kInit = 1, kMetropolis = 2, kResample = 3, kMetropolisTie = 4 };
+enum Purpose : uint32_t { kCouplings = 0, kInit = 1, kMetropolis = 2, kResample = 3 };
 
 // Device status flags (OR-ed into one word by the kernels).
 enum StatusFlag : int32_t { kFlagCapacity = 1, kFlagExtinct = 2, kFlagTimeout = 4 };
@@ -67,7 +67,6 @@ struct PopDev {
   unsigned long long* e2part;  // [2 * n_measure_blocks] 128-bit partial sums of E^2
   GRec* grec;           // [n_temps]
   uint32_t key_met[2];
-  uint32_t key_tie[2];   // tie-break stream of the +-1 Metropolis test
   uint32_t key_res[2];
   uint32_t key_init[2];
 };
@@ -75,7 +74,7 @@ struct PopDev {
 // Geometry of one run.
 struct RunGeom {
   int32_t L, N, n_levels;
-  int64_t pitch;        // bytes per site row of the spin arrays (multiple of 128)
+  int64_t pitch;        // bytes per site row of the spin arrays (multiple of 1024)
   int32_t R;            // target population
   int32_t R_cap;
   int32_t n_pop;

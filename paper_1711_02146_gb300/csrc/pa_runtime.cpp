@@ -465,7 +465,7 @@ int pa_footprint(const pa_config* cfg, size_t* bytes) {
     return PA_ERR_INVALID;
   const int64_t R_cap = cfg->R_cap ? cfg->R_cap : cfg->R + 10 * (int64_t)std::ceil(std::sqrt((double)cfg->R)) + 1024;
   const size_t N = (size_t)cfg->L * cfg->L * cfg->L, nlev = 3 * N + 1, T = (size_t)cfg->n_temps;
-  const size_t pitch = (size_t)((R_cap + 255) / 256) * 256;
+  const size_t pitch = (size_t)((R_cap + 1023) / 1024) * 1024;
   const size_t ncb = (size_t)((R_cap + pa::kSlotsPerCountBlock - 1) / pa::kSlotsPerCountBlock);
   const size_t neb = (size_t)((R_cap + pa::kEntropyPerBlock - 1) / pa::kEntropyPerBlock);
   size_t b = 3 * N + 16 * N + 4 + T * (size_t)cfg->q_bins * 8;
@@ -531,7 +531,7 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
   g.L = cfg->L;
   g.N = cfg->L * cfg->L * cfg->L;
   g.n_levels = 3 * g.N + 1;
-  g.pitch = ((R_cap + 255) / 256) * 256;  // a whole number of sweep tiles (<= 256 replicas)
+  g.pitch = ((R_cap + 1023) / 1024) * 1024;  // a whole number of sweep tiles (<= 1024 replicas)
   g.R = (int32_t)cfg->R;
   g.R_cap = (int32_t)R_cap;
   g.n_pop = cfg->n_pop;
@@ -569,7 +569,6 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
     rc = rc ? rc : dalloc(c, &P.partials, (size_t)g.n_entropy_blocks);
     rc = rc ? rc : dalloc(c, &P.rec, T);
     make_key(cfg->run_seed, pa::kMetropolis, (uint32_t)p, P.key_met);
-    make_key(cfg->run_seed, pa::kMetropolisTie, (uint32_t)p, P.key_tie);
     make_key(cfg->run_seed, pa::kResample, (uint32_t)p, P.key_res);
     make_key(cfg->run_seed, pa::kInit, (uint32_t)p, P.key_init);
     if (g.model == PA_MODEL_GAUSS) {

@@ -1,61 +1,48 @@
-// pa_sweep.cu — the Metropolis sweep kernel (the dominant cost of a PA step).
+// pa_sweep.cu — the Metropolis sweep kernels (the dominant cost of a PA step).
 //
-// One CTA owns a tile of TJ = 8W consecutive slots of the NEW population and
-// all N sites of those replicas in shared memory (W 32-bit words per site row,
-// eight replicas per word, one 4-bit nibble each).  It
+// One CTA owns a tile of consecutive slots of the NEW population and all N sites
+// of those replicas in shared memory.  It
 //   1. gathers each slot's spins from its parent in the old population (the
 //      replica copy of the resampling, §II, fused into the load),
 //   2. runs S checkerboard Metropolis sweeps at beta_t in shared memory (colour
 //      c = (x + y + z) & 1, colour 0 then colour 1; the neighbours of a site all
 //      have the other colour, so all sites of one colour update independently),
-//   3. counts each replica's unsatisfied bonds (its energy level k) and adds
-//      the tile to the level histogram of step t, and
+//   3. counts each replica's energy and adds the tile to the histogram of step t,
 //   4. writes the tile to the new population buffer (int8 +1 / -1).
 // HBM traffic is one read and one write of the tile per step, whatever S is.
 //
-// Metropolis rule: flipping s_n costs dE = 2 s_n h_n = 12 - 4u, u = unsatisfied
-// bonds at n.  It is taken when u >= 3 (dE <= 0), or with probability
-// thr / 2^32, thr = floor(2^32 exp(-beta dE)), read as a 32-bit uniform in two
-// halves: the replica's 16-bit uniform U against the top half of thr decides
-// unless the two are equal (probability 2^-16), and only then the tie-break
-// uniform V against the low half.  U is half (j & 1) of word (j & 7) >> 1 of
-// Philox4x32-10 at counter (n >> 1, 2s + c, j >> 3, t) keyed by (run_seed,
-// Metropolis, population): one block serves the eight replicas of a word.  V is
-// the same half of the same word under the tie-break key.
-//
-// Shared-memory encoding: replica i of a word is nibble i, spin -1 <=> bit 0
-// set.  For a bond, s_a ^ s_b ^ Jmask (Jmask = 1 per nibble for J = -1) is 1
-// exactly when the bond is unsatisfied, so the nibble-wise sum of the six bond
-// terms plus 5 is v = u + 5 in [5, 11]: bit 3 of v says u >= 3 (always flip),
-// and a byte of v (replicas 2k and 2k+1) indexes a 256-entry table holding both
-// replicas' thresholds, so one 64-bit shared load serves the two replicas whose
-// uniforms share Philox word k.  Comparing that whole word with a threshold
-// decides the high-half replica whenever it is not tied, and the low half
-// shifted up decides the other; a tie anywhere in a site sends it to tie_corrections,
-// which recomputes both blocks and corrects the tied replicas.
+// +-1 couplings (k_sweep): bit-sliced tiles.  Word w of a site row holds slots
+// tile0 + 32w + b as bit b (set for spin -1), so one 32-bit logic instruction
+// tests a bond, adds a bit or takes a comparison step for 32 replicas.  Flipping
+// s_n costs dE = 12 - 4u, u = unsatisfied bonds at n; u comes from the six
+// bond bits by a tree of full adders as three bit planes.  u >= 3 (dE <= 0)
+// always flips; otherwise the flip is taken when the replica's 32-bit uniform r
+// is below thr(u) = floor(2^32 exp(-beta dE)).  r is the replica's bit column:
+// bit 31 - p of r is bit b of word p mod 4 of Philox4x32-10 at counter
+// (n >> 1, 2s + c, 8 (slot >> 5) + p / 4, t) keyed by (run_seed, Metropolis,
+// population), so one block gives four bit planes of 32 replicas' uniforms.
+// The comparison runs from the top plane down: a replica is decided at the first
+// plane where its bit differs from its threshold's (accepted if the threshold
+// has the 1), two planes on average; blocks are drawn until every replica of
+// the word is decided (blocks 0 and 1 always, the rest on demand).
 //
 // Philox hoisting (same function, fewer multiplies): with counter words
 // (h, q, g, t) = (site, half-sweep, group, step), the round-1 and round-2
 // products depend either on the site and step only (tabulated once per launch
 // in shared memory) or on the thread and half-sweep only (registers), so each
-// block costs the 16 wide multiplies of rounds 3..10, two per update.
+// block costs the 16 wide multiplies of rounds 3..10.
+//
+// Gaussian couplings (k_sweep_g, below): nibble-packed tiles, eight replicas per
+// word, with a 32-bit Philox word per update.
 #include <cuda_runtime.h>
 
 #include "pa_device.cuh"
 #include "pa_internal.h"
 
-// Build-time knobs of the sweep's launch shape and code generation.
-#ifndef PA_SWEEP_ROW_UNROLL
-#define PA_SWEEP_ROW_UNROLL 8  // rows of a partition unrolled per loop trip (8: all of them)
-#endif
-
 namespace pa {
 
-constexpr int kSweepRowUnroll = PA_SWEEP_ROW_UNROLL;
 constexpr uint32_t kM0 = 0xD2511F53u;
 constexpr uint32_t kM1 = 0xCD9E8D57u;
-constexpr uint32_t kNib = 0x11111111u;   // bit 0 of every nibble: the spin bit
-constexpr uint32_t kBias = 0x55555555u;  // 5 per nibble
 
 struct SweepArgs {
   PopDev pop;
@@ -68,11 +55,13 @@ struct SweepArgs {
   uint32_t thr4, thr8, thr12;
   uint32_t k0[10];  // Metropolis round keys of this population
   uint32_t k1[10];
+  uint32_t tm[32][4];  // +-1: bit 31 - p of thr(u), u = 0, 1, 2, as an all-zero / all-one word
+  uint32_t live[4];    // +-1: all ones where thr(u) > 0 (a replica with thr(u) = 0 never flips)
 };
 
-// Per-site shared-memory record: the six bond masks of the site, and the
-// site/step-dependent parts of Philox rounds 2-3 for h = n >> 1 (the third,
-// lo(M0 h), is one multiply and is recomputed).
+// Per-site shared-memory record: the six bond masks of the site (all ones for
+// J = -1), and the site/step-dependent parts of Philox rounds 2-3 for h = n >> 1
+// (the third, lo(M0 h), is one multiply and is recomputed).
 struct __align__(16) SiteRec {
   uint32_t jxp, jxm, jyp, jym;
   uint32_t jzp, jzm, ua, ub;
@@ -90,10 +79,6 @@ struct SweepShape {
   static_assert(L % 2 == 0 && L / 2 <= 8, "even L up to 16");
   static_assert(NP % 2 == 0 && (ROWS / 2) % (NP / 2) == 0, "row partitions must split each parity class");
 };
-
-// Thresholds of two replicas by one byte of v = u + 5 (low nibble: .x, high
-// nibble: .y); entries for u >= 3 are 0 (those flips come from bit 3 of v).
-__shared__ __align__(16) uint2 g_thr_pair[256];
 
 __device__ __forceinline__ void mulhilo(uint32_t m, uint32_t a, uint32_t& hi, uint32_t& lo) {
   hi = __umulhi(m, a);
@@ -155,153 +140,6 @@ __device__ __forceinline__ void philox_site(uint32_t h, const SiteRec& sr, const
   }
 }
 
-// Philox blocks (rounds 3..10) of the L/2 colour sites of one row for the one
-// group of a word (+-1 couplings): q[b][xh] is word b at site h = h0 + xh.
-template <int L>
-__device__ __forceinline__ void philox_row1(uint32_t h0, const SiteRec* __restrict__ rec, const ThreadPhilox& tp,
-                                            const uint32_t* k0, const uint32_t* k1, uint32_t (&q)[4][L / 2]) {
-  constexpr int H = L / 2;
-#pragma unroll
-  for (int xh = 0; xh < H; ++xh) {  // round 3 from the hoisted parts
-    const SiteRec& sr = rec[2 * xh];
-    const uint32_t uc = kM0 * (h0 + (uint32_t)xh);  // lo(M0 h)
-    uint32_t h, l, h2, l2;
-    mulhilo(kM1, tp.tb ^ uc, h, l);
-    mulhilo(kM0, sr.ua ^ tp.ta, h2, l2);
-    q[0][xh] = h ^ sr.ub;
-    q[1][xh] = l;
-    q[2][xh] = h2 ^ tp.tdk;
-    q[3][xh] = l2;
-  }
-#pragma unroll
-  for (int rr = 3; rr < 10; ++rr) {  // rounds 4..10 (key index rr)
-#pragma unroll
-    for (int xh = 0; xh < H; ++xh) {
-      uint32_t h, l, h2, l2;
-      mulhilo(kM1, q[2][xh], h, l);
-      mulhilo(kM0, q[0][xh], h2, l2);
-      const uint32_t n0 = h ^ q[1][xh] ^ k0[rr];
-      const uint32_t n2 = h2 ^ q[3][xh] ^ k1[rr];
-      q[0][xh] = n0;
-      q[1][xh] = l;
-      q[2][xh] = n2;
-      q[3][xh] = l2;
-    }
-  }
-}
-
-// Full Philox4x32-10 block from the per-round keys k0[r], k1[r].
-__device__ __forceinline__ void philox_rounds(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, const uint32_t* k0,
-                                              const uint32_t* k1, uint32_t (&o)[4]) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    uint32_t h0, l0, h1, l1;
-    mulhilo(kM0, c0, h0, l0);
-    mulhilo(kM1, c2, h1, l1);
-    c0 = h1 ^ c1 ^ k0[r];
-    c1 = l1;
-    c2 = h0 ^ c3 ^ k1[r];
-    c3 = l0;
-  }
-  o[0] = c0;
-  o[1] = c1;
-  o[2] = c2;
-  o[3] = c3;
-}
-
-// Corrections for the tied replicas of one word at one site (v = u + 5 per
-// nibble, counter (h, qc, g, t)): bit 4i is set where replica i's exact decision
-// (the tie-break uniform against the low half of its threshold) differs from the
-// one the fast test took.  Rare, so both blocks are recomputed.
-// Its inputs are plain values and key pointers: handing it the kernel's argument
-// block instead made the fast path of the sweep about 5% slower on GB300.
-__device__ __noinline__ uint32_t tie_corrections(uint32_t v, uint32_t h, uint32_t qc, uint32_t g, uint32_t t,
-                                                 const uint32_t* k0, const uint32_t* k1, const uint32_t* ktie) {
-  const char* tb = reinterpret_cast<const char*>(g_thr_pair);
-  uint32_t om[4];
-  philox_rounds(h, qc, g, t, k0, k1, om);
-  const uint4 otv = philox4x32_10(make_uint4(h, qc, g, t), ktie[0], ktie[1]);
-  const uint32_t ot[4] = {otv.x, otv.y, otv.z, otv.w};
-  uint32_t corr = 0;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const uint2 th = *reinterpret_cast<const uint2*>(tb + (((v >> (8 * k)) & 0xFFu) << 3));
-    const uint32_t r = om[k], rl = r << 16;
-    if (((rl ^ th.x) < 0x10000u) && ((rl < th.x) != ((ot[k] & 0xFFFFu) < (th.x & 0xFFFFu)))) corr ^= 1u << (8 * k);
-    if (((r ^ th.y) < 0x10000u) && ((r < th.y) != ((ot[k] >> 16) < (th.y & 0xFFFFu)))) corr ^= 1u << (8 * k + 4);
-  }
-  return corr;
-}
-
-// Metropolis update of the colour sites x = X0, X0 + 2, ... of one row from the
-// row's random words q (counter words h0 + xh, qc, g).  The row is read in full
-// first (own row: all L sites, whose other-colour half are the x neighbours;
-// the four neighbour rows: the L/2 sites next to the updated ones).  All
-// neighbour offsets are compile-time; pointers are at (row base, this thread's word).
-template <int L, int W, int X0>
-__device__ __forceinline__ void update_row(uint32_t* __restrict__ p0, const uint32_t* __restrict__ pyp,
-                                           const uint32_t* __restrict__ pym, const uint32_t* __restrict__ pzp,
-                                           const uint32_t* __restrict__ pzm, const SiteRec* __restrict__ rec,
-                                           const uint32_t (&q)[4][L / 2], uint32_t h0, uint32_t qc, uint32_t g,
-                                           uint32_t t, const uint32_t* k0, const uint32_t* k1, const uint32_t* ktie) {
-  constexpr int H = L / 2;
-  const char* tb = reinterpret_cast<const char*>(g_thr_pair);
-  uint32_t row[L], nyp[H], nym[H], nzp[H], nzm[H];
-#pragma unroll
-  for (int x = 0; x < L; ++x) row[x] = p0[x * W];
-#pragma unroll
-  for (int xh = 0; xh < H; ++xh) {
-    const int x = 2 * xh + X0;
-    nyp[xh] = pyp[x * W];
-    nym[xh] = pym[x * W];
-    nzp[xh] = pzp[x * W];
-    nzm[xh] = pzm[x * W];
-  }
-  // v = u + 5 per nibble, u = unsatisfied bonds of each replica at the site
-  uint32_t v[H];
-#pragma unroll
-  for (int xh = 0; xh < H; ++xh) {
-    const int x = 2 * xh + X0;
-    const int xp = x == L - 1 ? 0 : x + 1;
-    const int xm = x == 0 ? L - 1 : x - 1;
-    const SiteRec& sr = rec[x];
-    const uint32_t s0 = row[x];
-    v[xh] = (s0 ^ row[xp] ^ sr.jxp) + (s0 ^ row[xm] ^ sr.jxm) + (s0 ^ nyp[xh] ^ sr.jyp) + (s0 ^ nym[xh] ^ sr.jym) +
-            (s0 ^ nzp[xh] ^ sr.jzp) + (s0 ^ nzm[xh] ^ sr.jzm) + kBias;
-  }
-  // flips: replicas 2k and 2k+1 (byte k of v) read the low and high halves of word k
-  uint32_t acc[H];
-  uint32_t tied = 0;  // bit xh: some replica of site xh has its uniform equal to its threshold's top half
-#pragma unroll
-  for (int xh = 0; xh < H; ++xh) {
-    const int x = 2 * xh + X0;
-    uint32_t f = row[x];
-    bool tie = false;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const uint2 th = *reinterpret_cast<const uint2*>(tb + (k == 0 ? ((v[xh] << 3) & 0x7F8u)
-                                                                     : ((v[xh] >> (8 * k - 3)) & 0x7F8u)));
-      const uint32_t r = q[k][xh];
-      const uint32_t rl = r << 16;
-      if (rl < th.x) f ^= 1u << (8 * k);
-      if (r < th.y) f ^= 1u << (8 * k + 4);
-      tie = tie || ((rl ^ th.x) < 0x10000u) || ((r ^ th.y) < 0x10000u);
-    }
-    acc[xh] = f;
-    if (tie) tied |= 1u << xh;
-  }
-  if (tied) {
-#pragma unroll
-    for (int xh = 0; xh < H; ++xh)
-      if ((tied >> xh) & 1u) acc[xh] ^= tie_corrections(v[xh], h0 + (uint32_t)xh, qc, g, t, k0, k1, ktie);
-  }
-#pragma unroll
-  for (int xh = 0; xh < H; ++xh) {
-    const int x = 2 * xh + X0;
-    p0[x * W] = (acc[xh] ^ (v[xh] >> 3)) & kNib;  // bit 3 of v: u >= 3 always flips
-  }
-}
-
 // Row k of a partition: rows of one parity class (y + z) & 1 = p, interleaved
 // across the partitions of that class.
 template <int L, int NP>
@@ -311,29 +149,6 @@ __device__ __forceinline__ int row_index(int part, int k, int p) {
   const int z = i / H;
   const int y = 2 * (i % H) + ((p + z) & 1);
   return y + L * z;
-}
-
-// All rows of one partition for one half-sweep; the colour sites sit at
-// x = X0 mod 2 in every row of the partition's parity class.
-template <int L, int W, int NP, int X0>
-__device__ __forceinline__ void sweep_rows(uint32_t* sp, const SiteRec* recs, int part, int p, const ThreadPhilox& tp,
-                                           const uint32_t* k0, const uint32_t* k1, uint32_t qc, uint32_t g, uint32_t t,
-                                           const uint32_t* ktie) {
-  constexpr int RPP = L * L / NP;  // rows per partition
-  constexpr int UNROLL = RPP < kSweepRowUnroll ? RPP : kSweepRowUnroll;
-#pragma unroll UNROLL
-  for (int k = 0; k < RPP; ++k) {
-    const int r = row_index<L, NP>(part, k, p);
-    const uint32_t h0 = (uint32_t)(r * L) >> 1;
-    uint32_t q[4][L / 2];
-    philox_row1<L>(h0, recs + r * L, tp, k0, k1, q);
-    const int y = r % L, z = r / L;
-    const int yp = y == L - 1 ? 0 : y + 1, ym = y == 0 ? L - 1 : y - 1;
-    const int zp = z == L - 1 ? 0 : z + 1, zm = z == 0 ? L - 1 : z - 1;
-    update_row<L, W, X0>(sp + (size_t)r * L * W, sp + (size_t)(yp + L * z) * L * W, sp + (size_t)(ym + L * z) * L * W,
-                         sp + (size_t)(y + L * zp) * L * W, sp + (size_t)(y + L * zm) * L * W, recs + r * L, q, h0,
-                         qc, g, t, k0, k1, ktie);
-  }
 }
 
 // int8 spins (0x01 / 0xFF) of four replicas -> nibbles 0..3 (bit 1 of a byte is the sign)
@@ -349,8 +164,8 @@ __device__ __forceinline__ uint32_t nibbles_to_bytes(uint32_t x) {
 
 // ---- phases of a tile shared by both sweep kernels (nt consumer threads take part)
 
-// Site records (bond masks, site/step parts of Philox rounds 1-3) and the
-// threshold-pair table; all `nthreads` threads of the CTA help.
+// Site records (bond masks, site/step parts of Philox rounds 1-3); all
+// `nthreads` threads of the CTA help.
 template <int L>
 __device__ __forceinline__ void init_tables(const SweepArgs& a, SiteRec* recs, int tid, int nthreads) {
   constexpr int N = L * L * L;
@@ -362,12 +177,12 @@ __device__ __forceinline__ void init_tables(const SweepArgs& a, SiteRec* recs, i
     const int nym = x + L * ((y == 0 ? L - 1 : y - 1) + L * z);
     const int nzm = x + L * (y + L * (z == 0 ? L - 1 : z - 1));
     SiteRec r;
-    r.jxp = a.jtab[4 * n + 0] ? kNib : 0u;
-    r.jyp = a.jtab[4 * n + 1] ? kNib : 0u;
-    r.jzp = a.jtab[4 * n + 2] ? kNib : 0u;
-    r.jxm = a.jtab[4 * nxm + 0] ? kNib : 0u;
-    r.jym = a.jtab[4 * nym + 1] ? kNib : 0u;
-    r.jzm = a.jtab[4 * nzm + 2] ? kNib : 0u;
+    r.jxp = a.jtab[4 * n + 0] ? ~0u : 0u;
+    r.jyp = a.jtab[4 * n + 1] ? ~0u : 0u;
+    r.jzp = a.jtab[4 * n + 2] ? ~0u : 0u;
+    r.jxm = a.jtab[4 * nxm + 0] ? ~0u : 0u;
+    r.jym = a.jtab[4 * nym + 1] ? ~0u : 0u;
+    r.jzm = a.jtab[4 * nzm + 2] ? ~0u : 0u;
     const uint32_t h = (uint32_t)n >> 1;
     uint32_t hi0, lo0, hi1, lo1;
     mulhilo(kM0, h, hi0, lo0);
@@ -376,12 +191,6 @@ __device__ __forceinline__ void init_tables(const SweepArgs& a, SiteRec* recs, i
     r.ua = hi1 ^ k0[1];
     r.ub = lo1 ^ k0[2];
     recs[n] = r;
-  }
-  for (int b = tid; b < 256; b += nthreads) {
-    const int lo = (b & 15) - 5, hi = (b >> 4) - 5;  // u of the two replicas
-    const uint32_t tlo = lo == 0 ? a.thr12 : lo == 1 ? a.thr8 : lo == 2 ? a.thr4 : 0u;
-    const uint32_t thi = hi == 0 ? a.thr12 : hi == 1 ? a.thr8 : hi == 2 ? a.thr4 : 0u;
-    g_thr_pair[b] = make_uint2(tlo, thi);
   }
 }
 
@@ -429,37 +238,6 @@ __device__ __forceinline__ void gather_tile(const SweepArgs& a, uint32_t* sp, in
   }
 }
 
-// Unsatisfied forward bonds of every replica of the tile, summed into ecnt.
-template <int L, int W, int NP>
-__device__ __forceinline__ void count_levels(const uint32_t* sp, const SiteRec* recs, int* ecnt, int word, int part) {
-  constexpr int ROWS = L * L;
-  int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int r = part; r < ROWS; r += NP) {
-    const int y = r % L, z = r / L;
-    const int yp = y == L - 1 ? 0 : y + 1, zp = z == L - 1 ? 0 : z + 1;
-    const uint32_t* p0 = sp + (size_t)r * L * W + word;
-    const uint32_t* pyp = sp + (size_t)(yp + L * z) * L * W + word;
-    const uint32_t* pzp = sp + (size_t)(y + L * zp) * L * W + word;
-    const SiteRec* rr = recs + r * L;
-    uint32_t even = 0, odd = 0;  // nibbles 0,2,4,6 / 1,3,5,7 in byte lanes, <= 3L each
-#pragma unroll
-    for (int x = 0; x < L; ++x) {
-      const int xp = x == L - 1 ? 0 : x + 1;
-      const uint32_t s0 = p0[x * W];
-      const uint32_t e = (s0 ^ p0[xp * W] ^ rr[x].jxp) + (s0 ^ pyp[x * W] ^ rr[x].jyp) + (s0 ^ pzp[x * W] ^ rr[x].jzp);
-      even += e & 0x0F0F0F0Fu;
-      odd += (e >> 4) & 0x0F0F0F0Fu;
-    }
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      cnt[2 * b] += (even >> (8 * b)) & 0xFFu;
-      cnt[2 * b + 1] += (odd >> (8 * b)) & 0xFFu;
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < 8; ++i) atomicAdd(&ecnt[8 * word + i], cnt[i]);
-}
-
 // Levels and histogram of the tile's slots (after count_levels and a barrier).
 template <int TJ>
 __device__ __forceinline__ void publish_levels(const SweepArgs& a, const int* ecnt, int tile0, int R_new, int tid,
@@ -488,46 +266,287 @@ __device__ __forceinline__ void store_tile(const SweepArgs& a, const uint32_t* s
   }
 }
 
-// Row-partitioned sweep kernel: every warp generates its own random words and
-// updates its rows.
+// ---- +-1 couplings: the bit-sliced sweep
+
+// Bits needed to hold 0..n.
+constexpr int bits_for(int n) { return n < 2 ? 1 : 1 + bits_for(n / 2); }
+
+template <int L, int W, int NT>
+struct BitShape {
+  static constexpr int N = L * L * L;
+  static constexpr int ROWS = L * L;
+  static constexpr int NP = NT / W;       // row partitions
+  static constexpr int TJ = 32 * W;       // replicas per tile
+  static constexpr int SLOTS = 33 * W;    // parents (padded by one per word), then level counts
+  static constexpr int CB = bits_for(3 * L * (ROWS / NP));  // bit planes of a thread's level counter
+  static constexpr size_t SMEM = (size_t)N * W * 4 + (size_t)N * sizeof(SiteRec) + (size_t)SLOTS * 4;
+  static_assert(NT % W == 0 && 32 % W == 0 && NT <= 1024, "threads must tile the words of a row");
+  static_assert(L % 2 == 0 && L / 2 <= 8, "even L up to 16");
+  static_assert(NP % 2 == 0 && (ROWS / 2) % (NP / 2) == 0, "row partitions must split each parity class");
+  static_assert(1024 % TJ == 0, "a tile never crosses the 1024-slot pitch unit");
+};
+
+__device__ __forceinline__ uint32_t majority(uint32_t a, uint32_t b, uint32_t c) { return (a & b) | (c & (a ^ b)); }
+
+// One Philox block (rounds 3..10 from the hoisted parts) of site h for the
+// thread's group of block index b (its ThreadPhilox tp).
+__device__ __forceinline__ void philox_block(uint32_t h, const SiteRec& sr, const ThreadPhilox& tp, const uint32_t* k0,
+                                             const uint32_t* k1, uint32_t (&w)[4]) {
+  const uint32_t uc = kM0 * h;  // lo(M0 h)
+  uint32_t hh, l, h2, l2;
+  mulhilo(kM1, tp.tb ^ uc, hh, l);
+  mulhilo(kM0, sr.ua ^ tp.ta, h2, l2);
+  w[0] = hh ^ sr.ub;
+  w[1] = l;
+  w[2] = h2 ^ tp.tdk;
+  w[3] = l2;
+#pragma unroll
+  for (int rr = 3; rr < 10; ++rr) {  // rounds 4..10 (key index rr)
+    mulhilo(kM1, w[2], hh, l);
+    mulhilo(kM0, w[0], h2, l2);
+    const uint32_t n0 = hh ^ w[1] ^ k0[rr];
+    const uint32_t n2 = h2 ^ w[3] ^ k1[rr];
+    w[0] = n0;
+    w[1] = l;
+    w[2] = n2;
+    w[3] = l2;
+  }
+}
+
+// One plane of the comparison uniform < threshold for the 32 replicas of a word:
+// r holds the plane's bit of every replica's uniform, t0..t2 the plane's bit of
+// thr(u) for u = 0, 1, 2 as all-zero / all-one words, m0..m2 the replicas of
+// each u.  eq: replicas whose uniform has matched its threshold so far; acc:
+// replicas decided below it.
+__device__ __forceinline__ void compare_plane(uint32_t r, uint32_t m0, uint32_t m1, uint32_t m2, uint32_t t0,
+                                              uint32_t t1, uint32_t t2, uint32_t& eq, uint32_t& acc) {
+  const uint32_t t = (m0 & t0) | (m1 & t1) | (m2 & t2);
+  acc |= eq & t & ~r;
+  eq &= ~(r ^ t);
+}
+
+// One half-sweep of the rows of partition `part` (parity class p, colour sites at
+// x = X0 mod 2).  spw points at this thread's word of site 0; tp[b] are the
+// thread's hoisted Philox parts of block b for this half-sweep q; g8 = 8 x the
+// thread's global word index (the group of block b is g8 + b).
+template <int L, int W, int NP, int X0>
+__device__ __forceinline__ void sweep_rows_bits(uint32_t* spw, const SiteRec* recs, int part, int p,
+                                                const ThreadPhilox (&tp)[4], uint32_t q, uint32_t g8,
+                                                const SweepArgs& a) {
+  constexpr int H = L / 2, RPP = L * L / NP;
+#pragma unroll 1
+  for (int k = 0; k < RPP; ++k) {
+    const int r = row_index<L, NP>(part, k, p);
+    const int y = r % L, z = r / L;
+    const int yp = y == L - 1 ? 0 : y + 1, ym = y == 0 ? L - 1 : y - 1;
+    const int zp = z == L - 1 ? 0 : z + 1, zm = z == 0 ? L - 1 : z - 1;
+    uint32_t* p0 = spw + (size_t)r * L * W;
+    const uint32_t* pyp = spw + (size_t)(yp + L * z) * L * W;
+    const uint32_t* pym = spw + (size_t)(ym + L * z) * L * W;
+    const uint32_t* pzp = spw + (size_t)(y + L * zp) * L * W;
+    const uint32_t* pzm = spw + (size_t)(y + L * zm) * L * W;
+    const SiteRec* rr = recs + r * L;
+    const uint32_t h0 = (uint32_t)(r * L) >> 1;
+#pragma unroll 1
+    for (int xh = 0; xh < H; ++xh) {
+      const int x = 2 * xh + X0;
+      const int xp = x == L - 1 ? 0 : x + 1, xm = x == 0 ? L - 1 : x - 1;
+      const SiteRec sr = rr[x];
+      const uint32_t s0 = p0[x * W];
+      // unsatisfied bonds (one bit per replica) and their count u in three planes
+      const uint32_t b0 = s0 ^ p0[xp * W] ^ sr.jxp, b1 = s0 ^ p0[xm * W] ^ sr.jxm;
+      const uint32_t b2 = s0 ^ pyp[x * W] ^ sr.jyp, b3 = s0 ^ pym[x * W] ^ sr.jym;
+      const uint32_t b4 = s0 ^ pzp[x * W] ^ sr.jzp, b5 = s0 ^ pzm[x * W] ^ sr.jzm;
+      const uint32_t sa = b0 ^ b1 ^ b2, ca = majority(b0, b1, b2);
+      const uint32_t sb = b3 ^ b4 ^ b5, cb = majority(b3, b4, b5);
+      const uint32_t u0 = sa ^ sb, k2 = sa & sb;
+      const uint32_t u1 = ca ^ cb ^ k2, u2 = majority(ca, cb, k2);
+      const uint32_t always = u2 | (u1 & u0);  // u >= 3: dE <= 0
+      const uint32_t m0 = ~(u0 | u1 | u2);      // u = 0: dE = 12
+      const uint32_t m1 = u0 & ~(u1 | u2);      // u = 1: dE = 8
+      const uint32_t m2 = u1 & ~(u0 | u2);      // u = 2: dE = 4
+      uint32_t eq = (m0 & a.live[0]) | (m1 & a.live[1]) | (m2 & a.live[2]);
+      uint32_t acc = 0;
+      const uint32_t h = h0 + (uint32_t)xh;
+      {
+        uint32_t w0[4], w1[4];
+        philox_block(h, sr, tp[0], a.k0, a.k1, w0);
+        philox_block(h, sr, tp[1], a.k0, a.k1, w1);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) compare_plane(w0[i], m0, m1, m2, a.tm[i][0], a.tm[i][1], a.tm[i][2], eq, acc);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          compare_plane(w1[i], m0, m1, m2, a.tm[4 + i][0], a.tm[4 + i][1], a.tm[4 + i][2], eq, acc);
+      }
+      if (eq) {
+        uint32_t w[4];
+        philox_block(h, sr, tp[2], a.k0, a.k1, w);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          compare_plane(w[i], m0, m1, m2, a.tm[8 + i][0], a.tm[8 + i][1], a.tm[8 + i][2], eq, acc);
+      }
+      if (eq) {
+        uint32_t w[4];
+        philox_block(h, sr, tp[3], a.k0, a.k1, w);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          compare_plane(w[i], m0, m1, m2, a.tm[12 + i][0], a.tm[12 + i][1], a.tm[12 + i][2], eq, acc);
+      }
+#pragma unroll 1
+      for (int b = 4; b < 8 && eq; ++b) {  // rare: some replica matched its threshold for 16 bits
+        const ThreadPhilox tb = thread_philox(g8 + (uint32_t)b, q, a.k0, a.k1);
+        uint32_t w[4];
+        philox_block(h, sr, tb, a.k0, a.k1, w);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const uint32_t* tmp = a.tm[4 * b + i];
+          compare_plane(w[i], m0, m1, m2, tmp[0], tmp[1], tmp[2], eq, acc);
+        }
+      }
+      p0[x * W] = s0 ^ (acc | always);
+    }
+  }
+}
+
+// Gather the tile's spins from the parents of its slots into bit words; spar
+// holds the tile's parents (-1 past R~), slot i at index 33 (i >> 5) + (i & 31).
+template <int L, int W, int NP>
+__device__ __forceinline__ void gather_bits(const SweepArgs& a, uint32_t* sp, const int* spar, int word, int part) {
+  constexpr int N = L * L * L;
+  int par[32];
+#pragma unroll
+  for (int b = 0; b < 32; ++b) par[b] = spar[33 * word + b];
+  bool contiguous = par[0] >= 0 && (par[0] & 15) == 0;
+#pragma unroll
+  for (int b = 1; b < 32; ++b) contiguous = contiguous && par[b] == par[0] + b;
+  const int8_t* src = a.pop.spins[a.cur];
+  for (int n = part; n < N; n += NP) {
+    const int8_t* row = src + (size_t)n * a.pitch;
+    uint32_t bits = 0;
+    if (contiguous) {
+      const uint4* v = reinterpret_cast<const uint4*>(row + par[0]);
+      const uint4 lo = v[0], hi = v[1];
+      const uint32_t q8[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)  // bit 1 of each byte is the sign; gather four of them
+        bits |= ((((q8[i] >> 1) & 0x01010101u) * 0x01020408u) >> 24) << (4 * i);
+    } else {
+#pragma unroll
+      for (int b = 0; b < 32; ++b)
+        if (par[b] >= 0) bits |= (((uint32_t)(uint8_t)row[par[b]] >> 1) & 1u) << b;
+    }
+    sp[n * W + word] = bits;
+  }
+}
+
+// Unsatisfied forward bonds of every replica of the tile, counted per thread in
+// CB bit planes and then added per replica into ecnt (slot i at index i).
+template <int L, int W, int NP, int CB>
+__device__ __forceinline__ void count_levels_bits(const uint32_t* sp, const SiteRec* recs, int* ecnt, int word,
+                                                  int part) {
+  constexpr int ROWS = L * L;
+  uint32_t c[CB];
+#pragma unroll
+  for (int i = 0; i < CB; ++i) c[i] = 0;
+  for (int r = part; r < ROWS; r += NP) {
+    const int y = r % L, z = r / L;
+    const int yp = y == L - 1 ? 0 : y + 1, zp = z == L - 1 ? 0 : z + 1;
+    const uint32_t* p0 = sp + (size_t)r * L * W + word;
+    const uint32_t* pyp = sp + (size_t)(yp + L * z) * L * W + word;
+    const uint32_t* pzp = sp + (size_t)(y + L * zp) * L * W + word;
+    const SiteRec* rr = recs + r * L;
+#pragma unroll
+    for (int x = 0; x < L; ++x) {
+      const int xp = x == L - 1 ? 0 : x + 1;
+      const uint32_t s0 = p0[x * W];
+      const uint32_t e0 = s0 ^ p0[xp * W] ^ rr[x].jxp, e1 = s0 ^ pyp[x * W] ^ rr[x].jyp,
+                     e2 = s0 ^ pzp[x * W] ^ rr[x].jzp;
+      const uint32_t sum = e0 ^ e1 ^ e2, two = majority(e0, e1, e2);  // e0 + e1 + e2 = sum + 2 two
+      uint32_t carry = c[0] & sum;
+      c[0] ^= sum;
+      const uint32_t c1 = c[1] ^ two ^ carry;
+      carry = majority(c[1], two, carry);
+      c[1] = c1;
+#pragma unroll
+      for (int i = 2; i < CB; ++i) {
+        const uint32_t ci = c[i] ^ carry;
+        carry &= c[i];
+        c[i] = ci;
+      }
+    }
+  }
+#pragma unroll 1
+  for (int bb = 0; bb < 32; ++bb) {
+    const int b = (bb + word) & 31;  // lanes of a warp hit different banks
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < CB; ++i) k |= (int)((c[i] >> b) & 1u) << i;
+    if (k) atomicAdd(&ecnt[32 * word + b], k);
+  }
+}
+
+// Write the tile back as int8 +1 (0x01) / -1 (0xFF), 32 slots per word.
+template <int L, int W, int NP>
+__device__ __forceinline__ void store_bits(const SweepArgs& a, const uint32_t* sp, int tile0, int word, int part) {
+  constexpr int N = L * L * L;
+  int8_t* dst = a.pop.spins[1 - a.cur];
+  for (int n = part; n < N; n += NP) {
+    const uint32_t w = sp[n * W + word];
+    uint32_t q8[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {  // four bits -> bit 0 of four bytes -> 0x01 / 0xFF
+      const uint32_t m = (((w >> (4 * i)) & 15u) * 0x00204081u) & 0x01010101u;
+      q8[i] = m * 0xFEu + 0x01010101u;
+    }
+    uint4* out = reinterpret_cast<uint4*>(dst + (size_t)n * a.pitch + tile0 + 32 * word);
+    out[0] = make_uint4(q8[0], q8[1], q8[2], q8[3]);
+    out[1] = make_uint4(q8[4], q8[5], q8[6], q8[7]);
+  }
+}
+
+// Bit-sliced sweep kernel (+-1 couplings).
 template <int L, int W, int NT, int MB>
 __global__ void __launch_bounds__(NT, MB) k_sweep(const __grid_constant__ SweepArgs a) {
-  using S = SweepShape<L, W, NT>;
+  using S = BitShape<L, W, NT>;
   constexpr int N = S::N, NP = S::NP, TJ = S::TJ;
   extern __shared__ __align__(16) uint32_t sm[];
   uint32_t* sp = sm;                                               // spins [N][W]
   SiteRec* recs = reinterpret_cast<SiteRec*>(sm + (size_t)N * W);  // [N]
-  int* ecnt = reinterpret_cast<int*>(recs + N);                    // [TJ]
+  int* slots = reinterpret_cast<int*>(recs + N);                   // [33 W]: parents, then level counts
   const int R_new = a.pop.rec[a.t].R_tilde;
   const int tile0 = blockIdx.x * TJ;
   if (tile0 >= R_new) return;
   const int tid = threadIdx.x, word = tid % W, part = tid / W;
   init_tables<L>(a, recs, tid, NT);
-  for (int i = tid; i < TJ; i += NT) ecnt[i] = 0;
-  gather_tile<L, W, NP>(a, sp, tile0, R_new, word, part);
+  for (int i = tid; i < TJ; i += NT) slots[33 * (i >> 5) + (i & 31)] = tile0 + i < R_new ? a.pop.parents[tile0 + i] : -1;
+  __syncthreads();
+  gather_bits<L, W, NP>(a, sp, slots, word, part);
+  __syncthreads();
+  for (int i = tid; i < S::SLOTS; i += NT) slots[i] = 0;
   __syncthreads();
 
   // sweeps: partition `part` owns rows of parity class p = (y + z) & 1; in
   // half-sweep c its colour sites sit at x = p ^ c mod 2 in every row.
-  const uint32_t g = (uint32_t)(tile0 >> 3) + (uint32_t)word;  // Philox group: the word's eight replicas
+  const uint32_t g8 = 8u * ((uint32_t)(tile0 >> 5) + (uint32_t)word);  // Philox group of block 0 of this word
   const int pclass = part / (NP / 2);
   uint32_t* spw = sp + word;
   for (int s = 0; s < a.n_sweeps; ++s) {
 #pragma unroll 1
     for (int c = 0; c < 2; ++c) {
       const uint32_t q = 2u * (uint32_t)s + (uint32_t)c;
-      const ThreadPhilox tp = thread_philox(g, q, a.k0, a.k1);
+      const ThreadPhilox tp[4] = {thread_philox(g8, q, a.k0, a.k1), thread_philox(g8 + 1u, q, a.k0, a.k1),
+                                  thread_philox(g8 + 2u, q, a.k0, a.k1), thread_philox(g8 + 3u, q, a.k0, a.k1)};
       if ((pclass ^ c) == 0)
-        sweep_rows<L, W, NP, 0>(spw, recs, part, pclass, tp, a.k0, a.k1, q, g, (uint32_t)a.t, a.pop.key_tie);
+        sweep_rows_bits<L, W, NP, 0>(spw, recs, part, pclass, tp, q, g8, a);
       else
-        sweep_rows<L, W, NP, 1>(spw, recs, part, pclass, tp, a.k0, a.k1, q, g, (uint32_t)a.t, a.pop.key_tie);
+        sweep_rows_bits<L, W, NP, 1>(spw, recs, part, pclass, tp, q, g8, a);
       __syncthreads();
     }
   }
-  count_levels<L, W, NP>(sp, recs, ecnt, word, part);
+  count_levels_bits<L, W, NP, S::CB>(sp, recs, slots, word, part);
   __syncthreads();
-  publish_levels<TJ>(a, ecnt, tile0, R_new, tid, NT);
-  store_tile<L, W, NP>(a, sp, tile0, word, part);
+  publish_levels<TJ>(a, slots, tile0, R_new, tid, NT);
+  store_bits<L, W, NP>(a, sp, tile0, word, part);
 }
 
 // ---- Gaussian couplings (§II.A): the same tiles, gather, store and Philox words;
@@ -677,7 +696,7 @@ static int launch_g_t(const RunGeom& g, const GSweepArgs& args, cudaStream_t s) 
 
 template <int L, int W, int NT, int MB>
 static int launch_t(const RunGeom& g, const SweepArgs& args, cudaStream_t s) {
-  using S = SweepShape<L, W, NT>;
+  using S = BitShape<L, W, NT>;
   cudaError_t e =
       cudaFuncSetAttribute(k_sweep<L, W, NT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
   if (e != cudaSuccess) return (int)e;
@@ -688,27 +707,25 @@ static int launch_t(const RunGeom& g, const SweepArgs& args, cudaStream_t s) {
 
 namespace {
 
-// Candidate launch shapes: words per site row W (8W replicas per tile),
-// threads per CTA, CTAs per SM the kernel is compiled for (its register cap).
-// The first entry of each L is the default (the fastest measured on GB300);
-// the autotuner may pick another.  All give identical results.  At L = 14 no
-// shape with whole warps keeps 8W | 256 and fits: 784 and 392 threads leave a
-// partial last warp and one warp whose rows straddle the two parity classes
-// (it runs both colour offsets; still far faster than 224 threads).
+// Candidate launch shapes of the +-1 sweep: words per site row W (32W replicas
+// per tile), threads per CTA, CTAs per SM the kernel is compiled for (its
+// register cap).  The first entry of each L is the default; the autotuner may
+// pick another.  All give identical results.  At L = 14 the partitions of a
+// warp may straddle the two parity classes (it then runs both colour offsets).
 struct ShapeEntry {
   int L, W, NT, MB;
   size_t smem;
   int (*launch)(const RunGeom&, const SweepArgs&, cudaStream_t);
 };
-#define PA_SHAPE(L, W, NT, MB) {L, W, NT, MB, SweepShape<L, W, NT>::SMEM, &launch_t<L, W, NT, MB>}
+#define PA_SHAPE(L, W, NT, MB) {L, W, NT, MB, BitShape<L, W, NT>::SMEM, &launch_t<L, W, NT, MB>}
 const ShapeEntry kShapes[] = {
-    PA_SHAPE(2, 32, 128, 1),
-    PA_SHAPE(4, 32, 256, 3),   PA_SHAPE(4, 32, 256, 1),  PA_SHAPE(4, 32, 512, 2),
-    PA_SHAPE(6, 32, 384, 2),   PA_SHAPE(6, 32, 384, 1),  PA_SHAPE(6, 32, 576, 1),
-    PA_SHAPE(8, 32, 512, 2),   PA_SHAPE(8, 32, 512, 1),  PA_SHAPE(8, 32, 256, 2),
-    PA_SHAPE(10, 32, 640, 1),  PA_SHAPE(10, 16, 320, 2),
-    PA_SHAPE(12, 16, 768, 1),  PA_SHAPE(12, 16, 576, 1), PA_SHAPE(12, 8, 384, 2),
-    PA_SHAPE(14, 8, 784, 1),   PA_SHAPE(14, 4, 392, 1),
+    PA_SHAPE(2, 32, 128, 1),   PA_SHAPE(2, 32, 64, 2),
+    PA_SHAPE(4, 32, 256, 2),   PA_SHAPE(4, 32, 128, 4),  PA_SHAPE(4, 32, 512, 1),
+    PA_SHAPE(6, 32, 384, 2),   PA_SHAPE(6, 32, 192, 4),  PA_SHAPE(6, 32, 576, 1),
+    PA_SHAPE(8, 32, 256, 2),   PA_SHAPE(8, 32, 512, 1),  PA_SHAPE(8, 16, 256, 4),
+    PA_SHAPE(10, 32, 640, 1),  PA_SHAPE(10, 16, 320, 2), PA_SHAPE(10, 16, 800, 1),
+    PA_SHAPE(12, 16, 576, 1),  PA_SHAPE(12, 16, 768, 1), PA_SHAPE(12, 8, 384, 2),
+    PA_SHAPE(14, 8, 784, 1),   PA_SHAPE(14, 8, 224, 1),  PA_SHAPE(14, 4, 392, 1),
     PA_SHAPE(16, 4, 512, 1),   PA_SHAPE(16, 4, 1024, 1),
 };
 #undef PA_SHAPE
@@ -766,6 +783,13 @@ int launch_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, 
     args.thr4 = met_thr[0];
     args.thr8 = met_thr[1];
     args.thr12 = met_thr[2];
+    const uint32_t thr_u[3] = {met_thr[2], met_thr[1], met_thr[0]};  // u = 0, 1, 2: dE = 12, 8, 4
+    for (int p = 0; p < 32; ++p) {
+      for (int u = 0; u < 3; ++u) args.tm[p][u] = ((thr_u[u] >> (31 - p)) & 1u) ? ~0u : 0u;
+      args.tm[p][3] = 0u;
+    }
+    for (int u = 0; u < 3; ++u) args.live[u] = thr_u[u] ? ~0u : 0u;
+    args.live[3] = 0u;
     const int e = shape->launch(g, args, s);
     if (e != 0) return e;
   }

@@ -5,11 +5,12 @@
 // global memory; the energy levels are counted afterwards by k_levels_and_hist.
 //
 // Layout as everywhere: int8 spins +1 = 0x01 / -1 = 0xFF, site-major rows of
-// pitch bytes, so one 64-bit word holds eight replicas of one site and one
-// thread updates those eight with one Philox4x32-10 block: counter (n >> 1,
-// 2s + c, j >> 3, t), half j & 1 of word (j & 7) >> 1 for slot j, with the
-// tie-break block under its own key when a 16-bit uniform equals the top half
-// of its threshold (the acceptance rule of the shared-memory sweep).
+// pitch bytes; one thread updates eight replicas (one 64-bit word) of one site.
+// The acceptance test is the tile kernel's: a replica's 32-bit uniform is its bit
+// column (bit 31 - p is bit j & 31 of word p & 3 of Philox4x32-10 at counter
+// (n >> 1, 2s + c, 8 (j >> 5) + p / 4, t)), compared with its threshold from the
+// top bit down until the first differing bit; the thread draws blocks until its
+// eight replicas are decided.
 #include <cuda_runtime.h>
 
 #include "pa_device.cuh"
@@ -82,31 +83,39 @@ __global__ void __launch_bounds__(kThreads) k_sweep_global(RunGeom g, PopDev P, 
                  jzp = jtab[4 * n + 2], jzm = jtab[4 * zm + 2];
   const uint32_t u2[2] = {unsatisfied2(s0.x, sxp.x, sxm.x, syp.x, sym.x, szp.x, szm.x, jxp, jxm, jyp, jym, jzp, jzm),
                           unsatisfied2(s0.y, sxp.y, sxm.y, syp.y, sym.y, szp.y, szm.y, jxp, jxm, jyp, jym, jzp, jzm)};
-  const uint4 ctr = make_uint4((uint32_t)(n >> 1), (uint32_t)(2 * s + c), (uint32_t)wi, (uint32_t)t);
-  const uint4 rw = philox4x32_10(ctr, P.key_met[0], P.key_met[1]);
-  uint32_t flip[2] = {0u, 0u};
-  bool have_tie = false;
-  uint4 rt = make_uint4(0u, 0u, 0u, 0u);
+  const uint32_t j0 = 8u * (uint32_t)wi, sh = j0 & 31u;  // slots j0 .. j0 + 7: bits sh .. sh + 7 of the words
+  uint32_t thr[8], undecided = 0, accept = 0;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const uint32_t u = (u2[i >> 2] >> (8 * (i & 3) + 1)) & 0xFu;  // 0..6; flipping costs dE = 12 - 4u
-    bool accept = u >= 3;
-    if (!accept) {
-      const uint32_t thr = u == 2 ? thr4 : u == 1 ? thr8 : thr12;
-      const uint32_t w = word_of(rw, i >> 1);
-      const uint32_t U = (i & 1) ? w >> 16 : w & 0xFFFFu;
-      accept = U < (thr >> 16);
-      if (U == (thr >> 16)) {
-        if (!have_tie) {
-          rt = philox4x32_10(ctr, P.key_tie[0], P.key_tie[1]);
-          have_tie = true;
+    thr[i] = u == 2 ? thr4 : u == 1 ? thr8 : thr12;
+    if (u >= 3)
+      accept |= 1u << i;
+    else if (thr[i] != 0)
+      undecided |= 1u << i;
+  }
+  for (int b = 0; b < 8 && undecided; ++b) {
+    const uint4 rw = philox4x32_10(make_uint4((uint32_t)(n >> 1), (uint32_t)(2 * s + c), 8u * (j0 >> 5) + (uint32_t)b,
+                                              (uint32_t)t),
+                                   P.key_met[0], P.key_met[1]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int p = 4 * b + k;
+      const uint32_t bits = word_of(rw, k) >> sh;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const uint32_t rb = (bits >> i) & 1u, tb = (thr[i] >> (31 - p)) & 1u;
+        if (((undecided >> i) & 1u) && rb != tb) {
+          undecided &= ~(1u << i);
+          if (tb) accept |= 1u << i;
         }
-        const uint32_t wt = word_of(rt, i >> 1);
-        accept = ((i & 1) ? wt >> 16 : wt & 0xFFFFu) < (thr & 0xFFFFu);
       }
     }
-    if (accept) flip[i >> 2] |= 0xFEu << (8 * (i & 3));
   }
+  uint32_t flip[2] = {0u, 0u};
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    if ((accept >> i) & 1u) flip[i >> 2] |= 0xFEu << (8 * (i & 3));
   S[n * pw + wi] = make_uint2(s0.x ^ flip[0], s0.y ^ flip[1]);
 }
 

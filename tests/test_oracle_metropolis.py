@@ -69,22 +69,32 @@ def test_sweep_replica_is_deterministic_and_seeded(oracle_lib):
     assert dEz <= 0
 
 
-@pytest.mark.parametrize("thr", [0, 1, 0xFFFF, 0x10000, 0x10001, 0x1234ABCD, 0x8000FFFF, 0xFFFF0000, 0xFFFFFFFE,
-                                 0xFFFFFFFF])
-def test_two_stage_acceptance_has_the_probability_of_one_32bit_uniform(oracle_lib, thr):
-    """Over all 16-bit U (the replica's uniform) and V (its tie-break uniform) the
-    rule accepts exactly thr of the 2^32 pairs, i.e. with probability thr / 2^32,
-    the same as one 32-bit uniform below thr; and V matters only when U equals
-    the top half of thr."""
-    accept = oracle_lib.metropolis_accept
-    rng = np.random.default_rng(thr & 0xFFFF)
-    top = thr >> 16
-    total = 0
-    for U in range(1 << 16):
-        if U == top:
-            total += sum(accept(U, V, thr) for V in range(1 << 16))
-        else:
-            a = accept(U, 0, thr)
-            assert a == accept(U, 0xFFFF, thr) == accept(U, int(rng.integers(1 << 16)), thr)
-            total += (1 << 16) * a
-    assert total == thr
+def test_bitwise_test_is_the_comparison_of_the_whole_uniform(oracle_lib):
+    """The sweep's test reads the uniform from its top bit and stops at the first bit
+    that differs from the threshold; that must be exactly uniform < thr, also for
+    thresholds equal to the uniform, one off, 0 and 2^32 - 1."""
+    rng = np.random.default_rng(11)
+    for _ in range(300):
+        seed, pop, site, hs, slot, t = (int(rng.integers(1, 2 ** 40)), int(rng.integers(0, 2)),
+                                        int(rng.integers(0, 2 ** 15)), int(rng.integers(0, 40)),
+                                        int(rng.integers(0, 10 ** 6)), int(rng.integers(0, 200)))
+        r = oracle_lib.metropolis_uniform(seed, pop, site, hs, slot, t)
+        for thr in {0, 1, 0xFFFFFFFF, r, max(r - 1, 0), min(r + 1, 0xFFFFFFFF), r ^ 0x80000000, r >> 7,
+                    int(rng.integers(0, 2 ** 32))}:
+            assert oracle_lib.metropolis_test(seed, pop, site, hs, slot, t, thr) == (r < thr), (r, thr)
+
+
+def test_bit_column_uniforms_are_uniform_and_independent_between_slots(oracle_lib):
+    """The uniforms of the 32 slots that share the stream's words are bit columns of
+    the same Philox blocks: each must still be uniform (Kolmogorov-Smirnov) and
+    uncorrelated with its neighbours in the word, and slot 32 (the next group of
+    blocks) and the next half-sweep must give other numbers."""
+    n = 400
+    u = np.array([[oracle_lib.metropolis_uniform(77, 0, site, 3, slot, 5) for slot in range(34)]
+                  for site in range(n)], dtype=np.float64) / 2.0 ** 32
+    for slot in (0, 1, 13, 31, 32, 33):
+        assert stats.kstest(u[:, slot], "uniform").pvalue > 1e-4
+    for a, b in ((0, 1), (5, 6), (30, 31), (31, 32), (0, 32)):
+        assert abs(np.corrcoef(u[:, a], u[:, b])[0, 1]) < 5 / np.sqrt(n)
+    assert oracle_lib.metropolis_uniform(77, 0, 9, 3, 0, 5) != oracle_lib.metropolis_uniform(77, 0, 9, 4, 0, 5)
+    assert oracle_lib.metropolis_uniform(77, 0, 9, 3, 0, 5) != oracle_lib.metropolis_uniform(77, 1, 9, 3, 0, 5)

@@ -28,8 +28,8 @@ def test_shapes_follow_the_tiling_rules(pa, L):
         assert 32 % W == 0 and NT % W == 0 and NT <= 1024   # a partial last warp is allowed (L = 14)
         NP = NT // W                                   # row partitions
         assert NP % 2 == 0 and (L * L // 2) % (NP // 2) == 0
-        assert 8 * W <= 256                            # a tile never crosses the 256-slot pitch unit
-        assert s["smem_bytes"] == N * W * 4 + N * 32 + 8 * W * 4
+        assert 1024 % (32 * W) == 0                    # a tile never crosses the 1024-slot pitch unit
+        assert s["smem_bytes"] == N * W * 4 + N * 32 + 33 * W * 4   # bit words, site records, slot table
         assert s["smem_bytes"] <= SMEM_PER_CTA
         assert MB * (s["smem_bytes"] + RESERVED_PER_CTA) <= SMEM_PER_SM
         assert MB * NT <= 2048
