@@ -41,21 +41,22 @@ if ROOT not in sys.path:
 
 METRIC = "Metropolis updates/s (L=10,R=1e6)"
 UNIT = "updates/s"
-# Roofline of the sweep kernels: the 32x32->64 integer multiply.  Philox4x32-10
-# with the counter (site, half-sweep, group, step) needs 16 such multiplies per
-# block once rounds 1-2 are hoisted (they depend only on the site or only on the
-# thread).  The +-1 sweep reads 16 bits per update (one block for eight replicas,
-# the tie-break block only on a tie, probability 2^-16), i.e. 2 per update; the
-# Gaussian sweep reads a 32-bit word per update, i.e. 4.  An SM issues 32 of them
-# per clock (the "mulwide" probe of include/pa_bench.h measures it).
-WIDE_MULS_PER_UPDATE = 2
-WIDE_MULS_PER_UPDATE_GAUSS = 4
-WIDE_MULS_PER_CLK_PER_SM = 32
+# Rooflines of the sweep kernels: instruction issue.  For the +-1 kernel, whose
+# instructions are logic (LOP3, ISETP, SHF, ...) and integer multiplies (IMAD, the
+# 32x32->64 IMAD.WIDE of Philox), these share 16 lanes per clock per SM
+# sub-partition, 64 thread-operations per clock per SM: LOP3 alone, IMAD alone
+# and 64-bit-multiply + LOP3 pairs all reach 2.0e13/s on 152 SMs at 2.07 GHz, and
+# logic added to a multiply-bound Philox loop adds its own time (probes of
+# include/pa_bench.h).  The Gaussian kernel's mix also holds full-rate adds and
+# FP32 products, so its bound is the issue slot: one warp instruction per clock
+# per scheduler.  The work of one update (instructions per update, ncu) and the
+# rate are read from each kernel's committed profile summary.
 # HBM bytes per update of the sweep kernel: the tile is read (gather) and
 # written once per step, i.e. 2 bytes per site and replica every S sweeps, plus
 # 8 bytes of parent index and energy level per replica.
 
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sweep_L10_R1e6_adaptive.txt")
+GAUSS_PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sweep_gauss_L10_R1e6_linear101.txt")
 SWEEP_SOURCE = os.path.join(ROOT, "paper_1711_02146_gb300", "csrc", "pa_sweep.cu")
 
 
@@ -219,18 +220,26 @@ def reference_arm(args):
 
 # ---------------------------------------------------------------- GPU arm
 
+def profile_lines(path: str):
+    """The machine-read `key: value` lines of a committed profile summary."""
+    vals = {}
+    if os.path.exists(path):
+        for line in open(path):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    return vals
+
+
+def source_digest() -> str:
+    return hashlib.sha256(open(SWEEP_SOURCE, "rb").read()).hexdigest()[:16]
+
+
 def profile_traffic(kernel: str = "k_sweep<10,32,640,1>"):
     """DRAM bytes per sweep launch from the committed ncu summary, if it was taken
     on the current sweep kernel source and the launch shape in use (else None)."""
-    if not os.path.exists(PROFILE_SUMMARY):
-        return None
-    digest = hashlib.sha256(open(SWEEP_SOURCE, "rb").read()).hexdigest()[:16]
-    vals = {}
-    for line in open(PROFILE_SUMMARY):
-        if ":" in line:
-            k, v = line.split(":", 1)
-            vals[k.strip()] = v.strip()
-    if vals.get("sweep_source_sha256_16") != digest:
+    vals = profile_lines(PROFILE_SUMMARY)
+    if vals.get("sweep_source_sha256_16") != source_digest():
         return None
     if vals.get("sweep_kernel", "k_sweep<10,32,640,1>") != kernel:
         return None
@@ -238,6 +247,27 @@ def profile_traffic(kernel: str = "k_sweep<10,32,640,1>"):
         return float(vals["dram_bytes_per_full_launch"])
     except (KeyError, ValueError):
         return None
+
+
+def ops_per_update(path: str):
+    """(instructions per update, instructions per clock per SM, their kind, whether they
+    were profiled on the current source) from a committed profile summary."""
+    vals = profile_lines(path)
+    try:
+        return (float(vals["ops_per_update"]), float(vals["ops_per_clk_per_sm"]), vals.get("ops_kind", ""),
+                vals.get("sweep_source_sha256_16") == source_digest())
+    except (KeyError, ValueError):
+        return None, None, "", False
+
+
+def issue_peak(n_sm: int, sm_mhz: float, path: str):
+    """Issue roofline in Gupdates/s and its basis, for the kernel profiled in path."""
+    ops, per_clk, kind, current = ops_per_update(path)
+    if ops is None:
+        return None, "no instruction count profiled"
+    peak = n_sm * per_clk * sm_mhz * 1e6 / ops / 1e9
+    return peak, (f"{n_sm} SMs x {per_clk:.0f} thread instructions/clk x {sm_mhz:.0f} MHz / {ops:.3f} {kind} "
+                  f"per update (ncu, {'this source' if current else 'an earlier source of the kernel'})")
 
 
 def reduce_over_ranks(ms: float, updates: float, dist=None, device: str = "cpu"):
@@ -375,7 +405,7 @@ def gaussian_workload():
                     betas=linear_betas(101, 5.0), n_sweeps=10, model=1)
 
 
-def gaussian_measurement(pa, steps: int, warmup: int, peak: float, cpu: bool, R: int = 0):
+def gaussian_measurement(pa, steps: int, warmup: int, n_sm: int, cpu: bool, R: int = 0):
     """Whole-step and sweep-kernel updates/s of the Gaussian-coupling model, and
     the Gaussian oracle timed on a sample of the same run."""
     import torch
@@ -405,10 +435,11 @@ def gaussian_measurement(pa, steps: int, warmup: int, peak: float, cpu: bool, R:
     sweep_ms = st["phase_ms"]["sweep"] / max(st["phase_count"]["sweep"], 1)
     per_launch = st["updates"] / max(st["phase_count"]["sweep"], 1)
     achieved = per_launch / (sweep_ms / 1e3) / 1e9
+    peak, peak_basis = issue_peak(n_sm, 2070.0, GAUSS_PROFILE_SUMMARY)
     out = {"workload": w.name, "steps_timed": f"temperature steps {warmup + 1}..{warmup + done}",
            "value": st["updates"] / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / max(done, 1),
-           "sweep": {"achieved": achieved, "peak": peak, "unit": "Gupdates/s", "frac": achieved / peak,
-                     "launch_ms": sweep_ms, "kernel": "k_sweep_g<10,32,640,1>"},
+           "sweep": {"achieved": achieved, "peak": peak, "unit": "Gupdates/s", "frac": achieved / peak if peak else None,
+                     "peak_basis": peak_basis, "launch_ms": sweep_ms, "kernel": "k_sweep_g<10,32,640,1>"},
            "phase_share": {k: v / max(ms, 1e-9) for k, v in st["phase_ms"].items()},
            "last_step": {"beta": o["beta"], "R_tilde": o["R_tilde"], "mean_E_per_spin": o["mean_E"] / w.N,
                          "rho_t": o["rho_t"]}}
@@ -452,8 +483,7 @@ def ours(args):
     build.build()
     if args.gaussian_only:
         n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-        peak = n_sm * (WIDE_MULS_PER_CLK_PER_SM / WIDE_MULS_PER_UPDATE_GAUSS) * 2070.0 * 1e6 / 1e9
-        print(json.dumps(gaussian_measurement(pa, args.gaussian_steps, args.warmup, peak, cpu=False,
+        print(json.dumps(gaussian_measurement(pa, args.gaussian_steps, args.warmup, n_sm, cpu=False,
                                               R=args.gaussian_R)), flush=True)
         return
     w = C3.with_(run_seed=C3.run_seed + 7919 * rank)
@@ -519,7 +549,7 @@ def ours(args):
     sweep_ms = st["phase_ms"]["sweep"] / max(st["phase_count"]["sweep"], 1)
     updates_per_launch = st["updates"] / max(st["phase_count"]["sweep"], 1)
     sm_mhz = clk["sm_mhz"] if clk else 2070.0
-    peak = n_sm * (WIDE_MULS_PER_CLK_PER_SM / WIDE_MULS_PER_UPDATE) * sm_mhz * 1e6 / 1e9   # Gupdates/s
+    peak, peak_basis = issue_peak(n_sm, sm_mhz, PROFILE_SUMMARY)   # Gupdates/s
     achieved = updates_per_launch / (sweep_ms / 1e3) / 1e9
     kernel = f"k_sweep<{w.L},{shape['words']},{shape['threads']},{shape['ctas_per_sm']}>"
     traffic = profile_traffic(kernel)
@@ -529,12 +559,11 @@ def ours(args):
     hbm_bytes = 2.0 * w.N * replicas + 8.0 * replicas
     hbm_peak = measured_hbm_gbs()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gupdates/s",
-                "frac": achieved / peak, "traffic": traffic,
+                "frac": achieved / peak if peak else None, "traffic": traffic,
                 "kernel": kernel,
                 "launch_ms": sweep_ms, "updates_per_launch": updates_per_launch,
-                "peak_basis": f"{n_sm} SMs x {WIDE_MULS_PER_CLK_PER_SM} 64-bit multiplies/clk / "
-                              f"{WIDE_MULS_PER_UPDATE} per update x {sm_mhz:.0f} MHz "
-                              f"({'median SM clock sampled during the timed region' if clk else 'max clock, no samples'})",
+                "peak_basis": peak_basis + (" (median SM clock sampled during the timed region)" if clk
+                                            else " (max clock, no samples)"),
                 "algorithmic_bytes_per_launch": hbm_bytes,
                 "hbm_GBps_achieved": hbm_bytes / (sweep_ms / 1e3) / 1e9, "hbm_GBps_peak_measured": hbm_peak}
     phase_share = {k: v / max(ms, 1e-9) for k, v in st["phase_ms"].items()}
@@ -557,8 +586,7 @@ def ours(args):
         free, _ = torch.cuda.mem_get_info()
         line["served"] = served_vs_serial(pa, args.served_requests, int(0.5 * free))
     if rank == 0 and world == 1 and args.gaussian_steps > 0:
-        line["gaussian"] = gaussian_measurement(pa, args.gaussian_steps, args.warmup,
-                                                peak * WIDE_MULS_PER_UPDATE / WIDE_MULS_PER_UPDATE_GAUSS,
+        line["gaussian"] = gaussian_measurement(pa, args.gaussian_steps, args.warmup, n_sm,
                                                 cpu=world == 1 and not args.no_cpu_baseline, R=args.gaussian_R)
     if args.probe:
         line["int_probes_per_s"] = {k: pa.int_throughput(k) for k in pa.PROBES}

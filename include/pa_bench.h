@@ -14,6 +14,10 @@
  *   PA_BENCH_PHILOX    one Philox4x32-10 block (4 words)        counted as 4 words
  *   PA_BENCH_MULWIDE_ADD  mul.wide.u32 + add.u32 (hi + lo)      2 ops
  *   PA_BENCH_LOP3_IADD    lop3.b32 + add.u32                    2 ops
+ *   PA_BENCH_PHILOX_LOP3  one Philox4x32-10 block + 16 independent lop3.b32 on
+ *                         other registers                      counted as 4 words
+ *                         (against PA_BENCH_PHILOX: whether logic work overlaps
+ *                         the multiplies or adds its own time)
  * The pairs tell how the issue of a wide multiply (or a 3-input logic op) and a
  * full-rate add share one scheduler: with no sharing a pair costs the slower of
  * the two, with full sharing the sum.
@@ -36,6 +40,7 @@ extern "C" {
 #define PA_BENCH_PHILOX 4
 #define PA_BENCH_MULWIDE_ADD 5
 #define PA_BENCH_LOP3_IADD 6
+#define PA_BENCH_PHILOX_LOP3 7
 
 int pa_bench_int_throughput(int kind, int64_t iters, int blocks, int threads, double* ms, double* ops);
 

@@ -43,13 +43,20 @@ __global__ void k_probe(int64_t iters, uint32_t seed, uint32_t* out) {
 #pragma unroll
   for (int i = 0; i < 8; ++i) x[i] = gid * 2654435761u + seed + (uint32_t)i * 40503u;
   const uint32_t b = seed ^ 0x9E3779B9u, c = seed + 0x7F4A7C15u;
-  if (KIND == PA_BENCH_PHILOX) {
+  if (KIND == PA_BENCH_PHILOX || KIND == PA_BENCH_PHILOX_LOP3) {
     uint32_t acc = 0;
     for (int64_t it = 0; it < iters; ++it) {
       const uint4 r = pa::philox4x32_10(make_uint4(gid, (uint32_t)it, x[0], seed), b, c);
       acc ^= r.x ^ r.y ^ r.z ^ r.w;
+      if (KIND == PA_BENCH_PHILOX_LOP3) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = lop3_xor(lop3_xor(x[i], b, c), c, b);  // independent of the block
+      }
     }
-    out[gid] = acc;
+    uint32_t fold = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) fold ^= x[i];
+    out[gid] = acc ^ (KIND == PA_BENCH_PHILOX_LOP3 ? fold : 0u);
     return;
   }
   for (int64_t it = 0; it < iters; ++it) {
@@ -103,6 +110,7 @@ extern "C" int pa_bench_int_throughput(int kind, int64_t iters, int blocks, int 
     case PA_BENCH_PHILOX: *ops = 4 * n; return run_probe<PA_BENCH_PHILOX>(iters, blocks, threads, ms);
     case PA_BENCH_MULWIDE_ADD: *ops = 16 * n; return run_probe<PA_BENCH_MULWIDE_ADD>(iters, blocks, threads, ms);
     case PA_BENCH_LOP3_IADD: *ops = 16 * n; return run_probe<PA_BENCH_LOP3_IADD>(iters, blocks, threads, ms);
+    case PA_BENCH_PHILOX_LOP3: *ops = 4 * n; return run_probe<PA_BENCH_PHILOX_LOP3>(iters, blocks, threads, ms);
     default: return PA_ERR_INVALID;
   }
 }

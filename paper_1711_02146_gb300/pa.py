@@ -230,7 +230,8 @@ def resample_counts_noalloc(levels, n_old, fl, thr, n_levels, run_seed, pop, t, 
                                                 parents_cap, n_new, _stream_handle(stream)))
 
 
-PROBES = {"lop3": 0, "iadd": 1, "imad": 2, "mulwide": 3, "philox": 4, "mulwide_add": 5, "lop3_iadd": 6}
+PROBES = {"lop3": 0, "iadd": 1, "imad": 2, "mulwide": 3, "philox": 4, "mulwide_add": 5, "lop3_iadd": 6,
+          "philox_lop3": 7}
 
 
 def int_throughput(kind: str, iters: int = 4096, blocks: int = 0, threads: int = 256):
