@@ -385,10 +385,11 @@ def served_vs_serial(pa, n_req: int, mem_budget: int):
 
 def autotune_shapes(pa, sizes):
     """Selects the sweep kernel's launch shape for every lattice size the bench
-    runs (pa_sweep_autotune on a scratch population of about 1e8 spins)."""
+    runs (pa_sweep_autotune on a scratch population of about 6e8 spins: some four
+    waves of the largest tiles at L = 10)."""
     out = {}
     for L in sorted(sizes):
-        R = max(4096, int(1e8 // L ** 3))
+        R = max(4096, int(6e8 // L ** 3))
         best, ms = pa.sweep_autotune(L, R, launches=3)
         shapes = pa.sweep_shapes(L)
         name = lambda sh: f"W{sh['words']}/T{sh['threads']}/x{sh['ctas_per_sm']}"

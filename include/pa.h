@@ -317,7 +317,10 @@ int pa_restore(const pa_config* cfg, const void* buf, size_t size, void* cuda_st
  * and the CTAs per SM it is compiled for.  Every shape gives bit-identical
  * results (the random words depend on slot and site, never on the tiling); they
  * differ only in speed.  The first shape of each L is the default.  A run uses
- * the shape selected for its L on the current device when it is created. */
+ * the shape selected for its L on the current device when it is created; when
+ * that choice is the default or the autotuner's (not pinned by pa_sweep_select
+ * with an index) and the run's population gives fewer tiles than the device has
+ * SMs, it takes the shape of that L with the most tiles instead. */
 typedef struct {
   int32_t L;
   int32_t words;         /* W: 32-bit words per site row of a tile (32 replicas each) */

@@ -133,6 +133,12 @@ int launch_g_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab
 int launch_g_eps_trial(const RunGeom& g, PopDev* pops, int t, const double* wtab, void* stream);
 int launch_g_measure(const RunGeom& g, PopDev* pops, int cur, int t, unsigned long long* qlhist, void* stream);
 int launch_overlap(const RunGeom& g, PopDev* pops, int cur, int t, unsigned long long* qhist, void* stream);
+}  // namespace pa
+struct pa_ctx;
+namespace pa {
+// A run created for overlapped execution keeps the device's chosen sweep shape
+// (no switch to smaller tiles for a small population).
+void use_chosen_shape(pa_ctx* c);
 // Largest lattice size the sweep kernel supports.
 constexpr int kMaxL = 16;
 // Largest lattice size of a run (larger lattices than kMaxL sweep in global memory).

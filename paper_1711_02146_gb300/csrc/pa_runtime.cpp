@@ -71,6 +71,32 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? PA_OK : PA_ERR_CUDA; 
 // shapes compiled for L; static storage starts at 0, the default shape).
 constexpr int kMaxDevices = 64;
 std::atomic<int32_t> g_sweep_choice[kMaxDevices][pa::kMaxL + 1];
+std::atomic<bool> g_sweep_pinned[kMaxDevices][pa::kMaxL + 1];  // set by pa_sweep_select with an index
+
+// The shape a +-1 run of population capacity R_cap takes: the chosen one, unless it
+// was not pinned and the population gives fewer tiles than the device has SMs; then
+// the shape of that L with the most tiles (every shape gives identical results).
+int run_shape(int L, int64_t R_cap, int dev) {
+  const int chosen = g_sweep_choice[dev][L].load();
+  if (g_sweep_pinned[dev][L].load()) return chosen;
+  int n_sm = 0;
+  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return chosen;
+  auto tiles = [&](int i) {
+    pa::SweepShapeInfo si;
+    if (!pa::sweep_shape_info(L, i, &si)) return (int64_t)0;
+    const int64_t tj = 32LL * si.W;
+    return (R_cap + tj - 1) / tj;
+  };
+  int best = chosen;
+  int64_t best_tiles = tiles(chosen);
+  if (best_tiles >= n_sm) return chosen;
+  for (int i = 0; i < pa::sweep_shape_count(L); ++i)
+    if (tiles(i) > best_tiles) {
+      best = i;
+      best_tiles = tiles(i);
+    }
+  return best;
+}
 
 int current_device(int* dev) {
   int d = 0;
@@ -442,6 +468,15 @@ size_t ckpt_bytes(const RunGeom& g, int t, int n_temps, const int32_t* Rt, const
 
 }  // namespace
 
+namespace pa {
+// Runs overlapped with many others (pa_batch, pa_server) keep the device's chosen
+// sweep shape: their tiles need not fill the GPU by themselves.
+void use_chosen_shape(pa_ctx* c) {
+  int dev = 0;
+  if (c && sweep_supported(c->g.L) && current_device(&dev) == PA_OK) c->g.sweep_shape = g_sweep_choice[dev][c->g.L].load();
+}
+}  // namespace pa
+
 extern "C" {
 
 const char* pa_strerror(int s) {
@@ -539,7 +574,7 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
   g.n_count_blocks = (int32_t)((R_cap + pa::kSlotsPerCountBlock - 1) / pa::kSlotsPerCountBlock);
   g.n_entropy_blocks = (int32_t)((R_cap + pa::kEntropyPerBlock - 1) / pa::kEntropyPerBlock);
   int dev = 0;
-  g.sweep_shape = (pa::sweep_supported(g.L) && current_device(&dev) == PA_OK) ? g_sweep_choice[dev][g.L].load() : 0;
+  g.sweep_shape = (pa::sweep_supported(g.L) && current_device(&dev) == PA_OK) ? run_shape(g.L, R_cap, dev) : 0;
   g.model = cfg->model;
   g.n_chunks = (int32_t)((R_cap + pa::kChunk - 1) / pa::kChunk);
   g.n_measure_blocks = (int32_t)((R_cap + 4095) / 4096);
@@ -1262,6 +1297,7 @@ int pa_sweep_select(int32_t L, int32_t index) {
   const int rc = current_device(&dev);
   if (rc != PA_OK) return rc;
   g_sweep_choice[dev][L].store(index < 0 ? 0 : index);
+  g_sweep_pinned[dev][L].store(index >= 0);
   return PA_OK;
 }
 
@@ -1336,6 +1372,7 @@ int pa_sweep_autotune(int32_t L, int32_t R, int32_t launches, double* ms_per_lau
   if (rc != PA_OK) return rc;
   if (best_i < 0) return PA_ERR_CUDA;
   g_sweep_choice[dev][L].store(best_i);
+  g_sweep_pinned[dev][L].store(false);
   *best = best_i;
   return PA_OK;
 }

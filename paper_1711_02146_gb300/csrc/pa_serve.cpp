@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "../../include/pa.h"
+#include "pa_internal.h"
 
 namespace {
 
@@ -100,6 +101,7 @@ int pa_batch_create(const pa_config* cfgs, int32_t n, pa_batch** out) {
     int rc = make_stream(&s);
     pa_ctx* c = nullptr;
     if (rc == PA_OK) rc = pa_create(&cfgs[i], s, &c);
+    if (rc == PA_OK) pa::use_chosen_shape(c);
     if (rc != PA_OK) {
       if (s) cudaStreamDestroy(s);
       pa_batch_destroy(b);
@@ -203,6 +205,7 @@ int admit(pa_server* s) {
     }
     pa_ctx* c = nullptr;
     const int rc = pa_create(&r.cfg.cfg, st, &c);
+    if (rc == PA_OK) pa::use_chosen_shape(c);
     if (rc != PA_OK) {
       // the request fails on its own; the server keeps serving the others
       pa_server::Finished f;

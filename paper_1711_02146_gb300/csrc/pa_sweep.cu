@@ -710,7 +710,9 @@ namespace {
 // Candidate launch shapes of the +-1 sweep: words per site row W (32W replicas
 // per tile), threads per CTA, CTAs per SM the kernel is compiled for (its
 // register cap).  The first entry of each L is the default; the autotuner may
-// pick another.  All give identical results.  At L = 14 the partitions of a
+// pick another, and a run too small to give every SM a tile takes the shape
+// with the most tiles (the W = 8 entries exist for those).  All give identical
+// results.  At L = 14 the partitions of a
 // warp may straddle the two parity classes (it then runs both colour offsets).
 struct ShapeEntry {
   int L, W, NT, MB;
@@ -720,13 +722,13 @@ struct ShapeEntry {
 #define PA_SHAPE(L, W, NT, MB) {L, W, NT, MB, BitShape<L, W, NT>::SMEM, &launch_t<L, W, NT, MB>}
 const ShapeEntry kShapes[] = {
     PA_SHAPE(2, 32, 128, 1),   PA_SHAPE(2, 32, 64, 2),
-    PA_SHAPE(4, 32, 256, 2),   PA_SHAPE(4, 32, 128, 4),  PA_SHAPE(4, 32, 512, 1),
-    PA_SHAPE(6, 32, 384, 2),   PA_SHAPE(6, 32, 192, 4),  PA_SHAPE(6, 32, 576, 1),
-    PA_SHAPE(8, 32, 256, 2),   PA_SHAPE(8, 32, 512, 1),  PA_SHAPE(8, 16, 256, 4),
-    PA_SHAPE(10, 32, 640, 1),  PA_SHAPE(10, 16, 320, 2), PA_SHAPE(10, 16, 800, 1),
+    PA_SHAPE(4, 32, 256, 2),   PA_SHAPE(4, 32, 128, 4),  PA_SHAPE(4, 32, 512, 1),  PA_SHAPE(4, 8, 128, 4),
+    PA_SHAPE(6, 32, 384, 2),   PA_SHAPE(6, 32, 192, 4),  PA_SHAPE(6, 32, 576, 1),  PA_SHAPE(6, 8, 288, 2),
+    PA_SHAPE(8, 32, 256, 2),   PA_SHAPE(8, 32, 512, 1),  PA_SHAPE(8, 16, 256, 2),  PA_SHAPE(8, 8, 256, 2),
+    PA_SHAPE(10, 32, 640, 1),  PA_SHAPE(10, 16, 320, 2), PA_SHAPE(10, 8, 160, 3),
     PA_SHAPE(12, 16, 576, 1),  PA_SHAPE(12, 16, 768, 1), PA_SHAPE(12, 8, 384, 2),
     PA_SHAPE(14, 8, 784, 1),   PA_SHAPE(14, 8, 224, 1),  PA_SHAPE(14, 4, 392, 1),
-    PA_SHAPE(16, 4, 512, 1),   PA_SHAPE(16, 4, 1024, 1),
+    PA_SHAPE(16, 4, 512, 1),   PA_SHAPE(16, 4, 256, 1),
 };
 #undef PA_SHAPE
 constexpr int kNumShapes = (int)(sizeof(kShapes) / sizeof(kShapes[0]));
