@@ -67,6 +67,7 @@ struct __align__(16) SiteRec {
   uint32_t jzp, jzm, ua, ub;
 };
 
+// Nibble tiles of the Gaussian kernel: 8 replicas per word.
 template <int L, int W, int NT>
 struct SweepShape {
   static constexpr int N = L * L * L;
@@ -162,7 +163,8 @@ __device__ __forceinline__ uint32_t nibbles_to_bytes(uint32_t x) {
   return b * 0xFEu + 0x01010101u;
 }
 
-// ---- phases of a tile shared by both sweep kernels (nt consumer threads take part)
+// ---- phases of a tile: init_tables and publish_levels serve both kernels,
+// gather_tile and store_tile are the Gaussian kernel's (nibble tiles)
 
 // Site records (bond masks, site/step parts of Philox rounds 1-3); all
 // `nthreads` threads of the CTA help.
