@@ -293,7 +293,9 @@ int pa_server_destroy(pa_server* server);
  * counter-based, so there is no generator state): the current population
  * (spins, labels, levels), the step records, level and overlap histograms of
  * steps 0..t, the last copy numbers and parent map, the family-size histogram,
- * and the schedule so far.  A run restored from a checkpoint continues exactly
+ * and the schedule so far; for Gaussian couplings the energies (int64 fixed
+ * point) and Gaussian step records replace levels and level histograms, and the
+ * link-overlap histograms are kept too.  A run restored from a checkpoint continues exactly
  * as the original would have.  The paper has no counterpart (its runs are
  * single CPU jobs); long runs at large R need it.
  *
@@ -304,8 +306,8 @@ int pa_server_destroy(pa_server* server);
 int pa_checkpoint(pa_ctx* ctx, void* buf, size_t cap, size_t* size);
 
 /* Creates a run on cuda_stream from a checkpoint of a run with the same
- * configuration (same sizes, seeds, schedule or adaptive target; a different
- * configuration or a damaged buffer gives PA_ERR_INVALID).  The new context
+ * configuration (same model, sizes, seeds, schedule or adaptive target; a
+ * different configuration or a damaged buffer gives PA_ERR_INVALID).  The new context
  * owns its memory like one from pa_create. */
 int pa_restore(const pa_config* cfg, const void* buf, size_t size, void* cuda_stream, pa_ctx** out);
 

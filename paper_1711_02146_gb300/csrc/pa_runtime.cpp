@@ -438,7 +438,11 @@ void destroy(pa_ctx* c) {
 // histograms of steps 0..t, the spins of the current population (site-major,
 // N rows of R~ bytes), its labels and levels, the copy numbers of the last
 // resampling (R~_{t-1} entries), the parent map (R~ entries) and the family-size
-// histogram (R~ + 1 entries); then the overlap histograms of steps 0..t.
+// histogram (R~ + 1 entries); then the overlap histograms of steps 0..t.  A run
+// with Gaussian couplings stores, per population, the step records and Gaussian
+// step records of steps 0..t, the spins, labels, energies (int64, fixed point),
+// copy numbers, parents and family-size histogram, then the overlap and
+// link-overlap histograms of steps 0..t.
 
 namespace {
 
@@ -451,18 +455,23 @@ struct CkptHeader {
   double eps_target, beta_max;
   int32_t t, done, adaptive, n_sweeps;
   int32_t R_tilde[2], R_prev[2];
+  int32_t model, pad;
   uint64_t total_bytes;
 };
 constexpr char kCkptMagic[8] = {'P', 'A', 'C', 'K', 'P', 'T', '0', '1'};
+constexpr uint32_t kCkptVersion = 2;
 
-size_t ckpt_bytes(const RunGeom& g, int t, int n_temps, const int32_t* Rt, const int32_t* Rp) {
+size_t ckpt_bytes(const RunGeom& g, int model, int t, int n_temps, const int32_t* Rt, const int32_t* Rp) {
   size_t b = sizeof(CkptHeader) + (size_t)n_temps * (sizeof(double) + sizeof(int32_t));
+  const bool gauss = model == PA_MODEL_GAUSS;
   for (int p = 0; p < g.n_pop; ++p) {
-    b += (size_t)(t + 1) * (sizeof(StepRec) + sizeof(uint32_t) * (size_t)g.n_levels);
-    b += (size_t)g.N * (size_t)Rt[p];                         // spins
-    b += sizeof(int32_t) * ((size_t)Rt[p] * 3 + (size_t)Rp[p] + (size_t)Rt[p] + 1);  // labels, levels, parents, counts, mhist
+    b += (size_t)(t + 1) * (sizeof(StepRec) + (gauss ? sizeof(pa::GRec) : sizeof(uint32_t) * (size_t)g.n_levels));
+    b += (size_t)g.N * (size_t)Rt[p];  // spins
+    // labels, levels or energies, parents, counts, family-size histogram
+    b += sizeof(int32_t) * ((size_t)Rt[p] * 2 + (size_t)Rp[p] + (size_t)Rt[p] + 1);
+    b += (gauss ? sizeof(int64_t) : sizeof(int32_t)) * (size_t)Rt[p];
   }
-  b += sizeof(unsigned long long) * (size_t)(t + 1) * (size_t)g.q_bins;
+  b += (gauss ? 2 : 1) * sizeof(unsigned long long) * (size_t)(t + 1) * (size_t)g.q_bins;
   return b;
 }
 
@@ -1123,7 +1132,7 @@ int pa_get_gcouplings(pa_ctx* c, int32_t* Jq, int64_t cap) {
 
 
 int pa_checkpoint(pa_ctx* c, void* buf, size_t cap, size_t* size) {
-  if (!c || !size || c->model != PA_MODEL_PM1) return PA_ERR_INVALID;
+  if (!c || !size) return PA_ERR_INVALID;
   int rc = pa_sync(c);
   if (rc != PA_OK) return rc;
   const RunGeom& g = c->g;
@@ -1136,13 +1145,14 @@ int pa_checkpoint(pa_ctx* c, void* buf, size_t cap, size_t* size) {
     Rt[p] = r.R_tilde;
     Rp[p] = t > 0 ? r.R_prev : 0;
   }
-  const size_t need = ckpt_bytes(g, t, c->cfg.n_temps, Rt, Rp);
+  const bool gauss = c->model == PA_MODEL_GAUSS;
+  const size_t need = ckpt_bytes(g, c->model, t, c->cfg.n_temps, Rt, Rp);
   *size = need;
   if (!buf || cap < need) return PA_ERR_CAPACITY;
   char* o = static_cast<char*>(buf);
   CkptHeader h{};
   std::memcpy(h.magic, kCkptMagic, sizeof h.magic);
-  h.version = 1;
+  h.version = kCkptVersion;
   h.header_bytes = sizeof(CkptHeader);
   h.L = g.L;
   h.n_pop = g.n_pop;
@@ -1162,6 +1172,7 @@ int pa_checkpoint(pa_ctx* c, void* buf, size_t cap, size_t* size) {
     h.R_tilde[p] = Rt[p];
     h.R_prev[p] = Rp[p];
   }
+  h.model = c->model;
   h.total_bytes = need;
   std::memcpy(o, &h, sizeof h);
   o += sizeof h;
@@ -1177,7 +1188,10 @@ int pa_checkpoint(pa_ctx* c, void* buf, size_t cap, size_t* size) {
       o += bytes;
     };
     get(P.rec, sizeof(StepRec) * (size_t)(t + 1));
-    get(P.hist, sizeof(uint32_t) * (size_t)(t + 1) * (size_t)g.n_levels);
+    if (gauss)
+      get(P.grec, sizeof(pa::GRec) * (size_t)(t + 1));
+    else
+      get(P.hist, sizeof(uint32_t) * (size_t)(t + 1) * (size_t)g.n_levels);
     if (rc == PA_OK && R) {
       c->stats.d2h_bytes += (int64_t)(g.N * R);
       rc = cuda_status(cudaMemcpy2DAsync(o, R, P.spins[c->cur], (size_t)g.pitch, R, (size_t)g.N,
@@ -1186,12 +1200,17 @@ int pa_checkpoint(pa_ctx* c, void* buf, size_t cap, size_t* size) {
     }
     o += (size_t)g.N * R;
     get(P.labels[c->cur], sizeof(int32_t) * R);
-    get(P.levels, sizeof(int32_t) * R);
+    if (gauss)
+      get(P.E64, sizeof(int64_t) * R);
+    else
+      get(P.levels, sizeof(int32_t) * R);
     get(P.counts, sizeof(int32_t) * (size_t)Rp[p]);
     get(P.parents, sizeof(int32_t) * R);
     get(P.mhist, sizeof(int32_t) * (R + 1));
   }
-  if (rc == PA_OK) rc = copy_d2h(c, o, c->qhist, sizeof(unsigned long long) * (size_t)(t + 1) * (size_t)g.q_bins);
+  const size_t qbytes = sizeof(unsigned long long) * (size_t)(t + 1) * (size_t)g.q_bins;
+  if (rc == PA_OK) rc = copy_d2h(c, o, c->qhist, qbytes);
+  if (rc == PA_OK && gauss) rc = copy_d2h(c, o + qbytes, c->qlhist, qbytes);
   return rc == PA_OK ? PA_OK : fail(c, rc);
 }
 
@@ -1201,12 +1220,13 @@ int pa_restore(const pa_config* cfg, const void* buf, size_t size, void* cuda_st
   if (!cfg || !buf || size < sizeof(CkptHeader)) return PA_ERR_INVALID;
   CkptHeader h;
   std::memcpy(&h, buf, sizeof h);
-  if (std::memcmp(h.magic, kCkptMagic, sizeof h.magic) != 0 || h.version != 1 ||
+  if (std::memcmp(h.magic, kCkptMagic, sizeof h.magic) != 0 || h.version != kCkptVersion ||
       h.header_bytes != sizeof(CkptHeader) || h.total_bytes != size)
     return PA_ERR_INVALID;
   const int64_t R_cap = cfg->R_cap ? cfg->R_cap : cfg->R + 10 * (int64_t)std::ceil(std::sqrt((double)cfg->R)) + 1024;
   const bool adaptive = cfg->betas == nullptr;
-  if (cfg->model != PA_MODEL_PM1) return PA_ERR_INVALID;
+  if (h.model != cfg->model) return PA_ERR_INVALID;
+  const bool gauss = cfg->model == PA_MODEL_GAUSS;
   if (h.L != cfg->L || h.n_pop != cfg->n_pop || h.q_bins != cfg->q_bins || h.n_temps != cfg->n_temps ||
       h.R != cfg->R || h.R_cap != R_cap || h.disorder_seed != cfg->disorder_seed || h.run_seed != cfg->run_seed ||
       h.adaptive != (adaptive ? 1 : 0) || h.n_sweeps != cfg->n_sweeps || h.t < 0 || h.t >= h.n_temps ||
@@ -1222,7 +1242,7 @@ int pa_restore(const pa_config* cfg, const void* buf, size_t size, void* cuda_st
       pa_destroy(c);
       return PA_ERR_INVALID;
     }
-  if (ckpt_bytes(g, t, h.n_temps, h.R_tilde, h.R_prev) != size) {
+  if (ckpt_bytes(g, h.model, t, h.n_temps, h.R_tilde, h.R_prev) != size) {
     pa_destroy(c);
     return PA_ERR_INVALID;
   }
@@ -1250,7 +1270,10 @@ int pa_restore(const pa_config* cfg, const void* buf, size_t size, void* cuda_st
       in += bytes;
     };
     put(P.rec, sizeof(StepRec) * (size_t)(t + 1));
-    put(P.hist, sizeof(uint32_t) * (size_t)(t + 1) * (size_t)g.n_levels);
+    if (gauss)
+      put(P.grec, sizeof(pa::GRec) * (size_t)(t + 1));
+    else
+      put(P.hist, sizeof(uint32_t) * (size_t)(t + 1) * (size_t)g.n_levels);
     if (rc == PA_OK) {
       c->stats.h2d_bytes += (int64_t)(g.N * R);
       rc = cuda_status(cudaMemcpy2DAsync(P.spins[0], (size_t)g.pitch, in, R, R, (size_t)g.N,
@@ -1259,12 +1282,17 @@ int pa_restore(const pa_config* cfg, const void* buf, size_t size, void* cuda_st
     }
     in += (size_t)g.N * R;
     put(P.labels[0], sizeof(int32_t) * R);
-    put(P.levels, sizeof(int32_t) * R);
+    if (gauss)
+      put(P.E64, sizeof(int64_t) * R);
+    else
+      put(P.levels, sizeof(int32_t) * R);
     put(P.counts, sizeof(int32_t) * (size_t)h.R_prev[p]);
     put(P.parents, sizeof(int32_t) * R);
     put(P.mhist, sizeof(int32_t) * (R + 1));
   }
-  if (rc == PA_OK) rc = copy_h2d(c, c->qhist, in, sizeof(unsigned long long) * (size_t)(t + 1) * (size_t)g.q_bins);
+  const size_t qbytes = sizeof(unsigned long long) * (size_t)(t + 1) * (size_t)g.q_bins;
+  if (rc == PA_OK) rc = copy_h2d(c, c->qhist, in, qbytes);
+  if (rc == PA_OK && gauss) rc = copy_h2d(c, c->qlhist, in + qbytes, qbytes);
   if (rc != PA_OK) {
     pa_destroy(c);
     return rc;

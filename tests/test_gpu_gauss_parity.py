@@ -96,8 +96,7 @@ def test_longer_run_and_sweep_schedule(pa, oracle_lib):
 
 def test_gaussian_runs_refuse_the_pm1_readers(pa):
     run = pa.Run(4, 100, 1, 1, np.linspace(0, 1, 3), model=pa.PA_MODEL_GAUSS)
-    for call in (lambda: run.obs(0), lambda: run.energy_hist(0), lambda: run.checkpoint(),
-                 lambda: run.replicas(0, 0, 5)):
+    for call in (lambda: run.obs(0), lambda: run.energy_hist(0), lambda: run.replicas(0, 0, 5)):
         with pytest.raises(pa.PAError) as e:
             call()
         assert e.value.status == pa.PA_ERR_INVALID

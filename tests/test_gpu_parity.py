@@ -108,6 +108,22 @@ def test_large_lattices_sweep_in_global_memory(pa, oracle_lib, L, R):
         pa.sweep_shapes(L)
 
 
+@pytest.mark.parametrize("L,R", [(4, 900), (10, 700), (18, 50)])
+def test_extreme_temperatures(pa, oracle_lib, L, R):
+    """Thresholds at both ends of the Metropolis test: beta ~ 1e-9 makes every
+    threshold bit 1 for ~28 planes (long runs of the bitwise comparison), beta = 40
+    makes every threshold 0 (no replica compares at all), and a jump between them
+    culls hard.  Tile kernel (L <= 16) and global-memory kernel (L = 18)."""
+    betas = np.array([0.0, 1e-9, 2e-9, 1e-6, 0.3, 1.0, 40.0, 40.0])
+    gpu, ref = make_pair(pa, oracle_lib, L, R, betas, n_sweeps=2, run_seed=17 + L)
+    for t in range(1, len(betas)):
+        assert gpu.step() == 0
+        ref.step()
+        assert np.array_equal(gpu.copy_counts(), ref.last_counts()), f"copy numbers at t={t}"
+        assert_state_equal(gpu, ref, 1, f"L={L} t={t}")
+        assert_obs_equal(gpu.obs(t), ref.obs(t), f"L={L} t={t}")
+
+
 def test_lattices_beyond_64_are_rejected(pa):
     for L in (66, 65, 17):
         with pytest.raises(pa.PAError) as e:
