@@ -281,9 +281,13 @@ typedef struct pa_server pa_server;
 int pa_server_create(size_t mem_budget, int32_t max_active, int32_t steps_per_poll, pa_server** out);
 int pa_server_submit(pa_server* server, const pa_config* cfg, uint64_t* request_id);
 int pa_server_poll(pa_server* server, uint64_t* done_ids, int32_t cap, int32_t* n_done);
-/* Observables of population pop at the last step of a finished request, and
- * that step's index; PA_ERR_STATE if the request has not finished. */
+/* Observables of population pop at the last step of a finished request with +-1
+ * couplings (pa_server_result) or Gaussian couplings (pa_server_gresult), and
+ * that step's index; PA_ERR_STATE if the request has not finished, PA_ERR_INVALID
+ * for a population it does not have or the other model's reader, the request's
+ * own error status if it failed. */
 int pa_server_result(pa_server* server, uint64_t request_id, int32_t pop, pa_obs* out, int32_t* last_step);
+int pa_server_gresult(pa_server* server, uint64_t request_id, int32_t pop, pa_gobs* out, int32_t* last_step);
 /* Requests waiting and running. */
 int pa_server_load(pa_server* server, int32_t* queued, int32_t* active);
 int pa_server_destroy(pa_server* server);

@@ -71,9 +71,11 @@ struct pa_server {
     cudaEvent_t done;
     bool all_issued;
     int n_pop;
+    int model;
   };
   struct Finished {
-    std::vector<pa_obs> obs;  // per population, last step
+    std::vector<pa_obs> obs;    // per population, last step (+-1 couplings)
+    std::vector<pa_gobs> gobs;  // per population, last step (Gaussian couplings)
     int32_t last_step;
     int status;
   };
@@ -168,7 +170,7 @@ int pa_server_create(size_t mem_budget, int32_t max_active, int32_t steps_per_po
 }
 
 int pa_server_submit(pa_server* s, const pa_config* cfg, uint64_t* id) {
-  if (!s || !cfg || !id || cfg->model != PA_MODEL_PM1) return PA_ERR_INVALID;  // results are pa_obs (+-1 runs)
+  if (!s || !cfg || !id) return PA_ERR_INVALID;
   size_t fp = 0;
   int rc = pa_footprint(cfg, &fp);
   if (rc != PA_OK) return rc;
@@ -217,7 +219,7 @@ int admit(pa_server* s) {
       s->queue.pop_front();
       continue;
     }
-    s->active.push_back({r.id, c, st, r.footprint, ev, false, r.cfg.cfg.n_pop});
+    s->active.push_back({r.id, c, st, r.footprint, ev, false, r.cfg.cfg.n_pop, r.cfg.cfg.model});
     s->used += r.footprint;
     s->queue.pop_front();
   }
@@ -252,8 +254,15 @@ int pa_server_poll(pa_server* s, uint64_t* done_ids, int32_t cap, int32_t* n_don
     pa_server::Finished f;
     f.last_step = pa_current_step(a.ctx);
     f.status = pa_sync(a.ctx);
-    f.obs.resize((size_t)a.n_pop);
-    for (int p = 0; p < a.n_pop && f.status == PA_OK; ++p) f.status = pa_observables(a.ctx, f.last_step, p, &f.obs[(size_t)p]);
+    if (a.model == PA_MODEL_GAUSS) {
+      f.gobs.resize((size_t)a.n_pop);
+      for (int p = 0; p < a.n_pop && f.status == PA_OK; ++p)
+        f.status = pa_gobservables(a.ctx, f.last_step, p, &f.gobs[(size_t)p]);
+    } else {
+      f.obs.resize((size_t)a.n_pop);
+      for (int p = 0; p < a.n_pop && f.status == PA_OK; ++p)
+        f.status = pa_observables(a.ctx, f.last_step, p, &f.obs[(size_t)p]);
+    }
     s->finished[a.id] = std::move(f);
     pa_destroy(a.ctx);
     s->free_streams.push_back(a.stream);
@@ -270,8 +279,19 @@ int pa_server_result(pa_server* s, uint64_t id, int32_t pop, pa_obs* out, int32_
   auto it = s->finished.find(id);
   if (it == s->finished.end()) return PA_ERR_STATE;
   if (it->second.status != PA_OK) return it->second.status;
-  if (pop < 0 || (size_t)pop >= it->second.obs.size()) return PA_ERR_INVALID;
+  if (pop < 0 || (size_t)pop >= it->second.obs.size()) return PA_ERR_INVALID;  // also: a Gaussian request
   *out = it->second.obs[(size_t)pop];
+  if (last_step) *last_step = it->second.last_step;
+  return PA_OK;
+}
+
+int pa_server_gresult(pa_server* s, uint64_t id, int32_t pop, pa_gobs* out, int32_t* last_step) {
+  if (!s || !out) return PA_ERR_INVALID;
+  auto it = s->finished.find(id);
+  if (it == s->finished.end()) return PA_ERR_STATE;
+  if (it->second.status != PA_OK) return it->second.status;
+  if (pop < 0 || (size_t)pop >= it->second.gobs.size()) return PA_ERR_INVALID;  // also: a +-1 request
+  *out = it->second.gobs[(size_t)pop];
   if (last_step) *last_step = it->second.last_step;
   return PA_OK;
 }

@@ -169,6 +169,8 @@ SIGNATURES = {
     "pa_server_poll": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "pa_server_result": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(Obs),
                                         ctypes.POINTER(ctypes.c_int32)]),
+    "pa_server_gresult": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(GObs),
+                                         ctypes.POINTER(ctypes.c_int32)]),
     "pa_server_load": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "pa_server_destroy": (ctypes.c_int, [_vp]),
     "pa_gobservables": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(GObs)]),
@@ -389,6 +391,13 @@ class Server:
         o = Obs()
         t = ctypes.c_int32()
         _check("pa_server_result", lib().pa_server_result(self._h, rid, pop, ctypes.byref(o), ctypes.byref(t)))
+        return o.as_dict(), t.value
+
+    def gresult(self, rid: int, pop: int = 0):
+        """(Gaussian observables dict, last step) of a finished Gaussian-coupling request."""
+        o = GObs()
+        t = ctypes.c_int32()
+        _check("pa_server_gresult", lib().pa_server_gresult(self._h, rid, pop, ctypes.byref(o), ctypes.byref(t)))
         return o.as_dict(), t.value
 
     def load(self):

@@ -151,3 +151,35 @@ def test_batch_mixes_models(pa):
         if w.n_pop == 2:
             assert np.array_equal(a.ql_hist(t), b.ql_hist(t))
     batch.close()
+
+
+def test_server_serves_both_models(pa):
+    """Gaussian and +-1 requests in one server: each result equals its standalone
+    run's, and each model's reader refuses the other's requests."""
+    ws = [Workload("pm", L=6, R=900, disorder_seed=3, run_seed=4, betas=linear_betas(6, 2.0), n_sweeps=2),
+          Workload("ga", L=8, R=700, disorder_seed=5, run_seed=6, betas=linear_betas(7, 2.5), n_sweeps=2, model=1),
+          Workload("ga2", L=4, R=1500, disorder_seed=7, run_seed=8, betas=linear_betas(5, 1.5), n_sweeps=3,
+                   n_pop=2, model=1),
+          Workload("pm2", L=4, R=2000, disorder_seed=9, run_seed=10, betas=linear_betas(9, 3.0), n_sweeps=2,
+                   n_pop=2)]
+    budget = int(3 * max(pa.footprint(w) for w in ws))
+    server = pa.Server(budget, max_active=4, steps_per_poll=2)
+    ids = [server.submit(w) for w in ws]
+    done, t0 = set(), time.time()
+    while len(done) < len(ids):
+        done.update(server.poll())
+        assert time.time() - t0 < 120.0
+    for rid, w in zip(ids, ws):
+        ref = standalone(pa, w)
+        for pop in range(w.n_pop):
+            if w.model == 1:
+                obs, last = server.gresult(rid, pop)
+                assert last == ref.t and obs == ref.gobs(ref.t, pop)
+                with pytest.raises(pa.PAError):
+                    server.result(rid, pop)
+            else:
+                obs, last = server.result(rid, pop)
+                assert last == ref.t and obs == ref.obs(ref.t, pop)
+                with pytest.raises(pa.PAError):
+                    server.gresult(rid, pop)
+    server.close()
