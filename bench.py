@@ -41,16 +41,14 @@ if ROOT not in sys.path:
 
 METRIC = "Metropolis updates/s (L=10,R=1e6)"
 UNIT = "updates/s"
-# Rooflines of the sweep kernels: instruction issue.  For the +-1 kernel, whose
-# instructions are logic (LOP3, ISETP, SHF, ...) and integer multiplies (IMAD, the
-# 32x32->64 IMAD.WIDE of Philox), these share 16 lanes per clock per SM
-# sub-partition, 64 thread-operations per clock per SM: LOP3 alone, IMAD alone
-# and 64-bit-multiply + LOP3 pairs all reach 2.0e13/s on 152 SMs at 2.07 GHz, and
-# logic added to a multiply-bound Philox loop adds its own time (probes of
-# include/pa_bench.h).  The Gaussian kernel's mix also holds full-rate adds and
-# FP32 products, so its bound is the issue slot: one warp instruction per clock
-# per scheduler.  The work of one update (instructions per update, ncu) and the
-# rate are read from each kernel's committed profile summary.
+# Rooflines of the sweep kernels: integer instruction issue.  Their instructions
+# are logic (LOP3, ISETP, SHF, ...) and integer multiplies (IMAD, the 32x32->64
+# IMAD.WIDE of Philox), which share 16 lanes per clock per SM sub-partition, 64
+# thread-operations per clock per SM: LOP3 alone, IMAD alone and 64-bit multiply
+# + LOP3 pairs all reach 2.0e13/s on 152 SMs at 2.07 GHz, and logic added to a
+# multiply-bound Philox loop adds its own time (probes of include/pa_bench.h).
+# The work of one update (integer instructions per update, ncu) and the rate are
+# read from each kernel's committed profile summary.
 # HBM bytes per update of the sweep kernel: the tile is read (gather) and
 # written once per step, i.e. 2 bytes per site and replica every S sweeps, plus
 # 8 bytes of parent index and energy level per replica.

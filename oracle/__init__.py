@@ -161,8 +161,7 @@ def lib():
             "or_destroy": (None, [vp]),
             "org_couplings": (None, [ctypes.c_int32, ctypes.c_uint64, i32p]),
             "org_energy": (ctypes.c_int64, [ctypes.c_int32, i32p, i8p]),
-            "org_half_factor": (ctypes.c_float, [ctypes.c_double, ctypes.c_int64]),
-            "org_acceptance_threshold": (ctypes.c_uint32, [ctypes.c_double, ctypes.c_int64, ctypes.c_int64]),
+            "org_acceptance_threshold": (ctypes.c_uint32, [ctypes.c_double, ctypes.c_int64]),
             "org_sweep_replica": (ctypes.c_int64, [ctypes.c_int32, i32p, i8p, ctypes.c_uint64, ctypes.c_int32,
                                                    ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_double]),
             "org_weight_tables": (None, [ctypes.c_double, dp]),
@@ -450,8 +449,9 @@ def gsweep_replica(L: int, Jq: np.ndarray, s: np.ndarray, run_seed: int, pop: in
     return s2, int(dE)
 
 
-def gacceptance_threshold(beta: float, dE1: int, dE2: int) -> int:
-    return int(lib().org_acceptance_threshold(beta, dE1, dE2))
+def gacceptance_threshold(beta: float, dE: int) -> int:
+    """Metropolis threshold of a flip costing dE > 0 (units of 2^-20), Gaussian couplings."""
+    return int(lib().org_acceptance_threshold(beta, dE))
 
 
 def gweight_tables(dbeta: float) -> np.ndarray:

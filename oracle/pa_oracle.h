@@ -161,8 +161,8 @@ typedef struct org_run org_run;
 
 void org_couplings(int32_t L, uint64_t disorder_seed, int32_t* Jq);
 int64_t org_energy(int32_t L, const int32_t* Jq, const int8_t* s);
-float org_half_factor(double beta, int64_t dEh);
-uint32_t org_acceptance_threshold(double beta, int64_t dE1, int64_t dE2);
+/* Metropolis threshold of a flip costing dE > 0 (fixed point, units of 2^-20) */
+uint32_t org_acceptance_threshold(double beta, int64_t dE);
 int64_t org_sweep_replica(int32_t L, const int32_t* Jq, int8_t* s, uint64_t run_seed, int32_t pop, int64_t slot,
                           int32_t t, int32_t n_sweeps, double beta);
 void org_weight_tables(double dbeta, double* T);   /* T: 8192 + ORG_T2_SIZE doubles */

@@ -8,11 +8,10 @@
  *   - J(n,d) ~ N(0,1) by Box-Muller from Philox words at counter (n, 1, 0, 0),
  *     clamped to [-5, 5] and held in fixed point, Jq = round(J * 2^20); energies
  *     and energy changes are then exact integers (units of 2^-20);
- *   - a Metropolis flip with dE <= 0 is taken; otherwise the acceptance
- *     probability exp(-beta dE) is the single-precision product F1 * F2 of the
- *     Boltzmann factors of the two halves of the site's bonds, F_h = (float)
- *     exp(-beta dE_h) (halves: bonds to x+1, x-1, y+1 | y-1, z+1, z-1), and the
- *     flip is taken when the Philox word r < min(floor(2^32 p), 2^32 - 1);
+ *   - a Metropolis flip with dE <= 0 is taken; otherwise it is taken when the
+ *     Philox word r < thr(dE) = min(floor(2^32 exp(-beta dE)), 2^32 - 2), the
+ *     exponential in double precision (2^32 p is then exact, a power-of-two
+ *     scaling, and the floor the only rounding);
  *   - resampling weights w = exp(-dbeta (E - E_min)) are the double products
  *     (T2[d >> 24] * T1[(d >> 12) & 4095]) * T0[d & 4095] of per-step tables
  *     T_k[m] = exp(-dbeta m 2^(12k) 2^-20), d = (E - E_min) in fixed point;
@@ -92,22 +91,19 @@ int64_t org_energy(int32_t L, const int32_t* Jq, const int8_t* s) {
 /* ---- Metropolis ---- */
 
 /* Energy change of flipping s_n, split over the two halves of its bonds. */
-static void half_changes(int32_t L, const int32_t* Jq, const int8_t* s, int32_t n, int64_t* dE1, int64_t* dE2) {
+/* Energy change of flipping s_n: dE = 2 s_n sum_m J_nm s_m over its six bonds. */
+static int64_t flip_change(int32_t L, const int32_t* Jq, const int8_t* s, int32_t n) {
   int32_t xp = g_neighbour(L, n, 0, +1), xm = g_neighbour(L, n, 0, -1);
   int32_t yp = g_neighbour(L, n, 1, +1), ym = g_neighbour(L, n, 1, -1);
   int32_t zp = g_neighbour(L, n, 2, +1), zm = g_neighbour(L, n, 2, -1);
-  int64_t h1 = (int64_t)Jq[3 * n + 0] * s[xp] + (int64_t)Jq[3 * xm + 0] * s[xm] + (int64_t)Jq[3 * n + 1] * s[yp];
-  int64_t h2 = (int64_t)Jq[3 * ym + 1] * s[ym] + (int64_t)Jq[3 * n + 2] * s[zp] + (int64_t)Jq[3 * zm + 2] * s[zm];
-  *dE1 = 2 * s[n] * h1;
-  *dE2 = 2 * s[n] * h2;
+  int64_t h = (int64_t)Jq[3 * n + 0] * s[xp] + (int64_t)Jq[3 * xm + 0] * s[xm] + (int64_t)Jq[3 * n + 1] * s[yp] +
+              (int64_t)Jq[3 * ym + 1] * s[ym] + (int64_t)Jq[3 * n + 2] * s[zp] + (int64_t)Jq[3 * zm + 2] * s[zm];
+  return 2 * s[n] * h;
 }
 
-float org_half_factor(double beta, int64_t dEh) { return (float)exp(-(beta * ((double)dEh * 0x1p-20))); }
-
-uint32_t org_acceptance_threshold(double beta, int64_t dE1, int64_t dE2) {
-  float p = org_half_factor(beta, dE1) * org_half_factor(beta, dE2);
-  double v = floor((double)p * 4294967296.0);
-  if (v > 4294967295.0) v = 4294967295.0;
+uint32_t org_acceptance_threshold(double beta, int64_t dE) {
+  double v = floor(exp(-(beta * ((double)dE * 0x1p-20))) * 4294967296.0);
+  if (v > 4294967294.0) v = 4294967294.0;
   return (uint32_t)v;
 }
 
@@ -123,12 +119,10 @@ int64_t org_sweep_replica(int32_t L, const int32_t* Jq, int8_t* s, uint64_t run_
           for (int32_t x = 0; x < L; ++x) {
             if ((x + y + z) % 2 != c) continue;
             int32_t n = g_site(L, x, y, z);
-            int64_t dE1, dE2;
-            half_changes(L, Jq, s, n, &dE1, &dE2);
-            int64_t dE = dE1 + dE2;
+            int64_t dE = flip_change(L, Jq, s, n);
             uint32_t r = g_word(key, (uint32_t)(n >> 1), (uint32_t)(2 * sw + c), (uint32_t)(slot >> 2), (uint32_t)t,
                                 (int)(slot & 3));
-            if (dE <= 0 || r < org_acceptance_threshold(beta, dE1, dE2)) {
+            if (dE <= 0 || r < org_acceptance_threshold(beta, dE)) {
               s[n] = (int8_t)(-s[n]);
               total += dE;
             }

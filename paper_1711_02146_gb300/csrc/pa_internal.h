@@ -87,13 +87,11 @@ struct RunGeom {
   int32_t n_measure_blocks;  // Gaussian: blocks of the energy-moment reduction
 };
 
-// One entry of a site's acceptance table (Gaussian model): for one half of the
-// site's bonds and one pattern of antiparallel neighbours, the energy change of
-// that half (units of 2^-20) and its Boltzmann factor exp(-beta dE_h) in FP32.
-struct GTabEntry {
-  int32_t dE;
-  float F;
-};
+// Acceptance table of a site (Gaussian model): for each of the 64 patterns of
+// antiparallel neighbours (bit k: bond k, in the order x+1, x-1, y+1, y-1, z+1,
+// z-1), the Metropolis threshold of flipping the site: 0xFFFFFFFF when the flip
+// costs dE <= 0 (always taken), else min(floor(2^32 exp(-beta dE)), 2^32 - 2).
+constexpr int kGPatterns = 64;
 
 constexpr int kChunk = 256;            // slots per fixed-order partial sum (Gaussian weights)
 constexpr int kGTableWeights = 16384;  // doubles per step: weight tables T0 | T1 | T2
@@ -126,7 +124,7 @@ int launch_g_energy_init(const RunGeom& g, PopDev* pops, int cur, const int32_t*
 int launch_g_resample(const RunGeom& g, PopDev* pops, int cur, int t, const double* wtab, int32_t* status,
                       void* stream);
 int launch_g_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, const int32_t* Jq, long long Jtot,
-                   const GTabEntry* gtab, int t, int n_sweeps, void* stream);
+                   const uint32_t* gtab, int t, int n_sweeps, void* stream);
 // The expected culling fraction of population 0 for the weight tables wtab, into
 // rec[t].eps_expected (also overwrites the step-t weights, sums and tables, which the
 // resampling recomputes): one evaluation of the adaptive bisection.

@@ -57,7 +57,7 @@ struct pa_ctx {
   int model = PA_MODEL_PM1;
   int32_t* Jq = nullptr;                 // device [3N] fixed-point couplings
   long long Jtot = 0;                    // sum of the couplings
-  pa::GTabEntry* gtab = nullptr;         // device [n_temps][N][16] acceptance tables
+  uint32_t* gtab = nullptr;              // device [n_temps][N][64] acceptance thresholds
   double* gw = nullptr;                  // device [n_temps][16384] weight tables
   unsigned long long* qlhist = nullptr;  // device [n_temps][q_bins] link-overlap histograms
   std::vector<int32_t> Jq_host;
@@ -226,27 +226,31 @@ void gauss_couplings(int L, uint64_t seed, std::vector<int32_t>& Jq) {
   }
 }
 
-// Acceptance tables of one step: site n, half h (bonds x+1, x-1, y+1 | y-1,
-// z+1, z-1), pattern b (bit k set: bond k antiparallel): dE_h = 2 sum_k J_k
-// (1 - 2 b_k) and F_h = (float) exp(-beta dE_h 2^-20).
-void gauss_site_tables(const std::vector<int32_t>& Jq, int L, double beta, pa::GTabEntry* out) {
+// Acceptance tables of one step: site n, pattern b of its bonds x+1, x-1, y+1,
+// y-1, z+1, z-1 (bit k set: bond k antiparallel), dE = 2 sum_k J_k (1 - 2 b_k):
+// the flip's Metropolis threshold, 0xFFFFFFFF for dE <= 0 (always taken), else
+// min(floor(2^32 exp(-beta dE 2^-20)), 2^32 - 2) in double precision.
+void gauss_site_tables(const std::vector<int32_t>& Jq, int L, double beta, uint32_t* out) {
   const int N = L * L * L;
   for (int n = 0; n < N; ++n) {
     const int x = n % L, y = (n / L) % L, z = n / (L * L);
     const int xm = (x == 0 ? L - 1 : x - 1) + L * (y + L * z);
     const int ym = x + L * ((y == 0 ? L - 1 : y - 1) + L * z);
     const int zm = x + L * (y + L * (z == 0 ? L - 1 : z - 1));
-    const int64_t bond[2][3] = {{Jq[(size_t)3 * n + 0], Jq[(size_t)3 * xm + 0], Jq[(size_t)3 * n + 1]},
-                                {Jq[(size_t)3 * ym + 1], Jq[(size_t)3 * n + 2], Jq[(size_t)3 * zm + 2]}};
-    for (int h = 0; h < 2; ++h)
-      for (int b = 0; b < 8; ++b) {
-        int64_t dE = 0;
-        for (int k = 0; k < 3; ++k) dE += bond[h][k] * (((b >> k) & 1) ? -1 : 1);
-        dE *= 2;
-        pa::GTabEntry& e = out[(size_t)n * 16 + h * 8 + b];
-        e.dE = (int32_t)dE;
-        e.F = (float)std::exp(-(beta * ((double)dE * 0x1p-20)));
+    const int64_t bond[6] = {Jq[(size_t)3 * n + 0], Jq[(size_t)3 * xm + 0], Jq[(size_t)3 * n + 1],
+                             Jq[(size_t)3 * ym + 1], Jq[(size_t)3 * n + 2], Jq[(size_t)3 * zm + 2]};
+    for (int b = 0; b < pa::kGPatterns; ++b) {
+      int64_t dE = 0;  // flipping s_n: +2J for a parallel neighbour, -2J for an antiparallel one
+      for (int k = 0; k < 6; ++k) dE += bond[k] * (((b >> k) & 1) ? -1 : 1);
+      dE *= 2;
+      uint32_t thr = 0xFFFFFFFFu;
+      if (dE > 0) {
+        double v = std::floor(std::exp(-(beta * ((double)dE * 0x1p-20))) * 4294967296.0);
+        if (v > 4294967294.0) v = 4294967294.0;
+        thr = (uint32_t)v;
       }
+      out[(size_t)n * pa::kGPatterns + b] = thr;
+    }
   }
 }
 
@@ -526,7 +530,7 @@ int pa_footprint(const pa_config* cfg, size_t* bytes) {
   if (cfg->model == PA_MODEL_GAUSS) {
     const size_t nchunk = (size_t)((R_cap + pa::kChunk - 1) / pa::kChunk), nmb = (size_t)((R_cap + 4095) / 4096);
     const size_t slots = cfg->betas ? T : 1;
-    b += 12 * N + slots * N * sizeof(pa::GTabEntry) * 16 + slots * (size_t)pa::kGTableWeights * 8 +
+    b += 12 * N + slots * N * sizeof(uint32_t) * pa::kGPatterns + slots * (size_t)pa::kGTableWeights * 8 +
          T * (size_t)cfg->q_bins * 8;
     b += (size_t)cfg->n_pop * (8 * pitch + 16 * (size_t)R_cap + 8 * nchunk + 16 * nmb + T * sizeof(pa::GRec));
   }
@@ -628,7 +632,7 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
   if (g.model == PA_MODEL_GAUSS) {
     rc = rc ? rc : dalloc(c, &c->Jq, (size_t)3 * g.N);
     const size_t slots = c->adaptive ? 1 : T;  // adaptive: this step's tables, rebuilt every step
-    rc = rc ? rc : dalloc(c, &c->gtab, slots * (size_t)g.N * 16);
+    rc = rc ? rc : dalloc(c, &c->gtab, slots * (size_t)g.N * pa::kGPatterns);
     rc = rc ? rc : dalloc(c, &c->gw, slots * (size_t)pa::kGTableWeights);
     rc = rc ? rc : dalloc(c, &c->qlhist, T * (size_t)g.q_bins);
   }
@@ -648,13 +652,13 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
     // couplings, and the acceptance and weight tables of every step, on the host
     gauss_couplings(g.L, cfg->disorder_seed, c->Jq_host);
     for (int32_t v : c->Jq_host) c->Jtot += v;
-    std::vector<pa::GTabEntry> tab((size_t)g.N * 16);
+    std::vector<uint32_t> tab((size_t)g.N * pa::kGPatterns);
     std::vector<double> wt((size_t)pa::kGTableWeights);
     if (rc == PA_OK) rc = copy_h2d(c, c->Jq, c->Jq_host.data(), sizeof(int32_t) * c->Jq_host.size());
     for (int t = 1; t < cfg->n_temps && rc == PA_OK && !c->adaptive; ++t) {
       gauss_site_tables(c->Jq_host, g.L, c->betas[(size_t)t], tab.data());
       gauss_weight_tables(c->betas[(size_t)t] - c->betas[(size_t)t - 1], wt.data());
-      rc = copy_h2d(c, c->gtab + (size_t)t * g.N * 16, tab.data(), sizeof(pa::GTabEntry) * tab.size());
+      rc = copy_h2d(c, c->gtab + (size_t)t * g.N * pa::kGPatterns, tab.data(), sizeof(uint32_t) * tab.size());
       if (rc == PA_OK) rc = copy_h2d(c, c->gw + (size_t)t * pa::kGTableWeights, wt.data(), sizeof(double) * wt.size());
     }
     if (rc == PA_OK) rc = cuda_status(cudaMemsetAsync(c->J, 0, (size_t)3 * g.N, s));
@@ -707,11 +711,11 @@ int pa_step(pa_ctx* c) {
   if (c->model == PA_MODEL_GAUSS) {
     const size_t slot = c->adaptive ? 0 : (size_t)t;
     if (c->adaptive && rc == PA_OK) {  // this step's tables, for the beta just chosen
-      std::vector<pa::GTabEntry> tab((size_t)c->g.N * 16);
+      std::vector<uint32_t> tab((size_t)c->g.N * pa::kGPatterns);
       std::vector<double> wt((size_t)pa::kGTableWeights);
       gauss_site_tables(c->Jq_host, c->g.L, c->betas[(size_t)t], tab.data());
       gauss_weight_tables(dbeta, wt.data());
-      rc = copy_h2d(c, c->gtab, tab.data(), sizeof(pa::GTabEntry) * tab.size());
+      rc = copy_h2d(c, c->gtab, tab.data(), sizeof(uint32_t) * tab.size());
       if (rc == PA_OK) rc = copy_h2d(c, c->gw, wt.data(), sizeof(double) * wt.size());
     }
     if (rc == PA_OK) {
@@ -722,7 +726,7 @@ int pa_step(pa_ctx* c) {
     if (rc == PA_OK) {
       PhaseTimer pt(c, PA_PHASE_SWEEP, 1);
       rc = launch_rc(pa::launch_g_sweep(c->g, c->pops, c->cur, c->jtab, c->Jq, c->Jtot,
-                                        c->gtab + slot * c->g.N * 16, t, c->sweeps[(size_t)t], s));
+                                        c->gtab + slot * c->g.N * pa::kGPatterns, t, c->sweeps[(size_t)t], s));
     }
   } else {
     const double* w = nullptr;

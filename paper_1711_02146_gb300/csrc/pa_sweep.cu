@@ -554,19 +554,19 @@ __global__ void __launch_bounds__(NT, MB) k_sweep(const __grid_constant__ SweepA
   store_bits<L, W, NP>(a, sp, tile0, word, part);
 }
 
-// ---- Gaussian couplings (§II.A): the same tiles, gather, store and Philox words;
-// the acceptance of a flip comes from per-site tables built on the host for the
-// step's beta.  For each half of a site's bonds (x+1, x-1, y+1 | y-1, z+1, z-1)
-// and each pattern of antiparallel neighbours (bit k: bond k of the half), the
-// table holds that half's energy change dE_h (fixed point, units of 2^-20) and
-// F_h = (float) exp(-beta dE_h).  A flip is taken when dE_1 + dE_2 <= 0, or
-// when the Philox word is below min(floor(2^32 F_1 F_2), 2^32 - 1) with the
-// product rounded once in FP32.  Energies are recounted from scratch after the
-// sweeps: E = -sum J + 2 sum over antiparallel bonds of J (exact integers).
+// ---- Gaussian couplings (§II.A): nibble tiles (eight replicas per word, four
+// bits each: gather_tile, store_tile) and a 32-bit Philox word per update, at counter (n >> 1, 2s + c, j >> 2, t), word
+// j & 3.  The acceptance comes from a per-site table built on the host for the
+// step's beta: for each of the 64 patterns of antiparallel neighbours (bit k:
+// bond k, in the order x+1, x-1, y+1, y-1, z+1, z-1) the threshold of the flip,
+// 0xFFFFFFFF when it costs dE <= 0 (always taken) and otherwise
+// min(floor(2^32 exp(-beta dE)), 2^32 - 2); the flip is taken when the Philox
+// word is below it.  Energies are recounted from scratch after the sweeps:
+// E = -sum J + 2 sum over antiparallel bonds of J (exact integers).
 
 struct GSweepArgs {
   SweepArgs base;
-  const GTabEntry* gtab;  // [N][2][8] acceptance tables of this step
+  const uint32_t* gtab;   // [N][64] acceptance thresholds of this step
   const int32_t* Jq;      // [3N] fixed-point couplings of the forward bonds
   long long Jtot;         // sum of all couplings
 };
@@ -574,9 +574,8 @@ struct GSweepArgs {
 template <int L, int W, int NP, int X0>
 __device__ __forceinline__ void sweep_rows_g(uint32_t* sp, const SiteRec* recs, int part, int p,
                                              const ThreadPhilox& tpa, const ThreadPhilox& tpb, const uint32_t* k0,
-                                             const uint32_t* k1, const GTabEntry* __restrict__ gtab) {
+                                             const uint32_t* k1, const uint32_t* __restrict__ gtab) {
   constexpr int H = L / 2, RPP = L * L / NP;
-  const int2* tab = reinterpret_cast<const int2*>(gtab);
 #pragma unroll 1
   for (int k = 0; k < RPP; ++k) {
     const int r = row_index<L, NP>(part, k, p);
@@ -601,15 +600,13 @@ __device__ __forceinline__ void sweep_rows_g(uint32_t* sp, const SiteRec* recs, 
       const uint32_t s0 = row[x];
       const uint32_t P1 = (s0 ^ row[xp]) | ((s0 ^ row[xm]) << 1) | ((s0 ^ pyp[x * W]) << 2);
       const uint32_t P2 = (s0 ^ pym[x * W]) | ((s0 ^ pzp[x * W]) << 1) | ((s0 ^ pzm[x * W]) << 2);
-      const int2* tb = tab + (size_t)(r * L + x) * 16;
+      const uint32_t* tb = gtab + (size_t)(r * L + x) * kGPatterns;
       uint32_t flip = 0;
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const int2 e1 = __ldg(tb + ((P1 >> (4 * i)) & 7u));
-        const int2 e2 = __ldg(tb + 8 + ((P2 >> (4 * i)) & 7u));
-        const float pr = __fmul_rn(__int_as_float(e1.y), __int_as_float(e2.y));
-        const uint32_t thr = __float2uint_rz(__fmul_rn(pr, 4294967296.0f));
-        if (e1.x + e2.x <= 0 || w8[i] < thr) flip |= 1u << (4 * i);
+        const uint32_t b = ((P1 >> (4 * i)) & 7u) | (((P2 >> (4 * i)) & 7u) << 3);  // the replica's pattern
+        const uint32_t thr = __ldg(tb + b);
+        if (w8[i] < thr || thr == 0xFFFFFFFFu) flip |= 1u << (4 * i);
       }
       p0[x * W] = s0 ^ flip;
     }
@@ -804,7 +801,7 @@ int launch_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, 
 }
 
 int launch_g_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, const int32_t* Jq, long long Jtot,
-                   const GTabEntry* gtab, int t, int n_sweeps, void* stream) {
+                   const uint32_t* gtab, int t, int n_sweeps, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   for (int i = 0; i < g.n_pop; ++i) {
     GSweepArgs ga;

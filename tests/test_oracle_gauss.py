@@ -81,16 +81,27 @@ def test_energy_symmetries():
     assert oracle.genergy(L, Jq, s2) - E == 2 * int(s[n0]) * h
 
 
-@pytest.mark.parametrize("beta", [0.1, 0.7, 2.0])
+@pytest.mark.parametrize("beta", [1e-6, 0.1, 0.7, 2.0])
 def test_acceptance_threshold_is_the_boltzmann_factor(beta):
+    """thr(dE) = floor(2^32 exp(-beta dE)), capped at 2^32 - 2, against the closed
+    form in exact decimal arithmetic (60 digits): equal, or one below when 2^32 p
+    lies within a few ulp above an integer."""
+    import decimal
+    decimal.getcontext().prec = 60
     rng = np.random.default_rng(1)
-    for _ in range(300):
-        d1, d2 = (int(x) for x in rng.integers(-20 * 2 ** 20, 20 * 2 ** 20, size=2))
-        if d1 + d2 <= 0:
-            continue
-        exact = math.exp(-beta * (d1 + d2) * SCALE) * 2 ** 32
-        thr = oracle.gacceptance_threshold(beta, d1, d2)
-        assert abs(thr - min(exact, 2 ** 32 - 1)) <= 4e-7 * exact + 1   # single-precision product of two factors
+    dEs = [1, 2, 4095, 2 ** 20, 3 * 2 ** 20 + 17] + [int(x) for x in rng.integers(1, 40 * 2 ** 20, size=300)]
+    prev = None
+    for dE in sorted(dEs):
+        exact = (decimal.Decimal(-beta) * decimal.Decimal(dE) / decimal.Decimal(2 ** 20)).exp() * (2 ** 32)
+        want = min(int(exact), 2 ** 32 - 2)      # floor of a positive number
+        thr = oracle.gacceptance_threshold(beta, dE)
+        assert thr in (want, want - 1), (beta, dE, thr, want)
+        if thr != want:
+            assert exact - int(exact) < decimal.Decimal(2 ** 32) * decimal.Decimal(2) ** -50
+        assert prev is None or thr <= prev     # monotone in dE
+        prev = thr
+    if beta < 1e-4:
+        assert oracle.gacceptance_threshold(beta, 1) == 2 ** 32 - 2   # the cap: "always" stays ΔE <= 0 only
 
 
 def test_weight_tables_and_tree_sum():
