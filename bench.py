@@ -524,6 +524,12 @@ def ours(args):
     st = run.stats()
     ms, updates = reduce_over_ranks(ms, st["updates"], dist, "cuda")
     value = updates / (ms / 1e3)
+    # resampling traffic of the timed steps: levels read and copy numbers written
+    # (k_counts), copy numbers and labels read (k_scatter) per old slot, parents and
+    # labels written per new slot; the replica copy itself is the sweep's gather
+    sizes = [run.obs(u)["R_tilde"] for u in range(run.t - done, run.t + 1)]
+    resample_bytes = sum(16 * r_old + 8 * r_new for r_old, r_new in zip(sizes[:-1], sizes[1:]))
+    resample_ms = st["phase_ms"]["resample"]
 
     # e2e: the same steps through the public API, reading every step's observables back
     e2e = None
@@ -566,6 +572,12 @@ def ours(args):
                 "algorithmic_bytes_per_launch": hbm_bytes,
                 "hbm_GBps_achieved": hbm_bytes / (sweep_ms / 1e3) / 1e9, "hbm_GBps_peak_measured": hbm_peak}
     phase_share = {k: v / max(ms, 1e-9) for k, v in st["phase_ms"].items()}
+    resample_gbs = resample_bytes / (resample_ms / 1e3) / 1e9 if resample_ms > 0 else None
+    resample = {"GBps": resample_gbs, "peak_GBps": hbm_peak, "unit": "GB/s",
+                "frac": resample_gbs / hbm_peak if resample_gbs and hbm_peak else None,
+                "bytes_per_step": resample_bytes / max(done, 1), "ms_per_step": resample_ms / max(done, 1),
+                "kernels": "k_counts + k_scan_blocks + k_scatter (CUDA events around their launches)",
+                "bytes_basis": "16 B per old slot + 8 B per new slot (algorithmic; spins move in the sweep's gather)"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": done,
             "warmup": args.warmup, "ms_per_step": ms / max(done, 1), "higher_is_better": True,
@@ -575,7 +587,7 @@ def ours(args):
                                                               f"{args.warmup + done}",
                        "l2": "inputs larger than L2 (2 GB double-buffered int8 population)",
                        "sweep_shapes": tuned},
-            "roofline": roofline, "e2e": e2e, "gpu_launches": st["kernel_launches"],
+            "roofline": roofline, "resample": resample, "e2e": e2e, "gpu_launches": st["kernel_launches"],
             "phase_share": phase_share, "clocks": clk}
     run.close()
     # the many-run workloads and the Gaussian model are single-GPU measurements

@@ -51,6 +51,8 @@ struct PopDev {
   int32_t* counts;      // [R_cap] copy numbers of the old slots
   int32_t* parents;     // [R_cap] parent (old slot) of each new slot
   int32_t* blocksums;   // [n_count_blocks] per-block copy totals, then their exclusive scan
+  unsigned long long* tiles;  // [n_count_blocks] single-pass resampling: (2t+1 | 2t+2) << 32 | total or prefix
+  int32_t* ticket;      // [1] single-pass resampling: next tile number (reset before each pass)
   uint32_t* hist;       // [n_temps][n_levels] energy-level histograms
   int32_t* fl;          // [n_levels] floor(tau_k)
   uint32_t* thr;        // [n_levels] 2^32 frac(tau_k)
@@ -114,6 +116,8 @@ int launch_init_couplings(const RunGeom& g, uint64_t disorder_seed, int8_t* J, u
 int launch_init_population(const RunGeom& g, PopDev* pops, int cur, void* stream);
 int launch_levels_and_hist(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, int t, void* stream);
 int launch_reweight(const RunGeom& g, PopDev* pops, const double* w, int t, void* stream);
+// Single-pass resampling of the +-1 model; launch_reweight of the same step, on the
+// same stream just before, resets the tile ticket it relies on.
 int launch_resample(const RunGeom& g, PopDev* pops, int cur, int t, int32_t* status, void* stream);
 int launch_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, int t, int n_sweeps,
                  const uint32_t met_thr[3], void* stream);

@@ -129,6 +129,7 @@ __global__ void k_reweight(RunGeom g, PopArgs a, const double* __restrict__ w, i
   __shared__ int scratch[33];
   __shared__ double S_sh;
   const PopDev& P = a.p[blockIdx.x];
+  if (threadIdx.x == 0) *P.ticket = 0;  // the tile ticket of this step's single-pass resampling
   // the list lives in shared memory when it fits; otherwise in the floor table,
   // which is only written (below) after the list has been read
   int* lst = list_in_smem ? lst_sh : P.fl;
@@ -190,45 +191,8 @@ __global__ void k_reweight(RunGeom g, PopArgs a, const double* __restrict__ w, i
 
 // ---------------------------------------------------------------- resampling (a5, a6)
 
-// Copy numbers: n_i = fl(k_i) + [r_i < thr(k_i)], r_i = word (i & 3) of Philox at
-// counter (i >> 2, 0, 0, t) — the nearest-integer rule of §II.  Each block
-// covers 1024 old slots (four per thread) and stores its total.
-__global__ void __launch_bounds__(kCountThreads) k_counts(RunGeom g, PopArgs a, int t) {
-  __shared__ int red[kCountThreads / 32];
-  const PopDev& P = a.p[blockIdx.y];
-  const int R_old = P.rec[t - 1].R_tilde;
-  const int i0 = blockIdx.x * kSlotsPerCountBlock + 4 * threadIdx.x;
-  int sum = 0, cul = 0;
-  if (i0 < R_old) {
-    const uint4 r = philox4x32_10(make_uint4((uint32_t)(i0 >> 2), 0u, 0u, (uint32_t)t), P.key_res[0], P.key_res[1]);
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int i = i0 + b;
-      if (i < R_old) {
-        const int k = P.levels[i];
-        const int n = P.fl[k] + (word_of(r, b) < P.thr[k] ? 1 : 0);
-        P.counts[i] = n;
-        sum += n;
-        cul += (n == 0);
-      }
-    }
-  }
-  sum = warp_sum(sum);
-  cul = warp_sum(cul);
-  if ((threadIdx.x & 31) == 0) {
-    red[threadIdx.x >> 5] = sum;
-    if (cul) atomicAdd(&P.rec[t].culled, cul);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int s = 0;
-    for (int i = 0; i < kCountThreads / 32; ++i) s += red[i];
-    P.blocksums[blockIdx.x] = s;
-  }
-}
-
-// Exclusive scan of the block totals (one block per population); the grand
-// total is the new population size R~_t.  A total above R_cap sets the capacity
+// Exclusive scan of per-block copy totals (one block per population; the
+// Gaussian model's resampling); the grand total is the new population size R~_t.  A total above R_cap sets the capacity
 // flag and is clamped so that no later kernel writes out of bounds.
 __global__ void k_scan_blocks(RunGeom g, PopArgs a, int t, int32_t* status) {
   __shared__ int scratch[33];
@@ -298,6 +262,149 @@ __global__ void __launch_bounds__(kCountThreads) k_scatter(RunGeom g, PopArgs a,
       }
     }
     off += n[b];
+  }
+}
+
+// Single-pass resampling of the +-1 model (§II): copy numbers n_i = fl(k_i) +
+// [r_i < thr(k_i)], r_i = word (i & 3) of Philox at counter (i >> 2, 0, 0, t) —
+// the nearest-integer rule — their running offsets, and the new population's
+// parents and labels (new slot offset_i + q, q < n_i, takes old slot i as parent
+// and inherits its label, so labels stay sorted along the slots) in one launch.
+// Tiles of kResampleTile old slots are numbered in the order blocks start (a ticket), so a
+// block only ever waits on tiles whose blocks are already running or done.  Each
+// block publishes its copy total, then walks back over its predecessors' entries
+// (a total, or a total including everything before it) until it has its offset,
+// and publishes that inclusive prefix.  Entries carry the step in their upper
+// word (2t + 1: total, 2t + 2: inclusive), so older steps' entries read as not
+// ready.  A wait gives up after kLookbackSpins polls and sets the timeout flag.
+constexpr int kLookbackSpins = 1 << 20;
+constexpr int kResampleSlots = 4;  // old slots per thread (4096-slot tiles measured slower)
+constexpr int kResampleTile = kResampleSlots * kCountThreads;  // old slots per tile
+
+__device__ __forceinline__ unsigned long long poll_tile(const unsigned long long* p) {
+  return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+
+__global__ void __launch_bounds__(kCountThreads) k_resample(RunGeom g, PopArgs a, int cur, int t, int32_t* status) {
+  __shared__ int scratch[33];
+  __shared__ int tile_sh;
+  __shared__ long long base_sh;
+  const PopDev& P = a.p[blockIdx.y];
+  if (threadIdx.x == 0) tile_sh = atomicAdd(P.ticket, 1);
+  __syncthreads();
+  const int tile = tile_sh;
+  const int R_old = P.rec[t - 1].R_tilde;
+  // chunk m (m < kResampleSlots / 4) of the tile: slots base + 1024 m + 4 threadIdx.x + b, b < 4
+  constexpr int kChunks = kResampleSlots / 4, kChunkSlots = 4 * kCountThreads;
+  const int base = tile * kResampleTile;
+  int n[kResampleSlots];
+  int cul = 0, ex[kChunks], chunk_base[kChunks], total = 0;
+#pragma unroll
+  for (int m = 0; m < kChunks; ++m) {
+    const int j0 = base + m * kChunkSlots + 4 * threadIdx.x;
+    int local = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) n[4 * m + b] = 0;
+    if (j0 < R_old) {
+      const uint4 r = philox4x32_10(make_uint4((uint32_t)(j0 >> 2), 0u, 0u, (uint32_t)t), P.key_res[0], P.key_res[1]);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int i = j0 + b;
+        if (i < R_old) {
+          const int k = P.levels[i];
+          const int c = P.fl[k] + (word_of(r, b) < P.thr[k] ? 1 : 0);
+          n[4 * m + b] = c;
+          P.counts[i] = c;
+          cul += (c == 0);
+          local += c;
+        }
+      }
+    }
+    int tot;
+    ex[m] = block_exclusive_scan(local, scratch, &tot);
+    chunk_base[m] = total;
+    total += tot;
+  }
+  cul = warp_sum(cul);
+  if ((threadIdx.x & 31) == 0 && cul) atomicAdd(&P.rec[t].culled, cul);
+  if (threadIdx.x < 32) {  // warp 0: publish the total, look back 32 tiles at a time, publish the prefix
+    const uint32_t ep_total = 2u * (uint32_t)t + 1u, ep_incl = ep_total + 1u;
+    const int lane = threadIdx.x;
+    if (lane == 0 && tile > 0) atomicExch(&P.tiles[tile], ((unsigned long long)ep_total << 32) | (unsigned)total);
+    long long prefix = 0;
+    bool ok = true;
+    for (int hi = tile - 1; hi >= 0 && ok; hi -= 32) {
+      const int q = hi - lane;  // lane 0 nearest; tiles before 0 read as an inclusive 0
+      unsigned long long v = q >= 0 ? poll_tile(&P.tiles[q]) : ((unsigned long long)ep_incl << 32);
+      int spins = 0;
+      while (__any_sync(0xffffffffu, (uint32_t)(v >> 32) < ep_total)) {
+        if (++spins > kLookbackSpins) {
+          ok = false;
+          break;
+        }
+        __nanosleep(32);
+        if ((uint32_t)(v >> 32) < ep_total) v = poll_tile(&P.tiles[q]);
+      }
+      if (!ok) break;
+      const unsigned incl = __ballot_sync(0xffffffffu, (uint32_t)(v >> 32) == ep_incl);
+      const int stop = incl ? __ffs(incl) - 1 : 31;  // sum lanes 0..stop
+      long long c = lane <= stop ? (long long)(uint32_t)v : 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+      prefix += __shfl_sync(0xffffffffu, c, 0);
+      if (incl) break;
+    }
+    if (lane == 0) {
+      if (!ok) atomicOr(status, kFlagTimeout);
+      const long long inc = prefix + total;
+      atomicExch(&P.tiles[tile], ((unsigned long long)ep_incl << 32) | (unsigned)(inc > 0x7fffffffLL ? 0x7fffffffLL : inc));
+      base_sh = prefix;
+      // the tile holding the last old slot (tile 0 for an empty population) records R~
+      if (tile == (R_old > 0 ? (R_old - 1) / kResampleTile : 0)) {
+        P.rec[t].R_tilde = inc > g.R_cap ? g.R_cap : (int)inc;
+        if (inc > g.R_cap) atomicOr(status, kFlagCapacity);
+        if (inc == 0) atomicOr(status, kFlagExtinct);
+      }
+    }
+  }
+  __syncthreads();
+  const int32_t* lab_old = P.labels[cur];
+  int32_t* lab_new = P.labels[1 - cur];
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int m = 0; m < kChunks; ++m) {
+    long long off = base_sh + chunk_base[m] + ex[m];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = base + m * kChunkSlots + 4 * threadIdx.x + b;
+      const int nb = n[4 * m + b];
+      const bool big = nb > kScatterOwn;  // a large family is written by the whole warp
+      if (!big)
+        for (int q = 0; q < nb; ++q) {
+          const long long j = off + q;
+          if (j < g.R_cap) {
+            P.parents[j] = i;
+            lab_new[j] = lab_old[i];
+          }
+        }
+      unsigned int pending = __ballot_sync(0xffffffffu, big);
+      while (pending) {
+        const int src = __ffs(pending) - 1;
+        pending &= pending - 1;
+        const long long o = __shfl_sync(0xffffffffu, off, src);
+        const int cnt = __shfl_sync(0xffffffffu, nb, src);
+        const int ii = __shfl_sync(0xffffffffu, i, src);
+        const int32_t lab = lab_old[ii];
+        for (int q = lane; q < cnt; q += 32) {
+          const long long j = o + q;
+          if (j < g.R_cap) {
+            P.parents[j] = ii;
+            lab_new[j] = lab;
+          }
+        }
+      }
+      off += nb;
+    }
   }
 }
 
@@ -476,10 +583,9 @@ int launch_reweight(const RunGeom& g, PopDev* pops, const double* w, int t, void
 int launch_resample(const RunGeom& g, PopDev* pops, int cur, int t, int32_t* status, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   PopArgs a = pack(pops, g.n_pop);
-  dim3 grid(g.n_count_blocks, g.n_pop);
-  k_counts<<<grid, kCountThreads, 0, s>>>(g, a, t);
-  k_scan_blocks<<<g.n_pop, 1024, 0, s>>>(g, a, t, status);
-  k_scatter<<<grid, kCountThreads, 0, s>>>(g, a, cur, t);
+  // the tile ticket was reset by k_reweight, which runs just before on this stream
+  const unsigned tiles = (unsigned)((g.R_cap + kResampleTile - 1) / kResampleTile);  // <= n_count_blocks entries
+  k_resample<<<dim3(tiles, g.n_pop), kCountThreads, 0, s>>>(g, a, cur, t, status);
   return (int)cudaGetLastError();
 }
 

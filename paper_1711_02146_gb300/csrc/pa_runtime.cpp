@@ -517,7 +517,7 @@ int pa_footprint(const pa_config* cfg, size_t* bytes) {
   const size_t ncb = (size_t)((R_cap + pa::kSlotsPerCountBlock - 1) / pa::kSlotsPerCountBlock);
   const size_t neb = (size_t)((R_cap + pa::kEntropyPerBlock - 1) / pa::kEntropyPerBlock);
   size_t b = 3 * N + 16 * N + 4 + T * (size_t)cfg->q_bins * 8;
-  const size_t per_pop = 2 * N * pitch + 2 * 4 * pitch + 3 * 4 * pitch + 4 * ncb + 4 * T * nlev + 8 * nlev +
+  const size_t per_pop = 2 * N * pitch + 2 * 4 * pitch + 3 * 4 * pitch + 12 * ncb + 4 + 4 * T * nlev + 8 * nlev +
                          4 * (size_t)cfg->R + 4 * ((size_t)R_cap + 1) + 8 * neb + T * sizeof(StepRec);
   b += per_pop * (size_t)cfg->n_pop;
   size_t tables = 1;
@@ -609,6 +609,8 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
     rc = rc ? rc : dalloc(c, &P.counts, (size_t)g.pitch);
     rc = rc ? rc : dalloc(c, &P.parents, (size_t)g.pitch);
     rc = rc ? rc : dalloc(c, &P.blocksums, (size_t)g.n_count_blocks);
+    rc = rc ? rc : dalloc(c, &P.tiles, (size_t)g.n_count_blocks);
+    rc = rc ? rc : dalloc(c, &P.ticket, (size_t)1);
     rc = rc ? rc : dalloc(c, &P.hist, T * (size_t)g.n_levels);
     rc = rc ? rc : dalloc(c, &P.fl, (size_t)g.n_levels);
     rc = rc ? rc : dalloc(c, &P.thr, (size_t)g.n_levels);
@@ -646,6 +648,8 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
   for (int p = 0; p < g.n_pop && rc == PA_OK; ++p) {
     rc = cuda_status(cudaMemsetAsync(c->pops[p].hist, 0, sizeof(uint32_t) * T * (size_t)g.n_levels, s));
     if (rc == PA_OK) rc = cuda_status(cudaMemsetAsync(c->pops[p].rec, 0, sizeof(StepRec) * T, s));
+    if (rc == PA_OK)  // no stale tile state may carry a step's epoch
+      rc = cuda_status(cudaMemsetAsync(c->pops[p].tiles, 0, sizeof(unsigned long long) * (size_t)g.n_count_blocks, s));
   }
   if (rc == PA_OK) rc = cuda_status(cudaStreamSynchronize(s));
   if (g.model == PA_MODEL_GAUSS) {
@@ -738,7 +742,7 @@ int pa_step(pa_ctx* c) {
       rc = launch_rc(pa::launch_reweight(c->g, c->pops, w, t, s));
     }
     if (rc == PA_OK) {
-      PhaseTimer pt(c, PA_PHASE_RESAMPLE, 3);
+      PhaseTimer pt(c, PA_PHASE_RESAMPLE, 1);
       rc = launch_rc(pa::launch_resample(c->g, c->pops, c->cur, t, c->status, s));
     }
     if (rc == PA_OK && pa::sweep_supported(c->g.L)) {
