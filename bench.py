@@ -576,7 +576,7 @@ def ours(args):
     resample = {"GBps": resample_gbs, "peak_GBps": hbm_peak, "unit": "GB/s",
                 "frac": resample_gbs / hbm_peak if resample_gbs and hbm_peak else None,
                 "bytes_per_step": resample_bytes / max(done, 1), "ms_per_step": resample_ms / max(done, 1),
-                "kernels": "k_counts + k_scan_blocks + k_scatter (CUDA events around their launches)",
+                "kernels": "k_resample (CUDA events around its launch)",
                 "bytes_basis": "16 B per old slot + 8 B per new slot (algorithmic; spins move in the sweep's gather)"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": done,

@@ -252,6 +252,39 @@ def test_full_size_sampled_step(pa, oracle_lib):
         assert np.array_equal(np.bincount((E_new + 3 * N) // 2, minlength=3 * N + 1), gpu.energy_hist(t))
 
 
+@pytest.mark.parametrize("L,R,dbeta", [(4, 4_000_000, 0.4), (4, 4_000_000, 3.0), (2, 3_000_000, 0.0)])
+def test_resampling_beyond_resident_tiles(pa, oracle_lib, L, R, dbeta):
+    """More resampling tiles (R / 1024 > 2900) than the GPU holds at once, so the
+    single-pass scan's later tiles start only after earlier ones have finished.
+    First step out of beta = 0: sampled copy numbers (every tile's first and last
+    slot among them) against the oracle's rule on the GPU's integer histogram, the
+    whole parent map, the labels and R~; dbeta = 3 culls most replicas, dbeta = 0
+    with R_{t-1} = R gives tau = 1 and so one copy of every replica."""
+    gpu = pa.Run(L, R, 3, 11 + L, np.array([0.0, dbeta, dbeta + 0.5]), n_sweeps=1)
+    N = L ** 3
+    _, lab_old, E_old = gpu.population()
+    h_old = gpu.energy_hist(0)
+    assert gpu.step() == 0
+    t, o = gpu.t, gpu.obs(gpu.t)
+    assert t == 1
+    kmin, S, fl, thr, eps = oracle_lib.reweight(h_old, R, o["dbeta"])
+    assert o["kmin_prev"] == kmin and o["S_prime"] == S
+    counts = gpu.copy_counts()
+    assert counts.size == len(E_old) == R
+    k = (E_old.astype(np.int64) + 3 * N) // 2
+    rng = np.random.default_rng(5)
+    for i in np.concatenate([rng.integers(0, R, 3000), np.arange(0, R, 1024), np.arange(1023, R, 1024), [R - 1]]):
+        assert counts[i] == oracle_lib.copy_count(11 + L, 0, t, int(i), int(fl[k[i]]), int(thr[k[i]])), int(i)
+    if dbeta == 0.0:
+        assert np.all(counts == 1)
+    parents = gpu.parents()
+    assert parents.size == counts.sum() == o["R_tilde"]
+    assert np.array_equal(parents, np.repeat(np.arange(R, dtype=np.int32), counts))
+    _, lab_new, _ = gpu.population()
+    assert np.array_equal(lab_new, lab_old[parents])
+    assert o["culled"] == int((counts == 0).sum())
+
+
 def test_c2_full_size_two_populations(pa, oracle_lib):
     """L = 8, R = 1e5, two populations (the overlap workload) at full size: the whole
     q histogram and I(0.2) recomputed from both GPU populations, and sampled replicas
