@@ -35,6 +35,10 @@ import time
 
 import numpy as np
 
+# Hardware work queues for the many-stream batched and served runs (read by CUDA
+# when it creates the context; the default is 8).
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)

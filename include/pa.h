@@ -147,10 +147,12 @@ typedef struct {
 
 typedef struct pa_ctx pa_ctx;
 
-/* Creates a run: allocates its device memory (owned by the context), draws the
- * couplings and the initial population (uniform spins, label = slot) with
- * kernels on `cuda_stream` (a cudaStream_t; NULL = the legacy default stream)
- * and measures step 0.  Returns PA_OK and *out, or an error (and *out = NULL). */
+/* Creates a run: allocates its device memory (owned by the context; one
+ * stream-ordered allocation of pa_footprint bytes, carved into the run's
+ * buffers), draws the couplings and the initial population (uniform spins,
+ * label = slot) with kernels on `cuda_stream` (a cudaStream_t; NULL = the legacy
+ * default stream) and measures step 0.  Returns PA_OK and *out, or an error (and
+ * *out = NULL; PA_ERR_NOMEM when the allocation fails). */
 int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out);
 
 /* Runs the next temperature step (resample, sweep, measure).  Asynchronous for
@@ -258,7 +260,8 @@ const char* pa_strerror(int status);
  * gives exactly the results it gives alone (its random streams depend only on
  * its configuration).  These objects are not thread-safe. */
 
-/* Device bytes that pa_create allocates for cfg (for admission control). */
+/* Device bytes that pa_create allocates for cfg, exactly (for admission control;
+ * no device call). */
 int pa_footprint(const pa_config* cfg, size_t* bytes);
 
 typedef struct pa_batch pa_batch;

@@ -44,7 +44,12 @@ struct pa_ctx {
   // Boltzmann weight tables exp(-dbeta 2j), one per distinct dbeta (device)
   std::map<uint64_t, double*> wtables;
   double* wadapt = nullptr;     // adaptive schedule: the table of the current step
-  std::vector<void*> allocations;
+  // All device buffers of the run are carved from one stream-ordered allocation:
+  // a run costs the memory pool one block, so the pool's free list stays short
+  // when many runs come and go (a request server).
+  char* slab = nullptr;
+  size_t slab_bytes = 0;        // sizing pass: running total; carving pass: the slab's size
+  size_t slab_used = 0;
   // instrumentation (pa_stats)
   pa_stats stats{};
   bool timing = false;
@@ -119,6 +124,13 @@ int copy_h2d(pa_ctx* c, void* dst, const void* src, size_t bytes) {
   return rc == PA_OK ? cuda_status(cudaStreamSynchronize(c->stream)) : rc;
 }
 
+// Stream-ordered host-to-device copy; the caller keeps src alive until the stream
+// has been synchronised.
+int copy_async(pa_ctx* c, void* dst, const void* src, size_t bytes) {
+  c->stats.h2d_bytes += (int64_t)bytes;
+  return cuda_status(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+}
+
 cudaEvent_t next_event(pa_ctx* c) {
   if (c->events_used == c->events.size()) {
     cudaEvent_t e = nullptr;
@@ -155,17 +167,22 @@ struct PhaseTimer {
   }
 };
 
+constexpr size_t kSlabAlign = 256;
+
+// One buffer of the run: with no slab yet (sizing pass) it only adds the buffer's
+// aligned size to the total; afterwards it hands out the next piece of the slab.
 template <typename T>
 int dalloc(pa_ctx* c, T** p, size_t count) {
-  void* q = nullptr;
   if (count == 0) count = 1;
-  // stream-ordered allocation: no device-wide synchronisation, so other runs keep going
-  if (cudaMallocAsync(&q, sizeof(T) * count, c->stream) != cudaSuccess) {
-    cudaGetLastError();
-    return PA_ERR_NOMEM;
+  const size_t bytes = (sizeof(T) * count + kSlabAlign - 1) / kSlabAlign * kSlabAlign;
+  if (!c->slab) {
+    c->slab_bytes += bytes;
+    *p = nullptr;
+    return PA_OK;
   }
-  c->allocations.push_back(q);
-  *p = static_cast<T*>(q);
+  if (c->slab_used + bytes > c->slab_bytes) return PA_ERR_NOMEM;  // not laid out in the sizing pass
+  *p = reinterpret_cast<T*>(c->slab + c->slab_used);
+  c->slab_used += bytes;
   return PA_OK;
 }
 
@@ -280,25 +297,16 @@ std::vector<double> host_weights(int n_levels, double dbeta) {
 // distinct dbeta at creation; the adaptive schedule rewrites one buffer after
 // the host has synchronised to choose dbeta (so no kernel still reads it).
 int weight_table(pa_ctx* c, double dbeta, const double** out) {
-  auto it = c->wtables.find(bits_of(dbeta));
-  if (it != c->wtables.end()) {
+  if (!c->adaptive) {  // every table of an explicit schedule was uploaded at creation
+    auto it = c->wtables.find(bits_of(dbeta));
+    if (it == c->wtables.end()) return PA_ERR_INVALID;
     *out = it->second;
     return PA_OK;
   }
   std::vector<double> w = host_weights(c->g.n_levels, dbeta);
-  double* d = nullptr;
-  int rc = PA_OK;
-  if (c->adaptive) {
-    if (!c->wadapt) rc = dalloc(c, &c->wadapt, w.size());
-    d = c->wadapt;
-  } else {
-    rc = dalloc(c, &d, w.size());
-  }
+  const int rc = copy_h2d(c, c->wadapt, w.data(), sizeof(double) * w.size());
   if (rc != PA_OK) return rc;
-  rc = copy_h2d(c, d, w.data(), sizeof(double) * w.size());
-  if (rc != PA_OK) return rc;
-  if (!c->adaptive) c->wtables[bits_of(dbeta)] = d;
-  *out = d;
+  *out = c->wadapt;
   return PA_OK;
 }
 
@@ -428,7 +436,7 @@ int measure(pa_ctx* c, int t) {
 
 void destroy(pa_ctx* c) {
   if (!c) return;
-  for (void* p : c->allocations) cudaFreeAsync(p, c->stream);
+  if (c->slab) cudaFreeAsync(c->slab, c->stream);
   for (cudaEvent_t e : c->events) cudaEventDestroy(e);
   delete c;
 }
@@ -479,6 +487,112 @@ size_t ckpt_bytes(const RunGeom& g, int model, int t, int n_temps, const int32_t
   return b;
 }
 
+// Population capacity of a configuration (R_cap = 0: R + 10 sqrt(R) + 1024).
+int64_t capacity_of(const pa_config* cfg) {
+  return cfg->R_cap ? cfg->R_cap : cfg->R + 10 * (int64_t)std::ceil(std::sqrt((double)cfg->R)) + 1024;
+}
+
+// The distinct increments beta_t - beta_{t-1} of an explicit schedule, in order of
+// first use (one Boltzmann weight table each).
+std::vector<double> distinct_dbetas(const std::vector<double>& betas) {
+  std::vector<double> out;
+  std::map<uint64_t, int> seen;
+  for (size_t t = 1; t < betas.size(); ++t) {
+    const double d = betas[t] - betas[t - 1];
+    if (seen.emplace(bits_of(d), 0).second) out.push_back(d);
+  }
+  return out;
+}
+
+// Copies the configuration and schedule into c and sets up the run's geometry
+// (no device call; the sweep shape is left at the default).
+void init_run(pa_ctx* c, const pa_config* cfg, int64_t R_cap) {
+  c->cfg = *cfg;
+  c->cfg.R_cap = R_cap;
+  c->adaptive = cfg->betas == nullptr;
+  c->betas.assign((size_t)cfg->n_temps, 0.0);
+  c->sweeps.assign((size_t)cfg->n_temps, cfg->n_sweeps);
+  for (int t = 0; t < cfg->n_temps; ++t) {
+    if (cfg->betas) c->betas[(size_t)t] = cfg->betas[t];
+    if (cfg->sweeps_per_step) c->sweeps[(size_t)t] = cfg->sweeps_per_step[t];
+  }
+  c->cfg.betas = nullptr;
+  c->cfg.sweeps_per_step = nullptr;
+  RunGeom& g = c->g;
+  g.L = cfg->L;
+  g.N = cfg->L * cfg->L * cfg->L;
+  g.n_levels = 3 * g.N + 1;
+  g.pitch = ((R_cap + 1023) / 1024) * 1024;  // a whole number of sweep tiles (<= 1024 replicas)
+  g.R = (int32_t)cfg->R;
+  g.R_cap = (int32_t)R_cap;
+  g.n_pop = cfg->n_pop;
+  g.q_bins = cfg->q_bins;
+  g.n_count_blocks = (int32_t)((R_cap + pa::kSlotsPerCountBlock - 1) / pa::kSlotsPerCountBlock);
+  g.n_entropy_blocks = (int32_t)((R_cap + pa::kEntropyPerBlock - 1) / pa::kEntropyPerBlock);
+  g.sweep_shape = 0;
+  g.model = cfg->model;
+  g.n_chunks = (int32_t)((R_cap + pa::kChunk - 1) / pa::kChunk);
+  g.n_measure_blocks = (int32_t)((R_cap + 4095) / 4096);
+  c->model = cfg->model;
+}
+
+// The run's device buffers in one fixed order: sizes only while c has no slab,
+// else carved from it (the two passes lay out the same buffers).
+int layout_buffers(pa_ctx* c) {
+  const RunGeom& g = c->g;
+  const size_t T = c->betas.size();
+  int rc = PA_OK;
+  rc = rc ? rc : dalloc(c, &c->J, (size_t)3 * g.N);
+  rc = rc ? rc : dalloc(c, &c->jtab, (size_t)4 * g.N);
+  rc = rc ? rc : dalloc(c, &c->status, 1);
+  rc = rc ? rc : dalloc(c, &c->qhist, T * (size_t)g.q_bins);
+  for (int p = 0; p < g.n_pop && rc == PA_OK; ++p) {
+    PopDev& P = c->pops[p];
+    for (int b = 0; b < 2 && rc == PA_OK; ++b) {
+      rc = dalloc(c, &P.spins[b], (size_t)g.N * (size_t)g.pitch);
+      rc = rc ? rc : dalloc(c, &P.labels[b], (size_t)g.pitch);
+    }
+    rc = rc ? rc : dalloc(c, &P.levels, (size_t)g.pitch);
+    rc = rc ? rc : dalloc(c, &P.counts, (size_t)g.pitch);
+    rc = rc ? rc : dalloc(c, &P.parents, (size_t)g.pitch);
+    rc = rc ? rc : dalloc(c, &P.blocksums, (size_t)g.n_count_blocks);
+    rc = rc ? rc : dalloc(c, &P.tiles, (size_t)g.n_count_blocks);
+    rc = rc ? rc : dalloc(c, &P.ticket, (size_t)1);
+    rc = rc ? rc : dalloc(c, &P.hist, T * (size_t)g.n_levels);
+    rc = rc ? rc : dalloc(c, &P.fl, (size_t)g.n_levels);
+    rc = rc ? rc : dalloc(c, &P.thr, (size_t)g.n_levels);
+    rc = rc ? rc : dalloc(c, &P.famcnt, (size_t)g.R);
+    rc = rc ? rc : dalloc(c, &P.mhist, (size_t)g.R_cap + 1);
+    rc = rc ? rc : dalloc(c, &P.partials, (size_t)g.n_entropy_blocks);
+    rc = rc ? rc : dalloc(c, &P.rec, T);
+    if (g.model == PA_MODEL_GAUSS) {
+      rc = rc ? rc : dalloc(c, &P.E64, (size_t)g.pitch);
+      rc = rc ? rc : dalloc(c, &P.w, (size_t)g.R_cap);
+      rc = rc ? rc : dalloc(c, &P.part, (size_t)g.n_chunks);
+      rc = rc ? rc : dalloc(c, &P.gfl, (size_t)g.R_cap);
+      rc = rc ? rc : dalloc(c, &P.gthr, (size_t)g.R_cap);
+      rc = rc ? rc : dalloc(c, &P.e2part, (size_t)2 * g.n_measure_blocks);
+      rc = rc ? rc : dalloc(c, &P.grec, T);
+    }
+  }
+  if (g.model == PA_MODEL_GAUSS) {
+    rc = rc ? rc : dalloc(c, &c->Jq, (size_t)3 * g.N);
+    const size_t slots = c->adaptive ? 1 : T;  // adaptive: this step's tables, rebuilt every step
+    rc = rc ? rc : dalloc(c, &c->gtab, slots * (size_t)g.N * pa::kGPatterns);
+    rc = rc ? rc : dalloc(c, &c->gw, slots * (size_t)pa::kGTableWeights);
+    rc = rc ? rc : dalloc(c, &c->qlhist, T * (size_t)g.q_bins);
+  } else if (c->adaptive) {
+    rc = rc ? rc : dalloc(c, &c->wadapt, (size_t)g.n_levels);
+  } else {  // one Boltzmann weight table per distinct increment
+    const std::vector<double> d = distinct_dbetas(c->betas);
+    double* all = nullptr;
+    rc = rc ? rc : dalloc(c, &all, d.size() * (size_t)g.n_levels);
+    if (rc == PA_OK && all)
+      for (size_t i = 0; i < d.size(); ++i) c->wtables[bits_of(d[i])] = all + i * (size_t)g.n_levels;
+  }
+  return rc;
+}
+
 }  // namespace
 
 namespace pa {
@@ -509,32 +623,13 @@ const char* pa_strerror(int s) {
 
 int pa_footprint(const pa_config* cfg, size_t* bytes) {
   if (!cfg || !bytes || !pa::lattice_supported(cfg->L) || cfg->R < 1 || cfg->n_temps < 1 || cfg->n_pop < 1 ||
-      cfg->n_pop > 2 || cfg->model < PA_MODEL_PM1 || cfg->model > PA_MODEL_GAUSS)
+      cfg->n_pop > 2 || cfg->model < PA_MODEL_PM1 || cfg->model > PA_MODEL_GAUSS || cfg->q_bins < 0)
     return PA_ERR_INVALID;
-  const int64_t R_cap = cfg->R_cap ? cfg->R_cap : cfg->R + 10 * (int64_t)std::ceil(std::sqrt((double)cfg->R)) + 1024;
-  const size_t N = (size_t)cfg->L * cfg->L * cfg->L, nlev = 3 * N + 1, T = (size_t)cfg->n_temps;
-  const size_t pitch = (size_t)((R_cap + 1023) / 1024) * 1024;
-  const size_t ncb = (size_t)((R_cap + pa::kSlotsPerCountBlock - 1) / pa::kSlotsPerCountBlock);
-  const size_t neb = (size_t)((R_cap + pa::kEntropyPerBlock - 1) / pa::kEntropyPerBlock);
-  size_t b = 3 * N + 16 * N + 4 + T * (size_t)cfg->q_bins * 8;
-  const size_t per_pop = 2 * N * pitch + 2 * 4 * pitch + 3 * 4 * pitch + 12 * ncb + 4 + 4 * T * nlev + 8 * nlev +
-                         4 * (size_t)cfg->R + 4 * ((size_t)R_cap + 1) + 8 * neb + T * sizeof(StepRec);
-  b += per_pop * (size_t)cfg->n_pop;
-  size_t tables = 1;
-  if (cfg->betas) {
-    std::map<uint64_t, int> distinct;
-    for (int t = 1; t < cfg->n_temps; ++t) distinct[bits_of(cfg->betas[t] - cfg->betas[t - 1])] = 1;
-    tables = distinct.size();
-  }
-  b += tables * nlev * 8;
-  if (cfg->model == PA_MODEL_GAUSS) {
-    const size_t nchunk = (size_t)((R_cap + pa::kChunk - 1) / pa::kChunk), nmb = (size_t)((R_cap + 4095) / 4096);
-    const size_t slots = cfg->betas ? T : 1;
-    b += 12 * N + slots * N * sizeof(uint32_t) * pa::kGPatterns + slots * (size_t)pa::kGTableWeights * 8 +
-         T * (size_t)cfg->q_bins * 8;
-    b += (size_t)cfg->n_pop * (8 * pitch + 16 * (size_t)R_cap + 8 * nchunk + 16 * nmb + T * sizeof(pa::GRec));
-  }
-  *bytes = b;
+  pa_ctx sizing;  // the sizing pass of the buffer layout: no device memory is touched
+  init_run(&sizing, cfg, capacity_of(cfg));
+  const int rc = layout_buffers(&sizing);
+  if (rc != PA_OK) return rc;
+  *bytes = sizing.slab_bytes;
   return PA_OK;
 }
 
@@ -542,7 +637,7 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
   if (!out) return PA_ERR_INVALID;
   *out = nullptr;
   if (!cfg) return PA_ERR_INVALID;
-  const int64_t R_cap = cfg->R_cap ? cfg->R_cap : cfg->R + 10 * (int64_t)std::ceil(std::sqrt((double)cfg->R)) + 1024;
+  const int64_t R_cap = capacity_of(cfg);
   if (!pa::lattice_supported(cfg->L) || cfg->R < 1 || cfg->n_pop < 1 || cfg->n_pop > 2 || cfg->n_temps < 1 ||
       R_cap < cfg->R || R_cap >= ((int64_t)1 << 31) - 4096 || cfg->disorder_seed >= ((uint64_t)1 << 56) ||
       cfg->run_seed >= ((uint64_t)1 << 56) || cfg->q_bins < 3 || cfg->q_bins > 4097 || cfg->n_sweeps < 0)
@@ -562,82 +657,26 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
 
   pa_ctx* c = new (std::nothrow) pa_ctx();
   if (!c) return PA_ERR_NOMEM;
-  c->cfg = *cfg;
-  c->cfg.R_cap = R_cap;
-  c->adaptive = cfg->betas == nullptr;
-  c->betas.assign((size_t)cfg->n_temps, 0.0);
-  c->sweeps.assign((size_t)cfg->n_temps, cfg->n_sweeps);
-  for (int t = 0; t < cfg->n_temps; ++t) {
-    if (cfg->betas) c->betas[(size_t)t] = cfg->betas[t];
-    if (cfg->sweeps_per_step) c->sweeps[(size_t)t] = cfg->sweeps_per_step[t];
-  }
-  c->cfg.betas = nullptr;
-  c->cfg.sweeps_per_step = nullptr;
+  init_run(c, cfg, R_cap);
   c->stream = (cudaStream_t)cuda_stream;
-
   RunGeom& g = c->g;
-  g.L = cfg->L;
-  g.N = cfg->L * cfg->L * cfg->L;
-  g.n_levels = 3 * g.N + 1;
-  g.pitch = ((R_cap + 1023) / 1024) * 1024;  // a whole number of sweep tiles (<= 1024 replicas)
-  g.R = (int32_t)cfg->R;
-  g.R_cap = (int32_t)R_cap;
-  g.n_pop = cfg->n_pop;
-  g.q_bins = cfg->q_bins;
-  g.n_count_blocks = (int32_t)((R_cap + pa::kSlotsPerCountBlock - 1) / pa::kSlotsPerCountBlock);
-  g.n_entropy_blocks = (int32_t)((R_cap + pa::kEntropyPerBlock - 1) / pa::kEntropyPerBlock);
   int dev = 0;
-  g.sweep_shape = (pa::sweep_supported(g.L) && current_device(&dev) == PA_OK) ? run_shape(g.L, R_cap, dev) : 0;
-  g.model = cfg->model;
-  g.n_chunks = (int32_t)((R_cap + pa::kChunk - 1) / pa::kChunk);
-  g.n_measure_blocks = (int32_t)((R_cap + 4095) / 4096);
-  c->model = cfg->model;
+  if (pa::sweep_supported(g.L) && current_device(&dev) == PA_OK) g.sweep_shape = run_shape(g.L, R_cap, dev);
+  for (int p = 0; p < g.n_pop; ++p) {
+    make_key(cfg->run_seed, pa::kMetropolis, (uint32_t)p, c->pops[p].key_met);
+    make_key(cfg->run_seed, pa::kResample, (uint32_t)p, c->pops[p].key_res);
+    make_key(cfg->run_seed, pa::kInit, (uint32_t)p, c->pops[p].key_init);
+  }
   const size_t T = (size_t)cfg->n_temps;
 
-  int rc = PA_OK;
-  rc = rc ? rc : dalloc(c, &c->J, (size_t)3 * g.N);
-  rc = rc ? rc : dalloc(c, &c->jtab, (size_t)4 * g.N);
-  rc = rc ? rc : dalloc(c, &c->status, 1);
-  rc = rc ? rc : dalloc(c, &c->qhist, T * (size_t)g.q_bins);
-  for (int p = 0; p < g.n_pop && rc == PA_OK; ++p) {
-    PopDev& P = c->pops[p];
-    for (int b = 0; b < 2 && rc == PA_OK; ++b) {
-      rc = dalloc(c, &P.spins[b], (size_t)g.N * (size_t)g.pitch);
-      rc = rc ? rc : dalloc(c, &P.labels[b], (size_t)g.pitch);
-    }
-    rc = rc ? rc : dalloc(c, &P.levels, (size_t)g.pitch);
-    rc = rc ? rc : dalloc(c, &P.counts, (size_t)g.pitch);
-    rc = rc ? rc : dalloc(c, &P.parents, (size_t)g.pitch);
-    rc = rc ? rc : dalloc(c, &P.blocksums, (size_t)g.n_count_blocks);
-    rc = rc ? rc : dalloc(c, &P.tiles, (size_t)g.n_count_blocks);
-    rc = rc ? rc : dalloc(c, &P.ticket, (size_t)1);
-    rc = rc ? rc : dalloc(c, &P.hist, T * (size_t)g.n_levels);
-    rc = rc ? rc : dalloc(c, &P.fl, (size_t)g.n_levels);
-    rc = rc ? rc : dalloc(c, &P.thr, (size_t)g.n_levels);
-    rc = rc ? rc : dalloc(c, &P.famcnt, (size_t)g.R);
-    rc = rc ? rc : dalloc(c, &P.mhist, (size_t)R_cap + 1);
-    rc = rc ? rc : dalloc(c, &P.partials, (size_t)g.n_entropy_blocks);
-    rc = rc ? rc : dalloc(c, &P.rec, T);
-    make_key(cfg->run_seed, pa::kMetropolis, (uint32_t)p, P.key_met);
-    make_key(cfg->run_seed, pa::kResample, (uint32_t)p, P.key_res);
-    make_key(cfg->run_seed, pa::kInit, (uint32_t)p, P.key_init);
-    if (g.model == PA_MODEL_GAUSS) {
-      rc = rc ? rc : dalloc(c, &P.E64, (size_t)g.pitch);
-      rc = rc ? rc : dalloc(c, &P.w, (size_t)R_cap);
-      rc = rc ? rc : dalloc(c, &P.part, (size_t)g.n_chunks);
-      rc = rc ? rc : dalloc(c, &P.gfl, (size_t)R_cap);
-      rc = rc ? rc : dalloc(c, &P.gthr, (size_t)R_cap);
-      rc = rc ? rc : dalloc(c, &P.e2part, (size_t)2 * g.n_measure_blocks);
-      rc = rc ? rc : dalloc(c, &P.grec, T);
-    }
+  // sizing pass, one stream-ordered allocation, carving pass
+  int rc = layout_buffers(c);
+  if (rc == PA_OK && cudaMallocAsync(reinterpret_cast<void**>(&c->slab), c->slab_bytes, c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    c->slab = nullptr;
+    rc = PA_ERR_NOMEM;
   }
-  if (g.model == PA_MODEL_GAUSS) {
-    rc = rc ? rc : dalloc(c, &c->Jq, (size_t)3 * g.N);
-    const size_t slots = c->adaptive ? 1 : T;  // adaptive: this step's tables, rebuilt every step
-    rc = rc ? rc : dalloc(c, &c->gtab, slots * (size_t)g.N * pa::kGPatterns);
-    rc = rc ? rc : dalloc(c, &c->gw, slots * (size_t)pa::kGTableWeights);
-    rc = rc ? rc : dalloc(c, &c->qlhist, T * (size_t)g.q_bins);
-  }
+  if (rc == PA_OK) rc = layout_buffers(c);
   if (rc != PA_OK) {
     destroy(c);
     return rc;
@@ -651,19 +690,26 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
     if (rc == PA_OK)  // no stale tile state may carry a step's epoch
       rc = cuda_status(cudaMemsetAsync(c->pops[p].tiles, 0, sizeof(unsigned long long) * (size_t)g.n_count_blocks, s));
   }
-  if (rc == PA_OK) rc = cuda_status(cudaStreamSynchronize(s));
+  // Host tables go up in one copy per kind; their host buffers live until the
+  // stream synchronisation at the end of creation.
+  std::vector<double> wall;
+  std::vector<uint32_t> gtab_all;
+  std::vector<double> gw_all;
   if (g.model == PA_MODEL_GAUSS) {
     // couplings, and the acceptance and weight tables of every step, on the host
     gauss_couplings(g.L, cfg->disorder_seed, c->Jq_host);
     for (int32_t v : c->Jq_host) c->Jtot += v;
-    std::vector<uint32_t> tab((size_t)g.N * pa::kGPatterns);
-    std::vector<double> wt((size_t)pa::kGTableWeights);
-    if (rc == PA_OK) rc = copy_h2d(c, c->Jq, c->Jq_host.data(), sizeof(int32_t) * c->Jq_host.size());
-    for (int t = 1; t < cfg->n_temps && rc == PA_OK && !c->adaptive; ++t) {
-      gauss_site_tables(c->Jq_host, g.L, c->betas[(size_t)t], tab.data());
-      gauss_weight_tables(c->betas[(size_t)t] - c->betas[(size_t)t - 1], wt.data());
-      rc = copy_h2d(c, c->gtab + (size_t)t * g.N * pa::kGPatterns, tab.data(), sizeof(uint32_t) * tab.size());
-      if (rc == PA_OK) rc = copy_h2d(c, c->gw + (size_t)t * pa::kGTableWeights, wt.data(), sizeof(double) * wt.size());
+    if (rc == PA_OK) rc = copy_async(c, c->Jq, c->Jq_host.data(), sizeof(int32_t) * c->Jq_host.size());
+    if (!c->adaptive && T > 1) {
+      const size_t per_tab = (size_t)g.N * pa::kGPatterns;
+      gtab_all.assign(T * per_tab, 0u);
+      gw_all.assign(T * (size_t)pa::kGTableWeights, 0.0);
+      for (size_t t = 1; t < T; ++t) {
+        gauss_site_tables(c->Jq_host, g.L, c->betas[t], gtab_all.data() + t * per_tab);
+        gauss_weight_tables(c->betas[t] - c->betas[t - 1], gw_all.data() + t * (size_t)pa::kGTableWeights);
+      }
+      if (rc == PA_OK) rc = copy_async(c, c->gtab, gtab_all.data(), sizeof(uint32_t) * gtab_all.size());
+      if (rc == PA_OK) rc = copy_async(c, c->gw, gw_all.data(), sizeof(double) * gw_all.size());
     }
     if (rc == PA_OK) rc = cuda_status(cudaMemsetAsync(c->J, 0, (size_t)3 * g.N, s));
     if (rc == PA_OK) rc = cuda_status(cudaMemsetAsync(c->jtab, 0, sizeof(uint32_t) * 4 * g.N, s));
@@ -671,9 +717,16 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
     if (rc == PA_OK) rc = launch_rc(pa::launch_init_population(g, c->pops, 0, s));
     if (rc == PA_OK) rc = launch_rc(pa::launch_g_energy_init(g, c->pops, 0, c->Jq, s));
   } else {
-    for (int t = 1; t < cfg->n_temps && rc == PA_OK && !c->adaptive; ++t) {
-      const double* w = nullptr;
-      rc = weight_table(c, c->betas[(size_t)t] - c->betas[(size_t)t - 1], &w);
+    if (!c->adaptive) {
+      const std::vector<double> d = distinct_dbetas(c->betas);
+      const size_t nl = (size_t)g.n_levels;
+      wall.resize(d.size() * nl);
+      for (size_t i = 0; i < d.size(); ++i) {
+        const std::vector<double> w = host_weights(g.n_levels, d[i]);
+        std::copy(w.begin(), w.end(), wall.begin() + (ptrdiff_t)(i * nl));
+      }
+      if (rc == PA_OK && !d.empty())
+        rc = copy_async(c, c->wtables[bits_of(d[0])], wall.data(), sizeof(double) * wall.size());
     }
     if (rc == PA_OK) rc = launch_rc(pa::launch_init_couplings(g, cfg->disorder_seed, c->J, c->jtab, s));
     if (rc == PA_OK) rc = launch_rc(pa::launch_init_population(g, c->pops, 0, s));
@@ -1231,7 +1284,7 @@ int pa_restore(const pa_config* cfg, const void* buf, size_t size, void* cuda_st
   if (std::memcmp(h.magic, kCkptMagic, sizeof h.magic) != 0 || h.version != kCkptVersion ||
       h.header_bytes != sizeof(CkptHeader) || h.total_bytes != size)
     return PA_ERR_INVALID;
-  const int64_t R_cap = cfg->R_cap ? cfg->R_cap : cfg->R + 10 * (int64_t)std::ceil(std::sqrt((double)cfg->R)) + 1024;
+  const int64_t R_cap = capacity_of(cfg);
   const bool adaptive = cfg->betas == nullptr;
   if (h.model != cfg->model) return PA_ERR_INVALID;
   const bool gauss = cfg->model == PA_MODEL_GAUSS;

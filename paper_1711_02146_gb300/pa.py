@@ -17,6 +17,12 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpa.so")
 
+# Runs on separate streams (Batch, Server) overlap on the device only as far as its
+# hardware work queues allow; CUDA reads the queue count when it creates the
+# context, so this default (the driver's own is 8) applies only when this module is
+# imported before the process's first CUDA call, and never overrides a user's value.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 PA_OK, PA_DONE = 0, 1
 PA_ERR_INVALID, PA_ERR_NOMEM, PA_ERR_CAPACITY, PA_ERR_TIMEOUT = -1, -2, -3, -4
 PA_ERR_CUDA, PA_ERR_STATE, PA_ERR_EXTINCT = -5, -6, -7

@@ -54,3 +54,35 @@ def test_binding_refuses_to_run_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(pa, "_lib", None)
     with pytest.raises(ImportError):
         pa.lib()
+
+
+def _up(n):
+    return (n + 255) // 256 * 256
+
+
+def test_footprint_is_the_slab_layout_without_gpu(palib):
+    """pa_footprint is host-only and gives the exact size of the run's one device
+    allocation: every buffer of the +-1 layout rounded up to 256 bytes, one
+    Boltzmann weight table per distinct temperature increment (one table for the
+    adaptive schedule)."""
+    import numpy as np
+    from paper_1711_02146_gb300 import pa
+    from paper_1711_02146_gb300.workloads import Workload, linear_betas
+    step_rec = 80
+    for L, R, n_pop, betas in [(4, 1000, 1, linear_betas(51, 5.0)), (10, 123457, 2, np.array([0.0, 0.1, 0.2, 0.25])),
+                               (6, 7, 1, None)]:
+        w = Workload("fp", L=L, R=R, disorder_seed=1, run_seed=2, betas=betas, n_temps=0 if betas is not None else 40,
+                     eps_target=0.0 if betas is not None else 0.2, n_pop=n_pop)
+        N, T, Rc = L ** 3, (len(betas) if betas is not None else 40), w.capacity
+        pitch, nlev = -(-Rc // 1024) * 1024, 3 * L ** 3 + 1
+        ncb, neb = -(-Rc // 1024), -(-Rc // 4096)
+        want = _up(3 * N) + _up(16 * N) + _up(4) + _up(8 * T * 65)
+        per_pop = (2 * (_up(N * pitch) + _up(4 * pitch)) + 3 * _up(4 * pitch) + _up(4 * ncb) + _up(8 * ncb) + _up(4)
+                   + _up(4 * T * nlev) + 2 * _up(4 * nlev) + _up(4 * R) + _up(4 * (Rc + 1)) + _up(8 * neb)
+                   + _up(step_rec * T))
+        want += n_pop * per_pop
+        n_tables = len({float(d).hex() for d in np.diff(betas)}) if betas is not None else 1
+        want += _up(8 * n_tables * nlev)
+        assert pa.footprint(w) == want, (L, R, n_pop)
+    g = Workload("g", L=4, R=1000, disorder_seed=1, run_seed=2, betas=linear_betas(11, 2.0), model=1)
+    assert pa.footprint(g) > pa.footprint(g.with_(model=0))
