@@ -279,7 +279,10 @@ int pa_batch_destroy(pa_batch* batch);
  * and at most max_active runs are on the GPU; every pa_server_poll issues up to
  * steps_per_poll steps of each admitted run, retires runs whose last step has
  * completed on the device (freeing their memory), admits waiting runs, and
- * reports the ids that finished. */
+ * reports the ids that finished.  A run's stream priority follows its work
+ * (Metropolis updates of its schedule), one level per decade, smaller runs
+ * higher: the device runs short requests first and fills the rest with long
+ * ones. */
 typedef struct pa_server pa_server;
 int pa_server_create(size_t mem_budget, int32_t max_active, int32_t steps_per_poll, pa_server** out);
 int pa_server_submit(pa_server* server, const pa_config* cfg, uint64_t* request_id);

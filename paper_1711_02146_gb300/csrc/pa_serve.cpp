@@ -4,13 +4,16 @@
 //
 // Each run lives on its own non-blocking stream, so the kernels of different
 // runs overlap on the device while the host issues their steps round-robin
-// (pa_step of an explicit schedule does not wait for the device).  Memory is
-// stream-ordered (cudaMallocAsync / cudaFreeAsync in pa_create / pa_destroy),
-// so admitting or retiring a run never synchronises the other runs.  Results
-// of a run depend only on its configuration, never on what else is running.
+// (pa_step of an explicit schedule does not wait for the device); a server run's
+// stream priority is set by its work, smaller runs higher.  Memory is
+// stream-ordered (one cudaMallocAsync / cudaFreeAsync per run in pa_create /
+// pa_destroy), so admitting or retiring a run never synchronises the other runs.
+// Results of a run depend only on its configuration, never on what else is
+// running.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -46,8 +49,36 @@ struct OwnedConfig {
   }
 };
 
-int make_stream(cudaStream_t* s) {
-  return cudaStreamCreateWithFlags(s, cudaStreamNonBlocking) == cudaSuccess ? PA_OK : PA_ERR_CUDA;
+int make_stream(cudaStream_t* s, int priority) {
+  return cudaStreamCreateWithPriority(s, cudaStreamNonBlocking, priority) == cudaSuccess ? PA_OK : PA_ERR_CUDA;
+}
+
+// Metropolis updates a run will do (its schedule's sweeps times N R per population;
+// an adaptive schedule counts its step limit).
+double run_work(const pa_config& c) {
+  double sweeps = 0.0;
+  for (int t = 1; t < c.n_temps; ++t) sweeps += c.sweeps_per_step ? (double)c.sweeps_per_step[t] : (double)c.n_sweeps;
+  return sweeps * (double)c.L * c.L * c.L * (double)c.R * (double)c.n_pop;
+}
+
+// The device's stream priorities: least (numerically largest) and greatest.
+void priority_range(int* least, int* greatest) {
+  *least = 0;
+  *greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(least, greatest) != cudaSuccess) {
+    cudaGetLastError();
+    *least = *greatest = 0;
+  }
+}
+
+// Server requests: the smaller the run, the higher its stream's priority, one level
+// per decade of work (shortest job first, so short requests are not held up behind
+// long ones); runs of 1e12 updates and more share the least priority.
+int server_priority_level(const pa_config& c, int n_levels) {
+  const double w = run_work(c);
+  int decade = w < 1.0 ? 0 : (int)std::floor(std::log10(w));
+  int level = 12 - decade;  // 0: least priority
+  return std::max(0, std::min(n_levels - 1, level));
 }
 
 }  // namespace
@@ -72,6 +103,7 @@ struct pa_server {
     bool all_issued;
     int n_pop;
     int model;
+    int level;  // stream priority level
   };
   struct Finished {
     std::vector<pa_obs> obs;    // per population, last step (+-1 couplings)
@@ -84,7 +116,8 @@ struct pa_server {
   uint64_t next_id = 1;
   std::deque<Request> queue;
   std::vector<Active> active;
-  std::vector<cudaStream_t> free_streams;
+  std::vector<std::vector<cudaStream_t>> free_streams;  // per priority level, 0 = least
+  int least_priority = 0, n_levels = 1;
   std::vector<cudaEvent_t> free_events;
   std::map<uint64_t, Finished> finished;
 };
@@ -100,7 +133,7 @@ int pa_batch_create(const pa_config* cfgs, int32_t n, pa_batch** out) {
   if (!b) return PA_ERR_NOMEM;
   for (int32_t i = 0; i < n; ++i) {
     cudaStream_t s = nullptr;
-    int rc = make_stream(&s);
+    int rc = make_stream(&s, 0);  // default priority (largest-first priorities measured 2 % slower)
     pa_ctx* c = nullptr;
     if (rc == PA_OK) rc = pa_create(&cfgs[i], s, &c);
     if (rc == PA_OK) pa::use_chosen_shape(c);
@@ -165,6 +198,11 @@ int pa_server_create(size_t mem_budget, int32_t max_active, int32_t steps_per_po
   s->budget = mem_budget;
   s->max_active = max_active;
   s->steps_per_poll = steps_per_poll;
+  int least = 0, greatest = 0;
+  priority_range(&least, &greatest);
+  s->least_priority = least;
+  s->n_levels = least - greatest + 1;
+  s->free_streams.resize((size_t)s->n_levels);
   *out = s;
   return PA_OK;
 }
@@ -190,11 +228,13 @@ int admit(pa_server* s) {
   while (!s->queue.empty() && (int32_t)s->active.size() < s->max_active &&
          s->used + s->queue.front().footprint <= s->budget) {
     pa_server::Request& r = s->queue.front();
+    const int level = server_priority_level(r.cfg.cfg, s->n_levels);
+    std::vector<cudaStream_t>& pool = s->free_streams[(size_t)level];
     cudaStream_t st = nullptr;
-    if (!s->free_streams.empty()) {
-      st = s->free_streams.back();
-      s->free_streams.pop_back();
-    } else if (make_stream(&st) != PA_OK) {
+    if (!pool.empty()) {
+      st = pool.back();
+      pool.pop_back();
+    } else if (make_stream(&st, s->least_priority - level) != PA_OK) {
       return PA_ERR_CUDA;
     }
     cudaEvent_t ev = nullptr;
@@ -202,7 +242,7 @@ int admit(pa_server* s) {
       ev = s->free_events.back();
       s->free_events.pop_back();
     } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
-      s->free_streams.push_back(st);
+      pool.push_back(st);
       return PA_ERR_CUDA;
     }
     pa_ctx* c = nullptr;
@@ -214,12 +254,12 @@ int admit(pa_server* s) {
       f.last_step = -1;
       f.status = rc;
       s->finished[r.id] = f;
-      s->free_streams.push_back(st);
+      pool.push_back(st);
       s->free_events.push_back(ev);
       s->queue.pop_front();
       continue;
     }
-    s->active.push_back({r.id, c, st, r.footprint, ev, false, r.cfg.cfg.n_pop, r.cfg.cfg.model});
+    s->active.push_back({r.id, c, st, r.footprint, ev, false, r.cfg.cfg.n_pop, r.cfg.cfg.model, level});
     s->used += r.footprint;
     s->queue.pop_front();
   }
@@ -265,7 +305,7 @@ int pa_server_poll(pa_server* s, uint64_t* done_ids, int32_t cap, int32_t* n_don
     }
     s->finished[a.id] = std::move(f);
     pa_destroy(a.ctx);
-    s->free_streams.push_back(a.stream);
+    s->free_streams[(size_t)a.level].push_back(a.stream);
     s->free_events.push_back(a.done);
     s->used -= a.footprint;
     done_ids[(*n_done)++] = a.id;
@@ -307,13 +347,14 @@ int pa_server_destroy(pa_server* s) {
   if (!s) return PA_ERR_INVALID;
   for (auto& a : s->active) {
     pa_destroy(a.ctx);
-    s->free_streams.push_back(a.stream);
+    s->free_streams[(size_t)a.level].push_back(a.stream);
     s->free_events.push_back(a.done);
   }
-  for (cudaStream_t st : s->free_streams) {
-    cudaStreamSynchronize(st);
-    cudaStreamDestroy(st);
-  }
+  for (auto& pool : s->free_streams)
+    for (cudaStream_t st : pool) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
   for (cudaEvent_t ev : s->free_events) cudaEventDestroy(ev);
   delete s;
   return PA_OK;
