@@ -15,9 +15,10 @@
  *   - resampling weights w = exp(-dbeta (E - E_min)) are the double products
  *     (T2[d >> 24] * T1[(d >> 12) & 4095]) * T0[d & 4095] of per-step tables
  *     T_k[m] = exp(-dbeta m 2^(12k) 2^-20), d = (E - E_min) in fixed point;
- *   - S' and the culling sum are taken in a fixed order: chunks of 256 slots,
- *     each by a binary tree (a[i] += a[i + h], h = 128, 64, ..., 1), and the
- *     chunk totals one after another;
+ *   - S' and the culling sum are taken in a fixed order: groups of 256 values
+ *     (the last one padded with zeros), each by a binary tree (a[i] += a[i + h],
+ *     h = 128, 64, ..., 1); the group totals again in groups of 256 by the same
+ *     tree, and so on until one value remains (the paper fixes no order);
  *   - the adaptive schedule (§IV.B) bisects on the culling fraction computed
  *     with exactly these weights and sums.
  */
@@ -143,13 +144,25 @@ double org_weight(const double* T, int64_t d) {
 }
 
 double org_tree_sum(const double* x, int64_t n) {
-  double total = 0.0, a[256];
-  for (int64_t c0 = 0; c0 < n; c0 += 256) {
-    for (int i = 0; i < 256; ++i) a[i] = (c0 + i < n) ? x[c0 + i] : 0.0;
-    for (int h = 128; h >= 1; h >>= 1)
-      for (int i = 0; i < h; ++i) a[i] = a[i] + a[i + h];
-    total = total + a[0];
+  if (n <= 0) return 0.0;
+  double* cur = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!cur) abort();
+  memcpy(cur, x, sizeof(double) * (size_t)n);
+  int64_t m = n;
+  for (;;) {
+    const int64_t groups = (m + 255) / 256;
+    for (int64_t k = 0; k < groups; ++k) {
+      double a[256];
+      for (int i = 0; i < 256; ++i) a[i] = (256 * k + i < m) ? cur[256 * k + i] : 0.0;
+      for (int h = 128; h >= 1; h >>= 1)
+        for (int i = 0; i < h; ++i) a[i] = a[i] + a[i + h];
+      cur[k] = a[0];  /* group k reads entries >= 256 k, so this write is behind the reads */
+    }
+    m = groups;
+    if (m == 1) break;
   }
+  const double total = cur[0];
+  free(cur);
   return total;
 }
 

@@ -116,21 +116,34 @@ def test_weight_tables_and_tree_sum():
     for n in (1, 255, 256, 257, 5000):
         x = rng.random(n)
         assert abs(oracle.tree_sum(x) - math.fsum(x)) <= 1e-13 * math.fsum(x)
-    x = rng.random(1000)
-    # the fixed order is the definition: chunk trees, then chunks in sequence
-    chunks = []
-    for c0 in range(0, 1000, 256):
-        a = np.zeros(256)
-        a[: min(256, 1000 - c0)] = x[c0:c0 + 256]
-        h = 128
-        while h >= 1:
-            a[:h] = a[:h] + a[h:2 * h]
-            h //= 2
-        chunks.append(a[0])
-    total = 0.0
-    for c in chunks:
-        total = total + c
-    assert oracle.tree_sum(x) == total
+    # the fixed order is the definition: groups of 256 by the binary tree, the group
+    # totals again in groups of 256, until one value remains
+    def group_tree(v):
+        out = []
+        for c0 in range(0, len(v), 256):
+            a = np.zeros(256)
+            a[: min(256, len(v) - c0)] = v[c0:c0 + 256]
+            h = 128
+            while h >= 1:
+                a[:h] = a[:h] + a[h:2 * h]
+                h //= 2
+            out.append(a[0])
+        return np.array(out)
+    for n in (1, 256, 1000, 256 * 256 + 1, 300_000):
+        x = rng.random(n) * rng.choice([1e-9, 1.0, 1e9], n)  # wide magnitudes: orders round differently
+        v = x
+        while True:
+            v = group_tree(v)
+            if len(v) == 1:
+                break
+        assert oracle.tree_sum(x) == v[0], n
+    # a dropped level or a sequential pass over the group totals is a different sum
+    x = rng.random(70_000) * rng.choice([1e-9, 1.0, 1e9], 70_000)
+    seq = 0.0
+    for c in group_tree(x):
+        seq = seq + c
+    assert oracle.tree_sum(x) != seq
+    assert oracle.tree_sum(np.array([])) == 0.0
 
 
 def test_katzgraber_young_identity_by_enumeration():
