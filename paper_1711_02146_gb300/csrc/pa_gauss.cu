@@ -8,7 +8,8 @@
 //   - weight of old slot i: w_i = (T2[d >> 24] * T1[(d >> 12) & 4095]) * T0[d & 4095]
 //     with d = E_i - E_min and host tables T_k[m] = exp(-dbeta m 2^(12k) 2^-20);
 //   - S' = sum_i w_i and the culling sum sum_i (1 - tau_i)_+ in a fixed order:
-//     chunks of 256 slots, each by a binary tree, then the chunk totals in order;
+//     groups of 256 values (zero-padded) each by a binary tree, the group totals
+//     again in groups of 256, until one value remains;
 //   - tau_i = R w_i / S', n_i = floor(tau_i) + [r_i < 2^32 frac(tau_i)] (§II).
 #include <cuda_runtime.h>
 
@@ -119,27 +120,40 @@ __global__ void __launch_bounds__(kChunk) k_g_weights(RunGeom g, GArgs a, int t,
   }
 }
 
-// The chunk totals one after another, into S' (which = 0) or the expected
-// culling fraction (which = 1, divided by R).  The block stages the partials in
-// shared memory, 4096 at a time, and one thread adds them in order.
-__global__ void __launch_bounds__(1024) k_g_chunks(RunGeom g, GArgs a, int t, int which) {
-  __shared__ double buf[4096];
-  PopDev& P = a.p[blockIdx.x];
-  const int n = blocks_for(P.rec[t - 1].R_tilde, kChunk);
-  double total = 0.0;
-  for (int c0 = 0; c0 < n; c0 += 4096) {
-    const int m = min(4096, n - c0);
-    for (int k = threadIdx.x; k < m; k += blockDim.x) buf[k] = P.part[c0 + k];
-    __syncthreads();
-    if (threadIdx.x == 0)
-      for (int k = 0; k < m; ++k) total = __dadd_rn(total, buf[k]);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    if (which == 0)
-      P.rec[t].S_prime = total;
-    else
-      P.rec[t].eps_expected = __ddiv_rn(total, (double)g.R);
+// One level of the fixed-order sum: block b reduces entries [256 b, 256 b + 256)
+// of part + in_off (zeros past n_in) by the binary tree into part[out_off + b];
+// the last level (one block) writes S' (which = 0) or the expected culling
+// fraction (which = 1, divided by R) instead.  Entries past a population's own
+// chunk count are zero, and adding +0.0 is exact, so counting up to the capacity
+// gives the same sum.
+__global__ void __launch_bounds__(kChunk) k_g_level(RunGeom g, GArgs a, int t, long long in_off, int n_in,
+                                                   long long out_off, int which) {
+  __shared__ double sh[kChunk];
+  PopDev& P = a.p[blockIdx.y];
+  const int i = blockIdx.x * kChunk + threadIdx.x;
+  sh[threadIdx.x] = i < n_in ? P.part[in_off + i] : 0.0;
+  __syncthreads();
+  chunk_tree(sh);
+  if (threadIdx.x != 0) return;
+  if (which < 0)
+    P.part[out_off + blockIdx.x] = sh[0];
+  else if (which == 0)
+    P.rec[t].S_prime = sh[0];
+  else
+    P.rec[t].eps_expected = __ddiv_rn(sh[0], (double)g.R);
+}
+
+// All levels over the n_chunks chunk totals at the start of part (scratch for
+// the upper levels follows them: tree_sum_scratch entries in all).
+void launch_levels(const RunGeom& g, const GArgs& a, int n_pop, int t, int which, cudaStream_t s) {
+  long long off = 0;
+  int n = g.n_chunks;
+  for (;;) {
+    const int nb = blocks_for(n, kChunk);
+    k_g_level<<<dim3(nb, n_pop), kChunk, 0, s>>>(g, a, t, off, n, off + n, nb == 1 ? which : -1);
+    if (nb == 1) break;
+    off += n;
+    n = nb;
   }
 }
 
@@ -361,9 +375,9 @@ int launch_g_resample(const RunGeom& g, PopDev* pops, int cur, int t, const doub
   GArgs a = gpack(pops, g.n_pop);
   const dim3 chunks(g.n_chunks, g.n_pop);
   k_g_weights<<<chunks, kChunk, 0, s>>>(g, a, t, wtab);
-  k_g_chunks<<<g.n_pop, 1024, 0, s>>>(g, a, t, 0);
+  launch_levels(g, a, g.n_pop, t, 0, s);
   k_g_tau<<<chunks, kChunk, 0, s>>>(g, a, t);
-  k_g_chunks<<<g.n_pop, 1024, 0, s>>>(g, a, t, 1);
+  launch_levels(g, a, g.n_pop, t, 1, s);
   k_g_counts<<<dim3(g.n_count_blocks, g.n_pop), kCountThreads, 0, s>>>(g, a, t);
   const int e = (int)cudaGetLastError();
   return e ? e : launch_scan_scatter(g, pops, cur, t, status, stream);
@@ -376,9 +390,9 @@ int launch_g_eps_trial(const RunGeom& g, PopDev* pops, int t, const double* wtab
   GArgs a = gpack(pops, 1);
   const dim3 chunks(g1.n_chunks, 1);
   k_g_weights<<<chunks, kChunk, 0, s>>>(g1, a, t, wtab);
-  k_g_chunks<<<1, 1024, 0, s>>>(g1, a, t, 0);
+  launch_levels(g1, a, 1, t, 0, s);
   k_g_tau<<<chunks, kChunk, 0, s>>>(g1, a, t);
-  k_g_chunks<<<1, 1024, 0, s>>>(g1, a, t, 1);
+  launch_levels(g1, a, 1, t, 1, s);
   return (int)cudaGetLastError();
 }
 

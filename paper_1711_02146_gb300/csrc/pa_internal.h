@@ -63,7 +63,7 @@ struct PopDev {
   // Gaussian-coupling model only (null otherwise)
   long long* E64;       // [pitch] energies of the current population, units of 2^-20
   double* w;            // [R_cap] resampling weights of the old population
-  double* part;         // [n_chunks] fixed-order partial sums (chunks of 256 slots)
+  double* part;         // [tree_sum_scratch(n_chunks)] fixed-order partial sums (chunks of 256 slots, then levels)
   int32_t* gfl;         // [R_cap] floor(tau_i)
   uint32_t* gthr;       // [R_cap] 2^32 frac(tau_i)
   unsigned long long* e2part;  // [2 * n_measure_blocks] 128-bit partial sums of E^2
@@ -96,6 +96,16 @@ struct RunGeom {
 constexpr int kGPatterns = 64;
 
 constexpr int kChunk = 256;            // slots per fixed-order partial sum (Gaussian weights)
+// Entries of the Gaussian partial-sum buffer for n chunk totals: the totals, then
+// the outputs of every level of the fixed-order tree but the last.
+inline int64_t tree_sum_scratch(int64_t n) {
+  int64_t total = n;
+  for (int64_t m = n; m > kChunk;) {
+    m = (m + kChunk - 1) / kChunk;
+    total += m;
+  }
+  return total;
+}
 constexpr int kGTableWeights = 16384;  // doubles per step: weight tables T0 | T1 | T2
 
 // One launch shape of the sweep kernel (every shape gives identical results).

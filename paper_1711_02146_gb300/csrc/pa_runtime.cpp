@@ -568,7 +568,7 @@ int layout_buffers(pa_ctx* c) {
     if (g.model == PA_MODEL_GAUSS) {
       rc = rc ? rc : dalloc(c, &P.E64, (size_t)g.pitch);
       rc = rc ? rc : dalloc(c, &P.w, (size_t)g.R_cap);
-      rc = rc ? rc : dalloc(c, &P.part, (size_t)g.n_chunks);
+      rc = rc ? rc : dalloc(c, &P.part, (size_t)pa::tree_sum_scratch(g.n_chunks));
       rc = rc ? rc : dalloc(c, &P.gfl, (size_t)g.R_cap);
       rc = rc ? rc : dalloc(c, &P.gthr, (size_t)g.R_cap);
       rc = rc ? rc : dalloc(c, &P.e2part, (size_t)2 * g.n_measure_blocks);
