@@ -151,6 +151,13 @@ namespace pa {
 // A run created for overlapped execution keeps the device's chosen sweep shape
 // (no switch to smaller tiles for a small population).
 void use_chosen_shape(pa_ctx* c);
+#ifdef PA_H
+// pa_create, optionally without its final stream synchronisation (a Gaussian run
+// always synchronises, its host tables being temporaries): for runs created among
+// many others (pa_batch, pa_server), whose next synchronisation reports any error
+// of the initialisation.
+int create_run(const pa_config* cfg, void* cuda_stream, pa_ctx** out, bool synchronize);
+#endif
 // Largest lattice size the sweep kernel supports.
 constexpr int kMaxL = 16;
 // Largest lattice size of a run (larger lattices than kMaxL sweep in global memory).

@@ -15,6 +15,8 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -43,6 +45,7 @@ struct pa_ctx {
   PopDev pops[2]{};
   // Boltzmann weight tables exp(-dbeta 2j), one per distinct dbeta (device)
   std::map<uint64_t, double*> wtables;
+  std::vector<double> wtables_host;  // host copy of the explicit schedule's tables (source of their upload)
   double* wadapt = nullptr;     // adaptive schedule: the table of the current step
   // All device buffers of the run are carved from one stream-ordered allocation:
   // a run costs the memory pool one block, so the pool's free list stays short
@@ -107,6 +110,37 @@ int current_device(int* dev) {
   int d = 0;
   if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) return PA_ERR_CUDA;
   *dev = d;
+  return PA_OK;
+}
+
+// Device memory pool of the runs, one per device, created on first use.  Runs
+// allocate from it stream-ordered (one slab each) like from the default pool, but
+// with every cross-stream reuse policy off: with hundreds of run streams, checking
+// earlier runs' frees for reuse made each allocation take about a millisecond.
+// Memory freed on one stream is still reused by later allocations on that stream,
+// and by any stream once the free has been seen complete through a synchronisation.
+int runs_pool(int dev, cudaMemPool_t* out) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[kMaxDevices] = {};
+  std::lock_guard<std::mutex> lock(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return PA_ERR_CUDA;
+    int off = 0;
+    for (cudaMemPoolAttr a : {cudaMemPoolReuseFollowEventDependencies, cudaMemPoolReuseAllowOpportunistic,
+                              cudaMemPoolReuseAllowInternalDependencies})
+      if (cudaMemPoolSetAttribute(p, a, &off) != cudaSuccess) {
+        cudaMemPoolDestroy(p);
+        return PA_ERR_CUDA;
+      }
+    pools[dev] = p;
+  }
+  *out = pools[dev];
   return PA_OK;
 }
 
@@ -290,6 +324,21 @@ uint64_t bits_of(double x) {
 std::vector<double> host_weights(int n_levels, double dbeta) {
   std::vector<double> w((size_t)n_levels);
   for (int j = 0; j < n_levels; ++j) w[(size_t)j] = std::exp(-(dbeta * (double)(2 * j)));
+  return w;
+}
+
+// Explicit schedules of many runs share their increments (a linear schedule has a
+// handful of distinct ones), so their tables are computed once per process.
+std::shared_ptr<const std::vector<double>> cached_weights(int n_levels, double dbeta) {
+  static std::mutex mu;
+  static std::map<std::pair<int, uint64_t>, std::shared_ptr<const std::vector<double>>> cache;
+  const std::pair<int, uint64_t> key(n_levels, bits_of(dbeta));
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  if (cache.size() >= 1024) cache.clear();  // bounded: at most 1024 tables of <= 12289 doubles
+  auto w = std::make_shared<const std::vector<double>>(host_weights(n_levels, dbeta));
+  cache.emplace(key, w);
   return w;
 }
 
@@ -633,7 +682,9 @@ int pa_footprint(const pa_config* cfg, size_t* bytes) {
   return PA_OK;
 }
 
-int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
+}  // extern "C"
+
+int pa::create_run(const pa_config* cfg, void* cuda_stream, pa_ctx** out, bool synchronize) {
   if (!out) return PA_ERR_INVALID;
   *out = nullptr;
   if (!cfg) return PA_ERR_INVALID;
@@ -671,7 +722,10 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
 
   // sizing pass, one stream-ordered allocation, carving pass
   int rc = layout_buffers(c);
-  if (rc == PA_OK && cudaMallocAsync(reinterpret_cast<void**>(&c->slab), c->slab_bytes, c->stream) != cudaSuccess) {
+  cudaMemPool_t pool = nullptr;
+  if (rc == PA_OK) rc = current_device(&dev) == PA_OK ? runs_pool(dev, &pool) : PA_ERR_CUDA;
+  if (rc == PA_OK &&
+      cudaMallocFromPoolAsync(reinterpret_cast<void**>(&c->slab), c->slab_bytes, pool, c->stream) != cudaSuccess) {
     cudaGetLastError();
     c->slab = nullptr;
     rc = PA_ERR_NOMEM;
@@ -690,9 +744,9 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
     if (rc == PA_OK)  // no stale tile state may carry a step's epoch
       rc = cuda_status(cudaMemsetAsync(c->pops[p].tiles, 0, sizeof(unsigned long long) * (size_t)g.n_count_blocks, s));
   }
-  // Host tables go up in one copy per kind; their host buffers live until the
-  // stream synchronisation at the end of creation.
-  std::vector<double> wall;
+  // Host tables go up in one copy per kind; the +-1 tables' host buffer lives in
+  // the run, the Gaussian ones until the stream synchronisation at the end of
+  // creation (always taken for that model).
   std::vector<uint32_t> gtab_all;
   std::vector<double> gw_all;
   if (g.model == PA_MODEL_GAUSS) {
@@ -720,20 +774,20 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
     if (!c->adaptive) {
       const std::vector<double> d = distinct_dbetas(c->betas);
       const size_t nl = (size_t)g.n_levels;
-      wall.resize(d.size() * nl);
+      c->wtables_host.resize(d.size() * nl);
       for (size_t i = 0; i < d.size(); ++i) {
-        const std::vector<double> w = host_weights(g.n_levels, d[i]);
-        std::copy(w.begin(), w.end(), wall.begin() + (ptrdiff_t)(i * nl));
+        const auto w = cached_weights(g.n_levels, d[i]);
+        std::copy(w->begin(), w->end(), c->wtables_host.begin() + (ptrdiff_t)(i * nl));
       }
       if (rc == PA_OK && !d.empty())
-        rc = copy_async(c, c->wtables[bits_of(d[0])], wall.data(), sizeof(double) * wall.size());
+        rc = copy_async(c, c->wtables[bits_of(d[0])], c->wtables_host.data(), sizeof(double) * c->wtables_host.size());
     }
     if (rc == PA_OK) rc = launch_rc(pa::launch_init_couplings(g, cfg->disorder_seed, c->J, c->jtab, s));
     if (rc == PA_OK) rc = launch_rc(pa::launch_init_population(g, c->pops, 0, s));
     if (rc == PA_OK) rc = launch_rc(pa::launch_levels_and_hist(g, c->pops, 0, c->jtab, 0, s));
   }
   if (rc == PA_OK) rc = measure(c, 0);
-  if (rc == PA_OK) rc = cuda_status(cudaStreamSynchronize(s));
+  if (rc == PA_OK && (synchronize || g.model == PA_MODEL_GAUSS)) rc = cuda_status(cudaStreamSynchronize(s));
   if (rc != PA_OK) {
     destroy(c);
     return rc;
@@ -742,6 +796,12 @@ int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
   c->done = cfg->n_temps == 1;
   *out = c;
   return PA_OK;
+}
+
+extern "C" {
+
+int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
+  return pa::create_run(cfg, cuda_stream, out, true);
 }
 
 int pa_step(pa_ctx* c) {

@@ -6,10 +6,10 @@
 // runs overlap on the device while the host issues their steps round-robin
 // (pa_step of an explicit schedule does not wait for the device); a server run's
 // stream priority is set by its work, smaller runs higher.  Memory is
-// stream-ordered (one cudaMallocAsync / cudaFreeAsync per run in pa_create /
-// pa_destroy), so admitting or retiring a run never synchronises the other runs.
-// Results of a run depend only on its configuration, never on what else is
-// running.
+// stream-ordered (per run one allocation from the runs' memory pool in pa_create
+// and one cudaFreeAsync in pa_destroy), so admitting or retiring a run never
+// synchronises the other runs.  Results of a run depend only on its
+// configuration, never on what else is running.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -135,7 +135,7 @@ int pa_batch_create(const pa_config* cfgs, int32_t n, pa_batch** out) {
     cudaStream_t s = nullptr;
     int rc = make_stream(&s, 0);  // default priority (largest-first priorities measured 2 % slower)
     pa_ctx* c = nullptr;
-    if (rc == PA_OK) rc = pa_create(&cfgs[i], s, &c);
+    if (rc == PA_OK) rc = pa::create_run(&cfgs[i], s, &c, false);
     if (rc == PA_OK) pa::use_chosen_shape(c);
     if (rc != PA_OK) {
       if (s) cudaStreamDestroy(s);
@@ -246,7 +246,7 @@ int admit(pa_server* s) {
       return PA_ERR_CUDA;
     }
     pa_ctx* c = nullptr;
-    const int rc = pa_create(&r.cfg.cfg, st, &c);
+    const int rc = pa::create_run(&r.cfg.cfg, st, &c, false);
     if (rc == PA_OK) pa::use_chosen_shape(c);
     if (rc != PA_OK) {
       // the request fails on its own; the server keeps serving the others
@@ -305,6 +305,9 @@ int pa_server_poll(pa_server* s, uint64_t* done_ids, int32_t cap, int32_t* n_don
     }
     s->finished[a.id] = std::move(f);
     pa_destroy(a.ctx);
+    // the run's work is done, so this waits only for its memory's release, after
+    // which any stream may reuse that memory
+    cudaStreamSynchronize(a.stream);
     s->free_streams[(size_t)a.level].push_back(a.stream);
     s->free_events.push_back(a.done);
     s->used -= a.footprint;
