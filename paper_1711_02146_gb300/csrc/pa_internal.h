@@ -56,7 +56,7 @@ struct PopDev {
   uint32_t* hist;       // [n_temps][n_levels] energy-level histograms
   int32_t* fl;          // [n_levels] floor(tau_k)
   uint32_t* thr;        // [n_levels] 2^32 frac(tau_k)
-  int32_t* famcnt;      // [R] members per family label
+  int32_t* famdone;     // [1] blocks of the family-entropy kernel that have finished (0 between steps)
   int32_t* mhist;       // [R_cap + 1] number of families of each size
   double* partials;     // [n_entropy_blocks] fixed-order partial sums of nu ln nu
   StepRec* rec;         // [n_temps]

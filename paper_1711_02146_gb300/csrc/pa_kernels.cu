@@ -410,29 +410,35 @@ __global__ void __launch_bounds__(kCountThreads) k_resample(RunGeom g, PopArgs a
 
 // ---------------------------------------------------------------- families (a7)
 
-// Members per label (warp-aggregated: sorted labels make equal labels adjacent).
-__global__ void k_fam_count(RunGeom g, PopArgs a, int cur, int t) {
-  const PopDev& P = a.p[blockIdx.y];
-  const int R_new = P.rec[t].R_tilde;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int l = j < R_new ? P.labels[cur][j] : -1;
-  const unsigned peers = __match_any_sync(0xffffffffu, l);
-  if (l >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&P.famcnt[l], __popc(peers));
-}
-
-// sum eta^2, alive families, and the family-size histogram m(eta).  Lanes of a
-// warp with the same family size add to m(eta) with one atomic (most families
-// share a few small sizes, so per-thread atomics would pile onto one address).
-__global__ void k_fam_reduce(RunGeom g, PopArgs a, int t) {
+// Families from the sorted labels: a family is a run of equal labels along the
+// slots (labels start as slot numbers and every copy keeps their order), so the
+// thread at a run's first slot finds its end by binary search and knows the
+// family size eta.  Sum of eta^2, alive families, and the family-size histogram
+// m(eta); lanes of a warp with the same size add to m(eta) with one atomic (most
+// families share a few small sizes, so per-thread atomics would pile onto one
+// address).
+__global__ void k_fam_runs(RunGeom g, PopArgs a, int cur, int t) {
   __shared__ unsigned long long red[2][32];
   const PopDev& P = a.p[blockIdx.y];
-  const int l = blockIdx.x * blockDim.x + threadIdx.x;
-  unsigned long long s2 = 0, nf = 0;
-  const int eta = l < g.R ? P.famcnt[l] : 0;
-  if (eta > 0) {
-    s2 = (unsigned long long)eta * (unsigned long long)eta;
-    nf = 1;
+  const int R_new = P.rec[t].R_tilde;
+  const int32_t* lab = P.labels[cur];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int eta = 0;
+  if (j < R_new) {
+    const int32_t l = lab[j];
+    if (j == 0 || lab[j - 1] != l) {
+      int lo = j + 1, hi = R_new;  // first slot past the run: lab[k] > l for k >= hi
+      while (lo < hi) {
+        const int mid = lo + ((hi - lo) >> 1);
+        if (lab[mid] == l)
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      eta = lo - j;
+    }
   }
+  unsigned long long s2 = (unsigned long long)eta * (unsigned long long)eta, nf = eta > 0 ? 1ull : 0ull;
   const unsigned peers = __match_any_sync(0xffffffffu, eta);
   if (eta > 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&P.mhist[eta], __popc(peers));
   s2 = warp_sum(s2);
@@ -456,9 +462,11 @@ __global__ void k_fam_reduce(RunGeom g, PopArgs a, int t) {
 
 // Fixed-order partial sums of m(eta) nu ln nu, nu = eta / R~ (the family
 // entropy is S_f = -sum): each block covers kEntropyPerBlock sizes, each thread
-// a contiguous run of them, then a fixed tree.
+// a contiguous run of them, then a fixed tree.  The last block to finish adds the
+// partials in block order (a ticket counts finished blocks; no block waits).
 __global__ void __launch_bounds__(kEntropyThreads) k_fam_entropy(RunGeom g, PopArgs a, int t) {
   __shared__ double red[kEntropyThreads];
+  __shared__ bool last;
   const PopDev& P = a.p[blockIdx.y];
   const int R_new = P.rec[t].R_tilde;
   constexpr int per = kEntropyPerBlock / kEntropyThreads;
@@ -480,15 +488,19 @@ __global__ void __launch_bounds__(kEntropyThreads) k_fam_entropy(RunGeom g, PopA
     if (threadIdx.x < h) red[threadIdx.x] = __dadd_rn(red[threadIdx.x], red[threadIdx.x + h]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) P.partials[blockIdx.x] = red[0];
-}
-
-__global__ void k_fam_finish(RunGeom g, PopArgs a, int t) {
-  const PopDev& P = a.p[blockIdx.x];
-  if (threadIdx.x != 0) return;
-  double s = 0.0;
-  for (int b = 0; b < g.n_entropy_blocks; ++b) s = __dadd_rn(s, P.partials[b]);
-  P.rec[t].nu_ln_nu = s;
+  if (threadIdx.x == 0) {
+    P.partials[blockIdx.x] = red[0];
+    __threadfence();
+    last = atomicAdd(P.famdone, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  const volatile double* part = P.partials;
+  double tot = 0.0;
+  for (int b = 0; b < (int)gridDim.x; ++b) tot = __dadd_rn(tot, part[b]);
+  P.rec[t].nu_ln_nu = tot;
+  *P.famdone = 0;  // ready for the next step
 }
 
 // ---------------------------------------------------------------- overlap (a8)
@@ -600,14 +612,9 @@ int launch_scan_scatter(const RunGeom& g, PopDev* pops, int cur, int t, int32_t*
 int launch_families(const RunGeom& g, PopDev* pops, int cur, int t, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   PopArgs a = pack(pops, g.n_pop);
-  for (int p = 0; p < g.n_pop; ++p) {
-    cudaMemsetAsync(pops[p].famcnt, 0, sizeof(int32_t) * (size_t)g.R, s);
-    cudaMemsetAsync(pops[p].mhist, 0, sizeof(int32_t) * ((size_t)g.R_cap + 1), s);
-  }
-  k_fam_count<<<dim3(grid_for(g.R_cap, 256), g.n_pop), 256, 0, s>>>(g, a, cur, t);
-  k_fam_reduce<<<dim3(grid_for(g.R, 256), g.n_pop), 256, 0, s>>>(g, a, t);
+  for (int p = 0; p < g.n_pop; ++p) cudaMemsetAsync(pops[p].mhist, 0, sizeof(int32_t) * ((size_t)g.R_cap + 1), s);
+  k_fam_runs<<<dim3(grid_for(g.R_cap, 256), g.n_pop), 256, 0, s>>>(g, a, cur, t);
   k_fam_entropy<<<dim3(g.n_entropy_blocks, g.n_pop), kEntropyThreads, 0, s>>>(g, a, t);
-  k_fam_finish<<<g.n_pop, 32, 0, s>>>(g, a, t);
   return (int)cudaGetLastError();
 }
 

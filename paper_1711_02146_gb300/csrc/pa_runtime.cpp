@@ -473,7 +473,7 @@ int measure(pa_ctx* c, int t) {
     rc = launch_rc(pa::launch_g_measure(c->g, c->pops, c->cur, t, c->qlhist, c->stream));
   }
   if (rc == PA_OK) {
-    PhaseTimer pt(c, PA_PHASE_FAMILY, 4);
+    PhaseTimer pt(c, PA_PHASE_FAMILY, 2);
     rc = launch_rc(pa::launch_families(c->g, c->pops, c->cur, t, c->stream));
   }
   if (rc == PA_OK && c->g.n_pop == 2) {
@@ -610,7 +610,7 @@ int layout_buffers(pa_ctx* c) {
     rc = rc ? rc : dalloc(c, &P.hist, T * (size_t)g.n_levels);
     rc = rc ? rc : dalloc(c, &P.fl, (size_t)g.n_levels);
     rc = rc ? rc : dalloc(c, &P.thr, (size_t)g.n_levels);
-    rc = rc ? rc : dalloc(c, &P.famcnt, (size_t)g.R);
+    rc = rc ? rc : dalloc(c, &P.famdone, (size_t)1);
     rc = rc ? rc : dalloc(c, &P.mhist, (size_t)g.R_cap + 1);
     rc = rc ? rc : dalloc(c, &P.partials, (size_t)g.n_entropy_blocks);
     rc = rc ? rc : dalloc(c, &P.rec, T);
@@ -741,6 +741,7 @@ int pa::create_run(const pa_config* cfg, void* cuda_stream, pa_ctx** out, bool s
   for (int p = 0; p < g.n_pop && rc == PA_OK; ++p) {
     rc = cuda_status(cudaMemsetAsync(c->pops[p].hist, 0, sizeof(uint32_t) * T * (size_t)g.n_levels, s));
     if (rc == PA_OK) rc = cuda_status(cudaMemsetAsync(c->pops[p].rec, 0, sizeof(StepRec) * T, s));
+    if (rc == PA_OK) rc = cuda_status(cudaMemsetAsync(c->pops[p].famdone, 0, sizeof(int32_t), s));
     if (rc == PA_OK)  // no stale tile state may carry a step's epoch
       rc = cuda_status(cudaMemsetAsync(c->pops[p].tiles, 0, sizeof(unsigned long long) * (size_t)g.n_count_blocks, s));
   }

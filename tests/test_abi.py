@@ -78,7 +78,7 @@ def test_footprint_is_the_slab_layout_without_gpu(palib):
         ncb, neb = -(-Rc // 1024), -(-Rc // 4096)
         want = _up(3 * N) + _up(16 * N) + _up(4) + _up(8 * T * 65)
         per_pop = (2 * (_up(N * pitch) + _up(4 * pitch)) + 3 * _up(4 * pitch) + _up(4 * ncb) + _up(8 * ncb) + _up(4)
-                   + _up(4 * T * nlev) + 2 * _up(4 * nlev) + _up(4 * R) + _up(4 * (Rc + 1)) + _up(8 * neb)
+                   + _up(4 * T * nlev) + 2 * _up(4 * nlev) + _up(4) + _up(4 * (Rc + 1)) + _up(8 * neb)
                    + _up(step_rec * T))
         want += n_pop * per_pop
         n_tables = len({float(d).hex() for d in np.diff(betas)}) if betas is not None else 1
