@@ -84,5 +84,24 @@ def test_footprint_is_the_slab_layout_without_gpu(palib):
         n_tables = len({float(d).hex() for d in np.diff(betas)}) if betas is not None else 1
         want += _up(8 * n_tables * nlev)
         assert pa.footprint(w) == want, (L, R, n_pop)
-    g = Workload("g", L=4, R=1000, disorder_seed=1, run_seed=2, betas=linear_betas(11, 2.0), model=1)
-    assert pa.footprint(g) > pa.footprint(g.with_(model=0))
+    # Gaussian couplings: energies, weights and their fixed-order partial sums (the
+    # chunk totals of 256 slots, then every tree level but the last), copy-number
+    # tables, moment partials and records; per-step site and weight tables instead of
+    # the +-1 weight tables
+    grec, kpat, kgw = 64, 64, 16384
+    for L, R, T in [(4, 1000, 11), (6, 300_000, 5)]:
+        w = Workload("g", L=L, R=R, disorder_seed=1, run_seed=2, betas=linear_betas(T, 2.0), model=1)
+        N, Rc = L ** 3, w.capacity
+        pitch, nlev = -(-Rc // 1024) * 1024, 3 * N + 1
+        ncb, neb, nchunk, nmb = -(-Rc // 1024), -(-Rc // 4096), -(-Rc // 256), -(-Rc // 4096)
+        levels, m = nchunk, nchunk
+        while m > 256:
+            m = -(-m // 256)
+            levels += m
+        want = _up(3 * N) + _up(16 * N) + _up(4) + _up(8 * T * 65)
+        want += (2 * (_up(N * pitch) + _up(4 * pitch)) + 3 * _up(4 * pitch) + _up(4 * ncb) + _up(8 * ncb) + _up(4)
+                 + _up(4 * T * nlev) + 2 * _up(4 * nlev) + _up(4) + _up(4 * (Rc + 1)) + _up(8 * neb)
+                 + _up(step_rec * T))
+        want += (_up(8 * pitch) + _up(8 * Rc) + _up(8 * levels) + 2 * _up(4 * Rc) + _up(16 * nmb) + _up(grec * T))
+        want += _up(12 * N) + _up(4 * T * N * kpat) + _up(8 * T * kgw) + _up(8 * T * 65)
+        assert pa.footprint(w) == want, (L, R)
