@@ -528,11 +528,11 @@ def ours(args):
     st = run.stats()
     ms, updates = reduce_over_ranks(ms, st["updates"], dist, "cuda")
     value = updates / (ms / 1e3)
-    # resampling traffic of the timed steps: levels read and copy numbers written
-    # (k_counts), copy numbers and labels read (k_scatter) per old slot, parents and
-    # labels written per new slot; the replica copy itself is the sweep's gather
+    # resampling traffic of the timed steps (k_resample): level read, copy number
+    # written and label read per old slot, parent and label written per new slot; the
+    # replica copy itself is the sweep's gather
     sizes = [run.obs(u)["R_tilde"] for u in range(run.t - done, run.t + 1)]
-    resample_bytes = sum(16 * r_old + 8 * r_new for r_old, r_new in zip(sizes[:-1], sizes[1:]))
+    resample_bytes = sum(12 * r_old + 8 * r_new for r_old, r_new in zip(sizes[:-1], sizes[1:]))
     resample_ms = st["phase_ms"]["resample"]
 
     # e2e: the same steps through the public API, reading every step's observables back
@@ -581,7 +581,7 @@ def ours(args):
                 "frac": resample_gbs / hbm_peak if resample_gbs and hbm_peak else None,
                 "bytes_per_step": resample_bytes / max(done, 1), "ms_per_step": resample_ms / max(done, 1),
                 "kernels": "k_resample (CUDA events around its launch)",
-                "bytes_basis": "16 B per old slot + 8 B per new slot (algorithmic; spins move in the sweep's gather)"}
+                "bytes_basis": "12 B per old slot + 8 B per new slot (algorithmic; spins move in the sweep's gather)"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": done,
             "warmup": args.warmup, "ms_per_step": ms / max(done, 1), "higher_is_better": True,
