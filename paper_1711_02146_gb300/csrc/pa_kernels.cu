@@ -273,8 +273,8 @@ __global__ void __launch_bounds__(kCountThreads) k_scatter(RunGeom g, PopArgs a,
 // Tiles of kResampleTile old slots are numbered in the order blocks start (a ticket), so a
 // block only ever waits on tiles whose blocks are already running or done.  Each
 // block publishes its copy total, then walks back over its predecessors' entries
-// (a total, or a total including everything before it) until it has its offset,
-// and publishes that inclusive prefix.  Entries carry the step in their upper
+// (a total, or a total including everything before it), kCountThreads at a time,
+// until it has its offset, and publishes that inclusive prefix.  Entries carry the step in their upper
 // word (2t + 1: total, 2t + 2: inclusive), so older steps' entries read as not
 // ready.  A wait gives up after kLookbackSpins polls and sets the timeout flag.
 constexpr int kLookbackSpins = 1 << 20;
@@ -289,6 +289,8 @@ __global__ void __launch_bounds__(kCountThreads) k_resample(RunGeom g, PopArgs a
   __shared__ int scratch[33];
   __shared__ int tile_sh;
   __shared__ long long base_sh;
+  __shared__ unsigned incl_sh[kCountThreads / 32];
+  __shared__ long long sum_sh[kCountThreads / 32];
   const PopDev& P = a.p[blockIdx.y];
   if (threadIdx.x == 0) tile_sh = atomicAdd(P.ticket, 1);
   __syncthreads();
@@ -327,50 +329,63 @@ __global__ void __launch_bounds__(kCountThreads) k_resample(RunGeom g, PopArgs a
   }
   cul = warp_sum(cul);
   if ((threadIdx.x & 31) == 0 && cul) atomicAdd(&P.rec[t].culled, cul);
-  if (threadIdx.x < 32) {  // warp 0: publish the total, look back 32 tiles at a time, publish the prefix
-    const uint32_t ep_total = 2u * (uint32_t)t + 1u, ep_incl = ep_total + 1u;
-    const int lane = threadIdx.x;
-    if (lane == 0 && tile > 0) atomicExch(&P.tiles[tile], ((unsigned long long)ep_total << 32) | (unsigned)total);
-    long long prefix = 0;
-    bool ok = true;
-    for (int hi = tile - 1; hi >= 0 && ok; hi -= 32) {
-      const int q = hi - lane;  // lane 0 nearest; tiles before 0 read as an inclusive 0
-      unsigned long long v = q >= 0 ? poll_tile(&P.tiles[q]) : ((unsigned long long)ep_incl << 32);
-      int spins = 0;
-      while (__any_sync(0xffffffffu, (uint32_t)(v >> 32) < ep_total)) {
-        if (++spins > kLookbackSpins) {
-          ok = false;
-          break;
-        }
-        __nanosleep(32);
-        if ((uint32_t)(v >> 32) < ep_total) v = poll_tile(&P.tiles[q]);
-      }
-      if (!ok) break;
+  // Publish the total, then look back kCountThreads tiles at a time with the whole
+  // block (thread x reads the entry of tile hi - x): the window's nearest inclusive
+  // entry ends the walk, and only the entries nearer than it must be ready.  Every
+  // decision is block-wide (__syncthreads_or, shared words), so all threads leave
+  // the loops together.
+  const uint32_t ep_total = 2u * (uint32_t)t + 1u, ep_incl = ep_total + 1u;
+  if (threadIdx.x == 0 && tile > 0) atomicExch(&P.tiles[tile], ((unsigned long long)ep_total << 32) | (unsigned)total);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int kWarps = kCountThreads / 32;
+  long long prefix = 0;
+  bool ok = true;
+  for (int hi = tile - 1; hi >= 0; hi -= kCountThreads) {
+    const int q = hi - (int)threadIdx.x;  // tiles before 0 read as an inclusive 0
+    unsigned long long v = q >= 0 ? poll_tile(&P.tiles[q]) : ((unsigned long long)ep_incl << 32);
+    int first = kCountThreads;  // nearest inclusive entry of the window (kCountThreads: none)
+    for (int spins = 0;; ++spins) {
       const unsigned incl = __ballot_sync(0xffffffffu, (uint32_t)(v >> 32) == ep_incl);
-      const int stop = incl ? __ffs(incl) - 1 : 31;  // sum lanes 0..stop
-      long long c = lane <= stop ? (long long)(uint32_t)v : 0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-      prefix += __shfl_sync(0xffffffffu, c, 0);
-      if (incl) break;
-    }
-    if (lane == 0) {
-      if (!ok) atomicOr(status, kFlagTimeout);
-      const long long inc = prefix + total;
-      atomicExch(&P.tiles[tile], ((unsigned long long)ep_incl << 32) | (unsigned)(inc > 0x7fffffffLL ? 0x7fffffffLL : inc));
-      base_sh = prefix;
-      // the tile holding the last old slot (tile 0 for an empty population) records R~
-      if (tile == (R_old > 0 ? (R_old - 1) / kResampleTile : 0)) {
-        P.rec[t].R_tilde = inc > g.R_cap ? g.R_cap : (int)inc;
-        if (inc > g.R_cap) atomicOr(status, kFlagCapacity);
-        if (inc == 0) atomicOr(status, kFlagExtinct);
+      if (lane == 0) incl_sh[warp] = incl;
+      __syncthreads();
+      first = kCountThreads;
+      for (int w = kWarps - 1; w >= 0; --w)
+        if (incl_sh[w]) first = 32 * w + __ffs(incl_sh[w]) - 1;
+      const bool waiting = (uint32_t)(v >> 32) < ep_total && (int)threadIdx.x < first;
+      if (!__syncthreads_or(waiting)) break;  // also orders the reads of incl_sh before its next write
+      if (spins >= kLookbackSpins) {
+        ok = false;
+        break;
       }
+      if (waiting) {
+        __nanosleep(32);
+        v = poll_tile(&P.tiles[q]);
+      }
+    }
+    if (!ok) break;
+    long long c = (int)threadIdx.x <= first ? (long long)(uint32_t)v : 0;
+    c = warp_sum(c);
+    if (lane == 0) sum_sh[warp] = c;
+    __syncthreads();
+    for (int w = 0; w < kWarps; ++w) prefix += sum_sh[w];
+    __syncthreads();  // sum_sh is read before the next window writes it
+    if (first < kCountThreads) break;
+  }
+  if (threadIdx.x == 0) {
+    if (!ok) atomicOr(status, kFlagTimeout);
+    const long long inc = prefix + total;
+    atomicExch(&P.tiles[tile], ((unsigned long long)ep_incl << 32) | (unsigned)(inc > 0x7fffffffLL ? 0x7fffffffLL : inc));
+    base_sh = prefix;
+    // the tile holding the last old slot (tile 0 for an empty population) records R~
+    if (tile == (R_old > 0 ? (R_old - 1) / kResampleTile : 0)) {
+      P.rec[t].R_tilde = inc > g.R_cap ? g.R_cap : (int)inc;
+      if (inc > g.R_cap) atomicOr(status, kFlagCapacity);
+      if (inc == 0) atomicOr(status, kFlagExtinct);
     }
   }
   __syncthreads();
   const int32_t* lab_old = P.labels[cur];
   int32_t* lab_new = P.labels[1 - cur];
-  const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int m = 0; m < kChunks; ++m) {
     long long off = base_sh + chunk_base[m] + ex[m];
