@@ -43,7 +43,7 @@ __global__ void k_probe(int64_t iters, uint32_t seed, uint32_t* out) {
 #pragma unroll
   for (int i = 0; i < 8; ++i) x[i] = gid * 2654435761u + seed + (uint32_t)i * 40503u;
   const uint32_t b = seed ^ 0x9E3779B9u, c = seed + 0x7F4A7C15u;
-  if (KIND == PA_BENCH_PHILOX || KIND == PA_BENCH_PHILOX_LOP3) {
+  if constexpr (KIND == PA_BENCH_PHILOX || KIND == PA_BENCH_PHILOX_LOP3) {
     uint32_t acc = 0;
     for (int64_t it = 0; it < iters; ++it) {
       const uint4 r = pa::philox4x32_10(make_uint4(gid, (uint32_t)it, x[0], seed), b, c);
@@ -57,23 +57,23 @@ __global__ void k_probe(int64_t iters, uint32_t seed, uint32_t* out) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) fold ^= x[i];
     out[gid] = acc ^ (KIND == PA_BENCH_PHILOX_LOP3 ? fold : 0u);
-    return;
-  }
-  for (int64_t it = 0; it < iters; ++it) {
+  } else {
+    for (int64_t it = 0; it < iters; ++it) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      if (KIND == PA_BENCH_LOP3) x[i] = lop3_xor(x[i], b, c);
-      if (KIND == PA_BENCH_IADD) x[i] = add_u32(x[i], b);
-      if (KIND == PA_BENCH_IMAD) x[i] = mad_lo(x[i], b, c);
-      if (KIND == PA_BENCH_MULWIDE) x[i] = mulwide_fold(x[i], b);
-      if (KIND == PA_BENCH_MULWIDE_ADD) x[i] = mulwide_add(x[i], b);
-      if (KIND == PA_BENCH_LOP3_IADD) x[i] = add_u32(lop3_xor(x[i], b, c), c);
+      for (int i = 0; i < 8; ++i) {
+        if (KIND == PA_BENCH_LOP3) x[i] = lop3_xor(x[i], b, c);
+        if (KIND == PA_BENCH_IADD) x[i] = add_u32(x[i], b);
+        if (KIND == PA_BENCH_IMAD) x[i] = mad_lo(x[i], b, c);
+        if (KIND == PA_BENCH_MULWIDE) x[i] = mulwide_fold(x[i], b);
+        if (KIND == PA_BENCH_MULWIDE_ADD) x[i] = mulwide_add(x[i], b);
+        if (KIND == PA_BENCH_LOP3_IADD) x[i] = add_u32(lop3_xor(x[i], b, c), c);
+      }
     }
-  }
-  uint32_t acc = 0;
+    uint32_t acc = 0;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) acc ^= x[i];
-  out[gid] = acc;
+    for (int i = 0; i < 8; ++i) acc ^= x[i];
+    out[gid] = acc;
+  }
 }
 
 template <int KIND>
