@@ -105,6 +105,7 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.skip = 0
 
     def __enter__(self):
         try:
@@ -115,6 +116,13 @@ class ClockSampler:
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return self
+        # nvidia-smi takes a moment to start: wait (at most 3 s) for its first sample so
+        # that the samples fall inside the timed region that follows
+        t_end = time.perf_counter() + 3.0
+        while time.perf_counter() < t_end and self.proc.poll() is None and os.path.getsize(self.path) == 0:
+            time.sleep(0.01)
+        self.skip = 1 if os.path.getsize(self.path) > 0 else 0  # that first sample precedes the timed region
         return self
 
     def __exit__(self, *exc):
@@ -130,7 +138,10 @@ class ClockSampler:
             return None
         sm, smax, reasons = [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for line in open(self.path):
+        lines = open(self.path).read().splitlines()
+        if len(lines) > self.skip:
+            lines = lines[self.skip:]
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
