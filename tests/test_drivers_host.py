@@ -85,3 +85,47 @@ def test_hardness_adaptive_population_boundary_is_strict(fake_runs):
     fake_runs.rho_of_R = staticmethod(lambda R: R / 100.0)
     res = drivers.hardness_adaptive_population(_w(), R0=500, max_rounds=2)
     assert fake_runs.created == [500, 750] and not res["equilibrated"]
+
+
+class _FakeView:
+    def __init__(self, m, T):
+        self.m, self.T = m, T
+
+    def obs(self, t):
+        # run m: -beta F = m * t (so the variance over m = 0, 1, 2 is t^2), rho_t = 1 + m,
+        # eps = 0.1 at every step but 0 (run-independent)
+        return {"minus_beta_F": float(self.m * t), "rho_t": 1.0 + self.m, "eps_expected": 0.0 if t == 0 else 0.1}
+
+
+class _FakeBatch:
+    seeds = []
+
+    def __init__(self, ws):
+        _FakeBatch.seeds = [w.run_seed for w in ws]
+        self.T = len(ws[0].betas)
+
+    def run(self):
+        pass
+
+    def run_view(self, m):
+        return _FakeView(m, self.T)
+
+    def close(self):
+        pass
+
+
+def test_free_energy_variance_aggregates_the_runs(monkeypatch):
+    monkeypatch.setattr(drivers.pa, "Batch", _FakeBatch)
+    w = Workload("fv", L=4, R=1000, disorder_seed=1, run_seed=2, betas=linear_betas(5, 1.0))
+    r = drivers.free_energy_variance(w, M=3, first_run_seed=40)
+    assert _FakeBatch.seeds == [40, 41, 42]                     # runs differ only in their run seed
+    t = np.arange(5)
+    assert np.allclose(r["rho_f"], 1000 * t ** 2)               # R var(beta F~), var over m = 0, 1, 2 of m t is t^2
+    assert np.allclose(r["rho_f_err"], np.sqrt(2 / 2) * 1000 * t ** 2)
+    assert np.allclose(r["rho_t"], 2.0) and np.allclose(r["rho_t_err"], 1 / np.sqrt(3))
+    eps = np.where(t == 0, 0.0, 0.1)
+    assert np.allclose(r["rho_t_grow"], 1 + 0.2 * t)            # Eq. rhotb with eps = 0.1 from step 1
+    assert np.allclose(r["rho_f_grow"], 2 * np.pi * 0.01 * t)   # Eq. rhofgrow
+    assert np.allclose(r["rho_f_from_rho_t"], 2.0 - 1.0 - np.cumsum(2 * eps - 2 * np.pi * eps ** 2))
+    with pytest.raises(ValueError):
+        drivers.free_energy_variance(w, M=1)
