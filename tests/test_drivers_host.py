@@ -129,3 +129,44 @@ def test_free_energy_variance_aggregates_the_runs(monkeypatch):
     assert np.allclose(r["rho_f_from_rho_t"], 2.0 - 1.0 - np.cumsum(2 * eps - 2 * np.pi * eps ** 2))
     with pytest.raises(ValueError):
         drivers.free_energy_variance(w, M=1)
+
+
+class _FakeGView:
+    def __init__(self, w):
+        self.w = w
+
+    def gobs(self, t, pop):
+        assert pop == 0
+        d = self.w.disorder_seed
+        # sample d: mean energy -N (d + t) (so e = -(d + t)), link energy e_l = -(d + t) + 0.01 d
+        return {"mean_E": -float(self.w.N * (d + t)), "e_l": -(d + t) + 0.01 * d}
+
+
+class _FakeGBatch:
+    made = []
+
+    def __init__(self, ws):
+        _FakeGBatch.made = list(ws)
+        self.ws = ws
+
+    def run(self):
+        pass
+
+    def run_view(self, i):
+        return _FakeGView(self.ws[i])
+
+    def close(self):
+        pass
+
+
+def test_katzgraber_young_aggregates_over_disorder(monkeypatch):
+    monkeypatch.setattr(drivers.pa, "Batch", _FakeGBatch)
+    betas = np.linspace(0.0, 1.0, 4)
+    r = drivers.katzgraber_young(4, 500, [1, 2, 3], betas, n_sweeps=5, run_seed=9)
+    ws = _FakeGBatch.made
+    assert [w.disorder_seed for w in ws] == [1, 2, 3]
+    assert all(w.n_pop == 2 and w.model == 1 and w.run_seed == 9 and w.n_sweeps == 5 for w in ws)
+    t = np.arange(4)
+    assert np.allclose(r["e"], -(2 + t))                # disorder mean of e = E / N
+    assert np.allclose(r["delta_KY"], 0.02)              # [e_l - e] = mean of 0.01 d over d = 1, 2, 3
+    assert np.allclose(r["delta_KY_err"], np.std([0.01, 0.02, 0.03], ddof=1) / np.sqrt(3))
