@@ -360,19 +360,22 @@ int weight_table(pa_ctx* c, double dbeta, const double** out) {
 }
 
 // Expected culling fraction (1/R) sum_k c(k) (1 - tau_k)_+ of a move by dbeta
-// from level histogram c (occupied levels only; empty ones add exact zeros).
-double culling_fraction(const std::vector<int32_t>& occ, const std::vector<uint32_t>& c, int64_t R, double dbeta) {
+// from level histogram c (occupied levels only; empty ones add exact zeros).  The
+// weights of the first sum are kept in w for the second (each is one exp of the
+// same argument either way, so the result does not change).
+double culling_fraction(const std::vector<int32_t>& occ, const std::vector<uint32_t>& c, int64_t R, double dbeta,
+                        std::vector<double>& w) {
   const int kmin = occ[0];
+  w.resize(occ.size());
   double S = 0.0;
-  for (int k : occ) {
-    double w = std::exp(-(dbeta * (double)(2 * (k - kmin))));
-    S = S + (double)c[(size_t)k] * w;
+  for (size_t i = 0; i < occ.size(); ++i) {
+    w[i] = std::exp(-(dbeta * (double)(2 * (occ[i] - kmin))));
+    S = S + (double)c[(size_t)occ[i]] * w[i];
   }
   double eps = 0.0;
-  for (int k : occ) {
-    double w = std::exp(-(dbeta * (double)(2 * (k - kmin))));
-    double tau = ((double)R * w) / S;
-    if (tau < 1.0) eps = eps + (double)c[(size_t)k] * (1.0 - tau);
+  for (size_t i = 0; i < occ.size(); ++i) {
+    const double tau = ((double)R * w[i]) / S;
+    if (tau < 1.0) eps = eps + (double)c[(size_t)occ[i]] * (1.0 - tau);
   }
   return eps / (double)R;
 }
@@ -393,14 +396,15 @@ int choose_dbeta(pa_ctx* c, double* dbeta) {
   const double prev = c->betas[(size_t)c->t];
   const double rem = c->cfg.beta_max - prev;
   const double target = c->cfg.eps_target;
-  if (culling_fraction(occ, h, c->cfg.R, rem) <= target) {
+  std::vector<double> w;
+  if (culling_fraction(occ, h, c->cfg.R, rem, w) <= target) {
     *dbeta = rem;
     return PA_OK;
   }
   double lo = 0.0, hi = rem;
   for (int it = 0; it < 64; ++it) {
     double mid = 0.5 * (lo + hi);
-    if (culling_fraction(occ, h, c->cfg.R, mid) <= target)
+    if (culling_fraction(occ, h, c->cfg.R, mid, w) <= target)
       lo = mid;
     else
       hi = mid;
