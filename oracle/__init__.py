@@ -144,7 +144,10 @@ def lib():
                                              i32p, u32p, dp]),
             "or_copy_count": (ctypes.c_int32, [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
                                                ctypes.c_int32, ctypes.c_uint32]),
-            "or_resample_tau": (None, [ctypes.c_int64, dp, ctypes.c_uint64, ctypes.c_int32, i32p]),
+            "or_copy_counts": (None, [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, i32p, i32p,
+                                      u32p, i32p]),
+            "or_resample_uniforms": (None, [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, u32p]),
+            "or_resample_tau": (None, [ctypes.c_int64, dp, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, i32p]),
             "or_enumerate_levels": (ctypes.c_int, [ctypes.c_int32, i8p, i64p]),
             "or_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(vp)]),
             "or_step": (ctypes.c_int, [vp]),
@@ -164,9 +167,9 @@ def lib():
             "org_acceptance_threshold": (ctypes.c_uint32, [ctypes.c_double, ctypes.c_int64]),
             "org_sweep_replica": (ctypes.c_int64, [ctypes.c_int32, i32p, i8p, ctypes.c_uint64, ctypes.c_int32,
                                                    ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_double]),
-            "org_weight_tables": (None, [ctypes.c_double, dp]),
-            "org_weight": (ctypes.c_double, [dp, ctypes.c_int64]),
-            "org_tree_sum": (ctypes.c_double, [dp, ctypes.c_int64]),
+            "org_weight": (ctypes.c_double, [ctypes.c_double, ctypes.c_int64]),
+            "org_reweight": (ctypes.c_int, [i64p, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, i64p, dp, dp,
+                                            dp]),
             "org_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(vp)]),
             "org_step": (ctypes.c_int, [vp]),
             "org_run_all": (ctypes.c_int, [vp]),
@@ -262,10 +265,30 @@ def copy_count(run_seed: int, pop: int, t: int, i: int, fl: int, thr: int) -> in
     return int(lib().or_copy_count(run_seed, pop, t, i, fl, thr))
 
 
-def resample_tau(tau: np.ndarray, seed: int, t: int) -> np.ndarray:
+def resample_tau(tau: np.ndarray, seed: int, t: int, pop: int = 0) -> np.ndarray:
+    """Copy numbers by the nearest-integer rule for the given tau of old slots 0..n-1."""
     tau = np.ascontiguousarray(tau, dtype=np.float64)
     out = np.zeros(tau.shape[0], dtype=np.int32)
-    lib().or_resample_tau(tau.shape[0], _p(tau, ctypes.c_double), seed, t, _p(out, ctypes.c_int32))
+    lib().or_resample_tau(tau.shape[0], _p(tau, ctypes.c_double), seed, pop, t, _p(out, ctypes.c_int32))
+    return out
+
+
+def copy_counts(seed: int, pop: int, t: int, levels: np.ndarray, fl: np.ndarray, thr: np.ndarray) -> np.ndarray:
+    """Copy numbers of old slots 0..n-1 at energy levels `levels` from per-level floor/fraction tables."""
+    levels = np.ascontiguousarray(levels, dtype=np.int32)
+    fl = np.ascontiguousarray(fl, dtype=np.int32)
+    thr = np.ascontiguousarray(thr, dtype=np.uint32)
+    assert levels.size == 0 or (levels.min() >= 0 and levels.max() < fl.size == thr.size)
+    out = np.zeros(levels.shape[0], dtype=np.int32)
+    lib().or_copy_counts(seed, pop, t, levels.shape[0], _p(levels, ctypes.c_int32), _p(fl, ctypes.c_int32),
+                         _p(thr, ctypes.c_uint32), _p(out, ctypes.c_int32))
+    return out
+
+
+def resample_uniforms(seed: int, t: int, n: int, pop: int = 0) -> np.ndarray:
+    """The uniform words the resampling at step t draws for old slots 0..n-1."""
+    out = np.zeros(n, dtype=np.uint32)
+    lib().or_resample_uniforms(seed, pop, t, n, _p(out, ctypes.c_uint32))
     return out
 
 
@@ -423,7 +446,6 @@ class Run:
 # ---------------------------------------------------------------- Gaussian couplings
 
 JSCALE = 2 ** 20
-T_SIZE = 8192 + 8192
 
 
 def gcouplings(L: int, seed: int) -> np.ndarray:
@@ -454,19 +476,22 @@ def gacceptance_threshold(beta: float, dE: int) -> int:
     return int(lib().org_acceptance_threshold(beta, dE))
 
 
-def gweight_tables(dbeta: float) -> np.ndarray:
-    T = np.zeros(T_SIZE, dtype=np.float64)
-    lib().org_weight_tables(dbeta, _p(T, ctypes.c_double))
-    return T
+def gweight(dbeta: float, d: int) -> float:
+    """Resampling weight exp(-dbeta d 2^-20) of a replica d above the lowest energy (Eq. Q)."""
+    return float(lib().org_weight(dbeta, int(d)))
 
 
-def gweight(T: np.ndarray, d: int) -> float:
-    return float(lib().org_weight(_p(np.ascontiguousarray(T), ctypes.c_double), d))
-
-
-def tree_sum(x: np.ndarray) -> float:
-    x = np.ascontiguousarray(x, dtype=np.float64)
-    return float(lib().org_tree_sum(_p(x, ctypes.c_double), x.shape[0]))
+def greweight(E: np.ndarray, R: int, dbeta: float):
+    """Reweighting of Gaussian-coupling energies E (units of 2^-20) by dbeta, Eqs. (tau),
+    (Q), (eq_num_elim): returns (E_min, S', expected culling fraction, tau per replica)."""
+    E = np.ascontiguousarray(E, dtype=np.int64)
+    tau = np.zeros(E.shape[0], dtype=np.float64)
+    Emin, S, eps = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+    rc = lib().org_reweight(_p(E, ctypes.c_int64), E.shape[0], R, dbeta, ctypes.byref(Emin), ctypes.byref(S),
+                            ctypes.byref(eps), _p(tau, ctypes.c_double))
+    if rc != OK:
+        raise RuntimeError(f"org_reweight failed: {rc}")
+    return int(Emin.value), float(S.value), float(eps.value), tau
 
 
 class GRun:

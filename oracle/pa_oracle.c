@@ -13,8 +13,9 @@
  *   or_energy            pinned: ferromagnet / Neel ground states, enumeration identities
  *   or_enumerate_levels  pinned: sum g = 2^N, g(E) = g(-E) for even L, beta=0 variance 3N,
  *                        ferromagnet degeneracies, gauge invariance, high-T expansion
- *   or_metropolis_test   pinned: equals the plain comparison of the full bit-column uniform;
- *                        the uniform is uniform and independent between slots
+ *   or_metropolis_uniform pinned: the bit-column uniform is uniform and independent
+ *                        between slots, half-sweeps and populations
+ *   or_metropolis_test   pinned: equals the plain comparison of the full bit-column uniform
  *   or_sweep_replica     pinned: Boltzmann energy distribution vs enumeration (L=2, 3)
  *   or_reweight          pinned: sum_k c_k tau_k = R, tau ratios = Boltzmann ratios
  *   or_copy_count / or_resample_tau
@@ -136,10 +137,12 @@ static int32_t local_field(int32_t L, const int8_t* J, const int8_t* s, int32_t 
  *
  * r is the replica's bit column in the Metropolis stream: bit 31 - p of r
  * (p = 0 .. 31) is bit (slot mod 32) of word (p mod 4) of the Philox block at
- * counter (site, half-sweep, 8 floor(slot / 32) + floor(p / 4), t).  The test
- * r < thr reads r from its top bit down and stops at the first bit where r and
- * thr differ (r < thr exactly when there r has 0 and thr has 1), so a decision
- * draws only the blocks that reach that bit: two bits on average. */
+ * counter (site, half-sweep, 8 floor(slot / 32) + floor(p / 4), t).  The sweep
+ * below draws the whole uniform and compares it with thr.  or_metropolis_test is
+ * the same comparison read from the top bit down, stopping at the first bit where
+ * r and thr differ (r < thr exactly when there r has 0 and thr has 1); it is kept
+ * as a separate helper, pinned against the plain comparison, because the CUDA
+ * path decides its flips that way. */
 
 void or_metropolis_thresholds(double beta, uint32_t thr[3]) {
   for (int m = 1; m <= 3; ++m) {
@@ -190,8 +193,6 @@ static int32_t n_colours(int32_t L) { return (L % 2 == 0) ? 2 : 3; }
 int32_t or_sweep_replica(int32_t L, const int8_t* J, int8_t* s, uint64_t run_seed, int32_t pop,
                          int64_t slot, int32_t t, int32_t n_sweeps, const uint32_t thr[3]) {
   int32_t ncol = n_colours(L);
-  uint32_t key[2];
-  or_key(run_seed, OR_P_METROPOLIS, (uint32_t)pop, key);
   int32_t dE_total = 0;
   for (int32_t sw = 0; sw < n_sweeps; ++sw) {
     for (int32_t c = 0; c < ncol; ++c) {
@@ -204,7 +205,7 @@ int32_t or_sweep_replica(int32_t L, const int8_t* J, int8_t* s, uint64_t run_see
             int32_t dE = 2 * s[n] * h;
             uint32_t site_index = (ncol == 2) ? (uint32_t)(n >> 1) : (uint32_t)n;
             uint32_t half_sweep = (uint32_t)(ncol * sw + c);
-            if (dE <= 0 || test_below(key, site_index, half_sweep, slot, t, thr[dE / 4 - 1])) {
+            if (dE <= 0 || or_metropolis_uniform(run_seed, pop, site_index, half_sweep, slot, t) < thr[dE / 4 - 1]) {
               s[n] = (int8_t)(-s[n]);
               dE_total += dE;
             }
@@ -260,11 +261,25 @@ int32_t or_copy_count(uint64_t run_seed, int32_t pop, int32_t t, int64_t i, int3
   return fl + (r < thr ? 1 : 0);
 }
 
-void or_resample_tau(int64_t n, const double* tau, uint64_t seed, int32_t t, int32_t* n_out) {
+/* Copy numbers of old slots 0..n-1 whose energy levels are given, from per-level
+ * tables of floor(tau) and 2^32 frac(tau) (the rule above, tau taken per level). */
+void or_copy_counts(uint64_t run_seed, int32_t pop, int32_t t, int64_t n, const int32_t* levels, const int32_t* fl,
+                    const uint32_t* thr, int32_t* out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = or_copy_count(run_seed, pop, t, i, fl[levels[i]], thr[levels[i]]);
+}
+
+/* The uniform words r_i that the resampling at step t draws for old slots 0..n-1. */
+void or_resample_uniforms(uint64_t run_seed, int32_t pop, int32_t t, int64_t n, uint32_t* r) {
+  uint32_t key[2];
+  or_key(run_seed, OR_P_RESAMPLE, (uint32_t)pop, key);
+  for (int64_t i = 0; i < n; ++i) r[i] = philox_word(key, (uint32_t)(i >> 2), 0, 0, (uint32_t)t, (int)(i & 3));
+}
+
+void or_resample_tau(int64_t n, const double* tau, uint64_t seed, int32_t pop, int32_t t, int32_t* n_out) {
   for (int64_t i = 0; i < n; ++i) {
     double f = floor(tau[i]);
     uint32_t thr = (uint32_t)((tau[i] - f) * 4294967296.0);
-    n_out[i] = or_copy_count(seed, 0, t, i, (int32_t)f, thr);
+    n_out[i] = or_copy_count(seed, pop, t, i, (int32_t)f, thr);
   }
 }
 

@@ -105,7 +105,10 @@ int32_t or_reweight(int32_t n_levels, const int64_t* c, int64_t R, double dbeta,
 int32_t or_copy_count(uint64_t run_seed, int32_t pop, int32_t t, int64_t i, int32_t fl, uint32_t thr);
 /* Nearest-integer resampling of arbitrary expected copy numbers tau[0..n) (used to
  * check the resampling law and the family process on synthetic weights). */
-void or_resample_tau(int64_t n, const double* tau, uint64_t seed, int32_t t, int32_t* n_out);
+void or_copy_counts(uint64_t run_seed, int32_t pop, int32_t t, int64_t n, const int32_t* levels, const int32_t* fl,
+                    const uint32_t* thr, int32_t* out);
+void or_resample_uniforms(uint64_t run_seed, int32_t pop, int32_t t, int64_t n, uint32_t* r);
+void or_resample_tau(int64_t n, const double* tau, uint64_t seed, int32_t pop, int32_t t, int32_t* n_out);
 /* Exact density of states g[k], k = 0..3N, by enumerating all 2^N states (N <= 30) */
 int or_enumerate_levels(int32_t L, const int8_t* J, int64_t* g);
 
@@ -133,7 +136,6 @@ void or_destroy(or_run* run);
 /* ---- Gaussian couplings (the paper's model, §II.A): pa_oracle_gauss.c ----
  * Couplings J ~ N(0,1) clamped to [-5, 5] in fixed point Jq = round(J 2^20);
  * energies in the same units (int64).  Explicit or adaptive schedules, even L. */
-#define ORG_T2_SIZE 8192   /* entries of the coarsest weight table */
 
 typedef struct {
   int32_t t;
@@ -165,9 +167,11 @@ int64_t org_energy(int32_t L, const int32_t* Jq, const int8_t* s);
 uint32_t org_acceptance_threshold(double beta, int64_t dE);
 int64_t org_sweep_replica(int32_t L, const int32_t* Jq, int8_t* s, uint64_t run_seed, int32_t pop, int64_t slot,
                           int32_t t, int32_t n_sweeps, double beta);
-void org_weight_tables(double dbeta, double* T);   /* T: 8192 + ORG_T2_SIZE doubles */
-double org_weight(const double* T, int64_t d);
-double org_tree_sum(const double* x, int64_t n);
+/* resampling weight exp(-dbeta d 2^-20) of a replica d above the lowest energy */
+double org_weight(double dbeta, int64_t d);
+/* E_min, S' = sum_i w_i, (1/R) sum_{tau_i<1} (1 - tau_i), and tau_i (if tau != NULL) */
+int org_reweight(const int64_t* E, int64_t n, int64_t R, double dbeta, int64_t* E_min, double* S_prime,
+                 double* eps_expected, double* tau);
 int org_create(const or_config* cfg, org_run** out);
 int org_step(org_run* run);
 int org_run_all(org_run* run);

@@ -12,15 +12,12 @@
  *     Philox word r < thr(dE) = min(floor(2^32 exp(-beta dE)), 2^32 - 2), the
  *     exponential in double precision (2^32 p is then exact, a power-of-two
  *     scaling, and the floor the only rounding);
- *   - resampling weights w = exp(-dbeta (E - E_min)) are the double products
- *     (T2[d >> 24] * T1[(d >> 12) & 4095]) * T0[d & 4095] of per-step tables
- *     T_k[m] = exp(-dbeta m 2^(12k) 2^-20), d = (E - E_min) in fixed point;
- *   - S' and the culling sum are taken in a fixed order: groups of 256 values
- *     (the last one padded with zeros), each by a binary tree (a[i] += a[i + h],
- *     h = 128, 64, ..., 1); the group totals again in groups of 256 by the same
- *     tree, and so on until one value remains (the paper fixes no order);
- *   - the adaptive schedule (§IV.B) bisects on the culling fraction computed
- *     with exactly these weights and sums.
+ *   - resampling follows Eqs. (tau), (Q) and (eq_num_elim) as written, replica by
+ *     replica: each weight is one exponential, w_i = exp(-dbeta (E_i - E_min)) with
+ *     E_min the lowest energy present (Eq. Q divided by its largest term); S' is
+ *     the sum of the weights in slot order, tau_i = R w_i / S', and the culling sum
+ *     adds 1 - tau_i over the replicas with tau_i < 1, again in slot order;
+ *   - the adaptive schedule (§IV.B) bisects on that culling fraction.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -91,7 +88,6 @@ int64_t org_energy(int32_t L, const int32_t* Jq, const int8_t* s) {
 
 /* ---- Metropolis ---- */
 
-/* Energy change of flipping s_n, split over the two halves of its bonds. */
 /* Energy change of flipping s_n: dE = 2 s_n sum_m J_nm s_m over its six bonds. */
 static int64_t flip_change(int32_t L, const int32_t* Jq, const int8_t* s, int32_t n) {
   int32_t xp = g_neighbour(L, n, 0, +1), xm = g_neighbour(L, n, 0, -1);
@@ -131,39 +127,34 @@ int64_t org_sweep_replica(int32_t L, const int32_t* Jq, int8_t* s, uint64_t run_
   return total;
 }
 
-/* ---- resampling weights and the fixed summation order ---- */
+/* ---- resampling, §II Eqs. (tau), (Q) and (eq_num_elim) ---- */
 
-void org_weight_tables(double dbeta, double* T) {
-  for (int32_t m = 0; m < 4096; ++m) T[m] = exp(-(dbeta * ((double)m * 0x1p-20)));
-  for (int32_t m = 0; m < 4096; ++m) T[4096 + m] = exp(-(dbeta * ((double)((int64_t)m << 12) * 0x1p-20)));
-  for (int32_t m = 0; m < ORG_T2_SIZE; ++m) T[8192 + m] = exp(-(dbeta * ((double)((int64_t)m << 24) * 0x1p-20)));
-}
+/* Weight of a replica whose energy lies d above the lowest one (fixed point,
+ * units of 2^-20): exp(-dbeta (E - E_min)). */
+double org_weight(double dbeta, int64_t d) { return exp(-(dbeta * ((double)d * 0x1p-20))); }
 
-double org_weight(const double* T, int64_t d) {
-  return (T[8192 + (d >> 24)] * T[4096 + ((d >> 12) & 4095)]) * T[d & 4095];
-}
-
-double org_tree_sum(const double* x, int64_t n) {
-  if (n <= 0) return 0.0;
-  double* cur = (double*)malloc(sizeof(double) * (size_t)n);
-  if (!cur) abort();
-  memcpy(cur, x, sizeof(double) * (size_t)n);
-  int64_t m = n;
-  for (;;) {
-    const int64_t groups = (m + 255) / 256;
-    for (int64_t k = 0; k < groups; ++k) {
-      double a[256];
-      for (int i = 0; i < 256; ++i) a[i] = (256 * k + i < m) ? cur[256 * k + i] : 0.0;
-      for (int h = 128; h >= 1; h >>= 1)
-        for (int i = 0; i < h; ++i) a[i] = a[i] + a[i + h];
-      cur[k] = a[0];  /* group k reads entries >= 256 k, so this write is behind the reads */
-    }
-    m = groups;
-    if (m == 1) break;
+/* The reweighting of a population of n replicas with energies E to a temperature
+ * dbeta lower: E_min, S' = sum_i w_i (slot order), the expected culling fraction
+ * (1/R) sum_{tau_i < 1} (1 - tau_i) (slot order), and tau_i = R w_i / S' when tau
+ * is not NULL.  Returns OR_ERR_INVALID for an empty population. */
+int org_reweight(const int64_t* E, int64_t n, int64_t R, double dbeta, int64_t* E_min, double* S_prime,
+                 double* eps_expected, double* tau) {
+  if (n < 1) return OR_ERR_INVALID;
+  int64_t Emin = E[0];
+  for (int64_t i = 1; i < n; ++i)
+    if (E[i] < Emin) Emin = E[i];
+  double S = 0.0;
+  for (int64_t i = 0; i < n; ++i) S = S + org_weight(dbeta, E[i] - Emin);
+  double cull = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double t_i = ((double)R * org_weight(dbeta, E[i] - Emin)) / S;
+    if (t_i < 1.0) cull = cull + (1.0 - t_i);
+    if (tau) tau[i] = t_i;
   }
-  const double total = cur[0];
-  free(cur);
-  return total;
+  *E_min = Emin;
+  *S_prime = S;
+  *eps_expected = cull / (double)R;
+  return OR_OK;
 }
 
 /* ---- the run (§II), explicit schedules ---- */
@@ -398,52 +389,33 @@ int org_create(const or_config* cfg, org_run** out) {
   return OR_OK;
 }
 
-/* Expected culling fraction (Eq. eq_num_elim / R) of a move by dbeta from the
- * population p, with this file's weights and summation order. */
-static double eps_g(const org_run* r, const org_pop* P, double dbeta, double* T, double* w) {
-  const int64_t* E = P->E[P->cur];
-  int64_t Emin = INT64_MAX;
-  for (int64_t i = 0; i < P->Rt; ++i)
-    if (E[i] < Emin) Emin = E[i];
-  org_weight_tables(dbeta, T);
-  for (int64_t i = 0; i < P->Rt; ++i) w[i] = org_weight(T, E[i] - Emin);
-  double S = org_tree_sum(w, P->Rt);
-  for (int64_t i = 0; i < P->Rt; ++i) {
-    double tau = ((double)r->cfg.R * w[i]) / S;
-    w[i] = tau < 1.0 ? 1.0 - tau : 0.0;
-  }
-  return org_tree_sum(w, P->Rt) / (double)r->cfg.R;
+/* Expected culling fraction (Eq. eq_num_elim / R) of a move by dbeta from population p. */
+static double eps_g(const org_run* r, const org_pop* P, double dbeta) {
+  int64_t Emin;
+  double S, eps;
+  org_reweight(P->E[P->cur], P->Rt, r->cfg.R, dbeta, &Emin, &S, &eps, NULL);
+  return eps;
 }
 
 /* Adaptive step (§IV.B), as for +-1 couplings: the largest dbeta in
  * (0, beta_max - beta] whose culling fraction does not exceed the target, by 64
  * bisection halvings; population 0 decides. */
-static int choose_dbeta_g(const org_run* r, int32_t t, double* dbeta) {
+static void choose_dbeta_g(const org_run* r, int32_t t, double* dbeta) {
   const org_pop* P = &r->pops[0];
-  double* T = (double*)malloc(sizeof(double) * (8192 + ORG_T2_SIZE));
-  double* w = (double*)malloc(sizeof(double) * (size_t)(P->Rt > 0 ? P->Rt : 1));
-  if (!T || !w) {
-    free(T);
-    free(w);
-    return OR_ERR_NOMEM;
-  }
   double rem = r->cfg.beta_max - r->betas[t - 1];
-  if (eps_g(r, P, rem, T, w) <= r->cfg.eps_target) {
+  if (eps_g(r, P, rem) <= r->cfg.eps_target) {
     *dbeta = rem;
-  } else {
-    double lo = 0.0, hi = rem;
-    for (int it = 0; it < 64; ++it) {
-      double mid = 0.5 * (lo + hi);
-      if (eps_g(r, P, mid, T, w) <= r->cfg.eps_target)
-        lo = mid;
-      else
-        hi = mid;
-    }
-    *dbeta = lo > 0.0 ? lo : hi;
+    return;
   }
-  free(T);
-  free(w);
-  return OR_OK;
+  double lo = 0.0, hi = rem;
+  for (int it = 0; it < 64; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (eps_g(r, P, mid) <= r->cfg.eps_target)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  *dbeta = lo > 0.0 ? lo : hi;
 }
 
 int org_step(org_run* r) {
@@ -453,63 +425,35 @@ int org_step(org_run* r) {
   if (r->cfg.betas) {
     dbeta = r->betas[t] - r->betas[t - 1];
   } else {
-    int rc = choose_dbeta_g(r, t, &dbeta);
-    if (rc != OR_OK) return rc;
+    choose_dbeta_g(r, t, &dbeta);
     double b = r->betas[t - 1] + dbeta;
     if (b >= r->cfg.beta_max || dbeta == r->cfg.beta_max - r->betas[t - 1]) b = r->cfg.beta_max;
     r->betas[t] = b;
   }
-  double* T = (double*)malloc(sizeof(double) * (8192 + ORG_T2_SIZE));
-  if (!T) return OR_ERR_NOMEM;
-  org_weight_tables(dbeta, T);
   for (int32_t p = 0; p < r->cfg.n_pop; ++p) {
     org_pop* P = &r->pops[p];
     org_obs* o = gobs_at(r, t, p);
     const int64_t* Eold = P->E[P->cur];
     int64_t R = P->Rt;
     /* 1. weights measured from the lowest energy (Eq. Q), S' and tau (Eq. tau) */
-    int64_t Emin = INT64_MAX;
-    for (int64_t i = 0; i < R; ++i)
-      if (Eold[i] < Emin) Emin = Eold[i];
-    double* w = (double*)malloc(sizeof(double) * (size_t)R);
-    double* c = (double*)malloc(sizeof(double) * (size_t)R);
-    if (!w || !c) {
-      free(w);
-      free(c);
-      free(T);
-      return OR_ERR_NOMEM;
-    }
-    for (int64_t i = 0; i < R; ++i) {
-      int64_t d = Eold[i] - Emin;
-      if ((d >> 24) >= ORG_T2_SIZE) {
-        free(w);
-        free(c);
-        free(T);
-        return OR_ERR_INVALID;
-      }
-      w[i] = org_weight(T, d);
-    }
-    double S = org_tree_sum(w, R);
+    double* tau = (double*)malloc(sizeof(double) * (size_t)R);
+    if (!tau) return OR_ERR_NOMEM;
+    int64_t Emin;
+    double S, eps;
+    org_reweight(Eold, R, r->cfg.R, dbeta, &Emin, &S, &eps, tau);
     /* 2. copy numbers, nearest-integer rule */
     int64_t newR = 0, culled = 0;
     for (int64_t i = 0; i < R; ++i) {
-      double tau = ((double)r->cfg.R * w[i]) / S;
-      double f = floor(tau);
-      uint32_t thr = (uint32_t)((tau - f) * 4294967296.0);
-      c[i] = tau < 1.0 ? 1.0 - tau : 0.0;
+      double f = floor(tau[i]);
+      uint32_t thr = (uint32_t)((tau[i] - f) * 4294967296.0);
       int32_t n = or_copy_count(r->cfg.run_seed, p, t, i, (int32_t)f, thr);
       P->counts[i] = n;
       newR += n;
       culled += n == 0;
     }
-    double eps = org_tree_sum(c, R) / (double)r->cfg.R;
-    free(w);
-    free(c);
+    free(tau);
     P->counts_n = R;
-    if (newR > r->cfg.R_cap || newR == 0) {
-      free(T);
-      return newR == 0 ? OR_ERR_INVALID : OR_ERR_CAPACITY;
-    }
+    if (newR > r->cfg.R_cap || newR == 0) return newR == 0 ? OR_ERR_INVALID : OR_ERR_CAPACITY;
     /* 3. the new population, copies in slot order with inherited labels */
     int nxt = 1 - P->cur;
     int64_t j = 0;
@@ -537,7 +481,6 @@ int org_step(org_run* r) {
     o->eps_expected = eps;
     o->culled = culled;
   }
-  free(T);
   int rc = measure_g(r, t);
   if (rc != OR_OK) return rc;
   r->t = t;

@@ -3,7 +3,7 @@ that do not come from the oracle itself: the normal law of the couplings, exact
 enumeration of all states at L = 2 (partition function, energy, link overlap),
 the Katzgraber-Young identity of Gaussian disorder (Eqs. KY, el), the Boltzmann
 distribution reached by the Metropolis sweeps, and the closed forms behind the
-acceptance and resampling tables."""
+acceptance thresholds and the resampling weights and sums."""
 import itertools
 import math
 
@@ -104,46 +104,57 @@ def test_acceptance_threshold_is_the_boltzmann_factor(beta):
         assert oracle.gacceptance_threshold(beta, 1) == 2 ** 32 - 2   # the cap: "always" stays ΔE <= 0 only
 
 
-def test_weight_tables_and_tree_sum():
+def test_reweighting_is_eqs_tau_q_and_eq_num_elim():
+    """The resampling quantities of a population with real energies against the
+    paper's definitions computed independently: each weight against the exact
+    exponential (60-digit decimal), S' against the correctly rounded sum of exact
+    weights (math.fsum) within the n-ulp bound of a sum of positive terms,
+    sum_i tau_i = R, tau ratios = Boltzmann ratios, the culling fraction against
+    Eq. (eq_num_elim) summed exactly, and shift invariance (weights measured from
+    E_min)."""
+    import decimal
+    decimal.getcontext().prec = 60
     rng = np.random.default_rng(2)
+    u = 2.0 ** -53
     for dbeta in (0.013, 0.2, 1.5):
-        T = oracle.gweight_tables(dbeta)
-        for d in [0, 1, 4095, 4096, 2 ** 24 - 1, 2 ** 24, 3 * 2 ** 30] + list(rng.integers(0, 2 ** 36, 50)):
-            x = dbeta * int(d) * SCALE
-            exact = math.exp(-x)
-            # a few roundings of the argument and of three factors: relative error ~ (1 + x) ulp
-            assert abs(oracle.gweight(T, int(d)) - exact) <= (2e-15 + 4e-16 * x) * exact + 1e-300
-    for n in (1, 255, 256, 257, 5000):
-        x = rng.random(n)
-        assert abs(oracle.tree_sum(x) - math.fsum(x)) <= 1e-13 * math.fsum(x)
-    # the fixed order is the definition: groups of 256 by the binary tree, the group
-    # totals again in groups of 256, until one value remains
-    def group_tree(v):
-        out = []
-        for c0 in range(0, len(v), 256):
-            a = np.zeros(256)
-            a[: min(256, len(v) - c0)] = v[c0:c0 + 256]
-            h = 128
-            while h >= 1:
-                a[:h] = a[:h] + a[h:2 * h]
-                h //= 2
-            out.append(a[0])
-        return np.array(out)
-    for n in (1, 256, 1000, 256 * 256 + 1, 300_000):
-        x = rng.random(n) * rng.choice([1e-9, 1.0, 1e9], n)  # wide magnitudes: orders round differently
-        v = x
-        while True:
-            v = group_tree(v)
-            if len(v) == 1:
-                break
-        assert oracle.tree_sum(x) == v[0], n
-    # a dropped level or a sequential pass over the group totals is a different sum
-    x = rng.random(70_000) * rng.choice([1e-9, 1.0, 1e9], 70_000)
-    seq = 0.0
-    for c in group_tree(x):
-        seq = seq + c
-    assert oracle.tree_sum(x) != seq
-    assert oracle.tree_sum(np.array([])) == 0.0
+        for d in [0, 1, 4095, 4096, 2 ** 24 - 1, 2 ** 24, 3 * 2 ** 30] + [int(v) for v in rng.integers(0, 2 ** 36, 50)]:
+            exact = float((decimal.Decimal(-dbeta) * decimal.Decimal(d) / decimal.Decimal(2 ** 20)).exp())
+            x = dbeta * d * SCALE
+            # one rounding of the argument (relative u, so absolute u x) and one of exp
+            assert abs(oracle.gweight(dbeta, d) - exact) <= (2 * u + 2 * u * x) * exact + 1e-300
+    for n, R, dbeta in ((1, 1, 0.5), (700, 1000, 0.3), (5000, 4000, 0.05), (20000, 20000, 1.1)):
+        E = rng.normal(-1.5 * 1000, 40.0, n)
+        Eq = np.rint(E / SCALE).astype(np.int64)
+        Emin, S, eps, tau = oracle.greweight(Eq, R, dbeta)
+        assert Emin == int(Eq.min())
+        w = [float((decimal.Decimal(-dbeta) * decimal.Decimal(int(e - Emin)) / decimal.Decimal(2 ** 20)).exp())
+             for e in Eq]
+        S_exact = math.fsum(w)
+        assert abs(S - S_exact) <= (n + 2) * u * S_exact
+        assert abs(math.fsum(tau) - R) <= 1e-12 * R
+        i, j = rng.integers(0, n, 2)
+        ratio = math.exp(-dbeta * (int(Eq[i]) - int(Eq[j])) * SCALE)
+        assert abs(tau[i] / tau[j] - ratio) <= 1e-12 * ratio
+        eps_exact = math.fsum(max(0.0, 1.0 - R * wk / S_exact) for wk in w) / R
+        assert abs(eps - eps_exact) <= 1e-12 * max(eps_exact, 1e-300) + 1e-15
+        # the same population shifted by a constant energy: the same S', tau and eps
+        E2, S2, eps2, tau2 = oracle.greweight(Eq + 123456789, R, dbeta)
+        assert E2 == Emin + 123456789 and S2 == S and eps2 == eps and np.array_equal(tau2, tau)
+    with pytest.raises(RuntimeError):
+        oracle.greweight(np.zeros(0, np.int64), 10, 0.1)
+
+
+def test_culling_fraction_of_gaussian_energies_is_eq_eps():
+    """Eq. (eps): for normally distributed energies and small dbeta sigma, the
+    expected culling fraction is dbeta sigma_E / sqrt(2 pi) to leading order."""
+    rng = np.random.default_rng(5)
+    n, sigma = 200_000, 30.0
+    Eq = np.rint(rng.normal(-1200.0, sigma, n) / SCALE).astype(np.int64)
+    for x in (0.005, 0.02):
+        dbeta = x / sigma
+        _, _, eps, _ = oracle.greweight(Eq, n, dbeta)
+        want = x / math.sqrt(2 * math.pi)
+        assert abs(eps - want) < 0.03 * want + 4 / math.sqrt(n) * want, (x, eps, want)
 
 
 def test_katzgraber_young_identity_by_enumeration():
