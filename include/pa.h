@@ -244,6 +244,20 @@ typedef struct {
 int pa_stats_reset(pa_ctx* ctx, int enable_timing);
 int pa_get_stats(pa_ctx* ctx, pa_stats* out);
 
+/* ---- testing hook: the bounded wait of the resampling (§II, +-1 couplings) ----
+ * The single-pass resampling finds each tile's offset by waiting, with a bounded
+ * number of polls, for the entries its predecessor tiles publish.  This sets, for
+ * the later steps of run ctx, that number of polls (spins >= 1; 0 restores the
+ * default of 2^20) and a tile (numbered in the order its block starts) whose block
+ * publishes neither its total nor its offset (withheld_tile >= 0; -1: none), so
+ * that the waits of the blocks after it run out.  A wait that runs out ends the
+ * kernel normally with the device timeout flag set: that step's results are not
+ * valid, and the run reports PA_ERR_TIMEOUT from its next synchronising call
+ * (pa_sync, pa_observables, ...) and every call after it.  The device, and other
+ * runs on it, are not affected.  For tests of that failure path only;
+ * PA_ERR_INVALID for spins < 0 or withheld_tile < -1. */
+int pa_debug_lookback(pa_ctx* ctx, int32_t spins, int32_t withheld_tile);
+
 /* Waits for the context's stream; returns the first recorded error, if any. */
 int pa_sync(pa_ctx* ctx);
 
@@ -371,23 +385,33 @@ int pa_sweep_autotune(int32_t L, int32_t R, int32_t launches, double* ms_per_lau
  * buffers: for old slots i < n_old with energy level levels[i] (unsatisfied
  * bonds), the copy numbers counts[i] = fl[k] + [r_i < thr[k]] with
  * r_i = word (i & 3) of Philox4x32-10 keyed by (run_seed, resampling, pop) at
- * counter (i >> 2, 0, 0, t) (the nearest-integer rule of §II); the parent of
- * every new slot j < min(*n_new, parents_cap) (parents[j] = i for
+ * counter (i >> 2, 0, 0, t): floor(tau) copies, plus one more when the uniform
+ * word falls below the fraction of tau scaled to 2^32; the parent of every new
+ * slot j < min(*n_new, parents_cap) (parents[j] = i for
  * offset_i <= j < offset_i + n_i, offsets the exclusive scan of the counts);
- * and *n_new = sum_i n_i (device int64; parents beyond parents_cap are not
- * written, so the caller compares *n_new with parents_cap).  fl and thr hold
- * n_levels entries (floor(tau_k) and 2^32 frac(tau_k), as pa_step uses them).
+ * and *n_new = sum_i n_i (device int64, exact up to 2^63; parents beyond
+ * parents_cap are not written, so the caller compares *n_new with
+ * parents_cap).  fl and thr hold n_levels entries (floor(tau_k) and
+ * 2^32 frac(tau_k), as pa_step uses them).
  *
- * It allocates nothing: its scratch (the per-block totals of the scan) is a
- * fixed 16 KiB array in the library's device memory, held by every GPU that
- * loads the library until the process exits, which limits n_old to
- * PA_NOALLOC_MAX_SLOTS (larger inputs return PA_ERR_INVALID before any launch).
- * All calls on a device share that array: calls whose work overlaps on the GPU
- * (other streams, other host threads) race and must be serialised by the
- * caller.  The first call on a device looks up the array's device address
- * (once per device, with that device current), so make that first call before
- * any stream capture.  Asynchronous on `cuda_stream` (NULL = legacy default
- * stream); returns PA_OK, PA_ERR_INVALID or PA_ERR_CUDA. */
+ * Invalid device data is reported on the device, not clamped: when a level lies
+ * outside [0, n_levels) or an fl entry outside [0, 2^31 - 2], the slot's count
+ * is written as 0, *n_new is set to -1 and no parent is written.  Nothing is
+ * ever written outside counts[0, n_old) and parents[0, parents_cap).
+ *
+ * It allocates nothing: its scratch (the per-block totals and offsets of the
+ * scan and an error mark) is a fixed array of 4097 64-bit words (about 32 KiB)
+ * in the library's device memory, held by every GPU that loads the library
+ * until the process exits, which limits n_old to PA_NOALLOC_MAX_SLOTS (larger
+ * inputs return PA_ERR_INVALID before any launch).  All calls on a device share
+ * that array: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  The first call on a
+ * device looks up the array's device address (once per device, with that device
+ * current), so make that first call before any stream capture.  The address is
+ * kept for the life of the process: do not call this entry point on a device
+ * after cudaDeviceReset (or any other teardown of its primary context) in the
+ * same process.  Asynchronous on `cuda_stream` (NULL = legacy default stream);
+ * returns PA_OK, PA_ERR_INVALID or PA_ERR_CUDA. */
 #define PA_NOALLOC_MAX_BLOCKS 4096
 #define PA_NOALLOC_MAX_SLOTS (PA_NOALLOC_MAX_BLOCKS * 1024)
 int pa_resample_counts_noalloc(const int32_t* levels, int64_t n_old, const int32_t* fl, const uint32_t* thr,

@@ -126,9 +126,18 @@ int launch_init_couplings(const RunGeom& g, uint64_t disorder_seed, int8_t* J, u
 int launch_init_population(const RunGeom& g, PopDev* pops, int cur, void* stream);
 int launch_levels_and_hist(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, int t, void* stream);
 int launch_reweight(const RunGeom& g, PopDev* pops, const double* w, int t, void* stream);
+// Polls after which a look-back wait of the single-pass resampling gives up.
+constexpr int kLookbackSpins = 1 << 20;
+// Test setting of that wait: the poll limit (0: kLookbackSpins) and a tile whose
+// block publishes nothing (-1: none).
+struct LookbackTest {
+  int32_t spins = 0;
+  int32_t withheld_tile = -1;
+};
 // Single-pass resampling of the +-1 model; launch_reweight of the same step, on the
 // same stream just before, resets the tile ticket it relies on.
-int launch_resample(const RunGeom& g, PopDev* pops, int cur, int t, int32_t* status, void* stream);
+int launch_resample(const RunGeom& g, PopDev* pops, int cur, int t, int32_t* status, const LookbackTest& test,
+                    void* stream);
 int launch_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, int t, int n_sweeps,
                  const uint32_t met_thr[3], void* stream);
 int launch_families(const RunGeom& g, PopDev* pops, int cur, int t, void* stream);

@@ -276,8 +276,10 @@ __global__ void __launch_bounds__(kCountThreads) k_scatter(RunGeom g, PopArgs a,
 // (a total, or a total including everything before it), kCountThreads at a time,
 // until it has its offset, and publishes that inclusive prefix.  Entries carry the step in their upper
 // word (2t + 1: total, 2t + 2: inclusive), so older steps' entries read as not
-// ready.  A wait gives up after kLookbackSpins polls and sets the timeout flag.
-constexpr int kLookbackSpins = 1 << 20;
+// ready.  A wait gives up after spin_limit polls (kLookbackSpins unless a test
+// lowers it) and sets the timeout flag.  A test may also name a tile whose block
+// publishes neither its total nor its prefix (withheld >= 0), so that the waits of
+// the blocks after it run out; -1 in normal runs.
 constexpr int kResampleSlots = 4;  // old slots per thread (4096-slot tiles measured slower)
 constexpr int kResampleTile = kResampleSlots * kCountThreads;  // old slots per tile
 
@@ -285,7 +287,8 @@ __device__ __forceinline__ unsigned long long poll_tile(const unsigned long long
   return *reinterpret_cast<const volatile unsigned long long*>(p);
 }
 
-__global__ void __launch_bounds__(kCountThreads) k_resample(RunGeom g, PopArgs a, int cur, int t, int32_t* status) {
+__global__ void __launch_bounds__(kCountThreads) k_resample(RunGeom g, PopArgs a, int cur, int t, int32_t* status,
+                                                             int spin_limit, int withheld) {
   __shared__ int scratch[33];
   __shared__ int tile_sh;
   __shared__ long long base_sh;
@@ -335,7 +338,8 @@ __global__ void __launch_bounds__(kCountThreads) k_resample(RunGeom g, PopArgs a
   // decision is block-wide (__syncthreads_or, shared words), so all threads leave
   // the loops together.
   const uint32_t ep_total = 2u * (uint32_t)t + 1u, ep_incl = ep_total + 1u;
-  if (threadIdx.x == 0 && tile > 0) atomicExch(&P.tiles[tile], ((unsigned long long)ep_total << 32) | (unsigned)total);
+  if (threadIdx.x == 0 && tile > 0 && tile != withheld)
+    atomicExch(&P.tiles[tile], ((unsigned long long)ep_total << 32) | (unsigned)total);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int kWarps = kCountThreads / 32;
   long long prefix = 0;
@@ -353,7 +357,7 @@ __global__ void __launch_bounds__(kCountThreads) k_resample(RunGeom g, PopArgs a
         if (incl_sh[w]) first = 32 * w + __ffs(incl_sh[w]) - 1;
       const bool waiting = (uint32_t)(v >> 32) < ep_total && (int)threadIdx.x < first;
       if (!__syncthreads_or(waiting)) break;  // also orders the reads of incl_sh before its next write
-      if (spins >= kLookbackSpins) {
+      if (spins >= spin_limit) {
         ok = false;
         break;
       }
@@ -374,7 +378,8 @@ __global__ void __launch_bounds__(kCountThreads) k_resample(RunGeom g, PopArgs a
   if (threadIdx.x == 0) {
     if (!ok) atomicOr(status, kFlagTimeout);
     const long long inc = prefix + total;
-    atomicExch(&P.tiles[tile], ((unsigned long long)ep_incl << 32) | (unsigned)(inc > 0x7fffffffLL ? 0x7fffffffLL : inc));
+    if (tile != withheld)
+      atomicExch(&P.tiles[tile], ((unsigned long long)ep_incl << 32) | (unsigned)(inc > 0x7fffffffLL ? 0x7fffffffLL : inc));
     base_sh = prefix;
     // the tile holding the last old slot (tile 0 for an empty population) records R~
     if (tile == (R_old > 0 ? (R_old - 1) / kResampleTile : 0)) {
@@ -607,12 +612,14 @@ int launch_reweight(const RunGeom& g, PopDev* pops, const double* w, int t, void
   return (int)cudaGetLastError();
 }
 
-int launch_resample(const RunGeom& g, PopDev* pops, int cur, int t, int32_t* status, void* stream) {
+int launch_resample(const RunGeom& g, PopDev* pops, int cur, int t, int32_t* status, const LookbackTest& test,
+                    void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   PopArgs a = pack(pops, g.n_pop);
   // the tile ticket was reset by k_reweight, which runs just before on this stream
   const unsigned tiles = (unsigned)((g.R_cap + kResampleTile - 1) / kResampleTile);  // <= n_count_blocks entries
-  k_resample<<<dim3(tiles, g.n_pop), kCountThreads, 0, s>>>(g, a, cur, t, status);
+  const int spin_limit = test.spins > 0 ? test.spins : kLookbackSpins;
+  k_resample<<<dim3(tiles, g.n_pop), kCountThreads, 0, s>>>(g, a, cur, t, status, spin_limit, test.withheld_tile);
   return (int)cudaGetLastError();
 }
 

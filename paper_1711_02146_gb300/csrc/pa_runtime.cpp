@@ -69,6 +69,7 @@ struct pa_ctx {
   double* gw = nullptr;                  // device [n_temps][16384] weight tables
   unsigned long long* qlhist = nullptr;  // device [n_temps][q_bins] link-overlap histograms
   std::vector<int32_t> Jq_host;
+  pa::LookbackTest lookback;             // pa_debug_lookback (tests of the bounded wait)
 };
 
 namespace {
@@ -657,6 +658,114 @@ void use_chosen_shape(pa_ctx* c) {
 }
 }  // namespace pa
 
+namespace {
+
+template <typename T>
+T read_at(const char* p, size_t i) {
+  T v;
+  std::memcpy(&v, p + i * sizeof(T), sizeof(T));
+  return v;
+}
+
+// Checks the population part of a checkpoint on the host, before any of it
+// reaches the device: every value a kernel later uses as an index or a size must
+// be in range and consistent.  Step records chain (each step's previous size is
+// the last step's size, sizes within the capacity, the lowest level in range),
+// level histograms add up to their population, spins are +-1, labels ascend and
+// stay below R, levels lie in range and match the last histogram, copy numbers
+// are non-negative and add up to the population, parents ascend within the old
+// population, family-size counts are non-negative and cover the population.  `in` points just past the
+// schedule; the size of the whole buffer has been checked already.
+bool ckpt_payload_ok(const RunGeom& g, bool gauss, int t, int64_t R, const CkptHeader& h, const char* in) {
+  const int64_t max_abs_E = 3 * (int64_t)g.N * 5 * ((int64_t)1 << 20);  // Gaussian couplings are clamped to 5
+  for (int p = 0; p < g.n_pop; ++p) {
+    const int64_t Rt = h.R_tilde[p], Rp = h.R_prev[p];
+    std::vector<StepRec> rec((size_t)t + 1);
+    std::memcpy(rec.data(), in, sizeof(StepRec) * rec.size());
+    in += sizeof(StepRec) * rec.size();
+    for (int u = 0; u <= t; ++u) {
+      const StepRec& r = rec[(size_t)u];
+      if (r.R_tilde < 1 || r.R_tilde > g.R_cap) return false;
+      if (u > 0 && (r.R_prev != rec[(size_t)u - 1].R_tilde || r.S_t < 0 || r.culled < 0 || r.culled > r.R_prev))
+        return false;
+      if (u > 0 && !gauss && (r.kmin_prev < 0 || r.kmin_prev >= g.n_levels)) return false;
+    }
+    if (rec[0].R_tilde != R || rec[(size_t)t].R_tilde != Rt || (t > 0 ? rec[(size_t)t].R_prev : 0) != Rp)
+      return false;
+    long long E_min = 0;
+    std::vector<int64_t> last_hist;
+    if (gauss) {
+      E_min = read_at<pa::GRec>(in, (size_t)t).E_min;
+      in += sizeof(pa::GRec) * ((size_t)t + 1);
+    } else {
+      for (int u = 0; u <= t; ++u) {
+        int64_t sum = 0;
+        for (int k = 0; k < g.n_levels; ++k) sum += read_at<uint32_t>(in, (size_t)u * g.n_levels + k);
+        if (sum != rec[(size_t)u].R_tilde) return false;
+      }
+      last_hist.resize((size_t)g.n_levels);
+      for (int k = 0; k < g.n_levels; ++k)
+        last_hist[(size_t)k] = read_at<uint32_t>(in, (size_t)t * g.n_levels + k);
+      in += sizeof(uint32_t) * ((size_t)t + 1) * (size_t)g.n_levels;
+    }
+    const size_t n_spins = (size_t)g.N * (size_t)Rt;
+    for (size_t i = 0; i < n_spins; ++i) {
+      const uint8_t b = (uint8_t)in[i];
+      if (b != 0x01 && b != 0xFF) return false;
+    }
+    in += n_spins;
+    for (int64_t j = 0; j < Rt; ++j) {
+      const int32_t l = read_at<int32_t>(in, (size_t)j);
+      if (l < 0 || l >= R || (j > 0 && l < read_at<int32_t>(in, (size_t)j - 1))) return false;
+    }
+    in += sizeof(int32_t) * (size_t)Rt;
+    if (gauss) {
+      long long lo = 0;
+      for (int64_t j = 0; j < Rt; ++j) {
+        const long long e = read_at<int64_t>(in, (size_t)j);
+        if (e < -max_abs_E || e > max_abs_E) return false;
+        lo = j == 0 ? e : std::min(lo, e);
+      }
+      if (lo != E_min) return false;
+      in += sizeof(int64_t) * (size_t)Rt;
+    } else {
+      for (int64_t j = 0; j < Rt; ++j) {
+        const int32_t k = read_at<int32_t>(in, (size_t)j);
+        if (k < 0 || k >= g.n_levels) return false;
+        --last_hist[(size_t)k];
+      }
+      for (int64_t c : last_hist)
+        if (c != 0) return false;
+      in += sizeof(int32_t) * (size_t)Rt;
+    }
+    int64_t copies = 0;
+    for (int64_t i = 0; i < Rp; ++i) {
+      const int32_t n = read_at<int32_t>(in, (size_t)i);
+      if (n < 0) return false;
+      copies += n;
+    }
+    if (t > 0 && copies != Rt) return false;
+    in += sizeof(int32_t) * (size_t)Rp;
+    for (int64_t j = 0; j < Rt; ++j) {
+      const int32_t q = read_at<int32_t>(in, (size_t)j);
+      if (q < 0 || q >= g.R_cap) return false;
+      if (t > 0 && (q >= Rp || (j > 0 && q < read_at<int32_t>(in, (size_t)j - 1)))) return false;
+    }
+    in += sizeof(int32_t) * (size_t)Rt;
+    int64_t members = 0;
+    for (int64_t e = 0; e <= Rt; ++e) {
+      const int32_t m = read_at<int32_t>(in, (size_t)e);
+      if (m < 0) return false;
+      members += e * (int64_t)m;
+    }
+    if (members != Rt) return false;
+    in += sizeof(int32_t) * ((size_t)Rt + 1);
+  }
+  return true;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* pa_strerror(int s) {
@@ -748,6 +857,8 @@ int pa::create_run(const pa_config* cfg, void* cuda_stream, pa_ctx** out, bool s
     if (rc == PA_OK) rc = cuda_status(cudaMemsetAsync(c->pops[p].famdone, 0, sizeof(int32_t), s));
     if (rc == PA_OK)  // no stale tile state may carry a step's epoch
       rc = cuda_status(cudaMemsetAsync(c->pops[p].tiles, 0, sizeof(unsigned long long) * (size_t)g.n_count_blocks, s));
+    if (rc == PA_OK)  // every parent entry is a valid slot at all times, even where a failed step leaves gaps
+      rc = cuda_status(cudaMemsetAsync(c->pops[p].parents, 0, sizeof(int32_t) * (size_t)g.pitch, s));
   }
   // Host tables go up in one copy per kind; the +-1 tables' host buffer lives in
   // the run, the Gaussian ones until the stream synchronisation at the end of
@@ -861,7 +972,7 @@ int pa_step(pa_ctx* c) {
     }
     if (rc == PA_OK) {
       PhaseTimer pt(c, PA_PHASE_RESAMPLE, 1);
-      rc = launch_rc(pa::launch_resample(c->g, c->pops, c->cur, t, c->status, s));
+      rc = launch_rc(pa::launch_resample(c->g, c->pops, c->cur, t, c->status, c->lookback, s));
     }
     if (rc == PA_OK && pa::sweep_supported(c->g.L)) {
       PhaseTimer pt(c, PA_PHASE_SWEEP, 1);
@@ -879,6 +990,13 @@ int pa_step(pa_ctx* c) {
   c->stats.steps += 1;
   c->counted_steps.emplace_back(t, c->sweeps[(size_t)t]);
   if (t == c->cfg.n_temps - 1 || (c->adaptive && c->betas[(size_t)t] >= c->cfg.beta_max)) c->done = true;
+  return PA_OK;
+}
+
+int pa_debug_lookback(pa_ctx* c, int32_t spins, int32_t withheld_tile) {
+  if (!c || spins < 0 || withheld_tile < -1) return PA_ERR_INVALID;
+  c->lookback.spins = spins;
+  c->lookback.withheld_tile = withheld_tile;
   return PA_OK;
 }
 
@@ -1385,6 +1503,10 @@ int pa_restore(const pa_config* cfg, const void* buf, size_t size, void* cuda_st
   if (rc != PA_OK) {
     pa_destroy(c);
     return rc;
+  }
+  if (!ckpt_payload_ok(g, gauss, t, h.R, h, in)) {
+    pa_destroy(c);
+    return PA_ERR_INVALID;
   }
   for (int u = 0; u <= t; ++u) c->betas[(size_t)u] = betas[u];
   c->cur = 0;

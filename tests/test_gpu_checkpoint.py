@@ -108,6 +108,79 @@ def test_refuses_other_configurations_and_damaged_buffers(pa):
     assert n.value == len(blob)
 
 
+def _sections(blob, run, t, n_temps, n_levels, gauss=False):
+    """Byte offsets of population 0's sections in a checkpoint taken at step t (the
+    layout pa_checkpoint writes: header, schedule, then per population the step
+    records, level histograms or Gaussian records, spins, labels, levels or
+    energies, copy numbers, parents, family-size histogram)."""
+    header = int(np.frombuffer(blob[12:16], np.uint32)[0])
+    Rt, Rp = len(run.population(0)[1]), len(run.copy_counts(0))
+    off, out = header + 12 * n_temps, {}
+    sizes = [("rec", 80 * (t + 1)), ("hist", (64 if gauss else 4 * n_levels) * (t + 1)), ("spins", run.N * Rt),
+             ("labels", 4 * Rt), ("levels", (8 if gauss else 4) * Rt), ("counts", 4 * Rp), ("parents", 4 * Rt),
+             ("mhist", 4 * (Rt + 1))]
+    for name, size in sizes:
+        out[name] = (off, size)
+        off += size
+    return out, Rt, Rp
+
+
+def _put(blob, at, dtype, value):
+    b = bytearray(blob)
+    b[at:at + np.dtype(dtype).itemsize] = np.array([value], dtype=dtype).tobytes()
+    return bytes(b)
+
+
+def test_refuses_damaged_contents(pa):
+    """A buffer of the right size whose contents were damaged is refused before any of
+    it reaches the device: every value a kernel uses as an index or a size is checked
+    on the host (records, histograms, spins, labels, levels, copy numbers, parents,
+    family sizes)."""
+    from paper_1711_02146_gb300.workloads import default_capacity
+    t = 3
+    run = make(pa, EXPLICIT)
+    for _ in range(t):
+        run.step()
+    blob = run.checkpoint()
+    n_levels = 3 * run.N + 1
+    sec, Rt, Rp = _sections(blob, run, t, len(EXPLICIT["betas"]), n_levels)
+    rec, hist, spins = sec["rec"][0], sec["hist"][0], sec["spins"][0]
+    lab, lev, cnt, par, mh = (sec[k][0] for k in ("labels", "levels", "counts", "parents", "mhist"))
+    levels0 = np.frombuffer(blob[lev:lev + 4 * Rt], np.int32)
+    other = int(levels0[0] + 1 if levels0[0] + 1 < n_levels else levels0[0] - 1)
+    damaged = {
+        "R_tilde of the last record": _put(blob, rec + 80 * t, np.int32, default_capacity(EXPLICIT["R"]) + 5),
+        "R_prev of a record": _put(blob, rec + 80 * 2 + 4, np.int32, 3),
+        "lowest level of a record": _put(blob, rec + 80 * 1 + 8, np.int32, n_levels),
+        "a histogram bin": _put(blob, hist + 4 * (t * n_levels + 7), np.uint32, 99),
+        "a spin byte": _put(blob, spins + 1234, np.int8, 0),
+        "a label above R": _put(blob, lab + 4 * (Rt - 1), np.int32, EXPLICIT["R"]),
+        "a descending label": _put(blob, lab, np.int32, EXPLICIT["R"] - 1),
+        "a level beyond the table": _put(blob, lev + 4 * 5, np.int32, n_levels),
+        "a level not in the histogram": _put(blob, lev, np.int32, other),
+        "a negative copy number": _put(blob, cnt + 4 * 9, np.int32, -1),
+        "a parent beyond the old population": _put(blob, par + 4 * (Rt - 1), np.int32, Rp),
+        "a family-size count": _put(blob, mh + 4 * 1, np.int32, -4),
+    }
+    for what, bad in damaged.items():
+        assert len(bad) == len(blob) and bad != blob, what
+        with pytest.raises(pa.PAError) as e:
+            make(pa, EXPLICIT, checkpoint=bad)
+        assert e.value.status == pa.PA_ERR_INVALID, what
+    restored = make(pa, EXPLICIT, checkpoint=blob)
+    assert_same(trace(restored), trace(run))
+    gr = make(pa, GAUSS, model=pa.PA_MODEL_GAUSS)
+    for _ in range(2):
+        gr.step()
+    gblob = gr.checkpoint()
+    gsec, gRt, _ = _sections(gblob, gr, 2, len(GAUSS["betas"]), 0, gauss=True)
+    for what, bad in {"an energy below the lowest": _put(gblob, gsec["levels"][0], np.int64, -(2 ** 40)),
+                      "a label above R": _put(gblob, gsec["labels"][0] + 4 * (gRt - 1), np.int32, GAUSS["R"])}.items():
+        with pytest.raises(pa.PAError) as e:
+            make(pa, GAUSS, model=pa.PA_MODEL_GAUSS, checkpoint=bad)
+        assert e.value.status == pa.PA_ERR_INVALID, what
+
+
 GAUSS = dict(L=6, R=800, disorder_seed=3, run_seed=8, betas=np.linspace(0.0, 2.5, 7), n_sweeps=2, n_pop=2)
 GAUSS_ADAPTIVE = dict(L=4, R=600, disorder_seed=5, run_seed=6, betas=None, n_temps=300, beta_max=2.0,
                       eps_target=0.3, n_sweeps=2)
