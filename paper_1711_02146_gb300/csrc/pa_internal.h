@@ -23,7 +23,8 @@ struct StepRec {
   double eps_expected;  // (1/R) sum_k c(k) (1 - tau_k)_+
   unsigned long long sum_eta2;
   unsigned long long n_families;
-  double nu_ln_nu;      // sum over families of nu ln nu, nu = eta / R~
+  long long nll_hi;             // sum over families of nu ln nu (nu = eta / R~) as a 128-bit
+  unsigned long long nll_lo;    // fixed-point number in units of 2^-100 (hi * 2^64 + lo), exact
   unsigned long long q_pairs;   // population 0 only
   unsigned long long q_small;   // population 0 only: pairs with 5|Q| <= N
   int32_t S_t;          // sweeps done at this step
@@ -56,9 +57,10 @@ struct PopDev {
   uint32_t* hist;       // [n_temps][n_levels] energy-level histograms
   int32_t* fl;          // [n_levels] floor(tau_k)
   uint32_t* thr;        // [n_levels] 2^32 frac(tau_k)
-  int32_t* famdone;     // [1] blocks of the family-entropy kernel that have finished (0 between steps)
-  int32_t* mhist;       // [R_cap + 1] number of families of each size
-  double* partials;     // [n_entropy_blocks] fixed-order partial sums of nu ln nu
+  int32_t* mhist;       // [R_cap + 1] number of families of each size (filled on request)
+  int32_t* fhist;       // [R_cap + 1] the running step's family sizes (zero between steps)
+  int32_t* fsizes;      // [n_fsizes] the distinct sizes counted in fhist this step
+  int32_t* fcount;      // [2] listed sizes, blocks done with this step's families (zero between steps)
   StepRec* rec;         // [n_temps]
   // Gaussian-coupling model only (null otherwise)
   long long* E64;       // [pitch] energies of the current population, units of 2^-20
@@ -82,7 +84,7 @@ struct RunGeom {
   int32_t n_pop;
   int32_t q_bins;
   int32_t n_count_blocks;    // resampling blocks (1024 slots each)
-  int32_t n_entropy_blocks;  // family-entropy reduction blocks
+  int32_t n_fsizes;          // bound on the distinct family sizes of a population: floor(sqrt(2 R_cap)) + 2
   int32_t sweep_shape;       // index of the sweep kernel's launch shape among those of L
   int32_t model;             // 0: +-1 couplings, 1: Gaussian couplings (fixed point)
   int32_t n_chunks;          // Gaussian: chunks of 256 slots of the weight sums
@@ -118,8 +120,6 @@ bool sweep_shape_info(int L, int i, SweepShapeInfo* out);
 
 constexpr int kCountThreads = 256;     // threads per resampling block
 constexpr int kSlotsPerCountBlock = 1024;
-constexpr int kEntropyThreads = 256;
-constexpr int kEntropyPerBlock = 4096;
 
 // ---- launchers (pa_kernels.cu / pa_sweep.cu); each returns a cudaError_t as int ----
 int launch_init_couplings(const RunGeom& g, uint64_t disorder_seed, int8_t* J, uint32_t* jtab, void* stream);
@@ -140,7 +140,12 @@ int launch_resample(const RunGeom& g, PopDev* pops, int cur, int t, int32_t* sta
                     void* stream);
 int launch_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, int t, int n_sweeps,
                  const uint32_t met_thr[3], void* stream);
+// Family statistics of step t (sum of eta^2, families, sum of nu ln nu) into the step
+// records; the +-1 shared-memory sweep does the same in its epilogue.
 int launch_families(const RunGeom& g, PopDev* pops, int cur, int t, void* stream);
+// The family-size histogram m(eta) of population pop at step t into its mhist
+// (on request: the step records are not touched).
+int launch_family_hist(const RunGeom& g, PopDev* pops, int pop, int cur, int t, void* stream);
 // Gaussian-coupling model (pa_gauss.cu, and k_sweep_g in pa_sweep.cu)
 int launch_scan_scatter(const RunGeom& g, PopDev* pops, int cur, int t, int32_t* status, void* stream);
 int launch_g_energy_init(const RunGeom& g, PopDev* pops, int cur, const int32_t* Jq, void* stream);

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "pa_device.cuh"
+#include "pa_family.cuh"
 #include "pa_internal.h"
 
 namespace pa {
@@ -432,13 +433,13 @@ __global__ void __launch_bounds__(kCountThreads) k_resample(RunGeom g, PopArgs a
 
 // Families from the sorted labels: a family is a run of equal labels along the
 // slots (labels start as slot numbers and every copy keeps their order), so the
-// thread at a run's first slot finds its end by binary search and knows the
-// family size eta.  Sum of eta^2, alive families, and the family-size histogram
-// m(eta); lanes of a warp with the same size add to m(eta) with one atomic (most
-// families share a few small sizes, so per-thread atomics would pile onto one
-// address).
-__global__ void k_fam_runs(RunGeom g, PopArgs a, int cur, int t) {
-  __shared__ unsigned long long red[2][32];
+// thread at a run's first slot finds its end (galloping through the labels) and
+// knows the family size eta.  Without write_hist: the step's family statistics
+// (pa_family.cuh; the last block adds the entropy).  With write_hist: only the
+// size histogram m(eta) for the host (lanes of a warp with the same size add with
+// one atomic: most families share a few small sizes).
+__global__ void __launch_bounds__(256) k_fam_runs(RunGeom g, PopArgs a, int cur, int t, int write_hist) {
+  __shared__ long long sh[64];
   const PopDev& P = a.p[blockIdx.y];
   const int R_new = P.rec[t].R_tilde;
   const int32_t* lab = P.labels[cur];
@@ -446,81 +447,18 @@ __global__ void k_fam_runs(RunGeom g, PopArgs a, int cur, int t) {
   int eta = 0;
   if (j < R_new) {
     const int32_t l = lab[j];
-    if (j == 0 || lab[j - 1] != l) {
-      int lo = j + 1, hi = R_new;  // first slot past the run: lab[k] > l for k >= hi
-      while (lo < hi) {
-        const int mid = lo + ((hi - lo) >> 1);
-        if (lab[mid] == l)
-          lo = mid + 1;
-        else
-          hi = mid;
-      }
-      eta = lo - j;
-    }
+    if (j == 0 || lab[j - 1] != l) eta = run_end(lab, l, j + 1, R_new) - j;
   }
-  unsigned long long s2 = (unsigned long long)eta * (unsigned long long)eta, nf = eta > 0 ? 1ull : 0ull;
-  const unsigned peers = __match_any_sync(0xffffffffu, eta);
-  if (eta > 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&P.mhist[eta], __popc(peers));
-  s2 = warp_sum(s2);
-  nf = warp_sum(nf);
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  if (lane == 0) {
-    red[0][wp] = s2;
-    red[1][wp] = nf;
+  if (write_hist) {
+    const unsigned peers = __match_any_sync(0xffffffffu, eta);
+    if (eta > 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&P.mhist[eta], __popc(peers));
+    return;
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long a2 = 0, an = 0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-      a2 += red[0][i];
-      an += red[1][i];
-    }
-    if (a2) atomicAdd(&P.rec[t].sum_eta2, a2);
-    if (an) atomicAdd(&P.rec[t].n_families, an);
-  }
-}
-
-// Fixed-order partial sums of m(eta) nu ln nu, nu = eta / R~ (the family
-// entropy is S_f = -sum): each block covers kEntropyPerBlock sizes, each thread
-// a contiguous run of them, then a fixed tree.  The last block to finish adds the
-// partials in block order (a ticket counts finished blocks; no block waits).
-__global__ void __launch_bounds__(kEntropyThreads) k_fam_entropy(RunGeom g, PopArgs a, int t) {
-  __shared__ double red[kEntropyThreads];
-  __shared__ bool last;
-  const PopDev& P = a.p[blockIdx.y];
-  const int R_new = P.rec[t].R_tilde;
-  constexpr int per = kEntropyPerBlock / kEntropyThreads;
-  const int e0 = 1 + blockIdx.x * kEntropyPerBlock + threadIdx.x * per;
-  double s = 0.0;
-  for (int i = 0; i < per; ++i) {
-    const int eta = e0 + i;
-    if (eta <= R_new) {
-      const int m = P.mhist[eta];
-      if (m > 0) {
-        const double nu = __ddiv_rn((double)eta, (double)R_new);
-        s = __dadd_rn(s, __dmul_rn((double)m, __dmul_rn(nu, log(nu))));
-      }
-    }
-  }
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int h = kEntropyThreads / 2; h > 0; h >>= 1) {
-    if (threadIdx.x < h) red[threadIdx.x] = __dadd_rn(red[threadIdx.x], red[threadIdx.x + h]);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    P.partials[blockIdx.x] = red[0];
-    __threadfence();
-    last = atomicAdd(P.famdone, 1) == (int)gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!last || threadIdx.x != 0) return;
-  __threadfence();
-  const volatile double* part = P.partials;
-  double tot = 0.0;
-  for (int b = 0; b < (int)gridDim.x; ++b) tot = __dadd_rn(tot, part[b]);
-  P.rec[t].nu_ln_nu = tot;
-  *P.famdone = 0;  // ready for the next step
+  FamilyAcc f;
+  if (eta > 0) f.add(eta);
+  family_size(P, eta, 0xffffffffu);
+  family_flush(f, 0xffffffffu, &P.rec[t]);
+  family_entropy_last(P, &P.rec[t], R_new, (int)gridDim.x, (int)threadIdx.x, (int)blockDim.x, sh);
 }
 
 // ---------------------------------------------------------------- overlap (a8)
@@ -634,9 +572,15 @@ int launch_scan_scatter(const RunGeom& g, PopDev* pops, int cur, int t, int32_t*
 int launch_families(const RunGeom& g, PopDev* pops, int cur, int t, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   PopArgs a = pack(pops, g.n_pop);
-  for (int p = 0; p < g.n_pop; ++p) cudaMemsetAsync(pops[p].mhist, 0, sizeof(int32_t) * ((size_t)g.R_cap + 1), s);
-  k_fam_runs<<<dim3(grid_for(g.R_cap, 256), g.n_pop), 256, 0, s>>>(g, a, cur, t);
-  k_fam_entropy<<<dim3(g.n_entropy_blocks, g.n_pop), kEntropyThreads, 0, s>>>(g, a, t);
+  k_fam_runs<<<dim3(grid_for(g.R_cap, 256), g.n_pop), 256, 0, s>>>(g, a, cur, t, 0);
+  return (int)cudaGetLastError();
+}
+
+int launch_family_hist(const RunGeom& g, PopDev* pops, int pop, int cur, int t, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  PopArgs a = pack(pops + pop, 1);
+  cudaMemsetAsync(pops[pop].mhist, 0, sizeof(int32_t) * ((size_t)g.R_cap + 1), s);
+  k_fam_runs<<<dim3(grid_for(g.R_cap, 256), 1), 256, 0, s>>>(g, a, cur, t, 1);
   return (int)cudaGetLastError();
 }
 

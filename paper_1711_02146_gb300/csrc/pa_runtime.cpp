@@ -76,6 +76,13 @@ namespace {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? PA_OK : PA_ERR_CUDA; }
 
+// The step's sum over families of nu ln nu from its exact 128-bit fixed-point form
+// (units of 2^-100), rounded to double once.
+double nu_ln_nu(const StepRec& r) {
+  const unsigned __int128 u = ((unsigned __int128)(uint64_t)r.nll_hi << 64) | (unsigned __int128)r.nll_lo;
+  return (double)(__int128)u * 0x1p-100;
+}
+
 // Sweep launch shape selected per device and lattice size (an index among the
 // shapes compiled for L; static storage starts at 0, the default shape).
 constexpr int kMaxDevices = 64;
@@ -477,8 +484,10 @@ int measure(pa_ctx* c, int t) {
     PhaseTimer pt(c, PA_PHASE_FAMILY, 3);
     rc = launch_rc(pa::launch_g_measure(c->g, c->pops, c->cur, t, c->qlhist, c->stream));
   }
-  if (rc == PA_OK) {
-    PhaseTimer pt(c, PA_PHASE_FAMILY, 2);
+  // the +-1 shared-memory sweep adds the family statistics of steps t >= 1 itself
+  const bool in_sweep = c->model == PA_MODEL_PM1 && t > 0 && pa::sweep_supported(c->g.L);
+  if (rc == PA_OK && !in_sweep) {
+    PhaseTimer pt(c, PA_PHASE_FAMILY, 1);
     rc = launch_rc(pa::launch_families(c->g, c->pops, c->cur, t, c->stream));
   }
   if (rc == PA_OK && c->g.n_pop == 2) {
@@ -525,7 +534,7 @@ struct CkptHeader {
   uint64_t total_bytes;
 };
 constexpr char kCkptMagic[8] = {'P', 'A', 'C', 'K', 'P', 'T', '0', '1'};
-constexpr uint32_t kCkptVersion = 2;
+constexpr uint32_t kCkptVersion = 3;
 
 size_t ckpt_bytes(const RunGeom& g, int model, int t, int n_temps, const int32_t* Rt, const int32_t* Rp) {
   size_t b = sizeof(CkptHeader) + (size_t)n_temps * (sizeof(double) + sizeof(int32_t));
@@ -582,7 +591,11 @@ void init_run(pa_ctx* c, const pa_config* cfg, int64_t R_cap) {
   g.n_pop = cfg->n_pop;
   g.q_bins = cfg->q_bins;
   g.n_count_blocks = (int32_t)((R_cap + pa::kSlotsPerCountBlock - 1) / pa::kSlotsPerCountBlock);
-  g.n_entropy_blocks = (int32_t)((R_cap + pa::kEntropyPerBlock - 1) / pa::kEntropyPerBlock);
+  // K distinct family sizes add up to at least K (K + 1) / 2 <= R~, so K <= floor(sqrt(2 R_cap))
+  int64_t k = (int64_t)std::sqrt(2.0 * (double)R_cap);
+  while ((k + 1) * (k + 1) <= 2 * R_cap) ++k;
+  while (k * k > 2 * R_cap) --k;
+  g.n_fsizes = (int32_t)k + 2;
   g.sweep_shape = 0;
   g.model = cfg->model;
   g.n_chunks = (int32_t)((R_cap + pa::kChunk - 1) / pa::kChunk);
@@ -615,9 +628,10 @@ int layout_buffers(pa_ctx* c) {
     rc = rc ? rc : dalloc(c, &P.hist, T * (size_t)g.n_levels);
     rc = rc ? rc : dalloc(c, &P.fl, (size_t)g.n_levels);
     rc = rc ? rc : dalloc(c, &P.thr, (size_t)g.n_levels);
-    rc = rc ? rc : dalloc(c, &P.famdone, (size_t)1);
     rc = rc ? rc : dalloc(c, &P.mhist, (size_t)g.R_cap + 1);
-    rc = rc ? rc : dalloc(c, &P.partials, (size_t)g.n_entropy_blocks);
+    rc = rc ? rc : dalloc(c, &P.fhist, (size_t)g.R_cap + 1);
+    rc = rc ? rc : dalloc(c, &P.fsizes, (size_t)g.n_fsizes);
+    rc = rc ? rc : dalloc(c, &P.fcount, (size_t)2);
     rc = rc ? rc : dalloc(c, &P.rec, T);
     if (g.model == PA_MODEL_GAUSS) {
       rc = rc ? rc : dalloc(c, &P.E64, (size_t)g.pitch);
@@ -854,9 +868,11 @@ int pa::create_run(const pa_config* cfg, void* cuda_stream, pa_ctx** out, bool s
   for (int p = 0; p < g.n_pop && rc == PA_OK; ++p) {
     rc = cuda_status(cudaMemsetAsync(c->pops[p].hist, 0, sizeof(uint32_t) * T * (size_t)g.n_levels, s));
     if (rc == PA_OK) rc = cuda_status(cudaMemsetAsync(c->pops[p].rec, 0, sizeof(StepRec) * T, s));
-    if (rc == PA_OK) rc = cuda_status(cudaMemsetAsync(c->pops[p].famdone, 0, sizeof(int32_t), s));
     if (rc == PA_OK)  // no stale tile state may carry a step's epoch
       rc = cuda_status(cudaMemsetAsync(c->pops[p].tiles, 0, sizeof(unsigned long long) * (size_t)g.n_count_blocks, s));
+    if (rc == PA_OK)
+      rc = cuda_status(cudaMemsetAsync(c->pops[p].fhist, 0, sizeof(int32_t) * ((size_t)g.R_cap + 1), s));
+    if (rc == PA_OK) rc = cuda_status(cudaMemsetAsync(c->pops[p].fcount, 0, sizeof(int32_t) * 2, s));
     if (rc == PA_OK)  // every parent entry is a valid slot at all times, even where a failed step leaves gaps
       rc = cuda_status(cudaMemsetAsync(c->pops[p].parents, 0, sizeof(int32_t) * (size_t)g.pitch, s));
   }
@@ -1123,7 +1139,7 @@ int pa_observables(pa_ctx* c, int32_t t, int32_t pop, pa_obs* out) {
   o.sum_eta2 = (int64_t)r.sum_eta2;
   o.n_families = (int64_t)r.n_families;
   o.rho_t = (double)o.sum_eta2 / (double)o.R_tilde;
-  o.S_f = -r.nu_ln_nu;
+  o.S_f = -nu_ln_nu(r);
   o.rho_s = (double)o.R_tilde / std::exp(o.S_f);
   o.E0 = E0;
   o.g0_tilde = (double)h[(E0 + 3 * N) / 2] / (double)o.R_tilde;
@@ -1172,6 +1188,7 @@ int pa_family_hist(pa_ctx* c, int32_t pop, int64_t cap, int64_t* eta, int64_t* m
   if (rc != PA_OK) return rc;
   int32_t R = 0;
   rc = copy_d2h(c, &R, &c->pops[pop].rec[c->t].R_tilde, sizeof R);
+  if (rc == PA_OK) rc = launch_rc(pa::launch_family_hist(c->g, c->pops, pop, c->cur, c->t, c->stream));
   std::vector<int32_t> mh((size_t)R + 1);
   if (rc == PA_OK)
     rc = copy_d2h(c, mh.data(), c->pops[pop].mhist, sizeof(int32_t) * mh.size());
@@ -1318,7 +1335,7 @@ int pa_gobservables(pa_ctx* c, int32_t t, int32_t pop, pa_gobs* out) {
   o.sum_eta2 = (int64_t)r.sum_eta2;
   o.n_families = (int64_t)r.n_families;
   o.rho_t = (double)o.sum_eta2 / (double)o.R_tilde;
-  o.S_f = -r.nu_ln_nu;
+  o.S_f = -nu_ln_nu(r);
   o.rho_s = (double)o.R_tilde / std::exp(o.S_f);
   o.E0 = q.E0;
   o.g0_tilde = (double)q.n_at_E0 / (double)o.R_tilde;
@@ -1450,6 +1467,7 @@ int pa_checkpoint(pa_ctx* c, void* buf, size_t cap, size_t* size) {
       get(P.levels, sizeof(int32_t) * R);
     get(P.counts, sizeof(int32_t) * (size_t)Rp[p]);
     get(P.parents, sizeof(int32_t) * R);
+    if (rc == PA_OK) rc = launch_rc(pa::launch_family_hist(g, c->pops, p, c->cur, t, c->stream));
     get(P.mhist, sizeof(int32_t) * (R + 1));
   }
   const size_t qbytes = sizeof(unsigned long long) * (size_t)(t + 1) * (size_t)g.q_bins;

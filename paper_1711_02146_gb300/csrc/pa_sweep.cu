@@ -8,7 +8,9 @@
 //      c = (x + y + z) & 1, colour 0 then colour 1; the neighbours of a site all
 //      have the other colour, so all sites of one colour update independently),
 //   3. counts each replica's energy and adds the tile to the histogram of step t,
-//   4. writes the tile to the new population buffer (int8 +1 / -1).
+//   4. writes the tile to the new population buffer (int8 +1 / -1),
+//   5. (+-1 couplings) adds the families of its slots to the step's family
+//      statistics (§III.A), so the step needs no family launch of its own.
 // HBM traffic is one read and one write of the tile per step, whatever S is.
 //
 // +-1 couplings (k_sweep): bit-sliced tiles.  Word w of a site row holds slots
@@ -37,6 +39,7 @@
 #include <cuda_runtime.h>
 
 #include "pa_device.cuh"
+#include "pa_family.cuh"
 #include "pa_internal.h"
 
 namespace pa {
@@ -277,7 +280,15 @@ __device__ __forceinline__ void store_tile(const SweepArgs& a, const uint32_t* s
 // Bits needed to hold 0..n.
 constexpr int bits_for(int n) { return n < 2 ? 1 : 1 + bits_for(n / 2); }
 
-template <int L, int W, int NT>
+// A word whose replicas the first two Philox blocks (bit planes 0..7) leave
+// undecided: its site n and word (n | word << 16), the undecided replicas, and
+// their classes u = 0 and u = 1 (u = 2 is the rest of them).
+struct __align__(16) Deferred {
+  uint32_t loc, eq, m0, m1;
+};
+constexpr int kQueueCap = 64;  // a warp queues at most 31 + 32 words before it finishes 32 of them
+
+template <int L, int W, int NT, int MB>
 struct BitShape {
   static constexpr int N = L * L * L;
   static constexpr int ROWS = L * L;
@@ -285,7 +296,16 @@ struct BitShape {
   static constexpr int TJ = 32 * W;       // replicas per tile
   static constexpr int SLOTS = 33 * W;    // parents (padded by one per word), then level counts
   static constexpr int CB = bits_for(3 * L * (ROWS / NP));  // bit planes of a thread's level counter
-  static constexpr size_t SMEM = (size_t)N * W * 4 + (size_t)N * sizeof(SiteRec) + (size_t)SLOTS * 4;
+  static constexpr size_t SMEM_TILE = (size_t)N * W * 4 + (size_t)N * sizeof(SiteRec) + (size_t)SLOTS * 4;
+  static constexpr size_t SMEM_QUEUES = (size_t)(NT / 32) * kQueueCap * sizeof(Deferred);
+  // Deferred comparisons need whole warps that each stay inside one parity class
+  // (every lane of a warp then runs the same half-sweep code in step), and room
+  // for the queues without fewer than MB CTAs per SM (228 KB per SM, 1 KB of it
+  // reserved per CTA).
+  static constexpr bool DEFER = NT % 32 == 0 && ((NP / 2) * W) % 32 == 0 &&
+                                (size_t)MB * (SMEM_TILE + SMEM_QUEUES + 1024) <= 233472;
+  static constexpr int NQ = DEFER ? NT / 32 : 0;  // one queue per warp
+  static constexpr size_t SMEM = SMEM_TILE + (DEFER ? SMEM_QUEUES : 0);
   static_assert(NT % W == 0 && 32 % W == 0 && NT <= 1024, "threads must tile the words of a row");
   static_assert(L % 2 == 0 && L / 2 <= 8, "even L up to 16");
   static_assert(NP % 2 == 0 && (ROWS / 2) % (NP / 2) == 0, "row partitions must split each parity class");
@@ -413,6 +433,117 @@ __device__ __forceinline__ void sweep_rows_bits(uint32_t* spw, const SiteRec* re
   }
 }
 
+// Finishes a deferred word: Philox blocks 2, 3, ... of its site and group until
+// every queued replica is decided, then flips the accepted ones (the word's owner
+// has already applied the flips decided in planes 0..7).  Any lane of the owner's
+// warp may run it: the same-colour sites of a half-sweep are independent.
+template <int W>
+__device__ __forceinline__ void finish_deferred(uint32_t* sp, const SiteRec* recs, const Deferred d, uint32_t q,
+                                                uint32_t gbase, const SweepArgs& a) {
+  const int n = (int)(d.loc & 0xffffu), word = (int)(d.loc >> 16);
+  const uint32_t m0 = d.m0, m1 = d.m1, m2 = ~(m0 | m1);
+  uint32_t eq = d.eq, acc = 0;
+  const uint32_t g8 = 8u * (gbase + (uint32_t)word);
+  const uint32_t uc = kM0 * ((uint32_t)n >> 1);
+  const SiteRec sr = recs[n];
+#pragma unroll 1
+  for (int b = 2; b < 8 && eq; ++b) {
+    const ThreadPhilox tb = thread_philox(g8 + (uint32_t)b, q, a.k0, a.k1);
+    uint32_t w[4];
+    philox_block(uc, sr, tb, a.k0, a.k1, w);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t* tmp = a.tm[4 * b + i];
+      compare_plane(w[i], m0, m1, m2, tmp[0], tmp[1], tmp[2], eq, acc);
+    }
+  }
+  sp[n * W + word] ^= acc;
+}
+
+// One half-sweep of the rows of partition `part`, as sweep_rows_bits, for shapes
+// whose warps stay inside one parity class: a word still undecided after blocks
+// 0 and 1 (about one in eight) goes to the warp's queue dq, and whenever 32 are
+// queued the warp finishes them with all lanes (finish_deferred); the rest are
+// finished at the end of the half-sweep.  The decisions are the same; only the
+// lanes that take them change.  sp: the tile (word-major within a site row);
+// gbase: the tile's first word index (Philox group 8 (gbase + word) + b).
+template <int L, int W, int NP, int X0>
+__device__ __forceinline__ void sweep_rows_bits_dq(uint32_t* sp, int word, const SiteRec* recs, int part, int p,
+                                                   const ThreadPhilox (&tp)[2], uint32_t q, uint32_t gbase,
+                                                   Deferred* dq, const SweepArgs& a) {
+  constexpr int H = L / 2, RPP = L * L / NP;
+  const int lane = (int)(threadIdx.x & 31u);
+  const unsigned below = (1u << lane) - 1u;
+  uint32_t* spw = sp + word;
+  int head = 0, cnt = 0;  // the same in every lane of the warp
+#pragma unroll 1
+  for (int k = 0; k < RPP; ++k) {
+    const int r = row_index<L, NP>(part, k, p);
+    const int y = r % L, z = r / L;
+    const int yp = y == L - 1 ? 0 : y + 1, ym = y == 0 ? L - 1 : y - 1;
+    const int zp = z == L - 1 ? 0 : z + 1, zm = z == 0 ? L - 1 : z - 1;
+    uint32_t* p0 = spw + (size_t)r * L * W;
+    const uint32_t* pyp = spw + (size_t)(yp + L * z) * L * W;
+    const uint32_t* pym = spw + (size_t)(ym + L * z) * L * W;
+    const uint32_t* pzp = spw + (size_t)(y + L * zp) * L * W;
+    const uint32_t* pzm = spw + (size_t)(y + L * zm) * L * W;
+    const SiteRec* rr = recs + r * L;
+    const uint32_t h0 = (uint32_t)(r * L) >> 1;
+#pragma unroll 2
+    for (int xh = 0; xh < H; ++xh) {
+      const int x = 2 * xh + X0;
+      const int xp = x == L - 1 ? 0 : x + 1, xm = x == 0 ? L - 1 : x - 1;
+      const SiteRec sr = rr[x];
+      const uint32_t s0 = p0[x * W];
+      const uint32_t b0 = s0 ^ p0[xp * W] ^ sr.jxp, b1 = s0 ^ p0[xm * W] ^ sr.jxm;
+      const uint32_t b2 = s0 ^ pyp[x * W] ^ sr.jyp, b3 = s0 ^ pym[x * W] ^ sr.jym;
+      const uint32_t b4 = s0 ^ pzp[x * W] ^ sr.jzp, b5 = s0 ^ pzm[x * W] ^ sr.jzm;
+      const uint32_t sa = b0 ^ b1 ^ b2, ca = majority(b0, b1, b2);
+      const uint32_t sb = b3 ^ b4 ^ b5, cb = majority(b3, b4, b5);
+      const uint32_t u0 = sa ^ sb, k2 = sa & sb;
+      const uint32_t u1 = ca ^ cb ^ k2, u2 = majority(ca, cb, k2);
+      const uint32_t always = u2 | (u1 & u0);  // u >= 3: dE <= 0
+      const uint32_t m0 = ~(u0 | u1 | u2);      // u = 0: dE = 12
+      const uint32_t m1 = u0 & ~(u1 | u2);      // u = 1: dE = 8
+      const uint32_t m2 = u1 & ~(u0 | u2);      // u = 2: dE = 4
+      uint32_t eq = (m0 & a.live[0]) | (m1 & a.live[1]) | (m2 & a.live[2]);
+      uint32_t acc = 0;
+      const uint32_t uc = kM0 * (h0 + (uint32_t)xh);  // lo(M0 h), h = n >> 1
+      {
+        uint32_t w0[4], w1[4];
+        philox_block(uc, sr, tp[0], a.k0, a.k1, w0);
+        philox_block(uc, sr, tp[1], a.k0, a.k1, w1);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) compare_plane(w0[i], m0, m1, m2, a.tm[i][0], a.tm[i][1], a.tm[i][2], eq, acc);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          compare_plane(w1[i], m0, m1, m2, a.tm[4 + i][0], a.tm[4 + i][1], a.tm[4 + i][2], eq, acc);
+      }
+      p0[x * W] = s0 ^ (acc | always);
+      const unsigned dm = __ballot_sync(0xffffffffu, eq != 0u);
+      if (eq) {
+        Deferred d;
+        d.loc = (uint32_t)(r * L + x) | ((uint32_t)word << 16);
+        d.eq = eq;
+        d.m0 = m0;
+        d.m1 = m1;
+        dq[(head + cnt + __popc(dm & below)) & (kQueueCap - 1)] = d;
+      }
+      cnt += __popc(dm);
+      if (cnt >= 32) {
+        __syncwarp();
+        finish_deferred<W>(sp, recs, dq[(head + lane) & (kQueueCap - 1)], q, gbase, a);
+        __syncwarp();
+        head = (head + 32) & (kQueueCap - 1);
+        cnt -= 32;
+      }
+    }
+  }
+  __syncwarp();
+  if (lane < cnt) finish_deferred<W>(sp, recs, dq[(head + lane) & (kQueueCap - 1)], q, gbase, a);
+  __syncwarp();
+}
+
 // Gather the tile's spins from the parents of its slots into bit words; spar
 // holds the tile's parents (-1 past R~), slot i at index 33 (i >> 5) + (i & 31).
 template <int L, int W, int NP>
@@ -509,19 +640,75 @@ __device__ __forceinline__ void store_bits(const SweepArgs& a, const uint32_t* s
   }
 }
 
+// Families (a7) of the tile's new slots, so that a step needs no family launch
+// of its own: a family is a run of equal labels along the slots (labels ascend).
+// sh (shared memory, free by now) holds labs[0..TJ] (the slot before the tile,
+// then the tile's slots; -1 past R~), a bit mask per 32 slots of the slots that
+// start a run, and 64 words for the final sum.  The thread at a run's first slot
+// takes its end from the next start in the tile, or, for the tile's last run, by
+// galloping through the labels after the tile (run_end), and records the family
+// (pa_family.cuh); the last tile to finish adds the entropy.
+template <int TJ, int NT>
+__device__ __forceinline__ void tile_families(const SweepArgs& a, int* sh, int tile0, int R_new, int tid) {
+  constexpr int NC = TJ / 32;  // chunks of 32 slots (TJ <= 1024)
+  int* labs = sh;
+  unsigned* bm = reinterpret_cast<unsigned*>(sh + TJ + 1);
+  long long* red = reinterpret_cast<long long*>(sh + ((TJ + 1 + NC + 1) & ~1));
+  const int32_t* lab = a.pop.labels[1 - a.cur];
+  for (int i = tid; i <= TJ; i += NT) {
+    const int j = tile0 - 1 + i;
+    labs[i] = (j >= 0 && j < R_new) ? lab[j] : -1;
+  }
+  __syncthreads();
+  for (int c = tid; c < NC; c += NT) {
+    unsigned m = 0;
+    for (int l = 0; l < 32; ++l) m |= (labs[32 * c + l + 1] != labs[32 * c + l] ? 1u : 0u) << l;
+    bm[c] = m;
+  }
+  __syncthreads();
+  unsigned nz = 0;  // chunks that hold a run start
+  for (int c = 0; c < NC; ++c) nz |= (bm[c] != 0u ? 1u : 0u) << c;
+  const unsigned mask = warp_lanes(tid, NT);
+  FamilyAcc f;
+  for (int base = 0; base < TJ; base += NT) {  // the same iterations in every lane of a warp
+    const int i = base + tid, j = tile0 + i, c = i >> 5, l = i & 31;
+    int eta = 0;
+    if (i < TJ && j < R_new && (bm[c] >> l & 1u)) {
+      const unsigned above = l == 31 ? 0u : bm[c] & (~0u << (l + 1));
+      const unsigned later = c == 31 ? 0u : nz & (~0u << (c + 1));
+      int end;
+      if (above) {
+        end = tile0 + 32 * c + __ffs(above) - 1;
+      } else if (later) {
+        const int c2 = __ffs(later) - 1;
+        end = tile0 + 32 * c2 + __ffs(bm[c2]) - 1;
+      } else {
+        end = run_end(lab, labs[i + 1], tile0 + TJ, R_new);
+      }
+      eta = end - j;
+      f.add(eta);
+    }
+    family_size(a.pop, eta, mask);
+  }
+  family_flush(f, mask, &a.pop.rec[a.t]);
+  family_entropy_last(a.pop, &a.pop.rec[a.t], R_new, (R_new + TJ - 1) / TJ, tid, NT, red);
+}
+
 // Bit-sliced sweep kernel (+-1 couplings).
 template <int L, int W, int NT, int MB>
 __global__ void __launch_bounds__(NT, MB) k_sweep(const __grid_constant__ SweepArgs a) {
-  using S = BitShape<L, W, NT>;
+  using S = BitShape<L, W, NT, MB>;
   constexpr int N = S::N, NP = S::NP, TJ = S::TJ;
   extern __shared__ __align__(16) uint32_t sm[];
   uint32_t* sp = sm;                                               // spins [N][W]
   SiteRec* recs = reinterpret_cast<SiteRec*>(sm + (size_t)N * W);  // [N]
-  int* slots = reinterpret_cast<int*>(recs + N);                   // [33 W]: parents, then level counts
+  Deferred* queues = reinterpret_cast<Deferred*>(recs + N);        // [NQ][kQueueCap]
+  int* slots = reinterpret_cast<int*>(queues + S::NQ * kQueueCap);  // [33 W]: parents, then level counts
   const int R_new = a.pop.rec[a.t].R_tilde;
   const int tile0 = blockIdx.x * TJ;
   if (tile0 >= R_new) return;
   const int tid = threadIdx.x, word = tid % W, part = tid / W;
+  Deferred* dq = queues + (S::DEFER ? (tid >> 5) * kQueueCap : 0);
   init_tables<L>(a, recs, tid, NT);
   for (int i = tid; i < TJ; i += NT) slots[33 * (i >> 5) + (i & 31)] = tile0 + i < R_new ? a.pop.parents[tile0 + i] : -1;
   __syncthreads();
@@ -539,12 +726,21 @@ __global__ void __launch_bounds__(NT, MB) k_sweep(const __grid_constant__ SweepA
 #pragma unroll 1
     for (int c = 0; c < 2; ++c) {
       const uint32_t q = 2u * (uint32_t)s + (uint32_t)c;
-      const ThreadPhilox tp[4] = {thread_philox(g8, q, a.k0, a.k1), thread_philox(g8 + 1u, q, a.k0, a.k1),
-                                  thread_philox(g8 + 2u, q, a.k0, a.k1), thread_philox(g8 + 3u, q, a.k0, a.k1)};
-      if ((pclass ^ c) == 0)
-        sweep_rows_bits<L, W, NP, 0>(spw, recs, part, pclass, tp, q, g8, a);
-      else
-        sweep_rows_bits<L, W, NP, 1>(spw, recs, part, pclass, tp, q, g8, a);
+      if constexpr (S::DEFER) {
+        const ThreadPhilox tp[2] = {thread_philox(g8, q, a.k0, a.k1), thread_philox(g8 + 1u, q, a.k0, a.k1)};
+        const uint32_t gbase = (uint32_t)(tile0 >> 5);
+        if ((pclass ^ c) == 0)  // the same in every lane of the warp
+          sweep_rows_bits_dq<L, W, NP, 0>(sp, word, recs, part, pclass, tp, q, gbase, dq, a);
+        else
+          sweep_rows_bits_dq<L, W, NP, 1>(sp, word, recs, part, pclass, tp, q, gbase, dq, a);
+      } else {
+        const ThreadPhilox tp[4] = {thread_philox(g8, q, a.k0, a.k1), thread_philox(g8 + 1u, q, a.k0, a.k1),
+                                    thread_philox(g8 + 2u, q, a.k0, a.k1), thread_philox(g8 + 3u, q, a.k0, a.k1)};
+        if ((pclass ^ c) == 0)
+          sweep_rows_bits<L, W, NP, 0>(spw, recs, part, pclass, tp, q, g8, a);
+        else
+          sweep_rows_bits<L, W, NP, 1>(spw, recs, part, pclass, tp, q, g8, a);
+      }
       __syncthreads();
     }
   }
@@ -552,6 +748,8 @@ __global__ void __launch_bounds__(NT, MB) k_sweep(const __grid_constant__ SweepA
   __syncthreads();
   publish_levels<TJ>(a, slots, tile0, R_new, tid, NT);
   store_bits<L, W, NP>(a, sp, tile0, word, part);
+  __syncthreads();  // every shared array is dead now: the family pass takes the space
+  tile_families<TJ, NT>(a, reinterpret_cast<int*>(sm), tile0, R_new, tid);
 }
 
 // ---- Gaussian couplings (§II.A): nibble tiles (eight replicas per word, four
@@ -698,7 +896,7 @@ static int launch_g_t(const RunGeom& g, const GSweepArgs& args, cudaStream_t s) 
 
 template <int L, int W, int NT, int MB>
 static int launch_t(const RunGeom& g, const SweepArgs& args, cudaStream_t s) {
-  using S = BitShape<L, W, NT>;
+  using S = BitShape<L, W, NT, MB>;
   cudaError_t e =
       cudaFuncSetAttribute(k_sweep<L, W, NT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
   if (e != cudaSuccess) return (int)e;
@@ -721,7 +919,7 @@ struct ShapeEntry {
   size_t smem;
   int (*launch)(const RunGeom&, const SweepArgs&, cudaStream_t);
 };
-#define PA_SHAPE(L, W, NT, MB) {L, W, NT, MB, BitShape<L, W, NT>::SMEM, &launch_t<L, W, NT, MB>}
+#define PA_SHAPE(L, W, NT, MB) {L, W, NT, MB, BitShape<L, W, NT, MB>::SMEM, &launch_t<L, W, NT, MB>}
 const ShapeEntry kShapes[] = {
     PA_SHAPE(2, 32, 128, 1),   PA_SHAPE(2, 32, 64, 2),
     PA_SHAPE(4, 32, 256, 2),   PA_SHAPE(4, 32, 128, 4),  PA_SHAPE(4, 32, 512, 1),  PA_SHAPE(4, 8, 128, 4),

@@ -1,5 +1,6 @@
 """The C ABI library builds, loads and exports every entry point include/pa.h
 declares; the Python binding covers them all.  No compute calls (CPU only)."""
+import math
 import os
 import re
 
@@ -68,17 +69,17 @@ def test_footprint_is_the_slab_layout_without_gpu(palib):
     import numpy as np
     from paper_1711_02146_gb300 import pa
     from paper_1711_02146_gb300.workloads import Workload, linear_betas
-    step_rec = 80
+    step_rec = 88
     for L, R, n_pop, betas in [(4, 1000, 1, linear_betas(51, 5.0)), (10, 123457, 2, np.array([0.0, 0.1, 0.2, 0.25])),
                                (6, 7, 1, None)]:
         w = Workload("fp", L=L, R=R, disorder_seed=1, run_seed=2, betas=betas, n_temps=0 if betas is not None else 40,
                      eps_target=0.0 if betas is not None else 0.2, n_pop=n_pop)
         N, T, Rc = L ** 3, (len(betas) if betas is not None else 40), w.capacity
         pitch, nlev = -(-Rc // 1024) * 1024, 3 * L ** 3 + 1
-        ncb, neb = -(-Rc // 1024), -(-Rc // 4096)
+        ncb, nfs = -(-Rc // 1024), math.isqrt(2 * Rc) + 2
         want = _up(3 * N) + _up(16 * N) + _up(4) + _up(8 * T * 65)
         per_pop = (2 * (_up(N * pitch) + _up(4 * pitch)) + 3 * _up(4 * pitch) + _up(4 * ncb) + _up(8 * ncb) + _up(4)
-                   + _up(4 * T * nlev) + 2 * _up(4 * nlev) + _up(4) + _up(4 * (Rc + 1)) + _up(8 * neb)
+                   + _up(4 * T * nlev) + 2 * _up(4 * nlev) + 2 * _up(4 * (Rc + 1)) + _up(4 * nfs) + _up(8)
                    + _up(step_rec * T))
         want += n_pop * per_pop
         n_tables = len({float(d).hex() for d in np.diff(betas)}) if betas is not None else 1
@@ -93,14 +94,14 @@ def test_footprint_is_the_slab_layout_without_gpu(palib):
         w = Workload("g", L=L, R=R, disorder_seed=1, run_seed=2, betas=linear_betas(T, 2.0), model=1)
         N, Rc = L ** 3, w.capacity
         pitch, nlev = -(-Rc // 1024) * 1024, 3 * N + 1
-        ncb, neb, nchunk, nmb = -(-Rc // 1024), -(-Rc // 4096), -(-Rc // 256), -(-Rc // 4096)
+        ncb, nchunk, nmb, nfs = -(-Rc // 1024), -(-Rc // 256), -(-Rc // 4096), math.isqrt(2 * Rc) + 2
         levels, m = nchunk, nchunk
         while m > 256:
             m = -(-m // 256)
             levels += m
         want = _up(3 * N) + _up(16 * N) + _up(4) + _up(8 * T * 65)
         want += (2 * (_up(N * pitch) + _up(4 * pitch)) + 3 * _up(4 * pitch) + _up(4 * ncb) + _up(8 * ncb) + _up(4)
-                 + _up(4 * T * nlev) + 2 * _up(4 * nlev) + _up(4) + _up(4 * (Rc + 1)) + _up(8 * neb)
+                 + _up(4 * T * nlev) + 2 * _up(4 * nlev) + 2 * _up(4 * (Rc + 1)) + _up(4 * nfs) + _up(8)
                  + _up(step_rec * T))
         want += (_up(8 * pitch) + _up(8 * Rc) + _up(8 * levels) + 2 * _up(4 * Rc) + _up(16 * nmb) + _up(grec * T))
         want += _up(12 * N) + _up(4 * T * N * kpat) + _up(8 * T * kgw) + _up(8 * T * 65)

@@ -116,7 +116,7 @@ def _sections(blob, run, t, n_temps, n_levels, gauss=False):
     header = int(np.frombuffer(blob[12:16], np.uint32)[0])
     Rt, Rp = len(run.population(0)[1]), len(run.copy_counts(0))
     off, out = header + 12 * n_temps, {}
-    sizes = [("rec", 80 * (t + 1)), ("hist", (64 if gauss else 4 * n_levels) * (t + 1)), ("spins", run.N * Rt),
+    sizes = [("rec", 88 * (t + 1)), ("hist", (64 if gauss else 4 * n_levels) * (t + 1)), ("spins", run.N * Rt),
              ("labels", 4 * Rt), ("levels", (8 if gauss else 4) * Rt), ("counts", 4 * Rp), ("parents", 4 * Rt),
              ("mhist", 4 * (Rt + 1))]
     for name, size in sizes:
@@ -149,9 +149,9 @@ def test_refuses_damaged_contents(pa):
     levels0 = np.frombuffer(blob[lev:lev + 4 * Rt], np.int32)
     other = int(levels0[0] + 1 if levels0[0] + 1 < n_levels else levels0[0] - 1)
     damaged = {
-        "R_tilde of the last record": _put(blob, rec + 80 * t, np.int32, default_capacity(EXPLICIT["R"]) + 5),
-        "R_prev of a record": _put(blob, rec + 80 * 2 + 4, np.int32, 3),
-        "lowest level of a record": _put(blob, rec + 80 * 1 + 8, np.int32, n_levels),
+        "R_tilde of the last record": _put(blob, rec + 88 * t, np.int32, default_capacity(EXPLICIT["R"]) + 5),
+        "R_prev of a record": _put(blob, rec + 88 * 2 + 4, np.int32, 3),
+        "lowest level of a record": _put(blob, rec + 88 * 1 + 8, np.int32, n_levels),
         "a histogram bin": _put(blob, hist + 4 * (t * n_levels + 7), np.uint32, 99),
         "a spin byte": _put(blob, spins + 1234, np.int8, 0),
         "a label above R": _put(blob, lab + 4 * (Rt - 1), np.int32, EXPLICIT["R"]),

@@ -1,5 +1,7 @@
 """The table of sweep launch shapes (host logic, no GPU): every shape fits the
-kernel's tiling rules and one SM of a GB300, and the default comes first."""
+kernel's tiling rules and one SM of a GB300, and the default comes first.  Shapes
+whose warps each stay in one parity class get a queue of deferred comparisons per
+warp, where it costs no CTAs per SM."""
 import pytest
 
 SMEM_PER_SM = 228 * 1024      # shared memory per SM
@@ -29,7 +31,10 @@ def test_shapes_follow_the_tiling_rules(pa, L):
         NP = NT // W                                   # row partitions
         assert NP % 2 == 0 and (L * L // 2) % (NP // 2) == 0
         assert 1024 % (32 * W) == 0                    # a tile never crosses the 1024-slot pitch unit
-        assert s["smem_bytes"] == N * W * 4 + N * 32 + 33 * W * 4   # bit words, site records, slot table
+        tile = N * W * 4 + N * 32 + 33 * W * 4          # bit words, site records, slot table
+        queues = (NT // 32) * 64 * 16                     # 64 deferred words of 16 bytes per warp
+        defer = NT % 32 == 0 and (NP // 2 * W) % 32 == 0 and MB * (tile + queues + RESERVED_PER_CTA) <= SMEM_PER_SM
+        assert s["smem_bytes"] == tile + (queues if defer else 0)
         assert s["smem_bytes"] <= SMEM_PER_CTA
         assert MB * (s["smem_bytes"] + RESERVED_PER_CTA) <= SMEM_PER_SM
         assert MB * NT <= 2048
