@@ -1,5 +1,6 @@
 // pa_device.cuh — device helpers: Philox4x32-10 and block reductions.
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -63,6 +64,23 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* scratch, int* to
   if (total) *total = scratch[32];
   __syncthreads();
   return out;
+}
+
+// Raises kernel k's dynamic shared-memory limit to `bytes` on the current device,
+// once per device and process: the attribute persists, and setting it before every
+// launch costs host time (and is not part of what a stream capture records).  `done`
+// holds one flag per device (static storage of the launcher); a device reset in
+// between is not supported.
+template <typename K>
+inline cudaError_t smem_limit_once(K k, int bytes, std::atomic<int>* done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done[dev].store(1, std::memory_order_release);
+  return e;
 }
 
 }  // namespace pa

@@ -543,7 +543,8 @@ int launch_reweight(const RunGeom& g, PopDev* pops, const double* w, int t, void
   const bool in_smem = g.n_levels <= 3 * kMaxL * kMaxL * kMaxL + 1;  // every lattice of the shared-memory sweep
   const size_t smem = in_smem ? sizeof(int) * (size_t)g.n_levels : 0;
   if (smem > 48 * 1024) {
-    const cudaError_t e = cudaFuncSetAttribute(k_reweight, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static std::atomic<int> done[64];
+    const cudaError_t e = smem_limit_once(k_reweight, (int)(sizeof(int) * (3 * kMaxL * kMaxL * kMaxL + 1)), done);
     if (e != cudaSuccess) return (int)e;
   }
   k_reweight<<<g.n_pop, 1024, smem, (cudaStream_t)stream>>>(g, pack(pops, g.n_pop), w, t, in_smem ? 1 : 0);

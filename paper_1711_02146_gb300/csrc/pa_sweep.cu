@@ -23,10 +23,11 @@
 // bit 31 - p of r is bit b of word p mod 4 of Philox4x32-10 at counter
 // (n >> 1, 2s + c, 8 (slot >> 5) + p / 4, t) keyed by (run_seed, Metropolis,
 // population), so one block gives four bit planes of 32 replicas' uniforms.
-// The comparison runs from the top plane down: a replica is decided at the first
-// plane where its bit differs from its threshold's (accepted if the threshold
-// has the 1), two planes on average; blocks are drawn until every replica of
-// the word is decided (blocks 0 and 1 always, the rest on demand).
+// A replica is decided at the first plane, from the top, where its bit differs
+// from its threshold's (accepted if the threshold has the 1): two planes on
+// average.  Blocks 0 and 1 (planes 0..7) are always drawn and compared as one
+// 8-bit bit-sliced subtraction (its borrow is "below", plus an "equal so far"
+// mask); the words with replicas still equal draw further blocks on demand.
 //
 // Philox hoisting (same function, fewer multiplies): with counter words
 // (h, q, g, t) = (site, half-sweep, group, step), the round-1 and round-2
@@ -58,8 +59,12 @@ struct SweepArgs {
   uint32_t thr4, thr8, thr12;
   uint32_t k0[10];  // Metropolis round keys of this population
   uint32_t k1[10];
-  uint32_t tm[32][4];  // +-1: bit 31 - p of thr(u), u = 0, 1, 2, as an all-zero / all-one word
-  uint32_t live[4];    // +-1: all ones where thr(u) > 0 (a replica with thr(u) = 0 never flips)
+  // +-1: plane p's threshold bit as a function of the unsatisfied-bond count u
+  // (bits u0, u1; u = 0, 1, 2): T(u) = bit 31 - p of thr(u) as an all-zero / all-one
+  // word, stored as tm[p] = {T(0), T(0) ^ T(1), T(0) ^ T(2)}, so that the bit of a
+  // replica is tm[p][0] ^ (u0 & tm[p][1]) ^ (u1 & tm[p][2]) (u >= 3 never compares)
+  uint32_t tm[32][4];
+  uint32_t live[4];    // +-1: the same form of "thr(u) > 0" (a replica with thr(u) = 0 never flips)
 };
 
 // Per-site shared-memory record: the six bond masks of the site (all ones for
@@ -282,9 +287,9 @@ constexpr int bits_for(int n) { return n < 2 ? 1 : 1 + bits_for(n / 2); }
 
 // A word whose replicas the first two Philox blocks (bit planes 0..7) leave
 // undecided: its site n and word (n | word << 16), the undecided replicas, and
-// their classes u = 0 and u = 1 (u = 2 is the rest of them).
+// bits 0 and 1 of their unsatisfied-bond counts.
 struct __align__(16) Deferred {
-  uint32_t loc, eq, m0, m1;
+  uint32_t loc, eq, u0, u1;
 };
 constexpr int kQueueCap = 64;  // a warp queues at most 31 + 32 words before it finishes 32 of them
 
@@ -338,16 +343,32 @@ __device__ __forceinline__ void philox_block(uint32_t uc, const SiteRec& sr, con
   }
 }
 
-// One plane of the comparison uniform < threshold for the 32 replicas of a word:
-// r holds the plane's bit of every replica's uniform, t0..t2 the plane's bit of
-// thr(u) for u = 0, 1, 2 as all-zero / all-one words, m0..m2 the replicas of
-// each u.  eq: replicas whose uniform has matched its threshold so far; acc:
+// The plane's threshold bit of each replica of a word (SweepArgs::tm), from bits
+// u0, u1 of its unsatisfied-bond count.
+__device__ __forceinline__ uint32_t threshold_bits(const uint32_t* tm, uint32_t u0, uint32_t u1) {
+  return tm[0] ^ (u0 & tm[1]) ^ (u1 & tm[2]);
+}
+
+// One plane of the comparison uniform < threshold for the 32 replicas of a word,
+// most significant plane first: r holds the plane's bit of every replica's
+// uniform.  eq: replicas whose uniform has matched its threshold so far; acc:
 // replicas decided below it.
-__device__ __forceinline__ void compare_plane(uint32_t r, uint32_t m0, uint32_t m1, uint32_t m2, uint32_t t0,
-                                              uint32_t t1, uint32_t t2, uint32_t& eq, uint32_t& acc) {
-  const uint32_t t = (m0 & t0) | (m1 & t1) | (m2 & t2);
+__device__ __forceinline__ void compare_plane(uint32_t r, uint32_t u0, uint32_t u1, const uint32_t* tm, uint32_t& eq,
+                                              uint32_t& acc) {
+  const uint32_t t = threshold_bits(tm, u0, u1);
   acc |= eq & t & ~r;
   eq &= ~(r ^ t);
+}
+
+// One plane of the same comparison taken least significant plane first, as the
+// borrow of a bit-sliced subtraction r - thr: after the planes p..7, lt holds the
+// replicas whose bits p..7 of r are below those of thr, same those whose bits
+// p..7 are equal.
+__device__ __forceinline__ void borrow_plane(uint32_t r, uint32_t u0, uint32_t u1, const uint32_t* tm, uint32_t& lt,
+                                             uint32_t& same) {
+  const uint32_t t = threshold_bits(tm, u0, u1);
+  lt = (~r & t) | (~(r ^ t) & lt);
+  same &= ~(r ^ t);
 }
 
 // One half-sweep of the rows of partition `part` (parity class p, colour sites at
@@ -387,10 +408,8 @@ __device__ __forceinline__ void sweep_rows_bits(uint32_t* spw, const SiteRec* re
       const uint32_t u0 = sa ^ sb, k2 = sa & sb;
       const uint32_t u1 = ca ^ cb ^ k2, u2 = majority(ca, cb, k2);
       const uint32_t always = u2 | (u1 & u0);  // u >= 3: dE <= 0
-      const uint32_t m0 = ~(u0 | u1 | u2);      // u = 0: dE = 12
-      const uint32_t m1 = u0 & ~(u1 | u2);      // u = 1: dE = 8
-      const uint32_t m2 = u1 & ~(u0 | u2);      // u = 2: dE = 4
-      uint32_t eq = (m0 & a.live[0]) | (m1 & a.live[1]) | (m2 & a.live[2]);
+      // replicas to compare: u = 0, 1, 2 (dE = 12, 8, 4) with thr(u) > 0
+      uint32_t eq = ~always & threshold_bits(a.live, u0, u1);
       uint32_t acc = 0;
       const uint32_t uc = kM0 * (h0 + (uint32_t)xh);  // lo(M0 h), h = n >> 1
       {
@@ -398,24 +417,21 @@ __device__ __forceinline__ void sweep_rows_bits(uint32_t* spw, const SiteRec* re
         philox_block(uc, sr, tp[0], a.k0, a.k1, w0);
         philox_block(uc, sr, tp[1], a.k0, a.k1, w1);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) compare_plane(w0[i], m0, m1, m2, a.tm[i][0], a.tm[i][1], a.tm[i][2], eq, acc);
+        for (int i = 0; i < 4; ++i) compare_plane(w0[i], u0, u1, a.tm[i], eq, acc);
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-          compare_plane(w1[i], m0, m1, m2, a.tm[4 + i][0], a.tm[4 + i][1], a.tm[4 + i][2], eq, acc);
+        for (int i = 0; i < 4; ++i) compare_plane(w1[i], u0, u1, a.tm[4 + i], eq, acc);
       }
       if (eq) {
         uint32_t w[4];
         philox_block(uc, sr, tp[2], a.k0, a.k1, w);
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-          compare_plane(w[i], m0, m1, m2, a.tm[8 + i][0], a.tm[8 + i][1], a.tm[8 + i][2], eq, acc);
+        for (int i = 0; i < 4; ++i) compare_plane(w[i], u0, u1, a.tm[8 + i], eq, acc);
       }
       if (eq) {
         uint32_t w[4];
         philox_block(uc, sr, tp[3], a.k0, a.k1, w);
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-          compare_plane(w[i], m0, m1, m2, a.tm[12 + i][0], a.tm[12 + i][1], a.tm[12 + i][2], eq, acc);
+        for (int i = 0; i < 4; ++i) compare_plane(w[i], u0, u1, a.tm[12 + i], eq, acc);
       }
 #pragma unroll 1
       for (int b = 4; b < 8 && eq; ++b) {  // rare: some replica matched its threshold for 16 bits
@@ -423,10 +439,7 @@ __device__ __forceinline__ void sweep_rows_bits(uint32_t* spw, const SiteRec* re
         uint32_t w[4];
         philox_block(uc, sr, tb, a.k0, a.k1, w);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const uint32_t* tmp = a.tm[4 * b + i];
-          compare_plane(w[i], m0, m1, m2, tmp[0], tmp[1], tmp[2], eq, acc);
-        }
+        for (int i = 0; i < 4; ++i) compare_plane(w[i], u0, u1, a.tm[4 * b + i], eq, acc);
       }
       p0[x * W] = s0 ^ (acc | always);
     }
@@ -441,7 +454,7 @@ template <int W>
 __device__ __forceinline__ void finish_deferred(uint32_t* sp, const SiteRec* recs, const Deferred d, uint32_t q,
                                                 uint32_t gbase, const SweepArgs& a) {
   const int n = (int)(d.loc & 0xffffu), word = (int)(d.loc >> 16);
-  const uint32_t m0 = d.m0, m1 = d.m1, m2 = ~(m0 | m1);
+  const uint32_t u0 = d.u0, u1 = d.u1;
   uint32_t eq = d.eq, acc = 0;
   const uint32_t g8 = 8u * (gbase + (uint32_t)word);
   const uint32_t uc = kM0 * ((uint32_t)n >> 1);
@@ -452,10 +465,7 @@ __device__ __forceinline__ void finish_deferred(uint32_t* sp, const SiteRec* rec
     uint32_t w[4];
     philox_block(uc, sr, tb, a.k0, a.k1, w);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const uint32_t* tmp = a.tm[4 * b + i];
-      compare_plane(w[i], m0, m1, m2, tmp[0], tmp[1], tmp[2], eq, acc);
-    }
+    for (int i = 0; i < 4; ++i) compare_plane(w[i], u0, u1, a.tm[4 * b + i], eq, acc);
   }
   sp[n * W + word] ^= acc;
 }
@@ -503,30 +513,28 @@ __device__ __forceinline__ void sweep_rows_bits_dq(uint32_t* sp, int word, const
       const uint32_t u0 = sa ^ sb, k2 = sa & sb;
       const uint32_t u1 = ca ^ cb ^ k2, u2 = majority(ca, cb, k2);
       const uint32_t always = u2 | (u1 & u0);  // u >= 3: dE <= 0
-      const uint32_t m0 = ~(u0 | u1 | u2);      // u = 0: dE = 12
-      const uint32_t m1 = u0 & ~(u1 | u2);      // u = 1: dE = 8
-      const uint32_t m2 = u1 & ~(u0 | u2);      // u = 2: dE = 4
-      uint32_t eq = (m0 & a.live[0]) | (m1 & a.live[1]) | (m2 & a.live[2]);
-      uint32_t acc = 0;
+      // replicas to compare: u = 0, 1, 2 (dE = 12, 8, 4) with thr(u) > 0
+      const uint32_t cmp = ~always & threshold_bits(a.live, u0, u1);
+      uint32_t lt = 0, eq = cmp;
       const uint32_t uc = kM0 * (h0 + (uint32_t)xh);  // lo(M0 h), h = n >> 1
       {
         uint32_t w0[4], w1[4];
         philox_block(uc, sr, tp[0], a.k0, a.k1, w0);
         philox_block(uc, sr, tp[1], a.k0, a.k1, w1);
+        // bits 31..24 of each uniform against those of its threshold, lowest plane first
 #pragma unroll
-        for (int i = 0; i < 4; ++i) compare_plane(w0[i], m0, m1, m2, a.tm[i][0], a.tm[i][1], a.tm[i][2], eq, acc);
+        for (int i = 3; i >= 0; --i) borrow_plane(w1[i], u0, u1, a.tm[4 + i], lt, eq);
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-          compare_plane(w1[i], m0, m1, m2, a.tm[4 + i][0], a.tm[4 + i][1], a.tm[4 + i][2], eq, acc);
+        for (int i = 3; i >= 0; --i) borrow_plane(w0[i], u0, u1, a.tm[i], lt, eq);
       }
-      p0[x * W] = s0 ^ (acc | always);
+      p0[x * W] = s0 ^ ((cmp & lt) | always);
       const unsigned dm = __ballot_sync(0xffffffffu, eq != 0u);
       if (eq) {
         Deferred d;
         d.loc = (uint32_t)(r * L + x) | ((uint32_t)word << 16);
         d.eq = eq;
-        d.m0 = m0;
-        d.m1 = m1;
+        d.u0 = u0;
+        d.u1 = u1;
         dq[(head + cnt + __popc(dm & below)) & (kQueueCap - 1)] = d;
       }
       cnt += __popc(dm);
@@ -651,24 +659,31 @@ __device__ __forceinline__ void store_bits(const SweepArgs& a, const uint32_t* s
 template <int TJ, int NT>
 __device__ __forceinline__ void tile_families(const SweepArgs& a, int* sh, int tile0, int R_new, int tid) {
   constexpr int NC = TJ / 32;  // chunks of 32 slots (TJ <= 1024)
+  static_assert(NT % 32 == 0 || TJ <= NT, "the lanes of a warp take whole chunks");
   int* labs = sh;
-  unsigned* bm = reinterpret_cast<unsigned*>(sh + TJ + 1);
-  long long* red = reinterpret_cast<long long*>(sh + ((TJ + 1 + NC + 1) & ~1));
+  unsigned* bm = reinterpret_cast<unsigned*>(sh + TJ + 1);  // [NC + 1]: start bits per chunk, then chunks with starts
+  long long* red = reinterpret_cast<long long*>(sh + ((TJ + 1 + NC + 2) & ~1));
   const int32_t* lab = a.pop.labels[1 - a.cur];
+  const unsigned mask = warp_lanes(tid, NT);
   for (int i = tid; i <= TJ; i += NT) {
     const int j = tile0 - 1 + i;
     labs[i] = (j >= 0 && j < R_new) ? lab[j] : -1;
   }
   __syncthreads();
-  for (int c = tid; c < NC; c += NT) {
-    unsigned m = 0;
-    for (int l = 0; l < 32; ++l) m |= (labs[32 * c + l + 1] != labs[32 * c + l] ? 1u : 0u) << l;
-    bm[c] = m;
+  // run starts, one ballot per chunk (lanes of a warp take consecutive slots)
+  for (int base = 0; base < TJ; base += NT) {
+    const int i = base + tid;
+    const bool start = i < TJ && labs[i + 1] != labs[i];
+    const unsigned b = __ballot_sync(mask, start);
+    if ((i & 31) == 0 && i < TJ) bm[i >> 5] = b;
   }
   __syncthreads();
-  unsigned nz = 0;  // chunks that hold a run start
-  for (int c = 0; c < NC; ++c) nz |= (bm[c] != 0u ? 1u : 0u) << c;
-  const unsigned mask = warp_lanes(tid, NT);
+  if (tid < 32) {  // chunks that hold a run start
+    const unsigned nzb = __ballot_sync(0xffffffffu, tid < NC && bm[tid] != 0u);
+    if (tid == 0) bm[NC] = nzb;
+  }
+  __syncthreads();
+  const unsigned nz = bm[NC];
   FamilyAcc f;
   for (int base = 0; base < TJ; base += NT) {  // the same iterations in every lane of a warp
     const int i = base + tid, j = tile0 + i, c = i >> 5, l = i & 31;
@@ -887,7 +902,8 @@ template <int L, int W, int NT, int MB>
 static int launch_g_t(const RunGeom& g, const GSweepArgs& args, cudaStream_t s) {
   using S = SweepShape<L, W, NT>;
   const size_t smem = S::SMEM + (size_t)S::TJ * 4;  // energy counters are 8 bytes, not 4
-  cudaError_t e = cudaFuncSetAttribute(k_sweep_g<L, W, NT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static std::atomic<int> done[64];
+  const cudaError_t e = smem_limit_once(k_sweep_g<L, W, NT, MB>, (int)smem, done);
   if (e != cudaSuccess) return (int)e;
   dim3 grid((unsigned)((g.R_cap + S::TJ - 1) / S::TJ));
   k_sweep_g<L, W, NT, MB><<<grid, NT, smem, s>>>(args);
@@ -897,8 +913,8 @@ static int launch_g_t(const RunGeom& g, const GSweepArgs& args, cudaStream_t s) 
 template <int L, int W, int NT, int MB>
 static int launch_t(const RunGeom& g, const SweepArgs& args, cudaStream_t s) {
   using S = BitShape<L, W, NT, MB>;
-  cudaError_t e =
-      cudaFuncSetAttribute(k_sweep<L, W, NT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+  static std::atomic<int> done[64];
+  const cudaError_t e = smem_limit_once(k_sweep<L, W, NT, MB>, (int)S::SMEM, done);
   if (e != cudaSuccess) return (int)e;
   dim3 grid((unsigned)((g.R_cap + S::TJ - 1) / S::TJ));
   k_sweep<L, W, NT, MB><<<grid, NT, S::SMEM, s>>>(args);
@@ -987,10 +1003,18 @@ int launch_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, 
     args.thr12 = met_thr[2];
     const uint32_t thr_u[3] = {met_thr[2], met_thr[1], met_thr[0]};  // u = 0, 1, 2: dE = 12, 8, 4
     for (int p = 0; p < 32; ++p) {
-      for (int u = 0; u < 3; ++u) args.tm[p][u] = ((thr_u[u] >> (31 - p)) & 1u) ? ~0u : 0u;
+      uint32_t T[3];
+      for (int u = 0; u < 3; ++u) T[u] = ((thr_u[u] >> (31 - p)) & 1u) ? ~0u : 0u;
+      args.tm[p][0] = T[0];
+      args.tm[p][1] = T[0] ^ T[1];
+      args.tm[p][2] = T[0] ^ T[2];
       args.tm[p][3] = 0u;
     }
-    for (int u = 0; u < 3; ++u) args.live[u] = thr_u[u] ? ~0u : 0u;
+    uint32_t live[3];
+    for (int u = 0; u < 3; ++u) live[u] = thr_u[u] ? ~0u : 0u;
+    args.live[0] = live[0];
+    args.live[1] = live[0] ^ live[1];
+    args.live[2] = live[0] ^ live[2];
     args.live[3] = 0u;
     const int e = shape->launch(g, args, s);
     if (e != 0) return e;
