@@ -215,6 +215,33 @@ __global__ void __launch_bounds__(kCountThreads) k_g_counts(RunGeom g, GArgs a, 
   }
 }
 
+// ---------------------------------------------------------------- adaptive schedule
+
+// Weight tables T_k[m] = exp(-dbeta m 2^(12k) 2^-20) (T0 | T1 | T2, kGTableWeights
+// entries) for dbeta = *dbeta_dev, or dbeta_val when dbeta_dev is null: the
+// adaptive schedule's trials and its chosen step build their tables here, so a
+// trial and the resampling that follows it use the same weights.
+__global__ void k_g_tables(const double* __restrict__ dbeta_dev, double dbeta_val, double* T) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= kGTableWeights) return;
+  const double db = dbeta_dev ? *dbeta_dev : dbeta_val;
+  const long long q = m < 4096 ? (long long)m : m < 8192 ? (long long)(m - 4096) << 12 : (long long)(m - 8192) << 24;
+  T[m] = exp(-__dmul_rn(db, __dmul_rn((double)q, 0x1p-20)));
+}
+
+// One halving of the bisection (§IV.B): b = {lo, hi, mid}; the trial at mid gave
+// population 0's culling fraction in its step-t record.  Keeps mid as lo when the
+// fraction does not exceed the target, else as hi, and sets the next midpoint
+// 0.5 (lo + hi) (the host's arithmetic, rounded the same way).
+__global__ void k_g_decide(GArgs a, int t, double target, double* b) {
+  const double e = a.p[0].rec[t].eps_expected;
+  if (e <= target)
+    b[0] = b[2];
+  else
+    b[1] = b[2];
+  b[2] = __dmul_rn(0.5, __dadd_rn(b[0], b[1]));
+}
+
 // ---------------------------------------------------------------- measurement
 
 constexpr int kMeasureThreads = 256;
@@ -393,6 +420,24 @@ int launch_g_eps_trial(const RunGeom& g, PopDev* pops, int t, const double* wtab
   launch_levels(g1, a, 1, t, 0, s);
   k_g_tau<<<chunks, kChunk, 0, s>>>(g1, a, t);
   launch_levels(g1, a, 1, t, 1, s);
+  return (int)cudaGetLastError();
+}
+
+int launch_g_tables(const double* dbeta_dev, double dbeta_val, double* T, void* stream) {
+  k_g_tables<<<blocks_for(kGTableWeights, 256), 256, 0, (cudaStream_t)stream>>>(dbeta_dev, dbeta_val, T);
+  return (int)cudaGetLastError();
+}
+
+int launch_g_bisect(const RunGeom& g, PopDev* pops, int t, double* T, double* b, double target, int halvings,
+                    void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  GArgs a = gpack(pops, 1);
+  for (int it = 0; it < halvings; ++it) {
+    k_g_tables<<<blocks_for(kGTableWeights, 256), 256, 0, s>>>(b + 2, 0.0, T);
+    const int e = launch_g_eps_trial(g, pops, t, T, stream);
+    if (e) return e;
+    k_g_decide<<<1, 1, 0, s>>>(a, t, target, b);
+  }
   return (int)cudaGetLastError();
 }
 

@@ -158,6 +158,13 @@ int launch_g_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab
 // resampling recomputes): one evaluation of the adaptive bisection.
 int launch_g_eps_trial(const RunGeom& g, PopDev* pops, int t, const double* wtab, void* stream);
 int launch_g_measure(const RunGeom& g, PopDev* pops, int cur, int t, unsigned long long* qlhist, void* stream);
+// Weight tables of dbeta (*dbeta_dev, or dbeta_val when it is null) built on the device.
+int launch_g_tables(const double* dbeta_dev, double dbeta_val, double* T, void* stream);
+// `halvings` halvings of the adaptive bisection on the device, with no host wait:
+// b = {lo, hi, mid} in device memory; each halving builds mid's tables in T, runs
+// the trial of launch_g_eps_trial and updates b.
+int launch_g_bisect(const RunGeom& g, PopDev* pops, int t, double* T, double* b, double target, int halvings,
+                    void* stream);
 int launch_overlap(const RunGeom& g, PopDev* pops, int cur, int t, unsigned long long* qhist, void* stream);
 }  // namespace pa
 struct pa_ctx;

@@ -68,6 +68,7 @@ struct pa_ctx {
   uint32_t* gtab = nullptr;              // device [n_temps][N][64] acceptance thresholds
   double* gw = nullptr;                  // device [n_temps][16384] weight tables
   unsigned long long* qlhist = nullptr;  // device [n_temps][q_bins] link-overlap histograms
+  double* gbis = nullptr;                // device {lo, hi, mid}: the adaptive bisection (Gaussian)
   std::vector<int32_t> Jq_host;
   pa::LookbackTest lookback;             // pa_debug_lookback (tests of the bounded wait)
 };
@@ -424,37 +425,36 @@ int choose_dbeta(pa_ctx* c, double* dbeta) {
 // Adaptive step for Gaussian couplings: the same bisection, with the culling
 // fraction of each trial computed on the device from that trial's weight tables
 // (the definitions the resampling uses), population 0 deciding.
-int gauss_eps(pa_ctx* c, int t, double dbeta, double* eps) {
-  std::vector<double> wt((size_t)pa::kGTableWeights);
-  gauss_weight_tables(dbeta, wt.data());
-  int rc = copy_h2d(c, c->gw, wt.data(), sizeof(double) * wt.size());
-  if (rc == PA_OK) rc = pa::launch_g_eps_trial(c->g, c->pops, t, c->gw, c->stream) == 0 ? PA_OK : PA_ERR_CUDA;
-  if (rc == PA_OK) rc = copy_d2h(c, eps, &c->pops[0].rec[t].eps_expected, sizeof(double));
-  return rc;
-}
+int launch_rc(int e) { return e == 0 ? PA_OK : PA_ERR_CUDA; }
 
+// Adaptive step with Gaussian couplings (§IV.B), as for +-1 couplings: the largest
+// dbeta in (0, beta_max - beta] whose culling fraction (population 0, the
+// resampling's own weights and sums) does not exceed the target, by 64 bisection
+// halvings.  The halvings run on the device one after another (launch_g_bisect)
+// with no host wait between them; the host reads the first trial (the whole
+// remaining range) and the final interval.
 int choose_dbeta_gauss(pa_ctx* c, double* dbeta) {
   const int t = c->t + 1;
   const double rem = c->cfg.beta_max - c->betas[(size_t)c->t];
   const double target = c->cfg.eps_target;
+  double b[3] = {0.0, rem, rem};
+  int rc = copy_h2d(c, c->gbis, b, sizeof b);
+  if (rc == PA_OK) rc = launch_rc(pa::launch_g_tables(c->gbis + 2, 0.0, c->gw, c->stream));
+  if (rc == PA_OK) rc = launch_rc(pa::launch_g_eps_trial(c->g, c->pops, t, c->gw, c->stream));
   double e = 0.0;
-  int rc = gauss_eps(c, t, rem, &e);
+  if (rc == PA_OK) rc = copy_d2h(c, &e, &c->pops[0].rec[t].eps_expected, sizeof(double));
   if (rc != PA_OK) return rc;
   if (e <= target) {
     *dbeta = rem;
     return PA_OK;
   }
-  double lo = 0.0, hi = rem;
-  for (int it = 0; it < 64 && rc == PA_OK; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    rc = gauss_eps(c, t, mid, &e);
-    if (e <= target)
-      lo = mid;
-    else
-      hi = mid;
-  }
-  *dbeta = lo > 0.0 ? lo : hi;
-  return rc;
+  b[2] = 0.5 * (b[0] + b[1]);
+  rc = copy_h2d(c, c->gbis, b, sizeof b);
+  if (rc == PA_OK) rc = launch_rc(pa::launch_g_bisect(c->g, c->pops, t, c->gw, c->gbis, target, 64, c->stream));
+  if (rc == PA_OK) rc = copy_d2h(c, b, c->gbis, sizeof b);
+  if (rc != PA_OK) return rc;
+  *dbeta = b[0] > 0.0 ? b[0] : b[1];
+  return PA_OK;
 }
 
 int check_device_status(pa_ctx* c) {
@@ -473,7 +473,6 @@ int fail(pa_ctx* c, int rc) {
   return rc;
 }
 
-int launch_rc(int e) { return e == 0 ? PA_OK : PA_ERR_CUDA; }
 
 
 
@@ -649,6 +648,7 @@ int layout_buffers(pa_ctx* c) {
     rc = rc ? rc : dalloc(c, &c->gtab, slots * (size_t)g.N * pa::kGPatterns);
     rc = rc ? rc : dalloc(c, &c->gw, slots * (size_t)pa::kGTableWeights);
     rc = rc ? rc : dalloc(c, &c->qlhist, T * (size_t)g.q_bins);
+    if (c->adaptive) rc = rc ? rc : dalloc(c, &c->gbis, (size_t)4);
   } else if (c->adaptive) {
     rc = rc ? rc : dalloc(c, &c->wadapt, (size_t)g.n_levels);
   } else {  // one Boltzmann weight table per distinct increment
@@ -961,11 +961,11 @@ int pa_step(pa_ctx* c) {
     const size_t slot = c->adaptive ? 0 : (size_t)t;
     if (c->adaptive && rc == PA_OK) {  // this step's tables, for the beta just chosen
       std::vector<uint32_t> tab((size_t)c->g.N * pa::kGPatterns);
-      std::vector<double> wt((size_t)pa::kGTableWeights);
       gauss_site_tables(c->Jq_host, c->g.L, c->betas[(size_t)t], tab.data());
-      gauss_weight_tables(dbeta, wt.data());
       rc = copy_h2d(c, c->gtab, tab.data(), sizeof(uint32_t) * tab.size());
-      if (rc == PA_OK) rc = copy_h2d(c, c->gw, wt.data(), sizeof(double) * wt.size());
+      // the weight tables as the bisection's trials built them, so the resampling's
+      // culling fraction is the one the bisection accepted
+      if (rc == PA_OK) rc = launch_rc(pa::launch_g_tables(nullptr, dbeta, c->gw, c->stream));
     }
     if (rc == PA_OK) {
       PhaseTimer pt(c, PA_PHASE_RESAMPLE, 7);
