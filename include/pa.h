@@ -244,6 +244,58 @@ typedef struct {
 int pa_stats_reset(pa_ctx* ctx, int enable_timing);
 int pa_get_stats(pa_ctx* ctx, pa_stats* out);
 
+/* ---- one population split across ranks (§I: PA runs on computing clusters) ----
+ * A sharded run splits each population by slot across n_ranks processes: rank r
+ * holds the global slots [lo_r, hi_r) of every population, whole units of 1024
+ * slots as balanced as units allow (the last units of the population size), cut
+ * from the larger population of the step so that slot j of both populations is
+ * on one rank.  Every random word is addressed by global slot, so the results are
+ * those of one process bit for bit (+-1 couplings, explicit schedules, even
+ * L <= 16).  A temperature step (pa_shard_step, collective over all ranks):
+ *   1. the level histogram of the last step is summed over ranks (allreduce), so
+ *      every rank builds the same reweighting tables (Eqs. tau, Q);
+ *   2. copy numbers of the local old slots; their totals are gathered from all
+ *      ranks (allgather), which places each rank's copies in the global order;
+ *   3. every copy moves to the rank that holds its new slot (send / recv, each pair
+ *      of ranks in rank order: spins as N rows of bytes, then labels);
+ *   4. sweeps of the local slots, local level histograms;
+ *   5. measurements: histograms summed over ranks; families as runs of the sorted
+ *      labels, the first and last run of every rank joined across rank
+ *      boundaries; the overlap histogram of co-located slot pairs summed.
+ * The host functions in pa_comm carry the exchanges (for example over gloo); each
+ * returns 0 on success.  The runs of all ranks run on one device or several. */
+typedef struct {
+  void* user;
+  /* element-wise sum over the ranks of n int64 values, in place */
+  int (*allreduce_i64)(void* user, int64_t* values, int64_t n);
+  /* n int64 values from every rank: out[q n + i] is value i of rank q */
+  int (*allgather_i64)(void* user, const int64_t* values, int64_t n, int64_t* out);
+  /* blocking point-to-point transfer of `bytes` bytes to / from another rank */
+  int (*send)(void* user, int32_t dst, const void* buf, int64_t bytes);
+  int (*recv)(void* user, int32_t src, void* buf, int64_t bytes);
+} pa_comm;
+typedef struct pa_shard pa_shard;
+
+/* Rank `rank` of n_ranks (collective: all ranks call it with the same config).
+ * The rank's device buffers are sized for the whole capacity R_cap (a rank may
+ * receive every copy).  PA_ERR_INVALID for an adaptive schedule, Gaussian
+ * couplings, L outside the shared-memory sweep or a bad rank. */
+int pa_shard_create(const pa_config* cfg, int32_t rank, int32_t n_ranks, const pa_comm* comm, void* cuda_stream,
+                    pa_shard** out);
+/* One temperature step of every rank (collective); PA_DONE after the last. */
+int pa_shard_step(pa_shard* shard);
+/* Observables of step t (the whole population's, the same on every rank). */
+int pa_shard_observables(pa_shard* shard, int32_t t, int32_t pop, pa_obs* out);
+/* This rank's run (its slots of the current population), for the per-rank
+ * readers (pa_get_replicas, pa_population_size, pa_get_copy_counts ...); it
+ * belongs to the shard. */
+int pa_shard_local(pa_shard* shard, pa_ctx** local);
+/* Global slot of this rank's first slot, and the global population size. */
+int pa_shard_extent(pa_shard* shard, int32_t pop, int64_t* lo, int64_t* R_tilde);
+/* The overlap histogram of step t (q_bins entries, summed over the ranks). */
+int pa_shard_q_hist(pa_shard* shard, int32_t t, int64_t* out, int64_t cap);
+int pa_shard_destroy(pa_shard* shard);
+
 /* ---- testing hook: the bounded wait of the resampling (§II, +-1 couplings) ----
  * The single-pass resampling finds each tile's offset by waiting, with a bounded
  * number of polls, for the entries its predecessor tiles publish.  This sets, for

@@ -87,6 +87,13 @@ struct RunGeom {
   int32_t n_fsizes;          // bound on the distinct family sizes of a population: floor(sqrt(2 R_cap)) + 2
   int32_t sweep_shape;       // index of the sweep kernel's launch shape among those of L
   int32_t model;             // 0: +-1 couplings, 1: Gaussian couplings (fixed point)
+  // One rank's share of a sharded population (pa_shard): global slot of local slot
+  // 0 (a multiple of 1024; random words are addressed by global slot), the local
+  // initial population, and whether the sweep leaves the family statistics to the
+  // sharded step (families may straddle ranks).  0, R, 0 for a whole population.
+  int32_t slot_base;
+  int32_t n_init;
+  int32_t shard;
   int32_t n_chunks;          // Gaussian: chunks of 256 slots of the weight sums
   int32_t n_measure_blocks;  // Gaussian: blocks of the energy-moment reduction
 };
@@ -178,6 +185,10 @@ void use_chosen_shape(pa_ctx* c);
 // many others (pa_batch, pa_server), whose next synchronisation reports any error
 // of the initialisation.
 int create_run(const pa_config* cfg, void* cuda_stream, pa_ctx** out, bool synchronize);
+// The same for one rank's share of a sharded run: the global slots
+// [slot_base, slot_base + n_init) of the initial population (slot_base a multiple
+// of 1024), family statistics left to the sharded step.
+int create_run_share(const pa_config* cfg, void* cuda_stream, pa_ctx** out, int64_t slot_base, int64_t n_init);
 #endif
 // Largest lattice size the sweep kernel supports.
 constexpr int kMaxL = 16;
@@ -189,5 +200,17 @@ bool lattice_supported(int L);      // every lattice a run accepts (even L <= kM
 // S half-sweep launches in place, energy levels.
 int launch_sweep_global(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, int t, int n_sweeps,
                         const uint32_t met_thr[3], void* stream);
+// Sharded runs: the copies of population pop's resampling written out as replicas,
+// new[n][j] = old[n][parents[j]] for j < rec[t].R_tilde (pa_sweep_global.cu).
+int launch_copy_parents(const RunGeom& g, PopDev* pops, int pop, int cur, int t, void* stream);
+// Family runs of one rank's slots (labels[cur][0, rec[t].R_tilde)): the first and
+// the last run (they may continue on other ranks) into edge = {has slots, first
+// label, first length, last label, last length, runs, sum of eta^2 and number of
+// the other runs}, the other runs also into mhist (which starts at zero).
+int launch_shard_families(const RunGeom& g, PopDev* pops, int pop, int cur, int t, long long* edge, void* stream);
+// The sum over the sizes eta[k] (m[k] families each, k < K) of m nu ln nu,
+// nu = eta / R_new, exactly as the step's family statistics add it, into
+// out = {hi, lo} (pa_family.cuh).
+int launch_entropy_of_sizes(const int32_t* eta, const int32_t* m, int K, int R_new, long long* out, void* stream);
 
 }  // namespace pa

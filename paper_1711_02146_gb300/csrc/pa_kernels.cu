@@ -46,7 +46,8 @@ __global__ void k_init_couplings(int N, uint32_t k0, uint32_t k1, int8_t* J, uin
 }
 
 // Initial spins: slot j at site n is +1 if bit 0 of word (j & 3) of Philox at
-// counter (n, 0, j >> 2, 0) is 0, else -1.  Slots >= R are padded with +1.
+// counter (n, 0, j >> 2, 0) is 0, else -1, j the global slot (slot_base + local
+// slot); slots past the initial population are padded with +1.
 __global__ void k_init_population(RunGeom g, PopArgs a, int cur) {
   const int pop = blockIdx.y;
   const PopDev& P = a.p[pop];
@@ -55,12 +56,13 @@ __global__ void k_init_population(RunGeom g, PopArgs a, int cur) {
   if (gid >= words * g.N) return;
   const int n = (int)(gid / words);
   const uint32_t wi = (uint32_t)(gid % words);
-  const uint4 r = philox4x32_10(make_uint4((uint32_t)n, 0u, wi, 0u), P.key_init[0], P.key_init[1]);
+  const uint32_t gw = (uint32_t)(g.slot_base / 4) + wi;  // global word (slot_base is a multiple of 4)
+  const uint4 r = philox4x32_10(make_uint4((uint32_t)n, 0u, gw, 0u), P.key_init[0], P.key_init[1]);
   uint32_t out = 0;
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
     const int64_t j = 4 * (int64_t)wi + b;
-    const uint32_t byte = (j < g.R && (word_of(r, b) & 1u)) ? 0xFFu : 0x01u;
+    const uint32_t byte = (j < g.n_init && (word_of(r, b) & 1u)) ? 0xFFu : 0x01u;
     out |= byte << (8 * b);
   }
   reinterpret_cast<uint32_t*>(P.spins[cur] + (size_t)n * g.pitch)[wi] = out;
@@ -68,10 +70,10 @@ __global__ void k_init_population(RunGeom g, PopArgs a, int cur) {
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int64_t j = 4 * (int64_t)wi + b;
-      if (j < g.R) P.labels[cur][j] = (int32_t)j;
+      if (j < g.n_init) P.labels[cur][j] = (int32_t)(g.slot_base + j);
     }
   }
-  if (n == 0 && wi == 0) P.rec[0].R_tilde = g.R;
+  if (n == 0 && wi == 0) P.rec[0].R_tilde = g.n_init;
 }
 
 // Energy level (unsatisfied bonds) of every slot from scratch, and the level
@@ -311,8 +313,9 @@ __global__ void __launch_bounds__(kCountThreads) k_resample(RunGeom g, PopArgs a
     int local = 0;
 #pragma unroll
     for (int b = 0; b < 4; ++b) n[4 * m + b] = 0;
-    if (j0 < R_old) {
-      const uint4 r = philox4x32_10(make_uint4((uint32_t)(j0 >> 2), 0u, 0u, (uint32_t)t), P.key_res[0], P.key_res[1]);
+    if (j0 < R_old) {  // the uniform of old slot i is addressed by its global slot slot_base + i
+      const uint4 r = philox4x32_10(make_uint4((uint32_t)((g.slot_base + j0) >> 2), 0u, 0u, (uint32_t)t),
+                                    P.key_res[0], P.key_res[1]);
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         const int i = j0 + b;
@@ -461,6 +464,75 @@ __global__ void __launch_bounds__(256) k_fam_runs(RunGeom g, PopArgs a, int cur,
   family_entropy_last(P, &P.rec[t], R_new, (int)gridDim.x, (int)threadIdx.x, (int)blockDim.x, sh);
 }
 
+// Family runs of one rank's slots (sharded runs): the thread at a run's first
+// slot finds its end; the first and the last run of the rank's slots may continue
+// on the neighbouring ranks, so they go to edge for the host to join; every other
+// run is a whole family: eta^2, one family and its size into mhist.
+__global__ void __launch_bounds__(256) k_shard_families(RunGeom g, PopDev P, int cur, int t, long long* edge) {
+  const int n = P.rec[t].R_tilde;
+  const int32_t* lab = P.labels[cur];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  FamilyAcc f;
+  if (j < n) {
+    const int32_t l = lab[j];
+    if (j == 0 || lab[j - 1] != l) {
+      const int end = run_end(lab, l, j + 1, n);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&edge[5]), 1ull);
+      if (j == 0) {
+        edge[0] = 1;
+        edge[1] = l;
+        edge[2] = end;
+      }
+      if (end == n) {
+        edge[3] = l;
+        edge[4] = end - j;
+      }
+      if (j > 0 && end < n) {
+        f.add(end - j);
+        atomicAdd(&P.mhist[end - j], 1);
+      }
+    }
+  }
+  f.s2 = warp_sum(f.s2);
+  f.nf = warp_sum(f.nf);
+  if ((threadIdx.x & 31) == 0 && f.nf) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(&edge[6]), f.s2);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&edge[7]), f.nf);
+  }
+}
+
+// Sum over listed family sizes of m nu ln nu in 128-bit fixed point, one block.
+__global__ void __launch_bounds__(1024) k_entropy_of_sizes(const int32_t* eta, const int32_t* m, int K, int R_new,
+                                                          long long* out) {
+  __shared__ long long sh[64];
+  long long hi = 0;
+  unsigned long long lo = 0;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    long long h;
+    unsigned long long l;
+    entropy_term(m[k], eta[k], R_new, h, l);
+    add128(hi, lo, h, l);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long ho = __shfl_xor_sync(0xffffffffu, hi, o);
+    const unsigned long long lw = __shfl_xor_sync(0xffffffffu, lo, o);
+    add128(hi, lo, ho, lw);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[2 * (threadIdx.x >> 5)] = hi;
+    sh[2 * (threadIdx.x >> 5) + 1] = (long long)lo;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long H = 0;
+    unsigned long long Lo = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) add128(H, Lo, sh[2 * w], (unsigned long long)sh[2 * w + 1]);
+    out[0] = H;
+    out[1] = (long long)Lo;
+  }
+}
+
 // ---------------------------------------------------------------- overlap (a8)
 
 // q between slot j of population 0 and slot j of population 1, j < min(R~0, R~1):
@@ -574,6 +646,19 @@ int launch_families(const RunGeom& g, PopDev* pops, int cur, int t, void* stream
   cudaStream_t s = (cudaStream_t)stream;
   PopArgs a = pack(pops, g.n_pop);
   k_fam_runs<<<dim3(grid_for(g.R_cap, 256), g.n_pop), 256, 0, s>>>(g, a, cur, t, 0);
+  return (int)cudaGetLastError();
+}
+
+int launch_shard_families(const RunGeom& g, PopDev* pops, int pop, int cur, int t, long long* edge, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaMemsetAsync(edge, 0, sizeof(long long) * 8, s);
+  cudaMemsetAsync(pops[pop].mhist, 0, sizeof(int32_t) * ((size_t)g.R_cap + 1), s);
+  k_shard_families<<<grid_for(g.R_cap, 256), 256, 0, s>>>(g, pops[pop], cur, t, edge);
+  return (int)cudaGetLastError();
+}
+
+int launch_entropy_of_sizes(const int32_t* eta, const int32_t* m, int K, int R_new, long long* out, void* stream) {
+  k_entropy_of_sizes<<<1, 1024, 0, (cudaStream_t)stream>>>(eta, m, K, R_new, out);
   return (int)cudaGetLastError();
 }
 

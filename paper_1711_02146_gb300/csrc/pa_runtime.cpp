@@ -425,6 +425,74 @@ int choose_dbeta(pa_ctx* c, double* dbeta) {
 // Adaptive step for Gaussian couplings: the same bisection, with the culling
 // fraction of each trial computed on the device from that trial's weight tables
 // (the definitions the resampling uses), population 0 deciding.
+// Observables of step t of a +-1 population (pa_obs) from its step records and level
+// histograms of steps 0..t (rec, hall: (t + 1) x n_levels) and, with two
+// populations, population 0's record of step t (r0, else null): Eqs. (Q), (betaF),
+// (g0), the family statistics and the overlap counts.
+void pm1_observables(const RunGeom& g, const std::vector<double>& betas, const StepRec* rec, const uint32_t* hall,
+                     int t, const StepRec* r0, pa_obs* out) {
+  const uint32_t* h = hall + (size_t)t * g.n_levels;
+  const int N = g.N;
+  // free energy, Eq. (betaF), and the lowest energy over steps 0..t
+  double lnQ_sum = 0.0, lnQ = 0.0;
+  int32_t E0 = 3 * N + 1;
+  for (int u = 0; u <= t; ++u) {
+    if (u > 0) {
+      const StepRec& r = rec[(size_t)u];
+      const double db = betas[(size_t)u] - betas[(size_t)u - 1];
+      const int32_t Emin_prev = 2 * r.kmin_prev - 3 * N;
+      lnQ = std::log(r.S_prime / (double)r.R_prev) - db * (double)Emin_prev;
+      lnQ_sum = lnQ_sum + lnQ;
+    }
+    const uint32_t* hu = hall + (size_t)u * g.n_levels;
+    for (int k = 0; k < g.n_levels; ++k)
+      if (hu[k] > 0) {
+        E0 = std::min(E0, 2 * k - 3 * N);
+        break;
+      }
+  }
+  pa_obs o{};
+  const StepRec& r = rec[(size_t)t];
+  o.t = t;
+  o.beta = betas[(size_t)t];
+  o.dbeta = t > 0 ? betas[(size_t)t] - betas[(size_t)t - 1] : 0.0;
+  o.R_tilde = r.R_tilde;
+  int64_t sE = 0, sE2 = 0;
+  int32_t Emin = 3 * N + 1;
+  for (int k = 0; k < g.n_levels; ++k) {
+    if (!h[k]) continue;
+    const int64_t E = 2 * k - 3 * N;
+    sE += (int64_t)h[k] * E;
+    sE2 += (int64_t)h[k] * E * E;
+    Emin = std::min<int32_t>(Emin, (int32_t)E);
+  }
+  o.sum_E = sE;
+  o.sum_E2 = sE2;
+  o.E_min = Emin;
+  o.mean_E = (double)sE / (double)o.R_tilde;
+  o.var_E = (double)sE2 / (double)o.R_tilde - o.mean_E * o.mean_E;
+  o.kmin_prev = t > 0 ? r.kmin_prev : 0;
+  o.S_prime = t > 0 ? r.S_prime : 0.0;
+  o.lnQ = t > 0 ? lnQ : 0.0;
+  o.minus_beta_F = (double)N * std::log(2.0) + lnQ_sum;
+  o.eps_expected = t > 0 ? r.eps_expected : 0.0;
+  o.culled = t > 0 ? r.culled : 0;
+  o.sum_eta2 = (int64_t)r.sum_eta2;
+  o.n_families = (int64_t)r.n_families;
+  o.rho_t = (double)o.sum_eta2 / (double)o.R_tilde;
+  o.S_f = -nu_ln_nu(r);
+  o.rho_s = (double)o.R_tilde / std::exp(o.S_f);
+  o.E0 = E0;
+  o.g0_tilde = (double)h[(E0 + 3 * N) / 2] / (double)o.R_tilde;
+  o.g0_bar = 2.0 * std::exp(-(o.beta * (double)E0) - o.minus_beta_F);
+  if (r0) {
+    o.q_pairs = (int64_t)r0->q_pairs;
+    o.q_abs_le_02 = (int64_t)r0->q_small;
+    o.I02 = o.q_pairs > 0 ? (double)o.q_abs_le_02 / (double)o.q_pairs : 0.0;
+  }
+  *out = o;
+}
+
 int launch_rc(int e) { return e == 0 ? PA_OK : PA_ERR_CUDA; }
 
 // Adaptive step with Gaussian couplings (§IV.B), as for +-1 couplings: the largest
@@ -597,6 +665,9 @@ void init_run(pa_ctx* c, const pa_config* cfg, int64_t R_cap) {
   g.n_fsizes = (int32_t)k + 2;
   g.sweep_shape = 0;
   g.model = cfg->model;
+  g.slot_base = 0;
+  g.n_init = (int32_t)cfg->R;
+  g.shard = 0;
   g.n_chunks = (int32_t)((R_cap + pa::kChunk - 1) / pa::kChunk);
   g.n_measure_blocks = (int32_t)((R_cap + 4095) / 4096);
   c->model = cfg->model;
@@ -811,7 +882,28 @@ int pa_footprint(const pa_config* cfg, size_t* bytes) {
 
 }  // extern "C"
 
+namespace {
+struct SharePlacement {
+  bool share = false;
+  int64_t slot_base = 0, n_init = 0;
+};
+int create_run_impl(const pa_config* cfg, void* cuda_stream, pa_ctx** out, bool synchronize, const SharePlacement& sp);
+}  // namespace
+
 int pa::create_run(const pa_config* cfg, void* cuda_stream, pa_ctx** out, bool synchronize) {
+  return create_run_impl(cfg, cuda_stream, out, synchronize, SharePlacement{});
+}
+
+int pa::create_run_share(const pa_config* cfg, void* cuda_stream, pa_ctx** out, int64_t slot_base, int64_t n_init) {
+  SharePlacement sp;
+  sp.share = true;
+  sp.slot_base = slot_base;
+  sp.n_init = n_init;
+  return create_run_impl(cfg, cuda_stream, out, true, sp);
+}
+
+namespace {
+int create_run_impl(const pa_config* cfg, void* cuda_stream, pa_ctx** out, bool synchronize, const SharePlacement& sp) {
   if (!out) return PA_ERR_INVALID;
   *out = nullptr;
   if (!cfg) return PA_ERR_INVALID;
@@ -833,11 +925,18 @@ int pa::create_run(const pa_config* cfg, void* cuda_stream, pa_ctx** out, bool s
     for (int t = 0; t < cfg->n_temps; ++t)
       if (cfg->sweeps_per_step[t] < 0) return PA_ERR_INVALID;
 
+  if (sp.share && (sp.slot_base < 0 || sp.slot_base % 1024 != 0 || sp.n_init < 0 || sp.slot_base + sp.n_init > cfg->R))
+    return PA_ERR_INVALID;
   pa_ctx* c = new (std::nothrow) pa_ctx();
   if (!c) return PA_ERR_NOMEM;
   init_run(c, cfg, R_cap);
   c->stream = (cudaStream_t)cuda_stream;
   RunGeom& g = c->g;
+  if (sp.share) {
+    g.slot_base = (int32_t)sp.slot_base;
+    g.n_init = (int32_t)sp.n_init;
+    g.shard = 1;
+  }
   int dev = 0;
   if (pa::sweep_supported(g.L) && current_device(&dev) == PA_OK) g.sweep_shape = run_shape(g.L, R_cap, dev);
   for (int p = 0; p < g.n_pop; ++p) {
@@ -929,6 +1028,7 @@ int pa::create_run(const pa_config* cfg, void* cuda_stream, pa_ctx** out, bool s
   *out = c;
   return PA_OK;
 }
+}  // namespace
 
 extern "C" {
 
@@ -1089,70 +1189,10 @@ int pa_observables(pa_ctx* c, int32_t t, int32_t pop, pa_obs* out) {
   std::vector<uint32_t> hall((size_t)(t + 1) * g.n_levels);
   rc = copy_d2h(c, rec.data(), c->pops[pop].rec, sizeof(StepRec) * rec.size());
   if (rc == PA_OK) rc = copy_d2h(c, hall.data(), c->pops[pop].hist, sizeof(uint32_t) * hall.size());
+  StepRec r0{};
+  if (rc == PA_OK && g.n_pop == 2) rc = copy_d2h(c, &r0, c->pops[0].rec + t, sizeof r0);
   if (rc != PA_OK) return fail(c, rc);
-  const uint32_t* h = hall.data() + (size_t)t * g.n_levels;
-  const int N = g.N;
-  // free energy, Eq. (betaF), and the lowest energy over steps 0..t
-  double lnQ_sum = 0.0, lnQ = 0.0;
-  int32_t E0 = 3 * N + 1;
-  for (int u = 0; u <= t; ++u) {
-    if (u > 0) {
-      const StepRec& r = rec[(size_t)u];
-      const double db = c->betas[(size_t)u] - c->betas[(size_t)u - 1];
-      const int32_t Emin_prev = 2 * r.kmin_prev - 3 * N;
-      lnQ = std::log(r.S_prime / (double)r.R_prev) - db * (double)Emin_prev;
-      lnQ_sum = lnQ_sum + lnQ;
-    }
-    const uint32_t* hu = hall.data() + (size_t)u * g.n_levels;
-    for (int k = 0; k < g.n_levels; ++k)
-      if (hu[k] > 0) {
-        E0 = std::min(E0, 2 * k - 3 * N);
-        break;
-      }
-  }
-  pa_obs o{};
-  const StepRec& r = rec[(size_t)t];
-  o.t = t;
-  o.beta = c->betas[(size_t)t];
-  o.dbeta = t > 0 ? c->betas[(size_t)t] - c->betas[(size_t)t - 1] : 0.0;
-  o.R_tilde = r.R_tilde;
-  int64_t sE = 0, sE2 = 0;
-  int32_t Emin = 3 * N + 1;
-  for (int k = 0; k < g.n_levels; ++k) {
-    if (!h[k]) continue;
-    const int64_t E = 2 * k - 3 * N;
-    sE += (int64_t)h[k] * E;
-    sE2 += (int64_t)h[k] * E * E;
-    Emin = std::min<int32_t>(Emin, (int32_t)E);
-  }
-  o.sum_E = sE;
-  o.sum_E2 = sE2;
-  o.E_min = Emin;
-  o.mean_E = (double)sE / (double)o.R_tilde;
-  o.var_E = (double)sE2 / (double)o.R_tilde - o.mean_E * o.mean_E;
-  o.kmin_prev = t > 0 ? r.kmin_prev : 0;
-  o.S_prime = t > 0 ? r.S_prime : 0.0;
-  o.lnQ = t > 0 ? lnQ : 0.0;
-  o.minus_beta_F = (double)N * std::log(2.0) + lnQ_sum;
-  o.eps_expected = t > 0 ? r.eps_expected : 0.0;
-  o.culled = t > 0 ? r.culled : 0;
-  o.sum_eta2 = (int64_t)r.sum_eta2;
-  o.n_families = (int64_t)r.n_families;
-  o.rho_t = (double)o.sum_eta2 / (double)o.R_tilde;
-  o.S_f = -nu_ln_nu(r);
-  o.rho_s = (double)o.R_tilde / std::exp(o.S_f);
-  o.E0 = E0;
-  o.g0_tilde = (double)h[(E0 + 3 * N) / 2] / (double)o.R_tilde;
-  o.g0_bar = 2.0 * std::exp(-(o.beta * (double)E0) - o.minus_beta_F);
-  if (g.n_pop == 2) {
-    StepRec r0;
-    rc = copy_d2h(c, &r0, c->pops[0].rec + t, sizeof r0);
-    if (rc != PA_OK) return fail(c, rc);
-    o.q_pairs = (int64_t)r0.q_pairs;
-    o.q_abs_le_02 = (int64_t)r0.q_small;
-    o.I02 = o.q_pairs > 0 ? (double)o.q_abs_le_02 / (double)o.q_pairs : 0.0;
-  }
-  *out = o;
+  pm1_observables(g, c->betas, rec.data(), hall.data(), t, g.n_pop == 2 ? &r0 : nullptr, out);
   return PA_OK;
 }
 
@@ -1668,6 +1708,439 @@ int pa_sweep_autotune(int32_t L, int32_t R, int32_t launches, double* ms_per_lau
   g_sweep_choice[dev][L].store(best_i);
   g_sweep_pinned[dev][L].store(false);
   *best = best_i;
+  return PA_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- sharded runs
+//
+// One rank's share of a population split across ranks (pa.h, pa_shard_*): the
+// rank's slots live in an ordinary run (pa_ctx) whose global slot base makes every
+// random word the one-process run's; the exchanges between the phases of a step go
+// through the caller's host functions (pa_comm).
+
+struct pa_shard {
+  pa_ctx* c = nullptr;
+  pa_comm comm{};
+  int32_t rank = 0, n_ranks = 1;
+  int64_t lo = 0, hi = 0;                          // this rank's global slots [lo, hi)
+  int64_t R_glob[2] = {0, 0};                      // global population sizes of the current step
+  std::vector<StepRec> rec[2];                     // global step records of steps 0..t
+  std::vector<uint32_t> hist[2];                   // global level histograms, (t + 1) x n_levels
+  std::vector<std::vector<int64_t>> qhist;         // global overlap histograms
+  long long* dscratch = nullptr;                   // device: family edges (8), entropy sum (2)
+  int32_t* dsizes = nullptr;                       // device: family sizes and their counts
+};
+
+namespace {
+
+// Rank q's global slots [lo, hi) of a population cut from R slots: whole units of
+// 1024 slots (tiles and Philox word groups stay aligned with the global ones).
+void shard_block(int64_t R, int P, int q, int64_t* lo, int64_t* hi) {
+  const int64_t units = (R + 1023) / 1024;
+  *lo = std::min<int64_t>(R, 1024 * ((units * q) / P));
+  *hi = std::min<int64_t>(R, 1024 * ((units * (q + 1)) / P));
+}
+
+int comm_rc(int e) { return e == 0 ? PA_OK : PA_ERR_CUDA; }
+
+// The device status of one rank's run after its resampling: a rank may hold no
+// old slots, or receive no copies, while the population lives on other ranks, so
+// the extinction flag is cleared here (the step checks the global size instead).
+int shard_status(pa_ctx* c) {
+  int32_t flags = 0;
+  int rc = cuda_status(cudaStreamSynchronize(c->stream));
+  if (rc == PA_OK) rc = copy_d2h(c, &flags, c->status, sizeof flags);
+  if (rc == PA_OK && (flags & pa::kFlagExtinct)) {
+    const int32_t kept = flags & ~pa::kFlagExtinct;
+    rc = copy_h2d(c, c->status, &kept, sizeof kept);
+  }
+  if (rc != PA_OK) return rc;
+  if (flags & pa::kFlagCapacity) return PA_ERR_CAPACITY;
+  if (flags & pa::kFlagTimeout) return PA_ERR_TIMEOUT;
+  return PA_OK;
+}
+
+// Families of population p at step t over all ranks, and the global family
+// statistics in r: local runs, the ranks' first and last runs joined in rank order
+// (a family may span ranks), the global size histogram, and the entropy sum by the
+// device code of the one-process run.
+int shard_families(pa_shard* s, int p, int t, StepRec& r) {
+  pa_ctx* c = s->c;
+  const RunGeom& g = c->g;
+  const int P = s->n_ranks;
+  int rc = launch_rc(pa::launch_shard_families(g, c->pops, p, c->cur, t, s->dscratch, c->stream));
+  long long edge[8];
+  std::vector<int32_t> mh((size_t)g.R_cap + 1);
+  if (rc == PA_OK) rc = copy_d2h(c, edge, s->dscratch, sizeof edge);
+  if (rc == PA_OK) rc = copy_d2h(c, mh.data(), c->pops[p].mhist, sizeof(int32_t) * mh.size());
+  if (rc != PA_OK) return rc;
+  std::vector<int64_t> mine(edge, edge + 8), all((size_t)P * 8);
+  rc = comm_rc(s->comm.allgather_i64(s->comm.user, mine.data(), 8, all.data()));
+  std::vector<int64_t> m(mh.begin(), mh.end());
+  if (rc == PA_OK) rc = comm_rc(s->comm.allreduce_i64(s->comm.user, m.data(), (int64_t)m.size()));
+  if (rc != PA_OK) return rc;
+  // join the edge runs in rank order
+  std::vector<int64_t> joined;
+  bool open = false;
+  int64_t open_lab = 0, open_len = 0, s2 = 0, nf = 0;
+  for (int q = 0; q < P; ++q) {
+    const int64_t* e = &all[(size_t)q * 8];
+    s2 += e[6];
+    nf += e[7];
+    if (!e[0]) continue;
+    const int64_t f = e[1], lf = e[2], l = e[3], ll = e[4], runs = e[5];
+    if (runs == 1) {  // the rank's slots are one run
+      if (open && f == open_lab) {
+        open_len += lf;
+      } else {
+        if (open) joined.push_back(open_len);
+        open = true;
+        open_lab = f;
+        open_len = lf;
+      }
+      continue;
+    }
+    if (open && f == open_lab) {
+      joined.push_back(open_len + lf);
+    } else {
+      if (open) joined.push_back(open_len);
+      joined.push_back(lf);
+    }
+    open = true;
+    open_lab = l;
+    open_len = ll;
+  }
+  if (open) joined.push_back(open_len);
+  for (int64_t eta : joined) {
+    if (eta < 1 || eta >= (int64_t)m.size()) return PA_ERR_INVALID;
+    m[(size_t)eta] += 1;
+    s2 += eta * eta;
+    nf += 1;
+  }
+  std::vector<int32_t> eta_k, m_k;
+  for (size_t e = 1; e < m.size(); ++e)
+    if (m[e] > 0) {
+      eta_k.push_back((int32_t)e);
+      m_k.push_back((int32_t)m[e]);
+    }
+  const int K = (int)eta_k.size();
+  if (K > 0) {
+    rc = copy_h2d(c, s->dsizes, eta_k.data(), sizeof(int32_t) * (size_t)K);
+    if (rc == PA_OK) rc = copy_h2d(c, s->dsizes + g.R_cap + 1, m_k.data(), sizeof(int32_t) * (size_t)K);
+    if (rc == PA_OK)
+      rc = launch_rc(pa::launch_entropy_of_sizes(s->dsizes, s->dsizes + g.R_cap + 1, K, (int)r.R_tilde,
+                                                 s->dscratch + 8, c->stream));
+    long long nll[2] = {0, 0};
+    if (rc == PA_OK) rc = copy_d2h(c, nll, s->dscratch + 8, sizeof nll);
+    if (rc != PA_OK) return rc;
+    r.nll_hi = nll[0];
+    r.nll_lo = (unsigned long long)nll[1];
+  }
+  r.sum_eta2 = (unsigned long long)s2;
+  r.n_families = (unsigned long long)nf;
+  return PA_OK;
+}
+
+// The measurements of step t over all ranks: level histograms, families, overlap.
+int shard_measure(pa_shard* s, int t) {
+  pa_ctx* c = s->c;
+  const RunGeom& g = c->g;
+  int rc = PA_OK;
+  for (int p = 0; p < g.n_pop && rc == PA_OK; ++p) {
+    std::vector<uint32_t> h((size_t)g.n_levels);
+    uint32_t* dh = c->pops[p].hist + (size_t)t * g.n_levels;
+    rc = copy_d2h(c, h.data(), dh, sizeof(uint32_t) * h.size());
+    std::vector<int64_t> v(h.begin(), h.end());
+    if (rc == PA_OK) rc = comm_rc(s->comm.allreduce_i64(s->comm.user, v.data(), (int64_t)v.size()));
+    if (rc != PA_OK) break;
+    for (size_t k = 0; k < h.size(); ++k) h[k] = (uint32_t)v[k];
+    rc = copy_h2d(c, dh, h.data(), sizeof(uint32_t) * h.size());  // the next step's tables need the global one
+    s->hist[p].insert(s->hist[p].end(), h.begin(), h.end());
+    StepRec& r = s->rec[p][(size_t)t];
+    r.R_tilde = (int32_t)s->R_glob[p];
+    if (rc == PA_OK) rc = shard_families(s, p, t, r);
+  }
+  if (rc == PA_OK && g.n_pop == 2) {
+    // the overlap kernel adds to its outputs (a share's creation has measured step 0 once already)
+    rc = cuda_status(cudaMemsetAsync(c->qhist + (size_t)t * g.q_bins, 0, sizeof(unsigned long long) * g.q_bins,
+                                     c->stream));
+    if (rc == PA_OK)
+      rc = cuda_status(cudaMemsetAsync(&c->pops[0].rec[t].q_small, 0, sizeof(unsigned long long), c->stream));
+    if (rc == PA_OK) rc = launch_rc(pa::launch_overlap(g, c->pops, c->cur, t, c->qhist, c->stream));
+    std::vector<unsigned long long> q((size_t)g.q_bins);
+    StepRec r0{};
+    if (rc == PA_OK) rc = copy_d2h(c, q.data(), c->qhist + (size_t)t * g.q_bins, sizeof(unsigned long long) * q.size());
+    if (rc == PA_OK) rc = copy_d2h(c, &r0, c->pops[0].rec + t, sizeof r0);
+    std::vector<int64_t> v(q.begin(), q.end());
+    v.push_back((int64_t)r0.q_small);
+    if (rc == PA_OK) rc = comm_rc(s->comm.allreduce_i64(s->comm.user, v.data(), (int64_t)v.size()));
+    if (rc == PA_OK) {
+      s->rec[0][(size_t)t].q_small = (unsigned long long)v.back();
+      s->rec[0][(size_t)t].q_pairs = (unsigned long long)std::min(s->R_glob[0], s->R_glob[1]);
+      v.pop_back();
+      s->qhist.push_back(v);
+    }
+  }
+  return rc;
+}
+
+// Moves every copy of population p to the rank that holds its new slot: rank r's
+// copies are the global new slots [off[r], off[r] + tot[r]), already written out in
+// order at local slots [0, tot[r]) of the other buffer; rank q receives those in
+// [LO_q, HI_q).  Pairs of ranks exchange in rank order (the lower rank sends
+// first), each message a count, the copies' spins (N rows) and their labels.  The
+// new local population goes to the current buffer (spins) and the other (labels).
+int shard_exchange(pa_shard* s, int p, const std::vector<int64_t>& off, const std::vector<int64_t>& tot,
+                   int64_t R_new, int64_t R_part, int64_t* n_local) {
+  pa_ctx* c = s->c;
+  const RunGeom& g = c->g;
+  const PopDev& P = c->pops[p];
+  const int r = s->rank, Pn = s->n_ranks;
+  int64_t LO, HI;
+  shard_block(R_part, Pn, r, &LO, &HI);
+  HI = std::min(HI, R_new);
+  const int64_t n_new = std::max<int64_t>(0, HI - std::max<int64_t>(LO, 0));
+  const int64_t N = g.N;
+  std::vector<int8_t> rs((size_t)(N * std::max<int64_t>(n_new, 1)));
+  std::vector<int32_t> rl((size_t)std::max<int64_t>(n_new, 1));
+  auto range_to = [&](int q, int64_t* a, int64_t* b) {  // my local copies that rank q holds
+    int64_t lq, hq;
+    shard_block(R_part, Pn, q, &lq, &hq);
+    hq = std::min(hq, R_new);
+    const int64_t ga = std::max(off[(size_t)r], lq), gb = std::min(off[(size_t)r] + tot[(size_t)r], hq);
+    *a = ga - off[(size_t)r];
+    *b = std::max(*a, gb - off[(size_t)r]);
+  };
+  auto pack = [&](int64_t a, int64_t b, std::vector<int8_t>& sp, std::vector<int32_t>& lb) {
+    const int64_t n = b - a;
+    sp.assign((size_t)(N * std::max<int64_t>(n, 1)), 0);
+    lb.assign((size_t)std::max<int64_t>(n, 1), 0);
+    if (n == 0) return PA_OK;
+    int rc = cuda_status(cudaMemcpy2DAsync(sp.data(), (size_t)n, P.spins[1 - c->cur] + a, (size_t)g.pitch, (size_t)n,
+                                           (size_t)N, cudaMemcpyDeviceToHost, c->stream));
+    if (rc == PA_OK) rc = cuda_status(cudaStreamSynchronize(c->stream));
+    if (rc == PA_OK) rc = copy_d2h(c, lb.data(), P.labels[1 - c->cur] + a, sizeof(int32_t) * (size_t)n);
+    return rc;
+  };
+  auto place = [&](int q, int64_t n, const int8_t* sp, const int32_t* lb) {  // copies from rank q
+    const int64_t at = std::max(off[(size_t)q], LO) - LO;
+    if (n == 0) return PA_OK;
+    if (at < 0 || at + n > n_new) return PA_ERR_INVALID;
+    for (int64_t site = 0; site < N; ++site)
+      std::memcpy(&rs[(size_t)(site * n_new + at)], sp + site * n, (size_t)n);
+    std::memcpy(&rl[(size_t)at], lb, sizeof(int32_t) * (size_t)n);
+    return PA_OK;
+  };
+  int rc = PA_OK;
+  std::vector<int8_t> sp;
+  std::vector<int32_t> lb;
+  for (int q = 0; q < Pn && rc == PA_OK; ++q) {
+    int64_t a, b;
+    range_to(q, &a, &b);
+    if (q == r) {
+      rc = pack(a, b, sp, lb);
+      if (rc == PA_OK) rc = place(q, b - a, sp.data(), lb.data());
+      continue;
+    }
+    auto send_to = [&]() {
+      int e = pack(a, b, sp, lb);
+      const int64_t n = b - a;
+      if (e == PA_OK) e = comm_rc(s->comm.send(s->comm.user, q, &n, sizeof n));
+      if (e == PA_OK && n > 0) e = comm_rc(s->comm.send(s->comm.user, q, sp.data(), N * n));
+      if (e == PA_OK && n > 0) e = comm_rc(s->comm.send(s->comm.user, q, lb.data(), (int64_t)sizeof(int32_t) * n));
+      return e;
+    };
+    auto recv_from = [&]() {
+      int64_t n = 0;
+      int e = comm_rc(s->comm.recv(s->comm.user, q, &n, sizeof n));
+      if (e != PA_OK) return e;
+      if (n < 0 || n > n_new) return PA_ERR_INVALID;
+      std::vector<int8_t> rsp((size_t)(N * std::max<int64_t>(n, 1)));
+      std::vector<int32_t> rlb((size_t)std::max<int64_t>(n, 1));
+      if (n > 0) e = comm_rc(s->comm.recv(s->comm.user, q, rsp.data(), N * n));
+      if (e == PA_OK && n > 0) e = comm_rc(s->comm.recv(s->comm.user, q, rlb.data(), (int64_t)sizeof(int32_t) * n));
+      if (e == PA_OK) e = place(q, n, rsp.data(), rlb.data());
+      return e;
+    };
+    if (r < q) {
+      rc = send_to();
+      if (rc == PA_OK) rc = recv_from();
+    } else {
+      rc = recv_from();
+      if (rc == PA_OK) rc = send_to();
+    }
+  }
+  if (rc != PA_OK) return rc;
+  if (n_new > 0) {
+    rc = cuda_status(cudaMemcpy2DAsync(P.spins[c->cur], (size_t)g.pitch, rs.data(), (size_t)n_new, (size_t)n_new,
+                                       (size_t)N, cudaMemcpyHostToDevice, c->stream));
+    if (rc == PA_OK) rc = copy_h2d(c, P.labels[1 - c->cur], rl.data(), sizeof(int32_t) * (size_t)n_new);
+    std::vector<int32_t> iota((size_t)n_new);
+    for (int64_t j = 0; j < n_new; ++j) iota[(size_t)j] = (int32_t)j;
+    if (rc == PA_OK) rc = copy_h2d(c, P.parents, iota.data(), sizeof(int32_t) * (size_t)n_new);
+  }
+  *n_local = n_new;
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pa_shard_create(const pa_config* cfg, int32_t rank, int32_t n_ranks, const pa_comm* comm, void* cuda_stream,
+                    pa_shard** out) {
+  if (!out) return PA_ERR_INVALID;
+  *out = nullptr;
+  if (!cfg || !comm || !comm->allreduce_i64 || !comm->allgather_i64 || !comm->send || !comm->recv || n_ranks < 1 ||
+      rank < 0 || rank >= n_ranks || cfg->model != PA_MODEL_PM1 || !cfg->betas || !pa::sweep_supported(cfg->L))
+    return PA_ERR_INVALID;
+  pa_shard* s = new (std::nothrow) pa_shard();
+  if (!s) return PA_ERR_NOMEM;
+  s->comm = *comm;
+  s->rank = rank;
+  s->n_ranks = n_ranks;
+  shard_block(cfg->R, n_ranks, rank, &s->lo, &s->hi);
+  int rc = pa::create_run_share(cfg, cuda_stream, &s->c, s->lo, s->hi - s->lo);
+  const RunGeom* g = s->c ? &s->c->g : nullptr;
+  if (rc == PA_OK && (cudaMalloc(reinterpret_cast<void**>(&s->dscratch), sizeof(long long) * 10) != cudaSuccess ||
+                      cudaMalloc(reinterpret_cast<void**>(&s->dsizes), sizeof(int32_t) * 2 * ((size_t)g->R_cap + 1)) !=
+                          cudaSuccess)) {
+    cudaGetLastError();
+    rc = PA_ERR_NOMEM;
+  }
+  if (rc == PA_OK) {
+    for (int p = 0; p < cfg->n_pop; ++p) {
+      s->R_glob[p] = cfg->R;
+      s->rec[p].assign((size_t)cfg->n_temps, StepRec{});
+    }
+    rc = shard_measure(s, 0);
+  }
+  if (rc != PA_OK) {
+    pa_shard_destroy(s);
+    return rc;
+  }
+  *out = s;
+  return PA_OK;
+}
+
+int pa_shard_step(pa_shard* s) {
+  if (!s) return PA_ERR_INVALID;
+  pa_ctx* c = s->c;
+  if (c->error != PA_OK) return c->error;
+  if (c->done) return PA_DONE;
+  RunGeom& g = c->g;
+  const int t = c->t + 1, np = g.n_pop, Pn = s->n_ranks;
+  const double dbeta = c->betas[(size_t)t] - c->betas[(size_t)t - 1];
+  cudaStream_t st = c->stream;
+  int rc = PA_OK;
+  for (int p = 0; p < np && rc == PA_OK; ++p) rc = cuda_status(cudaMemsetAsync(c->pops[p].rec + t, 0, sizeof(StepRec), st));
+  // 1-2. tables from the global histogram of step t-1; copy numbers of the local old
+  // slots (their uniforms addressed by global slot) and the copies in local order
+  const double* w = nullptr;
+  if (rc == PA_OK) rc = weight_table(c, dbeta, &w);
+  g.slot_base = (int32_t)s->lo;
+  if (rc == PA_OK) rc = launch_rc(pa::launch_reweight(g, c->pops, w, t, st));
+  if (rc == PA_OK) rc = launch_rc(pa::launch_resample(g, c->pops, c->cur, t, c->status, c->lookback, st));
+  for (int p = 0; p < np && rc == PA_OK; ++p) rc = launch_rc(pa::launch_copy_parents(g, c->pops, p, c->cur, t, st));
+  if (rc == PA_OK) rc = shard_status(c);
+  StepRec loc[2];
+  for (int p = 0; p < np && rc == PA_OK; ++p) rc = copy_d2h(c, &loc[p], c->pops[p].rec + t, sizeof(StepRec));
+  if (rc != PA_OK) return fail(c, rc);
+  // 3. global offsets: the ranks' copy totals in rank order
+  std::vector<int64_t> mine((size_t)2 * np), all((size_t)2 * np * Pn);
+  for (int p = 0; p < np; ++p) {
+    mine[(size_t)2 * p] = loc[p].R_tilde;
+    mine[(size_t)2 * p + 1] = loc[p].culled;
+  }
+  rc = comm_rc(s->comm.allgather_i64(s->comm.user, mine.data(), 2 * np, all.data()));
+  if (rc != PA_OK) return fail(c, rc);
+  std::vector<int64_t> off[2], tot[2];
+  int64_t R_new[2] = {0, 0}, culled[2] = {0, 0}, R_part = 0;
+  for (int p = 0; p < np; ++p) {
+    for (int q = 0; q < Pn; ++q) {
+      off[p].push_back(R_new[p]);
+      tot[p].push_back(all[(size_t)(q * 2 * np + 2 * p)]);
+      R_new[p] += tot[p].back();
+      culled[p] += all[(size_t)(q * 2 * np + 2 * p + 1)];
+    }
+    if (R_new[p] > g.R_cap) return fail(c, PA_ERR_CAPACITY);
+    if (R_new[p] == 0) return fail(c, PA_ERR_EXTINCT);
+    R_part = std::max(R_part, R_new[p]);
+  }
+  // 4. every copy to the rank that holds its new slot
+  int64_t n_local[2] = {0, 0};
+  for (int p = 0; p < np && rc == PA_OK; ++p) rc = shard_exchange(s, p, off[p], tot[p], R_new[p], R_part, &n_local[p]);
+  for (int p = 0; p < np && rc == PA_OK; ++p) {
+    const int32_t n = (int32_t)n_local[p];
+    rc = copy_h2d(c, &c->pops[p].rec[t].R_tilde, &n, sizeof n);
+  }
+  if (rc != PA_OK) return fail(c, rc);
+  int64_t hi;
+  shard_block(R_part, Pn, s->rank, &s->lo, &hi);
+  // 5. sweeps of the local slots (Metropolis words addressed by global slot)
+  g.slot_base = (int32_t)s->lo;
+  uint32_t met[3];
+  metropolis_thresholds(c->betas[(size_t)t], met);
+  rc = launch_rc(pa::launch_sweep(g, c->pops, c->cur, c->jtab, t, c->sweeps[(size_t)t], met, st));
+  if (rc != PA_OK) return fail(c, rc);
+  c->cur = 1 - c->cur;
+  // 6. global records and measurements
+  for (int p = 0; p < np; ++p) {
+    StepRec& r = s->rec[p][(size_t)t];
+    r = StepRec{};
+    r.R_prev = (int32_t)s->R_glob[p];
+    r.kmin_prev = loc[p].kmin_prev;
+    r.culled = (int32_t)culled[p];
+    r.S_prime = loc[p].S_prime;
+    r.eps_expected = loc[p].eps_expected;
+    r.S_t = c->sweeps[(size_t)t];
+    s->R_glob[p] = R_new[p];
+  }
+  rc = shard_measure(s, t);
+  if (rc != PA_OK) return fail(c, rc);
+  c->t = t;
+  c->stats.steps += 1;
+  if (t == c->cfg.n_temps - 1) c->done = true;
+  return PA_OK;
+}
+
+int pa_shard_observables(pa_shard* s, int32_t t, int32_t pop, pa_obs* out) {
+  if (!s || !out || t < 0 || pop < 0 || pop >= s->c->g.n_pop) return PA_ERR_INVALID;
+  if (t > s->c->t) return PA_ERR_STATE;
+  const StepRec* r0 = s->c->g.n_pop == 2 ? &s->rec[0][(size_t)t] : nullptr;
+  pm1_observables(s->c->g, s->c->betas, s->rec[pop].data(), s->hist[pop].data(), t, r0, out);
+  return PA_OK;
+}
+
+int pa_shard_local(pa_shard* s, pa_ctx** local) {
+  if (!s || !local) return PA_ERR_INVALID;
+  *local = s->c;
+  return PA_OK;
+}
+
+int pa_shard_extent(pa_shard* s, int32_t pop, int64_t* lo, int64_t* R_tilde) {
+  if (!s || pop < 0 || pop >= s->c->g.n_pop) return PA_ERR_INVALID;
+  if (lo) *lo = s->lo;
+  if (R_tilde) *R_tilde = s->R_glob[pop];
+  return PA_OK;
+}
+
+int pa_shard_q_hist(pa_shard* s, int32_t t, int64_t* out, int64_t cap) {
+  if (!s || !out || t < 0 || s->c->g.n_pop != 2) return PA_ERR_INVALID;
+  if (t > s->c->t) return PA_ERR_STATE;
+  if (cap < s->c->g.q_bins) return PA_ERR_CAPACITY;
+  for (int i = 0; i < s->c->g.q_bins; ++i) out[i] = s->qhist[(size_t)t][(size_t)i];
+  return PA_OK;
+}
+
+int pa_shard_destroy(pa_shard* s) {
+  if (!s) return PA_ERR_INVALID;
+  if (s->c) pa_destroy(s->c);
+  if (s->dscratch) cudaFree(s->dscratch);
+  if (s->dsizes) cudaFree(s->dsizes);
+  delete s;
   return PA_OK;
 }
 

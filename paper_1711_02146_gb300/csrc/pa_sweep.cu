@@ -56,6 +56,8 @@ struct SweepArgs {
   int32_t t;
   int32_t cur;
   int32_t n_sweeps;
+  int32_t slot_base;  // global slot of local slot 0 (Philox groups are global); 0 for a whole population
+  int32_t fam;        // 1: add the tile's families to the step record (not for one rank's share)
   uint32_t thr4, thr8, thr12;
   uint32_t k0[10];  // Metropolis round keys of this population
   uint32_t k1[10];
@@ -734,7 +736,8 @@ __global__ void __launch_bounds__(NT, MB) k_sweep(const __grid_constant__ SweepA
 
   // sweeps: partition `part` owns rows of parity class p = (y + z) & 1; in
   // half-sweep c its colour sites sit at x = p ^ c mod 2 in every row.
-  const uint32_t g8 = 8u * ((uint32_t)(tile0 >> 5) + (uint32_t)word);  // Philox group of block 0 of this word
+  const uint32_t gbase = (uint32_t)((a.slot_base + tile0) >> 5);  // global index of the tile's first word
+  const uint32_t g8 = 8u * (gbase + (uint32_t)word);             // Philox group of block 0 of this word
   const int pclass = part / (NP / 2);
   uint32_t* spw = sp + word;
   for (int s = 0; s < a.n_sweeps; ++s) {
@@ -743,7 +746,6 @@ __global__ void __launch_bounds__(NT, MB) k_sweep(const __grid_constant__ SweepA
       const uint32_t q = 2u * (uint32_t)s + (uint32_t)c;
       if constexpr (S::DEFER) {
         const ThreadPhilox tp[2] = {thread_philox(g8, q, a.k0, a.k1), thread_philox(g8 + 1u, q, a.k0, a.k1)};
-        const uint32_t gbase = (uint32_t)(tile0 >> 5);
         if ((pclass ^ c) == 0)  // the same in every lane of the warp
           sweep_rows_bits_dq<L, W, NP, 0>(sp, word, recs, part, pclass, tp, q, gbase, dq, a);
         else
@@ -763,6 +765,7 @@ __global__ void __launch_bounds__(NT, MB) k_sweep(const __grid_constant__ SweepA
   __syncthreads();
   publish_levels<TJ>(a, slots, tile0, R_new, tid, NT);
   store_bits<L, W, NP>(a, sp, tile0, word, part);
+  if (!a.fam) return;
   __syncthreads();  // every shared array is dead now: the family pass takes the space
   tile_families<TJ, NT>(a, reinterpret_cast<int*>(sm), tile0, R_new, tid);
 }
@@ -998,6 +1001,8 @@ int launch_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, 
     args.t = t;
     args.cur = cur;
     args.n_sweeps = n_sweeps;
+    args.slot_base = g.slot_base;
+    args.fam = g.shard ? 0 : 1;
     args.thr4 = met_thr[0];
     args.thr8 = met_thr[1];
     args.thr12 = met_thr[2];
@@ -1042,6 +1047,8 @@ int launch_g_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab
     args.t = t;
     args.cur = cur;
     args.n_sweeps = n_sweeps;
+    args.slot_base = 0;
+    args.fam = 0;
     args.thr4 = args.thr8 = args.thr12 = 0u;
     ga.gtab = gtab;
     ga.Jq = Jq;

@@ -123,6 +123,13 @@ __global__ void __launch_bounds__(kThreads) k_sweep_global(RunGeom g, PopDev P, 
 
 bool lattice_supported(int L) { return L >= 2 && L <= kMaxLGlobal && L % 2 == 0; }
 
+int launch_copy_parents(const RunGeom& g, PopDev* pops, int pop, int cur, int t, void* stream) {
+  const int64_t words = (g.R_cap + 3) / 4;
+  k_copy_parents<<<(unsigned)((words * g.N + kThreads - 1) / kThreads), kThreads, 0, (cudaStream_t)stream>>>(
+      g, pops[pop], cur, t, words);
+  return (int)cudaGetLastError();
+}
+
 int launch_sweep_global(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, int t, int n_sweeps,
                         const uint32_t met_thr[3], void* stream) {
   cudaStream_t st = (cudaStream_t)stream;

@@ -145,6 +145,18 @@ _i8p = ctypes.POINTER(ctypes.c_int8)
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _i64p = ctypes.POINTER(ctypes.c_int64)
 _vp = ctypes.c_void_p
+_ALLREDUCE = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64)
+_ALLGATHER = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
+                              ctypes.POINTER(ctypes.c_int64))
+_XFER = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64)
+
+
+class Comm(ctypes.Structure):
+    """pa_comm: the host exchanges of a sharded run."""
+    _fields_ = [("user", ctypes.c_void_p), ("allreduce_i64", _ALLREDUCE), ("allgather_i64", _ALLGATHER),
+                ("send", _XFER), ("recv", _XFER)]
+
+
 SIGNATURES = {
     "pa_create": (ctypes.c_int, [ctypes.POINTER(Config), _vp, ctypes.POINTER(_vp)]),
     "pa_step": (ctypes.c_int, [_vp]),
@@ -194,6 +206,14 @@ SIGNATURES = {
     "pa_resample_counts_noalloc": (ctypes.c_int, [_vp, ctypes.c_int64, _vp, _vp, ctypes.c_int32, ctypes.c_uint64,
                                                    ctypes.c_int32, ctypes.c_int32, _vp, _vp, ctypes.c_int64, _vp,
                                                    _vp]),
+    "pa_shard_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(Comm),
+                                       _vp, ctypes.POINTER(_vp)]),
+    "pa_shard_step": (ctypes.c_int, [_vp]),
+    "pa_shard_observables": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(Obs)]),
+    "pa_shard_local": (ctypes.c_int, [_vp, ctypes.POINTER(_vp)]),
+    "pa_shard_extent": (ctypes.c_int, [_vp, ctypes.c_int32, _i64p, _i64p]),
+    "pa_shard_q_hist": (ctypes.c_int, [_vp, ctypes.c_int32, _i64p, ctypes.c_int64]),
+    "pa_shard_destroy": (ctypes.c_int, [_vp]),
     "pa_bench_int_throughput": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
 }
@@ -620,3 +640,112 @@ class Run:
         J = np.zeros(3 * self.N, dtype=np.int8)
         _check("pa_get_couplings", lib().pa_get_couplings(self._h, _p(J, ctypes.c_int8), J.size))
         return J
+
+
+class Shard:
+    """One rank's share of a population annealing run split across ranks (pa_shard):
+    the exchanges between the phases of a step go over torch.distributed (a process
+    group of n_ranks ranks, gloo or any backend with CPU send/recv), all ranks call
+    every method together.  ``local`` is this rank's run (its slots of the current
+    population) for the per-rank readers (population, copy_counts)."""
+
+    def __init__(self, L: int, R: int, disorder_seed: int, run_seed: int, betas, *, n_sweeps: int = 10,
+                 sweeps_per_step=None, n_pop: int = 1, q_bins: int = 65, R_cap: int = 0, group=None, stream=None):
+        import torch
+        import torch.distributed as dist
+
+        self.L, self.N, self.n_pop, self.q_bins = L, L ** 3, n_pop, q_bins
+        self.rank, self.n_ranks = dist.get_rank(group), dist.get_world_size(group)
+        self._holder = _ConfigHolder(L, R, disorder_seed, run_seed, betas, n_sweeps=n_sweeps,
+                                     sweeps_per_step=sweeps_per_step, n_pop=n_pop, q_bins=q_bins, R_cap=R_cap)
+        self._failure = None
+
+        def guard(fn):
+            def wrapped(*args):
+                try:
+                    fn(*args)
+                    return 0
+                except Exception as e:  # reported by the library as a failed step
+                    self._failure = e
+                    return 1
+            return wrapped
+
+        def allreduce(_, ptr, n):
+            a = np.ctypeslib.as_array(ptr, shape=(n,))
+            x = torch.from_numpy(a.copy())
+            dist.all_reduce(x, group=group)
+            a[:] = x.numpy()
+
+        def allgather(_, ptr, n, out):
+            x = torch.from_numpy(np.ctypeslib.as_array(ptr, shape=(n,)).copy())
+            parts = [torch.zeros_like(x) for _ in range(self.n_ranks)]
+            dist.all_gather(parts, x, group=group)
+            np.ctypeslib.as_array(out, shape=(n * self.n_ranks,))[:] = torch.cat(parts).numpy()
+
+        def send(_, dst, buf, nbytes):
+            x = torch.from_numpy(np.ctypeslib.as_array(ctypes.cast(buf, ctypes.POINTER(ctypes.c_uint8)),
+                                                       shape=(nbytes,)).copy())
+            dist.send(x, dst, group=group)
+
+        def recv(_, src, buf, nbytes):
+            x = torch.zeros(nbytes, dtype=torch.uint8)
+            dist.recv(x, src, group=group)
+            ctypes.memmove(buf, x.numpy().ctypes.data, nbytes)
+
+        self._callbacks = (_ALLREDUCE(guard(allreduce)), _ALLGATHER(guard(allgather)), _XFER(guard(send)),
+                           _XFER(guard(recv)))
+        self._comm = Comm(None, *self._callbacks)
+        h = _vp()
+        rc = lib().pa_shard_create(ctypes.byref(self._holder.cfg), self.rank, self.n_ranks, ctypes.byref(self._comm),
+                                   _stream_handle(stream), ctypes.byref(h))
+        self._raise_failure()
+        _check("pa_shard_create", rc)
+        self._h = h
+        loc = _vp()
+        _check("pa_shard_local", lib().pa_shard_local(self._h, ctypes.byref(loc)))
+        self.local = Run._borrowed(loc, self, L, n_pop, q_bins)
+
+    def _raise_failure(self):
+        if self._failure is not None:
+            e, self._failure = self._failure, None
+            raise RuntimeError(f"host exchange failed: {e!r}") from e
+
+    def step(self) -> int:
+        rc = lib().pa_shard_step(self._h)
+        self._raise_failure()
+        return _check("pa_shard_step", rc)
+
+    def run(self) -> None:
+        while self.step() == 0:
+            pass
+
+    @property
+    def t(self) -> int:
+        return self.local.t
+
+    def obs(self, t: int, pop: int = 0) -> dict:
+        o = Obs()
+        _check("pa_shard_observables", lib().pa_shard_observables(self._h, t, pop, ctypes.byref(o)))
+        return o.as_dict()
+
+    def extent(self, pop: int = 0):
+        """(global slot of this rank's first slot, global population size)."""
+        lo, R = ctypes.c_int64(), ctypes.c_int64()
+        _check("pa_shard_extent", lib().pa_shard_extent(self._h, pop, ctypes.byref(lo), ctypes.byref(R)))
+        return lo.value, R.value
+
+    def q_hist(self, t: int) -> np.ndarray:
+        out = np.zeros(self.q_bins, dtype=np.int64)
+        _check("pa_shard_q_hist", lib().pa_shard_q_hist(self._h, t, _p(out, ctypes.c_int64), out.size))
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().pa_shard_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
