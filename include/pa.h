@@ -416,6 +416,17 @@ int pa_sweep_shapes(int32_t L, pa_sweep_shape* shapes, int32_t cap, int32_t* n);
 int pa_sweep_select(int32_t L, int32_t index);
 int pa_sweep_selected(int32_t L, int32_t* index);
 
+/* The sweep launches of run c: *shape = the index (into pa_sweep_shapes(L)) of the
+ * shape its tiles use; when the population leaves the last wave of tiles mostly
+ * empty (the run's R replicas fill at least one wave of the device's SMs and a
+ * last wave at most 60 % full), that wave is a second launch of the next smaller
+ * tile shape: *tail_shape = its index and *tail_from = the first slot it covers
+ * (a multiple of both tile sizes); otherwise *tail_shape = -1 and *tail_from = 0.
+ * Both launches give the results of one.  Runs of the Gaussian model, sharded
+ * runs and runs whose shape is pinned with pa_sweep_select have no second launch.
+ * PA_ERR_INVALID for a NULL argument. */
+int pa_sweep_plan(const pa_ctx* c, int32_t* shape, int32_t* tail_shape, int32_t* tail_from);
+
 /* Autotuner: on the current device, creates a scratch run of size L with R
  * replicas (one population, one temperature step from beta 0 to 0.5, 10
  * sweeps), times `launches` sweep launches of every shape of L (after one

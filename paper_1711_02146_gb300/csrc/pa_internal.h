@@ -86,6 +86,11 @@ struct RunGeom {
   int32_t n_count_blocks;    // resampling blocks (1024 slots each)
   int32_t n_fsizes;          // bound on the distinct family sizes of a population: floor(sqrt(2 R_cap)) + 2
   int32_t sweep_shape;       // index of the sweep kernel's launch shape among those of L
+  // A run of a single GPU whose last wave of sweep tiles would be mostly empty sweeps
+  // the slots from tail_from on (a multiple of 1024) with the smaller tiles of shape
+  // tail_shape, spread over the SMs, in a second launch (-1: one launch).
+  int32_t tail_shape;
+  int32_t tail_from;
   int32_t model;             // 0: +-1 couplings, 1: Gaussian couplings (fixed point)
   // One rank's share of a sharded population (pa_shard): global slot of local slot
   // 0 (a multiple of 1024; random words are addressed by global slot), the local
@@ -124,6 +129,10 @@ struct SweepShapeInfo {
 };
 int sweep_shape_count(int L);
 bool sweep_shape_info(int L, int i, SweepShapeInfo* out);
+// The tail launch of a run of target population R with main shape `shape` on a
+// device of n_sm SMs: sets *tail_shape and *tail_from, or *tail_shape = -1 when one
+// launch is as good (its last wave is full enough, or L has no smaller tile).
+void sweep_tail_plan(int L, int shape, int64_t R, int n_sm, int32_t* tail_shape, int32_t* tail_from);
 
 constexpr int kCountThreads = 256;     // threads per resampling block
 constexpr int kSlotsPerCountBlock = 1024;

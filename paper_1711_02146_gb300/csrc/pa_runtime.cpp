@@ -664,6 +664,8 @@ void init_run(pa_ctx* c, const pa_config* cfg, int64_t R_cap) {
   while (k * k > 2 * R_cap) --k;
   g.n_fsizes = (int32_t)k + 2;
   g.sweep_shape = 0;
+  g.tail_shape = -1;
+  g.tail_from = 0;
   g.model = cfg->model;
   g.slot_base = 0;
   g.n_init = (int32_t)cfg->R;
@@ -740,6 +742,7 @@ namespace pa {
 void use_chosen_shape(pa_ctx* c) {
   int dev = 0;
   if (c && sweep_supported(c->g.L) && current_device(&dev) == PA_OK) c->g.sweep_shape = g_sweep_choice[dev][c->g.L].load();
+  if (c) c->g.tail_shape = -1;  // runs among many: other runs fill the SMs a last wave leaves idle
 }
 }  // namespace pa
 
@@ -938,7 +941,13 @@ int create_run_impl(const pa_config* cfg, void* cuda_stream, pa_ctx** out, bool 
     g.shard = 1;
   }
   int dev = 0;
-  if (pa::sweep_supported(g.L) && current_device(&dev) == PA_OK) g.sweep_shape = run_shape(g.L, R_cap, dev);
+  if (pa::sweep_supported(g.L) && current_device(&dev) == PA_OK) {
+    g.sweep_shape = run_shape(g.L, R_cap, dev);
+    int n_sm = 0;
+    if (!sp.share && g.model == PA_MODEL_PM1 && !g_sweep_pinned[dev][g.L].load() &&
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      pa::sweep_tail_plan(g.L, g.sweep_shape, cfg->R, n_sm, &g.tail_shape, &g.tail_from);
+  }
   for (int p = 0; p < g.n_pop; ++p) {
     make_key(cfg->run_seed, pa::kMetropolis, (uint32_t)p, c->pops[p].key_met);
     make_key(cfg->run_seed, pa::kResample, (uint32_t)p, c->pops[p].key_res);
@@ -1090,8 +1099,8 @@ int pa_step(pa_ctx* c) {
       PhaseTimer pt(c, PA_PHASE_RESAMPLE, 1);
       rc = launch_rc(pa::launch_resample(c->g, c->pops, c->cur, t, c->status, c->lookback, s));
     }
-    if (rc == PA_OK && pa::sweep_supported(c->g.L)) {
-      PhaseTimer pt(c, PA_PHASE_SWEEP, 1);
+    if (rc == PA_OK && pa::sweep_supported(c->g.L)) {  // per population: the tiles, then a partial last wave's
+      PhaseTimer pt(c, PA_PHASE_SWEEP, c->g.n_pop * (c->g.tail_shape >= 0 ? 2 : 1));
       rc = launch_rc(pa::launch_sweep(c->g, c->pops, c->cur, c->jtab, t, c->sweeps[(size_t)t], met, s));
     } else if (rc == PA_OK) {  // lattices beyond a shared-memory tile: sweeps in global memory
       PhaseTimer pt(c, PA_PHASE_SWEEP, c->g.n_pop * (1 + 2 * c->sweeps[(size_t)t]) + 1);
@@ -1644,6 +1653,14 @@ int pa_sweep_selected(int32_t L, int32_t* index) {
   return PA_OK;
 }
 
+int pa_sweep_plan(const pa_ctx* c, int32_t* shape, int32_t* tail_shape, int32_t* tail_from) {
+  if (!c || !shape || !tail_shape || !tail_from) return PA_ERR_INVALID;
+  *shape = c->g.sweep_shape;
+  *tail_shape = c->g.tail_shape;
+  *tail_from = c->g.tail_from;
+  return PA_OK;
+}
+
 int pa_sweep_autotune(int32_t L, int32_t R, int32_t launches, double* ms_per_launch, int32_t cap, int32_t* best) {
   if (!best || !pa::sweep_supported(L) || R < 1 || launches < 1 || cap < 0 || (cap > 0 && !ms_per_launch))
     return PA_ERR_INVALID;
@@ -1681,6 +1698,7 @@ int pa_sweep_autotune(int32_t L, int32_t R, int32_t launches, double* ms_per_lau
     const int n = pa::sweep_shape_count(L);
     for (int i = 0; i < n && rc == PA_OK; ++i) {
       c->g.sweep_shape = i;
+      c->g.tail_shape = -1;
       double t_ms = -1.0;
       int e = pa::launch_sweep(c->g, c->pops, src, c->jtab, 1, cfg.n_sweeps, met, s);
       if (e == 0) {

@@ -39,6 +39,8 @@
 // word, with a 32-bit Philox word per update.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "pa_device.cuh"
 #include "pa_family.cuh"
 #include "pa_internal.h"
@@ -58,6 +60,9 @@ struct SweepArgs {
   int32_t n_sweeps;
   int32_t slot_base;  // global slot of local slot 0 (Philox groups are global); 0 for a whole population
   int32_t fam;        // 1: add the tile's families to the step record (not for one rank's share)
+  // this launch's first local slot (tile 0 of the grid), and the split of a two-launch
+  // sweep: slots below `split` in tiles of tj_main, the rest in tiles of tj_tail
+  int32_t tile_base, split, tj_main, tj_tail;
   uint32_t thr4, thr8, thr12;
   uint32_t k0[10];  // Metropolis round keys of this population
   uint32_t k1[10];
@@ -708,7 +713,11 @@ __device__ __forceinline__ void tile_families(const SweepArgs& a, int* sh, int t
     family_size(a.pop, eta, mask);
   }
   family_flush(f, mask, &a.pop.rec[a.t]);
-  family_entropy_last(a.pop, &a.pop.rec[a.t], R_new, (R_new + TJ - 1) / TJ, tid, NT, red);
+  // the tiles of both launches that hold slots take part
+  const int in_main = min(R_new, a.split);
+  const int participants = (in_main + a.tj_main - 1) / a.tj_main +
+                           (R_new > a.split ? (R_new - a.split + a.tj_tail - 1) / a.tj_tail : 0);
+  family_entropy_last(a.pop, &a.pop.rec[a.t], R_new, participants, tid, NT, red);
 }
 
 // Bit-sliced sweep kernel (+-1 couplings).
@@ -722,7 +731,7 @@ __global__ void __launch_bounds__(NT, MB) k_sweep(const __grid_constant__ SweepA
   Deferred* queues = reinterpret_cast<Deferred*>(recs + N);        // [NQ][kQueueCap]
   int* slots = reinterpret_cast<int*>(queues + S::NQ * kQueueCap);  // [33 W]: parents, then level counts
   const int R_new = a.pop.rec[a.t].R_tilde;
-  const int tile0 = blockIdx.x * TJ;
+  const int tile0 = a.tile_base + blockIdx.x * TJ;
   if (tile0 >= R_new) return;
   const int tid = threadIdx.x, word = tid % W, part = tid / W;
   Deferred* dq = queues + (S::DEFER ? (tid >> 5) * kQueueCap : 0);
@@ -919,7 +928,10 @@ static int launch_t(const RunGeom& g, const SweepArgs& args, cudaStream_t s) {
   static std::atomic<int> done[64];
   const cudaError_t e = smem_limit_once(k_sweep<L, W, NT, MB>, (int)S::SMEM, done);
   if (e != cudaSuccess) return (int)e;
-  dim3 grid((unsigned)((g.R_cap + S::TJ - 1) / S::TJ));
+  // tiles from tile_base up to the split (main launch) or to the capacity (tail launch)
+  const int64_t end = args.tile_base < args.split ? std::min<int64_t>(args.split, g.R_cap) : g.R_cap;
+  if (end <= args.tile_base) return 0;
+  dim3 grid((unsigned)((end - args.tile_base + S::TJ - 1) / S::TJ));
   k_sweep<L, W, NT, MB><<<grid, NT, S::SMEM, s>>>(args);
   return (int)cudaGetLastError();
 }
@@ -1003,6 +1015,11 @@ int launch_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, 
     args.n_sweeps = n_sweeps;
     args.slot_base = g.slot_base;
     args.fam = g.shard ? 0 : 1;
+    const ShapeEntry* tail = g.tail_shape >= 0 ? shape_of(g.L, g.tail_shape) : nullptr;
+    args.tile_base = 0;
+    args.split = tail ? g.tail_from : 0x7fffffff;
+    args.tj_main = 32 * shape->W;
+    args.tj_tail = tail ? 32 * tail->W : 32 * shape->W;
     args.thr4 = met_thr[0];
     args.thr8 = met_thr[1];
     args.thr12 = met_thr[2];
@@ -1021,10 +1038,32 @@ int launch_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, 
     args.live[1] = live[0] ^ live[1];
     args.live[2] = live[0] ^ live[2];
     args.live[3] = 0u;
-    const int e = shape->launch(g, args, s);
+    int e = shape->launch(g, args, s);
+    if (e == 0 && tail) {
+      args.tile_base = g.tail_from;
+      e = tail->launch(g, args, s);
+    }
     if (e != 0) return e;
   }
   return 0;
+}
+
+void sweep_tail_plan(int L, int shape, int64_t R, int n_sm, int32_t* tail_shape, int32_t* tail_from) {
+  *tail_shape = -1;
+  *tail_from = 0;
+  const ShapeEntry* m = shape_of(L, shape);
+  if (!m || n_sm <= 0) return;
+  const int64_t tj = 32LL * m->W, slots = (int64_t)n_sm * m->MB, tiles = (R + tj - 1) / tj;
+  const int64_t full = tiles / slots, rest = tiles - full * slots;
+  if (full < 1 || rest == 0 || 10 * rest > 6 * slots) return;  // the last wave is more than 60 % full
+  int best = -1;
+  for (int i = 0; i < sweep_shape_count(L); ++i) {  // the largest smaller tile
+    const ShapeEntry* e = shape_of(L, i);
+    if (e->W < m->W && (best < 0 || e->W > shape_of(L, best)->W)) best = i;
+  }
+  if (best < 0) return;
+  *tail_shape = best;
+  *tail_from = (int32_t)(full * slots * tj);
 }
 
 int launch_g_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, const int32_t* Jq, long long Jtot,
@@ -1049,6 +1088,9 @@ int launch_g_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab
     args.n_sweeps = n_sweeps;
     args.slot_base = 0;
     args.fam = 0;
+    args.tile_base = 0;
+    args.split = 0x7fffffff;
+    args.tj_main = args.tj_tail = 1;
     args.thr4 = args.thr8 = args.thr12 = 0u;
     ga.gtab = gtab;
     ga.Jq = Jq;

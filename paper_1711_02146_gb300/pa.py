@@ -201,6 +201,7 @@ SIGNATURES = {
     "pa_sweep_shapes": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(SweepShape), ctypes.c_int32, _i32p]),
     "pa_sweep_select": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32]),
     "pa_sweep_selected": (ctypes.c_int, [ctypes.c_int32, _i32p]),
+    "pa_sweep_plan": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p]),
     "pa_sweep_autotune": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.POINTER(ctypes.c_double), ctypes.c_int32, _i32p]),
     "pa_resample_counts_noalloc": (ctypes.c_int, [_vp, ctypes.c_int64, _vp, _vp, ctypes.c_int32, ctypes.c_uint64,
@@ -619,6 +620,14 @@ class Run:
         out = np.zeros(3 * self.N, dtype=np.int32)
         _check("pa_get_gcouplings", lib().pa_get_gcouplings(self._h, _p(out, ctypes.c_int32), out.size))
         return out
+
+    def sweep_plan(self) -> dict:
+        """The sweep launches of this run: the tile shape's index in ``sweep_shapes(L)``
+        and, when the last wave of tiles runs as a second launch of smaller tiles, that
+        shape's index and the first slot it covers (else -1 and 0)."""
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check("pa_sweep_plan", lib().pa_sweep_plan(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"shape": a.value, "tail_shape": b.value, "tail_from": c.value}
 
     def copy_counts(self, pop: int = 0) -> np.ndarray:
         n = ctypes.c_int64()

@@ -312,3 +312,62 @@ def test_c2_full_size_two_populations(pa, oracle_lib):
             ref, dE = oracle_lib.sweep_replica(L, J, s_old[parents[j]], C2.run_seed, 1, int(j), t, C2.n_sweeps, met)
             assert np.array_equal(s_new[j], ref), f"pop 1 slot {j}"
             assert E_new[j] == E_old[parents[j]] + dE
+
+
+def test_two_launch_sweep_for_a_partial_last_wave(pa, oracle_lib):
+    """L = 10 with a population of 1.6e5: 157 tiles of 1024 replicas for 152 SMs, so the
+    sweep runs the first 152 tiles with the 1024-replica shape and the rest with
+    512-replica tiles in a second launch (when the device has 152 SMs; fewer SMs give
+    other splits).  Every slot, energy, label and family statistic is the oracle's."""
+    betas = linear(3, 0.8)
+    gpu, ref = make_pair(pa, oracle_lib, 10, 160_000, betas, n_sweeps=1, disorder_seed=5, run_seed=8)
+    if pa.sweep_selected(10) == 0 and _n_sm() == 152:
+        assert gpu.sweep_plan() == {"shape": 0, "tail_shape": 1, "tail_from": 152 * 1024}
+    for t in range(1, 3):
+        assert gpu.step() == 0
+        ref.step()
+        assert np.array_equal(gpu.copy_counts(), ref.last_counts()), f"copy numbers at t={t}"
+        assert np.array_equal(gpu.energy_hist(t), ref.energy_hist(t)), f"energy histogram at t={t}"
+        assert_obs_equal(gpu.obs(t), ref.obs(t), f"t={t}")
+    assert_state_equal(gpu, ref, 1, "two-launch sweep")
+
+
+def _n_sm():
+    import torch
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
+def test_sweep_plan_rule(pa):
+    """The second launch is planned exactly when the run's R replicas fill at least
+    one wave of tiles and leave a last wave at most 60 % full; it takes the next
+    smaller tile and starts where the full waves end.  Gaussian runs, pinned shapes
+    and runs among many have none."""
+    n_sm = _n_sm()
+    shapes = pa.sweep_shapes(10)
+    pa.sweep_select(10, -1)
+    for R in (1000, 100_000, 152 * 1024, 160_000, 250_000, 300_000, 1_000_000):
+        run = pa.Run(10, R, 1, 2, linear(2, 0.5), n_sweeps=1)
+        plan = run.sweep_plan()
+        run.close()
+        sh = shapes[plan["shape"]]
+        tj = 32 * sh["words"]
+        slots = n_sm * sh["ctas_per_sm"]
+        tiles = -(-R // tj)
+        full, rest = divmod(tiles, slots)
+        smaller = [i for i, s in enumerate(shapes) if s["words"] < sh["words"]]
+        if full >= 1 and rest > 0 and 10 * rest <= 6 * slots and smaller:
+            best = max(smaller, key=lambda i: shapes[i]["words"])
+            assert plan == {"shape": plan["shape"], "tail_shape": best, "tail_from": full * slots * tj}, R
+            assert plan["tail_from"] % (32 * shapes[best]["words"]) == 0
+        else:
+            assert plan["tail_shape"] == -1 and plan["tail_from"] == 0, R
+    pa.sweep_select(10, 0)   # pinned: one launch
+    try:
+        run = pa.Run(10, 160_000, 1, 2, linear(2, 0.5), n_sweeps=1)
+        assert run.sweep_plan()["tail_shape"] == -1
+        run.close()
+    finally:
+        pa.sweep_select(10, -1)
+    g = pa.Run(10, 160_000, 1, 2, linear(2, 0.5), n_sweeps=1, model=pa.PA_MODEL_GAUSS)
+    assert g.sweep_plan()["tail_shape"] == -1
+    g.close()
