@@ -312,17 +312,23 @@ def total_updates(w) -> int:
 
 
 def batched_vs_serial(pa, n_runs: int):
-    """The batched mix: all runs advanced together (pa_batch) vs one at a time
-    (pa_create + pa_run + pa_destroy), same GPU, creation included in both."""
+    """The batched mix: all runs advanced together (pa_batch: in fused rounds, one
+    CUDA graph launch per temperature step for the whole batch, and, for comparison,
+    each run on its own stream) vs one at a time (pa_create + pa_run + pa_destroy),
+    same GPU, creation included in all three."""
     import torch
     from paper_1711_02146_gb300.workloads import batched_mix
     ws = batched_mix(256)[:n_runs]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    b = pa.Batch(ws)
-    b.run()
-    t_batch = time.perf_counter() - t0
-    b.close()
+    times, launches = {}, {}
+    for mode in ("fused", "streams"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b = pa.Batch(ws, mode=mode)
+        b.run()
+        times[mode] = time.perf_counter() - t0
+        launches[mode] = b.launches()
+        b.close()
+    t_batch = times["fused"]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for w in ws:
@@ -333,9 +339,14 @@ def batched_vs_serial(pa, n_runs: int):
     upd = sum(total_updates(w) for w in ws)
     return {"runs": len(ws), "workload": "L in {4,6,8,10}, R log-uniform [1e4,1e5], 101 linear temperatures, "
                                         "10 sweeps (first %d of 256 disorder seeds 100..355)" % len(ws),
+            "mode": "fused: per temperature step one CUDA graph launch holding one reweighting, one resampling, "
+                    "one sweep launch per L and one round-counter launch for all runs",
             "runs_per_s": len(ws) / t_batch, "serial_runs_per_s": len(ws) / t_serial,
             "speedup_vs_serial": t_serial / t_batch, "updates_per_s": upd / t_batch,
-            "serial_updates_per_s": upd / t_serial, "seconds": t_batch, "serial_seconds": t_serial}
+            "serial_updates_per_s": upd / t_serial, "seconds": t_batch, "serial_seconds": t_serial,
+            "launches": launches["fused"],
+            "streams_mode": {"runs_per_s": len(ws) / times["streams"], "seconds": times["streams"],
+                             "speedup_vs_serial": t_serial / times["streams"], "launches": launches["streams"]}}
 
 
 def served_vs_serial(pa, n_req: int, mem_budget: int):

@@ -321,10 +321,12 @@ const char* pa_strerror(int status);
 
 /* ---- many runs at once (batched and served workloads) ----
  * Independent runs (different couplings, sizes, populations, schedules) share
- * the GPU by running on their own non-blocking streams: their steps are issued
- * round-robin from the host and their kernels overlap on the device.  Each run
- * gives exactly the results it gives alone (its random streams depend only on
- * its configuration).  These objects are not thread-safe. */
+ * the GPU.  A batch advances its runs in rounds of one temperature step each (see
+ * pa_batch_set_mode); the server runs each admitted run on its own non-blocking
+ * stream, issuing steps round-robin from the host, so that the kernels of
+ * different runs overlap on the device.  Each run gives exactly the results it
+ * gives alone (its random streams depend only on its configuration).  These
+ * objects are not thread-safe. */
 
 /* Device bytes that pa_create allocates for cfg, exactly (for admission control;
  * no device call). */
@@ -336,6 +338,27 @@ int pa_batch_create(const pa_config* cfgs, int32_t n, pa_batch** out);
 /* Advances every run to the end of its schedule, one step of each run per
  * round, then synchronises; returns PA_OK or the first error. */
 int pa_batch_run(pa_batch* batch);
+
+/* How pa_batch_run advances the runs (both give every run its results alone):
+ * PA_BATCH_FUSED (the default): the runs that qualify — +-1 couplings, an
+ *   explicit schedule, L <= 16, not finished — advance together, each round one
+ *   reweighting launch for all their populations, one resampling launch, one sweep
+ *   launch per lattice size and launch shape, one overlap launch for the
+ *   two-population runs and a one-thread launch that advances the device's round
+ *   counter.  The round reads each run's step (its weight table, Metropolis
+ *   thresholds and sweeps) from device tables built when pa_batch_run starts, so
+ *   the launches of one round are captured once as a CUDA graph and every round is
+ *   one graph launch, all issued without waiting; runs that finish earlier rest in
+ *   the later rounds.  The other runs step on their own streams as below.
+ * PA_BATCH_STREAMS: every run steps on its own stream, one pa_step of each run per
+ *   round, issued from the host.
+ * PA_ERR_INVALID for another mode. */
+#define PA_BATCH_FUSED 0
+#define PA_BATCH_STREAMS 1
+int pa_batch_set_mode(pa_batch* batch, int32_t mode);
+/* Kernels launched by pa_batch_run so far (each graph launch counts the kernels it
+ * holds) and CUDA graph launches. */
+int pa_batch_launches(const pa_batch* batch, int64_t* kernel_launches, int64_t* graph_launches);
 /* Borrowed view of run i (valid until pa_batch_destroy), for observables. */
 int pa_batch_ctx(pa_batch* batch, int32_t i, pa_ctx** view);
 int pa_batch_destroy(pa_batch* batch);

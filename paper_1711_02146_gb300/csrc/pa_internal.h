@@ -182,6 +182,46 @@ int launch_g_tables(const double* dbeta_dev, double dbeta_val, double* T, void* 
 int launch_g_bisect(const RunGeom& g, PopDev* pops, int t, double* T, double* b, double target, int halvings,
                     void* stream);
 int launch_overlap(const RunGeom& g, PopDev* pops, int cur, int t, unsigned long long* qhist, void* stream);
+
+// ---- a batch advanced by one launch per kernel and temperature step (pa_batch) ----
+// Every population of every run of the batch is a unit; a round takes each unit's
+// run one step further with one reweighting launch, one resampling launch, one
+// sweep launch per (L, launch shape) and one overlap launch, all reading the round
+// number from device memory, so the same CUDA graph serves every round.  In round
+// r a unit's step is t = t0 + 1 + r (the unit rests once t > last_t) and the
+// population it reads is buffer cur0 ^ (r & 1).
+struct GroupStep {   // step t of a run (t >= 1)
+  const double* w;   // the run's weight table of beta_t - beta_{t-1} (device)
+  uint32_t thr[3];   // Metropolis thresholds of beta_t for dE = 4, 8, 12
+  int32_t n_sweeps;
+};
+struct GroupUnit {   // one population of one run
+  RunGeom g;
+  PopDev P;
+  const uint32_t* jtab;
+  int32_t* status;
+  const GroupStep* steps;  // [n_temps], entry 0 unused
+  int32_t t0, cur0, last_t, pop;
+};
+struct GroupPair {   // the two populations of a two-population run
+  int32_t u0, u1;
+  unsigned long long* qhist;
+};
+// Block ranges: units (or pairs) k take the blocks [off[k], off[k + 1]) of a launch.
+int launch_group_reweight(const GroupUnit* units, int n_units, int max_levels, const int32_t* round, void* stream);
+int launch_group_resample(const GroupUnit* units, const int32_t* off, int n_units, int n_blocks,
+                          const int32_t* round, void* stream);
+// Sweep of the units list[0, n) (all of lattice size L and launch shape `shape`),
+// off[k] = first tile of unit list[k] in the launch.
+int launch_group_sweep(int L, int shape, const GroupUnit* units, const int32_t* list, const int32_t* off, int n,
+                       int n_blocks, const int32_t* round, void* stream);
+int launch_group_overlap(const GroupUnit* units, const GroupPair* pairs, const int32_t* off, int n_pairs,
+                         int n_blocks, int max_bins, const int32_t* round, void* stream);
+int launch_group_advance(int32_t* round, void* stream);
+// Tiles (slots per CTA) of sweep shape `shape` of L; 0 if there is none.
+int sweep_tile_slots(int L, int shape);
+constexpr int kResampleSlotsPerBlock = 1024;  // old slots per block of the single-pass resampling
+
 }  // namespace pa
 struct pa_ctx;
 namespace pa {
@@ -199,6 +239,17 @@ int create_run(const pa_config* cfg, void* cuda_stream, pa_ctx** out, bool synch
 // of 1024), family statistics left to the sharded step.
 int create_run_share(const pa_config* cfg, void* cuda_stream, pa_ctx** out, int64_t slot_base, int64_t n_init);
 #endif
+// Batch rounds (pa_batch): the runs that qualify (+-1 couplings, explicit schedule,
+// shared-memory sweep, not finished) advance together, one CUDA graph launch per
+// round; group_run issues every round (asynchronously), makes the runs' streams wait
+// for them and advances the runs' host state to their last step.
+struct Group;
+bool group_eligible(const pa_ctx* c);
+int group_create(pa_ctx* const* runs, int n, Group** out);
+int group_run(Group* grp, int64_t* kernel_launches, int64_t* graph_launches);
+void group_destroy(Group* grp);
+// Kernel launches a run has issued (its pa_stats count, without synchronising).
+int64_t run_kernel_launches(const pa_ctx* c);
 // Largest lattice size the sweep kernel supports.
 constexpr int kMaxL = 16;
 // Largest lattice size of a run (larger lattices than kMaxL sweep in global memory).

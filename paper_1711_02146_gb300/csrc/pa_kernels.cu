@@ -127,11 +127,12 @@ __global__ void k_levels_and_hist(RunGeom g, PopArgs a, int cur, const uint32_t*
 //   tau_k = R w[k - kmin] / S'  ->  fl_k = floor(tau_k), thr_k = 2^32 (tau_k - fl_k)
 //   eps = (1/R) sum_k c(k) (1 - tau_k)_+          (Eq. eq_num_elim; fixed tree order)
 // Empty levels add exact zeros to S', so they are skipped there.
-__global__ void k_reweight(RunGeom g, PopArgs a, const double* __restrict__ w, int t, int list_in_smem) {
-  extern __shared__ int lst_sh[];  // n_levels entries: occupied levels, ascending
+// One block per population; lst_sh (n_levels entries) holds the occupied levels,
+// ascending, when list_in_smem.
+__device__ __forceinline__ void reweight_pop(const RunGeom& g, const PopDev& P, const double* __restrict__ w, int t,
+                                             int* lst_sh, int list_in_smem) {
   __shared__ int scratch[33];
   __shared__ double S_sh;
-  const PopDev& P = a.p[blockIdx.x];
   if (threadIdx.x == 0) *P.ticket = 0;  // the tile ticket of this step's single-pass resampling
   // the list lives in shared memory when it fits; otherwise in the floor table,
   // which is only written (below) after the list has been read
@@ -190,6 +191,22 @@ __global__ void k_reweight(RunGeom g, PopArgs a, const double* __restrict__ w, i
     r.kmin_prev = kmin;
     r.R_prev = P.rec[t - 1].R_tilde;
   }
+}
+
+__global__ void k_reweight(RunGeom g, PopArgs a, const double* __restrict__ w, int t, int list_in_smem) {
+  extern __shared__ int lst_sh[];
+  reweight_pop(g, a.p[blockIdx.x], w, t, lst_sh, list_in_smem);
+}
+
+// Every unit of a batch, one block each; the step record of the round's step is
+// cleared here (a lone run clears it with a memset before this kernel).
+__global__ void k_group_reweight(const GroupUnit* __restrict__ units, const int32_t* __restrict__ round) {
+  extern __shared__ int lst_sh[];
+  const GroupUnit& u = units[blockIdx.x];
+  const int t = u.t0 + 1 + *round;
+  if (t > u.last_t) return;
+  if (threadIdx.x == 0) u.P.rec[t] = StepRec{};
+  reweight_pop(u.g, u.P, u.steps[t].w, t, lst_sh, 1);
 }
 
 // ---------------------------------------------------------------- resampling (a5, a6)
@@ -290,14 +307,15 @@ __device__ __forceinline__ unsigned long long poll_tile(const unsigned long long
   return *reinterpret_cast<const volatile unsigned long long*>(p);
 }
 
-__global__ void __launch_bounds__(kCountThreads) k_resample(RunGeom g, PopArgs a, int cur, int t, int32_t* status,
-                                                             int spin_limit, int withheld) {
+static_assert(kResampleTile == kResampleSlotsPerBlock, "resampling blocks of a batch are counted by the host");
+
+__device__ __forceinline__ void resample_pop(const RunGeom& g, const PopDev& P, int cur, int t, int32_t* status,
+                                             int spin_limit, int withheld) {
   __shared__ int scratch[33];
   __shared__ int tile_sh;
   __shared__ long long base_sh;
   __shared__ unsigned incl_sh[kCountThreads / 32];
   __shared__ long long sum_sh[kCountThreads / 32];
-  const PopDev& P = a.p[blockIdx.y];
   if (threadIdx.x == 0) tile_sh = atomicAdd(P.ticket, 1);
   __syncthreads();
   const int tile = tile_sh;
@@ -432,6 +450,43 @@ __global__ void __launch_bounds__(kCountThreads) k_resample(RunGeom g, PopArgs a
   }
 }
 
+__global__ void __launch_bounds__(kCountThreads) k_resample(RunGeom g, PopArgs a, int cur, int t, int32_t* status,
+                                                             int spin_limit, int withheld) {
+  resample_pop(g, a.p[blockIdx.y], cur, t, status, spin_limit, withheld);
+}
+
+// The block's unit: k with off[k] <= blockIdx.x < off[k + 1] (off ascending, n + 1 entries).
+__device__ __forceinline__ int group_block_unit(const int32_t* __restrict__ off, int n, int* sh) {
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = n - 1;
+    const int b = (int)blockIdx.x;
+    while (lo < hi) {  // the last k with off[k] <= b
+      const int mid = (lo + hi + 1) >> 1;
+      if (off[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    *sh = lo;
+  }
+  __syncthreads();
+  return *sh;
+}
+
+// Every unit of a batch: unit k takes blocks off[k] .. off[k+1]-1, one per 1024 slots
+// of its capacity; blocks past the old population's tiles take no ticket (the
+// tickets stay dense, so every wait is on a block that is running or done).
+__global__ void __launch_bounds__(kCountThreads) k_group_resample(const GroupUnit* __restrict__ units,
+                                                                   const int32_t* __restrict__ off, int n,
+                                                                   const int32_t* __restrict__ round) {
+  __shared__ int unit_sh;
+  const int k = group_block_unit(off, n, &unit_sh);
+  const GroupUnit& u = units[k];
+  const int r = *round, t = u.t0 + 1 + r;
+  if (t > u.last_t) return;
+  const int R_old = u.P.rec[t - 1].R_tilde;
+  const int needed = R_old > 0 ? (R_old + kResampleTile - 1) / kResampleTile : 1;
+  if ((int)blockIdx.x - off[k] >= needed) return;
+  resample_pop(u.g, u.P, u.cur0 ^ (r & 1), t, u.status, kLookbackSpins, -1);
+}
+
 // ---------------------------------------------------------------- families (a7)
 
 // Families from the sorted labels: a family is a run of equal labels along the
@@ -537,16 +592,15 @@ __global__ void __launch_bounds__(1024) k_entropy_of_sizes(const int32_t* eta, c
 
 // q between slot j of population 0 and slot j of population 1, j < min(R~0, R~1):
 // Q = N - 2 (sites that differ); bin = ((Q + N)(B - 1) + N) div 2N.
-__global__ void k_overlap(RunGeom g, PopArgs a, int cur, int t, unsigned long long* qhist) {
-  extern __shared__ unsigned int qh[];
+// Block `blk` of the pairs of populations A, B (256 words of four slots each).
+__device__ __forceinline__ void overlap_pops(const RunGeom& g, const PopDev& A, const PopDev& B, int cur, int t,
+                                             unsigned long long* qhist, unsigned int* qh, int blk) {
   __shared__ unsigned int small_sh;
-  const PopDev& A = a.p[0];
-  const PopDev& B = a.p[1];
   const int pairs = min(A.rec[t].R_tilde, B.rec[t].R_tilde);
   for (int i = threadIdx.x; i < g.q_bins; i += blockDim.x) qh[i] = 0u;
   if (threadIdx.x == 0) small_sh = 0u;
   __syncthreads();
-  const int wi = blockIdx.x * blockDim.x + threadIdx.x;
+  const int wi = blk * blockDim.x + threadIdx.x;
   if (4 * wi < pairs) {
     const uint32_t* SA = reinterpret_cast<const uint32_t*>(A.spins[cur]);
     const uint32_t* SB = reinterpret_cast<const uint32_t*>(B.spins[cur]);
@@ -582,10 +636,29 @@ __global__ void k_overlap(RunGeom g, PopArgs a, int cur, int t, unsigned long lo
   for (int i = threadIdx.x; i < g.q_bins; i += blockDim.x)
     if (qh[i]) atomicAdd(&row[i], (unsigned long long)qh[i]);
   if (threadIdx.x == 0) {
-    if (small_sh) atomicAdd(&a.p[0].rec[t].q_small, (unsigned long long)small_sh);
-    if (blockIdx.x == 0) a.p[0].rec[t].q_pairs = (unsigned long long)pairs;
+    if (small_sh) atomicAdd(&A.rec[t].q_small, (unsigned long long)small_sh);
+    if (blk == 0) A.rec[t].q_pairs = (unsigned long long)pairs;
   }
 }
+
+__global__ void k_overlap(RunGeom g, PopArgs a, int cur, int t, unsigned long long* qhist) {
+  extern __shared__ unsigned int qh[];
+  overlap_pops(g, a.p[0], a.p[1], cur, t, qhist, qh, (int)blockIdx.x);
+}
+
+__global__ void k_group_overlap(const GroupUnit* __restrict__ units, const GroupPair* __restrict__ pairs,
+                                const int32_t* __restrict__ off, int n, const int32_t* __restrict__ round) {
+  extern __shared__ unsigned int qh[];
+  __shared__ int pair_sh;
+  const int k = group_block_unit(off, n, &pair_sh);
+  const GroupPair& pr = pairs[k];
+  const GroupUnit& a = units[pr.u0];
+  const int r = *round, t = a.t0 + 1 + r;
+  if (t > a.last_t) return;
+  overlap_pops(a.g, a.P, units[pr.u1].P, a.cur0 ^ ((r + 1) & 1), t, pr.qhist, qh, (int)blockIdx.x - off[k]);
+}
+
+__global__ void k_group_advance(int32_t* round) { *round += 1; }
 
 // ---------------------------------------------------------------- launchers
 
@@ -667,6 +740,37 @@ int launch_family_hist(const RunGeom& g, PopDev* pops, int pop, int cur, int t, 
   PopArgs a = pack(pops + pop, 1);
   cudaMemsetAsync(pops[pop].mhist, 0, sizeof(int32_t) * ((size_t)g.R_cap + 1), s);
   k_fam_runs<<<dim3(grid_for(g.R_cap, 256), 1), 256, 0, s>>>(g, a, cur, t, 1);
+  return (int)cudaGetLastError();
+}
+
+int launch_group_reweight(const GroupUnit* units, int n_units, int max_levels, const int32_t* round, void* stream) {
+  const size_t smem = sizeof(int) * (size_t)max_levels;
+  if (smem > 48 * 1024) {
+    static std::atomic<int> done[64];
+    const cudaError_t e =
+        smem_limit_once(k_group_reweight, (int)(sizeof(int) * (3 * kMaxL * kMaxL * kMaxL + 1)), done);
+    if (e != cudaSuccess) return (int)e;
+  }
+  k_group_reweight<<<n_units, 1024, smem, (cudaStream_t)stream>>>(units, round);
+  return (int)cudaGetLastError();
+}
+
+int launch_group_resample(const GroupUnit* units, const int32_t* off, int n_units, int n_blocks, const int32_t* round,
+                          void* stream) {
+  k_group_resample<<<n_blocks, kCountThreads, 0, (cudaStream_t)stream>>>(units, off, n_units, round);
+  return (int)cudaGetLastError();
+}
+
+int launch_group_overlap(const GroupUnit* units, const GroupPair* pairs, const int32_t* off, int n_pairs,
+                         int n_blocks, int max_bins, const int32_t* round, void* stream) {
+  if (n_pairs == 0) return 0;
+  k_group_overlap<<<n_blocks, 256, sizeof(unsigned int) * (size_t)max_bins, (cudaStream_t)stream>>>(units, pairs, off,
+                                                                                                      n_pairs, round);
+  return (int)cudaGetLastError();
+}
+
+int launch_group_advance(int32_t* round, void* stream) {
+  k_group_advance<<<1, 1, 0, (cudaStream_t)stream>>>(round);
   return (int)cudaGetLastError();
 }
 

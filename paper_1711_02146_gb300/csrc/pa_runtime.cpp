@@ -2163,3 +2163,277 @@ int pa_shard_destroy(pa_shard* s) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- batch rounds
+//
+// The runs of a batch that qualify (+-1 couplings, an explicit schedule, a
+// shared-memory sweep) advance together: a round takes each of them one step, as
+// one reweighting launch for all their populations, one resampling launch, one
+// sweep launch per (L, launch shape), one overlap launch for the two-population
+// runs and a one-thread launch that advances the round counter.  Every launch
+// reads its units' steps from device tables built here, so one CUDA graph,
+// captured once, serves every round.  Each run's results are those of pa_step:
+// the kernels of a round do for every unit what a lone run's launches do for it.
+
+namespace pa {
+
+struct Group {
+  std::vector<pa_ctx*> runs;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  std::vector<char> image;  // host copy of the device tables (kept until the copy is done)
+  char* dev = nullptr;
+  int32_t* round = nullptr;
+  GroupUnit* units = nullptr;
+  int32_t* res_off = nullptr;
+  GroupPair* pairs = nullptr;
+  int32_t* pair_off = nullptr;
+  struct SweepLaunch {
+    int L, shape, n, n_blocks;
+    int32_t* list;
+    int32_t* off;
+  };
+  std::vector<SweepLaunch> sweeps;
+  int n_units = 0, res_blocks = 0, n_pairs = 0, pair_blocks = 0, max_levels = 0, max_bins = 0, n_rounds = 0;
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches_per_round = 0;
+  // the sweeps of different (L, shape) are parallel branches of the round's graph
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> join;
+};
+
+int64_t run_kernel_launches(const pa_ctx* c) { return c ? c->stats.kernel_launches : 0; }
+
+bool group_eligible(const pa_ctx* c) {
+  return c && c->model == PA_MODEL_PM1 && !c->adaptive && sweep_supported(c->g.L) && !c->g.shard &&
+         c->error == PA_OK && !c->done;
+}
+
+void group_destroy(Group* G) {
+  if (!G) return;
+  if (G->stream) cudaStreamSynchronize(G->stream);
+  if (G->exec) cudaGraphExecDestroy(G->exec);
+  if (G->dev) cudaFreeAsync(G->dev, G->stream);
+  if (G->stream) {
+    cudaStreamSynchronize(G->stream);
+    cudaStreamDestroy(G->stream);
+  }
+  if (G->ev) cudaEventDestroy(G->ev);
+  for (cudaStream_t x : G->side) cudaStreamDestroy(x);
+  for (cudaEvent_t e : G->join) cudaEventDestroy(e);
+  delete G;
+}
+
+namespace {
+
+// Offsets of the device tables within one allocation (16-byte aligned).
+struct Layout {
+  size_t bytes = 0;
+  size_t take(size_t n) {
+    const size_t at = (bytes + 15) & ~(size_t)15;
+    bytes = at + n;
+    return at;
+  }
+};
+
+int group_build(Group* G) {
+  const int n_runs = (int)G->runs.size();
+  Layout lay;
+  const size_t at_round = lay.take(sizeof(int32_t));
+  std::vector<size_t> at_steps((size_t)n_runs);
+  std::vector<int> first_unit((size_t)n_runs);
+  for (int i = 0; i < n_runs; ++i) {
+    const pa_ctx* c = G->runs[(size_t)i];
+    at_steps[(size_t)i] = lay.take(sizeof(GroupStep) * (size_t)c->cfg.n_temps);
+    first_unit[(size_t)i] = G->n_units;
+    G->n_units += c->g.n_pop;
+    if (c->g.n_pop == 2) ++G->n_pairs;
+    G->max_levels = std::max(G->max_levels, c->g.n_levels);
+    if (c->g.n_pop == 2) G->max_bins = std::max(G->max_bins, c->g.q_bins);
+    G->n_rounds = std::max(G->n_rounds, c->cfg.n_temps - 1 - c->t);
+  }
+  const size_t at_units = lay.take(sizeof(GroupUnit) * (size_t)G->n_units);
+  const size_t at_res = lay.take(sizeof(int32_t) * ((size_t)G->n_units + 1));
+  const size_t at_pairs = lay.take(sizeof(GroupPair) * (size_t)std::max(G->n_pairs, 1));
+  const size_t at_poff = lay.take(sizeof(int32_t) * ((size_t)G->n_pairs + 1));
+  // sweep launches: the units of each (L, shape), in batch order
+  std::map<std::pair<int, int>, std::vector<int32_t>> by_shape;
+  for (int i = 0; i < n_runs; ++i) {
+    const pa_ctx* c = G->runs[(size_t)i];
+    for (int p = 0; p < c->g.n_pop; ++p) by_shape[{c->g.L, c->g.sweep_shape}].push_back(first_unit[(size_t)i] + p);
+  }
+  std::vector<std::pair<size_t, size_t>> at_sweep;
+  for (const auto& kv : by_shape) {
+    const size_t n = kv.second.size();
+    at_sweep.emplace_back(lay.take(sizeof(int32_t) * n), lay.take(sizeof(int32_t) * (n + 1)));
+  }
+  G->image.assign(lay.bytes, 0);
+  int rc = cuda_status(cudaMallocAsync(reinterpret_cast<void**>(&G->dev), lay.bytes, G->stream));
+  if (rc != PA_OK) return rc;
+  char* img = G->image.data();
+  char* dev = G->dev;
+  G->round = reinterpret_cast<int32_t*>(dev + at_round);
+  G->units = reinterpret_cast<GroupUnit*>(dev + at_units);
+  G->res_off = reinterpret_cast<int32_t*>(dev + at_res);
+  G->pairs = reinterpret_cast<GroupPair*>(dev + at_pairs);
+  G->pair_off = reinterpret_cast<int32_t*>(dev + at_poff);
+  GroupUnit* units = reinterpret_cast<GroupUnit*>(img + at_units);
+  int32_t* res_off = reinterpret_cast<int32_t*>(img + at_res);
+  GroupPair* pairs = reinterpret_cast<GroupPair*>(img + at_pairs);
+  int32_t* pair_off = reinterpret_cast<int32_t*>(img + at_poff);
+  int k = 0, q = 0;
+  res_off[0] = 0;
+  pair_off[0] = 0;
+  for (int i = 0; i < n_runs; ++i) {
+    const pa_ctx* c = G->runs[(size_t)i];
+    GroupStep* steps = reinterpret_cast<GroupStep*>(img + at_steps[(size_t)i]);
+    for (int t = c->t + 1; t < c->cfg.n_temps; ++t) {
+      const double dbeta = c->betas[(size_t)t] - c->betas[(size_t)t - 1];
+      auto it = c->wtables.find(bits_of(dbeta));
+      if (it == c->wtables.end()) return PA_ERR_INVALID;
+      steps[t].w = it->second;
+      metropolis_thresholds(c->betas[(size_t)t], steps[t].thr);
+      steps[t].n_sweeps = c->sweeps[(size_t)t];
+    }
+    for (int p = 0; p < c->g.n_pop; ++p, ++k) {
+      GroupUnit& u = units[k];
+      u.g = c->g;
+      u.P = c->pops[p];
+      u.jtab = c->jtab;
+      u.status = c->status;
+      u.steps = reinterpret_cast<const GroupStep*>(dev + at_steps[(size_t)i]);
+      u.t0 = c->t;
+      u.cur0 = c->cur;
+      u.last_t = c->cfg.n_temps - 1;
+      u.pop = p;
+      res_off[k + 1] = res_off[k] + (int32_t)((c->g.R_cap + kResampleSlotsPerBlock - 1) / kResampleSlotsPerBlock);
+    }
+    if (c->g.n_pop == 2) {
+      pairs[q] = GroupPair{first_unit[(size_t)i], first_unit[(size_t)i] + 1, c->qhist};
+      pair_off[q + 1] = pair_off[q] + (int32_t)((c->g.pitch / 4 + 255) / 256);
+      ++q;
+    }
+  }
+  G->res_blocks = res_off[G->n_units];
+  G->pair_blocks = pair_off[G->n_pairs];
+  size_t s = 0;
+  for (const auto& kv : by_shape) {
+    const int L = kv.first.first, shape = kv.first.second, tj = sweep_tile_slots(L, shape);
+    if (tj <= 0) return PA_ERR_INVALID;
+    const int n = (int)kv.second.size();
+    int32_t* list = reinterpret_cast<int32_t*>(img + at_sweep[s].first);
+    int32_t* off = reinterpret_cast<int32_t*>(img + at_sweep[s].second);
+    off[0] = 0;
+    for (int j = 0; j < n; ++j) {
+      list[j] = kv.second[(size_t)j];
+      off[j + 1] = off[j] + (int32_t)((units[list[j]].g.R_cap + tj - 1) / tj);
+    }
+    G->sweeps.push_back({L, shape, n, off[n], reinterpret_cast<int32_t*>(dev + at_sweep[s].first),
+                         reinterpret_cast<int32_t*>(dev + at_sweep[s].second)});
+    ++s;
+  }
+  return cuda_status(cudaMemcpyAsync(G->dev, img, lay.bytes, cudaMemcpyHostToDevice, G->stream));
+}
+
+// The launches of one round, captured into the group's graph: reweighting and
+// resampling, then the sweeps of each (L, shape) as parallel branches (their last
+// waves overlap), then the overlaps and the round counter.
+int group_round(Group* G) {
+  int rc = launch_rc(launch_group_reweight(G->units, G->n_units, G->max_levels, G->round, G->stream));
+  if (rc == PA_OK)
+    rc = launch_rc(launch_group_resample(G->units, G->res_off, G->n_units, G->res_blocks, G->round, G->stream));
+  if (rc == PA_OK && !G->side.empty()) rc = cuda_status(cudaEventRecord(G->join[0], G->stream));
+  for (size_t i = 0; i < G->sweeps.size() && rc == PA_OK; ++i) {
+    const auto& sw = G->sweeps[i];
+    cudaStream_t s = i == 0 ? G->stream : G->side[i - 1];
+    if (i > 0) rc = cuda_status(cudaStreamWaitEvent(s, G->join[0], 0));
+    if (rc == PA_OK)
+      rc = launch_rc(launch_group_sweep(sw.L, sw.shape, G->units, sw.list, sw.off, sw.n, sw.n_blocks, G->round, s));
+    if (rc == PA_OK && i > 0) rc = cuda_status(cudaEventRecord(G->join[i], s));
+  }
+  for (size_t i = 1; i < G->sweeps.size() && rc == PA_OK; ++i)
+    rc = cuda_status(cudaStreamWaitEvent(G->stream, G->join[i], 0));
+  if (rc == PA_OK && G->n_pairs > 0)
+    rc = launch_rc(launch_group_overlap(G->units, G->pairs, G->pair_off, G->n_pairs, G->pair_blocks, G->max_bins,
+                                        G->round, G->stream));
+  if (rc == PA_OK) rc = launch_rc(launch_group_advance(G->round, G->stream));
+  return rc;
+}
+
+}  // namespace
+
+int group_create(pa_ctx* const* runs, int n, Group** out) {
+  *out = nullptr;
+  Group* G = new (std::nothrow) Group();
+  if (!G) return PA_ERR_NOMEM;
+  G->runs.assign(runs, runs + n);
+  int rc = cuda_status(cudaStreamCreateWithFlags(&G->stream, cudaStreamNonBlocking));
+  if (rc == PA_OK) rc = cuda_status(cudaEventCreateWithFlags(&G->ev, cudaEventDisableTiming));
+  // the group starts after everything already issued on the runs' own streams
+  for (pa_ctx* c : G->runs) {
+    if (rc != PA_OK) break;
+    rc = cuda_status(cudaEventRecord(G->ev, c->stream));
+    if (rc == PA_OK) rc = cuda_status(cudaStreamWaitEvent(G->stream, G->ev, 0));
+  }
+  if (rc == PA_OK) rc = group_build(G);
+  for (size_t i = 0; i < G->sweeps.size() && rc == PA_OK; ++i) {
+    cudaEvent_t e = nullptr;
+    rc = cuda_status(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    if (rc == PA_OK) G->join.push_back(e);
+    if (rc == PA_OK && i > 0) {
+      cudaStream_t x = nullptr;
+      rc = cuda_status(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+      if (rc == PA_OK) G->side.push_back(x);
+    }
+  }
+  // shared-memory limits of the sweep kernels are set before the capture
+  for (const auto& sw : G->sweeps)
+    if (rc == PA_OK)
+      rc = launch_rc(launch_group_sweep(sw.L, sw.shape, G->units, sw.list, sw.off, sw.n, 0, G->round, G->stream));
+  if (rc == PA_OK && G->n_rounds > 0) {
+    cudaGraph_t graph = nullptr;
+    rc = cuda_status(cudaStreamBeginCapture(G->stream, cudaStreamCaptureModeRelaxed));
+    if (rc == PA_OK) {
+      const int rr = group_round(G);
+      const int re = cuda_status(cudaStreamEndCapture(G->stream, &graph));
+      rc = rr != PA_OK ? rr : re;
+    }
+    if (rc == PA_OK) rc = cuda_status(cudaGraphInstantiate(&G->exec, graph, 0));
+    if (graph) cudaGraphDestroy(graph);
+    G->launches_per_round = 3 + (int64_t)G->sweeps.size() + (G->n_pairs > 0 ? 1 : 0);
+  }
+  if (rc != PA_OK) {
+    group_destroy(G);
+    return rc;
+  }
+  *out = G;
+  return PA_OK;
+}
+
+int group_run(Group* G, int64_t* kernel_launches, int64_t* graph_launches) {
+  int rc = PA_OK;
+  for (int r = 0; r < G->n_rounds && rc == PA_OK; ++r) {
+    rc = cuda_status(cudaGraphLaunch(G->exec, G->stream));
+    if (rc == PA_OK) {
+      *kernel_launches += G->launches_per_round;
+      *graph_launches += 1;
+    }
+  }
+  if (rc != PA_OK) return rc;
+  // later work on a run's own stream (observables, further steps) follows the rounds
+  rc = cuda_status(cudaEventRecord(G->ev, G->stream));
+  for (pa_ctx* c : G->runs)
+    if (rc == PA_OK) rc = cuda_status(cudaStreamWaitEvent(c->stream, G->ev, 0));
+  if (rc != PA_OK) return rc;
+  for (pa_ctx* c : G->runs) {
+    const int k = c->cfg.n_temps - 1 - c->t;
+    for (int t = c->t + 1; t <= c->t + k; ++t) c->counted_steps.emplace_back(t, c->sweeps[(size_t)t]);
+    c->stats.steps += k;
+    c->cur ^= (k & 1);
+    c->t += k;
+    c->done = true;
+  }
+  return PA_OK;
+}
+
+}  // namespace pa

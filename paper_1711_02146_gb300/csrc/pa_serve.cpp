@@ -86,6 +86,8 @@ int server_priority_level(const pa_config& c, int n_levels) {
 struct pa_batch {
   std::vector<pa_ctx*> ctx;
   std::vector<cudaStream_t> streams;
+  int32_t mode = PA_BATCH_FUSED;
+  int64_t kernel_launches = 0, graph_launches = 0;
 };
 
 struct pa_server {
@@ -151,24 +153,62 @@ int pa_batch_create(const pa_config* cfgs, int32_t n, pa_batch** out) {
 
 int pa_batch_run(pa_batch* b) {
   if (!b) return PA_ERR_INVALID;
+  // fused mode: the runs that qualify advance by rounds of one graph launch each
+  // (issued at once, asynchronously); the others step on their own streams meanwhile
+  std::vector<pa_ctx*> fused;
   std::vector<char> live(b->ctx.size(), 1);
-  size_t n_live = b->ctx.size();
-  while (n_live > 0) {
+  if (b->mode == PA_BATCH_FUSED)
+    for (size_t i = 0; i < b->ctx.size(); ++i)
+      if (pa::group_eligible(b->ctx[i])) {
+        fused.push_back(b->ctx[i]);
+        live[i] = 0;
+      }
+  pa::Group* grp = nullptr;
+  if (!fused.empty()) {
+    int rc = pa::group_create(fused.data(), (int)fused.size(), &grp);
+    if (rc == PA_OK) rc = pa::group_run(grp, &b->kernel_launches, &b->graph_launches);
+    if (rc != PA_OK) {
+      pa::group_destroy(grp);
+      return rc;
+    }
+  }
+  size_t n_live = 0;
+  for (char l : live) n_live += l ? 1 : 0;
+  std::vector<int64_t> before(b->ctx.size(), 0);
+  for (size_t i = 0; i < b->ctx.size(); ++i) before[i] = pa::run_kernel_launches(b->ctx[i]);
+  int rc = PA_OK;
+  while (n_live > 0 && rc == PA_OK) {
     for (size_t i = 0; i < b->ctx.size(); ++i) {
       if (!live[i]) continue;
-      const int rc = pa_step(b->ctx[i]);
-      if (rc == PA_DONE) {
+      const int r = pa_step(b->ctx[i]);
+      if (r == PA_DONE) {
         live[i] = 0;
         --n_live;
-      } else if (rc != PA_OK) {
-        return rc;
+      } else if (r != PA_OK) {
+        rc = r;
+        break;
       }
     }
   }
   for (pa_ctx* c : b->ctx) {
-    const int rc = pa_sync(c);
-    if (rc != PA_OK) return rc;
+    const int r = pa_sync(c);
+    if (rc == PA_OK && r != PA_OK) rc = r;
   }
+  for (size_t i = 0; i < b->ctx.size(); ++i) b->kernel_launches += pa::run_kernel_launches(b->ctx[i]) - before[i];
+  pa::group_destroy(grp);
+  return rc;
+}
+
+int pa_batch_set_mode(pa_batch* b, int32_t mode) {
+  if (!b || (mode != PA_BATCH_FUSED && mode != PA_BATCH_STREAMS)) return PA_ERR_INVALID;
+  b->mode = mode;
+  return PA_OK;
+}
+
+int pa_batch_launches(const pa_batch* b, int64_t* kernel_launches, int64_t* graph_launches) {
+  if (!b || !kernel_launches || !graph_launches) return PA_ERR_INVALID;
+  *kernel_launches = b->kernel_launches;
+  *graph_launches = b->graph_launches;
   return PA_OK;
 }
 

@@ -720,19 +720,16 @@ __device__ __forceinline__ void tile_families(const SweepArgs& a, int* sh, int t
   family_entropy_last(a.pop, &a.pop.rec[a.t], R_new, participants, tid, NT, red);
 }
 
-// Bit-sliced sweep kernel (+-1 couplings).
+// One tile of the bit-sliced sweep (+-1 couplings): the slots tile0 .. tile0 + TJ - 1
+// of the new population (R_new slots), in the dynamic shared memory sm.
 template <int L, int W, int NT, int MB>
-__global__ void __launch_bounds__(NT, MB) k_sweep(const __grid_constant__ SweepArgs a) {
+__device__ __forceinline__ void sweep_tile(const SweepArgs& a, uint32_t* sm, int tile0, int R_new) {
   using S = BitShape<L, W, NT, MB>;
   constexpr int N = S::N, NP = S::NP, TJ = S::TJ;
-  extern __shared__ __align__(16) uint32_t sm[];
   uint32_t* sp = sm;                                               // spins [N][W]
   SiteRec* recs = reinterpret_cast<SiteRec*>(sm + (size_t)N * W);  // [N]
   Deferred* queues = reinterpret_cast<Deferred*>(recs + N);        // [NQ][kQueueCap]
   int* slots = reinterpret_cast<int*>(queues + S::NQ * kQueueCap);  // [33 W]: parents, then level counts
-  const int R_new = a.pop.rec[a.t].R_tilde;
-  const int tile0 = a.tile_base + blockIdx.x * TJ;
-  if (tile0 >= R_new) return;
   const int tid = threadIdx.x, word = tid % W, part = tid / W;
   Deferred* dq = queues + (S::DEFER ? (tid >> 5) * kQueueCap : 0);
   init_tables<L>(a, recs, tid, NT);
@@ -777,6 +774,108 @@ __global__ void __launch_bounds__(NT, MB) k_sweep(const __grid_constant__ SweepA
   if (!a.fam) return;
   __syncthreads();  // every shared array is dead now: the family pass takes the space
   tile_families<TJ, NT>(a, reinterpret_cast<int*>(sm), tile0, R_new, tid);
+}
+
+// Bit-sliced sweep kernel (+-1 couplings): one tile per CTA.
+template <int L, int W, int NT, int MB>
+__global__ void __launch_bounds__(NT, MB) k_sweep(const __grid_constant__ SweepArgs a) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  const int R_new = a.pop.rec[a.t].R_tilde;
+  const int tile0 = a.tile_base + blockIdx.x * BitShape<L, W, NT, MB>::TJ;
+  if (tile0 >= R_new) return;
+  sweep_tile<L, W, NT, MB>(a, sm, tile0, R_new);
+}
+
+// The sweep arguments of population P at step t from buffer cur with thresholds
+// thr (dE = 4, 8, 12), as launch_sweep sets them for a run of one launch.
+__host__ __device__ inline void fill_sweep_args(SweepArgs& a, const PopDev& P, const uint32_t* jtab, int64_t pitch,
+                                                int n_levels, int t, int cur, int n_sweeps, int tj,
+                                                const uint32_t thr[3]) {
+  a.pop = P;
+  uint32_t k0 = P.key_met[0], k1 = P.key_met[1];
+  for (int r = 0; r < 10; ++r) {
+    a.k0[r] = k0;
+    a.k1[r] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  a.jtab = jtab;
+  a.pitch = pitch;
+  a.n_levels = n_levels;
+  a.t = t;
+  a.cur = cur;
+  a.n_sweeps = n_sweeps;
+  a.slot_base = 0;
+  a.fam = 1;
+  a.tile_base = 0;
+  a.split = 0x7fffffff;
+  a.tj_main = tj;
+  a.tj_tail = tj;
+  a.thr4 = thr[0];
+  a.thr8 = thr[1];
+  a.thr12 = thr[2];
+  const uint32_t thr_u[3] = {thr[2], thr[1], thr[0]};  // u = 0, 1, 2: dE = 12, 8, 4
+  for (int p = 0; p < 32; ++p) {
+    uint32_t T[3];
+    for (int u = 0; u < 3; ++u) T[u] = ((thr_u[u] >> (31 - p)) & 1u) ? ~0u : 0u;
+    a.tm[p][0] = T[0];
+    a.tm[p][1] = T[0] ^ T[1];
+    a.tm[p][2] = T[0] ^ T[2];
+    a.tm[p][3] = 0u;
+  }
+  uint32_t live[3];
+  for (int u = 0; u < 3; ++u) live[u] = thr_u[u] ? ~0u : 0u;
+  a.live[0] = live[0];
+  a.live[1] = live[0] ^ live[1];
+  a.live[2] = live[0] ^ live[2];
+  a.live[3] = 0u;
+}
+
+// The sweeps of a batch's units of one lattice size and launch shape: unit list[k]
+// takes the CTAs off[k] .. off[k+1]-1, one tile each; each CTA builds its unit's
+// arguments for the round's step in shared memory.
+template <int L, int W, int NT, int MB>
+__global__ void __launch_bounds__(NT, MB)
+    k_sweep_group(const GroupUnit* __restrict__ units, const int32_t* __restrict__ list,
+                  const int32_t* __restrict__ off, int n, const int32_t* __restrict__ round) {
+  constexpr int TJ = BitShape<L, W, NT, MB>::TJ;
+  extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ SweepArgs sa;
+  __shared__ int hdr[3];  // unit, tile0, R_new (tile0 < 0: nothing to do)
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = n - 1;
+    const int b = (int)blockIdx.x;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (off[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    const GroupUnit& u = units[list[lo]];
+    const int r = *round, t = u.t0 + 1 + r;
+    const int tile0 = (b - off[lo]) * TJ;
+    const int R_new = t <= u.last_t ? u.P.rec[t].R_tilde : 0;
+    hdr[0] = list[lo];
+    hdr[1] = tile0 < R_new ? tile0 : -1;
+    hdr[2] = R_new;
+    if (tile0 < R_new) {
+      const GroupStep& st = u.steps[t];
+      fill_sweep_args(sa, u.P, u.jtab, u.g.pitch, u.g.n_levels, t, u.cur0 ^ (r & 1), st.n_sweeps, TJ, st.thr);
+    }
+  }
+  __syncthreads();
+  if (hdr[1] < 0) return;
+  sweep_tile<L, W, NT, MB>(sa, sm, hdr[1], hdr[2]);
+}
+
+template <int L, int W, int NT, int MB>
+static int launch_group_t(const GroupUnit* units, const int32_t* list, const int32_t* off, int n, int n_blocks,
+                          const int32_t* round, cudaStream_t s) {
+  using S = BitShape<L, W, NT, MB>;
+  static std::atomic<int> done[64];
+  const cudaError_t e = smem_limit_once(k_sweep_group<L, W, NT, MB>, (int)S::SMEM, done);
+  if (e != cudaSuccess) return (int)e;
+  if (n_blocks <= 0) return 0;
+  k_sweep_group<L, W, NT, MB><<<n_blocks, NT, S::SMEM, s>>>(units, list, off, n, round);
+  return (int)cudaGetLastError();
 }
 
 // ---- Gaussian couplings (§II.A): nibble tiles (eight replicas per word, four
@@ -949,8 +1048,10 @@ struct ShapeEntry {
   int L, W, NT, MB;
   size_t smem;
   int (*launch)(const RunGeom&, const SweepArgs&, cudaStream_t);
+  int (*launch_group)(const GroupUnit*, const int32_t*, const int32_t*, int, int, const int32_t*, cudaStream_t);
 };
-#define PA_SHAPE(L, W, NT, MB) {L, W, NT, MB, BitShape<L, W, NT, MB>::SMEM, &launch_t<L, W, NT, MB>}
+#define PA_SHAPE(L, W, NT, MB) \
+  {L, W, NT, MB, BitShape<L, W, NT, MB>::SMEM, &launch_t<L, W, NT, MB>, &launch_group_t<L, W, NT, MB>}
 const ShapeEntry kShapes[] = {
     PA_SHAPE(2, 32, 128, 1),   PA_SHAPE(2, 32, 64, 2),
     PA_SHAPE(4, 32, 256, 2),   PA_SHAPE(4, 32, 128, 4),  PA_SHAPE(4, 32, 512, 1),  PA_SHAPE(4, 8, 128, 4),
@@ -997,47 +1098,14 @@ int launch_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, 
   cudaStream_t s = (cudaStream_t)stream;
   const ShapeEntry* shape = shape_of(g.L, g.sweep_shape);
   if (!shape) return (int)cudaErrorInvalidValue;
+  const ShapeEntry* tail = g.tail_shape >= 0 ? shape_of(g.L, g.tail_shape) : nullptr;
   for (int i = 0; i < g.n_pop; ++i) {
     SweepArgs args;
-    args.pop = pops[i];
-    uint32_t k0 = pops[i].key_met[0], k1 = pops[i].key_met[1];
-    for (int r = 0; r < 10; ++r) {
-      args.k0[r] = k0;
-      args.k1[r] = k1;
-      k0 += 0x9E3779B9u;
-      k1 += 0xBB67AE85u;
-    }
-    args.jtab = jtab;
-    args.pitch = g.pitch;
-    args.n_levels = g.n_levels;
-    args.t = t;
-    args.cur = cur;
-    args.n_sweeps = n_sweeps;
+    fill_sweep_args(args, pops[i], jtab, g.pitch, g.n_levels, t, cur, n_sweeps, 32 * shape->W, met_thr);
     args.slot_base = g.slot_base;
     args.fam = g.shard ? 0 : 1;
-    const ShapeEntry* tail = g.tail_shape >= 0 ? shape_of(g.L, g.tail_shape) : nullptr;
-    args.tile_base = 0;
     args.split = tail ? g.tail_from : 0x7fffffff;
-    args.tj_main = 32 * shape->W;
     args.tj_tail = tail ? 32 * tail->W : 32 * shape->W;
-    args.thr4 = met_thr[0];
-    args.thr8 = met_thr[1];
-    args.thr12 = met_thr[2];
-    const uint32_t thr_u[3] = {met_thr[2], met_thr[1], met_thr[0]};  // u = 0, 1, 2: dE = 12, 8, 4
-    for (int p = 0; p < 32; ++p) {
-      uint32_t T[3];
-      for (int u = 0; u < 3; ++u) T[u] = ((thr_u[u] >> (31 - p)) & 1u) ? ~0u : 0u;
-      args.tm[p][0] = T[0];
-      args.tm[p][1] = T[0] ^ T[1];
-      args.tm[p][2] = T[0] ^ T[2];
-      args.tm[p][3] = 0u;
-    }
-    uint32_t live[3];
-    for (int u = 0; u < 3; ++u) live[u] = thr_u[u] ? ~0u : 0u;
-    args.live[0] = live[0];
-    args.live[1] = live[0] ^ live[1];
-    args.live[2] = live[0] ^ live[2];
-    args.live[3] = 0u;
     int e = shape->launch(g, args, s);
     if (e == 0 && tail) {
       args.tile_base = g.tail_from;
@@ -1046,6 +1114,18 @@ int launch_sweep(const RunGeom& g, PopDev* pops, int cur, const uint32_t* jtab, 
     if (e != 0) return e;
   }
   return 0;
+}
+
+int sweep_tile_slots(int L, int shape) {
+  const ShapeEntry* e = shape_of(L, shape);
+  return e ? 32 * e->W : 0;
+}
+
+int launch_group_sweep(int L, int shape, const GroupUnit* units, const int32_t* list, const int32_t* off, int n,
+                       int n_blocks, const int32_t* round, void* stream) {
+  const ShapeEntry* e = shape_of(L, shape);
+  if (!e || n <= 0) return (int)cudaErrorInvalidValue;
+  return e->launch_group(units, list, off, n, n_blocks, round, (cudaStream_t)stream);
 }
 
 void sweep_tail_plan(int L, int shape, int64_t R, int n_sm, int32_t* tail_shape, int32_t* tail_from) {

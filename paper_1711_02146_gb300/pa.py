@@ -54,6 +54,7 @@ class Config(ctypes.Structure):
 
 
 PA_MODEL_PM1, PA_MODEL_GAUSS = 0, 1
+PA_BATCH_FUSED, PA_BATCH_STREAMS = 0, 1
 
 
 class GObs(ctypes.Structure):
@@ -183,6 +184,8 @@ SIGNATURES = {
     "pa_batch_run": (ctypes.c_int, [_vp]),
     "pa_batch_ctx": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(_vp)]),
     "pa_batch_destroy": (ctypes.c_int, [_vp]),
+    "pa_batch_set_mode": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "pa_batch_launches": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "pa_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_vp)]),
     "pa_server_submit": (ctypes.c_int, [_vp, ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_uint64)]),
     "pa_server_poll": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
@@ -360,9 +363,13 @@ class _View:
 
 
 class Batch:
-    """Many independent runs advanced together on their own streams (pa_batch)."""
+    """Many independent runs advanced together (pa_batch): by default in rounds of one
+    CUDA graph launch for all runs that qualify (``mode="fused"``), or each run on its
+    own stream (``mode="streams"``)."""
 
-    def __init__(self, workloads):
+    MODES = {"fused": PA_BATCH_FUSED, "streams": PA_BATCH_STREAMS}
+
+    def __init__(self, workloads, mode: str = "fused"):
         self.workloads = list(workloads)
         self._holders = [_ConfigHolder.from_workload(w) for w in self.workloads]
         arr = (Config * len(self._holders))(*[h.cfg for h in self._holders])
@@ -370,9 +377,16 @@ class Batch:
         h = _vp()
         _check("pa_batch_create", lib().pa_batch_create(arr, len(self._holders), ctypes.byref(h)))
         self._h = h
+        _check("pa_batch_set_mode", lib().pa_batch_set_mode(self._h, self.MODES[mode]))
 
     def run(self) -> None:
         _check("pa_batch_run", lib().pa_batch_run(self._h))
+
+    def launches(self) -> dict:
+        """Kernels and CUDA graphs launched by run() so far."""
+        k, g = ctypes.c_int64(), ctypes.c_int64()
+        _check("pa_batch_launches", lib().pa_batch_launches(self._h, ctypes.byref(k), ctypes.byref(g)))
+        return {"kernels": k.value, "graphs": g.value}
 
     def run_view(self, i: int) -> "Run":
         v = _vp()

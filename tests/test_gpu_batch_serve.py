@@ -39,25 +39,73 @@ def standalone(pa, w):
     return r
 
 
-def assert_same_run(a, b, w):
+def assert_same_run(a, b, w, every_step=False):
     t = a.t
     assert b.t == t
+    for u in (range(t + 1) if every_step else (t,)):
+        for pop in range(w.n_pop):
+            assert a.obs(u, pop) == b.obs(u, pop), f"{w.name} t={u} pop {pop}"
+            assert np.array_equal(a.energy_hist(u, pop), b.energy_hist(u, pop)), f"{w.name} t={u}"
+        if w.n_pop == 2:
+            assert np.array_equal(a.q_hist(u), b.q_hist(u)), f"{w.name} t={u}"
     for pop in range(w.n_pop):
-        assert a.obs(t, pop) == b.obs(t, pop)
         sa, la, ea = a.population(pop)
         sb, lb, eb = b.population(pop)
         assert np.array_equal(sa, sb) and np.array_equal(la, lb) and np.array_equal(ea, eb)
-        assert np.array_equal(a.energy_hist(t, pop), b.energy_hist(t, pop))
-    if w.n_pop == 2:
-        assert np.array_equal(a.q_hist(t), b.q_hist(t))
+        assert np.array_equal(a.copy_counts(pop), b.copy_counts(pop))
 
 
-def test_batch_matches_standalone_runs(pa):
+@pytest.mark.parametrize("mode", ["fused", "streams"])
+def test_batch_matches_standalone_runs(pa, mode):
     ws = mixed_workloads(9)
-    batch = pa.Batch(ws)
+    batch = pa.Batch(ws, mode=mode)
     batch.run()
     for i, w in enumerate(ws):
-        assert_same_run(batch.run_view(i), standalone(pa, w), w)
+        assert_same_run(batch.run_view(i), standalone(pa, w), w, every_step=True)
+    n = batch.launches()
+    if mode == "fused":   # 11 rounds (the longest schedule), one graph launch each
+        rounds = max(len(w.betas) for w in ws) - 1
+        assert n["graphs"] == rounds and n["kernels"] == rounds * (3 + 4 + 1)
+    else:
+        assert n["graphs"] == 0 and n["kernels"] > 0
+    batch.close()
+
+
+def test_fused_batch_every_size_and_shape(pa):
+    """The fused rounds with every lattice size of the shared-memory sweep,
+    populations of many tiles and many resampling blocks, two-population runs, schedules of different lengths (runs
+    that finish early rest), a run already stepped alone before the batch runs, and
+    runs that do not qualify (Gaussian couplings, an adaptive schedule, L = 18) beside
+    them: every run, every step, exactly as alone."""
+    ws = [Workload("a4", L=4, R=5000, disorder_seed=11, run_seed=12, betas=linear_betas(9, 3.0), n_sweeps=2),
+          Workload("a6", L=6, R=20000, disorder_seed=13, run_seed=14, betas=linear_betas(5, 1.5), n_sweeps=1),
+          Workload("a8p", L=8, R=9000, disorder_seed=15, run_seed=16, betas=linear_betas(7, 2.0), n_sweeps=2,
+                   n_pop=2),
+          Workload("a10", L=10, R=30000, disorder_seed=17, run_seed=18, betas=linear_betas(4, 1.0), n_sweeps=1),
+          Workload("a12", L=12, R=3000, disorder_seed=19, run_seed=20, betas=linear_betas(6, 2.5), n_sweeps=1),
+          Workload("a14", L=14, R=1500, disorder_seed=21, run_seed=22, betas=linear_betas(3, 1.0), n_sweeps=1),
+          Workload("a16", L=16, R=1100, disorder_seed=23, run_seed=24, betas=linear_betas(3, 0.6), n_sweeps=1,
+                   n_pop=2),
+          Workload("a10b", L=10, R=700, disorder_seed=25, run_seed=26, betas=linear_betas(8, 4.0), n_sweeps=3),
+          Workload("ga", L=6, R=800, disorder_seed=27, run_seed=28, betas=linear_betas(5, 2.0), n_sweeps=2, model=1),
+          Workload("ad", L=6, R=2000, disorder_seed=29, run_seed=30, betas=None, beta_max=2.0, eps_target=0.3,
+                   n_temps=60, n_sweeps=2),
+          Workload("g18", L=18, R=600, disorder_seed=31, run_seed=32, betas=linear_betas(3, 0.8), n_sweeps=1)]
+    batch = pa.Batch(ws)
+    batch.run_view(1).step()   # a6 starts the rounds at t = 1
+    batch.run()
+    for i, w in enumerate(ws):
+        a, b = batch.run_view(i), standalone(pa, w)
+        if w.model == 1:
+            t = a.t
+            assert b.t == t
+            for x, y in zip(a.population(0), b.population(0)):
+                assert np.array_equal(x, y)
+            assert a.gobs(t) == b.gobs(t)
+        else:
+            assert_same_run(a, b, w, every_step=True)
+    n = batch.launches()
+    assert n["graphs"] == 8   # a4: 8 steps
     batch.close()
 
 

@@ -1,14 +1,15 @@
 """The headline schedules run to their end on the GPU beside the oracle (§II, §IV.B).
 
 The full-size workloads are checked elsewhere on sampled steps; here the whole
-schedule runs, with the population reduced so that the oracle finishes in about a
-minute, so that the late steps (large beta, few occupied levels, heavy culling,
+schedule runs, with the population reduced so that the oracle finishes in a few
+minutes, so that the late steps (large beta, few occupied levels, heavy culling,
 large families) are compared too:
 
 * L = 10, adaptive schedule holding the culling fraction at 0.272 up to beta = 5,
-  10 sweeps per step (the L = 10 workload), R = 5000;
+  10 sweeps per step (the L = 10 workload), R = 20000 (about 70 steps, a few
+  minutes of oracle time);
 * L = 8, two populations, 201 linear temperatures to beta = 5, 10 sweeps (the
-  overlap workload), R = 2000 per population.
+  overlap workload), R = 5000 per population.
 
 Every step: beta_t bit for bit, the energy histogram and (two populations) the
 overlap histogram bit for bit, every observable (integers exactly, FP64 to 1e-12
@@ -20,7 +21,7 @@ import pytest
 
 from test_gpu_parity import assert_obs_equal, assert_state_equal
 
-pytestmark = pytest.mark.gpu
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 
 @pytest.fixture(scope="module")
@@ -70,7 +71,7 @@ def run_in_lockstep(pa, oracle_lib, w):
 
 def test_l10_adaptive_schedule_to_beta_5(pa, oracle_lib):
     from paper_1711_02146_gb300.workloads import C3
-    w = C3.with_(R=5000)
+    w = C3.with_(R=20000)
     gpu, ref, T = run_in_lockstep(pa, oracle_lib, w)
     assert gpu.beta(T) == w.beta_max and T > 40
     o = gpu.obs(T)
@@ -83,6 +84,6 @@ def test_l10_adaptive_schedule_to_beta_5(pa, oracle_lib):
 
 def test_l8_two_populations_201_temperatures(pa, oracle_lib):
     from paper_1711_02146_gb300.workloads import C2
-    w = C2.with_(R=2000)
+    w = C2.with_(R=5000)
     gpu, ref, T = run_in_lockstep(pa, oracle_lib, w)
     assert T == 200 and gpu.beta(T) == 5.0
