@@ -310,14 +310,16 @@ struct BitShape {
   static constexpr int CB = bits_for(3 * L * (ROWS / NP));  // bit planes of a thread's level counter
   static constexpr size_t SMEM_TILE = (size_t)N * W * 4 + (size_t)N * sizeof(SiteRec) + (size_t)SLOTS * 4;
   static constexpr size_t SMEM_QUEUES = (size_t)(NT / 32) * kQueueCap * sizeof(Deferred);
+  static constexpr int RPP = ROWS / NP;  // rows per partition
+  static constexpr size_t SMEM_ROWS = (size_t)NP * RPP * 8 * sizeof(int);
   // Deferred comparisons need whole warps that each stay inside one parity class
   // (every lane of a warp then runs the same half-sweep code in step), and room
   // for the queues without fewer than MB CTAs per SM (228 KB per SM, 1 KB of it
   // reserved per CTA).
   static constexpr bool DEFER = NT % 32 == 0 && ((NP / 2) * W) % 32 == 0 &&
-                                (size_t)MB * (SMEM_TILE + SMEM_QUEUES + 1024) <= 233472;
+                                (size_t)MB * (SMEM_TILE + SMEM_QUEUES + SMEM_ROWS + 1024) <= 233472;
   static constexpr int NQ = DEFER ? NT / 32 : 0;  // one queue per warp
-  static constexpr size_t SMEM = SMEM_TILE + (DEFER ? SMEM_QUEUES : 0);
+  static constexpr size_t SMEM = SMEM_TILE + (DEFER ? SMEM_QUEUES + SMEM_ROWS : 0);
   static_assert(NT % W == 0 && 32 % W == 0 && NT <= 1024, "threads must tile the words of a row");
   static_assert(L % 2 == 0 && L / 2 <= 8, "even L up to 16");
   static_assert(NP % 2 == 0 && (ROWS / 2) % (NP / 2) == 0, "row partitions must split each parity class");
@@ -483,11 +485,14 @@ __device__ __forceinline__ void finish_deferred(uint32_t* sp, const SiteRec* rec
 // queued the warp finishes them with all lanes (finish_deferred); the rest are
 // finished at the end of the half-sweep.  The decisions are the same; only the
 // lanes that take them change.  sp: the tile (word-major within a site row);
-// gbase: the tile's first word index (Philox group 8 (gbase + word) + b).
+// gbase: the tile's first word index (Philox group 8 (gbase + word) + b); rowtab:
+// per partition and row the word offsets of the row and its four neighbour rows
+// and the row's first site (built once per tile: a thread's rows never change).
+// The sites of a row are unrolled, so every column offset is a constant.
 template <int L, int W, int NP, int X0>
 __device__ __forceinline__ void sweep_rows_bits_dq(uint32_t* sp, int word, const SiteRec* recs, int part, int p,
                                                    const ThreadPhilox (&tp)[2], uint32_t q, uint32_t gbase,
-                                                   Deferred* dq, const SweepArgs& a) {
+                                                   Deferred* dq, const int* rowtab, const SweepArgs& a) {
   constexpr int H = L / 2, RPP = L * L / NP;
   const int lane = (int)(threadIdx.x & 31u);
   const unsigned below = (1u << lane) - 1u;
@@ -495,18 +500,16 @@ __device__ __forceinline__ void sweep_rows_bits_dq(uint32_t* sp, int word, const
   int head = 0, cnt = 0;  // the same in every lane of the warp
 #pragma unroll 1
   for (int k = 0; k < RPP; ++k) {
-    const int r = row_index<L, NP>(part, k, p);
-    const int y = r % L, z = r / L;
-    const int yp = y == L - 1 ? 0 : y + 1, ym = y == 0 ? L - 1 : y - 1;
-    const int zp = z == L - 1 ? 0 : z + 1, zm = z == 0 ? L - 1 : z - 1;
-    uint32_t* p0 = spw + (size_t)r * L * W;
-    const uint32_t* pyp = spw + (size_t)(yp + L * z) * L * W;
-    const uint32_t* pym = spw + (size_t)(ym + L * z) * L * W;
-    const uint32_t* pzp = spw + (size_t)(y + L * zp) * L * W;
-    const uint32_t* pzm = spw + (size_t)(y + L * zm) * L * W;
-    const SiteRec* rr = recs + r * L;
-    const uint32_t h0 = (uint32_t)(r * L) >> 1;
-#pragma unroll 2
+    const int4 e0 = *reinterpret_cast<const int4*>(rowtab + 8 * (part * RPP + k));
+    const int rL = rowtab[8 * (part * RPP + k) + 4];
+    uint32_t* p0 = spw + e0.x;
+    const uint32_t* pyp = spw + e0.y;
+    const uint32_t* pym = spw + e0.z;
+    const uint32_t* pzp = spw + e0.w;
+    const uint32_t* pzm = spw + rowtab[8 * (part * RPP + k) + 5];
+    const SiteRec* rr = recs + rL;
+    const uint32_t h0 = (uint32_t)rL >> 1;
+#pragma unroll
     for (int xh = 0; xh < H; ++xh) {
       const int x = 2 * xh + X0;
       const int xp = x == L - 1 ? 0 : x + 1, xm = x == 0 ? L - 1 : x - 1;
@@ -538,7 +541,7 @@ __device__ __forceinline__ void sweep_rows_bits_dq(uint32_t* sp, int word, const
       const unsigned dm = __ballot_sync(0xffffffffu, eq != 0u);
       if (eq) {
         Deferred d;
-        d.loc = (uint32_t)(r * L + x) | ((uint32_t)word << 16);
+        d.loc = (uint32_t)(rL + x) | ((uint32_t)word << 16);
         d.eq = eq;
         d.u0 = u0;
         d.u1 = u1;
@@ -730,9 +733,26 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, uint32_t* sm, int
   SiteRec* recs = reinterpret_cast<SiteRec*>(sm + (size_t)N * W);  // [N]
   Deferred* queues = reinterpret_cast<Deferred*>(recs + N);        // [NQ][kQueueCap]
   int* slots = reinterpret_cast<int*>(queues + S::NQ * kQueueCap);  // [33 W]: parents, then level counts
+  int* rowtab = slots + S::SLOTS;  // [NP][RPP][8]: word offsets of a row and its four neighbour rows, its first site
   const int tid = threadIdx.x, word = tid % W, part = tid / W;
   Deferred* dq = queues + (S::DEFER ? (tid >> 5) * kQueueCap : 0);
   init_tables<L>(a, recs, tid, NT);
+  if constexpr (S::DEFER) {
+    for (int e = tid; e < NP * S::RPP; e += NT) {
+      const int pt = e / S::RPP, kr = e % S::RPP;
+      const int r = row_index<L, NP>(pt, kr, pt / (NP / 2));
+      const int y = r % L, z = r / L;
+      const int yp = y == L - 1 ? 0 : y + 1, ym = y == 0 ? L - 1 : y - 1;
+      const int zp = z == L - 1 ? 0 : z + 1, zm = z == 0 ? L - 1 : z - 1;
+      int* o = rowtab + 8 * e;
+      o[0] = r * L * W;
+      o[1] = (yp + L * z) * L * W;
+      o[2] = (ym + L * z) * L * W;
+      o[3] = (y + L * zp) * L * W;
+      o[4] = r * L;
+      o[5] = (y + L * zm) * L * W;
+    }
+  }
   for (int i = tid; i < TJ; i += NT) slots[33 * (i >> 5) + (i & 31)] = tile0 + i < R_new ? a.pop.parents[tile0 + i] : -1;
   __syncthreads();
   gather_bits<L, W, NP>(a, sp, slots, word, part);
@@ -753,9 +773,9 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, uint32_t* sm, int
       if constexpr (S::DEFER) {
         const ThreadPhilox tp[2] = {thread_philox(g8, q, a.k0, a.k1), thread_philox(g8 + 1u, q, a.k0, a.k1)};
         if ((pclass ^ c) == 0)  // the same in every lane of the warp
-          sweep_rows_bits_dq<L, W, NP, 0>(sp, word, recs, part, pclass, tp, q, gbase, dq, a);
+          sweep_rows_bits_dq<L, W, NP, 0>(sp, word, recs, part, pclass, tp, q, gbase, dq, rowtab, a);
         else
-          sweep_rows_bits_dq<L, W, NP, 1>(sp, word, recs, part, pclass, tp, q, gbase, dq, a);
+          sweep_rows_bits_dq<L, W, NP, 1>(sp, word, recs, part, pclass, tp, q, gbase, dq, rowtab, a);
       } else {
         const ThreadPhilox tp[4] = {thread_philox(g8, q, a.k0, a.k1), thread_philox(g8 + 1u, q, a.k0, a.k1),
                                     thread_philox(g8 + 2u, q, a.k0, a.k1), thread_philox(g8 + 3u, q, a.k0, a.k1)};
