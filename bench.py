@@ -184,6 +184,37 @@ def oracle_updates_per_s(w, R_sample: int, min_seconds: float, max_steps: int, n
     return updates / dt, steps, dt
 
 
+def small_config_full_run(pa, cores: int):
+    """The small workload (L = 4, R = 1000, 51 linear temperatures, 10 sweeps) run
+    to its end on the GPU (pa_run, creation included) and by the oracle on the host
+    cores, with the two runs' final free energies side by side."""
+    import torch
+    import oracle
+    from paper_1711_02146_gb300.workloads import C1
+    oracle.build()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = pa.Run.from_workload(C1)
+    r.run()
+    r.sync()
+    gpu_s = time.perf_counter() - t0
+    g = r.obs(r.t)
+    r.close()
+    t0 = time.perf_counter()
+    o = oracle.Run(oracle.RunConfig(L=C1.L, R=C1.R, disorder_seed=C1.disorder_seed, run_seed=C1.run_seed,
+                                    betas=C1.betas, n_temps=C1.n_temps, beta_max=C1.beta_max,
+                                    eps_target=C1.eps_target, n_sweeps=C1.n_sweeps, n_pop=C1.n_pop,
+                                    n_threads=cores))
+    while o.step() == 0:
+        pass
+    oracle_s = time.perf_counter() - t0
+    upd = total_updates(C1)
+    return {"workload": f"{C1.name}: L=4, R=1000, 51 linear temperatures to beta=5, 10 sweeps, full run",
+            "gpu_seconds": gpu_s, "oracle_seconds": oracle_s, "oracle_cores": cores, "updates_approx": upd,
+            "gpu_updates_per_s": upd / gpu_s, "oracle_updates_per_s": upd / oracle_s,
+            "final_minus_beta_F_gpu": g["minus_beta_F"], "final_minus_beta_F_oracle": o.obs(o.t)["minus_beta_F"]}
+
+
 def cpu_model() -> str:
     try:
         out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
@@ -380,21 +411,11 @@ def served_vs_serial(pa, n_req: int, mem_budget: int):
     # the stream at 0.8 x capacity
     gap = 1.0 / (0.8 * capacity)
     arrivals = [a * gap for _, a in reqs]
-    srv = pa.Server(mem_budget, max_active=256, steps_per_poll=4)
-    t0 = time.perf_counter()
-    finish, arrive_of = {}, {}
-    nxt = 0
-    while len(finish) < len(ws):
-        now = time.perf_counter() - t0
-        while nxt < len(ws) and arrivals[nxt] <= now:
-            rid = srv.submit(ws[nxt])
-            arrive_of[rid] = arrivals[nxt]
-            nxt += 1
-        for rid in srv.poll():
-            finish[rid] = time.perf_counter() - t0
-    lat = np.array([finish[r] - arrive_of[r] for r in finish])
-    span = max(finish.values()) - arrivals[0]
-    srv.close()
+    lat, span = serve_stream(pa, ws, arrivals, mem_budget)
+    # a lighter load, 0.5 x capacity, on the first half of the stream
+    n_light = max(1, len(ws) // 2)
+    light_arrivals = [a / (0.5 * capacity) for _, a in reqs[:n_light]]
+    light_lat, light_span = serve_stream(pa, ws[:n_light], light_arrivals, mem_budget)
     # serial FIFO queue with the same arrivals
     f_prev, slat = 0.0, []
     for a, sv in zip(arrivals, service):
@@ -413,7 +434,32 @@ def served_vs_serial(pa, n_req: int, mem_budget: int):
             "throughput_vs_serial": (len(ws) / span) / (len(ws) / sum(service)),
             "capacity_vs_serial": capacity / (len(ws) / sum(service)),
             "p50_latency_serial_over_served": float(np.percentile(slat, 50) / np.percentile(lat, 50)),
+            "light_load": {"requests": n_light, "offered_load_runs_per_s": 0.5 * capacity,
+                           "runs_per_s": n_light / light_span,
+                           "p50_latency_s": float(np.percentile(light_lat, 50)),
+                           "p99_latency_s": float(np.percentile(light_lat, 99))},
             "mem_budget_bytes": mem_budget}
+
+
+def serve_stream(pa, ws, arrivals, mem_budget):
+    """Submits request i at arrivals[i] seconds after the start (the host polls in
+    between); returns the latencies (finish - arrival) and the span from the first
+    arrival to the last finish."""
+    srv = pa.Server(mem_budget, max_active=256, steps_per_poll=4)
+    t0 = time.perf_counter()
+    finish, arrive_of = {}, {}
+    nxt = 0
+    while len(finish) < len(ws):
+        now = time.perf_counter() - t0
+        while nxt < len(ws) and arrivals[nxt] <= now:
+            rid = srv.submit(ws[nxt])
+            arrive_of[rid] = arrivals[nxt]
+            nxt += 1
+        for rid in srv.poll():
+            finish[rid] = time.perf_counter() - t0
+    srv.close()
+    lat = np.array([finish[r] - arrive_of[r] for r in finish])
+    return lat, max(finish.values()) - arrivals[0]
 
 
 def autotune_shapes(pa, sizes):
@@ -656,6 +702,17 @@ def ours(args):
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"first {steps} temperature steps of the same run with R=2e4 "
                                           f"({dt:.1f} s, {cpu_model()})"}
+        line["small_config"] = small_config_full_run(pa, cores)
+        # the many-run workloads on the CPU, estimated from the oracle's measured rate (a
+        # full pass of the oracle over them would take hours)
+        for key in ("batched", "served"):
+            sec = line.get(key)
+            if sec and sec.get("updates_per_s"):
+                n = sec.get("runs", sec.get("requests"))
+                upd = sec["updates_per_s"] * (sec["seconds"] if key == "batched" else n / sec["runs_per_s"])
+                sec["oracle_runs_per_s_estimate"] = n / (upd / v)
+                sec["oracle_estimate_basis"] = ("the runs' updates divided by the oracle's updates/s on the "
+                                                "L=10 sample above (its rate varies with L)")
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
