@@ -165,6 +165,9 @@ def lib():
             "org_couplings": (None, [ctypes.c_int32, ctypes.c_uint64, i32p]),
             "org_energy": (ctypes.c_int64, [ctypes.c_int32, i32p, i8p]),
             "org_acceptance_threshold": (ctypes.c_uint32, [ctypes.c_double, ctypes.c_int64]),
+            "org_metropolis_uniform": (ctypes.c_uint32, [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32,
+                                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                                          ctypes.c_int32]),
             "org_sweep_replica": (ctypes.c_int64, [ctypes.c_int32, i32p, i8p, ctypes.c_uint64, ctypes.c_int32,
                                                    ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_double]),
             "org_weight": (ctypes.c_double, [ctypes.c_double, ctypes.c_int64]),
@@ -469,6 +472,12 @@ def gsweep_replica(L: int, Jq: np.ndarray, s: np.ndarray, run_seed: int, pop: in
     dE = lib().org_sweep_replica(L, _p(Jq, ctypes.c_int32), _p(s2, ctypes.c_int8), run_seed, pop, slot, t,
                                  n_sweeps, beta)
     return s2, int(dE)
+
+
+def gmetropolis_uniform(run_seed: int, pop: int, n: int, sweep: int, colour: int, slot: int, t: int) -> int:
+    """The 32-bit Metropolis uniform of a replica (Gaussian couplings): upper 16 bits
+    from one Philox stream, lower 16 bits from a second one (org_metropolis_uniform)."""
+    return int(lib().org_metropolis_uniform(run_seed, pop, n, sweep, colour, slot, t))
 
 
 def gacceptance_threshold(beta: float, dE: int) -> int:

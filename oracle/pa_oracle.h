@@ -165,6 +165,12 @@ void org_couplings(int32_t L, uint64_t disorder_seed, int32_t* Jq);
 int64_t org_energy(int32_t L, const int32_t* Jq, const int8_t* s);
 /* Metropolis threshold of a flip costing dE > 0 (fixed point, units of 2^-20) */
 uint32_t org_acceptance_threshold(double beta, int64_t dE);
+/* The 32-bit uniform of replica `slot` at site n in half-sweep (sweep, colour) of
+ * step t: upper 16 bits from half (slot & 1) of word (slot >> 1) & 3 of Philox at
+ * counter (n >> 1, 2 sweep + colour, slot >> 3, t), lower 16 bits from the upper half
+ * of word slot & 3 at counter (n >> 1, 2 sweep + colour, (slot >> 2) | 2^31, t). */
+uint32_t org_metropolis_uniform(uint64_t run_seed, int32_t pop, int32_t n, int32_t sweep, int32_t colour,
+                                int64_t slot, int32_t t);
 int64_t org_sweep_replica(int32_t L, const int32_t* Jq, int8_t* s, uint64_t run_seed, int32_t pop, int64_t slot,
                           int32_t t, int32_t n_sweeps, double beta);
 /* resampling weight exp(-dbeta d 2^-20) of a replica d above the lowest energy */

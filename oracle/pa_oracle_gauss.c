@@ -9,9 +9,14 @@
  *     clamped to [-5, 5] and held in fixed point, Jq = round(J * 2^20); energies
  *     and energy changes are then exact integers (units of 2^-20);
  *   - a Metropolis flip with dE <= 0 is taken; otherwise it is taken when the
- *     Philox word r < thr(dE) = min(floor(2^32 exp(-beta dE)), 2^32 - 2), the
- *     exponential in double precision (2^32 p is then exact, a power-of-two
- *     scaling, and the floor the only rounding);
+ *     replica's 32-bit uniform U < thr(dE) = min(floor(2^32 exp(-beta dE)),
+ *     2^32 - 2), the exponential in double precision (2^32 p is then exact, a
+ *     power-of-two scaling, and the floor the only rounding).  U is a random-stream
+ *     convention (the paper fixes no generator): its upper 16 bits are half
+ *     (slot & 1) of word (slot >> 1) & 3 of Philox at counter
+ *     (n >> 1, 2 sweep + colour, slot >> 3, t), its lower 16 bits the upper half of
+ *     word slot & 3 of Philox at counter (n >> 1, 2 sweep + colour,
+ *     (slot >> 2) | 2^31, t) (org_metropolis_uniform);
  *   - resampling follows Eqs. (tau), (Q) and (eq_num_elim) as written, replica by
  *     replica: each weight is one exponential, w_i = exp(-dbeta (E_i - E_min)) with
  *     E_min the lowest energy present (Eq. Q divided by its largest term); S' is
@@ -98,6 +103,18 @@ static int64_t flip_change(int32_t L, const int32_t* Jq, const int8_t* s, int32_
   return 2 * s[n] * h;
 }
 
+uint32_t org_metropolis_uniform(uint64_t run_seed, int32_t pop, int32_t n, int32_t sweep, int32_t colour,
+                                int64_t slot, int32_t t) {
+  uint32_t key[2];
+  or_key(run_seed, OR_P_METROPOLIS, (uint32_t)pop, key);
+  const uint32_t q = (uint32_t)(2 * sweep + colour), h = (uint32_t)(n >> 1);
+  const uint32_t upper_word = g_word(key, h, q, (uint32_t)(slot >> 3), (uint32_t)t, (int)((slot >> 1) & 3));
+  const uint32_t upper = (slot & 1) ? upper_word >> 16 : upper_word & 0xffffu;
+  const uint32_t lower_word =
+      g_word(key, h, q, (uint32_t)(slot >> 2) | 0x80000000u, (uint32_t)t, (int)(slot & 3));
+  return (upper << 16) | (lower_word >> 16);
+}
+
 uint32_t org_acceptance_threshold(double beta, int64_t dE) {
   double v = floor(exp(-(beta * ((double)dE * 0x1p-20))) * 4294967296.0);
   if (v > 4294967294.0) v = 4294967294.0;
@@ -106,8 +123,6 @@ uint32_t org_acceptance_threshold(double beta, int64_t dE) {
 
 int64_t org_sweep_replica(int32_t L, const int32_t* Jq, int8_t* s, uint64_t run_seed, int32_t pop, int64_t slot,
                           int32_t t, int32_t n_sweeps, double beta) {
-  uint32_t key[2];
-  or_key(run_seed, OR_P_METROPOLIS, (uint32_t)pop, key);
   int64_t total = 0;
   for (int32_t sw = 0; sw < n_sweeps; ++sw)
     for (int32_t c = 0; c < 2; ++c)
@@ -117,9 +132,7 @@ int64_t org_sweep_replica(int32_t L, const int32_t* Jq, int8_t* s, uint64_t run_
             if ((x + y + z) % 2 != c) continue;
             int32_t n = g_site(L, x, y, z);
             int64_t dE = flip_change(L, Jq, s, n);
-            uint32_t r = g_word(key, (uint32_t)(n >> 1), (uint32_t)(2 * sw + c), (uint32_t)(slot >> 2), (uint32_t)t,
-                                (int)(slot & 3));
-            if (dE <= 0 || r < org_acceptance_threshold(beta, dE)) {
+            if (dE <= 0 || org_metropolis_uniform(run_seed, pop, n, sw, c, slot, t) < org_acceptance_threshold(beta, dE)) {
               s[n] = (int8_t)(-s[n]);
               total += dE;
             }

@@ -601,7 +601,9 @@ struct CkptHeader {
   uint64_t total_bytes;
 };
 constexpr char kCkptMagic[8] = {'P', 'A', 'C', 'K', 'P', 'T', '0', '1'};
-constexpr uint32_t kCkptVersion = 3;
+// Version 4: the Gaussian model's Metropolis uniforms come from 16-bit halves (a
+// version 3 checkpoint would resume on other random numbers than it started with).
+constexpr uint32_t kCkptVersion = 4;
 
 size_t ckpt_bytes(const RunGeom& g, int model, int t, int n_temps, const int32_t* Rt, const int32_t* Rp) {
   size_t b = sizeof(CkptHeader) + (size_t)n_temps * (sizeof(double) + sizeof(int32_t));

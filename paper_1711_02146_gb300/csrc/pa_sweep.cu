@@ -126,40 +126,6 @@ __device__ __forceinline__ ThreadPhilox thread_philox(uint32_t g, uint32_t q, co
   return tp;
 }
 
-// Philox blocks (rounds 3..10) of one colour site h for the two groups of a
-// word: w8[b] is word b of group 0's block (b < 4) or group 1's (b >= 4).
-__device__ __forceinline__ void philox_site(uint32_t h, const SiteRec& sr, const ThreadPhilox& tpa,
-                                            const ThreadPhilox& tpb, const uint32_t* k0, const uint32_t* k1,
-                                            uint32_t (&w8)[8]) {
-  const uint32_t uc = kM0 * h;  // lo(M0 h)
-#pragma unroll
-  for (int gi = 0; gi < 2; ++gi) {
-    const ThreadPhilox& tp = gi ? tpb : tpa;
-    uint32_t hh, l, h2, l2;
-    mulhilo(kM1, tp.tb ^ uc, hh, l);
-    mulhilo(kM0, sr.ua ^ tp.ta, h2, l2);
-    w8[4 * gi + 0] = hh ^ sr.ub;
-    w8[4 * gi + 1] = l;
-    w8[4 * gi + 2] = h2 ^ tp.tdk;
-    w8[4 * gi + 3] = l2;
-  }
-#pragma unroll
-  for (int rr = 3; rr < 10; ++rr) {
-#pragma unroll
-    for (int gi = 0; gi < 2; ++gi) {
-      uint32_t hh, l, h2, l2;
-      mulhilo(kM1, w8[4 * gi + 2], hh, l);
-      mulhilo(kM0, w8[4 * gi + 0], h2, l2);
-      const uint32_t n0 = hh ^ w8[4 * gi + 1] ^ k0[rr];
-      const uint32_t n2 = h2 ^ w8[4 * gi + 3] ^ k1[rr];
-      w8[4 * gi + 0] = n0;
-      w8[4 * gi + 1] = l;
-      w8[4 * gi + 2] = n2;
-      w8[4 * gi + 3] = l2;
-    }
-  }
-}
-
 // Row k of a partition: rows of one parity class (y + z) & 1 = p, interleaved
 // across the partitions of that class.
 template <int L, int NP>
@@ -899,13 +865,14 @@ static int launch_group_t(const GroupUnit* units, const int32_t* list, const int
 }
 
 // ---- Gaussian couplings (§II.A): nibble tiles (eight replicas per word, four
-// bits each: gather_tile, store_tile) and a 32-bit Philox word per update, at counter (n >> 1, 2s + c, j >> 2, t), word
-// j & 3.  The acceptance comes from a per-site table built on the host for the
-// step's beta: for each of the 64 patterns of antiparallel neighbours (bit k:
-// bond k, in the order x+1, x-1, y+1, y-1, z+1, z-1) the threshold of the flip,
-// 0xFFFFFFFF when it costs dE <= 0 (always taken) and otherwise
-// min(floor(2^32 exp(-beta dE)), 2^32 - 2); the flip is taken when the Philox
-// word is below it.  Energies are recounted from scratch after the sweeps:
+// bits each: gather_tile, store_tile) and one Philox block per site for the eight
+// replicas of a word, whose 16-bit halves are the upper halves of their 32-bit
+// uniforms (sweep_rows_g).  The acceptance comes from a per-site table built on the
+// host for the step's beta: for each of the 64 patterns of antiparallel neighbours
+// (bit k: bond k, in the order x+1, x-1, y+1, y-1, z+1, z-1) the threshold of the
+// flip, 0xFFFFFFFF when it costs dE <= 0 (always taken) and otherwise
+// min(floor(2^32 exp(-beta dE)), 2^32 - 2); the flip is taken when the uniform is
+// below it.  Energies are recounted from scratch after the sweeps:
 // E = -sum J + 2 sum over antiparallel bonds of J (exact integers).
 
 struct GSweepArgs {
@@ -915,10 +882,23 @@ struct GSweepArgs {
   long long Jtot;         // sum of all couplings
 };
 
+// The Metropolis uniform U of a replica (Gaussian couplings): its upper 16 bits are
+// half (slot & 1) of word (slot >> 1) & 3 of the Philox block at counter
+// (h, q, slot >> 3, t) (one block per site for the eight replicas of a nibble word),
+// its lower 16 bits the upper half of word slot & 3 at counter (h, q, (slot >> 2) | 2^31,
+// t).  With u = the upper half in place, U < thr holds for sure when (u | 0xffff) <
+// thr and fails for sure when u >= thr; only in between (probability 2^-16 per
+// update) is the second word drawn (g_tie_word).
+__device__ __noinline__ uint32_t g_tie_word(uint32_t h, uint32_t q, uint32_t slot, uint32_t t, uint32_t k0,
+                                            uint32_t k1) {
+  return word_of(philox4x32_10(make_uint4(h, q, (slot >> 2) | 0x80000000u, t), k0, k1), (int)(slot & 3u)) >> 16;
+}
+
 template <int L, int W, int NP, int X0>
 __device__ __forceinline__ void sweep_rows_g(uint32_t* sp, const SiteRec* recs, int part, int p,
-                                             const ThreadPhilox& tpa, const ThreadPhilox& tpb, const uint32_t* k0,
-                                             const uint32_t* k1, const uint32_t* __restrict__ gtab) {
+                                             const ThreadPhilox& tp, const uint32_t* k0, const uint32_t* k1,
+                                             const uint32_t* __restrict__ gtab, uint32_t slot0, uint32_t q,
+                                             uint32_t t) {
   constexpr int H = L / 2, RPP = L * L / NP;
 #pragma unroll 1
   for (int k = 0; k < RPP; ++k) {
@@ -939,18 +919,28 @@ __device__ __forceinline__ void sweep_rows_g(uint32_t* sp, const SiteRec* recs, 
       const int x = 2 * xh + X0;
       const int xp = x == L - 1 ? 0 : x + 1;
       const int xm = x == 0 ? L - 1 : x - 1;
-      uint32_t w8[8];
-      philox_site((uint32_t)(r * L) / 2u + (uint32_t)xh, recs[r * L + x], tpa, tpb, k0, k1, w8);
+      const uint32_t h = (uint32_t)(r * L) / 2u + (uint32_t)xh;
+      uint32_t w4[4];
+      philox_block(kM0 * h, recs[r * L + x], tp, k0, k1, w4);
       const uint32_t s0 = row[x];
       const uint32_t P1 = (s0 ^ row[xp]) | ((s0 ^ row[xm]) << 1) | ((s0 ^ pyp[x * W]) << 2);
       const uint32_t P2 = (s0 ^ pym[x * W]) | ((s0 ^ pzp[x * W]) << 1) | ((s0 ^ pzm[x * W]) << 2);
       const uint32_t* tb = gtab + (size_t)(r * L + x) * kGPatterns;
-      uint32_t flip = 0;
+      uint32_t flip = 0, tie = 0;
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const uint32_t b = ((P1 >> (4 * i)) & 7u) | (((P2 >> (4 * i)) & 7u) << 3);  // the replica's pattern
         const uint32_t thr = __ldg(tb + b);
-        if (w8[i] < thr || thr == 0xFFFFFFFFu) flip |= 1u << (4 * i);
+        const uint32_t u = (i & 1) ? (w4[i >> 1] & 0xffff0000u) : (w4[i >> 1] << 16);
+        if (thr == 0xFFFFFFFFu || (u | 0xffffu) < thr) flip |= 1u << (4 * i);
+        else if (u < thr) tie |= 1u << i;
+      }
+      while (tie) {  // rare: the lower 16 bits decide
+        const int i = __ffs(tie) - 1;
+        tie &= tie - 1;
+        const uint32_t b = ((P1 >> (4 * i)) & 7u) | (((P2 >> (4 * i)) & 7u) << 3);
+        const uint32_t u = (i & 1) ? (w4[i >> 1] & 0xffff0000u) : (w4[i >> 1] << 16);
+        if ((u | g_tie_word(h, q, slot0 + (uint32_t)i, t, k0[0], k1[0])) < __ldg(tb + b)) flip |= 1u << (4 * i);
       }
       p0[x * W] = s0 ^ flip;
     }
@@ -1004,19 +994,19 @@ __global__ void __launch_bounds__(NT, MB) k_sweep_g(const __grid_constant__ GSwe
   for (int i = tid; i < TJ; i += NT) ecnt[i] = 0;
   gather_tile<L, W, NP>(a, sp, tile0, R_new, word, part);
   __syncthreads();
-  const uint32_t g0 = 2u * ((uint32_t)(tile0 >> 3) + (uint32_t)word);
+  const uint32_t slot0 = (uint32_t)tile0 + 8u * (uint32_t)word;  // the word's first replica
+  const uint32_t g = slot0 >> 3;                                     // Philox group of its eight replicas
   const int pclass = part / (NP / 2);
   uint32_t* spw = sp + word;
   for (int s = 0; s < a.n_sweeps; ++s) {
 #pragma unroll 1
     for (int c = 0; c < 2; ++c) {
       const uint32_t q = 2u * (uint32_t)s + (uint32_t)c;
-      const ThreadPhilox tpa = thread_philox(g0, q, a.k0, a.k1);
-      const ThreadPhilox tpb = thread_philox(g0 + 1u, q, a.k0, a.k1);
+      const ThreadPhilox tp = thread_philox(g, q, a.k0, a.k1);
       if ((pclass ^ c) == 0)
-        sweep_rows_g<L, W, NP, 0>(spw, recs, part, pclass, tpa, tpb, a.k0, a.k1, ga.gtab);
+        sweep_rows_g<L, W, NP, 0>(spw, recs, part, pclass, tp, a.k0, a.k1, ga.gtab, slot0, q, (uint32_t)a.t);
       else
-        sweep_rows_g<L, W, NP, 1>(spw, recs, part, pclass, tpa, tpb, a.k0, a.k1, ga.gtab);
+        sweep_rows_g<L, W, NP, 1>(spw, recs, part, pclass, tp, a.k0, a.k1, ga.gtab, slot0, q, (uint32_t)a.t);
       __syncthreads();
     }
   }

@@ -54,6 +54,15 @@ def assert_counts(gpu, ref, oracle_lib, E_old, R, dbeta, run_seed, t, pop=0):
     assert np.array_equal(gpu.copy_counts(pop), ref.last_counts(pop)), f"copy numbers at t={t} pop {pop}"
 
 
+def obs_scale(o, k):
+    """Magnitude that bounds the rounding of observable k: its own, except for
+    Delta_KY = e_l - <E>/N (the Katzgraber-Young check), a difference of two O(1)
+    terms that nearly cancel, whose rounding is relative to those terms."""
+    if k == "delta_KY":
+        return abs(o["e_l"]) + abs(o["e_l"] - o["delta_KY"])
+    return abs(o[k])
+
+
 def assert_obs(g, r, ctx):
     for k in INT_OBS:
         assert g[k] == r[k], f"{ctx} {k}: gpu {g[k]} oracle {r[k]}"
@@ -61,7 +70,8 @@ def assert_obs(g, r, ctx):
         a, b = g[k], r[k]
         if a == b:
             continue
-        assert abs(a - b) <= REL * max(abs(a), abs(b)) + 1e-300, f"{ctx} {k}: gpu {a!r} oracle {b!r}"
+        scale = max(obs_scale(g, k), obs_scale(r, k))
+        assert abs(a - b) <= REL * scale + 1e-300, f"{ctx} {k}: gpu {a!r} oracle {b!r}"
 
 
 def assert_state(gpu, ref, n_pop, ctx):

@@ -193,6 +193,34 @@ def test_sweep_energy_changes_add_up(L):
         assert (s2 != s).any()
 
 
+def test_metropolis_uniform_is_uniform_and_slots_are_independent():
+    """The Gaussian model's Metropolis uniform (a random-stream convention: its upper
+    16 bits from one Philox stream, its lower 16 bits from a second).  Over 2^15 slots
+    of one site and half-sweep it accepts a flip of threshold p 2^32 at rate p
+    (binomial bound) and its nibbles are uniform (chi-square); neighbouring slots
+    share an upper or a lower half no more often than chance allows, and so do the two
+    halves of one uniform (a wrong half, word or counter would make them equal); other
+    half-sweeps, sites, steps, populations and seeds draw other uniforms."""
+    n = 1 << 15
+    U = np.array([oracle.gmetropolis_uniform(7, 0, 5, 1, 0, j, 3) for j in range(n)], dtype=np.uint64)
+    for p in (0.5, 0.25, 0.01):
+        rate = float((U < int(p * 2 ** 32)).mean())
+        assert abs(rate - p) < 5 * math.sqrt(p * (1 - p) / n)
+    hi, lo = U >> np.uint64(16), U & np.uint64(0xFFFF)
+    for d in (1, 2, 3, 4, 8):   # slots of one word, one block, one group
+        assert (hi[d:] == hi[:-d]).sum() < 8 and (lo[d:] == lo[:-d]).sum() < 8
+    assert (hi == lo).sum() < 8
+    for v in (hi >> np.uint64(12), lo >> np.uint64(12), hi & np.uint64(15), lo & np.uint64(15)):
+        c = np.bincount(v.astype(np.int64), minlength=16)
+        chi2 = float(((c - n / 16) ** 2 / (n / 16)).sum())
+        assert chi2 < 15 + 5 * math.sqrt(30)
+    for seed, pop, site, sweep, colour, t in ((7, 0, 5, 1, 1, 3), (7, 0, 6, 1, 0, 3), (7, 0, 5, 2, 0, 3),
+                                              (7, 0, 5, 1, 0, 4), (7, 1, 5, 1, 0, 3), (8, 0, 5, 1, 0, 3)):
+        V = np.array([oracle.gmetropolis_uniform(seed, pop, site, sweep, colour, j, t) for j in range(256)],
+                     dtype=np.uint64)
+        assert (V == U[:256]).sum() < 2
+
+
 def test_sweeps_sample_the_boltzmann_distribution():
     L, beta, seed = 2, 0.8, 21
     Jq = oracle.gcouplings(L, seed)
