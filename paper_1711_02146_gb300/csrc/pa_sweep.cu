@@ -36,7 +36,8 @@
 // block costs the 16 wide multiplies of rounds 3..10.
 //
 // Gaussian couplings (k_sweep_g, below): nibble-packed tiles, eight replicas per
-// word, with a 32-bit Philox word per update.
+// word, with one Philox block per site for a word's eight replicas (the upper 16
+// bits of their uniforms; the lower 16 bits only on a tie).
 #include <cuda_runtime.h>
 
 #include <algorithm>
