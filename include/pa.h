@@ -336,7 +336,8 @@ typedef struct pa_batch pa_batch;
 /* Creates n runs (configs copied), each on its own stream. */
 int pa_batch_create(const pa_config* cfgs, int32_t n, pa_batch** out);
 /* Advances every run to the end of its schedule, one step of each run per
- * round, then synchronises; returns PA_OK or the first error. */
+ * round, then synchronises; returns PA_OK or the first error.  A run that fails
+ * (its own status, see pa_sync) stops there; the other runs still finish. */
 int pa_batch_run(pa_batch* batch);
 
 /* How pa_batch_run advances the runs (both give every run its results alone):

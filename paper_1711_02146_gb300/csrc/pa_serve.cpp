@@ -176,17 +176,15 @@ int pa_batch_run(pa_batch* b) {
   for (char l : live) n_live += l ? 1 : 0;
   std::vector<int64_t> before(b->ctx.size(), 0);
   for (size_t i = 0; i < b->ctx.size(); ++i) before[i] = pa::run_kernel_launches(b->ctx[i]);
-  int rc = PA_OK;
-  while (n_live > 0 && rc == PA_OK) {
+  int rc = PA_OK;  // a run that fails stops; the others finish (the first error is returned)
+  while (n_live > 0) {
     for (size_t i = 0; i < b->ctx.size(); ++i) {
       if (!live[i]) continue;
       const int r = pa_step(b->ctx[i]);
-      if (r == PA_DONE) {
+      if (r != PA_OK) {
         live[i] = 0;
         --n_live;
-      } else if (r != PA_OK) {
-        rc = r;
-        break;
+        if (r != PA_DONE && rc == PA_OK) rc = r;
       }
     }
   }

@@ -168,6 +168,37 @@ def test_server_isolates_a_failing_request(pa, oracle_lib):
     server.close()
 
 
+@pytest.mark.parametrize("mode", ["fused", "streams"])
+def test_batch_reports_a_failing_run_and_finishes_the_others(pa, oracle_lib, mode):
+    """A run whose population outgrows a capacity equal to R, in a batch: pa_batch_run
+    reports PA_ERR_CAPACITY (from the run's device flag), the run itself reports it,
+    and every other run of the batch gives its standalone results, every step."""
+    betas = linear_betas(6, 3.0)
+    for run_seed in range(30):  # a seed whose population outgrows a capacity equal to R
+        ref = oracle_lib.Run(oracle_lib.RunConfig(L=4, R=500, disorder_seed=1, run_seed=run_seed, betas=betas,
+                                                  n_sweeps=1, R_cap=500))
+        try:
+            ref.run()
+        except RuntimeError:
+            break
+    else:
+        pytest.skip("no overflowing seed found")
+    bad = Workload("bad", L=4, R=500, disorder_seed=1, run_seed=run_seed, betas=betas, n_sweeps=1, R_cap=500)
+    good = mixed_workloads(5, seed=3)
+    ws = good[:2] + [bad] + good[2:]
+    batch = pa.Batch(ws, mode=mode)
+    with pytest.raises(pa.PAError) as e:
+        batch.run()
+    assert e.value.status == pa.PA_ERR_CAPACITY
+    with pytest.raises(pa.PAError) as e:
+        batch.run_view(2).sync()
+    assert e.value.status == pa.PA_ERR_CAPACITY
+    for i, w in enumerate(ws):
+        if w is not bad:
+            assert_same_run(batch.run_view(i), standalone(pa, w), w, every_step=True)
+    batch.close()
+
+
 def test_server_rejects_requests_beyond_the_budget(pa):
     from paper_1711_02146_gb300.workloads import C1
     server = pa.Server(1000)
