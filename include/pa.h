@@ -167,7 +167,13 @@ int pa_run(pa_ctx* ctx);
 /* Index of the last step run (0 right after pa_create). */
 int32_t pa_current_step(const pa_ctx* ctx);
 
-/* Synchronises and fills *out for step t <= pa_current_step and population pop. */
+/* Fills *out for step t <= pa_current_step and population pop (+-1 couplings; the
+ * Gaussian model: pa_gobservables).  Waits until step t is done, not for steps
+ * issued after it: a caller may issue step t + 1 with pa_step and then read step t
+ * while the GPU runs.  An error recorded on the device by then (capacity,
+ * extinction, timeout) is returned; one of a later step is reported by a later call
+ * (pa_sync waits for everything).  Reads step t's records and energy histogram from
+ * the device (about 88 (t + 1) + 4 (3N + 1) bytes). */
 int pa_observables(pa_ctx* ctx, int32_t t, int32_t pop, pa_obs* out);
 
 /* Energy-level histogram c_t(k), k = 0..3N, of population pop at step t

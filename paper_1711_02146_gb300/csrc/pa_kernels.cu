@@ -151,14 +151,25 @@ __device__ __forceinline__ void reweight_pop(const RunGeom& g, const PopDev& P, 
   const int nnz = base;
   if (nnz == 0) return;  // cannot happen: the population is never empty here
   const int kmin = lst[0];
-  if (threadIdx.x == 0) {
-    double S = 0.0;
-    for (int i = 0; i < nnz; ++i) {
+  // S' = the sum over occupied levels, ascending, of c(k) w(k - kmin): every thread
+  // forms products, 1024 at a time, into shared memory, and one thread adds them in
+  // level order (the operations and their order of a single thread)
+  __shared__ double eps_sh[1024];  // the products here, the culling sums below
+  double acc = 0.0;
+  for (int base = 0; base < nnz; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    if (i < nnz) {
       const int k = lst[i];
-      S = __dadd_rn(S, __dmul_rn((double)c[k], w[k - kmin]));
+      eps_sh[threadIdx.x] = __dmul_rn((double)c[k], w[k - kmin]);
     }
-    S_sh = S;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int m = min(nnz - base, (int)blockDim.x);
+      for (int j = 0; j < m; ++j) acc = __dadd_rn(acc, eps_sh[j]);
+    }
+    __syncthreads();
   }
+  if (threadIdx.x == 0) S_sh = acc;
   __syncthreads();
   const double S = S_sh;
   const double Rd = (double)g.R;
@@ -177,7 +188,6 @@ __device__ __forceinline__ void reweight_pop(const RunGeom& g, const PopDev& P, 
     P.thr[k] = th;
   }
   // expected culling fraction (Eq. eq_num_elim / R): fixed tree over the threads
-  __shared__ double eps_sh[1024];
   eps_sh[threadIdx.x] = eps_part;
   __syncthreads();
   for (int h = blockDim.x / 2; h > 0; h >>= 1) {

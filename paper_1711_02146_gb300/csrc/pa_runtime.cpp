@@ -71,6 +71,12 @@ struct pa_ctx {
   double* gbis = nullptr;                // device {lo, hi, mid}: the adaptive bisection (Gaussian)
   std::vector<int32_t> Jq_host;
   pa::LookbackTest lookback;             // pa_debug_lookback (tests of the bounded wait)
+  // Completion events of the last steps (a ring, step u in entry u & 3, -1: none), so
+  // that reading step t's results waits for step t only, not for steps issued after
+  // it; those reads go through their own stream.
+  cudaEvent_t step_ev[4] = {};
+  int32_t step_ev_t[4] = {-1, -1, -1, -1};
+  cudaStream_t rd = nullptr;
 };
 
 namespace {
@@ -159,6 +165,49 @@ int copy_d2h(pa_ctx* c, void* dst, const void* src, size_t bytes) {
   c->stats.d2h_bytes += (int64_t)bytes;
   int rc = cuda_status(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream));
   return rc == PA_OK ? cuda_status(cudaStreamSynchronize(c->stream)) : rc;
+}
+
+// Records that everything issued for step t on the run's stream is done (entry t & 3).
+void record_step_done(pa_ctx* c, int t) {
+  const int i = t & 3;
+  c->step_ev_t[i] = -1;
+  if (!c->step_ev[i] && cudaEventCreateWithFlags(&c->step_ev[i], cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    c->step_ev[i] = nullptr;
+    return;
+  }
+  if (cudaEventRecord(c->step_ev[i], c->stream) == cudaSuccess)
+    c->step_ev_t[i] = t;
+  else
+    cudaGetLastError();
+}
+
+// The stream to read step t's results on, once they are complete: the read stream
+// waiting for the earliest recorded step u >= t, or, with no such record, the run's
+// stream after a full synchronisation.
+int read_stream_for(pa_ctx* c, int t, cudaStream_t* out) {
+  int best = -1;
+  for (int i = 0; i < 4; ++i)
+    if (c->step_ev_t[i] >= t && (best < 0 || c->step_ev_t[i] < c->step_ev_t[best])) best = i;
+  int prio = 0;
+  if (best >= 0 && !c->rd &&
+      (cudaStreamGetPriority(c->stream, &prio) != cudaSuccess ||
+       cudaStreamCreateWithPriority(&c->rd, cudaStreamNonBlocking, prio) != cudaSuccess)) {
+    cudaGetLastError();
+    c->rd = nullptr;
+  }
+  if (best < 0 || !c->rd) {
+    *out = c->stream;
+    return cuda_status(cudaStreamSynchronize(c->stream));
+  }
+  *out = c->rd;
+  return cuda_status(cudaStreamWaitEvent(c->rd, c->step_ev[best], 0));
+}
+
+int copy_d2h_on(pa_ctx* c, cudaStream_t st, void* dst, const void* src, size_t bytes) {
+  c->stats.d2h_bytes += (int64_t)bytes;
+  int rc = cuda_status(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st));
+  return rc == PA_OK ? cuda_status(cudaStreamSynchronize(st)) : rc;
 }
 
 int copy_h2d(pa_ctx* c, void* dst, const void* src, size_t bytes) {
@@ -429,27 +478,20 @@ int choose_dbeta(pa_ctx* c, double* dbeta) {
 // histograms of steps 0..t (rec, hall: (t + 1) x n_levels) and, with two
 // populations, population 0's record of step t (r0, else null): Eqs. (Q), (betaF),
 // (g0), the family statistics and the overlap counts.
-void pm1_observables(const RunGeom& g, const std::vector<double>& betas, const StepRec* rec, const uint32_t* hall,
+void pm1_observables(const RunGeom& g, const std::vector<double>& betas, const StepRec* rec, const uint32_t* h,
                      int t, const StepRec* r0, pa_obs* out) {
-  const uint32_t* h = hall + (size_t)t * g.n_levels;
   const int N = g.N;
-  // free energy, Eq. (betaF), and the lowest energy over steps 0..t
+  // free energy, Eq. (betaF), and the lowest energy over steps 0..t: the lowest
+  // occupied level of step u < t is the one the reweighting of step u + 1 recorded
   double lnQ_sum = 0.0, lnQ = 0.0;
   int32_t E0 = 3 * N + 1;
-  for (int u = 0; u <= t; ++u) {
-    if (u > 0) {
-      const StepRec& r = rec[(size_t)u];
-      const double db = betas[(size_t)u] - betas[(size_t)u - 1];
-      const int32_t Emin_prev = 2 * r.kmin_prev - 3 * N;
-      lnQ = std::log(r.S_prime / (double)r.R_prev) - db * (double)Emin_prev;
-      lnQ_sum = lnQ_sum + lnQ;
-    }
-    const uint32_t* hu = hall + (size_t)u * g.n_levels;
-    for (int k = 0; k < g.n_levels; ++k)
-      if (hu[k] > 0) {
-        E0 = std::min(E0, 2 * k - 3 * N);
-        break;
-      }
+  for (int u = 1; u <= t; ++u) {
+    const StepRec& r = rec[(size_t)u];
+    const double db = betas[(size_t)u] - betas[(size_t)u - 1];
+    const int32_t Emin_prev = 2 * r.kmin_prev - 3 * N;
+    lnQ = std::log(r.S_prime / (double)r.R_prev) - db * (double)Emin_prev;
+    lnQ_sum = lnQ_sum + lnQ;
+    E0 = std::min(E0, Emin_prev);
   }
   pa_obs o{};
   const StepRec& r = rec[(size_t)t];
@@ -469,6 +511,7 @@ void pm1_observables(const RunGeom& g, const std::vector<double>& betas, const S
   o.sum_E = sE;
   o.sum_E2 = sE2;
   o.E_min = Emin;
+  E0 = std::min(E0, Emin);
   o.mean_E = (double)sE / (double)o.R_tilde;
   o.var_E = (double)sE2 / (double)o.R_tilde - o.mean_E * o.mean_E;
   o.kmin_prev = t > 0 ? r.kmin_prev : 0;
@@ -568,6 +611,9 @@ void destroy(pa_ctx* c) {
   if (!c) return;
   if (c->slab) cudaFreeAsync(c->slab, c->stream);
   for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->step_ev)
+    if (e) cudaEventDestroy(e);
+  if (c->rd) cudaStreamDestroy(c->rd);
   delete c;
 }
 
@@ -1029,6 +1075,7 @@ int create_run_impl(const pa_config* cfg, void* cuda_stream, pa_ctx** out, bool 
     if (rc == PA_OK) rc = launch_rc(pa::launch_levels_and_hist(g, c->pops, 0, c->jtab, 0, s));
   }
   if (rc == PA_OK) rc = measure(c, 0);
+  if (rc == PA_OK) record_step_done(c, 0);
   if (rc == PA_OK && (synchronize || g.model == PA_MODEL_GAUSS)) rc = cuda_status(cudaStreamSynchronize(s));
   if (rc != PA_OK) {
     destroy(c);
@@ -1113,6 +1160,7 @@ int pa_step(pa_ctx* c) {
   c->cur = 1 - c->cur;
   rc = measure(c, t);
   if (rc != PA_OK) return fail(c, rc);
+  record_step_done(c, t);
   c->t = t;
   c->stats.steps += 1;
   c->counted_steps.emplace_back(t, c->sweeps[(size_t)t]);
@@ -1193,17 +1241,26 @@ double pa_beta(const pa_ctx* c, int32_t t) {
 int pa_observables(pa_ctx* c, int32_t t, int32_t pop, pa_obs* out) {
   if (!c || !out || t < 0 || pop < 0 || pop >= c->g.n_pop || c->model != PA_MODEL_PM1) return PA_ERR_INVALID;
   if (t > c->t) return PA_ERR_STATE;
-  int rc = pa_sync(c);
-  if (rc != PA_OK) return rc;
+  if (c->error != PA_OK) return c->error;
+  // step t's records and histogram, read once step t is done (later steps may run on)
+  cudaStream_t st = nullptr;
+  int rc = read_stream_for(c, t, &st);
+  if (rc != PA_OK) return fail(c, rc);
   const RunGeom& g = c->g;
   std::vector<StepRec> rec((size_t)t + 1);
-  std::vector<uint32_t> hall((size_t)(t + 1) * g.n_levels);
-  rc = copy_d2h(c, rec.data(), c->pops[pop].rec, sizeof(StepRec) * rec.size());
-  if (rc == PA_OK) rc = copy_d2h(c, hall.data(), c->pops[pop].hist, sizeof(uint32_t) * hall.size());
+  std::vector<uint32_t> h((size_t)g.n_levels);
+  int32_t flags = 0;
+  rc = copy_d2h_on(c, st, rec.data(), c->pops[pop].rec, sizeof(StepRec) * rec.size());
+  if (rc == PA_OK)
+    rc = copy_d2h_on(c, st, h.data(), c->pops[pop].hist + (size_t)t * g.n_levels, sizeof(uint32_t) * h.size());
   StepRec r0{};
-  if (rc == PA_OK && g.n_pop == 2) rc = copy_d2h(c, &r0, c->pops[0].rec + t, sizeof r0);
+  if (rc == PA_OK && g.n_pop == 2) rc = copy_d2h_on(c, st, &r0, c->pops[0].rec + t, sizeof r0);
+  if (rc == PA_OK) rc = copy_d2h_on(c, st, &flags, c->status, sizeof flags);
   if (rc != PA_OK) return fail(c, rc);
-  pm1_observables(g, c->betas, rec.data(), hall.data(), t, g.n_pop == 2 ? &r0 : nullptr, out);
+  if (flags & pa::kFlagCapacity) return fail(c, PA_ERR_CAPACITY);
+  if (flags & pa::kFlagExtinct) return fail(c, PA_ERR_EXTINCT);
+  if (flags & pa::kFlagTimeout) return fail(c, PA_ERR_TIMEOUT);
+  pm1_observables(g, c->betas, rec.data(), h.data(), t, g.n_pop == 2 ? &r0 : nullptr, out);
   return PA_OK;
 }
 
@@ -2130,7 +2187,8 @@ int pa_shard_observables(pa_shard* s, int32_t t, int32_t pop, pa_obs* out) {
   if (!s || !out || t < 0 || pop < 0 || pop >= s->c->g.n_pop) return PA_ERR_INVALID;
   if (t > s->c->t) return PA_ERR_STATE;
   const StepRec* r0 = s->c->g.n_pop == 2 ? &s->rec[0][(size_t)t] : nullptr;
-  pm1_observables(s->c->g, s->c->betas, s->rec[pop].data(), s->hist[pop].data(), t, r0, out);
+  pm1_observables(s->c->g, s->c->betas, s->rec[pop].data(), s->hist[pop].data() + (size_t)t * s->c->g.n_levels, t,
+                  r0, out);
   return PA_OK;
 }
 
