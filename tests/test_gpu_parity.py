@@ -181,6 +181,35 @@ def test_sweep_schedule_and_zero_steps(pa, oracle_lib):
         assert_obs_equal(gpu.obs(t), ref.obs(t), f"t={t}")
 
 
+def test_observables_read_while_the_next_step_runs(pa, oracle_lib):
+    """pa_observables(t) waits for step t only: reading step t after step t + 1 (and
+    t + 2) has been issued gives the oracle's step-t observables, for the adaptive
+    schedule (whose pa_step reads the histogram itself) and an explicit one."""
+    for betas in (None, linear(9, 2.0)):
+        kw = dict(n_sweeps=2, disorder_seed=6, run_seed=9)
+        if betas is None:
+            gpu = pa.Run(8, 3000, 6, 9, None, n_temps=40, beta_max=2.0, eps_target=0.3, n_sweeps=2)
+            ref = oracle_lib.Run(oracle_lib.RunConfig(L=8, R=3000, disorder_seed=6, run_seed=9, betas=None,
+                                                      n_temps=40, beta_max=2.0, eps_target=0.3, n_sweeps=2))
+        else:
+            gpu, ref = make_pair(pa, oracle_lib, 8, 3000, betas, **kw)
+        want = [ref.obs(0)]
+        while ref.step() == 0:
+            want.append(ref.obs(ref.t))
+        got, t = [], 0
+        while gpu.step() == 0:
+            if gpu.t >= 2:
+                got.append(gpu.obs(gpu.t - 2))   # two steps behind
+            t = gpu.t
+        for u in range(max(0, t - 1), t + 1):
+            got.append(gpu.obs(u))
+        assert t == ref.t and len(got) == len(want)
+        for u, (g, r) in enumerate(zip(got, want)):
+            assert_obs_equal(g, r, f"t={u}")
+        assert_obs_equal(gpu.obs(1), want[1], "t=1 read last")   # an old step, whose own event was reused
+        gpu.close()
+
+
 def test_capacity_overflow_is_reported(pa, oracle_lib):
     betas = linear(6, 3.0)
     for run_seed in range(20):
@@ -195,6 +224,12 @@ def test_capacity_overflow_is_reported(pa, oracle_lib):
     gpu = pa.Run(4, 500, 1, run_seed, betas, n_sweeps=1, R_cap=500)
     with pytest.raises(pa.PAError) as e:
         gpu.run()
+    assert e.value.status == pa.PA_ERR_CAPACITY
+    # the same error through the observables of each step (which wait for that step only)
+    gpu = pa.Run(4, 500, 1, run_seed, betas, n_sweeps=1, R_cap=500)
+    with pytest.raises(pa.PAError) as e:
+        while gpu.step() == 0:
+            gpu.obs(gpu.t)
     assert e.value.status == pa.PA_ERR_CAPACITY
 
 
