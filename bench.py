@@ -523,6 +523,28 @@ def gaussian_measurement(pa, steps: int, warmup: int, n_sm: int, cpu: bool, R: i
            "phase_share": {k: v / max(ms, 1e-9) for k, v in st["phase_ms"].items()},
            "last_step": {"beta": o["beta"], "R_tilde": o["R_tilde"], "mean_E_per_spin": o["mean_E"] / w.N,
                          "rho_t": o["rho_t"]}}
+    # the same model with the adaptive schedule (constant culling fraction 0.272 to beta = 5),
+    # whose steps include the on-device bisection of dbeta
+    wa = w.with_(betas=None, n_temps=4096, beta_max=5.0, eps_target=0.272, name=w.name.replace("linear101", "adaptive"))
+    run = pa.Run.from_workload(wa, stream=stream)
+    for _ in range(warmup):
+        run.step()
+    run.sync()
+    run.stats_reset(timing=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n_ad = 0
+    for _ in range(steps):
+        if run.step() != 0:
+            break
+        n_ad += 1
+    run.sync()
+    dt = time.perf_counter() - t0
+    sta = run.stats()
+    out["adaptive"] = {"workload": wa.name, "steps_timed": n_ad, "ms_per_step": 1e3 * dt / max(n_ad, 1),
+                       "updates_per_s": sta["updates"] / dt, "beta_reached": run.beta(run.t),
+                       "timing": "host clock around the steps (each step waits for the device's bisection)"}
+    run.close()
     if cpu:
         import oracle
         oracle.build()

@@ -90,8 +90,77 @@ __device__ __forceinline__ void chunk_tree(double* a) {
   }
 }
 
-// Weights of the old slots of step t-1 and their chunk partial sums.  Block 0
-// also opens the records of step t.
+// Whether this block is the last of the launch's n_blocks blocks (of its
+// population) to finish: each block, once its chunk total is written, counts
+// itself on the ticket; the last one sums every total (tree_total) and resets it.
+__device__ __forceinline__ bool last_block_done(int32_t* ticket, int n_blocks) {
+  __shared__ int last;
+  __syncthreads();  // the block's chunk total is written
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(ticket, 1) == n_blocks - 1;
+    if (last) *ticket = 0;
+  }
+  __syncthreads();
+  return last;
+}
+
+// The chunk_tree sum of the 256 entries src[base, base + 256) (zeros from n on),
+// by one warp: lane l holds entries l + 32 k, so the tree's steps 128, 64 and 32 are
+// additions within a lane and 16 .. 1 additions across lanes, each pair added in
+// the tree's order.  The sum in lane 0.
+__device__ __forceinline__ double warp_group_sum(const double* src, long long base, int n) {
+  const int lane = threadIdx.x & 31;
+  double v[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const long long i = base + lane + 32 * k;
+    v[k] = i < n ? __ldcg(src + i) : 0.0;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) v[k] = __dadd_rn(v[k], v[k + 4]);
+  v[0] = __dadd_rn(v[0], v[2]);
+  v[1] = __dadd_rn(v[1], v[3]);
+  v[0] = __dadd_rn(v[0], v[1]);
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) v[0] = __dadd_rn(v[0], __shfl_down_sync(0xffffffffu, v[0], h));
+  return v[0];
+}
+
+// The sum of the n_chunks chunk totals at the start of part by a fixed tree, in
+// this one block: each level's entries in groups of 256 (zeros past its last
+// entry) added by the chunk_tree order (warp_group_sum, one warp per group), the
+// group sums stored after the level's entries in part as the next level, until one
+// group is left.  The order depends only on n_chunks, so every launch adds in the
+// same order.  The total in thread 0.
+__device__ double tree_total(double* part, int n_chunks) {
+  __threadfence();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, n_warps = blockDim.x >> 5;
+  long long off = 0;
+  int n = n_chunks;
+  double total = 0.0;
+  for (;;) {
+    const int nb = (n + kChunk - 1) / kChunk;
+    for (int b = warp; b < nb; b += n_warps) {
+      const double v = warp_group_sum(part + off, (long long)b * kChunk, n);
+      if (lane == 0) {
+        if (nb == 1)
+          total = v;
+        else
+          part[off + n + b] = v;
+      }
+    }
+    __syncthreads();
+    if (nb == 1) break;
+    off += n;
+    n = nb;
+  }
+  return total;
+}
+
+// Weights of the old slots of step t-1 and their chunk partial sums; the last
+// block to finish adds the partial sums into S'.  Block 0 also opens the records
+// of step t.
 __global__ void __launch_bounds__(kChunk) k_g_weights(RunGeom g, GArgs a, int t, const double* __restrict__ T) {
   __shared__ double sh[kChunk];
   PopDev& P = a.p[blockIdx.y];
@@ -108,6 +177,10 @@ __global__ void __launch_bounds__(kChunk) k_g_weights(RunGeom g, GArgs a, int t,
   __syncthreads();
   chunk_tree(sh);
   if (threadIdx.x == 0) P.part[blockIdx.x] = sh[0];
+  if (last_block_done(P.ticket, (int)gridDim.x)) {
+    const double S = tree_total(P.part, (int)gridDim.x);
+    if (threadIdx.x == 0) P.rec[t].S_prime = S;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     P.rec[t].R_prev = R_old;
     GRec& r = P.grec[t];
@@ -120,46 +193,13 @@ __global__ void __launch_bounds__(kChunk) k_g_weights(RunGeom g, GArgs a, int t,
   }
 }
 
-// One level of the fixed-order sum: block b reduces entries [256 b, 256 b + 256)
-// of part + in_off (zeros past n_in) by the binary tree into part[out_off + b];
-// the last level (one block) writes S' (which = 0) or the expected culling
-// fraction (which = 1, divided by R) instead.  Entries past a population's own
-// chunk count are zero, and adding +0.0 is exact, so counting up to the capacity
-// gives the same sum.
-__global__ void __launch_bounds__(kChunk) k_g_level(RunGeom g, GArgs a, int t, long long in_off, int n_in,
-                                                   long long out_off, int which) {
-  __shared__ double sh[kChunk];
-  PopDev& P = a.p[blockIdx.y];
-  const int i = blockIdx.x * kChunk + threadIdx.x;
-  sh[threadIdx.x] = i < n_in ? P.part[in_off + i] : 0.0;
-  __syncthreads();
-  chunk_tree(sh);
-  if (threadIdx.x != 0) return;
-  if (which < 0)
-    P.part[out_off + blockIdx.x] = sh[0];
-  else if (which == 0)
-    P.rec[t].S_prime = sh[0];
-  else
-    P.rec[t].eps_expected = __ddiv_rn(sh[0], (double)g.R);
-}
-
-// All levels over the n_chunks chunk totals at the start of part (scratch for
-// the upper levels follows them: tree_sum_scratch entries in all).
-void launch_levels(const RunGeom& g, const GArgs& a, int n_pop, int t, int which, cudaStream_t s) {
-  long long off = 0;
-  int n = g.n_chunks;
-  for (;;) {
-    const int nb = blocks_for(n, kChunk);
-    k_g_level<<<dim3(nb, n_pop), kChunk, 0, s>>>(g, a, t, off, n, off + n, nb == 1 ? which : -1);
-    if (nb == 1) break;
-    off += n;
-    n = nb;
-  }
-}
-
 // tau_i = R w_i / S', its floor and 2^32-scaled fraction, and the chunk partial
-// sums of (1 - tau_i)_+.
-__global__ void __launch_bounds__(kChunk) k_g_tau(RunGeom g, GArgs a, int t) {
+// sums of (1 - tau_i)_+; the last block to finish adds them into the expected
+// culling fraction.  In the adaptive bisection (b = {lo, hi, mid}, population 0
+// only) that block also takes the halving's decision: mid becomes lo when the
+// fraction does not exceed the target, else hi, and the next midpoint is
+// 0.5 (lo + hi) (the host's arithmetic, rounded the same way).
+__global__ void __launch_bounds__(kChunk) k_g_tau(RunGeom g, GArgs a, int t, double* b, double target) {
   __shared__ double sh[kChunk];
   PopDev& P = a.p[blockIdx.y];
   const int R_old = P.rec[t - 1].R_tilde;
@@ -177,6 +217,20 @@ __global__ void __launch_bounds__(kChunk) k_g_tau(RunGeom g, GArgs a, int t) {
   __syncthreads();
   chunk_tree(sh);
   if (threadIdx.x == 0) P.part[blockIdx.x] = sh[0];
+  if (last_block_done(P.ticket, (int)gridDim.x)) {
+    const double total = tree_total(P.part, (int)gridDim.x);
+    if (threadIdx.x == 0) {
+      const double e = __ddiv_rn(total, (double)g.R);
+      P.rec[t].eps_expected = e;
+      if (b) {
+        if (e <= target)
+          b[0] = b[2];
+        else
+          b[1] = b[2];
+        b[2] = __dmul_rn(0.5, __dadd_rn(b[0], b[1]));
+      }
+    }
+  }
 }
 
 // Copy numbers n_i = fl_i + [r_i < thr_i], r_i = word (i & 3) of Philox at counter
@@ -227,19 +281,6 @@ __global__ void k_g_tables(const double* __restrict__ dbeta_dev, double dbeta_va
   const double db = dbeta_dev ? *dbeta_dev : dbeta_val;
   const long long q = m < 4096 ? (long long)m : m < 8192 ? (long long)(m - 4096) << 12 : (long long)(m - 8192) << 24;
   T[m] = exp(-__dmul_rn(db, __dmul_rn((double)q, 0x1p-20)));
-}
-
-// One halving of the bisection (§IV.B): b = {lo, hi, mid}; the trial at mid gave
-// population 0's culling fraction in its step-t record.  Keeps mid as lo when the
-// fraction does not exceed the target, else as hi, and sets the next midpoint
-// 0.5 (lo + hi) (the host's arithmetic, rounded the same way).
-__global__ void k_g_decide(GArgs a, int t, double target, double* b) {
-  const double e = a.p[0].rec[t].eps_expected;
-  if (e <= target)
-    b[0] = b[2];
-  else
-    b[1] = b[2];
-  b[2] = __dmul_rn(0.5, __dadd_rn(b[0], b[1]));
 }
 
 // ---------------------------------------------------------------- measurement
@@ -402,25 +443,27 @@ int launch_g_resample(const RunGeom& g, PopDev* pops, int cur, int t, const doub
   GArgs a = gpack(pops, g.n_pop);
   const dim3 chunks(g.n_chunks, g.n_pop);
   k_g_weights<<<chunks, kChunk, 0, s>>>(g, a, t, wtab);
-  launch_levels(g, a, g.n_pop, t, 0, s);
-  k_g_tau<<<chunks, kChunk, 0, s>>>(g, a, t);
-  launch_levels(g, a, g.n_pop, t, 1, s);
+  k_g_tau<<<chunks, kChunk, 0, s>>>(g, a, t, nullptr, 0.0);
   k_g_counts<<<dim3(g.n_count_blocks, g.n_pop), kCountThreads, 0, s>>>(g, a, t);
   const int e = (int)cudaGetLastError();
   return e ? e : launch_scan_scatter(g, pops, cur, t, status, stream);
 }
 
-int launch_g_eps_trial(const RunGeom& g, PopDev* pops, int t, const double* wtab, void* stream) {
-  cudaStream_t s = (cudaStream_t)stream;
+// One trial of the adaptive schedule on population 0; with b, also the bisection's
+// halving that follows from it.
+static int eps_trial(const RunGeom& g, PopDev* pops, int t, const double* wtab, double* b, double target,
+                     cudaStream_t s) {
   RunGeom g1 = g;  // population 0 decides the step
   g1.n_pop = 1;
   GArgs a = gpack(pops, 1);
   const dim3 chunks(g1.n_chunks, 1);
   k_g_weights<<<chunks, kChunk, 0, s>>>(g1, a, t, wtab);
-  launch_levels(g1, a, 1, t, 0, s);
-  k_g_tau<<<chunks, kChunk, 0, s>>>(g1, a, t);
-  launch_levels(g1, a, 1, t, 1, s);
+  k_g_tau<<<chunks, kChunk, 0, s>>>(g1, a, t, b, target);
   return (int)cudaGetLastError();
+}
+
+int launch_g_eps_trial(const RunGeom& g, PopDev* pops, int t, const double* wtab, void* stream) {
+  return eps_trial(g, pops, t, wtab, nullptr, 0.0, (cudaStream_t)stream);
 }
 
 int launch_g_tables(const double* dbeta_dev, double dbeta_val, double* T, void* stream) {
@@ -431,12 +474,10 @@ int launch_g_tables(const double* dbeta_dev, double dbeta_val, double* T, void* 
 int launch_g_bisect(const RunGeom& g, PopDev* pops, int t, double* T, double* b, double target, int halvings,
                     void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  GArgs a = gpack(pops, 1);
   for (int it = 0; it < halvings; ++it) {
     k_g_tables<<<blocks_for(kGTableWeights, 256), 256, 0, s>>>(b + 2, 0.0, T);
-    const int e = launch_g_eps_trial(g, pops, t, T, stream);
+    const int e = eps_trial(g, pops, t, T, b, target, s);
     if (e) return e;
-    k_g_decide<<<1, 1, 0, s>>>(a, t, target, b);
   }
   return (int)cudaGetLastError();
 }

@@ -1029,6 +1029,8 @@ int create_run_impl(const pa_config* cfg, void* cuda_stream, pa_ctx** out, bool 
     if (rc == PA_OK)
       rc = cuda_status(cudaMemsetAsync(c->pops[p].fhist, 0, sizeof(int32_t) * ((size_t)g.R_cap + 1), s));
     if (rc == PA_OK) rc = cuda_status(cudaMemsetAsync(c->pops[p].fcount, 0, sizeof(int32_t) * 2, s));
+    if (rc == PA_OK)  // the block count of the Gaussian model's last-block sums
+      rc = cuda_status(cudaMemsetAsync(c->pops[p].ticket, 0, sizeof(int32_t), s));
     if (rc == PA_OK)  // every parent entry is a valid slot at all times, even where a failed step leaves gaps
       rc = cuda_status(cudaMemsetAsync(c->pops[p].parents, 0, sizeof(int32_t) * (size_t)g.pitch, s));
   }
