@@ -927,10 +927,13 @@ __device__ __forceinline__ void sweep_rows_g(uint32_t* sp, const SiteRec* recs, 
       const uint32_t P1 = (s0 ^ row[xp]) | ((s0 ^ row[xm]) << 1) | ((s0 ^ pyp[x * W]) << 2);
       const uint32_t P2 = (s0 ^ pym[x * W]) | ((s0 ^ pzp[x * W]) << 1) | ((s0 ^ pzm[x * W]) << 2);
       const uint32_t* tb = gtab + (size_t)(r * L + x) * kGPatterns;
+      // byte k of Qe (Qo) is the pattern of replica 2k (2k + 1): its P1 bits, then its P2 bits
+      const uint32_t Qe = (P1 & 0x0F0F0F0Fu) | ((P2 & 0x0F0F0F0Fu) << 3);
+      const uint32_t Qo = ((P1 >> 4) & 0x0F0F0F0Fu) | (((P2 >> 4) & 0x0F0F0F0Fu) << 3);
       uint32_t flip = 0, tie = 0;
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const uint32_t b = ((P1 >> (4 * i)) & 7u) | (((P2 >> (4 * i)) & 7u) << 3);  // the replica's pattern
+        const uint32_t b = __byte_perm((i & 1) ? Qo : Qe, 0u, 0x4440u + (uint32_t)(i >> 1));  // the replica's pattern
         const uint32_t thr = __ldg(tb + b);
         const uint32_t u = (i & 1) ? (w4[i >> 1] & 0xffff0000u) : (w4[i >> 1] << 16);
         if (thr == 0xFFFFFFFFu || (u | 0xffffu) < thr) flip |= 1u << (4 * i);
