@@ -936,7 +936,9 @@ __device__ __forceinline__ void sweep_rows_g(uint32_t* sp, const SiteRec* recs, 
         const uint32_t b = __byte_perm((i & 1) ? Qo : Qe, 0u, 0x4440u + (uint32_t)(i >> 1));  // the replica's pattern
         const uint32_t thr = __ldg(tb + b);
         const uint32_t u = (i & 1) ? (w4[i >> 1] & 0xffff0000u) : (w4[i >> 1] << 16);
-        if (thr == 0xFFFFFFFFu || (u | 0xffffu) < thr) flip |= 1u << (4 * i);
+        // a flip with dE <= 0 (thr = 0xFFFFFFFF) passes here unless u = 0xFFFF0000,
+        // which the tie path takes
+        if ((u | 0xffffu) < thr) flip |= 1u << (4 * i);
         else if (u < thr) tie |= 1u << i;
       }
       while (tie) {  // rare: the lower 16 bits decide
@@ -944,7 +946,9 @@ __device__ __forceinline__ void sweep_rows_g(uint32_t* sp, const SiteRec* recs, 
         tie &= tie - 1;
         const uint32_t b = ((P1 >> (4 * i)) & 7u) | (((P2 >> (4 * i)) & 7u) << 3);
         const uint32_t u = (i & 1) ? (w4[i >> 1] & 0xffff0000u) : (w4[i >> 1] << 16);
-        if ((u | g_tie_word(h, q, slot0 + (uint32_t)i, t, k0[0], k1[0])) < __ldg(tb + b)) flip |= 1u << (4 * i);
+        const uint32_t thr = __ldg(tb + b);
+        if (thr == 0xFFFFFFFFu || (u | g_tie_word(h, q, slot0 + (uint32_t)i, t, k0[0], k1[0])) < thr)
+          flip |= 1u << (4 * i);
       }
       p0[x * W] = s0 ^ flip;
     }
