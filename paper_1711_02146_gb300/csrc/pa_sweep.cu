@@ -90,7 +90,9 @@ struct SweepShape {
   static constexpr int ROWS = L * L;
   static constexpr int NP = NT / W;  // row partitions
   static constexpr int TJ = 8 * W;   // replicas per tile
+  static constexpr int RPP = ROWS / NP;  // rows per partition
   static constexpr size_t SMEM = (size_t)N * W * 4 + (size_t)N * sizeof(SiteRec) + (size_t)TJ * 4;
+  static constexpr size_t SMEM_ROWS = (size_t)NP * RPP * 8 * sizeof(int);  // the row table
   static_assert(NT % W == 0, "threads must tile the words of a row");
   static_assert(32 % W == 0, "a warp must cover whole rows");
   static_assert(L % 2 == 0 && L / 2 <= 8, "even L up to 16");
@@ -136,6 +138,29 @@ __device__ __forceinline__ int row_index(int part, int k, int p) {
   const int z = i / H;
   const int y = 2 * (i % H) + ((p + z) & 1);
   return y + L * z;
+}
+
+// Per partition and row (rows of the partition's parity class, row_index), the
+// word offsets of the row and of its four neighbour rows in a tile of W words per
+// site and the row's first site: {row, y+1, y-1, z+1, first site, z-1}.  A
+// thread's rows never change, so each tile fills this once.
+template <int L, int W, int NP>
+__device__ __forceinline__ void fill_row_table(int* rowtab, int tid, int nthreads) {
+  constexpr int RPP = L * L / NP;
+  for (int e = tid; e < NP * RPP; e += nthreads) {
+    const int pt = e / RPP, kr = e % RPP;
+    const int r = row_index<L, NP>(pt, kr, pt / (NP / 2));
+    const int y = r % L, z = r / L;
+    const int yp = y == L - 1 ? 0 : y + 1, ym = y == 0 ? L - 1 : y - 1;
+    const int zp = z == L - 1 ? 0 : z + 1, zm = z == 0 ? L - 1 : z - 1;
+    int* o = rowtab + 8 * e;
+    o[0] = r * L * W;
+    o[1] = (yp + L * z) * L * W;
+    o[2] = (ym + L * z) * L * W;
+    o[3] = (y + L * zp) * L * W;
+    o[4] = r * L;
+    o[5] = (y + L * zm) * L * W;
+  }
 }
 
 // int8 spins (0x01 / 0xFF) of four replicas -> nibbles 0..3 (bit 1 of a byte is the sign)
@@ -704,22 +729,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, uint32_t* sm, int
   const int tid = threadIdx.x, word = tid % W, part = tid / W;
   Deferred* dq = queues + (S::DEFER ? (tid >> 5) * kQueueCap : 0);
   init_tables<L>(a, recs, tid, NT);
-  if constexpr (S::DEFER) {
-    for (int e = tid; e < NP * S::RPP; e += NT) {
-      const int pt = e / S::RPP, kr = e % S::RPP;
-      const int r = row_index<L, NP>(pt, kr, pt / (NP / 2));
-      const int y = r % L, z = r / L;
-      const int yp = y == L - 1 ? 0 : y + 1, ym = y == 0 ? L - 1 : y - 1;
-      const int zp = z == L - 1 ? 0 : z + 1, zm = z == 0 ? L - 1 : z - 1;
-      int* o = rowtab + 8 * e;
-      o[0] = r * L * W;
-      o[1] = (yp + L * z) * L * W;
-      o[2] = (ym + L * z) * L * W;
-      o[3] = (y + L * zp) * L * W;
-      o[4] = r * L;
-      o[5] = (y + L * zm) * L * W;
-    }
-  }
+  if constexpr (S::DEFER) fill_row_table<L, W, NP>(rowtab, tid, NT);
   for (int i = tid; i < TJ; i += NT) slots[33 * (i >> 5) + (i & 31)] = tile0 + i < R_new ? a.pop.parents[tile0 + i] : -1;
   __syncthreads();
   gather_bits<L, W, NP>(a, sp, slots, word, part);
@@ -896,22 +906,20 @@ __device__ __noinline__ uint32_t g_tie_word(uint32_t h, uint32_t q, uint32_t slo
 }
 
 template <int L, int W, int NP, int X0>
-__device__ __forceinline__ void sweep_rows_g(uint32_t* sp, const SiteRec* recs, int part, int p,
+__device__ __forceinline__ void sweep_rows_g(uint32_t* sp, const SiteRec* recs, int part, const int* rowtab,
                                              const ThreadPhilox& tp, const uint32_t* k0, const uint32_t* k1,
                                              const uint32_t* __restrict__ gtab, uint32_t slot0, uint32_t q,
                                              uint32_t t) {
   constexpr int H = L / 2, RPP = L * L / NP;
 #pragma unroll 1
   for (int k = 0; k < RPP; ++k) {
-    const int r = row_index<L, NP>(part, k, p);
-    const int y = r % L, z = r / L;
-    const int yp = y == L - 1 ? 0 : y + 1, ym = y == 0 ? L - 1 : y - 1;
-    const int zp = z == L - 1 ? 0 : z + 1, zm = z == 0 ? L - 1 : z - 1;
-    uint32_t* p0 = sp + (size_t)r * L * W;
-    const uint32_t* pyp = sp + (size_t)(yp + L * z) * L * W;
-    const uint32_t* pym = sp + (size_t)(ym + L * z) * L * W;
-    const uint32_t* pzp = sp + (size_t)(y + L * zp) * L * W;
-    const uint32_t* pzm = sp + (size_t)(y + L * zm) * L * W;
+    const int4 e0 = *reinterpret_cast<const int4*>(rowtab + 8 * (part * RPP + k));
+    const int rL = rowtab[8 * (part * RPP + k) + 4];  // the row's first site
+    uint32_t* p0 = sp + e0.x;
+    const uint32_t* pyp = sp + e0.y;
+    const uint32_t* pym = sp + e0.z;
+    const uint32_t* pzp = sp + e0.w;
+    const uint32_t* pzm = sp + rowtab[8 * (part * RPP + k) + 5];
     uint32_t row[L];
 #pragma unroll
     for (int x = 0; x < L; ++x) row[x] = p0[x * W];
@@ -920,13 +928,13 @@ __device__ __forceinline__ void sweep_rows_g(uint32_t* sp, const SiteRec* recs, 
       const int x = 2 * xh + X0;
       const int xp = x == L - 1 ? 0 : x + 1;
       const int xm = x == 0 ? L - 1 : x - 1;
-      const uint32_t h = (uint32_t)(r * L) / 2u + (uint32_t)xh;
+      const uint32_t h = (uint32_t)rL / 2u + (uint32_t)xh;
       uint32_t w4[4];
-      philox_block(kM0 * h, recs[r * L + x], tp, k0, k1, w4);
+      philox_block(kM0 * h, recs[rL + x], tp, k0, k1, w4);
       const uint32_t s0 = row[x];
       const uint32_t P1 = (s0 ^ row[xp]) | ((s0 ^ row[xm]) << 1) | ((s0 ^ pyp[x * W]) << 2);
       const uint32_t P2 = (s0 ^ pym[x * W]) | ((s0 ^ pzp[x * W]) << 1) | ((s0 ^ pzm[x * W]) << 2);
-      const uint32_t* tb = gtab + (size_t)(r * L + x) * kGPatterns;
+      const uint32_t* tb = gtab + (size_t)(rL + x) * kGPatterns;
       // byte k of Qe (Qo) is the pattern of replica 2k (2k + 1): its P1 bits, then its P2 bits
       const uint32_t Qe = (P1 & 0x0F0F0F0Fu) | ((P2 & 0x0F0F0F0Fu) << 3);
       const uint32_t Qo = ((P1 >> 4) & 0x0F0F0F0Fu) | (((P2 >> 4) & 0x0F0F0F0Fu) << 3);
@@ -994,11 +1002,13 @@ __global__ void __launch_bounds__(NT, MB) k_sweep_g(const __grid_constant__ GSwe
   uint32_t* sp = sm;
   SiteRec* recs = reinterpret_cast<SiteRec*>(sm + (size_t)N * W);
   long long* ecnt = reinterpret_cast<long long*>(recs + N);
+  int* rowtab = reinterpret_cast<int*>(ecnt + TJ);  // [NP][RPP][8], as the +-1 kernel's
   const int R_new = a.pop.rec[a.t].R_tilde;
   const int tile0 = blockIdx.x * TJ;
   if (tile0 >= R_new) return;
   const int tid = threadIdx.x, word = tid % W, part = tid / W;
   init_tables<L>(a, recs, tid, NT);
+  fill_row_table<L, W, NP>(rowtab, tid, NT);
   for (int i = tid; i < TJ; i += NT) ecnt[i] = 0;
   gather_tile<L, W, NP>(a, sp, tile0, R_new, word, part);
   __syncthreads();
@@ -1012,9 +1022,9 @@ __global__ void __launch_bounds__(NT, MB) k_sweep_g(const __grid_constant__ GSwe
       const uint32_t q = 2u * (uint32_t)s + (uint32_t)c;
       const ThreadPhilox tp = thread_philox(g, q, a.k0, a.k1);
       if ((pclass ^ c) == 0)
-        sweep_rows_g<L, W, NP, 0>(spw, recs, part, pclass, tp, a.k0, a.k1, ga.gtab, slot0, q, (uint32_t)a.t);
+        sweep_rows_g<L, W, NP, 0>(spw, recs, part, rowtab, tp, a.k0, a.k1, ga.gtab, slot0, q, (uint32_t)a.t);
       else
-        sweep_rows_g<L, W, NP, 1>(spw, recs, part, pclass, tp, a.k0, a.k1, ga.gtab, slot0, q, (uint32_t)a.t);
+        sweep_rows_g<L, W, NP, 1>(spw, recs, part, rowtab, tp, a.k0, a.k1, ga.gtab, slot0, q, (uint32_t)a.t);
       __syncthreads();
     }
   }
@@ -1030,7 +1040,7 @@ __global__ void __launch_bounds__(NT, MB) k_sweep_g(const __grid_constant__ GSwe
 template <int L, int W, int NT, int MB>
 static int launch_g_t(const RunGeom& g, const GSweepArgs& args, cudaStream_t s) {
   using S = SweepShape<L, W, NT>;
-  const size_t smem = S::SMEM + (size_t)S::TJ * 4;  // energy counters are 8 bytes, not 4
+  const size_t smem = S::SMEM + (size_t)S::TJ * 4 + S::SMEM_ROWS;  // energy counters are 8 bytes, not 4
   static std::atomic<int> done[64];
   const cudaError_t e = smem_limit_once(k_sweep_g<L, W, NT, MB>, (int)smem, done);
   if (e != cudaSuccess) return (int)e;
