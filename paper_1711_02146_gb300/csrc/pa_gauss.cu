@@ -193,13 +193,17 @@ __global__ void __launch_bounds__(kChunk) k_g_weights(RunGeom g, GArgs a, int t,
   }
 }
 
-// tau_i = R w_i / S', its floor and 2^32-scaled fraction, and the chunk partial
-// sums of (1 - tau_i)_+; the last block to finish adds them into the expected
-// culling fraction.  In the adaptive bisection (b = {lo, hi, mid}, population 0
-// only) that block also takes the halving's decision: mid becomes lo when the
-// fraction does not exceed the target, else hi, and the next midpoint is
-// 0.5 (lo + hi) (the host's arithmetic, rounded the same way).
-__global__ void __launch_bounds__(kChunk) k_g_tau(RunGeom g, GArgs a, int t, double* b, double target) {
+// tau_i = R w_i / S', its floor and 2^32-scaled fraction (not in a trial of the
+// adaptive schedule, which needs only the culling fraction), and the chunk partial
+// sums of S' (1 - tau_i)_+ = (S' - R w_i)_+; the last block to finish adds them and
+// divides by S' R into the expected culling fraction (Eq. eq_num_elim: the same sum
+// with one division instead of one per replica).  In the adaptive bisection
+// (b = {lo, hi, mid}, population 0 only) that block also takes the halving's
+// decision: mid becomes lo when the fraction does not exceed the target, else hi,
+// and the next midpoint is 0.5 (lo + hi) (the host's arithmetic, rounded the same
+// way).
+__global__ void __launch_bounds__(kChunk) k_g_tau(RunGeom g, GArgs a, int t, double* b, double target,
+                                                 int trial) {
   __shared__ double sh[kChunk];
   PopDev& P = a.p[blockIdx.y];
   const int R_old = P.rec[t - 1].R_tilde;
@@ -207,11 +211,14 @@ __global__ void __launch_bounds__(kChunk) k_g_tau(RunGeom g, GArgs a, int t, dou
   const int i = blockIdx.x * kChunk + threadIdx.x;
   double c = 0.0;
   if (i < R_old) {
-    const double tau = __ddiv_rn(__dmul_rn((double)g.R, P.w[i]), S);
-    const double f = floor(tau);
-    P.gfl[i] = (int32_t)f;
-    P.gthr[i] = __double2uint_rz(__dmul_rn(__dsub_rn(tau, f), 4294967296.0));
-    c = tau < 1.0 ? __dsub_rn(1.0, tau) : 0.0;
+    const double rw = __dmul_rn((double)g.R, P.w[i]);
+    if (!trial) {
+      const double tau = __ddiv_rn(rw, S);
+      const double f = floor(tau);
+      P.gfl[i] = (int32_t)f;
+      P.gthr[i] = __double2uint_rz(__dmul_rn(__dsub_rn(tau, f), 4294967296.0));
+    }
+    c = rw < S ? __dsub_rn(S, rw) : 0.0;
   }
   sh[threadIdx.x] = c;
   __syncthreads();
@@ -220,7 +227,7 @@ __global__ void __launch_bounds__(kChunk) k_g_tau(RunGeom g, GArgs a, int t, dou
   if (last_block_done(P.ticket, (int)gridDim.x)) {
     const double total = tree_total(P.part, (int)gridDim.x);
     if (threadIdx.x == 0) {
-      const double e = __ddiv_rn(total, (double)g.R);
+      const double e = __ddiv_rn(__ddiv_rn(total, S), (double)g.R);
       P.rec[t].eps_expected = e;
       if (b) {
         if (e <= target)
@@ -443,7 +450,7 @@ int launch_g_resample(const RunGeom& g, PopDev* pops, int cur, int t, const doub
   GArgs a = gpack(pops, g.n_pop);
   const dim3 chunks(g.n_chunks, g.n_pop);
   k_g_weights<<<chunks, kChunk, 0, s>>>(g, a, t, wtab);
-  k_g_tau<<<chunks, kChunk, 0, s>>>(g, a, t, nullptr, 0.0);
+  k_g_tau<<<chunks, kChunk, 0, s>>>(g, a, t, nullptr, 0.0, 0);
   k_g_counts<<<dim3(g.n_count_blocks, g.n_pop), kCountThreads, 0, s>>>(g, a, t);
   const int e = (int)cudaGetLastError();
   return e ? e : launch_scan_scatter(g, pops, cur, t, status, stream);
@@ -458,7 +465,7 @@ static int eps_trial(const RunGeom& g, PopDev* pops, int t, const double* wtab, 
   GArgs a = gpack(pops, 1);
   const dim3 chunks(g1.n_chunks, 1);
   k_g_weights<<<chunks, kChunk, 0, s>>>(g1, a, t, wtab);
-  k_g_tau<<<chunks, kChunk, 0, s>>>(g1, a, t, b, target);
+  k_g_tau<<<chunks, kChunk, 0, s>>>(g1, a, t, b, target, 1);
   return (int)cudaGetLastError();
 }
 
