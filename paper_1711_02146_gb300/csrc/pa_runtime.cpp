@@ -47,6 +47,7 @@ struct pa_ctx {
   std::map<uint64_t, double*> wtables;
   std::vector<double> wtables_host;  // host copy of the explicit schedule's tables (source of their upload)
   double* wadapt = nullptr;     // adaptive schedule: the table of the current step
+  double* wadapt_host = nullptr;  // its pinned host copy (uploaded without a wait)
   // All device buffers of the run are carved from one stream-ordered allocation:
   // a run costs the memory pool one block, so the pool's free list stays short
   // when many runs come and go (a request server).
@@ -411,8 +412,24 @@ int weight_table(pa_ctx* c, double dbeta, const double** out) {
     return PA_OK;
   }
   std::vector<double> w = host_weights(c->g.n_levels, dbeta);
-  const int rc = copy_h2d(c, c->wadapt, w.data(), sizeof(double) * w.size());
-  if (rc != PA_OK) return rc;
+  const size_t bytes = sizeof(double) * w.size();
+  if (!c->wadapt_host) {  // pinned, so the upload need not wait (first use; else plain copies)
+    void* h = nullptr;
+    if (cudaMallocHost(&h, bytes) == cudaSuccess)
+      c->wadapt_host = static_cast<double*>(h);
+    else
+      cudaGetLastError();
+  }
+  if (!c->wadapt_host) {
+    const int rc = copy_h2d(c, c->wadapt, w.data(), bytes);
+    if (rc != PA_OK) return rc;
+  } else {
+    // the previous step's upload from this buffer is done: choose_dbeta synchronised the
+    // stream before this step's table was built
+    std::memcpy(c->wadapt_host, w.data(), bytes);
+    const int rc = copy_async(c, c->wadapt, c->wadapt_host, bytes);
+    if (rc != PA_OK) return rc;
+  }
   *out = c->wadapt;
   return PA_OK;
 }
@@ -614,6 +631,7 @@ void destroy(pa_ctx* c) {
   for (cudaEvent_t e : c->step_ev)
     if (e) cudaEventDestroy(e);
   if (c->rd) cudaStreamDestroy(c->rd);
+  if (c->wadapt_host) cudaFreeHost(c->wadapt_host);
   delete c;
 }
 
