@@ -215,6 +215,41 @@ def small_config_full_run(pa, cores: int):
             "final_minus_beta_F_gpu": g["minus_beta_F"], "final_minus_beta_F_oracle": o.obs(o.t)["minus_beta_F"]}
 
 
+def two_population_full_run(pa, cpu: bool, cores: int):
+    """The overlap workload (L = 8, R = 1e5 per population, two populations, 201 linear
+    temperatures to beta = 5, 10 sweeps) run to its end on the GPU (creation included),
+    and, with cpu, the oracle timed on its first temperature steps with R = 5000."""
+    import torch
+    from paper_1711_02146_gb300.workloads import C2
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    run = pa.Run.from_workload(C2)
+    run.run()
+    run.sync()
+    dt = time.perf_counter() - t0
+    st = run.stats()
+    o = run.obs(run.t)
+    run.close()
+    out = {"workload": f"{C2.name}: L=8, R=1e5 x 2 populations, 201 linear temperatures to beta=5, 10 sweeps",
+           "seconds": dt, "updates_per_s": st["updates"] / dt, "I02_final": o["I02"], "rho_t_final": o["rho_t"],
+           "timing": "host clock around creation and the whole run (pa_run), one synchronisation"}
+    if cpu:
+        import oracle
+        oracle.build()
+        ref = oracle.Run(oracle.RunConfig(L=C2.L, R=5000, disorder_seed=C2.disorder_seed, run_seed=C2.run_seed,
+                                          betas=C2.betas, n_sweeps=C2.n_sweeps, n_pop=2, q_bins=C2.q_bins,
+                                          n_threads=cores))
+        updates, n, t0 = 0, 0, time.perf_counter()
+        while n < 20 and time.perf_counter() - t0 < 5.0:
+            ref.step()
+            n += 1
+            updates += C2.n_sweeps * C2.N * (ref.obs(ref.t, 0)["R_tilde"] + ref.obs(ref.t, 1)["R_tilde"])
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": updates / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"first {n} temperature steps of the same run with R=5000 ({dt:.1f} s)"}
+    return out
+
+
 def cpu_model() -> str:
     try:
         out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
@@ -717,6 +752,8 @@ def ours(args):
     if rank == 0 and world == 1 and args.served_requests > 0:
         free, _ = torch.cuda.mem_get_info()
         line["served"] = served_vs_serial(pa, args.served_requests, int(0.5 * free))
+    if rank == 0 and world == 1 and args.batched_runs > 0:   # the overlap workload, one full run
+        line["two_populations"] = two_population_full_run(pa, cpu=not args.no_cpu_baseline, cores=os.cpu_count() or 1)
     if rank == 0 and world == 1 and args.gaussian_steps > 0:
         line["gaussian"] = gaussian_measurement(pa, args.gaussian_steps, args.warmup, n_sm,
                                                 cpu=world == 1 and not args.no_cpu_baseline, R=args.gaussian_R)
