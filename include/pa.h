@@ -316,6 +316,14 @@ int pa_shard_destroy(pa_shard* shard);
  * PA_ERR_INVALID for spins < 0 or withheld_tile < -1. */
 int pa_debug_lookback(pa_ctx* ctx, int32_t spins, int32_t withheld_tile);
 
+/* ---- testing hook: the adaptive bisection of a Gaussian-coupling run (§IV.B) ----
+ * Its halvings run in one cooperative launch where the device allows it
+ * (one_launch = 1, the default) or as a few launches per halving (one_launch = 0);
+ * both take the same decisions from the same sums, so the temperatures and every
+ * result are the same.  For tests comparing the two; PA_ERR_INVALID for a run
+ * without Gaussian couplings or an adaptive schedule, or one_launch outside {0, 1}. */
+int pa_debug_bisect(pa_ctx* ctx, int32_t one_launch);
+
 /* Waits for the context's stream; returns the first recorded error, if any. */
 int pa_sync(pa_ctx* ctx);
 

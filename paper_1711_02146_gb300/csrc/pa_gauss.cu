@@ -13,6 +13,8 @@
 //   - tau_i = R w_i / S', n_i = floor(tau_i) + [r_i < 2^32 frac(tau_i)] (§II).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "pa_device.cuh"
 #include "pa_internal.h"
 
@@ -105,18 +107,11 @@ __device__ __forceinline__ bool last_block_done(int32_t* ticket, int n_blocks) {
   return last;
 }
 
-// The chunk_tree sum of the 256 entries src[base, base + 256) (zeros from n on),
-// by one warp: lane l holds entries l + 32 k, so the tree's steps 128, 64 and 32 are
-// additions within a lane and 16 .. 1 additions across lanes, each pair added in
-// the tree's order.  The sum in lane 0.
-__device__ __forceinline__ double warp_group_sum(const double* src, long long base, int n) {
-  const int lane = threadIdx.x & 31;
-  double v[8];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const long long i = base + lane + 32 * k;
-    v[k] = i < n ? __ldcg(src + i) : 0.0;
-  }
+// The chunk_tree sum of 256 values held by one warp, lane l holding entries l + 32 k
+// in v[k]: the tree's steps 128, 64 and 32 are additions within a lane and 16 .. 1
+// additions across lanes, each pair added in the tree's order.  The sum in lane 0.
+// warp_group_sum: the same for the entries src[base, base + 256) (zeros from n on).
+__device__ __forceinline__ double group8(double* v) {
 #pragma unroll
   for (int k = 0; k < 4; ++k) v[k] = __dadd_rn(v[k], v[k + 4]);
   v[0] = __dadd_rn(v[0], v[2]);
@@ -125,6 +120,17 @@ __device__ __forceinline__ double warp_group_sum(const double* src, long long ba
 #pragma unroll
   for (int h = 16; h >= 1; h >>= 1) v[0] = __dadd_rn(v[0], __shfl_down_sync(0xffffffffu, v[0], h));
   return v[0];
+}
+
+__device__ __forceinline__ double warp_group_sum(const double* src, long long base, int n) {
+  const int lane = threadIdx.x & 31;
+  double v[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const long long i = base + lane + 32 * k;
+    v[k] = i < n ? __ldcg(src + i) : 0.0;
+  }
+  return group8(v);
 }
 
 // The sum of the n_chunks chunk totals at the start of part by a fixed tree, in
@@ -160,9 +166,12 @@ __device__ double tree_total(double* part, int n_chunks) {
 
 // Weights of the old slots of step t-1 and their chunk partial sums; the last
 // block to finish adds the partial sums into S'.  Block 0 also opens the records
-// of step t.
-__global__ void __launch_bounds__(kChunk) k_g_weights(RunGeom g, GArgs a, int t, const double* __restrict__ T) {
+// of step t.  A trial of the bisection whose halvings have reached their fixed
+// point (*skip != 0, see k_g_tau) does nothing.
+__global__ void __launch_bounds__(kChunk) k_g_weights(RunGeom g, GArgs a, int t, const double* __restrict__ T,
+                                                     const double* skip) {
   __shared__ double sh[kChunk];
+  if (skip && *skip != 0.0) return;
   PopDev& P = a.p[blockIdx.y];
   const int R_old = P.rec[t - 1].R_tilde;
   const long long Emin = P.grec[t - 1].E_min;
@@ -201,10 +210,14 @@ __global__ void __launch_bounds__(kChunk) k_g_weights(RunGeom g, GArgs a, int t,
 // (b = {lo, hi, mid}, population 0 only) that block also takes the halving's
 // decision: mid becomes lo when the fraction does not exceed the target, else hi,
 // and the next midpoint is 0.5 (lo + hi) (the host's arithmetic, rounded the same
-// way).
+// way).  b[3] becomes 1 once that midpoint equals hi, a point already rejected, or
+// lo > 0, a point already accepted: every later halving then evaluates the same
+// point again, takes the same decision and leaves {lo, hi, mid} as they are, so the
+// remaining trials are skipped (identical results, fewer launches doing work).
 __global__ void __launch_bounds__(kChunk) k_g_tau(RunGeom g, GArgs a, int t, double* b, double target,
                                                  int trial) {
   __shared__ double sh[kChunk];
+  if (b && b[3] != 0.0) return;
   PopDev& P = a.p[blockIdx.y];
   const int R_old = P.rec[t - 1].R_tilde;
   const double S = P.rec[t].S_prime;
@@ -235,6 +248,7 @@ __global__ void __launch_bounds__(kChunk) k_g_tau(RunGeom g, GArgs a, int t, dou
         else
           b[1] = b[2];
         b[2] = __dmul_rn(0.5, __dadd_rn(b[0], b[1]));
+        b[3] = (b[2] == b[1] || (b[2] == b[0] && b[0] > 0.0)) ? 1.0 : 0.0;
       }
     }
   }
@@ -281,13 +295,178 @@ __global__ void __launch_bounds__(kCountThreads) k_g_counts(RunGeom g, GArgs a, 
 // Weight tables T_k[m] = exp(-dbeta m 2^(12k) 2^-20) (T0 | T1 | T2, kGTableWeights
 // entries) for dbeta = *dbeta_dev, or dbeta_val when dbeta_dev is null: the
 // adaptive schedule's trials and its chosen step build their tables here, so a
-// trial and the resampling that follows it use the same weights.
-__global__ void k_g_tables(const double* __restrict__ dbeta_dev, double dbeta_val, double* T) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= kGTableWeights) return;
-  const double db = dbeta_dev ? *dbeta_dev : dbeta_val;
+// trial and the resampling that follows it use the same weights.  Nothing is
+// written when *skip != 0 (a bisection at its fixed point, see k_g_tau).
+__device__ __forceinline__ double g_table_entry(double db, int m) {
   const long long q = m < 4096 ? (long long)m : m < 8192 ? (long long)(m - 4096) << 12 : (long long)(m - 8192) << 24;
-  T[m] = exp(-__dmul_rn(db, __dmul_rn((double)q, 0x1p-20)));
+  return exp(-__dmul_rn(db, __dmul_rn((double)q, 0x1p-20)));
+}
+
+__global__ void k_g_tables(const double* __restrict__ dbeta_dev, double dbeta_val, double* T, const double* skip) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= kGTableWeights || (skip && *skip != 0.0)) return;
+  T[m] = g_table_entry(dbeta_dev ? *dbeta_dev : dbeta_val, m);
+}
+
+// The whole bisection in one cooperative launch (every block resident, blocks of
+// kBisectThreads): each halving is one pass over the old population for the
+// weights of mid and their chunk partial sums, a grid barrier, a pass for the
+// culling terms (S' - R w_i)_+ and their chunk partial sums, and a second barrier.
+// Every block adds the partial sums itself (block_total, the order of tree_total)
+// and so takes the same decision with no third barrier; the weight tables of the
+// two possible next midpoints are built during the second pass, into the two table
+// sets not in use.  The values, sums and decisions are those of the launch-per-trial
+// path (k_g_tables, k_g_weights, k_g_tau), so both give the same lo, hi and mid.
+constexpr int kBisectThreads = 256;
+constexpr int kBisectWarps = kBisectThreads / 32;
+constexpr int kBisectMaxChunks = kChunk * kChunk;  // block_total keeps two tree levels
+constexpr unsigned kBarrierSpins = 1u << 22;       // polls of one barrier wait (about 0.5 s at most)
+
+// Grid barrier of a cooperative launch.  bar = {arrivals, generation, error}: the
+// last block to arrive resets the count and advances the generation; the others
+// poll it a bounded number of times.  A wait that runs out records the error, after
+// which every barrier returns at once (false) and the launch ends with the error set.
+__device__ bool grid_barrier(unsigned long long* bar) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned long long* vb = bar;
+    int good = vb[2] == 0ull;
+    if (good) {
+      const unsigned long long gen = vb[1];
+      __threadfence();
+      if (atomicAdd(&bar[0], 1ull) == (unsigned long long)gridDim.x - 1ull) {
+        atomicExch(&bar[0], 0ull);
+        __threadfence();
+        atomicAdd(&bar[1], 1ull);
+      } else {
+        unsigned spins = 0;
+        while (vb[1] == gen && vb[2] == 0ull && ++spins < kBarrierSpins) __nanosleep(64);
+        if (vb[1] == gen) {
+          atomicExch(&bar[2], 1ull);
+          good = 0;
+        }
+      }
+      __threadfence();
+    }
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// tree_total of the n partial sums part[0, n) (n <= kBisectMaxChunks), computed by
+// this block alone: the first level's groups by its warps, the second level (at
+// most 256 group sums) from shared memory by warp 0.  Every block gets the same value.
+__device__ double block_total(const double* part, int n, double* lvl) {
+  __shared__ double total;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nb = (n + kChunk - 1) / kChunk;
+  for (int b = warp; b < nb; b += kBisectWarps) {
+    const double v = warp_group_sum(part, (long long)b * kChunk, n);
+    if (lane == 0) lvl[b] = v;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int i = lane + 32 * k;
+      v[k] = i < nb ? lvl[i] : 0.0;
+    }
+    const double x = nb == 1 ? lvl[0] : group8(v);
+    if (lane == 0) total = x;
+  }
+  __syncthreads();
+  return total;
+}
+
+struct BisectArgs {
+  PopDev P;                 // population 0 decides the step
+  double* b;                // {lo, hi, mid, state}: in, and out (state 1 done, -1 a barrier wait ran out)
+  double* T;                // three sets of kGTableWeights table entries
+  double* part1;            // [n_chunks] chunk partial sums of the culling terms (those of the weights in P.part)
+  unsigned long long* bar;  // grid barrier {arrivals, generation, error}, zero at launch
+  int t, R, halvings;
+  double target;
+};
+
+__global__ void __launch_bounds__(kBisectThreads, 4) k_g_bisect(BisectArgs a) {
+  __shared__ double lvl[kChunk];
+  const PopDev& P = a.P;
+  const int R_old = P.rec[a.t - 1].R_tilde;
+  const long long Emin = P.grec[a.t - 1].E_min;
+  const int nch = (R_old + kChunk - 1) / kChunk;
+  const int lane = threadIdx.x & 31;
+  const int gwarp = blockIdx.x * kBisectWarps + (threadIdx.x >> 5);
+  const int n_warps = gridDim.x * kBisectWarps;
+  const int gtid = blockIdx.x * kBisectThreads + threadIdx.x;
+  const int n_threads = gridDim.x * kBisectThreads;
+  const double R = (double)a.R;
+  double lo = a.b[0], hi = a.b[1], mid = a.b[2];
+  for (int m = gtid; m < kGTableWeights; m += n_threads) a.T[m] = g_table_entry(mid, m);
+  int cur = 0;
+  bool ok = grid_barrier(a.bar);
+  for (int h = 0; h < a.halvings && ok; ++h) {
+    const double* Tc = a.T + (size_t)cur * kGTableWeights;
+    for (int c = gwarp; c < nch; c += n_warps) {  // weights of mid and their chunk sums
+      double v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int i = c * kChunk + lane + 32 * k;
+        v[k] = 0.0;
+        if (i < R_old) {
+          const long long d = P.E64[i] - Emin;
+          v[k] = __dmul_rn(__dmul_rn(__ldcg(Tc + 8192 + (d >> 24)), __ldcg(Tc + 4096 + ((d >> 12) & 4095))),
+                           __ldcg(Tc + (d & 4095)));
+          __stcg(P.w + i, v[k]);
+        }
+      }
+      const double sum = group8(v);
+      if (lane == 0) __stcg(P.part + c, sum);
+    }
+    if (!grid_barrier(a.bar)) break;
+    const double S = block_total(P.part, nch, lvl);
+    const int s_acc = cur == 2 ? 0 : cur + 1, s_rej = cur == 0 ? 2 : cur - 1;
+    const double m_acc = __dmul_rn(0.5, __dadd_rn(mid, hi)), m_rej = __dmul_rn(0.5, __dadd_rn(lo, mid));
+    for (int m = gtid; m < 2 * kGTableWeights; m += n_threads) {  // both possible next tables
+      const bool acc = m < kGTableWeights;
+      const int e = acc ? m : m - kGTableWeights;
+      a.T[(size_t)(acc ? s_acc : s_rej) * kGTableWeights + e] = g_table_entry(acc ? m_acc : m_rej, e);
+    }
+    for (int c = gwarp; c < nch; c += n_warps) {  // culling terms and their chunk sums
+      double v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int i = c * kChunk + lane + 32 * k;
+        v[k] = 0.0;
+        if (i < R_old) {
+          const double rw = __dmul_rn(R, __ldcg(P.w + i));
+          v[k] = rw < S ? __dsub_rn(S, rw) : 0.0;
+        }
+      }
+      const double sum = group8(v);
+      if (lane == 0) __stcg(a.part1 + c, sum);
+    }
+    if (!grid_barrier(a.bar)) break;
+    const double e = __ddiv_rn(__ddiv_rn(block_total(a.part1, nch, lvl), S), R);
+    if (e <= a.target) {
+      lo = mid;
+      cur = s_acc;
+    } else {
+      hi = mid;
+      cur = s_rej;
+    }
+    mid = __dmul_rn(0.5, __dadd_rn(lo, hi));
+    // the fixed point of k_g_tau: every later halving evaluates a point already decided
+    if (mid == hi || (mid == lo && lo > 0.0)) break;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.b[0] = lo;
+    a.b[1] = hi;
+    a.b[2] = mid;
+    a.b[3] = ((volatile unsigned long long*)a.bar)[2] != 0ull ? -1.0 : 1.0;
+  }
 }
 
 // ---------------------------------------------------------------- measurement
@@ -449,7 +628,7 @@ int launch_g_resample(const RunGeom& g, PopDev* pops, int cur, int t, const doub
   cudaStream_t s = (cudaStream_t)stream;
   GArgs a = gpack(pops, g.n_pop);
   const dim3 chunks(g.n_chunks, g.n_pop);
-  k_g_weights<<<chunks, kChunk, 0, s>>>(g, a, t, wtab);
+  k_g_weights<<<chunks, kChunk, 0, s>>>(g, a, t, wtab, nullptr);
   k_g_tau<<<chunks, kChunk, 0, s>>>(g, a, t, nullptr, 0.0, 0);
   k_g_counts<<<dim3(g.n_count_blocks, g.n_pop), kCountThreads, 0, s>>>(g, a, t);
   const int e = (int)cudaGetLastError();
@@ -464,7 +643,7 @@ static int eps_trial(const RunGeom& g, PopDev* pops, int t, const double* wtab, 
   g1.n_pop = 1;
   GArgs a = gpack(pops, 1);
   const dim3 chunks(g1.n_chunks, 1);
-  k_g_weights<<<chunks, kChunk, 0, s>>>(g1, a, t, wtab);
+  k_g_weights<<<chunks, kChunk, 0, s>>>(g1, a, t, wtab, b ? b + 3 : nullptr);
   k_g_tau<<<chunks, kChunk, 0, s>>>(g1, a, t, b, target, 1);
   return (int)cudaGetLastError();
 }
@@ -474,7 +653,7 @@ int launch_g_eps_trial(const RunGeom& g, PopDev* pops, int t, const double* wtab
 }
 
 int launch_g_tables(const double* dbeta_dev, double dbeta_val, double* T, void* stream) {
-  k_g_tables<<<blocks_for(kGTableWeights, 256), 256, 0, (cudaStream_t)stream>>>(dbeta_dev, dbeta_val, T);
+  k_g_tables<<<blocks_for(kGTableWeights, 256), 256, 0, (cudaStream_t)stream>>>(dbeta_dev, dbeta_val, T, nullptr);
   return (int)cudaGetLastError();
 }
 
@@ -482,11 +661,46 @@ int launch_g_bisect(const RunGeom& g, PopDev* pops, int t, double* T, double* b,
                     void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   for (int it = 0; it < halvings; ++it) {
-    k_g_tables<<<blocks_for(kGTableWeights, 256), 256, 0, s>>>(b + 2, 0.0, T);
+    k_g_tables<<<blocks_for(kGTableWeights, 256), 256, 0, s>>>(b + 2, 0.0, T, b + 3);
     const int e = eps_trial(g, pops, t, T, b, target, s);
     if (e) return e;
   }
   return (int)cudaGetLastError();
+}
+
+int g_bisect_blocks(const RunGeom& g) {
+  if (g.n_chunks > kBisectMaxChunks) return 0;
+  int dev = 0, n_sm = 0, per_sm = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop ||
+      cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_g_bisect, kBisectThreads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const int want = blocks_for(g.n_chunks, kBisectWarps);  // one chunk per warp when the device holds them
+  return std::max(1, std::min(want, per_sm * n_sm));
+}
+
+int launch_g_bisect_fused(const RunGeom& g, PopDev* pops, int t, double* tables, double* part1,
+                          unsigned long long* bar, double* b, double target, int halvings, int n_blocks,
+                          void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  BisectArgs a;
+  a.P = pops[0];
+  a.b = b;
+  a.T = tables;
+  a.part1 = part1;
+  a.bar = bar;
+  a.t = t;
+  a.R = g.R;
+  a.halvings = halvings;
+  a.target = target;
+  cudaError_t e = cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return (int)e;
+  void* args[] = {&a};
+  e = cudaLaunchCooperativeKernel((const void*)k_g_bisect, dim3((unsigned)n_blocks), dim3(kBisectThreads), args, 0, s);
+  return (int)e;
 }
 
 int launch_g_measure(const RunGeom& g, PopDev* pops, int cur, int t, unsigned long long* qlhist, void* stream) {

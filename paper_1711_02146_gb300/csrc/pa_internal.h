@@ -177,10 +177,20 @@ int launch_g_measure(const RunGeom& g, PopDev* pops, int cur, int t, unsigned lo
 // Weight tables of dbeta (*dbeta_dev, or dbeta_val when it is null) built on the device.
 int launch_g_tables(const double* dbeta_dev, double dbeta_val, double* T, void* stream);
 // `halvings` halvings of the adaptive bisection on the device, with no host wait:
-// b = {lo, hi, mid} in device memory; each halving builds mid's tables in T, runs
-// the trial of launch_g_eps_trial and updates b.
+// b = {lo, hi, mid, 0} in device memory; each halving builds mid's tables in T, runs
+// the trial of launch_g_eps_trial and updates b, until b[3] marks the fixed point
+// (mid equal to a point already decided), after which the halvings do no work.
 int launch_g_bisect(const RunGeom& g, PopDev* pops, int t, double* T, double* b, double target, int halvings,
                     void* stream);
+// The same halvings in one cooperative launch of n_blocks blocks (g_bisect_blocks:
+// 0 when the device or the population size does not allow it): tables = three sets
+// of kGTableWeights entries, part1 = n_chunks partial sums, bar = 3 barrier words
+// (cleared on the stream first).  On return b = {lo, hi, mid, state}, state -1 when
+// a grid barrier wait ran out (the interval is then not to be used).
+int g_bisect_blocks(const RunGeom& g);
+int launch_g_bisect_fused(const RunGeom& g, PopDev* pops, int t, double* tables, double* part1,
+                          unsigned long long* bar, double* b, double target, int halvings, int n_blocks,
+                          void* stream);
 int launch_overlap(const RunGeom& g, PopDev* pops, int cur, int t, unsigned long long* qhist, void* stream);
 
 // ---- a batch advanced by one launch per kernel and temperature step (pa_batch) ----

@@ -18,6 +18,7 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/pa.h"
@@ -48,6 +49,8 @@ struct pa_ctx {
   std::vector<double> wtables_host;  // host copy of the explicit schedule's tables (source of their upload)
   double* wadapt = nullptr;     // adaptive schedule: the table of the current step
   double* wadapt_host = nullptr;  // its pinned host copy (uploaded without a wait)
+  uint32_t* gtab_host = nullptr;  // pinned host copy of the adaptive Gaussian step's site tables
+  int32_t occ_span = -1;          // adaptive +-1: highest minus lowest occupied level of population 0
   // All device buffers of the run are carved from one stream-ordered allocation:
   // a run costs the memory pool one block, so the pool's free list stays short
   // when many runs come and go (a request server).
@@ -69,7 +72,10 @@ struct pa_ctx {
   uint32_t* gtab = nullptr;              // device [n_temps][N][64] acceptance thresholds
   double* gw = nullptr;                  // device [n_temps][16384] weight tables
   unsigned long long* qlhist = nullptr;  // device [n_temps][q_bins] link-overlap histograms
-  double* gbis = nullptr;                // device {lo, hi, mid}: the adaptive bisection (Gaussian)
+  double* gbis = nullptr;                // device {lo, hi, mid, state}: the adaptive bisection (Gaussian)
+  double* gbt = nullptr;                 // device: its three table sets and chunk sums (one-launch bisection)
+  unsigned long long* gbar = nullptr;    // device: that launch's grid barrier words
+  int gbis_blocks = -1;                  // blocks of the one-launch bisection (0: launch per halving)
   std::vector<int32_t> Jq_host;
   pa::LookbackTest lookback;             // pa_debug_lookback (tests of the bounded wait)
   // Completion events of the last steps (a ring, step u in entry u & 3, -1: none), so
@@ -340,9 +346,8 @@ void gauss_couplings(int L, uint64_t seed, std::vector<int32_t>& Jq) {
 // y-1, z+1, z-1 (bit k set: bond k antiparallel), dE = 2 sum_k J_k (1 - 2 b_k):
 // the flip's Metropolis threshold, 0xFFFFFFFF for dE <= 0 (always taken), else
 // min(floor(2^32 exp(-beta dE 2^-20)), 2^32 - 2) in double precision.
-void gauss_site_tables(const std::vector<int32_t>& Jq, int L, double beta, uint32_t* out) {
-  const int N = L * L * L;
-  for (int n = 0; n < N; ++n) {
+void gauss_site_tables_range(const std::vector<int32_t>& Jq, int L, double beta, uint32_t* out, int n0, int n1) {
+  for (int n = n0; n < n1; ++n) {
     const int x = n % L, y = (n / L) % L, z = n / (L * L);
     const int xm = (x == 0 ? L - 1 : x - 1) + L * (y + L * z);
     const int ym = x + L * ((y == 0 ? L - 1 : y - 1) + L * z);
@@ -362,6 +367,45 @@ void gauss_site_tables(const std::vector<int32_t>& Jq, int L, double beta, uint3
       out[(size_t)n * pa::kGPatterns + b] = thr;
     }
   }
+}
+
+// The site tables of all N sites; a large lattice's sites are split over a few
+// host threads (each entry is a function of its site alone, so the table is the same).
+void gauss_site_tables(const std::vector<int32_t>& Jq, int L, double beta, uint32_t* out) {
+  const int N = L * L * L;
+  const int n_thr = N < 512 ? 1 : (int)std::min<unsigned>(8u, std::max(1u, std::thread::hardware_concurrency()));
+  if (n_thr == 1) {
+    gauss_site_tables_range(Jq, L, beta, out, 0, N);
+    return;
+  }
+  std::vector<std::thread> pool;
+  const int per = (N + n_thr - 1) / n_thr;
+  for (int k = 1; k < n_thr && k * per < N; ++k)
+    pool.emplace_back(gauss_site_tables_range, std::cref(Jq), L, beta, out, k * per, std::min(N, (k + 1) * per));
+  gauss_site_tables_range(Jq, L, beta, out, 0, std::min(N, per));
+  for (std::thread& th : pool) th.join();
+}
+
+// Uploads the adaptive Gaussian step's site tables for beta, built into a pinned
+// buffer and copied without a wait (plain copy where pinned memory is not had).
+// The previous step's copy from that buffer is done: the bisection that chose beta
+// synchronised the stream.
+int upload_site_tables(pa_ctx* c, double beta) {
+  const size_t n = (size_t)c->g.N * pa::kGPatterns;
+  if (!c->gtab_host) {
+    void* h = nullptr;
+    if (cudaMallocHost(&h, sizeof(uint32_t) * n) == cudaSuccess)
+      c->gtab_host = static_cast<uint32_t*>(h);
+    else
+      cudaGetLastError();
+  }
+  if (!c->gtab_host) {
+    std::vector<uint32_t> tab(n);
+    gauss_site_tables(c->Jq_host, c->g.L, beta, tab.data());
+    return copy_h2d(c, c->gtab, tab.data(), sizeof(uint32_t) * n);
+  }
+  gauss_site_tables(c->Jq_host, c->g.L, beta, c->gtab_host);
+  return copy_async(c, c->gtab, c->gtab_host, sizeof(uint32_t) * n);
 }
 
 // Weight tables of one step: T0[m] = exp(-dbeta m 2^-20), T1[m] for m 2^12,
@@ -411,7 +455,13 @@ int weight_table(pa_ctx* c, double dbeta, const double** out) {
     *out = it->second;
     return PA_OK;
   }
-  std::vector<double> w = host_weights(c->g.n_levels, dbeta);
+  // The reweighting reads w[k - kmin] at the occupied levels k only; with one
+  // population they span occ_span + 1 entries (choose_dbeta found them), and the
+  // entries past those are zeros instead of exponentials.
+  const int n = c->g.n_levels;
+  const int used = c->g.n_pop == 1 && c->occ_span >= 0 ? std::min(n, c->occ_span + 1) : n;
+  std::vector<double> w((size_t)n, 0.0);
+  for (int j = 0; j < used; ++j) w[(size_t)j] = std::exp(-(dbeta * (double)(2 * j)));
   const size_t bytes = sizeof(double) * w.size();
   if (!c->wadapt_host) {  // pinned, so the upload need not wait (first use; else plain copies)
     void* h = nullptr;
@@ -468,6 +518,7 @@ int choose_dbeta(pa_ctx* c, double* dbeta) {
   for (int k = 0; k < n; ++k)
     if (h[(size_t)k] > 0) occ.push_back(k);
   if (occ.empty()) return PA_ERR_EXTINCT;
+  c->occ_span = occ.back() - occ.front();
   const double prev = c->betas[(size_t)c->t];
   const double rem = c->cfg.beta_max - prev;
   const double target = c->cfg.eps_target;
@@ -479,6 +530,9 @@ int choose_dbeta(pa_ctx* c, double* dbeta) {
   double lo = 0.0, hi = rem;
   for (int it = 0; it < 64; ++it) {
     double mid = 0.5 * (lo + hi);
+    // a midpoint equal to hi (rejected) or to lo > 0 (accepted) is decided already,
+    // and so is every later one: the remaining halvings would change nothing
+    if (mid == hi || (mid == lo && lo > 0.0)) break;
     if (culling_fraction(occ, h, c->cfg.R, mid, w) <= target)
       lo = mid;
     else
@@ -558,14 +612,15 @@ int launch_rc(int e) { return e == 0 ? PA_OK : PA_ERR_CUDA; }
 // Adaptive step with Gaussian couplings (§IV.B), as for +-1 couplings: the largest
 // dbeta in (0, beta_max - beta] whose culling fraction (population 0, the
 // resampling's own weights and sums) does not exceed the target, by 64 bisection
-// halvings.  The halvings run on the device one after another (launch_g_bisect)
-// with no host wait between them; the host reads the first trial (the whole
-// remaining range) and the final interval.
+// halvings.  The halvings run on the device in one cooperative launch
+// (launch_g_bisect_fused; one launch per halving where that is not possible) with
+// no host wait between them; the host reads the first trial (the whole remaining
+// range) and the final interval.
 int choose_dbeta_gauss(pa_ctx* c, double* dbeta) {
   const int t = c->t + 1;
   const double rem = c->cfg.beta_max - c->betas[(size_t)c->t];
   const double target = c->cfg.eps_target;
-  double b[3] = {0.0, rem, rem};
+  double b[4] = {0.0, rem, rem, 0.0};
   int rc = copy_h2d(c, c->gbis, b, sizeof b);
   if (rc == PA_OK) rc = launch_rc(pa::launch_g_tables(c->gbis + 2, 0.0, c->gw, c->stream));
   if (rc == PA_OK) rc = launch_rc(pa::launch_g_eps_trial(c->g, c->pops, t, c->gw, c->stream));
@@ -578,9 +633,15 @@ int choose_dbeta_gauss(pa_ctx* c, double* dbeta) {
   }
   b[2] = 0.5 * (b[0] + b[1]);
   rc = copy_h2d(c, c->gbis, b, sizeof b);
-  if (rc == PA_OK) rc = launch_rc(pa::launch_g_bisect(c->g, c->pops, t, c->gw, c->gbis, target, 64, c->stream));
+  if (c->gbis_blocks < 0) c->gbis_blocks = pa::g_bisect_blocks(c->g);
+  if (rc == PA_OK && c->gbis_blocks > 0)
+    rc = launch_rc(pa::launch_g_bisect_fused(c->g, c->pops, t, c->gbt, c->gbt + 3 * (size_t)pa::kGTableWeights,
+                                             c->gbar, c->gbis, target, 64, c->gbis_blocks, c->stream));
+  else if (rc == PA_OK)
+    rc = launch_rc(pa::launch_g_bisect(c->g, c->pops, t, c->gw, c->gbis, target, 64, c->stream));
   if (rc == PA_OK) rc = copy_d2h(c, b, c->gbis, sizeof b);
   if (rc != PA_OK) return rc;
+  if (b[3] < 0.0) return PA_ERR_TIMEOUT;
   *dbeta = b[0] > 0.0 ? b[0] : b[1];
   return PA_OK;
 }
@@ -632,6 +693,7 @@ void destroy(pa_ctx* c) {
     if (e) cudaEventDestroy(e);
   if (c->rd) cudaStreamDestroy(c->rd);
   if (c->wadapt_host) cudaFreeHost(c->wadapt_host);
+  if (c->gtab_host) cudaFreeHost(c->gtab_host);
   delete c;
 }
 
@@ -787,7 +849,11 @@ int layout_buffers(pa_ctx* c) {
     rc = rc ? rc : dalloc(c, &c->gtab, slots * (size_t)g.N * pa::kGPatterns);
     rc = rc ? rc : dalloc(c, &c->gw, slots * (size_t)pa::kGTableWeights);
     rc = rc ? rc : dalloc(c, &c->qlhist, T * (size_t)g.q_bins);
-    if (c->adaptive) rc = rc ? rc : dalloc(c, &c->gbis, (size_t)4);
+    if (c->adaptive) {
+      rc = rc ? rc : dalloc(c, &c->gbis, (size_t)4);
+      rc = rc ? rc : dalloc(c, &c->gbt, (size_t)3 * pa::kGTableWeights + (size_t)g.n_chunks);
+      rc = rc ? rc : dalloc(c, &c->gbar, (size_t)4);
+    }
   } else if (c->adaptive) {
     rc = rc ? rc : dalloc(c, &c->wadapt, (size_t)g.n_levels);
   } else {  // one Boltzmann weight table per distinct increment
@@ -1137,19 +1203,16 @@ int pa_step(pa_ctx* c) {
     rc = cuda_status(cudaMemsetAsync(c->pops[p].rec + t, 0, sizeof(StepRec), s));
   if (c->model == PA_MODEL_GAUSS) {
     const size_t slot = c->adaptive ? 0 : (size_t)t;
-    if (c->adaptive && rc == PA_OK) {  // this step's tables, for the beta just chosen
-      std::vector<uint32_t> tab((size_t)c->g.N * pa::kGPatterns);
-      gauss_site_tables(c->Jq_host, c->g.L, c->betas[(size_t)t], tab.data());
-      rc = copy_h2d(c, c->gtab, tab.data(), sizeof(uint32_t) * tab.size());
-      // the weight tables as the bisection's trials built them, so the resampling's
-      // culling fraction is the one the bisection accepted
-      if (rc == PA_OK) rc = launch_rc(pa::launch_g_tables(nullptr, dbeta, c->gw, c->stream));
-    }
+    // the weight tables as the bisection's trials built them, so the resampling's
+    // culling fraction is the one the bisection accepted
+    if (c->adaptive && rc == PA_OK) rc = launch_rc(pa::launch_g_tables(nullptr, dbeta, c->gw, c->stream));
     if (rc == PA_OK) {
       PhaseTimer pt(c, PA_PHASE_RESAMPLE, 7);
       rc = launch_rc(pa::launch_g_resample(c->g, c->pops, c->cur, t, c->gw + slot * pa::kGTableWeights,
                                            c->status, s));
     }
+    // this step's site tables for the beta just chosen, built while the device resamples
+    if (c->adaptive && rc == PA_OK) rc = upload_site_tables(c, c->betas[(size_t)t]);
     if (rc == PA_OK) {
       PhaseTimer pt(c, PA_PHASE_SWEEP, 1);
       rc = launch_rc(pa::launch_g_sweep(c->g, c->pops, c->cur, c->jtab, c->Jq, c->Jtot,
@@ -1192,6 +1255,12 @@ int pa_debug_lookback(pa_ctx* c, int32_t spins, int32_t withheld_tile) {
   if (!c || spins < 0 || withheld_tile < -1) return PA_ERR_INVALID;
   c->lookback.spins = spins;
   c->lookback.withheld_tile = withheld_tile;
+  return PA_OK;
+}
+
+int pa_debug_bisect(pa_ctx* c, int32_t one_launch) {
+  if (!c || c->model != PA_MODEL_GAUSS || !c->adaptive || one_launch < 0 || one_launch > 1) return PA_ERR_INVALID;
+  c->gbis_blocks = one_launch ? -1 : 0;  // -1: sized again at the next step
   return PA_OK;
 }
 

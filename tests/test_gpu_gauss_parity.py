@@ -217,3 +217,39 @@ def test_adaptive_schedule(pa, oracle_lib, L, R, eps, bmax, n_pop):
         assert_state(gpu, ref, n_pop, f"t={t}")
     assert t >= 3 and gpu.gobs(t)["beta"] == bmax
     assert all(gpu.gobs(u)["eps_expected"] <= eps for u in range(1, t + 1))
+
+
+@pytest.mark.parametrize("L,R,eps,bmax", [(6, 1500, 0.2, 3.0), (10, 300_000, 0.272, 1.0)])
+def test_adaptive_bisection_one_launch_equals_launch_per_halving(pa, L, R, eps, bmax):
+    """§IV.B: the bisection's halvings in one cooperative launch take the decisions of
+    the launch-per-halving form from the same sums, so every temperature, population
+    and observable of the two runs is the same to the bit (R = 3e5 spans 1172 chunk
+    sums: two levels of the fixed-order tree and several chunks per block)."""
+    runs = []
+    for one_launch in (1, 0):
+        r = pa.Run(L, R, 5, 70 + L, None, n_temps=400, beta_max=bmax, eps_target=eps, n_sweeps=1,
+                   model=pa.PA_MODEL_GAUSS)
+        assert pa.lib().pa_debug_bisect(r._h, one_launch) == pa.PA_OK
+        runs.append(r)
+    assert pa.lib().pa_debug_bisect(runs[0]._h, 2) == pa.PA_ERR_INVALID
+    t = 0
+    while True:
+        a, b = runs[0].step(), runs[1].step()
+        assert a == b
+        if a == pa.PA_DONE:
+            break
+        t += 1
+        oa, ob = runs[0].gobs(t), runs[1].gobs(t)
+        for k in INT_OBS + FLOAT_OBS:
+            va, vb = oa[k], ob[k]
+            assert va == vb or (va != va and vb != vb), (t, k, va, vb)
+        assert oa["eps_expected"] <= eps
+    assert t >= 3 and runs[0].gobs(t)["beta"] == bmax
+    for p in (0, 1, 2):
+        assert np.array_equal(runs[0].population()[p], runs[1].population()[p])
+    linear = pa.Run(4, 100, 1, 2, np.linspace(0.0, 1.0, 5), n_sweeps=1, model=pa.PA_MODEL_GAUSS)
+    pm1 = pa.Run(4, 100, 1, 2, None, n_temps=10, beta_max=1.0, eps_target=0.3, n_sweeps=1)
+    assert pa.lib().pa_debug_bisect(linear._h, 1) == pa.PA_ERR_INVALID
+    assert pa.lib().pa_debug_bisect(pm1._h, 1) == pa.PA_ERR_INVALID
+    for r in runs + [linear, pm1]:
+        r.close()
