@@ -310,56 +310,26 @@ __global__ void k_g_tables(const double* __restrict__ dbeta_dev, double dbeta_va
 
 // The whole bisection in one cooperative launch (every block resident, blocks of
 // kBisectThreads): each halving is one pass over the old population for the
-// weights of mid and their chunk partial sums, a grid barrier, a pass for the
-// culling terms (S' - R w_i)_+ and their chunk partial sums, and a second barrier.
-// Every block adds the partial sums itself (block_total, the order of tree_total)
-// and so takes the same decision with no third barrier; the weight tables of the
-// two possible next midpoints are built during the second pass, into the two table
-// sets not in use.  The values, sums and decisions are those of the launch-per-trial
-// path (k_g_tables, k_g_weights, k_g_tau), so both give the same lo, hi and mid.
+// weights of mid and their chunk partial sums, a grid barrier whose last block to
+// arrive adds the partial sums (block_total, the order of tree_total) into S', a
+// pass for the culling terms (S' - R w_i)_+ and their chunk partial sums, and a
+// second such barrier for their total; every block then takes the same decision.
+// The weight tables of the two possible next midpoints are built during the second
+// pass, into the two table sets not in use, T2 only up to the entry of the largest
+// d = E_i - E_min (found once, before the first halving).  The values, sums and
+// decisions are those of the launch-per-trial path (k_g_tables, k_g_weights,
+// k_g_tau), so both give the same lo, hi and mid.
 constexpr int kBisectThreads = 256;
 constexpr int kBisectWarps = kBisectThreads / 32;
 constexpr int kBisectMaxChunks = kChunk * kChunk;  // block_total keeps two tree levels
 constexpr unsigned kBarrierSpins = 1u << 22;       // polls of one barrier wait (about 0.5 s at most)
-
-// Grid barrier of a cooperative launch.  bar = {arrivals, generation, error}: the
-// last block to arrive resets the count and advances the generation; the others
-// poll it a bounded number of times.  A wait that runs out records the error, after
-// which every barrier returns at once (false) and the launch ends with the error set.
-__device__ bool grid_barrier(unsigned long long* bar) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned long long* vb = bar;
-    int good = vb[2] == 0ull;
-    if (good) {
-      const unsigned long long gen = vb[1];
-      __threadfence();
-      if (atomicAdd(&bar[0], 1ull) == (unsigned long long)gridDim.x - 1ull) {
-        atomicExch(&bar[0], 0ull);
-        __threadfence();
-        atomicAdd(&bar[1], 1ull);
-      } else {
-        unsigned spins = 0;
-        while (vb[1] == gen && vb[2] == 0ull && ++spins < kBarrierSpins) __nanosleep(64);
-        if (vb[1] == gen) {
-          atomicExch(&bar[2], 1ull);
-          good = 0;
-        }
-      }
-      __threadfence();
-    }
-    ok = good;
-  }
-  __syncthreads();
-  return ok != 0;
-}
+// words of the barrier block: arrivals, generation, error, largest d, S', culling sum
+enum { kBarArrive, kBarGen, kBarError, kBarDmax, kBarS, kBarCull, kBarWords = 8 };
 
 // tree_total of the n partial sums part[0, n) (n <= kBisectMaxChunks), computed by
 // this block alone: the first level's groups by its warps, the second level (at
-// most 256 group sums) from shared memory by warp 0.  Every block gets the same value.
+// most 256 group sums) from shared memory by warp 0.  The total in thread 0.
 __device__ double block_total(const double* part, int n, double* lvl) {
-  __shared__ double total;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nb = (n + kChunk - 1) / kChunk;
   for (int b = warp; b < nb; b += kBisectWarps) {
@@ -367,6 +337,7 @@ __device__ double block_total(const double* part, int n, double* lvl) {
     if (lane == 0) lvl[b] = v;
   }
   __syncthreads();
+  double x = 0.0;
   if (warp == 0) {
     double v[8];
 #pragma unroll
@@ -374,11 +345,59 @@ __device__ double block_total(const double* part, int n, double* lvl) {
       const int i = lane + 32 * k;
       v[k] = i < nb ? lvl[i] : 0.0;
     }
-    const double x = nb == 1 ? lvl[0] : group8(v);
-    if (lane == 0) total = x;
+    x = nb == 1 ? lvl[0] : group8(v);
   }
   __syncthreads();
-  return total;
+  return x;
+}
+
+// Grid barrier of a cooperative launch: the last block to arrive resets the count
+// and advances the generation, the others poll it a bounded number of times.  With
+// part, that last block first stores block_total(part, n) in bar[slot].  A wait that
+// runs out records the error, after which every barrier returns at once (false) and
+// the launch ends with the error set.
+__device__ bool grid_barrier(unsigned long long* bar, const double* part = nullptr, int n = 0, int slot = 0,
+                             double* lvl = nullptr) {
+  __shared__ int state;  // 0: wait, 1: last to arrive, -1: error
+  volatile unsigned long long* vb = bar;
+  unsigned long long gen = 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int st = vb[kBarError] == 0ull ? 0 : -1;
+    if (st == 0) {
+      gen = vb[kBarGen];
+      __threadfence();
+      if (atomicAdd(&bar[kBarArrive], 1ull) == (unsigned long long)gridDim.x - 1ull) st = 1;
+    }
+    state = st;
+  }
+  __syncthreads();
+  if (state == 1 && part) {
+    const double x = block_total(part, n, lvl);
+    if (threadIdx.x == 0) vb[slot] = (unsigned long long)__double_as_longlong(x);
+  }
+  if (threadIdx.x == 0) {
+    if (state == 1) {
+      __threadfence();
+      atomicExch(&bar[kBarArrive], 0ull);
+      __threadfence();
+      atomicAdd(&bar[kBarGen], 1ull);
+    } else if (state == 0) {
+      unsigned spins = 0;
+      while (vb[kBarGen] == gen && vb[kBarError] == 0ull && ++spins < kBarrierSpins) __nanosleep(64);
+      if (vb[kBarGen] == gen) {
+        atomicExch(&bar[kBarError], 1ull);
+        state = -1;
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return state >= 0;
+}
+
+__device__ __forceinline__ double bar_double(const unsigned long long* bar, int slot) {
+  return __longlong_as_double((long long)((volatile const unsigned long long*)bar)[slot]);
 }
 
 struct BisectArgs {
@@ -386,7 +405,7 @@ struct BisectArgs {
   double* b;                // {lo, hi, mid, state}: in, and out (state 1 done, -1 a barrier wait ran out)
   double* T;                // three sets of kGTableWeights table entries
   double* part1;            // [n_chunks] chunk partial sums of the culling terms (those of the weights in P.part)
-  unsigned long long* bar;  // grid barrier {arrivals, generation, error}, zero at launch
+  unsigned long long* bar;  // kBarWords words, zero at launch
   int t, R, halvings;
   double target;
 };
@@ -404,9 +423,21 @@ __global__ void __launch_bounds__(kBisectThreads, 4) k_g_bisect(BisectArgs a) {
   const int n_threads = gridDim.x * kBisectThreads;
   const double R = (double)a.R;
   double lo = a.b[0], hi = a.b[1], mid = a.b[2];
-  for (int m = gtid; m < kGTableWeights; m += n_threads) a.T[m] = g_table_entry(mid, m);
-  int cur = 0;
+  unsigned long long dmax = 0;  // the largest d: T2 beyond its entry is never read
+  for (int i = gtid; i < R_old; i += n_threads) {
+    const unsigned long long d = (unsigned long long)(P.E64[i] - Emin);
+    dmax = d > dmax ? d : dmax;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long x = __shfl_down_sync(0xffffffffu, dmax, o);
+    dmax = x > dmax ? x : dmax;
+  }
+  if (lane == 0 && dmax) atomicMax(&a.bar[kBarDmax], dmax);
   bool ok = grid_barrier(a.bar);
+  const int n_tab = 8192 + (int)min(8191ull, ((volatile unsigned long long*)a.bar)[kBarDmax] >> 24) + 1;
+  for (int m = gtid; m < n_tab; m += n_threads) a.T[m] = g_table_entry(mid, m);
+  int cur = 0;
+  ok = ok && grid_barrier(a.bar);
   for (int h = 0; h < a.halvings && ok; ++h) {
     const double* Tc = a.T + (size_t)cur * kGTableWeights;
     for (int c = gwarp; c < nch; c += n_warps) {  // weights of mid and their chunk sums
@@ -425,13 +456,14 @@ __global__ void __launch_bounds__(kBisectThreads, 4) k_g_bisect(BisectArgs a) {
       const double sum = group8(v);
       if (lane == 0) __stcg(P.part + c, sum);
     }
-    if (!grid_barrier(a.bar)) break;
-    const double S = block_total(P.part, nch, lvl);
+    if (!grid_barrier(a.bar, P.part, nch, kBarS, lvl)) break;
+    const double S = bar_double(a.bar, kBarS);
+    const long long S_bits = __double_as_longlong(S);
     const int s_acc = cur == 2 ? 0 : cur + 1, s_rej = cur == 0 ? 2 : cur - 1;
     const double m_acc = __dmul_rn(0.5, __dadd_rn(mid, hi)), m_rej = __dmul_rn(0.5, __dadd_rn(lo, mid));
-    for (int m = gtid; m < 2 * kGTableWeights; m += n_threads) {  // both possible next tables
-      const bool acc = m < kGTableWeights;
-      const int e = acc ? m : m - kGTableWeights;
+    for (int m = gtid; m < 2 * n_tab; m += n_threads) {  // both possible next tables
+      const bool acc = m < n_tab;
+      const int e = acc ? m : m - n_tab;
       a.T[(size_t)(acc ? s_acc : s_rej) * kGTableWeights + e] = g_table_entry(acc ? m_acc : m_rej, e);
     }
     for (int c = gwarp; c < nch; c += n_warps) {  // culling terms and their chunk sums
@@ -441,15 +473,17 @@ __global__ void __launch_bounds__(kBisectThreads, 4) k_g_bisect(BisectArgs a) {
         const int i = c * kChunk + lane + 32 * k;
         v[k] = 0.0;
         if (i < R_old) {
+          // rw < S' compared as the bit patterns of two non-negative doubles (an
+          // integer comparison, the same order)
           const double rw = __dmul_rn(R, __ldcg(P.w + i));
-          v[k] = rw < S ? __dsub_rn(S, rw) : 0.0;
+          if (__double_as_longlong(rw) < S_bits) v[k] = __dsub_rn(S, rw);
         }
       }
       const double sum = group8(v);
       if (lane == 0) __stcg(a.part1 + c, sum);
     }
-    if (!grid_barrier(a.bar)) break;
-    const double e = __ddiv_rn(__ddiv_rn(block_total(a.part1, nch, lvl), S), R);
+    if (!grid_barrier(a.bar, a.part1, nch, kBarCull, lvl)) break;
+    const double e = __ddiv_rn(__ddiv_rn(bar_double(a.bar, kBarCull), S), R);
     if (e <= a.target) {
       lo = mid;
       cur = s_acc;
@@ -465,7 +499,7 @@ __global__ void __launch_bounds__(kBisectThreads, 4) k_g_bisect(BisectArgs a) {
     a.b[0] = lo;
     a.b[1] = hi;
     a.b[2] = mid;
-    a.b[3] = ((volatile unsigned long long*)a.bar)[2] != 0ull ? -1.0 : 1.0;
+    a.b[3] = ((volatile unsigned long long*)a.bar)[kBarError] != 0ull ? -1.0 : 1.0;
   }
 }
 
@@ -696,7 +730,7 @@ int launch_g_bisect_fused(const RunGeom& g, PopDev* pops, int t, double* tables,
   a.R = g.R;
   a.halvings = halvings;
   a.target = target;
-  cudaError_t e = cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned long long), s);
+  cudaError_t e = cudaMemsetAsync(bar, 0, kBarWords * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return (int)e;
   void* args[] = {&a};
   e = cudaLaunchCooperativeKernel((const void*)k_g_bisect, dim3((unsigned)n_blocks), dim3(kBisectThreads), args, 0, s);

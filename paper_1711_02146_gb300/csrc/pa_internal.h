@@ -184,8 +184,8 @@ int launch_g_bisect(const RunGeom& g, PopDev* pops, int t, double* T, double* b,
                     void* stream);
 // The same halvings in one cooperative launch of n_blocks blocks (g_bisect_blocks:
 // 0 when the device or the population size does not allow it): tables = three sets
-// of kGTableWeights entries, part1 = n_chunks partial sums, bar = 3 barrier words
-// (cleared on the stream first).  On return b = {lo, hi, mid, state}, state -1 when
+// of kGTableWeights entries, part1 = n_chunks partial sums, bar = 8 words (barrier
+// and totals, cleared on the stream first).  On return b = {lo, hi, mid, state}, state -1 when
 // a grid barrier wait ran out (the interval is then not to be used).
 int g_bisect_blocks(const RunGeom& g);
 int launch_g_bisect_fused(const RunGeom& g, PopDev* pops, int t, double* tables, double* part1,

@@ -852,7 +852,7 @@ int layout_buffers(pa_ctx* c) {
     if (c->adaptive) {
       rc = rc ? rc : dalloc(c, &c->gbis, (size_t)4);
       rc = rc ? rc : dalloc(c, &c->gbt, (size_t)3 * pa::kGTableWeights + (size_t)g.n_chunks);
-      rc = rc ? rc : dalloc(c, &c->gbar, (size_t)4);
+      rc = rc ? rc : dalloc(c, &c->gbar, (size_t)8);
     }
   } else if (c->adaptive) {
     rc = rc ? rc : dalloc(c, &c->wadapt, (size_t)g.n_levels);
