@@ -320,9 +320,16 @@ int pa_debug_lookback(pa_ctx* ctx, int32_t spins, int32_t withheld_tile);
  * Its halvings run in one cooperative launch where the device allows it
  * (one_launch = 1, the default) or as a few launches per halving (one_launch = 0);
  * both take the same decisions from the same sums, so the temperatures and every
- * result are the same.  For tests comparing the two; PA_ERR_INVALID for a run
- * without Gaussian couplings or an adaptive schedule, or one_launch outside {0, 1}. */
-int pa_debug_bisect(pa_ctx* ctx, int32_t one_launch);
+ * result are the same.  In the one-launch form the blocks meet at grid barriers
+ * whose waits poll a bounded number of times; withheld_block >= 0 keeps that block
+ * (of the launch's blocks, numbered from 0; a number past the last keeps none) from
+ * arriving at the first barrier and lowers the poll limit to 4096, so that the
+ * others' waits run out: the launch then ends normally with its error set, and the
+ * run reports PA_ERR_TIMEOUT from that step on.  The device and other runs on it are
+ * not affected.  -1: none.  For tests only; PA_ERR_INVALID for a run without Gaussian
+ * couplings or an adaptive schedule, one_launch outside {0, 1}, withheld_block < -1,
+ * or withheld_block >= 0 with one_launch = 0. */
+int pa_debug_bisect(pa_ctx* ctx, int32_t one_launch, int32_t withheld_block);
 
 /* Waits for the context's stream; returns the first recorded error, if any. */
 int pa_sync(pa_ctx* ctx);

@@ -352,12 +352,13 @@ __device__ double block_total(const double* part, int n, double* lvl) {
 }
 
 // Grid barrier of a cooperative launch: the last block to arrive resets the count
-// and advances the generation, the others poll it a bounded number of times.  With
+// and advances the generation, the others poll it at most `spins` times.  With
 // part, that last block first stores block_total(part, n) in bar[slot].  A wait that
 // runs out records the error, after which every barrier returns at once (false) and
-// the launch ends with the error set.
-__device__ bool grid_barrier(unsigned long long* bar, const double* part = nullptr, int n = 0, int slot = 0,
-                             double* lvl = nullptr) {
+// the launch ends with the error set.  A block with withhold set waits without
+// arriving (a test of that path: the waits then run out).
+__device__ bool grid_barrier(unsigned long long* bar, unsigned spins_max, bool withhold = false,
+                             const double* part = nullptr, int n = 0, int slot = 0, double* lvl = nullptr) {
   __shared__ int state;  // 0: wait, 1: last to arrive, -1: error
   volatile unsigned long long* vb = bar;
   unsigned long long gen = 0;
@@ -367,7 +368,7 @@ __device__ bool grid_barrier(unsigned long long* bar, const double* part = nullp
     if (st == 0) {
       gen = vb[kBarGen];
       __threadfence();
-      if (atomicAdd(&bar[kBarArrive], 1ull) == (unsigned long long)gridDim.x - 1ull) st = 1;
+      if (!withhold && atomicAdd(&bar[kBarArrive], 1ull) == (unsigned long long)gridDim.x - 1ull) st = 1;
     }
     state = st;
   }
@@ -384,7 +385,7 @@ __device__ bool grid_barrier(unsigned long long* bar, const double* part = nullp
       atomicAdd(&bar[kBarGen], 1ull);
     } else if (state == 0) {
       unsigned spins = 0;
-      while (vb[kBarGen] == gen && vb[kBarError] == 0ull && ++spins < kBarrierSpins) __nanosleep(64);
+      while (vb[kBarGen] == gen && vb[kBarError] == 0ull && ++spins < spins_max) __nanosleep(64);
       if (vb[kBarGen] == gen) {
         atomicExch(&bar[kBarError], 1ull);
         state = -1;
@@ -406,6 +407,8 @@ struct BisectArgs {
   double* T;                // three sets of kGTableWeights table entries
   double* part1;            // [n_chunks] chunk partial sums of the culling terms (those of the weights in P.part)
   unsigned long long* bar;  // kBarWords words, zero at launch
+  unsigned spins;           // polls of a barrier wait
+  int withheld;             // block that does not arrive at the first barrier (-1: none; tests)
   int t, R, halvings;
   double target;
 };
@@ -433,11 +436,11 @@ __global__ void __launch_bounds__(kBisectThreads, 4) k_g_bisect(BisectArgs a) {
     dmax = x > dmax ? x : dmax;
   }
   if (lane == 0 && dmax) atomicMax(&a.bar[kBarDmax], dmax);
-  bool ok = grid_barrier(a.bar);
+  bool ok = grid_barrier(a.bar, a.spins, (int)blockIdx.x == a.withheld);
   const int n_tab = 8192 + (int)min(8191ull, ((volatile unsigned long long*)a.bar)[kBarDmax] >> 24) + 1;
   for (int m = gtid; m < n_tab; m += n_threads) a.T[m] = g_table_entry(mid, m);
   int cur = 0;
-  ok = ok && grid_barrier(a.bar);
+  ok = ok && grid_barrier(a.bar, a.spins);
   for (int h = 0; h < a.halvings && ok; ++h) {
     const double* Tc = a.T + (size_t)cur * kGTableWeights;
     for (int c = gwarp; c < nch; c += n_warps) {  // weights of mid and their chunk sums
@@ -456,7 +459,7 @@ __global__ void __launch_bounds__(kBisectThreads, 4) k_g_bisect(BisectArgs a) {
       const double sum = group8(v);
       if (lane == 0) __stcg(P.part + c, sum);
     }
-    if (!grid_barrier(a.bar, P.part, nch, kBarS, lvl)) break;
+    if (!grid_barrier(a.bar, a.spins, false, P.part, nch, kBarS, lvl)) break;
     const double S = bar_double(a.bar, kBarS);
     const long long S_bits = __double_as_longlong(S);
     const int s_acc = cur == 2 ? 0 : cur + 1, s_rej = cur == 0 ? 2 : cur - 1;
@@ -482,7 +485,7 @@ __global__ void __launch_bounds__(kBisectThreads, 4) k_g_bisect(BisectArgs a) {
       const double sum = group8(v);
       if (lane == 0) __stcg(a.part1 + c, sum);
     }
-    if (!grid_barrier(a.bar, a.part1, nch, kBarCull, lvl)) break;
+    if (!grid_barrier(a.bar, a.spins, false, a.part1, nch, kBarCull, lvl)) break;
     const double e = __ddiv_rn(__ddiv_rn(bar_double(a.bar, kBarCull), S), R);
     if (e <= a.target) {
       lo = mid;
@@ -718,7 +721,7 @@ int g_bisect_blocks(const RunGeom& g) {
 
 int launch_g_bisect_fused(const RunGeom& g, PopDev* pops, int t, double* tables, double* part1,
                           unsigned long long* bar, double* b, double target, int halvings, int n_blocks,
-                          void* stream) {
+                          int withheld, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   BisectArgs a;
   a.P = pops[0];
@@ -730,6 +733,8 @@ int launch_g_bisect_fused(const RunGeom& g, PopDev* pops, int t, double* tables,
   a.R = g.R;
   a.halvings = halvings;
   a.target = target;
+  a.withheld = withheld;
+  a.spins = withheld >= 0 ? 4096u : kBarrierSpins;
   cudaError_t e = cudaMemsetAsync(bar, 0, kBarWords * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return (int)e;
   void* args[] = {&a};

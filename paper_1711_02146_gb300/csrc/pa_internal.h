@@ -186,11 +186,12 @@ int launch_g_bisect(const RunGeom& g, PopDev* pops, int t, double* T, double* b,
 // 0 when the device or the population size does not allow it): tables = three sets
 // of kGTableWeights entries, part1 = n_chunks partial sums, bar = 8 words (barrier
 // and totals, cleared on the stream first).  On return b = {lo, hi, mid, state}, state -1 when
-// a grid barrier wait ran out (the interval is then not to be used).
+// a grid barrier wait ran out (the interval is then not to be used).  withheld >= 0 (tests):
+// that block does not arrive at the first barrier and the waits poll 4096 times, so they run out.
 int g_bisect_blocks(const RunGeom& g);
 int launch_g_bisect_fused(const RunGeom& g, PopDev* pops, int t, double* tables, double* part1,
                           unsigned long long* bar, double* b, double target, int halvings, int n_blocks,
-                          void* stream);
+                          int withheld, void* stream);
 int launch_overlap(const RunGeom& g, PopDev* pops, int cur, int t, unsigned long long* qhist, void* stream);
 
 // ---- a batch advanced by one launch per kernel and temperature step (pa_batch) ----

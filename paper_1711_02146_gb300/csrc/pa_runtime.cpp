@@ -76,6 +76,7 @@ struct pa_ctx {
   double* gbt = nullptr;                 // device: its three table sets and chunk sums (one-launch bisection)
   unsigned long long* gbar = nullptr;    // device: that launch's grid barrier words
   int gbis_blocks = -1;                  // blocks of the one-launch bisection (0: launch per halving)
+  int gbis_withheld = -1;                // pa_debug_bisect: block kept from the first barrier
   std::vector<int32_t> Jq_host;
   pa::LookbackTest lookback;             // pa_debug_lookback (tests of the bounded wait)
   // Completion events of the last steps (a ring, step u in entry u & 3, -1: none), so
@@ -636,7 +637,8 @@ int choose_dbeta_gauss(pa_ctx* c, double* dbeta) {
   if (c->gbis_blocks < 0) c->gbis_blocks = pa::g_bisect_blocks(c->g);
   if (rc == PA_OK && c->gbis_blocks > 0)
     rc = launch_rc(pa::launch_g_bisect_fused(c->g, c->pops, t, c->gbt, c->gbt + 3 * (size_t)pa::kGTableWeights,
-                                             c->gbar, c->gbis, target, 64, c->gbis_blocks, c->stream));
+                                             c->gbar, c->gbis, target, 64, c->gbis_blocks, c->gbis_withheld,
+                                             c->stream));
   else if (rc == PA_OK)
     rc = launch_rc(pa::launch_g_bisect(c->g, c->pops, t, c->gw, c->gbis, target, 64, c->stream));
   if (rc == PA_OK) rc = copy_d2h(c, b, c->gbis, sizeof b);
@@ -1258,9 +1260,12 @@ int pa_debug_lookback(pa_ctx* c, int32_t spins, int32_t withheld_tile) {
   return PA_OK;
 }
 
-int pa_debug_bisect(pa_ctx* c, int32_t one_launch) {
-  if (!c || c->model != PA_MODEL_GAUSS || !c->adaptive || one_launch < 0 || one_launch > 1) return PA_ERR_INVALID;
+int pa_debug_bisect(pa_ctx* c, int32_t one_launch, int32_t withheld_block) {
+  if (!c || c->model != PA_MODEL_GAUSS || !c->adaptive || one_launch < 0 || one_launch > 1 || withheld_block < -1 ||
+      (!one_launch && withheld_block >= 0))
+    return PA_ERR_INVALID;
   c->gbis_blocks = one_launch ? -1 : 0;  // -1: sized again at the next step
+  c->gbis_withheld = withheld_block;
   return PA_OK;
 }
 

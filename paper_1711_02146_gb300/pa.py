@@ -175,7 +175,7 @@ SIGNATURES = {
     "pa_beta": (ctypes.c_double, [_vp, ctypes.c_int32]),
     "pa_stats_reset": (ctypes.c_int, [_vp, ctypes.c_int]),
     "pa_debug_lookback": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
-    "pa_debug_bisect": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "pa_debug_bisect": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
     "pa_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(Stats)]),
     "pa_sync": (ctypes.c_int, [_vp]),
     "pa_destroy": (ctypes.c_int, [_vp]),

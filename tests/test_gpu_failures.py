@@ -59,3 +59,30 @@ def test_lookback_hook_restores_the_default(pa, oracle_lib):
     ref.run()
     assert_state_equal(gpu, ref, 1, "default look-back")
     assert_obs_equal(gpu.obs(2), ref.obs(2), "t=2")
+
+
+def test_bisection_barrier_wait_runs_out_and_is_reported(pa):
+    """The one-launch bisection of a Gaussian-coupling run (§IV.B): one block is kept
+    from the first grid barrier (a flag that nothing sets) and the poll limit lowered,
+    so the other blocks' waits run out; the launch ends normally with its error set,
+    the run reports PA_ERR_TIMEOUT from then on, and a run afterwards on the same GPU
+    is the same to the bit as one made before."""
+    cfg = dict(n_temps=80, beta_max=2.0, eps_target=0.3, n_sweeps=1, model=pa.PA_MODEL_GAUSS)
+    before = pa.Run(6, 3000, 5, 76, None, **cfg)
+    before.run()
+    bad = pa.Run(6, 3000, 5, 76, None, **cfg)
+    assert pa.lib().pa_debug_bisect(bad._h, 1, 0) == pa.PA_OK
+    for call in (bad.step, bad.sync, bad.step):
+        with pytest.raises(pa.PAError) as e:
+            call()
+        assert e.value.status == pa.PA_ERR_TIMEOUT
+    after = pa.Run(6, 3000, 5, 76, None, **cfg)
+    after.run()
+    assert before.t == after.t >= 3
+    for t in range(before.t + 1):
+        assert before.gobs(t) == after.gobs(t) or all(
+            a == b or (a != a and b != b) for a, b in zip(before.gobs(t).values(), after.gobs(t).values())), t
+    for x, y in zip(before.population(), after.population()):
+        assert np.array_equal(x, y)
+    for r in (before, bad, after):
+        r.close()

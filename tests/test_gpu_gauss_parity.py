@@ -229,9 +229,11 @@ def test_adaptive_bisection_one_launch_equals_launch_per_halving(pa, L, R, eps, 
     for one_launch in (1, 0):
         r = pa.Run(L, R, 5, 70 + L, None, n_temps=400, beta_max=bmax, eps_target=eps, n_sweeps=1,
                    model=pa.PA_MODEL_GAUSS)
-        assert pa.lib().pa_debug_bisect(r._h, one_launch) == pa.PA_OK
+        assert pa.lib().pa_debug_bisect(r._h, one_launch, -1) == pa.PA_OK
         runs.append(r)
-    assert pa.lib().pa_debug_bisect(runs[0]._h, 2) == pa.PA_ERR_INVALID
+    assert pa.lib().pa_debug_bisect(runs[0]._h, 2, -1) == pa.PA_ERR_INVALID
+    assert pa.lib().pa_debug_bisect(runs[0]._h, 0, 3) == pa.PA_ERR_INVALID
+    assert pa.lib().pa_debug_bisect(runs[0]._h, 1, -2) == pa.PA_ERR_INVALID
     t = 0
     while True:
         a, b = runs[0].step(), runs[1].step()
@@ -249,7 +251,7 @@ def test_adaptive_bisection_one_launch_equals_launch_per_halving(pa, L, R, eps, 
         assert np.array_equal(runs[0].population()[p], runs[1].population()[p])
     linear = pa.Run(4, 100, 1, 2, np.linspace(0.0, 1.0, 5), n_sweeps=1, model=pa.PA_MODEL_GAUSS)
     pm1 = pa.Run(4, 100, 1, 2, None, n_temps=10, beta_max=1.0, eps_target=0.3, n_sweeps=1)
-    assert pa.lib().pa_debug_bisect(linear._h, 1) == pa.PA_ERR_INVALID
-    assert pa.lib().pa_debug_bisect(pm1._h, 1) == pa.PA_ERR_INVALID
+    assert pa.lib().pa_debug_bisect(linear._h, 1, -1) == pa.PA_ERR_INVALID
+    assert pa.lib().pa_debug_bisect(pm1._h, 1, -1) == pa.PA_ERR_INVALID
     for r in runs + [linear, pm1]:
         r.close()
