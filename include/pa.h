@@ -41,7 +41,7 @@ extern "C" {
 #define PA_OK 0
 #define PA_DONE 1            /* pa_step: the schedule is complete, nothing was done */
 #define PA_ERR_INVALID (-1)  /* bad argument or configuration */
-#define PA_ERR_NOMEM (-2)    /* device or host allocation failed */
+#define PA_ERR_NOMEM (-2)    /* device or host allocation failed (no C++ exception leaves the library) */
 #define PA_ERR_CAPACITY (-3) /* population outgrew R_cap (detected on the device; nothing written out of bounds) */
 #define PA_ERR_TIMEOUT (-4)  /* a bounded device wait gave up */
 #define PA_ERR_CUDA (-5)     /* a CUDA runtime call failed */

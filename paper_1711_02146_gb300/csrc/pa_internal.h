@@ -7,6 +7,11 @@
 
 namespace pa {
 
+// The status code of the C++ exception being handled, for the catch block of every
+// entry point of the C interface (none lets an exception leave the library): a
+// failed host allocation is PA_ERR_NOMEM, anything else PA_ERR_INVALID.
+int exception_status() noexcept;
+
 // Random-stream purposes (4 bits above the seed in the Philox key).
 enum Purpose : uint32_t { kCouplings = 0, kInit = 1, kMetropolis = 2, kResample = 3 };
 

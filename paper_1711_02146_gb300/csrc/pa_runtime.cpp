@@ -18,6 +18,7 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <system_error>
 #include <thread>
 #include <vector>
 
@@ -380,9 +381,16 @@ void gauss_site_tables(const std::vector<int32_t>& Jq, int L, double beta, uint3
     return;
   }
   std::vector<std::thread> pool;
+  pool.reserve((size_t)n_thr);
   const int per = (N + n_thr - 1) / n_thr;
-  for (int k = 1; k < n_thr && k * per < N; ++k)
-    pool.emplace_back(gauss_site_tables_range, std::cref(Jq), L, beta, out, k * per, std::min(N, (k + 1) * per));
+  for (int k = 1; k < n_thr && k * per < N; ++k) {
+    const int a = k * per, b = std::min(N, (k + 1) * per);
+    try {
+      pool.emplace_back(gauss_site_tables_range, std::cref(Jq), L, beta, out, a, b);
+    } catch (const std::system_error&) {  // no thread to be had: this range here
+      gauss_site_tables_range(Jq, L, beta, out, a, b);
+    }
+  }
   gauss_site_tables_range(Jq, L, beta, out, 0, std::min(N, per));
   for (std::thread& th : pool) th.join();
 }
@@ -878,6 +886,16 @@ void use_chosen_shape(pa_ctx* c) {
   if (c && sweep_supported(c->g.L) && current_device(&dev) == PA_OK) c->g.sweep_shape = g_sweep_choice[dev][c->g.L].load();
   if (c) c->g.tail_shape = -1;  // runs among many: other runs fill the SMs a last wave leaves idle
 }
+
+int exception_status() noexcept {
+  try {
+    throw;
+  } catch (const std::bad_alloc&) {
+    return PA_ERR_NOMEM;
+  } catch (...) {
+    return PA_ERR_INVALID;
+  }
+}
 }  // namespace pa
 
 namespace {
@@ -1005,7 +1023,7 @@ const char* pa_strerror(int s) {
   }
 }
 
-int pa_footprint(const pa_config* cfg, size_t* bytes) {
+int pa_footprint(const pa_config* cfg, size_t* bytes) try {
   if (!cfg || !bytes || !pa::lattice_supported(cfg->L) || cfg->R < 1 || cfg->n_temps < 1 || cfg->n_pop < 1 ||
       cfg->n_pop > 2 || cfg->model < PA_MODEL_PM1 || cfg->model > PA_MODEL_GAUSS || cfg->q_bins < 0)
     return PA_ERR_INVALID;
@@ -1015,6 +1033,8 @@ int pa_footprint(const pa_config* cfg, size_t* bytes) {
   if (rc != PA_OK) return rc;
   *bytes = sizing.slab_bytes;
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
 }  // extern "C"
@@ -1178,11 +1198,13 @@ int create_run_impl(const pa_config* cfg, void* cuda_stream, pa_ctx** out, bool 
 
 extern "C" {
 
-int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) {
+int pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out) try {
   return pa::create_run(cfg, cuda_stream, out, true);
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_step(pa_ctx* c) {
+int pa_step(pa_ctx* c) try {
   if (!c) return PA_ERR_INVALID;
   NvtxRange range("pa_step");
   if (c->error != PA_OK) return c->error;
@@ -1251,25 +1273,31 @@ int pa_step(pa_ctx* c) {
   c->counted_steps.emplace_back(t, c->sweeps[(size_t)t]);
   if (t == c->cfg.n_temps - 1 || (c->adaptive && c->betas[(size_t)t] >= c->cfg.beta_max)) c->done = true;
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_debug_lookback(pa_ctx* c, int32_t spins, int32_t withheld_tile) {
+int pa_debug_lookback(pa_ctx* c, int32_t spins, int32_t withheld_tile) try {
   if (!c || spins < 0 || withheld_tile < -1) return PA_ERR_INVALID;
   c->lookback.spins = spins;
   c->lookback.withheld_tile = withheld_tile;
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_debug_bisect(pa_ctx* c, int32_t one_launch, int32_t withheld_block) {
+int pa_debug_bisect(pa_ctx* c, int32_t one_launch, int32_t withheld_block) try {
   if (!c || c->model != PA_MODEL_GAUSS || !c->adaptive || one_launch < 0 || one_launch > 1 || withheld_block < -1 ||
       (!one_launch && withheld_block >= 0))
     return PA_ERR_INVALID;
   c->gbis_blocks = one_launch ? -1 : 0;  // -1: sized again at the next step
   c->gbis_withheld = withheld_block;
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_stats_reset(pa_ctx* c, int enable_timing) {
+int pa_stats_reset(pa_ctx* c, int enable_timing) try {
   if (!c) return PA_ERR_INVALID;
   int rc = cuda_status(cudaStreamSynchronize(c->stream));
   c->stats = pa_stats{};
@@ -1278,9 +1306,11 @@ int pa_stats_reset(pa_ctx* c, int enable_timing) {
   c->events_used = 0;
   c->counted_steps.clear();
   return rc == PA_OK ? PA_OK : fail(c, rc);
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_get_stats(pa_ctx* c, pa_stats* out) {
+int pa_get_stats(pa_ctx* c, pa_stats* out) try {
   if (!c || !out) return PA_ERR_INVALID;
   int rc = cuda_status(cudaStreamSynchronize(c->stream));
   if (rc != PA_OK) return fail(c, rc);
@@ -1306,23 +1336,29 @@ int pa_get_stats(pa_ctx* c, pa_stats* out) {
     }
   *out = st;
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_sync(pa_ctx* c) {
+int pa_sync(pa_ctx* c) try {
   if (!c) return PA_ERR_INVALID;
   int rc = cuda_status(cudaStreamSynchronize(c->stream));
   if (rc == PA_OK) rc = check_device_status(c);
   if (rc != PA_OK) fail(c, rc);
   return c->error;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_run(pa_ctx* c) {
+int pa_run(pa_ctx* c) try {
   if (!c) return PA_ERR_INVALID;
   int rc;
   while ((rc = pa_step(c)) == PA_OK) {
   }
   if (rc != PA_DONE) return rc;
   return pa_sync(c);
+} catch (...) {
+  return pa::exception_status();
 }
 
 int32_t pa_current_step(const pa_ctx* c) { return c ? c->t : -1; }
@@ -1332,7 +1368,7 @@ double pa_beta(const pa_ctx* c, int32_t t) {
   return c->betas[(size_t)t];
 }
 
-int pa_observables(pa_ctx* c, int32_t t, int32_t pop, pa_obs* out) {
+int pa_observables(pa_ctx* c, int32_t t, int32_t pop, pa_obs* out) try {
   if (!c || !out || t < 0 || pop < 0 || pop >= c->g.n_pop || c->model != PA_MODEL_PM1) return PA_ERR_INVALID;
   if (t > c->t) return PA_ERR_STATE;
   if (c->error != PA_OK) return c->error;
@@ -1356,9 +1392,11 @@ int pa_observables(pa_ctx* c, int32_t t, int32_t pop, pa_obs* out) {
   if (flags & pa::kFlagTimeout) return fail(c, PA_ERR_TIMEOUT);
   pm1_observables(g, c->betas, rec.data(), h.data(), t, g.n_pop == 2 ? &r0 : nullptr, out);
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_energy_hist(pa_ctx* c, int32_t t, int32_t pop, int64_t* out, int64_t cap) {
+int pa_energy_hist(pa_ctx* c, int32_t t, int32_t pop, int64_t* out, int64_t cap) try {
   if (!c || !out || t < 0 || pop < 0 || pop >= c->g.n_pop || c->model != PA_MODEL_PM1) return PA_ERR_INVALID;
   if (t > c->t) return PA_ERR_STATE;
   if (cap < c->g.n_levels) return PA_ERR_CAPACITY;
@@ -1369,9 +1407,11 @@ int pa_energy_hist(pa_ctx* c, int32_t t, int32_t pop, int64_t* out, int64_t cap)
   if (rc != PA_OK) return fail(c, rc);
   for (size_t k = 0; k < h.size(); ++k) out[k] = h[k];
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_q_hist(pa_ctx* c, int32_t t, int64_t* out, int64_t cap) {
+int pa_q_hist(pa_ctx* c, int32_t t, int64_t* out, int64_t cap) try {
   if (!c || !out || t < 0 || c->g.n_pop != 2) return PA_ERR_INVALID;
   if (t > c->t) return PA_ERR_STATE;
   if (cap < c->g.q_bins) return PA_ERR_CAPACITY;
@@ -1382,9 +1422,11 @@ int pa_q_hist(pa_ctx* c, int32_t t, int64_t* out, int64_t cap) {
   if (rc != PA_OK) return fail(c, rc);
   for (size_t k = 0; k < q.size(); ++k) out[k] = (int64_t)q[k];
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_family_hist(pa_ctx* c, int32_t pop, int64_t cap, int64_t* eta, int64_t* m, int64_t* n) {
+int pa_family_hist(pa_ctx* c, int32_t pop, int64_t cap, int64_t* eta, int64_t* m, int64_t* n) try {
   if (!c || !n || pop < 0 || pop >= c->g.n_pop) return PA_ERR_INVALID;
   int rc = pa_sync(c);
   if (rc != PA_OK) return rc;
@@ -1406,9 +1448,11 @@ int pa_family_hist(pa_ctx* c, int32_t pop, int64_t cap, int64_t* eta, int64_t* m
     }
   *n = k;
   return k <= cap ? PA_OK : PA_ERR_CAPACITY;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_population_size(pa_ctx* c, int32_t pop, int64_t* count) {
+int pa_population_size(pa_ctx* c, int32_t pop, int64_t* count) try {
   if (!c || !count || pop < 0 || pop >= c->g.n_pop) return PA_ERR_INVALID;
   int rc = pa_sync(c);
   if (rc != PA_OK) return rc;
@@ -1417,10 +1461,12 @@ int pa_population_size(pa_ctx* c, int32_t pop, int64_t* count) {
   if (rc != PA_OK) return fail(c, rc);
   *count = R;
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
 int pa_get_replicas(pa_ctx* c, int32_t pop, int64_t first, int64_t n, int8_t* spins, int32_t* labels,
-                    int32_t* energies) {
+                    int32_t* energies) try {
   if (!c || pop < 0 || pop >= c->g.n_pop || first < 0 || n < 0) return PA_ERR_INVALID;
   int64_t R = 0;
   int rc = pa_population_size(c, pop, &R);
@@ -1450,9 +1496,11 @@ int pa_get_replicas(pa_ctx* c, int32_t pop, int64_t first, int64_t n, int8_t* sp
     for (int64_t j = 0; j < n; ++j) energies[j] = 2 * energies[j] - 3 * g.N;
   }
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_get_copy_counts(pa_ctx* c, int32_t pop, int32_t* counts, int64_t cap, int64_t* count) {
+int pa_get_copy_counts(pa_ctx* c, int32_t pop, int32_t* counts, int64_t cap, int64_t* count) try {
   if (!c || !count || pop < 0 || pop >= c->g.n_pop) return PA_ERR_INVALID;
   if (c->t == 0) return PA_ERR_STATE;
   int rc = pa_sync(c);
@@ -1465,9 +1513,11 @@ int pa_get_copy_counts(pa_ctx* c, int32_t pop, int32_t* counts, int64_t cap, int
   if (counts && r.R_prev > 0)
     rc = copy_d2h(c, counts, c->pops[pop].counts, sizeof(int32_t) * r.R_prev);
   return rc == PA_OK ? PA_OK : fail(c, rc);
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_get_parents(pa_ctx* c, int32_t pop, int32_t* parents, int64_t cap, int64_t* count) {
+int pa_get_parents(pa_ctx* c, int32_t pop, int32_t* parents, int64_t cap, int64_t* count) try {
   if (!c || !count || pop < 0 || pop >= c->g.n_pop) return PA_ERR_INVALID;
   if (c->t == 0) return PA_ERR_STATE;
   int64_t R = 0;
@@ -1478,24 +1528,30 @@ int pa_get_parents(pa_ctx* c, int32_t pop, int32_t* parents, int64_t cap, int64_
   if (parents && R > 0)
     rc = copy_d2h(c, parents, c->pops[pop].parents, sizeof(int32_t) * R);
   return rc == PA_OK ? PA_OK : fail(c, rc);
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_get_couplings(pa_ctx* c, int8_t* J, int64_t cap) {
+int pa_get_couplings(pa_ctx* c, int8_t* J, int64_t cap) try {
   if (!c || !J) return PA_ERR_INVALID;
   if (cap < 3 * c->g.N) return PA_ERR_CAPACITY;
   int rc = pa_sync(c);
   if (rc != PA_OK) return rc;
   rc = copy_d2h(c, J, c->J, (size_t)3 * c->g.N);
   return rc == PA_OK ? PA_OK : fail(c, rc);
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_destroy(pa_ctx* c) {
+int pa_destroy(pa_ctx* c) try {
   if (!c) return PA_ERR_INVALID;
   destroy(c);
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_gobservables(pa_ctx* c, int32_t t, int32_t pop, pa_gobs* out) {
+int pa_gobservables(pa_ctx* c, int32_t t, int32_t pop, pa_gobs* out) try {
   if (!c || !out || t < 0 || pop < 0 || pop >= c->g.n_pop || c->model != PA_MODEL_GAUSS) return PA_ERR_INVALID;
   if (t > c->t) return PA_ERR_STATE;
   int rc = pa_sync(c);
@@ -1559,9 +1615,11 @@ int pa_gobservables(pa_ctx* c, int32_t t, int32_t pop, pa_gobs* out) {
   }
   *out = o;
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_get_genergies(pa_ctx* c, int32_t pop, int64_t first, int64_t n, int64_t* E) {
+int pa_get_genergies(pa_ctx* c, int32_t pop, int64_t first, int64_t n, int64_t* E) try {
   if (!c || !E || pop < 0 || pop >= c->g.n_pop || first < 0 || n < 0 || c->model != PA_MODEL_GAUSS)
     return PA_ERR_INVALID;
   int64_t R = 0;
@@ -1571,9 +1629,11 @@ int pa_get_genergies(pa_ctx* c, int32_t pop, int64_t first, int64_t n, int64_t* 
   if (n == 0) return PA_OK;
   rc = copy_d2h(c, E, c->pops[pop].E64 + first, sizeof(int64_t) * n);
   return rc == PA_OK ? PA_OK : fail(c, rc);
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_ql_hist(pa_ctx* c, int32_t t, int64_t* out, int64_t cap) {
+int pa_ql_hist(pa_ctx* c, int32_t t, int64_t* out, int64_t cap) try {
   if (!c || !out || t < 0 || c->model != PA_MODEL_GAUSS || c->g.n_pop != 2) return PA_ERR_INVALID;
   if (t > c->t) return PA_ERR_STATE;
   if (cap < c->g.q_bins) return PA_ERR_CAPACITY;
@@ -1584,17 +1644,21 @@ int pa_ql_hist(pa_ctx* c, int32_t t, int64_t* out, int64_t cap) {
   if (rc != PA_OK) return fail(c, rc);
   for (size_t i = 0; i < h.size(); ++i) out[i] = (int64_t)h[i];
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_get_gcouplings(pa_ctx* c, int32_t* Jq, int64_t cap) {
+int pa_get_gcouplings(pa_ctx* c, int32_t* Jq, int64_t cap) try {
   if (!c || !Jq || c->model != PA_MODEL_GAUSS) return PA_ERR_INVALID;
   if (cap < 3 * c->g.N) return PA_ERR_CAPACITY;
   std::memcpy(Jq, c->Jq_host.data(), sizeof(int32_t) * c->Jq_host.size());
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
 
-int pa_checkpoint(pa_ctx* c, void* buf, size_t cap, size_t* size) {
+int pa_checkpoint(pa_ctx* c, void* buf, size_t cap, size_t* size) try {
   if (!c || !size) return PA_ERR_INVALID;
   int rc = pa_sync(c);
   if (rc != PA_OK) return rc;
@@ -1676,9 +1740,11 @@ int pa_checkpoint(pa_ctx* c, void* buf, size_t cap, size_t* size) {
   if (rc == PA_OK) rc = copy_d2h(c, o, c->qhist, qbytes);
   if (rc == PA_OK && gauss) rc = copy_d2h(c, o + qbytes, c->qlhist, qbytes);
   return rc == PA_OK ? PA_OK : fail(c, rc);
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_restore(const pa_config* cfg, const void* buf, size_t size, void* cuda_stream, pa_ctx** out) {
+int pa_restore(const pa_config* cfg, const void* buf, size_t size, void* cuda_stream, pa_ctx** out) try {
   if (!out) return PA_ERR_INVALID;
   *out = nullptr;
   if (!cfg || !buf || size < sizeof(CkptHeader)) return PA_ERR_INVALID;
@@ -1769,9 +1835,11 @@ int pa_restore(const pa_config* cfg, const void* buf, size_t size, void* cuda_st
   c->done = h.done != 0;
   *out = c;
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_sweep_shapes(int32_t L, pa_sweep_shape* shapes, int32_t cap, int32_t* n) {
+int pa_sweep_shapes(int32_t L, pa_sweep_shape* shapes, int32_t cap, int32_t* n) try {
   if (!n || cap < 0 || (cap > 0 && !shapes) || !pa::sweep_supported(L)) return PA_ERR_INVALID;
   const int k = pa::sweep_shape_count(L);
   *n = k;
@@ -1785,9 +1853,11 @@ int pa_sweep_shapes(int32_t L, pa_sweep_shape* shapes, int32_t cap, int32_t* n) 
     shapes[i].smem_bytes = si.smem;
   }
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_sweep_select(int32_t L, int32_t index) {
+int pa_sweep_select(int32_t L, int32_t index) try {
   if (!pa::sweep_supported(L) || index < -1 || index >= pa::sweep_shape_count(L)) return PA_ERR_INVALID;
   int dev = 0;
   const int rc = current_device(&dev);
@@ -1795,26 +1865,32 @@ int pa_sweep_select(int32_t L, int32_t index) {
   g_sweep_choice[dev][L].store(index < 0 ? 0 : index);
   g_sweep_pinned[dev][L].store(index >= 0);
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_sweep_selected(int32_t L, int32_t* index) {
+int pa_sweep_selected(int32_t L, int32_t* index) try {
   if (!index || !pa::sweep_supported(L)) return PA_ERR_INVALID;
   int dev = 0;
   const int rc = current_device(&dev);
   if (rc != PA_OK) return rc;
   *index = g_sweep_choice[dev][L].load();
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_sweep_plan(const pa_ctx* c, int32_t* shape, int32_t* tail_shape, int32_t* tail_from) {
+int pa_sweep_plan(const pa_ctx* c, int32_t* shape, int32_t* tail_shape, int32_t* tail_from) try {
   if (!c || !shape || !tail_shape || !tail_from) return PA_ERR_INVALID;
   *shape = c->g.sweep_shape;
   *tail_shape = c->g.tail_shape;
   *tail_from = c->g.tail_from;
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_sweep_autotune(int32_t L, int32_t R, int32_t launches, double* ms_per_launch, int32_t cap, int32_t* best) {
+int pa_sweep_autotune(int32_t L, int32_t R, int32_t launches, double* ms_per_launch, int32_t cap, int32_t* best) try {
   if (!best || !pa::sweep_supported(L) || R < 1 || launches < 1 || cap < 0 || (cap > 0 && !ms_per_launch))
     return PA_ERR_INVALID;
   int dev = 0;
@@ -1880,6 +1956,8 @@ int pa_sweep_autotune(int32_t L, int32_t R, int32_t launches, double* ms_per_lau
   g_sweep_pinned[dev][L].store(false);
   *best = best_i;
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
 }  // extern "C"
@@ -2161,7 +2239,7 @@ int shard_exchange(pa_shard* s, int p, const std::vector<int64_t>& off, const st
 extern "C" {
 
 int pa_shard_create(const pa_config* cfg, int32_t rank, int32_t n_ranks, const pa_comm* comm, void* cuda_stream,
-                    pa_shard** out) {
+                    pa_shard** out) try {
   if (!out) return PA_ERR_INVALID;
   *out = nullptr;
   if (!cfg || !comm || !comm->allreduce_i64 || !comm->allgather_i64 || !comm->send || !comm->recv || n_ranks < 1 ||
@@ -2194,9 +2272,11 @@ int pa_shard_create(const pa_config* cfg, int32_t rank, int32_t n_ranks, const p
   }
   *out = s;
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_shard_step(pa_shard* s) {
+int pa_shard_step(pa_shard* s) try {
   if (!s) return PA_ERR_INVALID;
   pa_ctx* c = s->c;
   if (c->error != PA_OK) return c->error;
@@ -2275,45 +2355,57 @@ int pa_shard_step(pa_shard* s) {
   c->stats.steps += 1;
   if (t == c->cfg.n_temps - 1) c->done = true;
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_shard_observables(pa_shard* s, int32_t t, int32_t pop, pa_obs* out) {
+int pa_shard_observables(pa_shard* s, int32_t t, int32_t pop, pa_obs* out) try {
   if (!s || !out || t < 0 || pop < 0 || pop >= s->c->g.n_pop) return PA_ERR_INVALID;
   if (t > s->c->t) return PA_ERR_STATE;
   const StepRec* r0 = s->c->g.n_pop == 2 ? &s->rec[0][(size_t)t] : nullptr;
   pm1_observables(s->c->g, s->c->betas, s->rec[pop].data(), s->hist[pop].data() + (size_t)t * s->c->g.n_levels, t,
                   r0, out);
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_shard_local(pa_shard* s, pa_ctx** local) {
+int pa_shard_local(pa_shard* s, pa_ctx** local) try {
   if (!s || !local) return PA_ERR_INVALID;
   *local = s->c;
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_shard_extent(pa_shard* s, int32_t pop, int64_t* lo, int64_t* R_tilde) {
+int pa_shard_extent(pa_shard* s, int32_t pop, int64_t* lo, int64_t* R_tilde) try {
   if (!s || pop < 0 || pop >= s->c->g.n_pop) return PA_ERR_INVALID;
   if (lo) *lo = s->lo;
   if (R_tilde) *R_tilde = s->R_glob[pop];
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_shard_q_hist(pa_shard* s, int32_t t, int64_t* out, int64_t cap) {
+int pa_shard_q_hist(pa_shard* s, int32_t t, int64_t* out, int64_t cap) try {
   if (!s || !out || t < 0 || s->c->g.n_pop != 2) return PA_ERR_INVALID;
   if (t > s->c->t) return PA_ERR_STATE;
   if (cap < s->c->g.q_bins) return PA_ERR_CAPACITY;
   for (int i = 0; i < s->c->g.q_bins; ++i) out[i] = s->qhist[(size_t)t][(size_t)i];
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_shard_destroy(pa_shard* s) {
+int pa_shard_destroy(pa_shard* s) try {
   if (!s) return PA_ERR_INVALID;
   if (s->c) pa_destroy(s->c);
   if (s->dscratch) cudaFree(s->dscratch);
   if (s->dsizes) cudaFree(s->dsizes);
   delete s;
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
 }  // extern "C"

@@ -128,7 +128,7 @@ extern "C" {
 
 // ---------------------------------------------------------------- batch
 
-int pa_batch_create(const pa_config* cfgs, int32_t n, pa_batch** out) {
+int pa_batch_create(const pa_config* cfgs, int32_t n, pa_batch** out) try {
   if (!out || !cfgs || n < 1) return PA_ERR_INVALID;
   *out = nullptr;
   pa_batch* b = new (std::nothrow) pa_batch();
@@ -149,9 +149,11 @@ int pa_batch_create(const pa_config* cfgs, int32_t n, pa_batch** out) {
   }
   *out = b;
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_batch_run(pa_batch* b) {
+int pa_batch_run(pa_batch* b) try {
   if (!b) return PA_ERR_INVALID;
   // fused mode: the runs that qualify advance by rounds of one graph launch each
   // (issued at once, asynchronously); the others step on their own streams meanwhile
@@ -195,28 +197,36 @@ int pa_batch_run(pa_batch* b) {
   for (size_t i = 0; i < b->ctx.size(); ++i) b->kernel_launches += pa::run_kernel_launches(b->ctx[i]) - before[i];
   pa::group_destroy(grp);
   return rc;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_batch_set_mode(pa_batch* b, int32_t mode) {
+int pa_batch_set_mode(pa_batch* b, int32_t mode) try {
   if (!b || (mode != PA_BATCH_FUSED && mode != PA_BATCH_STREAMS)) return PA_ERR_INVALID;
   b->mode = mode;
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_batch_launches(const pa_batch* b, int64_t* kernel_launches, int64_t* graph_launches) {
+int pa_batch_launches(const pa_batch* b, int64_t* kernel_launches, int64_t* graph_launches) try {
   if (!b || !kernel_launches || !graph_launches) return PA_ERR_INVALID;
   *kernel_launches = b->kernel_launches;
   *graph_launches = b->graph_launches;
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_batch_ctx(pa_batch* b, int32_t i, pa_ctx** view) {
+int pa_batch_ctx(pa_batch* b, int32_t i, pa_ctx** view) try {
   if (!b || !view || i < 0 || (size_t)i >= b->ctx.size()) return PA_ERR_INVALID;
   *view = b->ctx[(size_t)i];
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_batch_destroy(pa_batch* b) {
+int pa_batch_destroy(pa_batch* b) try {
   if (!b) return PA_ERR_INVALID;
   for (pa_ctx* c : b->ctx) pa_destroy(c);
   for (cudaStream_t s : b->streams) {
@@ -225,11 +235,13 @@ int pa_batch_destroy(pa_batch* b) {
   }
   delete b;
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
 // ---------------------------------------------------------------- server
 
-int pa_server_create(size_t mem_budget, int32_t max_active, int32_t steps_per_poll, pa_server** out) {
+int pa_server_create(size_t mem_budget, int32_t max_active, int32_t steps_per_poll, pa_server** out) try {
   if (!out || mem_budget == 0 || max_active < 1 || steps_per_poll < 1) return PA_ERR_INVALID;
   pa_server* s = new (std::nothrow) pa_server();
   if (!s) return PA_ERR_NOMEM;
@@ -243,9 +255,11 @@ int pa_server_create(size_t mem_budget, int32_t max_active, int32_t steps_per_po
   s->free_streams.resize((size_t)s->n_levels);
   *out = s;
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_server_submit(pa_server* s, const pa_config* cfg, uint64_t* id) {
+int pa_server_submit(pa_server* s, const pa_config* cfg, uint64_t* id) try {
   if (!s || !cfg || !id) return PA_ERR_INVALID;
   size_t fp = 0;
   int rc = pa_footprint(cfg, &fp);
@@ -258,6 +272,8 @@ int pa_server_submit(pa_server* s, const pa_config* cfg, uint64_t* id) {
   s->queue.push_back(std::move(r));
   *id = s->queue.back().id;
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
 namespace {
@@ -306,7 +322,7 @@ int admit(pa_server* s) {
 
 }  // namespace
 
-int pa_server_poll(pa_server* s, uint64_t* done_ids, int32_t cap, int32_t* n_done) {
+int pa_server_poll(pa_server* s, uint64_t* done_ids, int32_t cap, int32_t* n_done) try {
   if (!s || !n_done || cap < 0 || (cap > 0 && !done_ids)) return PA_ERR_INVALID;
   *n_done = 0;
   int rc = admit(s);
@@ -353,9 +369,11 @@ int pa_server_poll(pa_server* s, uint64_t* done_ids, int32_t cap, int32_t* n_don
     s->active.erase(s->active.begin() + (long)i);
   }
   return admit(s);
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_server_result(pa_server* s, uint64_t id, int32_t pop, pa_obs* out, int32_t* last_step) {
+int pa_server_result(pa_server* s, uint64_t id, int32_t pop, pa_obs* out, int32_t* last_step) try {
   if (!s || !out) return PA_ERR_INVALID;
   auto it = s->finished.find(id);
   if (it == s->finished.end()) return PA_ERR_STATE;
@@ -364,9 +382,11 @@ int pa_server_result(pa_server* s, uint64_t id, int32_t pop, pa_obs* out, int32_
   *out = it->second.obs[(size_t)pop];
   if (last_step) *last_step = it->second.last_step;
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_server_gresult(pa_server* s, uint64_t id, int32_t pop, pa_gobs* out, int32_t* last_step) {
+int pa_server_gresult(pa_server* s, uint64_t id, int32_t pop, pa_gobs* out, int32_t* last_step) try {
   if (!s || !out) return PA_ERR_INVALID;
   auto it = s->finished.find(id);
   if (it == s->finished.end()) return PA_ERR_STATE;
@@ -375,16 +395,20 @@ int pa_server_gresult(pa_server* s, uint64_t id, int32_t pop, pa_gobs* out, int3
   *out = it->second.gobs[(size_t)pop];
   if (last_step) *last_step = it->second.last_step;
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_server_load(pa_server* s, int32_t* queued, int32_t* active) {
+int pa_server_load(pa_server* s, int32_t* queued, int32_t* active) try {
   if (!s) return PA_ERR_INVALID;
   if (queued) *queued = (int32_t)s->queue.size();
   if (active) *active = (int32_t)s->active.size();
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
-int pa_server_destroy(pa_server* s) {
+int pa_server_destroy(pa_server* s) try {
   if (!s) return PA_ERR_INVALID;
   for (auto& a : s->active) {
     pa_destroy(a.ctx);
@@ -399,6 +423,8 @@ int pa_server_destroy(pa_server* s) {
   for (cudaEvent_t ev : s->free_events) cudaEventDestroy(ev);
   delete s;
   return PA_OK;
+} catch (...) {
+  return pa::exception_status();
 }
 
 }  // extern "C"
